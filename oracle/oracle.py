@@ -1,0 +1,269 @@
+"""ctypes wrapper of the plain C oracle (q4c_oracle.c).  Test infrastructure.
+
+Every function forwards to the C routine of the same name; the docstrings
+name the passage of the paper each one follows.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "q4c_oracle.c")
+_SO = os.path.join(_HERE, "liborc.so")
+_lock = threading.Lock()
+_lib: Optional[C.CDLL] = None
+
+_dp = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
+_ip = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
+_lp = np.ctypeslib.ndpointer(dtype=np.int64, flags="C_CONTIGUOUS")
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (no FMA contraction, no fast-math)."""
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        tmp = _SO + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+                               "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _SO)
+    return _SO
+
+
+class _Basis(C.Structure):
+    _fields_ = [
+        ("n_atoms", C.c_int), ("xyz", C.c_void_p), ("species", C.c_void_p),
+        ("n_species", C.c_int), ("n_rad", C.c_void_p), ("rad_l", C.c_void_p), ("rad_alpha", C.c_void_p),
+        ("n_log", C.c_int), ("r_min", C.c_double), ("r_c", C.c_double), ("r_on", C.c_double),
+        ("tab_u", C.c_void_p), ("tab_M", C.c_void_p), ("analytic", C.c_int),
+    ]
+
+
+def lib() -> C.CDLL:
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = C.CDLL(build())
+            L.orc_gauss_legendre.argtypes = [C.c_int, _dp, _dp]
+            L.orc_radial_shells.argtypes = [C.c_int, C.c_double, _dp, _dp]
+            L.orc_cutoff.argtypes = [C.c_double, C.c_double, C.c_double]
+            L.orc_cutoff.restype = C.c_double
+            L.orc_tabulate.argtypes = [C.c_int, C.c_double, C.c_int, C.c_double, C.c_double, C.c_double,
+                                       _dp, _dp, _dp]
+            L.orc_spline_eval.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, _dp, _dp, C.c_double,
+                                          C.POINTER(C.c_double), C.POINTER(C.c_double)]
+            L.orc_K.argtypes = [C.c_int, C.c_int]
+            L.orc_K.restype = C.c_double
+            L.orc_ylm_spherical.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double]
+            L.orc_ylm_spherical.restype = C.c_double
+            L.orc_solid_harmonic.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, C.c_double,
+                                             C.POINTER(C.c_double), _dp]
+            bp = C.POINTER(_Basis)
+            L.orc_count_functions.argtypes = [bp]
+            L.orc_function_table.argtypes = [bp, _ip, _ip, _ip, _ip]
+            L.orc_basis_eval.argtypes = [bp, C.c_int, _dp, C.c_int, _ip, _dp, _dp]
+            L.orc_becke_weight.argtypes = [C.c_int, _dp, C.c_int, _dp, C.c_double]
+            L.orc_becke_weight.restype = C.c_double
+            L.orc_grid.argtypes = [C.c_int, _dp, C.c_int, C.c_double, C.c_int, C.c_int, C.c_double,
+                                   C.c_double, _dp, _dp, _lp]
+            L.orc_grid.restype = C.c_long
+            L.orc_pattern.argtypes = [bp, C.c_void_p, C.c_void_p, C.c_void_p]
+            L.orc_pattern.restype = C.c_long
+            L.orc_matrix_pairs.argtypes = [bp, C.c_long, _dp, _dp, _dp, C.c_long, _ip, _ip,
+                                           _dp, _dp, _dp, _dp, _dp]
+            L.orc_matrix_blocks.argtypes = [bp, C.c_long, _dp, _dp, _dp, _lp, _ip, _lp,
+                                            _dp, _dp, _dp, _dp, _dp]
+            L.orc_matrix_blocks.restype = C.c_int
+            L.orc_density.argtypes = [bp, C.c_long, _dp, _lp, _ip, _lp, _dp, _dp]
+            vp = C.c_void_p
+            L.orc_adjoint.argtypes = [bp, C.c_long, _dp, _dp, _lp, _ip, _lp, vp, vp, vp, vp, vp, _dp]
+            L.orc_spinor_ss.argtypes = [bp, _lp, _ip, _lp, _dp, _dp, _dp, _dp, _dp]
+            _lib = L
+        return _lib
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+# --------------------------------------------------------------------------
+# quadrature and radial pieces
+# --------------------------------------------------------------------------
+
+def gauss_legendre(n: int):
+    x = np.zeros(n); w = np.zeros(n)
+    lib().orc_gauss_legendre(n, x, w)
+    return x, w
+
+
+def radial_shells(N: int, R: float = 1.0):
+    """Gauss-Chebyshev (2nd kind) shells with Becke's map (integrates F(r) r^2 dr)."""
+    r = np.zeros(N); w = np.zeros(N)
+    lib().orc_radial_shells(N, R, r, w)
+    return r, w
+
+
+def cutoff(r: float, r_on: float = 5.0, r_c: float = 6.0) -> float:
+    return lib().orc_cutoff(r, r_on, r_c)
+
+
+def tabulate(l: int, alpha: float, n: int = 200, r_min: float = 1e-4, r_c: float = 6.0, r_on: float = 5.0):
+    """Knots, knot values u_k and natural-spline second derivatives (Eq. 12 radial)."""
+    r = np.zeros(n); u = np.zeros(n); M = np.zeros(n)
+    rc = lib().orc_tabulate(l, alpha, n, r_min, r_c, r_on, r, u, M)
+    if rc != 0:
+        raise ValueError("tabulate failed")
+    return r, u, M
+
+
+def spline_eval(l: int, u: np.ndarray, M: np.ndarray, r: float, r_min: float = 1e-4, r_c: float = 6.0):
+    a = C.c_double(); b = C.c_double()
+    lib().orc_spline_eval(l, len(u), r_min, r_c, _f64(u), _f64(M), r, C.byref(a), C.byref(b))
+    return a.value, b.value
+
+
+def K_lm(l: int, m: int) -> float:
+    return lib().orc_K(l, m)
+
+
+def ylm_spherical(l: int, m: int, theta: float, phi: float) -> float:
+    """Y_l^m from Eqs. B1-B3 in spherical coordinates."""
+    return lib().orc_ylm_spherical(l, m, theta, phi)
+
+
+def solid_harmonic(l: int, m: int, x: float, y: float, z: float):
+    """S_lm = r^l Y_lm and its Cartesian gradient."""
+    S = C.c_double(); dS = np.zeros(3)
+    lib().orc_solid_harmonic(l, m, x, y, z, C.byref(S), dS)
+    return S.value, dS
+
+
+def becke_weight(centres: np.ndarray, owner: int, p, r_nb: float = 1e300) -> float:
+    c = _f64(centres).reshape(-1)
+    return lib().orc_becke_weight(len(c) // 3, c, owner, _f64(p), r_nb)
+
+
+def grid(wl):
+    """Kept grid points of a workload: (xyz (n,3), w (n,), raw id (n,))."""
+    n_raw = wl.n_raw_points
+    xyz = np.zeros(3 * n_raw); w = np.zeros(n_raw); ids = np.zeros(n_raw, dtype=np.int64)
+    n = lib().orc_grid(wl.n_atoms, _f64(wl.xyz).reshape(-1), wl.n_rad, wl.R, wl.n_theta, wl.n_phi,
+                       wl.r_c, wl.r_nb, xyz, w, ids)
+    return xyz[:3 * n].reshape(n, 3).copy(), w[:n].copy(), ids[:n].copy()
+
+
+# --------------------------------------------------------------------------
+# basis, pattern, matrices
+# --------------------------------------------------------------------------
+
+class Pattern:
+    """CSR block pattern over atoms: block (A, B) iff |R_A - R_B| < 2 r_c."""
+
+    def __init__(self, blk_ptr, blk_col, blk_off):
+        self.blk_ptr = blk_ptr
+        self.blk_col = blk_col
+        self.blk_off = blk_off
+
+    @property
+    def nnz(self) -> int:
+        return int(self.blk_off[-1])
+
+
+class OracleBasis:
+    """Basis of a workload with radial tables built by the oracle itself."""
+
+    def __init__(self, wl, analytic: bool = False):
+        self.wl = wl
+        self._xyz = _f64(wl.xyz).reshape(-1)
+        self._species = np.ascontiguousarray(wl.species_of_atom, dtype=np.int32)
+        self._n_rad = wl.n_rad_per_species
+        self._l = wl.rad_l
+        self._alpha = wl.rad_alpha
+        nr = len(self._l)
+        self.tab_r = np.zeros((nr, wl.n_log)); self.tab_u = np.zeros((nr, wl.n_log))
+        self.tab_M = np.zeros((nr, wl.n_log))
+        for k in range(nr):
+            r, u, M = tabulate(int(self._l[k]), float(self._alpha[k]), wl.n_log, wl.r_min, wl.r_c, wl.r_on)
+            self.tab_r[k] = r; self.tab_u[k] = u; self.tab_M[k] = M
+        self.s = _Basis(wl.n_atoms, self._xyz.ctypes.data, self._species.ctypes.data, len(wl.species),
+                        self._n_rad.ctypes.data, self._l.ctypes.data, self._alpha.ctypes.data, wl.n_log,
+                        wl.r_min, wl.r_c, wl.r_on, self.tab_u.ctypes.data, self.tab_M.ctypes.data,
+                        1 if analytic else 0)
+        self.n_fn = lib().orc_count_functions(C.byref(self.s))
+        self.fn_atom = np.zeros(self.n_fn, np.int32); self.fn_rad = np.zeros(self.n_fn, np.int32)
+        self.fn_l = np.zeros(self.n_fn, np.int32); self.fn_m = np.zeros(self.n_fn, np.int32)
+        lib().orc_function_table(C.byref(self.s), self.fn_atom, self.fn_rad, self.fn_l, self.fn_m)
+
+    def eval(self, pts: np.ndarray, fns: Optional[Sequence[int]] = None):
+        """phi (n_fn, n_pts) and grad (n_fn, n_pts, 3) at points."""
+        pts = _f64(pts).reshape(-1, 3)
+        fns = np.arange(self.n_fn, dtype=np.int32) if fns is None else np.ascontiguousarray(fns, np.int32)
+        phi = np.zeros(len(fns) * len(pts)); grad = np.zeros(len(fns) * len(pts) * 3)
+        lib().orc_basis_eval(C.byref(self.s), len(pts), pts.reshape(-1), len(fns), fns, phi, grad)
+        return phi.reshape(len(fns), len(pts)), grad.reshape(len(fns), len(pts), 3)
+
+    def pattern(self) -> Pattern:
+        nb = lib().orc_pattern(C.byref(self.s), None, None, None)
+        ptr = np.zeros(self.wl.n_atoms + 1, np.int64); col = np.zeros(max(nb, 1), np.int32)
+        off = np.zeros(nb + 1, np.int64)
+        lib().orc_pattern(C.byref(self.s), ptr.ctypes.data, col.ctypes.data, off.ctypes.data)
+        return Pattern(ptr, col[:nb].copy(), off)
+
+    def matrix_pairs(self, xyz, w, v, pi, pj):
+        """V, W0, SOx, SOy, SOz at listed (i, j) pairs (Eqs. 29-30 + the SS reading)."""
+        xyz = _f64(xyz).reshape(-1); w = _f64(w); v = _f64(v)
+        pi = np.ascontiguousarray(pi, np.int32); pj = np.ascontiguousarray(pj, np.int32)
+        outs = [np.zeros(len(pi)) for _ in range(5)]
+        lib().orc_matrix_pairs(C.byref(self.s), len(w), xyz, w, v, len(pi), pi, pj, *outs)
+        return outs
+
+    def matrix_blocks(self, xyz, w, v, pat: Pattern):
+        """Full V, W0, SOx, SOy, SOz on the block pattern."""
+        xyz = _f64(xyz).reshape(-1); w = _f64(w); v = _f64(v)
+        outs = [np.zeros(pat.nnz) for _ in range(5)]
+        miss = lib().orc_matrix_blocks(C.byref(self.s), len(w), xyz, w, v, pat.blk_ptr, pat.blk_col,
+                                       pat.blk_off, *outs)
+        if miss:
+            raise RuntimeError("active atom pair outside the block pattern")
+        return outs
+
+    def density(self, xyz, P, pat: Pattern):
+        """n_p = sum_ij P_ij phi_i phi_j (Eqs. 39-40)."""
+        xyz = _f64(xyz).reshape(-1)
+        n = np.zeros(len(xyz) // 3)
+        lib().orc_density(C.byref(self.s), len(n), xyz, pat.blk_ptr, pat.blk_col, pat.blk_off, _f64(P), n)
+        return n
+
+    def adjoint(self, xyz, w, G, pat: Pattern):
+        """dL/dv_p for L = sum_M <G^M, M>, G = [GV, GW0, GSOx, GSOy, GSOz] (None = 0)."""
+        xyz = _f64(xyz).reshape(-1); w = _f64(w)
+        keep = [None if g is None else _f64(g) for g in G]
+        ptrs = [None if g is None else g.ctypes.data for g in keep]
+        out = np.zeros(len(w))
+        lib().orc_adjoint(C.byref(self.s), len(w), xyz, w, pat.blk_ptr, pat.blk_col, pat.blk_off,
+                          *ptrs, out)
+        return out
+
+    def spinor_ss(self, W0, SOx, SOy, SOz, pat: Pattern):
+        """Complex SS spinor blocks (Eq. 16, kinetic-balance reading), complex128 [4*nnz]."""
+        out = np.zeros(8 * pat.nnz)
+        lib().orc_spinor_ss(C.byref(self.s), pat.blk_ptr, pat.blk_col, pat.blk_off, _f64(W0), _f64(SOx),
+                            _f64(SOy), _f64(SOz), out)
+        return out.view(np.complex128)
+
+    def dense(self, vals, pat: Pattern) -> np.ndarray:
+        """Scatter a block-pattern array into a dense n_fn x n_fn matrix."""
+        nf = self.wl.nf_of_atom
+        first = np.concatenate([[0], np.cumsum(nf)])
+        D = np.zeros((self.n_fn, self.n_fn))
+        for A in range(self.wl.n_atoms):
+            for q in range(int(pat.blk_ptr[A]), int(pat.blk_ptr[A + 1])):
+                B = int(pat.blk_col[q])
+                o = int(pat.blk_off[q])
+                D[first[A]:first[A + 1], first[B]:first[B + 1]] = \
+                    np.asarray(vals[o:o + nf[A] * nf[B]]).reshape(nf[A], nf[B])
+        return D

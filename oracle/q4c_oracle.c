@@ -1,0 +1,750 @@
+/*
+ * q4c_oracle.c -- plain, slow, FP64 CPU oracle for the Q4C real-space
+ * integration path.  TEST INFRASTRUCTURE ONLY: it is used by tests/, by
+ * __graft_entry__.smoke() and by bench.py's cpu_baseline / reference arm,
+ * never by the product path.  It shares no code, header or table with the
+ * CUDA library; the two meet only through the seeded inputs in workloads/.
+ *
+ * Everything here is the definition written out, one loop per sum, with no
+ * batching, screening beyond exact zeros, blocking or reordering:
+ *
+ *   V_ij    = sum_p w_p v_p phi_i(p) phi_j(p)                  (Eqs. 29-30,
+ *             grid sum of a matrix element with F = v)
+ *   W0_ij   = sum_p w_p v_p grad phi_i . grad phi_j            (kinetic-balance
+ *   SOk_ij  = sum_p w_p v_p (grad phi_i x grad phi_j)_k         small-component
+ *             reading of the SS block of Eq. 16: (s.a)(s.b) = a.b + i s.(a x b))
+ *   n_p     = sum_ij P_ij phi_i(p) phi_j(p)                    (Eqs. 39-40)
+ *   dL/dv_p = w_p sum_M sum_ij G^M_ij f^M_ij(p)                (adjoint of the
+ *             linear map v -> (V, W0, SOx, SOy, SOz); the paper has no gradients)
+ *
+ * Basis (Eq. 12a): phi = u_l(r)/r * Y_lm, Y_lm real spherical harmonics of
+ * Appendix B (Eqs. B1-B3) taken literally: the (-1)^m of B1 multiplies an
+ * associated Legendre function defined in B2 without a phase.
+ * Radial functions are tabulated on a logarithmic grid and interpolated by a
+ * natural cubic spline in the grid index (the paper only says "numerically
+ * on one-dimensional logarithmic grids", Eq. 12).
+ * Integration grid: overlapping atom-centred grids with a partition of unity
+ * (Section III A); Becke's partition (Becke 1988, three iterations of
+ * f(mu) = 1.5 mu - 0.5 mu^3), radial Gauss-Chebyshev of the second kind with
+ * Becke's map, angular Gauss-Legendre x uniform product grid.
+ *
+ * Sums use Neumaier's compensated summation in double so that results do
+ * not depend on the host's long double format.
+ *
+ * Parity pins (tests/test_oracle_*.py): Gaussian overlap and kinetic closed
+ * forms, the one-centre erf-potential integral, one-atom spin-orbit radial
+ * integral, Y_lm against scipy's complex harmonics and Eq. 13, orthonormality,
+ * Becke partition of unity, spline against scipy's natural CubicSpline,
+ * symmetry, translation invariance, Tr(PS) = sum_p w_p n_p, adjoint linearity.
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#include <stdint.h>
+
+#ifndef M_PI
+#define M_PI 3.14159265358979323846
+#endif
+
+/* ------------------------------------------------------------------ */
+/* compensated accumulator (Neumaier 1974)                              */
+/* ------------------------------------------------------------------ */
+typedef struct { double s, c; } orc_acc;
+static void acc_add(orc_acc* a, double x) {
+  double t = a->s + x;
+  if (fabs(a->s) >= fabs(x)) a->c += (a->s - t) + x;
+  else a->c += (x - t) + a->s;
+  a->s = t;
+}
+static double acc_get(const orc_acc* a) { return a->s + a->c; }
+
+/* ------------------------------------------------------------------ */
+/* quadrature                                                           */
+/* ------------------------------------------------------------------ */
+
+/* Gauss-Legendre nodes (ascending) and weights on [-1, 1], Newton's method
+ * on P_n with the three-term recurrence. */
+int orc_gauss_legendre(int n, double* x, double* w) {
+  if (n < 1) return -1;
+  for (int i = 0; i < n; ++i) {
+    double z = cos(M_PI * (i + 0.75) / (n + 0.5));
+    double pn = 0.0, pm = 0.0, dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      /* P_n(z) and P_{n-1}(z) by (k) P_k = (2k-1) z P_{k-1} - (k-1) P_{k-2} */
+      pn = z; pm = 1.0;
+      for (int k = 2; k <= n; ++k) {
+        double pk = ((2.0 * k - 1.0) * z * pn - (k - 1.0) * pm) / k;
+        pm = pn; pn = pk;
+      }
+      dp = n * (z * pn - pm) / (z * z - 1.0);
+      double dz = pn / dp;
+      z -= dz;
+      if (fabs(dz) < 1e-16) break;
+    }
+    pn = z; pm = 1.0;
+    for (int k = 2; k <= n; ++k) {
+      double pk = ((2.0 * k - 1.0) * z * pn - (k - 1.0) * pm) / k;
+      pm = pn; pn = pk;
+    }
+    dp = n * (z * pn - pm) / (z * z - 1.0);
+    /* the initial guesses descend; store ascending */
+    x[n - 1 - i] = z;
+    w[n - 1 - i] = 2.0 / ((1.0 - z * z) * dp * dp);
+  }
+  return 0;
+}
+
+/* Radial shells: Gauss-Chebyshev of the second kind, x_i = cos(i pi/(N+1)),
+ * i = 1..N, mapped by r = R (1+x)/(1-x).  The weight integrates
+ * int_0^inf F(r) r^2 dr:  w_i = pi/(N+1) sin(theta_i) r_i^2 2R/(1-x_i)^2. */
+void orc_radial_shells(int N, double R, double* r, double* w) {
+  for (int i = 1; i <= N; ++i) {
+    double th = i * M_PI / (N + 1);
+    double x = cos(th);
+    double ri = R * (1.0 + x) / (1.0 - x);
+    r[i - 1] = ri;
+    w[i - 1] = M_PI / (N + 1) * sin(th) * ri * ri * 2.0 * R / ((1.0 - x) * (1.0 - x));
+  }
+}
+
+/* ------------------------------------------------------------------ */
+/* radial functions                                                     */
+/* ------------------------------------------------------------------ */
+
+/* smooth cutoff: 1 below r_on, 0 from r_c on, quintic smoothstep between */
+double orc_cutoff(double r, double r_on, double r_c) {
+  if (r <= r_on) return 1.0;
+  if (r >= r_c) return 0.0;
+  double s = (r - r_on) / (r_c - r_on);
+  return 1.0 - (10.0 * s * s * s - 15.0 * s * s * s * s + 6.0 * s * s * s * s * s);
+}
+
+/* Knots r_k = r_min (r_c/r_min)^(k/(n-1)), values u_k = r^(l+1) e^(-alpha r^2) c(r),
+ * and the natural cubic spline second derivatives M_k in the index variable
+ * t = k (unit spacing): M_{k-1} + 4 M_k + M_{k+1} = 6 (u_{k+1} - 2u_k + u_{k-1}),
+ * M_0 = M_{n-1} = 0, solved by plain Gaussian elimination of the
+ * tridiagonal system. */
+int orc_tabulate(int l, double alpha, int n, double r_min, double r_c, double r_on,
+                 double* r, double* u, double* M) {
+  if (n < 3) return -1;
+  for (int k = 0; k < n; ++k) {
+    double rk = r_min * pow(r_c / r_min, (double)k / (double)(n - 1));
+    r[k] = rk;
+    u[k] = pow(rk, l + 1) * exp(-alpha * rk * rk) * orc_cutoff(rk, r_on, r_c);
+  }
+  int m = n - 2; /* unknowns M_1..M_{n-2} */
+  double* diag = (double*)malloc(sizeof(double) * m);
+  double* rhs = (double*)malloc(sizeof(double) * m);
+  for (int i = 0; i < m; ++i) {
+    int k = i + 1;
+    diag[i] = 4.0;
+    rhs[i] = 6.0 * (u[k + 1] - 2.0 * u[k] + u[k - 1]);
+  }
+  /* forward elimination with unit off-diagonals */
+  for (int i = 1; i < m; ++i) {
+    double f = 1.0 / diag[i - 1];
+    diag[i] -= f;
+    rhs[i] -= f * rhs[i - 1];
+  }
+  M[0] = 0.0;
+  M[n - 1] = 0.0;
+  M[m] = rhs[m - 1] / diag[m - 1];
+  for (int i = m - 2; i >= 0; --i) M[i + 1] = (rhs[i] - M[i + 2]) / diag[i];
+  free(diag);
+  free(rhs);
+  return 0;
+}
+
+/* Spline value u(r) and du/dr.  t = ln(r/r_min)/h, h = ln(r_c/r_min)/(n-1);
+ * on [k, k+1] with s = t - k:
+ *   u = (1-s) u_k + s u_{k+1} + ((1-s)^3 - (1-s)) M_k/6 + (s^3 - s) M_{k+1}/6.
+ * Below r_min: u = u_0 (r/r_min)^(l+1).  From r_c on: 0. */
+void orc_spline_eval(int l, int n, double r_min, double r_c, const double* u, const double* M,
+                     double r, double* uval, double* dudr) {
+  if (r >= r_c) { *uval = 0.0; *dudr = 0.0; return; }
+  if (r < r_min) {
+    double q = pow(r / r_min, l);
+    *uval = u[0] * q * (r / r_min);
+    *dudr = u[0] * (l + 1) * q / r_min;
+    return;
+  }
+  double h = log(r_c / r_min) / (n - 1);
+  double t = log(r / r_min) / h;
+  int k = (int)floor(t);
+  if (k > n - 2) k = n - 2;
+  if (k < 0) k = 0;
+  double s = t - k, a = 1.0 - s;
+  double val = a * u[k] + s * u[k + 1] + (a * a * a - a) * M[k] / 6.0 + (s * s * s - s) * M[k + 1] / 6.0;
+  double dt = -u[k] + u[k + 1] + (-3.0 * a * a + 1.0) * M[k] / 6.0 + (3.0 * s * s - 1.0) * M[k + 1] / 6.0;
+  *uval = val;
+  *dudr = dt / (h * r);
+}
+
+/* ------------------------------------------------------------------ */
+/* real spherical harmonics, Appendix B                                 */
+/* ------------------------------------------------------------------ */
+
+static double factorial(int k) {
+  double f = 1.0;
+  for (int i = 2; i <= k; ++i) f *= i;
+  return f;
+}
+static double binom(int a, int b) { return factorial(a) / (factorial(b) * factorial(a - b)); }
+
+/* K_l^m of Eq. B3 */
+double orc_K(int l, int m) {
+  int am = abs(m);
+  return sqrt((2.0 * l + 1.0) * factorial(l - am) / (4.0 * M_PI * factorial(l + am)));
+}
+
+/* Coefficients a_k of the m-th derivative of the Legendre polynomial P_l:
+ * d^m/dt^m P_l(t) = sum_k a[k] t^k, k = 0..l-m.  From the explicit sum
+ * P_l(t) = 2^-l sum_j (-1)^j C(l,j) C(2l-2j,l) t^(l-2j). */
+static void legendre_deriv_coeffs(int l, int m, double* a) {
+  for (int k = 0; k <= l; ++k) a[k] = 0.0;
+  for (int j = 0; 2 * j <= l; ++j) {
+    int p = l - 2 * j;
+    if (p < m) continue;
+    double c = ldexp(1.0, -l) * ((j & 1) ? -1.0 : 1.0) * binom(l, j) * binom(2 * l - 2 * j, l);
+    c *= factorial(p) / factorial(p - m);
+    a[p - m] += c;
+  }
+}
+
+static double ipow(double x, int k) {
+  double r = 1.0;
+  for (int i = 0; i < k; ++i) r *= x;
+  return r;
+}
+
+/* Y_l^m(theta, phi) straight from Eqs. B1-B3 (used by the pins). */
+double orc_ylm_spherical(int l, int m, double theta, double phi) {
+  int am = abs(m);
+  double a[16];
+  legendre_deriv_coeffs(l, am, a);
+  double ct = cos(theta), st = sin(theta);
+  double dP = 0.0;
+  for (int k = 0; k <= l - am; ++k) dP += a[k] * ipow(ct, k);
+  double Plm = ipow(st, am) * dP; /* Eq. B2: (sin)^m d^m/dx^m P_l */
+  double sgn = (am & 1) ? -1.0 : 1.0;
+  if (m > 0) return sgn * sqrt(2.0) * orc_K(l, m) * cos(m * phi) * Plm;
+  if (m == 0) return orc_K(l, 0) * Plm;
+  return sgn * sqrt(2.0) * orc_K(l, m) * sin(am * phi) * Plm;
+}
+
+/* Solid harmonic S_lm = r^l Y_lm and its Cartesian gradient.
+ * r^l Y_lm = N * A_m(x,y) * Pi_lm(z, r^2) with
+ *   A_m = Re (x+iy)^|m| (m > 0), Im (x+iy)^|m| (m < 0), 1 (m = 0),
+ *   Pi  = r^(l-|m|) (d^|m| P_l)(z/r) = sum_k a_k z^k (r^2)^((l-|m|-k)/2),
+ *   N   = (-1)^m sqrt(2) K_l^m (m != 0), K_l^0 (m = 0). */
+void orc_solid_harmonic(int l, int m, double x, double y, double z, double* S, double* dS) {
+  int am = abs(m);
+  double a[16];
+  legendre_deriv_coeffs(l, am, a);
+  double rho = x * x + y * y + z * z;
+  /* A_m and its partials via (x+iy)^m recurrences */
+  double C = 1.0, Sn = 0.0, Cm1 = 0.0, Sm1 = 0.0;
+  for (int k = 1; k <= am; ++k) {
+    Cm1 = C; Sm1 = Sn;
+    double c2 = x * C - y * Sn, s2 = x * Sn + y * C;
+    C = c2; Sn = s2;
+  }
+  double A, Ax, Ay;
+  if (m > 0) { A = C; Ax = am * Cm1; Ay = -am * Sm1; }
+  else if (m < 0) { A = Sn; Ax = am * Sm1; Ay = am * Cm1; }
+  else { A = 1.0; Ax = 0.0; Ay = 0.0; }
+  int q = l - am;
+  double Pi = 0.0, dPi_drho = 0.0, dPi_dz = 0.0;
+  for (int k = 0; k <= q; ++k) {
+    if (a[k] == 0.0) continue;
+    int e = (q - k) / 2; /* (q-k) is even whenever a[k] != 0 */
+    Pi += a[k] * ipow(z, k) * ipow(rho, e);
+    if (e > 0) dPi_drho += a[k] * ipow(z, k) * e * ipow(rho, e - 1);
+    if (k > 0) dPi_dz += a[k] * k * ipow(z, k - 1) * ipow(rho, e);
+  }
+  double N = (m == 0) ? orc_K(l, 0) : (((am & 1) ? -1.0 : 1.0) * sqrt(2.0) * orc_K(l, m));
+  *S = N * A * Pi;
+  dS[0] = N * (Ax * Pi + A * dPi_drho * 2.0 * x);
+  dS[1] = N * (Ay * Pi + A * dPi_drho * 2.0 * y);
+  dS[2] = N * (A * (dPi_dz + dPi_drho * 2.0 * z));
+}
+
+/* ------------------------------------------------------------------ */
+/* basis                                                                */
+/* ------------------------------------------------------------------ */
+
+typedef struct {
+  int n_atoms;
+  const double* xyz;        /* [n_atoms][3] Bohr */
+  const int* species;       /* [n_atoms] */
+  int n_species;
+  const int* n_rad;         /* [n_species] radial functions per species */
+  const int* rad_l;         /* [sum n_rad] species-major */
+  const double* rad_alpha;  /* [sum n_rad] */
+  int n_log;
+  double r_min, r_c, r_on;
+  const double* tab_u;      /* [sum n_rad][n_log] knot values (spline mode) */
+  const double* tab_M;      /* [sum n_rad][n_log] second derivatives */
+  int analytic;             /* 1: u = r^(l+1) exp(-alpha r^2), no cutoff (closed-form pins) */
+} orc_basis;
+
+/* Function table: atom a, radial k of its species, m = -l..l (radial-major). */
+int orc_count_functions(const orc_basis* b) {
+  int n = 0;
+  for (int a = 0; a < b->n_atoms; ++a) {
+    int s = b->species[a], off = 0;
+    for (int t = 0; t < s; ++t) off += b->n_rad[t];
+    for (int k = 0; k < b->n_rad[s]; ++k) n += 2 * b->rad_l[off + k] + 1;
+  }
+  return n;
+}
+void orc_function_table(const orc_basis* b, int* fn_atom, int* fn_rad, int* fn_l, int* fn_m) {
+  int n = 0;
+  for (int a = 0; a < b->n_atoms; ++a) {
+    int s = b->species[a], off = 0;
+    for (int t = 0; t < s; ++t) off += b->n_rad[t];
+    for (int k = 0; k < b->n_rad[s]; ++k) {
+      int l = b->rad_l[off + k];
+      for (int m = -l; m <= l; ++m) {
+        fn_atom[n] = a; fn_rad[n] = off + k; fn_l[n] = l; fn_m[n] = m; ++n;
+      }
+    }
+  }
+}
+
+/* g(r) = u(r)/r^(l+1) and g'(r) */
+static void radial_g(const orc_basis* b, int rad, int l, double r, double* g, double* gp) {
+  if (b->analytic) {
+    if (r >= b->r_c) { *g = 0.0; *gp = 0.0; return; }
+    double al = b->rad_alpha[rad];
+    double e = exp(-al * r * r);
+    *g = e;
+    *gp = -2.0 * al * r * e;
+    return;
+  }
+  if (r >= b->r_c) { *g = 0.0; *gp = 0.0; return; }
+  const double* u = b->tab_u + (size_t)rad * b->n_log;
+  const double* M = b->tab_M + (size_t)rad * b->n_log;
+  if (r < b->r_min) { /* u = u_0 (r/r_min)^(l+1): g constant */
+    *g = u[0] / ipow(b->r_min, l + 1);
+    *gp = 0.0;
+    return;
+  }
+  double uv, du;
+  orc_spline_eval(l, b->n_log, b->r_min, b->r_c, u, M, r, &uv, &du);
+  double rl1 = ipow(r, l + 1);
+  *g = uv / rl1;
+  *gp = (du - (l + 1) * uv / r) / rl1;
+}
+
+/* phi_i and grad phi_i at point p for the function centred at atom position c */
+static void phi_at(const orc_basis* b, int rad, int l, int m, const double c[3], const double p[3],
+                   double* phi, double grad[3]) {
+  double d[3] = {p[0] - c[0], p[1] - c[1], p[2] - c[2]};
+  double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+  if (r >= b->r_c) { *phi = 0.0; grad[0] = grad[1] = grad[2] = 0.0; return; }
+  double g, gp, S, dS[3];
+  radial_g(b, rad, l, r, &g, &gp);
+  orc_solid_harmonic(l, m, d[0], d[1], d[2], &S, dS);
+  *phi = g * S;
+  for (int k = 0; k < 3; ++k) grad[k] = (r > 0.0 ? gp * d[k] / r * S : 0.0) + g * dS[k];
+}
+
+/* evaluate one basis function (global index, centred in the 0-cell) at points */
+void orc_basis_eval(const orc_basis* b, int n_pts, const double* xyz, int n_fn, const int* fns,
+                    double* phi, double* grad) {
+  int nf = orc_count_functions(b);
+  int* fa = (int*)malloc(sizeof(int) * nf);
+  int* fr = (int*)malloc(sizeof(int) * nf);
+  int* fl = (int*)malloc(sizeof(int) * nf);
+  int* fm = (int*)malloc(sizeof(int) * nf);
+  orc_function_table(b, fa, fr, fl, fm);
+  for (int q = 0; q < n_fn; ++q) {
+    int i = fns[q];
+    for (int p = 0; p < n_pts; ++p) {
+      phi_at(b, fr[i], fl[i], fm[i], b->xyz + 3 * fa[i], xyz + 3 * (size_t)p,
+             &phi[(size_t)q * n_pts + p], &grad[((size_t)q * n_pts + p) * 3]);
+    }
+  }
+  free(fa); free(fr); free(fl); free(fm);
+}
+
+/* ------------------------------------------------------------------ */
+/* integration grid and Becke partition                                 */
+/* ------------------------------------------------------------------ */
+
+static double becke_s(double mu) {
+  double f = mu;
+  for (int k = 0; k < 3; ++k) f = 1.5 * f - 0.5 * f * f * f;
+  return 0.5 * (1.0 - f);
+}
+
+/* Becke weight p_owner(r) over the neighbour set N(r) = {B : |r - R_B| < r_nb}.
+ * centres: [n_c][3] (atoms, and periodic images if any). */
+double orc_becke_weight(int n_c, const double* centres, int owner, const double p[3], double r_nb) {
+  if (owner < 0 || owner >= n_c) return 0.0;
+  double* dist = (double*)malloc(sizeof(double) * n_c);
+  int* in = (int*)calloc(n_c, sizeof(int));
+  for (int B = 0; B < n_c; ++B) {
+    double dx = p[0] - centres[3 * B], dy = p[1] - centres[3 * B + 1], dz = p[2] - centres[3 * B + 2];
+    dist[B] = sqrt(dx * dx + dy * dy + dz * dz);
+    in[B] = dist[B] < r_nb;
+  }
+  double result = 0.0;
+  if (in[owner]) {
+    double sum = 0.0, Pown = 0.0;
+    for (int A = 0; A < n_c; ++A) {
+      if (!in[A]) continue;
+      double PA = 1.0;
+      for (int B = 0; B < n_c; ++B) {
+        if (B == A || !in[B]) continue;
+        double dx = centres[3 * A] - centres[3 * B], dy = centres[3 * A + 1] - centres[3 * B + 1],
+               dz = centres[3 * A + 2] - centres[3 * B + 2];
+        double RAB = sqrt(dx * dx + dy * dy + dz * dz);
+        PA *= becke_s((dist[A] - dist[B]) / RAB);
+      }
+      sum += PA;
+      if (A == owner) Pown = PA;
+    }
+    result = Pown / sum;
+  }
+  free(dist);
+  free(in);
+  return result;
+}
+
+/* Raw grid of every atom, Becke weights, pruning.
+ * Raw point id = ((atom*n_rad + i)*n_theta + a)*n_phi + b; i radial shell
+ * (ascending x_i order, i.e. decreasing r), a Gauss-Legendre node in cos(theta)
+ * (ascending), b azimuth phi_b = (b + 1/2) 2 pi / n_phi.
+ * Keep p iff some atom lies strictly within r_c of p and w_p != 0.
+ * Returns the number of kept points; out arrays must hold the raw count. */
+long orc_grid(int n_atoms, const double* xyz, int n_rad, double R, int n_theta, int n_phi,
+              double r_c, double r_nb, double* out_xyz, double* out_w, long long* out_id) {
+  double* rr = (double*)malloc(sizeof(double) * n_rad);
+  double* wr = (double*)malloc(sizeof(double) * n_rad);
+  double* ct = (double*)malloc(sizeof(double) * n_theta);
+  double* wt = (double*)malloc(sizeof(double) * n_theta);
+  orc_radial_shells(n_rad, R, rr, wr);
+  orc_gauss_legendre(n_theta, ct, wt);
+  long kept = 0;
+  for (int A = 0; A < n_atoms; ++A) {
+    for (int i = 0; i < n_rad; ++i) {
+      for (int a = 0; a < n_theta; ++a) {
+        double st = sqrt(1.0 - ct[a] * ct[a]);
+        for (int bb = 0; bb < n_phi; ++bb) {
+          double ph = (bb + 0.5) * 2.0 * M_PI / n_phi;
+          double p[3] = {xyz[3 * A] + rr[i] * st * cos(ph), xyz[3 * A + 1] + rr[i] * st * sin(ph),
+                         xyz[3 * A + 2] + rr[i] * ct[a]};
+          int near = 0;
+          for (int B = 0; B < n_atoms && !near; ++B) {
+            double dx = p[0] - xyz[3 * B], dy = p[1] - xyz[3 * B + 1], dz = p[2] - xyz[3 * B + 2];
+            if (sqrt(dx * dx + dy * dy + dz * dz) < r_c) near = 1;
+          }
+          if (!near) continue;
+          double w = wr[i] * wt[a] * (2.0 * M_PI / n_phi) * orc_becke_weight(n_atoms, xyz, A, p, r_nb);
+          if (w == 0.0) continue;
+          out_xyz[3 * kept] = p[0]; out_xyz[3 * kept + 1] = p[1]; out_xyz[3 * kept + 2] = p[2];
+          out_w[kept] = w;
+          out_id[kept] = (((long long)A * n_rad + i) * n_theta + a) * n_phi + bb;
+          ++kept;
+        }
+      }
+    }
+  }
+  free(rr); free(wr); free(ct); free(wt);
+  return kept;
+}
+
+/* ------------------------------------------------------------------ */
+/* block pattern (molecule): block (A,B) iff |R_A - R_B| < 2 r_c         */
+/* CSR over atom rows; blocks dense row-major nf_A x nf_B                */
+/* ------------------------------------------------------------------ */
+static int species_nfn(const orc_basis* b, int s) {
+  int off = 0, n = 0;
+  for (int t = 0; t < s; ++t) off += b->n_rad[t];
+  for (int k = 0; k < b->n_rad[s]; ++k) n += 2 * b->rad_l[off + k] + 1;
+  return n;
+}
+
+/* returns number of blocks; if blk_ptr != NULL fills CSR (blk_ptr[n_atoms+1],
+ * blk_col[nb], blk_off[nb+1]) */
+long orc_pattern(const orc_basis* b, long long* blk_ptr, int* blk_col, long long* blk_off) {
+  long nb = 0;
+  long long off = 0;
+  if (blk_ptr) blk_ptr[0] = 0;
+  for (int A = 0; A < b->n_atoms; ++A) {
+    for (int B = 0; B < b->n_atoms; ++B) {
+      double dx = b->xyz[3 * A] - b->xyz[3 * B], dy = b->xyz[3 * A + 1] - b->xyz[3 * B + 1],
+             dz = b->xyz[3 * A + 2] - b->xyz[3 * B + 2];
+      if (sqrt(dx * dx + dy * dy + dz * dz) < 2.0 * b->r_c) {
+        if (blk_col) {
+          blk_col[nb] = B;
+          blk_off[nb] = off;
+        }
+        off += (long long)species_nfn(b, b->species[A]) * species_nfn(b, b->species[B]);
+        ++nb;
+      }
+    }
+    if (blk_ptr) blk_ptr[A + 1] = nb;
+  }
+  if (blk_off) blk_off[nb] = off;
+  return nb;
+}
+
+/* ------------------------------------------------------------------ */
+/* per-point evaluation of all functions (zero where inactive)          */
+/* ------------------------------------------------------------------ */
+typedef struct {
+  int nf;
+  int *fa, *fr, *fl, *fm, *afirst; /* afirst[atom] = first function index */
+} ftab;
+
+static void ftab_init(const orc_basis* b, ftab* t) {
+  t->nf = orc_count_functions(b);
+  t->fa = (int*)malloc(sizeof(int) * (t->nf + 1));
+  t->fr = (int*)malloc(sizeof(int) * (t->nf + 1));
+  t->fl = (int*)malloc(sizeof(int) * (t->nf + 1));
+  t->fm = (int*)malloc(sizeof(int) * (t->nf + 1));
+  t->afirst = (int*)malloc(sizeof(int) * (b->n_atoms + 1));
+  orc_function_table(b, t->fa, t->fr, t->fl, t->fm);
+  int i = 0;
+  for (int a = 0; a <= b->n_atoms; ++a) {
+    while (i < t->nf && t->fa[i] < a) ++i;
+    t->afirst[a] = i;
+  }
+}
+static void ftab_free(ftab* t) { free(t->fa); free(t->fr); free(t->fl); free(t->fm); free(t->afirst); }
+
+static void eval_all(const orc_basis* b, const ftab* t, const double p[3], double* phi, double* grad) {
+  for (int i = 0; i < t->nf; ++i)
+    phi_at(b, t->fr[i], t->fl[i], t->fm[i], b->xyz + 3 * t->fa[i], p, &phi[i], &grad[3 * i]);
+}
+
+/* ------------------------------------------------------------------ */
+/* matrix elements                                                      */
+/* ------------------------------------------------------------------ */
+
+/* Listed pairs (global function indices): out arrays [n_pairs]. */
+void orc_matrix_pairs(const orc_basis* b, long n_pts, const double* xyz, const double* w, const double* v,
+                      long n_pairs, const int* pi, const int* pj,
+                      double* V, double* W0, double* SOx, double* SOy, double* SOz) {
+  ftab t;
+  ftab_init(b, &t);
+  /* unique functions touched */
+  int* used = (int*)calloc(t.nf, sizeof(int));
+  for (long q = 0; q < n_pairs; ++q) { used[pi[q]] = 1; used[pj[q]] = 1; }
+  int nu = 0;
+  int* list = (int*)malloc(sizeof(int) * t.nf);
+  for (int i = 0; i < t.nf; ++i) if (used[i]) list[nu++] = i;
+  double* phi = (double*)calloc(t.nf, sizeof(double));
+  double* grad = (double*)calloc(3 * (size_t)t.nf, sizeof(double));
+  orc_acc* acc = (orc_acc*)calloc(5 * (size_t)n_pairs, sizeof(orc_acc));
+  for (long p = 0; p < n_pts; ++p) {
+    const double* P = xyz + 3 * p;
+    for (int q = 0; q < nu; ++q) {
+      int i = list[q];
+      phi_at(b, t.fr[i], t.fl[i], t.fm[i], b->xyz + 3 * t.fa[i], P, &phi[i], &grad[3 * i]);
+    }
+    double wv = w[p] * v[p];
+    for (long q = 0; q < n_pairs; ++q) {
+      int i = pi[q], j = pj[q];
+      const double* a = &grad[3 * i];
+      const double* c = &grad[3 * j];
+      acc_add(&acc[5 * q + 0], wv * (phi[i] * phi[j]));
+      acc_add(&acc[5 * q + 1], wv * (a[0] * c[0] + a[1] * c[1] + a[2] * c[2]));
+      acc_add(&acc[5 * q + 2], wv * (a[1] * c[2] - a[2] * c[1]));
+      acc_add(&acc[5 * q + 3], wv * (a[2] * c[0] - a[0] * c[2]));
+      acc_add(&acc[5 * q + 4], wv * (a[0] * c[1] - a[1] * c[0]));
+    }
+  }
+  for (long q = 0; q < n_pairs; ++q) {
+    V[q] = acc_get(&acc[5 * q + 0]);
+    W0[q] = acc_get(&acc[5 * q + 1]);
+    SOx[q] = acc_get(&acc[5 * q + 2]);
+    SOy[q] = acc_get(&acc[5 * q + 3]);
+    SOz[q] = acc_get(&acc[5 * q + 4]);
+  }
+  free(used); free(list); free(phi); free(grad); free(acc);
+  ftab_free(&t);
+}
+
+/* locate block (A,B) in the CSR pattern, -1 if absent */
+static long find_block(const long long* blk_ptr, const int* blk_col, int A, int B) {
+  for (long long q = blk_ptr[A]; q < blk_ptr[A + 1]; ++q)
+    if (blk_col[q] == B) return (long)q;
+  return -1;
+}
+
+/* Full matrices on the block pattern: outputs [blk_off[nb]] each. */
+int orc_matrix_blocks(const orc_basis* b, long n_pts, const double* xyz, const double* w, const double* v,
+                      const long long* blk_ptr, const int* blk_col, const long long* blk_off,
+                      double* V, double* W0, double* SOx, double* SOy, double* SOz) {
+  ftab t;
+  ftab_init(b, &t);
+  long long nnz = blk_off[blk_ptr[b->n_atoms]];
+  orc_acc* acc = (orc_acc*)calloc(5 * (size_t)nnz, sizeof(orc_acc));
+  double* phi = (double*)calloc(t.nf, sizeof(double));
+  double* grad = (double*)calloc(3 * (size_t)t.nf, sizeof(double));
+  int* act = (int*)malloc(sizeof(int) * b->n_atoms);
+  int missing = 0;
+  for (long p = 0; p < n_pts; ++p) {
+    const double* P = xyz + 3 * p;
+    eval_all(b, &t, P, phi, grad);
+    int na = 0;
+    for (int A = 0; A < b->n_atoms; ++A) {
+      double dx = P[0] - b->xyz[3 * A], dy = P[1] - b->xyz[3 * A + 1], dz = P[2] - b->xyz[3 * A + 2];
+      if (sqrt(dx * dx + dy * dy + dz * dz) < b->r_c) act[na++] = A;
+    }
+    double wv = w[p] * v[p];
+    for (int ia = 0; ia < na; ++ia) {
+      for (int ib = 0; ib < na; ++ib) {
+        int A = act[ia], B = act[ib];
+        long q = find_block(blk_ptr, blk_col, A, B);
+        if (q < 0) { missing = 1; continue; }
+        int nfB = t.afirst[B + 1] - t.afirst[B];
+        for (int i = t.afirst[A]; i < t.afirst[A + 1]; ++i) {
+          for (int j = t.afirst[B]; j < t.afirst[B + 1]; ++j) {
+            long long e = blk_off[q] + (long long)(i - t.afirst[A]) * nfB + (j - t.afirst[B]);
+            const double* a = &grad[3 * i];
+            const double* c = &grad[3 * j];
+            acc_add(&acc[5 * e + 0], wv * (phi[i] * phi[j]));
+            acc_add(&acc[5 * e + 1], wv * (a[0] * c[0] + a[1] * c[1] + a[2] * c[2]));
+            acc_add(&acc[5 * e + 2], wv * (a[1] * c[2] - a[2] * c[1]));
+            acc_add(&acc[5 * e + 3], wv * (a[2] * c[0] - a[0] * c[2]));
+            acc_add(&acc[5 * e + 4], wv * (a[0] * c[1] - a[1] * c[0]));
+          }
+        }
+      }
+    }
+  }
+  for (long long e = 0; e < nnz; ++e) {
+    V[e] = acc_get(&acc[5 * e + 0]);
+    W0[e] = acc_get(&acc[5 * e + 1]);
+    SOx[e] = acc_get(&acc[5 * e + 2]);
+    SOy[e] = acc_get(&acc[5 * e + 3]);
+    SOz[e] = acc_get(&acc[5 * e + 4]);
+  }
+  free(acc); free(phi); free(grad); free(act);
+  ftab_free(&t);
+  return missing;
+}
+
+/* Density n_p = sum_ij P_ij phi_i phi_j with P on the block pattern (Eq. 39). */
+void orc_density(const orc_basis* b, long n_pts, const double* xyz,
+                 const long long* blk_ptr, const int* blk_col, const long long* blk_off,
+                 const double* P, double* n_out) {
+  ftab t;
+  ftab_init(b, &t);
+  double* phi = (double*)calloc(t.nf, sizeof(double));
+  double* grad = (double*)calloc(3 * (size_t)t.nf, sizeof(double));
+  int* act = (int*)malloc(sizeof(int) * b->n_atoms);
+  for (long p = 0; p < n_pts; ++p) {
+    const double* X = xyz + 3 * p;
+    int na = 0;
+    for (int A = 0; A < b->n_atoms; ++A) {
+      double dx = X[0] - b->xyz[3 * A], dy = X[1] - b->xyz[3 * A + 1], dz = X[2] - b->xyz[3 * A + 2];
+      if (sqrt(dx * dx + dy * dy + dz * dz) < b->r_c) act[na++] = A;
+    }
+    for (int ia = 0; ia < na; ++ia) {
+      int A = act[ia];
+      for (int i = t.afirst[A]; i < t.afirst[A + 1]; ++i)
+        phi_at(b, t.fr[i], t.fl[i], t.fm[i], b->xyz + 3 * A, X, &phi[i], &grad[3 * i]);
+    }
+    orc_acc acc = {0.0, 0.0};
+    for (int ia = 0; ia < na; ++ia) {
+      for (int ib = 0; ib < na; ++ib) {
+        int A = act[ia], B = act[ib];
+        long q = find_block(blk_ptr, blk_col, A, B);
+        if (q < 0) continue;
+        int nfB = t.afirst[B + 1] - t.afirst[B];
+        for (int i = t.afirst[A]; i < t.afirst[A + 1]; ++i)
+          for (int j = t.afirst[B]; j < t.afirst[B + 1]; ++j)
+            acc_add(&acc, P[blk_off[q] + (long long)(i - t.afirst[A]) * nfB + (j - t.afirst[B])] * phi[i] * phi[j]);
+      }
+    }
+    n_out[p] = acc_get(&acc);
+  }
+  free(phi); free(grad); free(act);
+  ftab_free(&t);
+}
+
+/* Adjoint: dL/dv_p = w_p sum_M sum_ij G^M_ij f^M_ij(p), M = V, W0, SOx, SOy, SOz,
+ * each G^M on the block pattern (a NULL slot counts as zero). */
+void orc_adjoint(const orc_basis* b, long n_pts, const double* xyz, const double* w,
+                 const long long* blk_ptr, const int* blk_col, const long long* blk_off,
+                 const double* GV, const double* GW, const double* Gx, const double* Gy, const double* Gz,
+                 double* dLdv) {
+  ftab t;
+  ftab_init(b, &t);
+  double* phi = (double*)calloc(t.nf, sizeof(double));
+  double* grad = (double*)calloc(3 * (size_t)t.nf, sizeof(double));
+  int* act = (int*)malloc(sizeof(int) * b->n_atoms);
+  for (long p = 0; p < n_pts; ++p) {
+    const double* X = xyz + 3 * p;
+    int na = 0;
+    for (int A = 0; A < b->n_atoms; ++A) {
+      double dx = X[0] - b->xyz[3 * A], dy = X[1] - b->xyz[3 * A + 1], dz = X[2] - b->xyz[3 * A + 2];
+      if (sqrt(dx * dx + dy * dy + dz * dz) < b->r_c) act[na++] = A;
+    }
+    for (int ia = 0; ia < na; ++ia) {
+      int A = act[ia];
+      for (int i = t.afirst[A]; i < t.afirst[A + 1]; ++i)
+        phi_at(b, t.fr[i], t.fl[i], t.fm[i], b->xyz + 3 * A, X, &phi[i], &grad[3 * i]);
+    }
+    orc_acc acc = {0.0, 0.0};
+    for (int ia = 0; ia < na; ++ia) {
+      for (int ib = 0; ib < na; ++ib) {
+        int A = act[ia], B = act[ib];
+        long q = find_block(blk_ptr, blk_col, A, B);
+        if (q < 0) continue;
+        int nfB = t.afirst[B + 1] - t.afirst[B];
+        for (int i = t.afirst[A]; i < t.afirst[A + 1]; ++i) {
+          for (int j = t.afirst[B]; j < t.afirst[B + 1]; ++j) {
+            long long e = blk_off[q] + (long long)(i - t.afirst[A]) * nfB + (j - t.afirst[B]);
+            const double* a = &grad[3 * i];
+            const double* c = &grad[3 * j];
+            if (GV) acc_add(&acc, GV[e] * phi[i] * phi[j]);
+            if (GW) acc_add(&acc, GW[e] * (a[0] * c[0] + a[1] * c[1] + a[2] * c[2]));
+            if (Gx) acc_add(&acc, Gx[e] * (a[1] * c[2] - a[2] * c[1]));
+            if (Gy) acc_add(&acc, Gy[e] * (a[2] * c[0] - a[0] * c[2]));
+            if (Gz) acc_add(&acc, Gz[e] * (a[0] * c[1] - a[1] * c[0]));
+          }
+        }
+      }
+    }
+    dLdv[p] = w[p] * acc_get(&acc);
+  }
+  free(phi); free(grad); free(act);
+  ftab_free(&t);
+}
+
+/* Spinor SS block assembly (Eq. 16 with the kinetic-balance reading):
+ * each scalar element (i,j) becomes the 2x2 complex block
+ *   [[W0 + i SOz,  SOy + i SOx], [-SOy + i SOx, W0 - i SOz]],
+ * stored per pattern block as a row-major (2 nf_A) x (2 nf_B) complex matrix
+ * with row 2i+s, column 2j+s' (interleaved re, im doubles). */
+void orc_spinor_ss(const orc_basis* b, const long long* blk_ptr, const int* blk_col, const long long* blk_off,
+                   const double* W0, const double* SOx, const double* SOy, const double* SOz, double* SS) {
+  for (int A = 0; A < b->n_atoms; ++A) {
+    int nfA = species_nfn(b, b->species[A]);
+    for (long long q = blk_ptr[A]; q < blk_ptr[A + 1]; ++q) {
+      int B = blk_col[q];
+      int nfB = species_nfn(b, b->species[B]);
+      for (int i = 0; i < nfA; ++i) {
+        for (int j = 0; j < nfB; ++j) {
+          long long e = blk_off[q] + (long long)i * nfB + j;
+          double w0 = W0[e], x = SOx[e], y = SOy[e], z = SOz[e];
+          /* complex entries (re, im) of the 2x2 block */
+          double blk[2][2][2] = {{{w0, z}, {y, x}}, {{-y, x}, {w0, -z}}};
+          for (int s = 0; s < 2; ++s)
+            for (int s2 = 0; s2 < 2; ++s2) {
+              long long o = 4 * blk_off[q] + (long long)(2 * i + s) * (2 * nfB) + (2 * j + s2);
+              SS[2 * o] = blk[s][s2][0];
+              SS[2 * o + 1] = blk[s][s2][1];
+            }
+        }
+      }
+    }
+  }
+}

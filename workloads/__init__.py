@@ -1,0 +1,253 @@
+"""Seeded synthetic inputs shared by the oracle and the CUDA path.
+
+This module holds none of the method's arithmetic.  It only draws and
+describes inputs:
+
+* geometries (atoms, species, nuclear charges) and basis rules
+  (radial functions per species: angular momentum l and a Gaussian exponent);
+* grid and batching parameters;
+* the input potential v(r) = sum_A -Z_A erf(|r - R_A|)/|r - R_A| evaluated at
+  whatever points a caller passes (an operator F = v of Eqs. 29-30);
+* random block-sparse matrices (density matrix P, adjoint seeds G) drawn per
+  atom-pair block with a counter-based generator (numpy Philox keyed by
+  seed, kind and the atom pair), so that any side that knows the block pattern
+  gets identical values without sharing code or files.
+
+Units: Bohr, Hartree.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import List, Optional
+
+import numpy as np
+
+# --------------------------------------------------------------------------
+# workload description
+# --------------------------------------------------------------------------
+
+
+@dataclasses.dataclass
+class Species:
+    name: str
+    Z: float
+    l: List[int]          # angular momentum of each radial function
+    alpha: List[float]    # Gaussian exponent of each radial function
+
+    @property
+    def n_fn(self) -> int:
+        return sum(2 * l + 1 for l in self.l)
+
+
+@dataclasses.dataclass
+class Workload:
+    name: str
+    xyz: np.ndarray               # (n_atoms, 3) Bohr
+    species_of_atom: np.ndarray   # (n_atoms,) int32 index into species
+    species: List[Species]
+    # radial tabulation
+    r_c: float = 6.0
+    r_on: float = 5.0
+    r_min: float = 1e-4
+    n_log: int = 200
+    # integration grid (per atom) and batching
+    n_rad: int = 30
+    R: float = 1.0
+    n_theta: int = 8
+    n_phi: int = 16
+    r_nb: float = 12.0
+    batch_max: int = 128
+
+    @property
+    def n_atoms(self) -> int:
+        return int(self.xyz.shape[0])
+
+    @property
+    def Z_of_atom(self) -> np.ndarray:
+        return np.array([self.species[s].Z for s in self.species_of_atom], dtype=np.float64)
+
+    @property
+    def nf_of_atom(self) -> np.ndarray:
+        return np.array([self.species[s].n_fn for s in self.species_of_atom], dtype=np.int64)
+
+    @property
+    def n_basis(self) -> int:
+        return int(self.nf_of_atom.sum())
+
+    # flat species-major radial arrays (the layout both sides consume)
+    @property
+    def n_rad_per_species(self) -> np.ndarray:
+        return np.array([len(s.l) for s in self.species], dtype=np.int32)
+
+    @property
+    def rad_l(self) -> np.ndarray:
+        return np.array([l for s in self.species for l in s.l], dtype=np.int32)
+
+    @property
+    def rad_alpha(self) -> np.ndarray:
+        return np.array([a for s in self.species for a in s.alpha], dtype=np.float64)
+
+    @property
+    def n_raw_points(self) -> int:
+        return self.n_atoms * self.n_rad * self.n_theta * self.n_phi
+
+    def translated(self, shift) -> "Workload":
+        return dataclasses.replace(self, xyz=self.xyz + np.asarray(shift, dtype=np.float64)[None, :])
+
+
+def _draw_alphas(rng: np.random.Generator, n: int) -> List[float]:
+    """Exponents log-uniform in [0.1, 10]."""
+    return [float(10.0 ** rng.uniform(-1.0, 1.0)) for _ in range(n)]
+
+
+# --------------------------------------------------------------------------
+# configurations
+# --------------------------------------------------------------------------
+
+LIGHT_MIX_L = {"O": [0, 0, 0, 1, 1, 2], "H": [0, 0, 1]}        # 3s2p1d = 14, 2s1p = 5
+HEAVY_L = [0, 0, 1, 1, 2, 3]                                     # 2s2p1d1f = 20
+LIGHT_L = [0, 0, 1]                                              # 2s1p = 5
+
+
+def water(seed: int = 1001, n_rad: int = 30, n_theta: int = 8, n_phi: int = 16,
+          batch_max: int = 128) -> Workload:
+    """Three atoms: Z=8 at the origin, Z=1 at (+-1.43, 1.11, 0) Bohr.
+    O carries 3s2p1d (14 functions), H 2s1p (5), 24 in total; exponents
+    log-uniform in [0.1, 10] drawn species by species from `seed`;
+    30 radial shells x (8 x 16) angular points per atom; batches <= 128."""
+    rng = np.random.default_rng(seed)
+    sp = [Species("O", 8.0, LIGHT_MIX_L["O"], _draw_alphas(rng, 6)),
+          Species("H", 1.0, LIGHT_MIX_L["H"], _draw_alphas(rng, 3))]
+    xyz = np.array([[0.0, 0.0, 0.0], [1.43, 1.11, 0.0], [-1.43, 1.11, 0.0]])
+    return Workload("water-3atom", xyz, np.array([0, 1, 1], dtype=np.int32), sp,
+                    n_rad=n_rad, n_theta=n_theta, n_phi=n_phi, batch_max=batch_max)
+
+
+def _place(rng: np.random.Generator, n: int, box: float, min_sep: float) -> np.ndarray:
+    pts: List[np.ndarray] = []
+    tries = 0
+    while len(pts) < n:
+        tries += 1
+        if tries > 1_000_000:
+            raise RuntimeError("could not place atoms with the requested separation")
+        c = rng.uniform(0.0, box, size=3)
+        if all(np.linalg.norm(c - p) >= min_sep for p in pts):
+            pts.append(c)
+    return np.array(pts)
+
+
+def heavy_light_cluster(n_atoms: int = 64, box: float = 24.0, min_sep: float = 4.0,
+                        seed: int = 1002, n_rad: int = 60, n_theta: int = 14, n_phi: int = 28,
+                        batch_max: int = 300, name: Optional[str] = None) -> Workload:
+    """Random cluster in a cube: half heavy (Z=82 or 53, 2s2p1d1f = 20 functions),
+    half light (Z=6 or 1, 2s1p = 5 functions), the four species in equal
+    numbers, assigned by a seeded permutation; positions uniform in the cube
+    with rejection below `min_sep`; exponents log-uniform in [0.1, 10]."""
+    rng = np.random.default_rng(seed)
+    sp = [Species("Pb", 82.0, HEAVY_L, _draw_alphas(rng, len(HEAVY_L))),
+          Species("I", 53.0, HEAVY_L, _draw_alphas(rng, len(HEAVY_L))),
+          Species("C", 6.0, LIGHT_L, _draw_alphas(rng, len(LIGHT_L))),
+          Species("H", 1.0, LIGHT_L, _draw_alphas(rng, len(LIGHT_L)))]
+    kinds = np.array([k % 4 for k in range(n_atoms)], dtype=np.int32)
+    kinds = rng.permutation(kinds).astype(np.int32)
+    xyz = _place(rng, n_atoms, box, min_sep)
+    return Workload(name or f"cluster-{n_atoms}atom", xyz, kinds, sp, n_rad=n_rad,
+                    n_theta=n_theta, n_phi=n_phi, batch_max=batch_max)
+
+
+def cluster64() -> Workload:
+    """64 atoms in a 24 Bohr cube (the throughput workload): ~800 functions,
+    60 radial x (14 x 28) = 392 angular points per atom, batches <= 300."""
+    return heavy_light_cluster(64, 24.0, 4.0, seed=1002, name="cluster-64atom")
+
+
+def small_cluster(n_atoms: int = 8, seed: int = 7, n_rad: int = 24, n_theta: int = 8,
+                  n_phi: int = 16, batch_max: int = 200) -> Workload:
+    """A reduced heavy/light cluster that the oracle finishes in seconds but
+    that still spans several batches, n_b above 64 and a ragged tail."""
+    box = 4.0 * n_atoms ** (1.0 / 3.0) + 2.0
+    return heavy_light_cluster(n_atoms, box, 3.0, seed=seed, n_rad=n_rad, n_theta=n_theta,
+                               n_phi=n_phi, batch_max=batch_max, name=f"small-{n_atoms}atom")
+
+
+def single_atom(l_list=(0, 1, 2, 3), alphas=None, Z: float = 8.0, n_rad: int = 60,
+                n_theta: int = 8, n_phi: int = 16, batch_max: int = 128) -> Workload:
+    """One atom at the origin (closed-form pins and edge cases)."""
+    l_list = list(l_list)
+    if alphas is None:
+        alphas = [1.5 + 0.5 * k for k in range(len(l_list))]
+    sp = [Species("X", Z, l_list, list(alphas))]
+    return Workload("single-atom", np.zeros((1, 3)), np.array([0], dtype=np.int32), sp,
+                    n_rad=n_rad, n_theta=n_theta, n_phi=n_phi, batch_max=batch_max)
+
+
+# --------------------------------------------------------------------------
+# input potential
+# --------------------------------------------------------------------------
+
+def _erf(x: np.ndarray) -> np.ndarray:
+    try:
+        from scipy.special import erf
+        return erf(x)
+    except ImportError:  # pragma: no cover
+        return np.vectorize(math.erf)(x)
+
+
+def potential(points: np.ndarray, wl: Workload, chunk: int = 65536) -> np.ndarray:
+    """v(r) = sum_A -Z_A erf(d_A)/d_A, d_A = |r - R_A|, with
+    erf(d)/d -> 2/sqrt(pi) (1 - d^2/3 + d^4/10) for d < 1e-4."""
+    points = np.ascontiguousarray(points, dtype=np.float64).reshape(-1, 3)
+    Z = wl.Z_of_atom
+    out = np.empty(points.shape[0], dtype=np.float64)
+    c = 2.0 / math.sqrt(math.pi)
+    for s in range(0, points.shape[0], chunk):
+        P = points[s:s + chunk]
+        d = np.sqrt(((P[:, None, :] - wl.xyz[None, :, :]) ** 2).sum(-1))
+        small = d < 1e-4
+        ds = np.where(small, 1.0, d)
+        f = np.where(small, c * (1.0 - d * d / 3.0 + d ** 4 / 10.0), _erf(ds) / ds)
+        out[s:s + chunk] = -(f * Z[None, :]).sum(-1)
+    return out
+
+
+# --------------------------------------------------------------------------
+# random block-sparse matrices on a CSR block pattern
+# --------------------------------------------------------------------------
+
+KINDS = {"P": 1, "GV": 2, "GW0": 3, "GSOx": 4, "GSOy": 5, "GSOz": 6}
+
+
+def _block_rng(seed: int, kind: str, A: int, B: int) -> np.random.Generator:
+    key = [(int(seed) << 8) | KINDS[kind], (int(A) << 32) | int(B)]
+    return np.random.Generator(np.random.Philox(key=key))
+
+
+def block_values(seed: int, kind: str, A: int, B: int, nfA: int, nfB: int, antisym: bool) -> np.ndarray:
+    """Block (A, B) of a random matrix that is symmetric (antisym=False) or
+    antisymmetric (antisym=True) as a whole: the pair's block is drawn once,
+    keyed by (min, max), and transposed (and negated) for the other order."""
+    if A == B:
+        R = _block_rng(seed, kind, A, A).standard_normal((nfA, nfA))
+        return 0.5 * (R - R.T) if antisym else 0.5 * (R + R.T)
+    if A < B:
+        return _block_rng(seed, kind, A, B).standard_normal((nfA, nfB))
+    R = _block_rng(seed, kind, B, A).standard_normal((nfB, nfA))
+    return -R.T if antisym else R.T.copy()
+
+
+def fill_pattern(blk_ptr: np.ndarray, blk_col: np.ndarray, blk_off: np.ndarray,
+                 nf_of_atom: np.ndarray, seed: int, kind: str, antisym: bool = False) -> np.ndarray:
+    """Values of a random matrix on a CSR block pattern (rows = atoms,
+    blocks dense row-major nf_A x nf_B at blk_off)."""
+    n_atoms = len(blk_ptr) - 1
+    out = np.zeros(int(blk_off[int(blk_ptr[-1])]), dtype=np.float64)
+    for A in range(n_atoms):
+        for q in range(int(blk_ptr[A]), int(blk_ptr[A + 1])):
+            B = int(blk_col[q])
+            blk = block_values(seed, kind, A, B, int(nf_of_atom[A]), int(nf_of_atom[B]), antisym)
+            out[int(blk_off[q]):int(blk_off[q]) + blk.size] = blk.ravel()
+    return out
+
+
+ADJOINT_KINDS = [("GV", False), ("GW0", False), ("GSOx", True), ("GSOy", True), ("GSOz", True)]
