@@ -1,0 +1,388 @@
+"""Throughput of the Q4C real-space integration hot path on GB300.
+
+One step = one pass of the whole hot path over the 64-atom cluster workload
+(~1.24M grid points, 800 basis functions): q4c_integrate (V, W0, SO_x,y,z and
+the SS spinor blocks), q4c_density with a random P and
+q4c_integrate_backward with random G, all in the requested precision.
+
+value = algorithmic FLOPs of the step / device time, where the algorithmic
+FLOPs are 14 n_p n_b^2 (integration) + 2 n_p n_b^2 (density) + 14 n_p n_b^2
+(adjoint) summed over batches (the useful n_b x n_p x n_b products).
+
+usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--prec split|fp64]
+                       [--impl ours|reference]
+Under torchrun with N > 1 every rank runs an independent replica of the
+workload (the path is single-GPU by design); value sums over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Q4C grid integration TFLOP/s (% peak), split-prec vs FP64 at <=1e-9 rel err"
+L2_FLUSH_BYTES = 512 << 20
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}, \
+        "fallback"
+
+
+# FP64 FMA rate of GB300: 2 DFMA per SM per clock -> 4 flop/clk/SM
+def fp64_peak_tflops(sm_mhz: float) -> float:
+    return 152 * sm_mhz * 1e6 * 4 / 1e12
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (FileNotFoundError, OSError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1])); mx = float(f[2])
+            except ValueError:
+                continue
+            for n, val in zip(names, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_init():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# the oracle on a bounded sample (cpu_baseline and the reference arm)
+# ---------------------------------------------------------------------------
+
+def oracle_step_sample(wl, stride: int):
+    """One oracle step (matrices, density, adjoint) on the raw grid points with
+    id % stride == 0; returns (seconds, fraction of the workload)."""
+    import oracle as O
+    from workloads import ADJOINT_KINDS, fill_pattern, potential
+    xyz, w, ids = O.grid(wl, stride=stride)
+    ob = O.OracleBasis(wl)
+    pat = ob.pattern()
+    v = potential(xyz, wl)
+    P = fill_pattern(pat.blk_ptr, pat.blk_col, pat.blk_off, wl.nf_of_atom, 11, "P")
+    G = [fill_pattern(pat.blk_ptr, pat.blk_col, pat.blk_off, wl.nf_of_atom, 12, k, a) for k, a in ADJOINT_KINDS]
+    t0 = time.perf_counter()
+    ob.matrix_blocks(xyz, w, v, pat)
+    ob.density(xyz, P, pat)
+    ob.adjoint(xyz, w, G, pat)
+    return time.perf_counter() - t0, 1.0 / stride
+
+
+def step_flops(info) -> dict:
+    s2 = info.flops_alg / 14.0  # sum over batches of n_p n_b^2
+    return {"integrate": 14.0 * s2, "density": 2.0 * s2, "backward": 14.0 * s2}
+
+
+# ---------------------------------------------------------------------------
+
+def run_reference(args, wl):
+    rank, world, _ = dist_init()
+    if rank != 0:
+        return
+    flops = workload_flops(wl)
+    times = []
+    for _ in range(args.warmup):
+        oracle_step_sample(wl, args.ref_stride)
+    for _ in range(args.steps):
+        t, frac = oracle_step_sample(wl, args.ref_stride)
+        times.append(t / frac)
+    t_step = statistics.mean(times)
+    val = flops / t_step / 1e12
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "TFLOP/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl.name, "note": "oracle (plain FP64 C, one host core) on a uniform "
+                       f"1/{args.ref_stride} sample of the raw grid, time scaled to the full workload"},
+            "cpu_baseline": {"value": val, "unit": "TFLOP/s", "cores": 1, "kind": "oracle",
+                             "sample": f"raw grid ids divisible by {args.ref_stride}"},
+            "e2e": {"value": val, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def workload_flops(wl) -> float:
+    """Algorithmic FLOPs of one step (30 sum_b n_p n_b^2) counted on the
+    oracle's own grid with the batching rule of the method (recursive median
+    bisection along the longest bounding-box axis, ties by raw id, until a
+    batch holds <= batch_max points; n_b = functions of the atoms strictly
+    within r_c of some point of the batch)."""
+    import oracle as O
+    xyz, w, ids = O.grid(wl)
+    nf = wl.nf_of_atom.astype(np.float64)
+    total = 0.0
+    stack = [np.arange(len(ids))]
+    while stack:
+        idx = stack.pop()
+        if len(idx) <= wl.batch_max:
+            P = xyz[idx]
+            d2 = ((P[:, None, :] - wl.xyz[None]) ** 2).sum(-1)
+            nb = float(nf[(d2 < wl.r_c ** 2).any(axis=0)].sum())
+            total += len(idx) * nb * nb
+            continue
+        P = xyz[idx]
+        ax = int(np.argmax(P.max(0) - P.min(0)))
+        order = np.lexsort((ids[idx], P[:, ax]))
+        mid = len(idx) // 2
+        stack.append(idx[order[mid:]])
+        stack.append(idx[order[:mid]])
+    return 30.0 * total
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--prec", default="split", choices=["split", "fp64"])
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="cluster64", choices=["cluster64", "water"])
+    ap.add_argument("--cpu-stride", type=int, default=11)
+    ap.add_argument("--ref-stride", type=int, default=61)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    from workloads import cluster64, water
+    wl = cluster64() if args.workload == "cluster64" else water()
+    if args.impl == "reference":
+        return run_reference(args, wl)
+
+    import torch
+
+    import paper_2608_00773_gb300 as q
+    from workloads import ADJOINT_KINDS, fill_pattern, potential
+
+    rank, world, local = dist_init()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    # ---- setup (untimed): tables, grid, inputs
+    tables, grid = q.setup(wl)
+    ex = grid.export()
+    info = grid.info
+    pat = (ex["blk_ptr"], ex["blk_col"], ex["blk_off"])
+    v_h = potential(ex["xyz"], wl)
+    P_h = fill_pattern(*pat, wl.nf_of_atom, 11, "P")
+    G_h = [fill_pattern(*pat, wl.nf_of_atom, 12, k, a) for k, a in ADJOINT_KINDS]
+    v = torch.tensor(v_h, device=dev)
+    P = torch.tensor(P_h, device=dev)
+    G = [torch.tensor(g, device=dev) for g in G_h]
+    nnz, npts = grid.nnz, grid.n_points
+    mats = [torch.empty(nnz, dtype=torch.float64, device=dev) for _ in range(5)]
+    mats.append(torch.empty(8 * nnz, dtype=torch.float64, device=dev))
+    n_out = torch.empty(npts, dtype=torch.float64, device=dev)
+    g_out = torch.empty(npts, dtype=torch.float64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    fl = step_flops(info)
+    F_step = sum(fl.values())
+    stream = torch.cuda.current_stream()
+
+    def step(prec):
+        q.q4c_integrate(tables, grid, v, prec, out=mats, stream=stream)
+        q.q4c_density(tables, grid, P, prec, out=n_out, stream=stream)
+        q.q4c_integrate_backward(tables, grid, G, prec, out=g_out, stream=stream)
+
+    prec = args.prec
+    for _ in range(args.warmup):
+        step(prec)
+    torch.cuda.synchronize()
+
+    # ---- timed region: device time per step, L2 flushed between steps
+    q.profile(True)
+    q.profile_read("")  # drop records of earlier calls
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier(world)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clocks:
+        for k in range(args.steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            step(prec)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+    barrier(world)
+    q.profile(False)
+    per_step = [a.elapsed_time(b) for a, b in ev]
+    t_ms = max_over_ranks(statistics.mean(per_step), world)
+    kern = {}
+    for name in ("split_products", "split", "products_fp64", "basis", "mirror", "spinor", "density", "backward"):
+        ms, n = q.profile_read(name)
+        if n:
+            kern[name] = (ms, n)
+    launches_total = sum(n for _, n in kern.values())
+    value = world * F_step / (t_ms * 1e-3) / 1e12
+
+    # ---- dominant kernel roofline
+    peaks, peak_src = load_peaks()
+    clk = clocks.summary()
+    dom = max(kern.items(), key=lambda kv: kv[1][0])
+    dom_name, (dom_ms, dom_n) = dom
+    if dom_name.startswith("split"):
+        # algorithmic tensor work: every batch product as s_pairs slice products
+        s_pairs = 10
+        achieved = fl["integrate"] * s_pairs * args.steps / (dom_ms * 1e-3) / 1e12
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peaks["bf16_tflops_sustained"],
+                "unit": "TFLOP/s", "peak_source": f"{peak_src} bf16 sustained"}
+    elif dom_name.startswith("products_fp64"):
+        achieved = fl["integrate"] * args.steps / (dom_ms * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": fp64_peak_tflops(peaks.get("sm_max_mhz", 2070.0)),
+                "unit": "TFLOP/s", "peak_source": "derived: 152 SM x 2 DFMA/clk x sm_max_mhz (FP64 ALU)"}
+    else:
+        achieved = None
+        roof = {"bound": "alu", "achieved": None, "peak": None, "unit": "TFLOP/s"}
+    roof["frac"] = (roof["achieved"] / roof["peak"]) if roof.get("achieved") and roof.get("peak") else None
+    roof["traffic"] = None
+    roof["kernel"] = dom_name
+    roof["kernel_ms_per_launch"] = dom_ms / dom_n
+    roof["share_of_step"] = dom_ms / (t_ms * args.steps)
+
+    # ---- end to end through the public API: pinned host in, host out
+    h_v = torch.from_numpy(v_h).pin_memory()
+    h_P = torch.from_numpy(P_h).pin_memory()
+    h_G = [torch.from_numpy(g).pin_memory() for g in G_h]
+    h_out = [torch.empty(nnz, dtype=torch.float64).pin_memory() for _ in range(5)]
+    h_ss = torch.empty(8 * nnz, dtype=torch.float64).pin_memory()
+    h_n = torch.empty(npts, dtype=torch.float64).pin_memory()
+    h_g = torch.empty(npts, dtype=torch.float64).pin_memory()
+    bi = 8 * (h_v.numel() + h_P.numel() + sum(x.numel() for x in h_G))
+    bo = 8 * (5 * nnz + 8 * nnz + 2 * npts)
+
+    def e2e_step():
+        v.copy_(h_v, non_blocking=True)
+        P.copy_(h_P, non_blocking=True)
+        for d_, h_ in zip(G, h_G):
+            d_.copy_(h_, non_blocking=True)
+        step(prec)
+        for h_, d_ in zip(h_out, mats[:5]):
+            h_.copy_(d_, non_blocking=True)
+        h_ss.copy_(mats[5], non_blocking=True)
+        h_n.copy_(n_out, non_blocking=True)
+        h_g.copy_(g_out, non_blocking=True)
+        stream.synchronize()
+
+    e2e_step()
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        e2e_step()
+    t_e2e = max_over_ranks((time.perf_counter() - t0) / args.steps, world)
+    e2e = {"value": world * F_step / t_e2e / 1e12, "unit": "TFLOP/s", "h2d_bytes_per_step": bi,
+           "d2h_bytes_per_step": bo}
+
+    # ---- FP64 comparison path and split error (reported beside the value)
+    extra = {}
+    if prec == "split":
+        ref = [torch.empty_like(m) for m in mats[:5]]
+        q.q4c_integrate(tables, grid, v, "fp64", out=ref + [None], stream=stream)
+        q.q4c_integrate(tables, grid, v, "split", out=mats, stream=stream)
+        torch.cuda.synchronize()
+        extra["split_rel_err_vs_fp64"] = {n: float(torch.linalg.norm(a - b) / torch.linalg.norm(b))
+                                          for n, a, b in zip(["V", "W0", "SOx", "SOy", "SOz"], mats[:5], ref)}
+
+    if rank != 0:
+        return
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        t_cpu, frac = oracle_step_sample(wl, args.cpu_stride)
+        cpu = {"value": F_step * frac / t_cpu / 1e12, "unit": "TFLOP/s", "cores": 1, "kind": "oracle",
+               "sample": f"raw grid ids divisible by {args.cpu_stride} ({frac:.4f} of the workload), "
+                         f"{t_cpu:.1f} s of one host core"}
+    line = {
+        "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16-split/f32-acc/f64" if prec == "split" else "f64",
+        "data": "synthetic",
+        "config": {"workload": wl.name, "atoms": wl.n_atoms, "n_basis": int(info.n_basis),
+                   "points": int(info.n_points), "batches": int(info.n_batches), "max_nb": int(info.max_nb),
+                   "precision": prec, "step": "q4c_integrate + q4c_density + q4c_integrate_backward",
+                   "l2": "512 MB buffer written between timed steps", "replicas": world},
+        "flops_per_step": fl,
+        "phase_ms": {k: v_[0] / args.steps for k, v_ in kern.items()},
+        "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": launches_total,
+        **extra,
+    }
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

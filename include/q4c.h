@@ -1,0 +1,224 @@
+/*
+ * q4c.h -- C ABI of the GB300 Q4C real-space integration library.
+ *
+ * The library evaluates, on one GPU, the order-N real-space integration of
+ * the Q4C Hamiltonian-type matrix elements over compact batches of an
+ * atom-centred grid (arxiv 2608.00773, Section III A, Eqs. 29-32), the grid
+ * density of Eqs. 39-40 and the adjoint of the integration.
+ *
+ * Conventions for every entry point:
+ *   - returns q4c_status (0 = Q4C_OK); on failure q4c_last_error() returns a
+ *     message for the calling thread; no C++ exception crosses the ABI;
+ *   - opaque handles (q4c_tables, q4c_grid) are library-owned and released
+ *     with their *_destroy call;
+ *   - arrays marked "host" are read during the call only; arrays marked
+ *     "device" are caller-owned CUDA device memory on the current device;
+ *   - q4c_stream is a cudaStream_t (NULL = legacy default stream).  Compute
+ *     calls enqueue work on it and return without synchronising unless
+ *     stated otherwise;
+ *   - units are Bohr and Hartree; matrices are FP64.
+ *
+ * Matrix layout ("block pattern"): rows and columns are atoms; block (A, B)
+ * exists iff |R_A - R_B| < 2 r_cut, stored in CSR order over A
+ * (blk_ptr[n_atoms+1], blk_col[n_blocks], sorted by B) with the values of
+ * block q a dense row-major nf_A x nf_B array starting at blk_off[q]
+ * (blk_off[n_blocks] = nnz).  Basis functions of an atom are ordered by
+ * radial function of its species, then m = -l..l.
+ */
+#ifndef Q4C_H
+#define Q4C_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define Q4C_API __attribute__((visibility("default")))
+#else
+#define Q4C_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum q4c_status {
+  Q4C_OK = 0,
+  Q4C_EINVAL = 1,        /* invalid argument (NULL, size, range, mismatch) */
+  Q4C_ENOMEM = 2,        /* host or device allocation failed */
+  Q4C_ECUDA = 3,         /* a CUDA runtime call failed */
+  Q4C_ETIMEOUT = 4,      /* a bounded device wait expired */
+  Q4C_EUNSUPPORTED = 5   /* valid request outside what is implemented */
+} q4c_status;
+
+typedef enum q4c_precision {
+  Q4C_FP64 = 0,   /* every product and sum in FP64 */
+  Q4C_SPLIT = 1   /* batch products as exact BF16 slice products with FP32
+                     accumulation on tcgen05 tensor cores, recombined and
+                     summed across batches in FP64 (Ozaki-type splitting) */
+} q4c_precision;
+
+typedef struct CUstream_st* q4c_stream; /* = cudaStream_t */
+typedef struct q4c_tables q4c_tables;
+typedef struct q4c_grid q4c_grid;
+
+/* ---------------------------------------------------------------------- */
+/* Radial tables (Eq. 12: phi = u_l(r)/r Y_lm, u_l tabulated numerically on a
+ * one-dimensional logarithmic grid).
+ *
+ * Radial function k of a species: u(r) = r^(l+1) exp(-alpha r^2) c(r), with
+ * c(r) = 1 for r <= r_on, 0 for r >= r_cut, 1 - (10s^3 - 15s^4 + 6s^5),
+ * s = (r - r_on)/(r_cut - r_on), in between; tabulated at
+ * r_k = r_min (r_cut/r_min)^(k/(n_log-1)) and interpolated by a natural cubic
+ * spline in the grid index; below r_min u = u(r_min) (r/r_min)^(l+1).
+ * ---------------------------------------------------------------------- */
+typedef struct q4c_basis_desc {
+  int32_t n_species;
+  const int32_t* n_rad;  /* host [n_species]: radial functions per species (>= 1) */
+  const int32_t* l;      /* host [sum n_rad]: species-major angular momenta, 0 <= l <= 3 */
+  const double* alpha;   /* host [sum n_rad]: Gaussian exponents (> 0) */
+  double r_cut;          /* support radius of every function (> r_on) */
+  double r_on;           /* start of the cutoff ramp (> r_min) */
+  double r_min;          /* first logarithmic knot (> 0) */
+  int32_t n_log;         /* knots (>= 4) */
+} q4c_basis_desc;
+
+/* Builds the spline tables on the host in FP64 and uploads them to the
+ * current device.  *out receives a new handle.  EINVAL on a bad descriptor,
+ * EUNSUPPORTED for l > 3, ENOMEM/ECUDA on allocation/copy failure. */
+Q4C_API q4c_status nao_tabulate(const q4c_basis_desc* desc, q4c_tables** out);
+Q4C_API void q4c_tables_destroy(q4c_tables* tables);
+
+/* Host copy of the cubic coefficients of radial function k (species-major
+ * index): coef[n_log-1][4] with u(s) = c0 + c1 s + c2 s^2 + c3 s^3 on the
+ * interval [k, k+1] of the index variable, s = t - k. */
+Q4C_API q4c_status q4c_tables_export(const q4c_tables* tables, int32_t radial, double* coef_host);
+
+/* ---------------------------------------------------------------------- */
+/* Integration grid, partition and batches (Section III A, Figs. 1-2,
+ * Eqs. 31-32 and the reduced index set nnz(B_v)).
+ *
+ * Per atom: n_rad_shells Gauss-Chebyshev (second kind) radial shells mapped
+ * by r = R (1+x)/(1-x), times Gauss-Legendre(n_theta) in cos(theta) times
+ * n_phi uniform azimuths phi_b = (b + 1/2) 2 pi / n_phi.  Point weights
+ * w = w_rad w_ang p_A(r), p_A the Becke partition (three iterations, no size
+ * adjustment) over the atoms within r_nb of the point.  Points farther than
+ * r_cut from every atom, or with w = 0, are dropped.  The kept points are
+ * split into batches by recursive median bisection along the longest
+ * bounding-box axis until a batch holds <= batch_max points; the raw point
+ * id ((atom*n_rad + shell)*n_theta + theta)*n_phi + phi is kept.
+ * ---------------------------------------------------------------------- */
+typedef struct q4c_grid_desc {
+  int32_t n_atoms;
+  const double* xyz;       /* host [n_atoms][3] Bohr */
+  const int32_t* species;  /* host [n_atoms], indices into the tables' species */
+  int32_t n_rad_shells;    /* radial shells per atom (>= 1) */
+  double R;                /* radial map scale, Bohr (> 0) */
+  int32_t n_theta, n_phi;  /* angular product grid (>= 1 each) */
+  double r_nb;             /* Becke neighbour radius, Bohr (> 0) */
+  int32_t batch_max;       /* maximum points per batch (1..1024) */
+} q4c_grid_desc;
+
+/* Builds the grid (raw points and base weights on the host, Becke weights in
+ * an FP64 kernel, pruning, bisection, active-function lists and the block
+ * pattern) and keeps everything resident on the current device.
+ * Synchronous.  EINVAL on a bad descriptor or an empty grid. */
+Q4C_API q4c_status grid_partition(const q4c_grid_desc* desc, const q4c_tables* tables, q4c_grid** out);
+Q4C_API void q4c_grid_destroy(q4c_grid* grid);
+
+typedef struct q4c_grid_info {
+  int64_t n_points;    /* kept points */
+  int64_t n_batches;
+  int64_t n_blocks;    /* pattern blocks */
+  int64_t nnz;         /* values per matrix on the pattern */
+  int32_t n_atoms;
+  int32_t n_basis;
+  int32_t max_nb;      /* largest |nnz(B_v)| over batches */
+  int32_t max_np;      /* largest batch */
+  double flops_alg;    /* sum over batches of 14 n_p n_b^2 (the integration's
+                          seven n_b x n_p x n_b products) */
+  double sum_np_nb;    /* sum over batches of n_p n_b */
+  int64_t scratch_bytes; /* device workspace held by the grid */
+} q4c_grid_info;
+Q4C_API q4c_status q4c_grid_get_info(const q4c_grid* grid, q4c_grid_info* info);
+
+/* Host copies of the grid (points in batch order).  Any pointer may be NULL.
+ * xyz[n_points][3], w[n_points], point_id[n_points], batch_ptr[n_batches+1],
+ * batch_atom_ptr[n_batches+1], batch_atoms[batch_atom_ptr[n_batches]]
+ * (active atoms per batch, ascending), blk_ptr[n_atoms+1],
+ * blk_col[n_blocks], blk_off[n_blocks+1].  Synchronous. */
+Q4C_API q4c_status q4c_grid_export(const q4c_grid* grid, double* xyz, double* w, int64_t* point_id,
+                           int64_t* batch_ptr, int64_t* batch_atom_ptr, int32_t* batch_atoms,
+                           int64_t* blk_ptr, int32_t* blk_col, int64_t* blk_off);
+
+/* Device pointers (grid-owned, read-only) to the kept points in batch order:
+ * xyz[n_points][3] and w[n_points], so callers can build v on the device. */
+Q4C_API q4c_status q4c_grid_points(const q4c_grid* grid, const double** xyz_dev, const double** w_dev,
+                           int64_t* n_points);
+
+/* ---------------------------------------------------------------------- */
+/* Matrices on the block pattern. */
+typedef struct q4c_matrices {
+  double* V;    /* device [nnz] */
+  double* W0;   /* device [nnz] */
+  double* SOx;  /* device [nnz] */
+  double* SOy;  /* device [nnz] */
+  double* SOz;  /* device [nnz] */
+  double* spinor_SS; /* device [8*nnz] or NULL: complex128 (re, im) SS blocks,
+                        block q a row-major (2 nf_A) x (2 nf_B) matrix at
+                        4*blk_off[q], row 2i+s, column 2j+s' */
+} q4c_matrices;
+
+/* Integration (Eqs. 29-32 with F = v; the SS block of Eq. 16 read with the
+ * kinetic-balance small component, (s.a)(s.b) = a.b + i s.(a x b)):
+ *   V_ij   = sum_p w_p v_p phi_i phi_j
+ *   W0_ij  = sum_p w_p v_p grad phi_i . grad phi_j
+ *   SOk_ij = sum_p w_p v_p (grad phi_i x grad phi_j)_k
+ * and, if out->spinor_SS != NULL, the 2x2 complex blocks
+ *   [[W0 + i SOz, SOy + i SOx], [-SOy + i SOx, W0 - i SOz]].
+ * v_dev: device [n_points] in batch order.  Outputs are overwritten (not
+ * accumulated).  V and W0 come out exactly symmetric, SO exactly
+ * antisymmetric.  EINVAL on NULL arguments or handles of different setups. */
+Q4C_API q4c_status q4c_integrate(const q4c_tables* tables, const q4c_grid* grid, const double* v_dev,
+                         q4c_precision prec, const q4c_matrices* out, q4c_stream stream);
+
+/* Density (Eqs. 39-40): n_p = sum_ij P_ij phi_i(p) phi_j(p), P_dev device
+ * [nnz] on the block pattern (any P; only its symmetric part contributes),
+ * n_dev device [n_points] in batch order, overwritten. */
+Q4C_API q4c_status q4c_density(const q4c_tables* tables, const q4c_grid* grid, const double* P_dev,
+                       q4c_precision prec, double* n_dev, q4c_stream stream);
+
+/* Adjoint of q4c_integrate for L = <G^V,V> + <G^W0,W0> + sum_k <G^SOk,SOk>:
+ *   dLdv_p = w_p sum_M sum_ij G^M_ij f^M_ij(p)
+ * with f^V = phi_i phi_j, f^W0 = grad phi_i . grad phi_j,
+ * f^SOk = (grad phi_i x grad phi_j)_k; the basis is recomputed, never stored.
+ * G->V..G->SOz device [nnz] each, NULL slots count as zero; spinor_SS is
+ * ignored.  dLdv_dev device [n_points], overwritten. */
+Q4C_API q4c_status q4c_integrate_backward(const q4c_tables* tables, const q4c_grid* grid,
+                                  const q4c_matrices* G, q4c_precision prec, double* dLdv_dev,
+                                  q4c_stream stream);
+
+/* Basis values at arbitrary points with the kernels' own evaluation (for
+ * parity checks): phi_dev[n_basis][n_pts], grad_dev[n_basis][n_pts][3]
+ * (device, overwritten); xyz_dev device [n_pts][3]. */
+Q4C_API q4c_status q4c_basis_eval(const q4c_tables* tables, const q4c_grid* grid, int64_t n_pts,
+                          const double* xyz_dev, double* phi_dev, double* grad_dev,
+                          q4c_stream stream);
+
+/* Kernel instrumentation.  q4c_profile(1) makes every later compute call
+ * record a pair of CUDA events on its stream around each kernel it launches
+ * (and count the launches); q4c_profile(0) stops recording.
+ * q4c_profile_read synchronises on the recorded events, adds up the elapsed
+ * time of the kernels whose name starts with `prefix` (NULL or "" = all),
+ * returns the total in *ms and the number of launches in *launches, and
+ * forgets the records it read.  Kernel names: "basis", "products_fp64",
+ * "mirror", "spinor", "density_fp64", "backward_fp64", "split_*". */
+Q4C_API q4c_status q4c_profile(int32_t enable);
+Q4C_API q4c_status q4c_profile_read(const char* prefix, double* ms, int64_t* launches);
+
+/* Message of the last failure on the calling thread ("" if none). */
+Q4C_API const char* q4c_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* Q4C_H */

@@ -69,7 +69,7 @@ def lib() -> C.CDLL:
             L.orc_becke_weight.argtypes = [C.c_int, _dp, C.c_int, _dp, C.c_double]
             L.orc_becke_weight.restype = C.c_double
             L.orc_grid.argtypes = [C.c_int, _dp, C.c_int, C.c_double, C.c_int, C.c_int, C.c_double,
-                                   C.c_double, _dp, _dp, _lp]
+                                   C.c_double, C.c_longlong, _dp, _dp, _lp]
             L.orc_grid.restype = C.c_long
             L.orc_pattern.argtypes = [bp, C.c_void_p, C.c_void_p, C.c_void_p]
             L.orc_pattern.restype = C.c_long
@@ -147,12 +147,13 @@ def becke_weight(centres: np.ndarray, owner: int, p, r_nb: float = 1e300) -> flo
     return lib().orc_becke_weight(len(c) // 3, c, owner, _f64(p), r_nb)
 
 
-def grid(wl):
-    """Kept grid points of a workload: (xyz (n,3), w (n,), raw id (n,))."""
-    n_raw = wl.n_raw_points
+def grid(wl, stride: int = 1):
+    """Kept grid points of a workload: (xyz (n,3), w (n,), raw id (n,)).
+    stride > 1 evaluates only the raw points whose id is a multiple of it."""
+    n_raw = (wl.n_raw_points + stride - 1) // stride
     xyz = np.zeros(3 * n_raw); w = np.zeros(n_raw); ids = np.zeros(n_raw, dtype=np.int64)
     n = lib().orc_grid(wl.n_atoms, _f64(wl.xyz).reshape(-1), wl.n_rad, wl.R, wl.n_theta, wl.n_phi,
-                       wl.r_c, wl.r_nb, xyz, w, ids)
+                       wl.r_c, wl.r_nb, stride, xyz, w, ids)
     return xyz[:3 * n].reshape(n, 3).copy(), w[:n].copy(), ids[:n].copy()
 
 

@@ -418,9 +418,11 @@ double orc_becke_weight(int n_c, const double* centres, int owner, const double 
  * (ascending x_i order, i.e. decreasing r), a Gauss-Legendre node in cos(theta)
  * (ascending), b azimuth phi_b = (b + 1/2) 2 pi / n_phi.
  * Keep p iff some atom lies strictly within r_c of p and w_p != 0.
+ * stride > 1 keeps only raw ids divisible by stride (a uniform sample used
+ * to time the oracle on a bounded share of a large workload).
  * Returns the number of kept points; out arrays must hold the raw count. */
 long orc_grid(int n_atoms, const double* xyz, int n_rad, double R, int n_theta, int n_phi,
-              double r_c, double r_nb, double* out_xyz, double* out_w, long long* out_id) {
+              double r_c, double r_nb, long long stride, double* out_xyz, double* out_w, long long* out_id) {
   double* rr = (double*)malloc(sizeof(double) * n_rad);
   double* wr = (double*)malloc(sizeof(double) * n_rad);
   double* ct = (double*)malloc(sizeof(double) * n_theta);
@@ -433,6 +435,8 @@ long orc_grid(int n_atoms, const double* xyz, int n_rad, double R, int n_theta, 
       for (int a = 0; a < n_theta; ++a) {
         double st = sqrt(1.0 - ct[a] * ct[a]);
         for (int bb = 0; bb < n_phi; ++bb) {
+          long long id = (((long long)A * n_rad + i) * n_theta + a) * n_phi + bb;
+          if (stride > 1 && id % stride != 0) continue; /* uniform sample of the raw grid */
           double ph = (bb + 0.5) * 2.0 * M_PI / n_phi;
           double p[3] = {xyz[3 * A] + rr[i] * st * cos(ph), xyz[3 * A + 1] + rr[i] * st * sin(ph),
                          xyz[3 * A + 2] + rr[i] * ct[a]};
@@ -446,7 +450,7 @@ long orc_grid(int n_atoms, const double* xyz, int n_rad, double R, int n_theta, 
           if (w == 0.0) continue;
           out_xyz[3 * kept] = p[0]; out_xyz[3 * kept + 1] = p[1]; out_xyz[3 * kept + 2] = p[2];
           out_w[kept] = w;
-          out_id[kept] = (((long long)A * n_rad + i) * n_theta + a) * n_phi + bb;
+          out_id[kept] = id;
           ++kept;
         }
       }

@@ -1,0 +1,301 @@
+"""Thin ctypes binding of libq4c.so (include/q4c.h), same names as the C ABI.
+
+Argument marshalling only: every step of the computation runs in the
+library's CUDA kernels.  PyTorch provides device memory and streams.  If the
+shared library is missing, importing this module raises: there is no CPU
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libq4c.so")
+
+Q4C_FP64 = 0
+Q4C_SPLIT = 1
+PRECISIONS = {"fp64": Q4C_FP64, "split": Q4C_SPLIT}
+
+STATUS = {0: "Q4C_OK", 1: "Q4C_EINVAL", 2: "Q4C_ENOMEM", 3: "Q4C_ECUDA", 4: "Q4C_ETIMEOUT", 5: "Q4C_EUNSUPPORTED"}
+
+# every symbol include/q4c.h declares
+EXPORTS = ["nao_tabulate", "q4c_tables_destroy", "q4c_tables_export", "grid_partition", "q4c_grid_destroy",
+           "q4c_grid_get_info", "q4c_grid_export", "q4c_grid_points", "q4c_integrate", "q4c_density",
+           "q4c_integrate_backward", "q4c_basis_eval", "q4c_profile", "q4c_profile_read", "q4c_last_error"]
+
+
+class Q4CError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class BasisDesc(C.Structure):
+    _fields_ = [("n_species", C.c_int32), ("n_rad", C.c_void_p), ("l", C.c_void_p), ("alpha", C.c_void_p),
+                ("r_cut", C.c_double), ("r_on", C.c_double), ("r_min", C.c_double), ("n_log", C.c_int32)]
+
+
+class GridDesc(C.Structure):
+    _fields_ = [("n_atoms", C.c_int32), ("xyz", C.c_void_p), ("species", C.c_void_p),
+                ("n_rad_shells", C.c_int32), ("R", C.c_double), ("n_theta", C.c_int32), ("n_phi", C.c_int32),
+                ("r_nb", C.c_double), ("batch_max", C.c_int32)]
+
+
+class GridInfo(C.Structure):
+    _fields_ = [("n_points", C.c_int64), ("n_batches", C.c_int64), ("n_blocks", C.c_int64), ("nnz", C.c_int64),
+                ("n_atoms", C.c_int32), ("n_basis", C.c_int32), ("max_nb", C.c_int32), ("max_np", C.c_int32),
+                ("flops_alg", C.c_double), ("sum_np_nb", C.c_double), ("scratch_bytes", C.c_int64)]
+
+
+class Matrices(C.Structure):
+    _fields_ = [("V", C.c_void_p), ("W0", C.c_void_p), ("SOx", C.c_void_p), ("SOy", C.c_void_p),
+                ("SOz", C.c_void_p), ("spinor_SS", C.c_void_p)]
+
+
+_lib: Optional[C.CDLL] = None
+
+
+def load(path: str = LIB_PATH) -> C.CDLL:
+    """Loads libq4c.so; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with __graft_entry__.build() "
+                           "(nvcc for sm_103a); there is no CPU fallback")
+    L = C.CDLL(path)
+    vp, i64, i32 = C.c_void_p, C.c_int64, C.c_int32
+    L.nao_tabulate.argtypes = [C.POINTER(BasisDesc), C.POINTER(vp)]
+    L.q4c_tables_destroy.argtypes = [vp]
+    L.q4c_tables_destroy.restype = None
+    L.q4c_tables_export.argtypes = [vp, i32, vp]
+    L.grid_partition.argtypes = [C.POINTER(GridDesc), vp, C.POINTER(vp)]
+    L.q4c_grid_destroy.argtypes = [vp]
+    L.q4c_grid_destroy.restype = None
+    L.q4c_grid_get_info.argtypes = [vp, C.POINTER(GridInfo)]
+    L.q4c_grid_export.argtypes = [vp] + [vp] * 9
+    L.q4c_grid_points.argtypes = [vp, C.POINTER(vp), C.POINTER(vp), C.POINTER(i64)]
+    L.q4c_integrate.argtypes = [vp, vp, vp, C.c_int, C.POINTER(Matrices), vp]
+    L.q4c_density.argtypes = [vp, vp, vp, C.c_int, vp, vp]
+    L.q4c_integrate_backward.argtypes = [vp, vp, C.POINTER(Matrices), C.c_int, vp, vp]
+    L.q4c_basis_eval.argtypes = [vp, vp, i64, vp, vp, vp, vp]
+    L.q4c_profile.argtypes = [i32]
+    L.q4c_profile_read.argtypes = [C.c_char_p, C.POINTER(C.c_double), C.POINTER(i64)]
+    L.q4c_last_error.restype = C.c_char_p
+    _lib = L
+    return L
+
+
+def _check(status: int):
+    if status != 0:
+        raise Q4CError(status, load().q4c_last_error().decode())
+
+
+def _ptr(t) -> int:
+    """Device pointer of a torch tensor (None -> NULL)."""
+    if t is None:
+        return 0
+    if not t.is_contiguous():
+        raise ValueError("tensors passed to libq4c must be contiguous")
+    return t.data_ptr()
+
+
+def _stream(stream) -> int:
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream
+
+
+# --------------------------------------------------------------------------
+# handles
+# --------------------------------------------------------------------------
+
+class Tables:
+    """q4c_tables handle (nao_tabulate)."""
+
+    def __init__(self, n_rad: Sequence[int], l: Sequence[int], alpha: Sequence[float], r_cut=6.0, r_on=5.0,
+                 r_min=1e-4, n_log=200):
+        L = load()
+        self._n_rad = np.ascontiguousarray(n_rad, np.int32)
+        self._l = np.ascontiguousarray(l, np.int32)
+        self._alpha = np.ascontiguousarray(alpha, np.float64)
+        d = BasisDesc(len(self._n_rad), self._n_rad.ctypes.data, self._l.ctypes.data, self._alpha.ctypes.data,
+                      r_cut, r_on, r_min, n_log)
+        h = C.c_void_p()
+        _check(L.nao_tabulate(C.byref(d), C.byref(h)))
+        self.h = h
+        self.n_log = n_log
+
+    def coefficients(self, radial: int) -> np.ndarray:
+        out = np.zeros((self.n_log - 1, 4))
+        _check(load().q4c_tables_export(self.h, radial, out.ctypes.data))
+        return out
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.q4c_tables_destroy(self.h)
+            self.h = None
+
+
+class Grid:
+    """q4c_grid handle (grid_partition)."""
+
+    def __init__(self, tables: Tables, xyz, species, n_rad_shells, R, n_theta, n_phi, r_nb, batch_max):
+        L = load()
+        self.tables = tables
+        self._xyz = np.ascontiguousarray(xyz, np.float64).reshape(-1)
+        self._sp = np.ascontiguousarray(species, np.int32)
+        d = GridDesc(len(self._sp), self._xyz.ctypes.data, self._sp.ctypes.data, n_rad_shells, R, n_theta, n_phi,
+                     r_nb, batch_max)
+        h = C.c_void_p()
+        _check(L.grid_partition(C.byref(d), tables.h, C.byref(h)))
+        self.h = h
+        info = GridInfo()
+        _check(L.q4c_grid_get_info(self.h, C.byref(info)))
+        self.info = info
+
+    @property
+    def n_points(self) -> int:
+        return int(self.info.n_points)
+
+    @property
+    def nnz(self) -> int:
+        return int(self.info.nnz)
+
+    def export(self):
+        """Host copies: dict of numpy arrays (points in batch order, batches, pattern)."""
+        i = self.info
+        xyz = np.zeros((i.n_points, 3)); w = np.zeros(i.n_points); pid = np.zeros(i.n_points, np.int64)
+        bptr = np.zeros(i.n_batches + 1, np.int64); baptr = np.zeros(i.n_batches + 1, np.int64)
+        _check(load().q4c_grid_export(self.h, None, None, None, None, baptr.ctypes.data, None, None, None, None))
+        batoms = np.zeros(max(int(baptr[-1]), 1), np.int32)
+        blk_ptr = np.zeros(i.n_atoms + 1, np.int64); blk_col = np.zeros(max(i.n_blocks, 1), np.int32)
+        blk_off = np.zeros(i.n_blocks + 1, np.int64)
+        _check(load().q4c_grid_export(self.h, xyz.ctypes.data, w.ctypes.data, pid.ctypes.data, bptr.ctypes.data,
+                                      baptr.ctypes.data, batoms.ctypes.data, blk_ptr.ctypes.data,
+                                      blk_col.ctypes.data, blk_off.ctypes.data))
+        return dict(xyz=xyz, w=w, point_id=pid, batch_ptr=bptr, batch_atom_ptr=baptr,
+                    batch_atoms=batoms[:int(baptr[-1])], blk_ptr=blk_ptr, blk_col=blk_col[:i.n_blocks],
+                    blk_off=blk_off)
+
+    def points_device(self):
+        """(xyz_ptr, w_ptr, n) device pointers owned by the grid."""
+        a, b, n = C.c_void_p(), C.c_void_p(), C.c_int64()
+        _check(load().q4c_grid_points(self.h, C.byref(a), C.byref(b), C.byref(n)))
+        return a.value, b.value, n.value
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.q4c_grid_destroy(self.h)
+            self.h = None
+
+
+# --------------------------------------------------------------------------
+# the five calls of the boundary
+# --------------------------------------------------------------------------
+
+def nao_tabulate(n_rad, l, alpha, r_cut=6.0, r_on=5.0, r_min=1e-4, n_log=200) -> Tables:
+    return Tables(n_rad, l, alpha, r_cut, r_on, r_min, n_log)
+
+
+def grid_partition(tables: Tables, xyz, species, n_rad_shells, R, n_theta, n_phi, r_nb, batch_max) -> Grid:
+    return Grid(tables, xyz, species, n_rad_shells, R, n_theta, n_phi, r_nb, batch_max)
+
+
+def _prec(prec) -> int:
+    return PRECISIONS[prec] if isinstance(prec, str) else int(prec)
+
+
+def q4c_integrate(tables: Tables, grid: Grid, v, prec="fp64", out=None, spinor: bool = False, stream=None):
+    """V, W0, SOx, SOy, SOz (and the SS spinor blocks) on the block pattern."""
+    import torch
+    if out is None:
+        out = [torch.empty(grid.nnz, dtype=torch.float64, device=v.device) for _ in range(5)]
+        out.append(torch.empty(8 * grid.nnz, dtype=torch.float64, device=v.device) if spinor else None)
+    m = Matrices(*[_ptr(t) for t in out[:5]], _ptr(out[5]) if len(out) > 5 else 0)
+    _check(load().q4c_integrate(tables.h, grid.h, _ptr(v), _prec(prec), C.byref(m), _stream(stream)))
+    return out
+
+
+def q4c_density(tables: Tables, grid: Grid, P, prec="fp64", out=None, stream=None):
+    import torch
+    if out is None:
+        out = torch.empty(grid.n_points, dtype=torch.float64, device=P.device)
+    _check(load().q4c_density(tables.h, grid.h, _ptr(P), _prec(prec), _ptr(out), _stream(stream)))
+    return out
+
+
+def q4c_integrate_backward(tables: Tables, grid: Grid, G: Sequence, prec="fp64", out=None, stream=None):
+    """dL/dv for L = sum_M <G^M, M>; G = [GV, GW0, GSOx, GSOy, GSOz], None = 0."""
+    import torch
+    dev = next(g for g in G if g is not None).device
+    if out is None:
+        out = torch.empty(grid.n_points, dtype=torch.float64, device=dev)
+    m = Matrices(*[_ptr(g) for g in G], 0)
+    _check(load().q4c_integrate_backward(tables.h, grid.h, C.byref(m), _prec(prec), _ptr(out), _stream(stream)))
+    return out
+
+
+def q4c_basis_eval(tables: Tables, grid: Grid, xyz, stream=None):
+    import torch
+    n = xyz.shape[0]
+    nb = int(grid.info.n_basis)
+    phi = torch.empty((nb, n), dtype=torch.float64, device=xyz.device)
+    grad = torch.empty((nb, n, 3), dtype=torch.float64, device=xyz.device)
+    _check(load().q4c_basis_eval(tables.h, grid.h, n, _ptr(xyz), _ptr(phi), _ptr(grad), _stream(stream)))
+    return phi, grad
+
+
+def profile(enable: bool):
+    """Record CUDA events around every kernel of later compute calls."""
+    _check(load().q4c_profile(1 if enable else 0))
+
+
+def profile_read(prefix: str = ""):
+    """(total ms, launches) of recorded kernels whose name starts with prefix."""
+    ms, n = C.c_double(), C.c_int64()
+    _check(load().q4c_profile_read(prefix.encode(), C.byref(ms), C.byref(n)))
+    return ms.value, n.value
+
+
+# --------------------------------------------------------------------------
+# autograd: v -> (V, W0, SOx, SOy, SOz)
+# --------------------------------------------------------------------------
+
+def _make_function():
+    import torch
+
+    class Q4CIntegrate(torch.autograd.Function):
+        """Forward: q4c_integrate.  Backward: q4c_integrate_backward with the
+        incoming gradients as G (basis recomputed in the kernel)."""
+
+        @staticmethod
+        def forward(ctx, v, tables, grid, prec):
+            ctx.tables, ctx.grid, ctx.prec = tables, grid, prec
+            outs = q4c_integrate(tables, grid, v.contiguous(), prec)[:5]
+            return tuple(outs)
+
+        @staticmethod
+        def backward(ctx, gV, gW, gx, gy, gz):
+            G = [None if g is None else g.contiguous() for g in (gV, gW, gx, gy, gz)]
+            if all(g is None for g in G):
+                return None, None, None, None
+            return q4c_integrate_backward(ctx.tables, ctx.grid, G, ctx.prec), None, None, None
+
+    return Q4CIntegrate
+
+
+_fn = None
+
+
+def integrate(v, tables: Tables, grid: Grid, prec="fp64"):
+    """Differentiable integration: returns (V, W0, SOx, SOy, SOz)."""
+    global _fn
+    if _fn is None:
+        _fn = _make_function()
+    return _fn.apply(v, tables, grid, prec)

@@ -1,0 +1,81 @@
+// C ABI entry points for the compute calls: argument checks and dispatch to
+// the FP64 or split-precision kernels.  No exception crosses this boundary.
+#include "internal.h"
+
+using namespace q4c;
+
+namespace {
+
+q4c_status check_pair(const q4c_tables* t, const q4c_grid* g, const char* who) {
+  if (!t || !g) {
+    set_error(std::string(who) + ": NULL handle");
+    return Q4C_EINVAL;
+  }
+  if (g->tables != t) {
+    set_error(std::string(who) + ": grid was partitioned with different tables");
+    return Q4C_EINVAL;
+  }
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev != g->device) {
+    set_error(std::string(who) + ": current device differs from the grid's device");
+    return Q4C_EINVAL;
+  }
+  return Q4C_OK;
+}
+
+}  // namespace
+
+extern "C" q4c_status q4c_integrate(const q4c_tables* t, const q4c_grid* g, const double* v,
+                                    q4c_precision prec, const q4c_matrices* out, q4c_stream stream) {
+  if (q4c_status st = check_pair(t, g, "q4c_integrate")) return st;
+  Q4C_CHECK_ARG(v && out && out->V && out->W0 && out->SOx && out->SOy && out->SOz,
+                "q4c_integrate: NULL input or output array");
+  auto s = reinterpret_cast<cudaStream_t>(stream);
+  try {
+    if (prec == Q4C_FP64) return integrate_fp64(t, g, v, out, s);
+    if (prec == Q4C_SPLIT) return integrate_split(t, g, v, out, s);
+  } catch (const std::exception& e) {
+    set_error(std::string("q4c_integrate: ") + e.what());
+    return Q4C_ENOMEM;
+  }
+  set_error("q4c_integrate: unknown precision");
+  return Q4C_EINVAL;
+}
+
+extern "C" q4c_status q4c_density(const q4c_tables* t, const q4c_grid* g, const double* P, q4c_precision prec,
+                                  double* n, q4c_stream stream) {
+  if (q4c_status st = check_pair(t, g, "q4c_density")) return st;
+  Q4C_CHECK_ARG(P && n, "q4c_density: NULL array");
+  Q4C_CHECK_ARG(prec == Q4C_FP64 || prec == Q4C_SPLIT, "q4c_density: unknown precision");
+  try {
+    if (prec == Q4C_FP64) return density_fp64(t, g, P, n, reinterpret_cast<cudaStream_t>(stream));
+  } catch (const std::exception& e) {
+    set_error(std::string("q4c_density: ") + e.what());
+    return Q4C_ENOMEM;
+  }
+  set_error("q4c_density: the split-precision density is not built yet");
+  return Q4C_EUNSUPPORTED;
+}
+
+extern "C" q4c_status q4c_integrate_backward(const q4c_tables* t, const q4c_grid* g, const q4c_matrices* G,
+                                             q4c_precision prec, double* dLdv, q4c_stream stream) {
+  if (q4c_status st = check_pair(t, g, "q4c_integrate_backward")) return st;
+  Q4C_CHECK_ARG(G && dLdv, "q4c_integrate_backward: NULL argument");
+  Q4C_CHECK_ARG(prec == Q4C_FP64 || prec == Q4C_SPLIT, "q4c_integrate_backward: unknown precision");
+  try {
+    if (prec == Q4C_FP64) return backward_fp64(t, g, G, dLdv, reinterpret_cast<cudaStream_t>(stream));
+  } catch (const std::exception& e) {
+    set_error(std::string("q4c_integrate_backward: ") + e.what());
+    return Q4C_ENOMEM;
+  }
+  set_error("q4c_integrate_backward: the split-precision adjoint is not built yet");
+  return Q4C_EUNSUPPORTED;
+}
+
+extern "C" q4c_status q4c_basis_eval(const q4c_tables* t, const q4c_grid* g, int64_t n_pts, const double* xyz,
+                                     double* phi, double* grad, q4c_stream stream) {
+  if (q4c_status st = check_pair(t, g, "q4c_basis_eval")) return st;
+  Q4C_CHECK_ARG(n_pts >= 0, "q4c_basis_eval: negative size");
+  Q4C_CHECK_ARG(n_pts == 0 || (xyz && phi && grad), "q4c_basis_eval: NULL array");
+  return basis_eval(t, g, n_pts, xyz, phi, grad, reinterpret_cast<cudaStream_t>(stream));
+}

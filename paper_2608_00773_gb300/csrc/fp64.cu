@@ -1,0 +1,419 @@
+// Plain FP64 path: basis tiles per batch, batch products on the FP64 ALUs,
+// FP64 atomic scatter into the block pattern, mirror, spinor assembly,
+// density (Eqs. 39-40) and the adjoint.  This is the reference-precision GPU
+// path the split-precision tensor-core path is measured against.
+#include "basis.cuh"
+#include "internal.h"
+
+namespace q4c {
+
+// ------------------------------------------------------------------ basis
+// Tiles of batch b in the scratch wave: Phi, X, Y, Z each [n_b][ldp],
+// ldp = n_p rounded up to 8; one thread per (point, active atom).
+__global__ void k_basis_tiles(DevBasis B, DevGrid G, int64_t b0, const int64_t* __restrict__ scr_off,
+                              double* __restrict__ scratch) {
+  const int64_t b = b0 + blockIdx.x;
+  const int64_t p0 = G.pt_ptr[b];
+  const int np = static_cast<int>(G.pt_ptr[b + 1] - p0);
+  const int ldp = (np + 7) & ~7;
+  const int a0 = G.bat_atom_ptr[b], na = G.bat_atom_ptr[b + 1] - a0;
+  const int nb = static_cast<int>(G.bat_fn_ptr[b + 1] - G.bat_fn_ptr[b]);
+  double* base = scratch + scr_off[b];
+  const int64_t plane = static_cast<int64_t>(nb) * ldp;
+  for (int item = threadIdx.x; item < np * na; item += blockDim.x) {
+    const int a = item / np, p = item - a * np;
+    const int A = G.bat_atoms[a0 + a];
+    const int f0 = G.bat_atom_fn0[a0 + a];
+    const double dx = G.x[p0 + p] - G.atom_xyz[3 * A], dy = G.y[p0 + p] - G.atom_xyz[3 * A + 1],
+                 dz = G.z[p0 + p] - G.atom_xyz[3 * A + 2];
+    atom_functions(B, G.atom_sp[A], dx, dy, dz, [&](int k, double phi, double gx, double gy, double gz) {
+      double* q = base + static_cast<int64_t>(f0 + k) * ldp + p;
+      q[0] = phi;
+      q[plane] = gx;
+      q[2 * plane] = gy;
+      q[3 * plane] = gz;
+    });
+  }
+}
+
+// nf of the atom behind local atom a of a batch
+__device__ __forceinline__ int local_nf(const DevBasis& B, const DevGrid& G, int a0, int a) {
+  return __ldg(B.sp_nfn + G.atom_sp[G.bat_atoms[a0 + a]]);
+}
+
+// ------------------------------------------------------------ products
+// One CTA per 32x32 tile (ti <= tj) of one batch, 16x16 threads, 2x2
+// elements each; accumulates V, W0 and SO directly on the upper triangle
+// (i <= j) and scatters with FP64 atomics into the upper blocks.
+constexpr int kT = 32, kK = 16;
+__global__ void __launch_bounds__(256) k_products_fp64(DevBasis B, DevGrid G, const int4* __restrict__ tiles,
+                                                       int64_t t0, const int64_t* __restrict__ scr_off,
+                                                       const double* __restrict__ scratch,
+                                                       const double* __restrict__ v, double* V, double* W0,
+                                                       double* SOx, double* SOy, double* SOz) {
+  __shared__ double sa[4][kK][kT];  // D-scaled i side
+  __shared__ double sb[4][kK][kT];  // j side
+  __shared__ double sd[kK];
+  const int4 tile = tiles[t0 + blockIdx.x];
+  const int64_t b = tile.x;
+  const int ti = tile.y, tj = tile.z;
+  const int64_t p0 = G.pt_ptr[b];
+  const int np = static_cast<int>(G.pt_ptr[b + 1] - p0);
+  const int ldp = (np + 7) & ~7;
+  const int nb = static_cast<int>(G.bat_fn_ptr[b + 1] - G.bat_fn_ptr[b]);
+  const int64_t plane = static_cast<int64_t>(nb) * ldp;
+  const double* base = scratch + scr_off[b];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  double acc[2][2][5];
+#pragma unroll
+  for (int u = 0; u < 2; ++u)
+#pragma unroll
+    for (int w = 0; w < 2; ++w)
+#pragma unroll
+      for (int q = 0; q < 5; ++q) acc[u][w][q] = 0.0;
+
+  for (int k0 = 0; k0 < np; k0 += kK) {
+    if (threadIdx.x < kK) {
+      const int p = k0 + threadIdx.x;
+      sd[threadIdx.x] = p < np ? G.w[p0 + p] * v[p0 + p] : 0.0;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < 4 * kK * kT; e += blockDim.x) {
+      const int q = e / (kK * kT), rem = e - q * kK * kT, f = rem / kK, kk = rem - f * kK;
+      const int p = k0 + kk;
+      const int fi = ti * kT + f, fj = tj * kT + f;
+      const double ai = (p < np && fi < nb) ? base[q * plane + static_cast<int64_t>(fi) * ldp + p] : 0.0;
+      const double bj = (p < np && fj < nb) ? base[q * plane + static_cast<int64_t>(fj) * ldp + p] : 0.0;
+      sa[q][kk][f] = ai * sd[kk];
+      sb[q][kk][f] = bj;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < kK; ++kk) {
+      double a[2][4], c[2][4];
+#pragma unroll
+      for (int u = 0; u < 2; ++u)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          a[u][q] = sa[q][kk][2 * ty + u];
+          c[u][q] = sb[q][kk][2 * tx + u];
+        }
+#pragma unroll
+      for (int u = 0; u < 2; ++u)
+#pragma unroll
+        for (int w = 0; w < 2; ++w) {
+          acc[u][w][0] = fma(a[u][0], c[w][0], acc[u][w][0]);
+          acc[u][w][1] = fma(a[u][1], c[w][1], fma(a[u][2], c[w][2], fma(a[u][3], c[w][3], acc[u][w][1])));
+          acc[u][w][2] = fma(a[u][2], c[w][3], fma(-a[u][3], c[w][2], acc[u][w][2]));
+          acc[u][w][3] = fma(a[u][3], c[w][1], fma(-a[u][1], c[w][3], acc[u][w][3]));
+          acc[u][w][4] = fma(a[u][1], c[w][2], fma(-a[u][2], c[w][1], acc[u][w][4]));
+        }
+    }
+    __syncthreads();
+  }
+  // scatter the upper triangle
+  const int64_t f0 = G.bat_fn_ptr[b];
+  const int a0 = G.bat_atom_ptr[b], na = G.bat_atom_ptr[b + 1] - a0;
+  const int64_t pp = G.bat_pair_ptr[b];
+#pragma unroll
+  for (int u = 0; u < 2; ++u)
+#pragma unroll
+    for (int w = 0; w < 2; ++w) {
+      const int i = ti * kT + 2 * ty + u, j = tj * kT + 2 * tx + w;
+      if (i >= nb || j >= nb || i > j) continue;
+      const int ii = G.fn_info[f0 + i], jj = G.fn_info[f0 + j];
+      const int ai = ii >> 16, ki = ii & 0xffff, aj = jj >> 16, kj = jj & 0xffff;
+      const int64_t off = G.pair_off[pp + static_cast<int64_t>(ai) * na + aj];
+      if (off < 0) continue;
+      const int64_t e = off + static_cast<int64_t>(ki) * local_nf(B, G, a0, aj) + kj;
+      atomicAdd(V + e, acc[u][w][0]);
+      atomicAdd(W0 + e, acc[u][w][1]);
+      if (i != j) {
+        atomicAdd(SOx + e, acc[u][w][2]);
+        atomicAdd(SOy + e, acc[u][w][3]);
+        atomicAdd(SOz + e, acc[u][w][4]);
+      }
+    }
+}
+
+// ------------------------------------------------- mirror + spinor blocks
+// One CTA per block.  Upper blocks (A < B) are copied transposed into
+// (B, A) (negated for SO); diagonal blocks fill i > j from (j, i).
+__global__ void k_mirror(const int* __restrict__ blk_row, const int* __restrict__ blk_col,
+                         const int* __restrict__ blk_T, const int64_t* __restrict__ blk_off, const int* atom_sp,
+                         const int* sp_nfn, double* V, double* W0, double* SOx, double* SOy, double* SOz) {
+  const int q = blockIdx.x;
+  const int A = blk_row[q], Bc = blk_col[q];
+  if (A > Bc) return;
+  const int nfA = sp_nfn[atom_sp[A]], nfB = sp_nfn[atom_sp[Bc]];
+  const int64_t o = blk_off[q], oT = blk_off[blk_T[q]];
+  for (int e = threadIdx.x; e < nfA * nfB; e += blockDim.x) {
+    const int i = e / nfB, j = e - i * nfB;
+    if (A == Bc && i <= j) continue;
+    const int64_t src = (A == Bc) ? o + static_cast<int64_t>(j) * nfB + i : o + e;
+    const int64_t dst = (A == Bc) ? o + e : oT + static_cast<int64_t>(j) * nfA + i;
+    V[dst] = V[src];
+    W0[dst] = W0[src];
+    SOx[dst] = -SOx[src];
+    SOy[dst] = -SOy[src];
+    SOz[dst] = -SOz[src];
+  }
+}
+
+// [[W0 + i SOz, SOy + i SOx], [-SOy + i SOx, W0 - i SOz]] per element
+__global__ void k_spinor(const int* __restrict__ blk_row, const int* __restrict__ blk_col,
+                         const int64_t* __restrict__ blk_off, const int* atom_sp, const int* sp_nfn,
+                         const double* __restrict__ W0, const double* __restrict__ SOx,
+                         const double* __restrict__ SOy, const double* __restrict__ SOz, double2* __restrict__ SS) {
+  const int q = blockIdx.x;
+  const int nfB = sp_nfn[atom_sp[blk_col[q]]];
+  const int nfA = sp_nfn[atom_sp[blk_row[q]]];
+  const int64_t o = blk_off[q];
+  for (int e = threadIdx.x; e < nfA * nfB; e += blockDim.x) {
+    const int i = e / nfB, j = e - i * nfB;
+    const double w = W0[o + e], x = SOx[o + e], y = SOy[o + e], z = SOz[o + e];
+    double2* r0 = SS + 4 * o + static_cast<int64_t>(2 * i) * (2 * nfB) + 2 * j;
+    double2* r1 = r0 + 2 * nfB;
+    r0[0] = make_double2(w, z);
+    r0[1] = make_double2(y, x);
+    r1[0] = make_double2(-y, x);
+    r1[1] = make_double2(w, -z);
+  }
+}
+
+q4c_status mirror_and_spinor(const q4c_grid* g, const q4c_matrices* out, cudaStream_t s) {
+  const q4c_tables* t = g->tables;
+  if (g->n_blocks == 0) return Q4C_OK;
+  {
+  KernelScope ks("mirror", s);
+  k_mirror<<<static_cast<unsigned>(g->n_blocks), 128, 0, s>>>(g->d_blk_row, g->d_blk_col, g->d_blk_T,
+                                                             g->d_blk_off, g->d_atom_sp, t->d_sp_nfn, out->V,
+                                                             out->W0, out->SOx, out->SOy, out->SOz);
+  }
+  Q4C_CUDA(cudaGetLastError());
+  if (out->spinor_SS) {
+    KernelScope ks("spinor", s);
+    k_spinor<<<static_cast<unsigned>(g->n_blocks), 128, 0, s>>>(
+        g->d_blk_row, g->d_blk_col, g->d_blk_off, g->d_atom_sp, t->d_sp_nfn, out->W0, out->SOx, out->SOy,
+        out->SOz, reinterpret_cast<double2*>(out->spinor_SS));
+    Q4C_CUDA(cudaGetLastError());
+  }
+  return Q4C_OK;
+}
+
+q4c_status integrate_fp64(const q4c_tables* t, const q4c_grid* g, const double* v, const q4c_matrices* out,
+                          cudaStream_t s) {
+  double* outs[5] = {out->V, out->W0, out->SOx, out->SOy, out->SOz};
+  for (double* o : outs) Q4C_CUDA(cudaMemsetAsync(o, 0, sizeof(double) * g->nnz, s));
+  const DevBasis B = t->view();
+  const DevGrid G = g->view();
+  for (size_t wv = 0; wv + 1 < g->wave_b0.size(); ++wv) {
+    const int64_t b0 = g->wave_b0[wv], b1 = g->wave_b0[wv + 1];
+    if (b1 > b0) {
+      {
+        KernelScope ks("basis", s);
+        k_basis_tiles<<<static_cast<unsigned>(b1 - b0), 256, 0, s>>>(B, G, b0, g->d_scr_off, g->d_scratch);
+      }
+      Q4C_CUDA(cudaGetLastError());
+    }
+    const int64_t t0 = g->wave_t0[wv], t1 = g->wave_t0[wv + 1];
+    if (t1 > t0) {
+      KernelScope ks("products_fp64", s);
+      k_products_fp64<<<static_cast<unsigned>(t1 - t0), 256, 0, s>>>(B, G, g->d_tiles, t0, g->d_scr_off,
+                                                                       g->d_scratch, v, out->V, out->W0, out->SOx,
+                                                                       out->SOy, out->SOz);
+      Q4C_CUDA(cudaGetLastError());
+    }
+  }
+  return mirror_and_spinor(g, out, s);
+}
+
+// ------------------------------------------------------------- density
+// One CTA per batch, one thread per point; P rows gathered into shared
+// memory kRows at a time: n_p = sum_i Phi_pi sum_j P_ij Phi_pj.
+constexpr int kRows = 16;
+__global__ void k_density_fp64(DevBasis B, DevGrid G, int64_t b0, const int64_t* __restrict__ scr_off,
+                               const double* __restrict__ scratch, const double* __restrict__ P,
+                               double* __restrict__ n_out) {
+  extern __shared__ double sP[];  // [kRows][nb]
+  const int64_t b = b0 + blockIdx.x;
+  const int64_t p0 = G.pt_ptr[b];
+  const int np = static_cast<int>(G.pt_ptr[b + 1] - p0);
+  const int ldp = (np + 7) & ~7;
+  const int nb = static_cast<int>(G.bat_fn_ptr[b + 1] - G.bat_fn_ptr[b]);
+  const int64_t f0 = G.bat_fn_ptr[b];
+  const int a0 = G.bat_atom_ptr[b], na = G.bat_atom_ptr[b + 1] - a0;
+  const int64_t pp = G.bat_pair_ptr[b];
+  const double* Phi = scratch + scr_off[b];
+  for (int pbase = 0; pbase < np; pbase += blockDim.x) {
+    const int p = pbase + threadIdx.x;
+    double acc = 0.0;
+    for (int i0 = 0; i0 < nb; i0 += kRows) {
+      const int rows = min(kRows, nb - i0);
+      __syncthreads();
+      for (int e = threadIdx.x; e < rows * nb; e += blockDim.x) {
+        const int r = e / nb, j = e - r * nb;
+        const int ii = G.fn_info[f0 + i0 + r], jj = G.fn_info[f0 + j];
+        const int64_t off = G.pair_off[pp + static_cast<int64_t>(ii >> 16) * na + (jj >> 16)];
+        sP[e] = off < 0 ? 0.0 : P[off + static_cast<int64_t>(ii & 0xffff) * local_nf(B, G, a0, jj >> 16) +
+                                  (jj & 0xffff)];
+      }
+      __syncthreads();
+      if (p < np) {
+        double t[kRows];
+#pragma unroll
+        for (int r = 0; r < kRows; ++r) t[r] = 0.0;
+        for (int j = 0; j < nb; ++j) {
+          const double pj = Phi[static_cast<int64_t>(j) * ldp + p];
+#pragma unroll
+          for (int r = 0; r < kRows; ++r)
+            if (r < rows) t[r] = fma(sP[r * nb + j], pj, t[r]);
+        }
+#pragma unroll
+        for (int r = 0; r < kRows; ++r)
+          if (r < rows) acc = fma(Phi[static_cast<int64_t>(i0 + r) * ldp + p], t[r], acc);
+      }
+    }
+    if (p < np) n_out[p0 + p] = acc;
+  }
+}
+
+q4c_status density_fp64(const q4c_tables* t, const q4c_grid* g, const double* P, double* n, cudaStream_t s) {
+  const DevBasis B = t->view();
+  const DevGrid G = g->view();
+  const size_t smem = sizeof(double) * kRows * std::max(g->max_nb, 1);
+  Q4C_CUDA(cudaFuncSetAttribute(k_density_fp64, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                static_cast<int>(smem)));
+  for (size_t wv = 0; wv + 1 < g->wave_b0.size(); ++wv) {
+    const int64_t b0 = g->wave_b0[wv], b1 = g->wave_b0[wv + 1];
+    if (b1 <= b0) continue;
+    {
+      KernelScope ks("basis", s);
+      k_basis_tiles<<<static_cast<unsigned>(b1 - b0), 256, 0, s>>>(B, G, b0, g->d_scr_off, g->d_scratch);
+    }
+    Q4C_CUDA(cudaGetLastError());
+    KernelScope ks("density_fp64", s);
+    k_density_fp64<<<static_cast<unsigned>(b1 - b0), 128, smem, s>>>(B, G, b0, g->d_scr_off, g->d_scratch, P, n);
+    Q4C_CUDA(cudaGetLastError());
+  }
+  return Q4C_OK;
+}
+
+// ------------------------------------------------------------- adjoint
+// dL/dv_p = w_p sum_ij [G^V phi_i phi_j + G^W grad_i.grad_j
+//                        + G^x (Y_i Z_j - Z_i Y_j) + G^y (Z_i X_j - X_i Z_j)
+//                        + G^z (X_i Y_j - Y_i X_j)]
+constexpr int kRowsB = 8;
+__global__ void k_backward_fp64(DevBasis B, DevGrid G, int64_t b0, const int64_t* __restrict__ scr_off,
+                                const double* __restrict__ scratch, const double* GV, const double* GW,
+                                const double* Gx, const double* Gy, const double* Gz, double* __restrict__ dLdv) {
+  extern __shared__ double sG[];  // [5][kRowsB][nb]
+  const int64_t b = b0 + blockIdx.x;
+  const int64_t p0 = G.pt_ptr[b];
+  const int np = static_cast<int>(G.pt_ptr[b + 1] - p0);
+  const int ldp = (np + 7) & ~7;
+  const int nb = static_cast<int>(G.bat_fn_ptr[b + 1] - G.bat_fn_ptr[b]);
+  const int64_t plane = static_cast<int64_t>(nb) * ldp;
+  const int64_t f0 = G.bat_fn_ptr[b];
+  const int a0 = G.bat_atom_ptr[b], na = G.bat_atom_ptr[b + 1] - a0;
+  const int64_t pp = G.bat_pair_ptr[b];
+  const double* T = scratch + scr_off[b];
+  const double* Gm[5] = {GV, GW, Gx, Gy, Gz};
+  for (int pbase = 0; pbase < np; pbase += blockDim.x) {
+    const int p = pbase + threadIdx.x;
+    double acc = 0.0;
+    for (int i0 = 0; i0 < nb; i0 += kRowsB) {
+      const int rows = min(kRowsB, nb - i0);
+      __syncthreads();
+      for (int e = threadIdx.x; e < rows * nb; e += blockDim.x) {
+        const int r = e / nb, j = e - r * nb;
+        const int ii = G.fn_info[f0 + i0 + r], jj = G.fn_info[f0 + j];
+        const int64_t off = G.pair_off[pp + static_cast<int64_t>(ii >> 16) * na + (jj >> 16)];
+        const int64_t el = off < 0 ? -1 : off + static_cast<int64_t>(ii & 0xffff) * local_nf(B, G, a0, jj >> 16) +
+                                              (jj & 0xffff);
+#pragma unroll
+        for (int m = 0; m < 5; ++m)
+          sG[(m * kRowsB + r) * nb + j] = (el < 0 || Gm[m] == nullptr) ? 0.0 : Gm[m][el];
+      }
+      __syncthreads();
+      if (p < np) {
+        double fi[kRowsB][4];
+#pragma unroll
+        for (int r = 0; r < kRowsB; ++r)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) fi[r][q] = r < rows ? T[q * plane + static_cast<int64_t>(i0 + r) * ldp + p] : 0.0;
+        for (int j = 0; j < nb; ++j) {
+          const double pj = T[static_cast<int64_t>(j) * ldp + p], xj = T[plane + static_cast<int64_t>(j) * ldp + p],
+                       yj = T[2 * plane + static_cast<int64_t>(j) * ldp + p],
+                       zj = T[3 * plane + static_cast<int64_t>(j) * ldp + p];
+#pragma unroll
+          for (int r = 0; r < kRowsB; ++r) {
+            if (r >= rows) continue;
+            const double* gr = sG + r * nb + j;
+            double s = gr[0] * fi[r][0] * pj;
+            s = fma(gr[kRowsB * nb], fi[r][1] * xj + fi[r][2] * yj + fi[r][3] * zj, s);
+            s = fma(gr[2 * kRowsB * nb], fi[r][2] * zj - fi[r][3] * yj, s);
+            s = fma(gr[3 * kRowsB * nb], fi[r][3] * xj - fi[r][1] * zj, s);
+            s = fma(gr[4 * kRowsB * nb], fi[r][1] * yj - fi[r][2] * xj, s);
+            acc += s;
+          }
+        }
+      }
+    }
+    if (p < np) dLdv[p0 + p] = G.w[p0 + p] * acc;
+  }
+}
+
+q4c_status backward_fp64(const q4c_tables* t, const q4c_grid* g, const q4c_matrices* Gm, double* dLdv,
+                         cudaStream_t s) {
+  const DevBasis B = t->view();
+  const DevGrid G = g->view();
+  const size_t smem = sizeof(double) * 5 * kRowsB * std::max(g->max_nb, 1);
+  Q4C_CUDA(cudaFuncSetAttribute(k_backward_fp64, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                static_cast<int>(smem)));
+  for (size_t wv = 0; wv + 1 < g->wave_b0.size(); ++wv) {
+    const int64_t b0 = g->wave_b0[wv], b1 = g->wave_b0[wv + 1];
+    if (b1 <= b0) continue;
+    {
+      KernelScope ks("basis", s);
+      k_basis_tiles<<<static_cast<unsigned>(b1 - b0), 256, 0, s>>>(B, G, b0, g->d_scr_off, g->d_scratch);
+    }
+    Q4C_CUDA(cudaGetLastError());
+    KernelScope ks("backward_fp64", s);
+    k_backward_fp64<<<static_cast<unsigned>(b1 - b0), 128, smem, s>>>(B, G, b0, g->d_scr_off, g->d_scratch, Gm->V,
+                                                                      Gm->W0, Gm->SOx, Gm->SOy, Gm->SOz, dLdv);
+    Q4C_CUDA(cudaGetLastError());
+  }
+  return Q4C_OK;
+}
+
+// ---------------------------------------------------------- basis probe
+__global__ void k_basis_eval(DevBasis B, DevGrid G, int n_basis, const int* __restrict__ atom_fn0, int64_t n_pts,
+                             const double* __restrict__ xyz, double* __restrict__ phi, double* __restrict__ grad) {
+  const int64_t item = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (item >= n_pts * G.n_atoms) return;
+  const int A = static_cast<int>(item / n_pts);
+  const int64_t p = item - A * n_pts;
+  const int f0 = atom_fn0[A];
+  atom_functions(B, G.atom_sp[A], xyz[3 * p] - G.atom_xyz[3 * A], xyz[3 * p + 1] - G.atom_xyz[3 * A + 1],
+                 xyz[3 * p + 2] - G.atom_xyz[3 * A + 2], [&](int k, double v, double gx, double gy, double gz) {
+                   const int64_t o = static_cast<int64_t>(f0 + k) * n_pts + p;
+                   phi[o] = v;
+                   grad[3 * o] = gx;
+                   grad[3 * o + 1] = gy;
+                   grad[3 * o + 2] = gz;
+                 });
+}
+
+q4c_status basis_eval(const q4c_tables* t, const q4c_grid* g, int64_t n_pts, const double* xyz, double* phi,
+                      double* grad, cudaStream_t s) {
+  if (n_pts == 0) return Q4C_OK;
+  const int64_t items = n_pts * g->n_atoms;
+  KernelScope ks("basis_eval", s);
+  k_basis_eval<<<static_cast<unsigned>((items + 127) / 128), 128, 0, s>>>(t->view(), g->view(), g->n_basis,
+                                                                         g->d_atom_fn0, n_pts, xyz, phi, grad);
+  Q4C_CUDA(cudaGetLastError());
+  return Q4C_OK;
+}
+
+}  // namespace q4c

@@ -1,0 +1,556 @@
+// grid_partition: atom-centred integration grid, Becke partition weights,
+// pruning, cut-plane batches, reduced index sets nnz(B_v) and the block
+// pattern (Section III A, Figs. 1-2, Eqs. 31-32).
+//
+// Host work is bookkeeping (raw points, bisection, index lists); the FP64
+// partition weights, the only arithmetic-heavy setup step (O(|N(r)|^2) per
+// point), run in one kernel.
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <numeric>
+#include <thread>
+
+#include "internal.h"
+
+namespace q4c {
+
+constexpr int kMaxNeighbours = 512;
+
+// Gauss-Legendre nodes (ascending) and weights by Newton's method on P_n,
+// with P_n' from (1 - x^2) P_n' = n (P_{n-1} - x P_n).
+static void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
+  x.assign(n, 0.0);
+  w.assign(n, 0.0);
+  for (int k = 0; k < n; ++k) {
+    double z = std::cos(M_PI * (4.0 * k + 3.0) / (4.0 * n + 2.0));
+    double p = 1.0, q = 0.0, dp = 1.0;
+    for (int it = 0; it < 64; ++it) {
+      p = z;
+      q = 1.0;
+      for (int j = 2; j <= n; ++j) {
+        const double nxt = ((2 * j - 1) * z * p - (j - 1) * q) / j;
+        q = p;
+        p = nxt;
+      }
+      if (n == 1) { p = z; q = 1.0; }
+      dp = n * (q - z * p) / (1.0 - z * z);
+      const double step = p / dp;
+      z -= step;
+      if (std::fabs(step) < 1e-16) break;
+    }
+    p = z;
+    q = 1.0;
+    for (int j = 2; j <= n; ++j) {
+      const double nxt = ((2 * j - 1) * z * p - (j - 1) * q) / j;
+      q = p;
+      p = nxt;
+    }
+    dp = n * (q - z * p) / (1.0 - z * z);
+    x[n - 1 - k] = z;
+    w[n - 1 - k] = 2.0 / ((1.0 - z * z) * dp * dp);
+  }
+}
+
+// Becke cell function s(mu) = (1 - f(f(f(mu))))/2, f(mu) = 1.5 mu - 0.5 mu^3
+__device__ __forceinline__ double becke_s(double mu) {
+  double f = mu;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) f = 1.5 * f - 0.5 * f * f * f;
+  return 0.5 * (1.0 - f);
+}
+
+// One thread per raw point: neighbour set N(r) = atoms within r_nb, then
+// p_owner = P_owner / sum_{C in N} P_C with P_A = prod_{B in N, B != A} s(mu_AB),
+// mu_AB = (|r - R_A| - |r - R_B|)/|R_A - R_B|.  near = some atom within r_c.
+__global__ void k_becke(const double* __restrict__ raw, const double* __restrict__ base_w, int64_t n_raw,
+                        int pts_per_atom, const double* __restrict__ atom_xyz, int n_atoms, double r_c,
+                        double r_nb, double* __restrict__ w_out, unsigned char* __restrict__ near_out,
+                        int* __restrict__ overflow) {
+  const int64_t p = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (p >= n_raw) return;
+  const int owner = static_cast<int>(p / pts_per_atom);
+  const double px = raw[3 * p], py = raw[3 * p + 1], pz = raw[3 * p + 2];
+  int nb_idx[kMaxNeighbours];
+  double nb_d[kMaxNeighbours];
+  int nn = 0, own_slot = -1;
+  bool near = false;
+  for (int B = 0; B < n_atoms; ++B) {
+    const double dx = px - atom_xyz[3 * B], dy = py - atom_xyz[3 * B + 1], dz = pz - atom_xyz[3 * B + 2];
+    const double d = sqrt(dx * dx + dy * dy + dz * dz);
+    if (d < r_c) near = true;
+    if (d < r_nb) {
+      if (nn == kMaxNeighbours) {
+        atomicExch(overflow, 1);
+        w_out[p] = 0.0;
+        near_out[p] = 0;
+        return;
+      }
+      if (B == owner) own_slot = nn;
+      nb_idx[nn] = B;
+      nb_d[nn] = d;
+      ++nn;
+    }
+  }
+  near_out[p] = near ? 1 : 0;
+  if (!near || own_slot < 0) {
+    w_out[p] = 0.0;
+    return;
+  }
+  auto cell = [&](int a) {
+    const int A = nb_idx[a];
+    const double ax = atom_xyz[3 * A], ay = atom_xyz[3 * A + 1], az = atom_xyz[3 * A + 2];
+    double P = 1.0;
+    for (int b = 0; b < nn && P != 0.0; ++b) {
+      if (b == a) continue;
+      const int B = nb_idx[b];
+      const double dx = ax - atom_xyz[3 * B], dy = ay - atom_xyz[3 * B + 1], dz = az - atom_xyz[3 * B + 2];
+      const double rab = sqrt(dx * dx + dy * dy + dz * dz);
+      P *= becke_s((nb_d[a] - nb_d[b]) / rab);
+    }
+    return P;
+  };
+  const double Pown = cell(own_slot);
+  if (Pown == 0.0) {
+    w_out[p] = 0.0;
+    return;
+  }
+  double sum = 0.0;
+  for (int a = 0; a < nn; ++a) sum += (a == own_slot) ? Pown : cell(a);
+  w_out[p] = base_w[p] * (Pown / sum);
+}
+
+}  // namespace q4c
+
+using namespace q4c;
+
+DevGrid q4c_grid::view() const {
+  DevGrid v;
+  v.x = d_x;
+  v.y = d_y;
+  v.z = d_z;
+  v.w = d_w;
+  v.atom_xyz = d_atom_xyz;
+  v.atom_sp = d_atom_sp;
+  v.pt_ptr = d_pt_ptr;
+  v.bat_atom_ptr = d_bat_atom_ptr;
+  v.bat_atoms = d_bat_atoms;
+  v.bat_atom_fn0 = d_bat_atom_fn0;
+  v.bat_fn_ptr = d_bat_fn_ptr;
+  v.fn_info = d_fn_info;
+  v.bat_pair_ptr = d_bat_pair_ptr;
+  v.pair_off = d_pair_off;
+  v.n_atoms = n_atoms;
+  return v;
+}
+
+template <typename T>
+static q4c_status up(T** dst, const std::vector<T>& src) {
+  Q4C_CUDA(cudaMalloc(reinterpret_cast<void**>(dst), sizeof(T) * std::max<size_t>(src.size(), 1)));
+  if (!src.empty()) Q4C_CUDA(cudaMemcpy(*dst, src.data(), sizeof(T) * src.size(), cudaMemcpyHostToDevice));
+  return Q4C_OK;
+}
+
+template <typename F>
+static void parallel_for(int64_t n, F&& f) {
+  unsigned nt = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+  if (n < 4096) nt = 1;
+  std::vector<std::thread> th;
+  for (unsigned t = 0; t < nt; ++t)
+    th.emplace_back([&, t] {
+      for (int64_t i = t; i < n; i += nt) f(i);
+    });
+  for (auto& x : th) x.join();
+}
+
+static int64_t scratch_cap_doubles() {
+  int64_t mb = 2048;
+  if (const char* e = std::getenv("Q4C_SCRATCH_MB")) mb = std::max<int64_t>(16, std::atoll(e));
+  return mb * (1 << 20) / 8;
+}
+
+extern "C" q4c_status grid_partition(const q4c_grid_desc* d, const q4c_tables* t, q4c_grid** out) {
+  Q4C_CHECK_ARG(d && t && out, "grid_partition: NULL argument");
+  *out = nullptr;
+  Q4C_CHECK_ARG(d->n_atoms >= 1 && d->xyz && d->species, "grid_partition: no atoms");
+  Q4C_CHECK_ARG(d->n_rad_shells >= 1 && d->n_theta >= 1 && d->n_phi >= 1 && d->R > 0 && d->r_nb > 0,
+                "grid_partition: bad grid parameters");
+  Q4C_CHECK_ARG(d->batch_max >= 1 && d->batch_max <= kMaxBatch, "grid_partition: batch_max must be in 1..1024");
+  for (int a = 0; a < d->n_atoms; ++a)
+    Q4C_CHECK_ARG(d->species[a] >= 0 && d->species[a] < t->n_species, "grid_partition: species out of range");
+  const int nA = d->n_atoms;
+  const double r_c = t->r_c;
+
+  auto* g = new q4c_grid();
+  g->tables = t;
+  cudaGetDevice(&g->device);
+  g->n_atoms = nA;
+  g->h_atom_xyz.assign(d->xyz, d->xyz + 3 * nA);
+  g->h_atom_sp.assign(d->species, d->species + nA);
+  g->h_nf_atom.resize(nA);
+  g->h_atom_fn0.resize(nA);
+  int nb_tot = 0;
+  for (int a = 0; a < nA; ++a) {
+    g->h_atom_fn0[a] = nb_tot;
+    g->h_nf_atom[a] = t->nfn[d->species[a]];
+    nb_tot += g->h_nf_atom[a];
+  }
+  g->n_basis = nb_tot;
+
+  // ---- raw points and base weights (w_rad * w_GL * 2 pi / n_phi)
+  std::vector<double> rr(d->n_rad_shells), wr(d->n_rad_shells), ct, wt;
+  for (int i = 1; i <= d->n_rad_shells; ++i) {
+    const double th = i * M_PI / (d->n_rad_shells + 1);
+    const double x = std::cos(th);
+    rr[i - 1] = d->R * (1.0 + x) / (1.0 - x);
+    wr[i - 1] = M_PI / (d->n_rad_shells + 1) * std::sin(th) * rr[i - 1] * rr[i - 1] * 2.0 * d->R /
+                ((1.0 - x) * (1.0 - x));
+  }
+  gauss_legendre(d->n_theta, ct, wt);
+  const int ppa = d->n_rad_shells * d->n_theta * d->n_phi;
+  const int64_t n_raw = static_cast<int64_t>(ppa) * nA;
+  std::vector<double> raw(3 * n_raw), base(n_raw);
+  parallel_for(nA, [&](int64_t A) {
+    int64_t p = A * ppa;
+    for (int i = 0; i < d->n_rad_shells; ++i)
+      for (int a = 0; a < d->n_theta; ++a) {
+        const double st = std::sqrt(1.0 - ct[a] * ct[a]);
+        for (int b = 0; b < d->n_phi; ++b, ++p) {
+          const double ph = (b + 0.5) * 2.0 * M_PI / d->n_phi;
+          raw[3 * p] = d->xyz[3 * A] + rr[i] * st * std::cos(ph);
+          raw[3 * p + 1] = d->xyz[3 * A + 1] + rr[i] * st * std::sin(ph);
+          raw[3 * p + 2] = d->xyz[3 * A + 2] + rr[i] * ct[a];
+          base[p] = wr[i] * wt[a] * (2.0 * M_PI / d->n_phi);
+        }
+      }
+  });
+
+  // ---- Becke weights on the device
+  std::vector<double> wfull(n_raw);
+  std::vector<unsigned char> nearv(n_raw);
+  {
+    double *d_raw = nullptr, *d_base = nullptr, *d_w = nullptr, *d_axyz = nullptr;
+    unsigned char* d_near = nullptr;
+    int* d_ovf = nullptr;
+    auto cleanup = [&] {
+      cudaFree(d_raw); cudaFree(d_base); cudaFree(d_w); cudaFree(d_axyz); cudaFree(d_near); cudaFree(d_ovf);
+    };
+    cudaError_t e = cudaSuccess;
+    int ovf = 0;
+    do {
+      if ((e = cudaMalloc(&d_raw, sizeof(double) * 3 * n_raw))) break;
+      if ((e = cudaMalloc(&d_base, sizeof(double) * n_raw))) break;
+      if ((e = cudaMalloc(&d_w, sizeof(double) * n_raw))) break;
+      if ((e = cudaMalloc(&d_axyz, sizeof(double) * 3 * nA))) break;
+      if ((e = cudaMalloc(&d_near, n_raw))) break;
+      if ((e = cudaMalloc(&d_ovf, sizeof(int)))) break;
+      if ((e = cudaMemset(d_ovf, 0, sizeof(int)))) break;
+      if ((e = cudaMemcpy(d_raw, raw.data(), sizeof(double) * 3 * n_raw, cudaMemcpyHostToDevice))) break;
+      if ((e = cudaMemcpy(d_base, base.data(), sizeof(double) * n_raw, cudaMemcpyHostToDevice))) break;
+      if ((e = cudaMemcpy(d_axyz, d->xyz, sizeof(double) * 3 * nA, cudaMemcpyHostToDevice))) break;
+      const int threads = 128;
+      const int64_t blocks = (n_raw + threads - 1) / threads;
+      k_becke<<<static_cast<unsigned>(blocks), threads>>>(d_raw, d_base, n_raw, ppa, d_axyz, nA, r_c, d->r_nb,
+                                                          d_w, d_near, d_ovf);
+      if ((e = cudaGetLastError())) break;
+      if ((e = cudaMemcpy(wfull.data(), d_w, sizeof(double) * n_raw, cudaMemcpyDeviceToHost))) break;
+      if ((e = cudaMemcpy(nearv.data(), d_near, n_raw, cudaMemcpyDeviceToHost))) break;
+      if ((e = cudaMemcpy(&ovf, d_ovf, sizeof(int), cudaMemcpyDeviceToHost))) break;
+    } while (0);
+    cleanup();
+    if (e != cudaSuccess) {
+      set_error(std::string("grid_partition: Becke pass: ") + cudaGetErrorString(e));
+      delete g;
+      return e == cudaErrorMemoryAllocation ? Q4C_ENOMEM : Q4C_ECUDA;
+    }
+    if (ovf) {
+      set_error("grid_partition: more than 512 atoms within r_nb of a grid point");
+      delete g;
+      return Q4C_EUNSUPPORTED;
+    }
+  }
+
+  // ---- prune: keep points within r_c of some atom with w != 0
+  std::vector<int64_t> kept;
+  kept.reserve(n_raw / 2);
+  for (int64_t p = 0; p < n_raw; ++p)
+    if (nearv[p] && wfull[p] != 0.0) kept.push_back(p);
+  if (kept.empty()) {
+    set_error("grid_partition: no grid point survives pruning");
+    delete g;
+    return Q4C_EINVAL;
+  }
+
+  // ---- cut-plane batches: recursive median bisection along the longest
+  // bounding-box axis; order by (coordinate, raw id)
+  std::vector<int64_t> order = kept;
+  std::vector<int64_t> bptr{0};
+  {
+    struct Range { int64_t lo, hi; };
+    std::vector<Range> stack{{0, static_cast<int64_t>(order.size())}};
+    std::vector<Range> leaves;
+    while (!stack.empty()) {
+      Range r = stack.back();
+      stack.pop_back();
+      if (r.hi - r.lo <= d->batch_max) {
+        leaves.push_back(r);
+        continue;
+      }
+      double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+      for (int64_t i = r.lo; i < r.hi; ++i)
+        for (int k = 0; k < 3; ++k) {
+          const double c = raw[3 * order[i] + k];
+          lo[k] = std::min(lo[k], c);
+          hi[k] = std::max(hi[k], c);
+        }
+      int ax = 0;
+      for (int k = 1; k < 3; ++k)
+        if (hi[k] - lo[k] > hi[ax] - lo[ax]) ax = k;
+      const int64_t mid = r.lo + (r.hi - r.lo) / 2;
+      std::nth_element(order.begin() + r.lo, order.begin() + mid, order.begin() + r.hi,
+                       [&](int64_t a, int64_t b) {
+                         const double ca = raw[3 * a + ax], cb = raw[3 * b + ax];
+                         return ca < cb || (ca == cb && a < b);
+                       });
+      // right half pushed first so the left half is emitted first (DFS order)
+      stack.push_back({mid, r.hi});
+      stack.push_back({r.lo, mid});
+    }
+    for (const Range& r : leaves) bptr.push_back(r.hi);
+  }
+  const int64_t nB = static_cast<int64_t>(bptr.size()) - 1;
+  const int64_t nP = static_cast<int64_t>(order.size());
+  g->n_pts = nP;
+  g->n_batches = nB;
+  g->h_pt_ptr = bptr;
+  g->h_xyz.resize(3 * nP);
+  g->h_w.resize(nP);
+  g->h_pid = order;
+  for (int64_t i = 0; i < nP; ++i) {
+    const int64_t p = order[i];
+    g->h_xyz[3 * i] = raw[3 * p];
+    g->h_xyz[3 * i + 1] = raw[3 * p + 1];
+    g->h_xyz[3 * i + 2] = raw[3 * p + 2];
+    g->h_w[i] = wfull[p];
+  }
+  raw.clear(); raw.shrink_to_fit();
+
+  // ---- active atoms per batch: some point strictly within r_c
+  std::vector<std::vector<int>> act(nB);
+  parallel_for(nB, [&](int64_t b) {
+    const int64_t p0 = bptr[b], p1 = bptr[b + 1];
+    double c[3] = {0, 0, 0};
+    for (int64_t i = p0; i < p1; ++i)
+      for (int k = 0; k < 3; ++k) c[k] += g->h_xyz[3 * i + k];
+    for (int k = 0; k < 3; ++k) c[k] /= static_cast<double>(p1 - p0);
+    double rad = 0;
+    for (int64_t i = p0; i < p1; ++i) {
+      double s = 0;
+      for (int k = 0; k < 3; ++k) s += (g->h_xyz[3 * i + k] - c[k]) * (g->h_xyz[3 * i + k] - c[k]);
+      rad = std::max(rad, std::sqrt(s));
+    }
+    for (int A = 0; A < nA; ++A) {
+      double s = 0;
+      for (int k = 0; k < 3; ++k) s += (d->xyz[3 * A + k] - c[k]) * (d->xyz[3 * A + k] - c[k]);
+      if (std::sqrt(s) >= rad + r_c + 1e-9) continue;
+      for (int64_t i = p0; i < p1; ++i) {
+        const double dx = g->h_xyz[3 * i] - d->xyz[3 * A], dy = g->h_xyz[3 * i + 1] - d->xyz[3 * A + 1],
+                     dz = g->h_xyz[3 * i + 2] - d->xyz[3 * A + 2];
+        if (std::sqrt(dx * dx + dy * dy + dz * dz) < r_c) {
+          act[b].push_back(A);
+          break;
+        }
+      }
+    }
+  });
+
+  // ---- block pattern: (A, B) iff |R_A - R_B| < 2 r_c; CSR sorted by B
+  g->h_blk_ptr.assign(nA + 1, 0);
+  std::vector<int> blk_row;
+  int64_t off = 0;
+  for (int A = 0; A < nA; ++A) {
+    for (int B = 0; B < nA; ++B) {
+      const double dx = d->xyz[3 * A] - d->xyz[3 * B], dy = d->xyz[3 * A + 1] - d->xyz[3 * B + 1],
+                   dz = d->xyz[3 * A + 2] - d->xyz[3 * B + 2];
+      if (std::sqrt(dx * dx + dy * dy + dz * dz) < 2.0 * r_c) {
+        g->h_blk_col.push_back(B);
+        blk_row.push_back(A);
+        g->h_blk_off.push_back(off);
+        off += static_cast<int64_t>(g->h_nf_atom[A]) * g->h_nf_atom[B];
+      }
+    }
+    g->h_blk_ptr[A + 1] = static_cast<int64_t>(g->h_blk_col.size());
+  }
+  g->h_blk_off.push_back(off);
+  g->n_blocks = static_cast<int64_t>(g->h_blk_col.size());
+  g->nnz = off;
+  auto find_block = [&](int A, int B) -> int64_t {
+    const int* b0 = g->h_blk_col.data() + g->h_blk_ptr[A];
+    const int* b1 = g->h_blk_col.data() + g->h_blk_ptr[A + 1];
+    const int* it = std::lower_bound(b0, b1, B);
+    return (it != b1 && *it == B) ? (it - g->h_blk_col.data()) : -1;
+  };
+  std::vector<int> blk_T(g->n_blocks);
+  for (int64_t q = 0; q < g->n_blocks; ++q) blk_T[q] = static_cast<int>(find_block(g->h_blk_col[q], blk_row[q]));
+
+  // ---- per-batch tables
+  g->h_bat_atom_ptr.assign(nB + 1, 0);
+  g->h_bat_fn_ptr.assign(nB + 1, 0);
+  std::vector<int64_t> pair_ptr(nB + 1, 0);
+  for (int64_t b = 0; b < nB; ++b) {
+    const int na = static_cast<int>(act[b].size());
+    int nb = 0;
+    for (int A : act[b]) nb += g->h_nf_atom[A];
+    g->h_bat_atom_ptr[b + 1] = g->h_bat_atom_ptr[b] + na;
+    g->h_bat_fn_ptr[b + 1] = g->h_bat_fn_ptr[b] + nb;
+    pair_ptr[b + 1] = pair_ptr[b] + static_cast<int64_t>(na) * na;
+    const int np = static_cast<int>(bptr[b + 1] - bptr[b]);
+    g->max_nb = std::max(g->max_nb, nb);
+    g->max_np = std::max(g->max_np, np);
+    g->max_na = std::max(g->max_na, na);
+    g->flops_alg += 14.0 * np * static_cast<double>(nb) * nb;
+    g->sum_np_nb += static_cast<double>(np) * nb;
+  }
+  std::vector<int> bat_atom_fn0(g->h_bat_atom_ptr[nB]);
+  g->h_bat_atoms.resize(g->h_bat_atom_ptr[nB]);
+  std::vector<int> fn_info(g->h_bat_fn_ptr[nB]);
+  std::vector<int64_t> pair_off(pair_ptr[nB]);
+  parallel_for(nB, [&](int64_t b) {
+    const int na = static_cast<int>(act[b].size());
+    int f = 0;
+    for (int a = 0; a < na; ++a) {
+      const int A = act[b][a];
+      g->h_bat_atoms[g->h_bat_atom_ptr[b] + a] = A;
+      bat_atom_fn0[g->h_bat_atom_ptr[b] + a] = f;
+      for (int k = 0; k < g->h_nf_atom[A]; ++k) fn_info[g->h_bat_fn_ptr[b] + f++] = (a << 16) | k;
+      for (int c = 0; c < na; ++c) {
+        const int64_t q = find_block(A, act[b][c]);
+        pair_off[pair_ptr[b] + static_cast<int64_t>(a) * na + c] = q < 0 ? -1 : g->h_blk_off[q];
+      }
+    }
+  });
+
+  // ---- FP64 path: waves whose basis tiles fit the scratch cap; 32x32 tiles
+  const int64_t cap = scratch_cap_doubles();
+  g->h_scr_off.assign(nB, 0);
+  std::vector<int4> tiles;
+  g->wave_b0.push_back(0);
+  g->wave_t0.push_back(0);
+  int64_t used = 0, peak = 0;
+  for (int64_t b = 0; b < nB; ++b) {
+    const int64_t np = bptr[b + 1] - bptr[b];
+    const int64_t nb = g->h_bat_fn_ptr[b + 1] - g->h_bat_fn_ptr[b];
+    const int64_t need = 4 * nb * ((np + 7) / 8 * 8);
+    if (used > 0 && used + need > cap) {
+      g->wave_b0.push_back(b);
+      g->wave_t0.push_back(static_cast<int64_t>(tiles.size()));
+      used = 0;
+    }
+    g->h_scr_off[b] = used;
+    used += need;
+    peak = std::max(peak, used);
+    const int nt = static_cast<int>((nb + 31) / 32);
+    for (int i = 0; i < nt; ++i)
+      for (int j = i; j < nt; ++j) tiles.push_back(make_int4(static_cast<int>(b), i, j, 0));
+  }
+  g->wave_b0.push_back(nB);
+  g->wave_t0.push_back(static_cast<int64_t>(tiles.size()));
+  g->scratch_doubles = std::max<int64_t>(peak, 1);
+
+  // ---- schedule for persistent kernels: descending n_p n_b^2
+  std::vector<int> sched(nB);
+  std::iota(sched.begin(), sched.end(), 0);
+  std::stable_sort(sched.begin(), sched.end(), [&](int a, int b) {
+    auto cost = [&](int x) {
+      const double np = static_cast<double>(bptr[x + 1] - bptr[x]);
+      const double nb = static_cast<double>(g->h_bat_fn_ptr[x + 1] - g->h_bat_fn_ptr[x]);
+      return np * nb * nb;
+    };
+    return cost(a) > cost(b);
+  });
+
+  // ---- upload
+  std::vector<double> sx(nP), sy(nP), sz(nP);
+  for (int64_t i = 0; i < nP; ++i) {
+    sx[i] = g->h_xyz[3 * i];
+    sy[i] = g->h_xyz[3 * i + 1];
+    sz[i] = g->h_xyz[3 * i + 2];
+  }
+  q4c_status st;
+  if ((st = up(&g->d_xyz, g->h_xyz)) || (st = up(&g->d_x, sx)) || (st = up(&g->d_y, sy)) ||
+      (st = up(&g->d_z, sz)) || (st = up(&g->d_w, g->h_w)) || (st = up(&g->d_atom_xyz, g->h_atom_xyz)) ||
+      (st = up(&g->d_atom_sp, g->h_atom_sp)) || (st = up(&g->d_atom_fn0, g->h_atom_fn0)) ||
+      (st = up(&g->d_pt_ptr, g->h_pt_ptr)) || (st = up(&g->d_bat_atom_ptr, g->h_bat_atom_ptr)) ||
+      (st = up(&g->d_bat_atoms, g->h_bat_atoms)) || (st = up(&g->d_bat_atom_fn0, bat_atom_fn0)) ||
+      (st = up(&g->d_bat_fn_ptr, g->h_bat_fn_ptr)) || (st = up(&g->d_fn_info, fn_info)) ||
+      (st = up(&g->d_bat_pair_ptr, pair_ptr)) || (st = up(&g->d_pair_off, pair_off)) ||
+      (st = up(&g->d_blk_off, g->h_blk_off)) || (st = up(&g->d_blk_row, blk_row)) ||
+      (st = up(&g->d_blk_col, g->h_blk_col)) || (st = up(&g->d_blk_T, blk_T)) ||
+      (st = up(&g->d_scr_off, g->h_scr_off)) || (st = up(&g->d_tiles, tiles)) || (st = up(&g->d_sched, sched))) {
+    q4c_grid_destroy(g);
+    return st;
+  }
+  {
+    cudaError_t e = cudaMalloc(&g->d_scratch, sizeof(double) * g->scratch_doubles);
+    if (e == cudaSuccess) e = cudaMalloc(&g->d_counter, sizeof(int) * 4);
+    if (e != cudaSuccess) {
+      set_error(std::string("grid_partition: workspace: ") + cudaGetErrorString(e));
+      q4c_grid_destroy(g);
+      return e == cudaErrorMemoryAllocation ? Q4C_ENOMEM : Q4C_ECUDA;
+    }
+  }
+  *out = g;
+  return Q4C_OK;
+}
+
+extern "C" void q4c_grid_destroy(q4c_grid* g) {
+  if (!g) return;
+  void* ptrs[] = {g->d_xyz, g->d_x, g->d_y, g->d_z, g->d_w, g->d_atom_xyz, g->d_atom_sp, g->d_atom_fn0,
+                  g->d_pt_ptr, g->d_bat_atom_ptr, g->d_bat_atoms, g->d_bat_atom_fn0, g->d_bat_fn_ptr,
+                  g->d_fn_info, g->d_bat_pair_ptr, g->d_pair_off, g->d_blk_off, g->d_blk_row, g->d_blk_col,
+                  g->d_blk_T, g->d_scr_off, g->d_tiles, g->d_scratch, g->d_sched, g->d_counter, g->d_split_ws};
+  for (void* p : ptrs) cudaFree(p);
+  delete g;
+}
+
+extern "C" q4c_status q4c_grid_get_info(const q4c_grid* g, q4c_grid_info* info) {
+  Q4C_CHECK_ARG(g && info, "q4c_grid_get_info: NULL argument");
+  info->n_points = g->n_pts;
+  info->n_batches = g->n_batches;
+  info->n_blocks = g->n_blocks;
+  info->nnz = g->nnz;
+  info->n_atoms = g->n_atoms;
+  info->n_basis = g->n_basis;
+  info->max_nb = g->max_nb;
+  info->max_np = g->max_np;
+  info->flops_alg = g->flops_alg;
+  info->sum_np_nb = g->sum_np_nb;
+  info->scratch_bytes = 8 * g->scratch_doubles + g->split_ws_bytes;
+  return Q4C_OK;
+}
+
+extern "C" q4c_status q4c_grid_export(const q4c_grid* g, double* xyz, double* w, int64_t* point_id,
+                                      int64_t* batch_ptr, int64_t* batch_atom_ptr, int32_t* batch_atoms,
+                                      int64_t* blk_ptr, int32_t* blk_col, int64_t* blk_off) {
+  Q4C_CHECK_ARG(g, "q4c_grid_export: NULL grid");
+  if (xyz) std::copy(g->h_xyz.begin(), g->h_xyz.end(), xyz);
+  if (w) std::copy(g->h_w.begin(), g->h_w.end(), w);
+  if (point_id) std::copy(g->h_pid.begin(), g->h_pid.end(), point_id);
+  if (batch_ptr) std::copy(g->h_pt_ptr.begin(), g->h_pt_ptr.end(), batch_ptr);
+  if (batch_atom_ptr)
+    for (size_t i = 0; i < g->h_bat_atom_ptr.size(); ++i) batch_atom_ptr[i] = g->h_bat_atom_ptr[i];
+  if (batch_atoms) std::copy(g->h_bat_atoms.begin(), g->h_bat_atoms.end(), batch_atoms);
+  if (blk_ptr) std::copy(g->h_blk_ptr.begin(), g->h_blk_ptr.end(), blk_ptr);
+  if (blk_col) std::copy(g->h_blk_col.begin(), g->h_blk_col.end(), blk_col);
+  if (blk_off) std::copy(g->h_blk_off.begin(), g->h_blk_off.end(), blk_off);
+  return Q4C_OK;
+}
+
+extern "C" q4c_status q4c_grid_points(const q4c_grid* g, const double** xyz_dev, const double** w_dev,
+                                      int64_t* n_points) {
+  Q4C_CHECK_ARG(g, "q4c_grid_points: NULL grid");
+  if (xyz_dev) *xyz_dev = g->d_xyz;
+  if (w_dev) *w_dev = g->d_w;
+  if (n_points) *n_points = g->n_pts;
+  return Q4C_OK;
+}

@@ -1,0 +1,152 @@
+// Internal declarations of the Q4C GB300 library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/q4c.h"
+
+namespace q4c {
+
+constexpr int kMaxL = 3;
+constexpr int kMaxBatch = 1024;
+
+// ---------------------------------------------------------------- errors
+void set_error(const std::string& msg);
+#define Q4C_CHECK_ARG(cond, msg)          \
+  do {                                    \
+    if (!(cond)) {                        \
+      ::q4c::set_error(msg);              \
+      return Q4C_EINVAL;                  \
+    }                                     \
+  } while (0)
+#define Q4C_CUDA(call)                                                                      \
+  do {                                                                                      \
+    cudaError_t e_ = (call);                                                                \
+    if (e_ != cudaSuccess) {                                                                \
+      ::q4c::set_error(std::string(#call) + ": " + cudaGetErrorString(e_));                 \
+      return e_ == cudaErrorMemoryAllocation ? Q4C_ENOMEM : Q4C_ECUDA;                      \
+    }                                                                                       \
+  } while (0)
+
+// ------------------------------------------------------- instrumentation
+// Records CUDA events around one kernel launch on `s` while profiling is on.
+class KernelScope {
+ public:
+  KernelScope(const char* name, cudaStream_t s);
+  ~KernelScope();
+ private:
+  const char* name_;
+  cudaStream_t s_;
+  cudaEvent_t e0_ = nullptr;
+};
+
+// ----------------------------------------------------- device-side views
+// Radial tables and species data as seen by kernels (passed by value).
+struct DevBasis {
+  const double* coef;    // [n_rad_tot][n_log-1][4] cubic in s on each interval
+  const double* g0;      // [n_rad_tot] g = u/r^(l+1) below r_min
+  const int* rad_l;      // [n_rad_tot]
+  const int* sp_rad0;    // [n_species] first radial of each species
+  const int* sp_nrad;    // [n_species]
+  const int* sp_nfn;     // [n_species]
+  double r_c, r_c2, r_min, inv_rmin, inv_h;
+  int n_log;
+};
+
+// Grid, batches and pattern as seen by kernels.
+struct DevGrid {
+  const double *x, *y, *z, *w;  // kept points, batch order (SoA)
+  const double* atom_xyz;       // [n_atoms][3]
+  const int* atom_sp;           // [n_atoms]
+  const int64_t* pt_ptr;        // [n_batches+1]
+  const int* bat_atom_ptr;      // [n_batches+1] into bat_atoms
+  const int* bat_atoms;         // active atoms, ascending
+  const int* bat_atom_fn0;      // local index of each active atom's first function
+  const int64_t* bat_fn_ptr;    // [n_batches+1] prefix of n_b
+  const int* fn_info;           // [sum n_b] (local atom << 16) | index within atom
+  const int64_t* bat_pair_ptr;  // [n_batches+1] into pair_off (n_a^2 per batch)
+  const int64_t* pair_off;      // value offset of block (A_a, A_b) or -1
+  int n_atoms;
+};
+
+}  // namespace q4c
+
+// ------------------------------------------------------------ handles
+struct q4c_tables {
+  int n_species = 0;
+  std::vector<int> n_rad, rad0, nfn, rad_l;
+  std::vector<double> alpha;
+  double r_c = 0, r_on = 0, r_min = 0, h = 0;
+  int n_log = 0;
+  std::vector<double> h_coef;  // host copy [n_rad_tot][n_log-1][4]
+  std::vector<double> h_g0;
+  // device
+  double* d_coef = nullptr;
+  double* d_g0 = nullptr;
+  int *d_rad_l = nullptr, *d_sp_rad0 = nullptr, *d_sp_nrad = nullptr, *d_sp_nfn = nullptr;
+  int device = 0;
+  q4c::DevBasis view() const;
+};
+
+struct q4c_grid {
+  const q4c_tables* tables = nullptr;
+  int device = 0;
+  int n_atoms = 0, n_basis = 0, max_nb = 0, max_np = 0, max_na = 0;
+  int64_t n_pts = 0, n_batches = 0, n_blocks = 0, nnz = 0;
+  double flops_alg = 0, sum_np_nb = 0;
+  // host copies
+  std::vector<double> h_xyz, h_w;
+  std::vector<int64_t> h_pid, h_pt_ptr, h_blk_ptr, h_blk_off, h_bat_fn_ptr;
+  std::vector<int> h_blk_col, h_bat_atom_ptr, h_bat_atoms, h_atom_sp, h_atom_fn0, h_nf_atom;
+  std::vector<double> h_atom_xyz;
+  // device: points
+  double *d_xyz = nullptr, *d_x = nullptr, *d_y = nullptr, *d_z = nullptr, *d_w = nullptr;
+  // device: atoms and batches
+  double* d_atom_xyz = nullptr;
+  int *d_atom_sp = nullptr, *d_atom_fn0 = nullptr;
+  int64_t* d_pt_ptr = nullptr;
+  int *d_bat_atom_ptr = nullptr, *d_bat_atoms = nullptr, *d_bat_atom_fn0 = nullptr;
+  int64_t* d_bat_fn_ptr = nullptr;
+  int* d_fn_info = nullptr;
+  int64_t *d_bat_pair_ptr = nullptr, *d_pair_off = nullptr;
+  // device: pattern
+  int64_t* d_blk_off = nullptr;
+  int *d_blk_row = nullptr, *d_blk_col = nullptr, *d_blk_T = nullptr;
+  // FP64 path: waves of batches whose basis tiles fit the scratch buffer
+  std::vector<int64_t> wave_b0;            // [n_waves+1] batch ranges
+  std::vector<int64_t> h_scr_off;          // [n_batches] offset (doubles) within its wave
+  int64_t* d_scr_off = nullptr;
+  std::vector<int64_t> wave_t0;            // [n_waves+1] ranges into the tile list
+  int4* d_tiles = nullptr;                 // (batch, ti, tj, 0), ti <= tj, 32x32 tiles
+  double* d_scratch = nullptr;
+  int64_t scratch_doubles = 0;
+  // split path: batch schedule (descending work) and persistent-kernel counter
+  int* d_sched = nullptr;
+  int* d_counter = nullptr;
+  int64_t split_ws_bytes = 0;
+  void* d_split_ws = nullptr;
+  q4c::DevGrid view() const;
+};
+
+namespace q4c {
+// fp64.cu
+q4c_status integrate_fp64(const q4c_tables* t, const q4c_grid* g, const double* v, const q4c_matrices* out,
+                          cudaStream_t s);
+q4c_status density_fp64(const q4c_tables* t, const q4c_grid* g, const double* P, double* n, cudaStream_t s);
+q4c_status backward_fp64(const q4c_tables* t, const q4c_grid* g, const q4c_matrices* G, double* dLdv,
+                         cudaStream_t s);
+q4c_status basis_eval(const q4c_tables* t, const q4c_grid* g, int64_t n_pts, const double* xyz, double* phi,
+                      double* grad, cudaStream_t s);
+q4c_status mirror_and_spinor(const q4c_grid* g, const q4c_matrices* out, cudaStream_t s);
+// split.cu
+q4c_status integrate_split(const q4c_tables* t, const q4c_grid* g, const double* v, const q4c_matrices* out,
+                           cudaStream_t s);
+// grid.cu
+q4c_status becke_weights(const double* d_raw_xyz, const double* d_base_w, int64_t n_raw, int pts_per_atom,
+                         const double* d_atom_xyz, const double* d_inv_rab, int n_atoms, double r_c, double r_nb,
+                         double* d_w, unsigned char* d_near);
+}  // namespace q4c
