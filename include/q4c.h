@@ -204,6 +204,13 @@ Q4C_API q4c_status q4c_basis_eval(const q4c_tables* tables, const q4c_grid* grid
                           const double* xyz_dev, double* phi_dev, double* grad_dev,
                           q4c_stream stream);
 
+/* Synchronises `stream` and reports whether any kernel that ran on this
+ * grid's data hit the iteration limit of one of its bounded waits (tensor-core
+ * completion barriers): Q4C_ETIMEOUT if so (the flag is then cleared), else
+ * Q4C_OK.  Such a kernel stops early instead of hanging, so its outputs are
+ * incomplete. */
+Q4C_API q4c_status q4c_grid_status(const q4c_grid* grid, q4c_stream stream);
+
 /* Kernel instrumentation.  q4c_profile(1) makes every later compute call
  * record a pair of CUDA events on its stream around each kernel it launches
  * (and count the launches); q4c_profile(0) stops recording.

@@ -25,7 +25,8 @@ STATUS = {0: "Q4C_OK", 1: "Q4C_EINVAL", 2: "Q4C_ENOMEM", 3: "Q4C_ECUDA", 4: "Q4C
 # every symbol include/q4c.h declares
 EXPORTS = ["nao_tabulate", "q4c_tables_destroy", "q4c_tables_export", "grid_partition", "q4c_grid_destroy",
            "q4c_grid_get_info", "q4c_grid_export", "q4c_grid_points", "q4c_integrate", "q4c_density",
-           "q4c_integrate_backward", "q4c_basis_eval", "q4c_profile", "q4c_profile_read", "q4c_last_error"]
+           "q4c_integrate_backward", "q4c_basis_eval", "q4c_grid_status", "q4c_profile", "q4c_profile_read",
+           "q4c_last_error"]
 
 
 class Q4CError(RuntimeError):
@@ -83,6 +84,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     L.q4c_density.argtypes = [vp, vp, vp, C.c_int, vp, vp]
     L.q4c_integrate_backward.argtypes = [vp, vp, C.POINTER(Matrices), C.c_int, vp, vp]
     L.q4c_basis_eval.argtypes = [vp, vp, i64, vp, vp, vp, vp]
+    L.q4c_grid_status.argtypes = [vp, vp]
     L.q4c_profile.argtypes = [i32]
     L.q4c_profile_read.argtypes = [C.c_char_p, C.POINTER(C.c_double), C.POINTER(i64)]
     L.q4c_last_error.restype = C.c_char_p
@@ -182,6 +184,10 @@ class Grid:
         return dict(xyz=xyz, w=w, point_id=pid, batch_ptr=bptr, batch_atom_ptr=baptr,
                     batch_atoms=batoms[:int(baptr[-1])], blk_ptr=blk_ptr, blk_col=blk_col[:i.n_blocks],
                     blk_off=blk_off)
+
+    def status(self, stream=None):
+        """Synchronise and raise Q4CError(Q4C_ETIMEOUT) if a bounded wait expired."""
+        _check(load().q4c_grid_status(self.h, _stream(stream)))
 
     def points_device(self):
         """(xyz_ptr, w_ptr, n) device pointers owned by the grid."""

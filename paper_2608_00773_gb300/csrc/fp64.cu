@@ -10,8 +10,18 @@ namespace q4c {
 // ------------------------------------------------------------------ basis
 // Tiles of batch b in the scratch wave: Phi, X, Y, Z each [n_b][ldp],
 // ldp = n_p rounded up to 8; one thread per (point, active atom).
+// With colexp != NULL (split path) it also records, per batch and local
+// function, binary exponents e with |value| < 2^e for the unscaled sets
+// (Phi, X, Y, Z: slots 4..7) and upper bounds for the D-scaled sets
+// (D = w v; slots 0..3, from e(D_p) + e(value)), colexp[8 n_b] per batch.
+__device__ __forceinline__ int binexp(double x) {  // |x| < 2^binexp(x), x != 0
+  const int E = static_cast<int>((__double_as_longlong(x) >> 52) & 0x7FF);
+  return E - 1022;
+}
+constexpr int kNoExp = -30000;
 __global__ void k_basis_tiles(DevBasis B, DevGrid G, int64_t b0, const int64_t* __restrict__ scr_off,
-                              double* __restrict__ scratch) {
+                              double* __restrict__ scratch, const double* __restrict__ v, int* __restrict__ colexp) {
+  extern __shared__ int s_exp[];  // [8][nb] when colexp != NULL
   const int64_t b = b0 + blockIdx.x;
   const int64_t p0 = G.pt_ptr[b];
   const int np = static_cast<int>(G.pt_ptr[b + 1] - p0);
@@ -20,20 +30,56 @@ __global__ void k_basis_tiles(DevBasis B, DevGrid G, int64_t b0, const int64_t* 
   const int nb = static_cast<int>(G.bat_fn_ptr[b + 1] - G.bat_fn_ptr[b]);
   double* base = scratch + scr_off[b];
   const int64_t plane = static_cast<int64_t>(nb) * ldp;
+  if (colexp) {
+    for (int i = threadIdx.x; i < 8 * nb; i += blockDim.x) s_exp[i] = kNoExp;
+    __syncthreads();
+  }
   for (int item = threadIdx.x; item < np * na; item += blockDim.x) {
     const int a = item / np, p = item - a * np;
     const int A = G.bat_atoms[a0 + a];
     const int f0 = G.bat_atom_fn0[a0 + a];
     const double dx = G.x[p0 + p] - G.atom_xyz[3 * A], dy = G.y[p0 + p] - G.atom_xyz[3 * A + 1],
                  dz = G.z[p0 + p] - G.atom_xyz[3 * A + 2];
+    int eD = kNoExp;
+    if (colexp) {
+      const double D = G.w[p0 + p] * v[p0 + p];
+      if (D != 0.0) eD = binexp(D);
+    }
     atom_functions(B, G.atom_sp[A], dx, dy, dz, [&](int k, double phi, double gx, double gy, double gz) {
       double* q = base + static_cast<int64_t>(f0 + k) * ldp + p;
       q[0] = phi;
       q[plane] = gx;
       q[2 * plane] = gy;
       q[3 * plane] = gz;
+      if (colexp) {
+        const double vals[4] = {phi, gx, gy, gz};
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+          if (vals[s] == 0.0) continue;
+          const int e = binexp(vals[s]);
+          atomicMax(&s_exp[(4 + s) * nb + f0 + k], e);
+          if (eD != kNoExp) atomicMax(&s_exp[s * nb + f0 + k], e + eD);
+        }
+      }
     });
   }
+  if (colexp) {
+    __syncthreads();
+    int* out = colexp + 8 * G.bat_fn_ptr[b];
+    for (int i = threadIdx.x; i < 8 * nb; i += blockDim.x) out[i] = s_exp[i];
+  }
+}
+
+q4c_status launch_basis_tiles(const q4c_tables* t, const q4c_grid* g, int64_t b0, int64_t b1, const double* v,
+                              int* colexp, cudaStream_t s) {
+  const size_t smem = colexp ? sizeof(int) * 8 * std::max(g->max_nb, 1) : 0;
+  if (smem > 48 * 1024)
+    Q4C_CUDA(cudaFuncSetAttribute(k_basis_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
+  KernelScope ks("basis", s);
+  k_basis_tiles<<<static_cast<unsigned>(b1 - b0), 256, smem, s>>>(t->view(), g->view(), b0, g->d_scr_off,
+                                                                   g->d_scratch, v, colexp);
+  Q4C_CUDA(cudaGetLastError());
+  return Q4C_OK;
 }
 
 // nf of the atom behind local atom a of a batch
@@ -210,11 +256,7 @@ q4c_status integrate_fp64(const q4c_tables* t, const q4c_grid* g, const double* 
   for (size_t wv = 0; wv + 1 < g->wave_b0.size(); ++wv) {
     const int64_t b0 = g->wave_b0[wv], b1 = g->wave_b0[wv + 1];
     if (b1 > b0) {
-      {
-        KernelScope ks("basis", s);
-        k_basis_tiles<<<static_cast<unsigned>(b1 - b0), 256, 0, s>>>(B, G, b0, g->d_scr_off, g->d_scratch);
-      }
-      Q4C_CUDA(cudaGetLastError());
+      if (q4c_status st = launch_basis_tiles(t, g, b0, b1, nullptr, nullptr, s)) return st;
     }
     const int64_t t0 = g->wave_t0[wv], t1 = g->wave_t0[wv + 1];
     if (t1 > t0) {
@@ -287,11 +329,7 @@ q4c_status density_fp64(const q4c_tables* t, const q4c_grid* g, const double* P,
   for (size_t wv = 0; wv + 1 < g->wave_b0.size(); ++wv) {
     const int64_t b0 = g->wave_b0[wv], b1 = g->wave_b0[wv + 1];
     if (b1 <= b0) continue;
-    {
-      KernelScope ks("basis", s);
-      k_basis_tiles<<<static_cast<unsigned>(b1 - b0), 256, 0, s>>>(B, G, b0, g->d_scr_off, g->d_scratch);
-    }
-    Q4C_CUDA(cudaGetLastError());
+    if (q4c_status st = launch_basis_tiles(t, g, b0, b1, nullptr, nullptr, s)) return st;
     KernelScope ks("density_fp64", s);
     k_density_fp64<<<static_cast<unsigned>(b1 - b0), 128, smem, s>>>(B, G, b0, g->d_scr_off, g->d_scratch, P, n);
     Q4C_CUDA(cudaGetLastError());
@@ -374,11 +412,7 @@ q4c_status backward_fp64(const q4c_tables* t, const q4c_grid* g, const q4c_matri
   for (size_t wv = 0; wv + 1 < g->wave_b0.size(); ++wv) {
     const int64_t b0 = g->wave_b0[wv], b1 = g->wave_b0[wv + 1];
     if (b1 <= b0) continue;
-    {
-      KernelScope ks("basis", s);
-      k_basis_tiles<<<static_cast<unsigned>(b1 - b0), 256, 0, s>>>(B, G, b0, g->d_scr_off, g->d_scratch);
-    }
-    Q4C_CUDA(cudaGetLastError());
+    if (q4c_status st = launch_basis_tiles(t, g, b0, b1, nullptr, nullptr, s)) return st;
     KernelScope ks("backward_fp64", s);
     k_backward_fp64<<<static_cast<unsigned>(b1 - b0), 128, smem, s>>>(B, G, b0, g->d_scr_off, g->d_scratch, Gm->V,
                                                                       Gm->W0, Gm->SOx, Gm->SOy, Gm->SOz, dLdv);

@@ -457,6 +457,30 @@ extern "C" q4c_status grid_partition(const q4c_grid_desc* d, const q4c_tables* t
   g->wave_t0.push_back(static_cast<int64_t>(tiles.size()));
   g->scratch_doubles = std::max<int64_t>(peak, 1);
 
+  // ---- split path: (batch, output, ti, tj) items per wave, 64x64 tiles;
+  // V and W0 need ti <= tj only, the A_yz/A_zx/A_xy products every tile.
+  // Largest work first inside each wave (persistent CTAs pull in order).
+  std::vector<int4> sitems;
+  g->split_w0.push_back(0);
+  for (size_t wv = 0; wv + 1 < g->wave_b0.size(); ++wv) {
+    std::vector<std::pair<double, int4>> lst;
+    for (int64_t b = g->wave_b0[wv]; b < g->wave_b0[wv + 1]; ++b) {
+      const int64_t np = bptr[b + 1] - bptr[b];
+      const int nb = static_cast<int>(g->h_bat_fn_ptr[b + 1] - g->h_bat_fn_ptr[b]);
+      const int nt = (nb + 63) / 64;
+      for (int o = 0; o < 5; ++o)
+        for (int i = 0; i < nt; ++i)
+          for (int j = 0; j < nt; ++j) {
+            if (o <= 1 && i > j) continue;
+            const double cost = static_cast<double>(np) * (o == 1 ? 3.0 : 1.0);
+            lst.push_back({cost, make_int4(static_cast<int>(b), o, i, j)});
+          }
+    }
+    std::stable_sort(lst.begin(), lst.end(), [](const auto& a, const auto& b) { return a.first > b.first; });
+    for (auto& x : lst) sitems.push_back(x.second);
+    g->split_w0.push_back(static_cast<int64_t>(sitems.size()));
+  }
+
   // ---- schedule for persistent kernels: descending n_p n_b^2
   std::vector<int> sched(nB);
   std::iota(sched.begin(), sched.end(), 0);
@@ -486,13 +510,19 @@ extern "C" q4c_status grid_partition(const q4c_grid_desc* d, const q4c_tables* t
       (st = up(&g->d_bat_pair_ptr, pair_ptr)) || (st = up(&g->d_pair_off, pair_off)) ||
       (st = up(&g->d_blk_off, g->h_blk_off)) || (st = up(&g->d_blk_row, blk_row)) ||
       (st = up(&g->d_blk_col, g->h_blk_col)) || (st = up(&g->d_blk_T, blk_T)) ||
-      (st = up(&g->d_scr_off, g->h_scr_off)) || (st = up(&g->d_tiles, tiles)) || (st = up(&g->d_sched, sched))) {
+      (st = up(&g->d_scr_off, g->h_scr_off)) || (st = up(&g->d_tiles, tiles)) || (st = up(&g->d_sched, sched)) ||
+      (st = up(&g->d_split_items, sitems))) {
     q4c_grid_destroy(g);
     return st;
   }
   {
+    const size_t n_waves = g->wave_b0.size() - 1;
     cudaError_t e = cudaMalloc(&g->d_scratch, sizeof(double) * g->scratch_doubles);
-    if (e == cudaSuccess) e = cudaMalloc(&g->d_counter, sizeof(int) * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&g->d_counter, sizeof(int) * std::max<size_t>(n_waves, 1));
+    if (e == cudaSuccess) e = cudaMalloc(&g->d_colexp, sizeof(int) * 8 * std::max<int64_t>(g->h_bat_fn_ptr[nB], 1));
+    if (e == cudaSuccess) e = cudaMalloc(&g->d_status, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMemset(g->d_status, 0, sizeof(unsigned));
+    g->split_ws_bytes = static_cast<int64_t>(sizeof(int)) * 8 * g->h_bat_fn_ptr[nB];
     if (e != cudaSuccess) {
       set_error(std::string("grid_partition: workspace: ") + cudaGetErrorString(e));
       q4c_grid_destroy(g);
@@ -508,7 +538,8 @@ extern "C" void q4c_grid_destroy(q4c_grid* g) {
   void* ptrs[] = {g->d_xyz, g->d_x, g->d_y, g->d_z, g->d_w, g->d_atom_xyz, g->d_atom_sp, g->d_atom_fn0,
                   g->d_pt_ptr, g->d_bat_atom_ptr, g->d_bat_atoms, g->d_bat_atom_fn0, g->d_bat_fn_ptr,
                   g->d_fn_info, g->d_bat_pair_ptr, g->d_pair_off, g->d_blk_off, g->d_blk_row, g->d_blk_col,
-                  g->d_blk_T, g->d_scr_off, g->d_tiles, g->d_scratch, g->d_sched, g->d_counter, g->d_split_ws};
+                  g->d_blk_T, g->d_scr_off, g->d_tiles, g->d_scratch, g->d_sched, g->d_counter, g->d_split_ws,
+                  g->d_split_items, g->d_colexp, g->d_status};
   for (void* p : ptrs) cudaFree(p);
   delete g;
 }
@@ -552,5 +583,18 @@ extern "C" q4c_status q4c_grid_points(const q4c_grid* g, const double** xyz_dev,
   if (xyz_dev) *xyz_dev = g->d_xyz;
   if (w_dev) *w_dev = g->d_w;
   if (n_points) *n_points = g->n_pts;
+  return Q4C_OK;
+}
+
+extern "C" q4c_status q4c_grid_status(const q4c_grid* g, q4c_stream stream) {
+  Q4C_CHECK_ARG(g, "q4c_grid_status: NULL grid");
+  Q4C_CUDA(cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream)));
+  unsigned st = 0;
+  Q4C_CUDA(cudaMemcpy(&st, g->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost));
+  if (st) {
+    Q4C_CUDA(cudaMemset(g->d_status, 0, sizeof(unsigned)));
+    set_error("a bounded device wait expired in a kernel of this grid");
+    return Q4C_ETIMEOUT;
+  }
   return Q4C_OK;
 }

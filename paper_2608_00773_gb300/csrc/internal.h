@@ -124,9 +124,14 @@ struct q4c_grid {
   int4* d_tiles = nullptr;                 // (batch, ti, tj, 0), ti <= tj, 32x32 tiles
   double* d_scratch = nullptr;
   int64_t scratch_doubles = 0;
-  // split path: batch schedule (descending work) and persistent-kernel counter
+  // split path: work items (batch, output, ti, tj) per wave, sorted by cost,
+  // per-batch column exponents, persistent-kernel counters, status word
   int* d_sched = nullptr;
-  int* d_counter = nullptr;
+  int* d_counter = nullptr;                // [n_waves]
+  std::vector<int64_t> split_w0;           // [n_waves+1] ranges into d_split_items
+  int4* d_split_items = nullptr;
+  int* d_colexp = nullptr;                 // [8 * sum n_b]
+  unsigned* d_status = nullptr;            // bit 0: a bounded wait expired
   int64_t split_ws_bytes = 0;
   void* d_split_ws = nullptr;
   q4c::DevGrid view() const;
@@ -142,6 +147,8 @@ q4c_status backward_fp64(const q4c_tables* t, const q4c_grid* g, const q4c_matri
 q4c_status basis_eval(const q4c_tables* t, const q4c_grid* g, int64_t n_pts, const double* xyz, double* phi,
                       double* grad, cudaStream_t s);
 q4c_status mirror_and_spinor(const q4c_grid* g, const q4c_matrices* out, cudaStream_t s);
+q4c_status launch_basis_tiles(const q4c_tables* t, const q4c_grid* g, int64_t b0, int64_t b1, const double* v,
+                              int* colexp, cudaStream_t s);
 // split.cu
 q4c_status integrate_split(const q4c_tables* t, const q4c_grid* g, const double* v, const q4c_matrices* out,
                            cudaStream_t s);

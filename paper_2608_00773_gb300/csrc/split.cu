@@ -1,11 +1,431 @@
-// Split-precision batch products on tcgen05 tensor cores (in progress).
+// Split-precision batch products on the tcgen05 tensor cores.
+//
+// Every batch product C = (D Q_a)^T Q_b (Eqs. 29-32 with F = v; D = diag(w v),
+// Q in {Phi, X, Y, Z}) is computed exactly enough for ~1e-9 relative error
+// from BF16 slices (an Ozaki-type error-free splitting; Ozaki, Ogita, Oishi
+// and Rump 2012):
+//   x = sum_s d_s 2^(e - 6 - 8s),  s = 0..3,  |d_0| <= 64, |d_s| <= 128,
+// with e a per-column binary exponent (|x| < 2^e over the batch).  Each digit
+// has <= 8 significant bits, so it is exact in BF16 and every slice product
+// is exact in FP32.  Per output element three FP32 accumulators are kept in
+// tensor memory:
+//   L0 = sum d0 e0          (exact: < 2^24 units for n_p <= 341)
+//   L1 = sum d0 e1 + d1 e0  (exact)
+//   L2 = the s + t in {2, 3} terms (rounded, 2^-16 below L0)
+// and combined as a double-float, then added into the FP64 block pattern.
+//
+// Layout trick: the four slices of one operand set live in shared memory as
+// five consecutive 64-row tiles [Z, A0, A1, A2, A3] (Z = zeros).  An M = 128
+// MMA starting at tile k reads rows [tile_k; tile_k+1], so six MMAs per
+// K-step cover the ten slice pairs with s + t <= 3:
+//   TMEM block 0 = [L0; L1]:  [A0;A1] x B0,  [Z;A0] x B1
+//   TMEM block 1 = [L2; L2']: [A2;A3] x B0,  [A1;A2] x B1,  [A0;A1] x B2,  [A0;A1] x B3
+// (the bottom halves of block 1 collect level-3 terms and one level-4 term).
+//
+// Outputs per (batch, 64x64 tile): V = (D Phi)^T Phi, W0 = sum_q (D Q)^T Q
+// (three products into one accumulator), and A_yz = (D Y)^T Z,
+// A_zx = (D Z)^T X, A_xy = (D X)^T Y with SO_x = A_yz - A_yz^T etc. applied
+// while scattering.  One persistent CTA per SM (128 threads, 128 TMEM
+// columns) loops over work items; every mbarrier wait is bounded and sets a
+// status bit instead of hanging.
+#include <cuda_bf16.h>
+
 #include "internal.h"
 
 namespace q4c {
+namespace split {
 
-q4c_status integrate_split(const q4c_tables*, const q4c_grid*, const double*, const q4c_matrices*, cudaStream_t) {
-  set_error("q4c_integrate: the split-precision path is not built yet");
-  return Q4C_EUNSUPPORTED;
+constexpr int kTile = 64;          // functions per tile (rows of one half of M)
+constexpr int kKc = 32;            // points per chunk (two K = 16 MMA steps)
+constexpr int kTileBytes = kTile * kKc * 2;  // 4 KB
+constexpr int kSBO = (kKc / 8) * 128;        // 512 B between 8-row groups
+constexpr int kLBO = 128;                    // core matrices adjacent in K
+constexpr int kThreads = 128;
+constexpr int kMaxProducts = 3;
+constexpr int kAStride = 5 * kTileBytes;     // [Z, A0, A1, A2, A3]
+constexpr int kBStride = 4 * kTileBytes;     // [B0, B1, B2, B3]
+constexpr int kSmemA = 0;
+constexpr int kSmemB = kSmemA + kMaxProducts * kAStride;        // 60 KB
+constexpr int kSmemD = kSmemB + kMaxProducts * kBStride;        // +48 KB
+constexpr int kSmemExp = kSmemD + kKc * 8;
+constexpr int kSmemBar = kSmemExp + 2 * kMaxProducts * kTile * 4;
+constexpr int kSmemTotal = kSmemBar + 64;
+constexpr uint32_t kTmemCols = 128;
+constexpr uint64_t kWaitLimitNs = 1000000000ull;  // 1 s of wall clock per wait
+
+// ------------------------------------------------------------ PTX helpers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// K-major, no-swizzle shared-memory matrix descriptor (tcgen05 format)
+__device__ __forceinline__ uint64_t make_desc(uint32_t addr) {
+  uint64_t d = 0;
+  d |= static_cast<uint64_t>((addr >> 4) & 0x3FFF);
+  d |= static_cast<uint64_t>((kLBO >> 4) & 0x3FFF) << 16;
+  d |= static_cast<uint64_t>((kSBO >> 4) & 0x3FFF) << 32;
+  d |= static_cast<uint64_t>(1) << 46;  // descriptor version for tcgen05
+  return d;                              // base offset 0, swizzle none
+}
+
+// kind::f16 instruction descriptor: BF16 x BF16 -> FP32, both K-major
+__device__ __forceinline__ uint32_t make_idesc(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | (static_cast<uint32_t>(N >> 3) << 17) |
+         (static_cast<uint32_t>(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// bounded wait; returns false (and sets the status bit) once 1 s has passed
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, unsigned* status) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  while (true) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (global_ns() - t0 > kWaitLimitNs) break;
+  }
+  atomicOr(status, 1u);
+  return false;
+}
+
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// ------------------------------------------------------------ slicing
+// x = sum_s d_s 2^(e - 6 - 8 s) + O(2^(e-31)), digits from the integer
+// N = round(x 2^(30 - e)) by balanced base-256 extraction (|d_0| <= 64).
+__device__ __forceinline__ void digits4(double x, int e, int d[4]) {
+  d[0] = d[1] = d[2] = d[3] = 0;
+  const long long bits = __double_as_longlong(x);
+  const int E = static_cast<int>((bits >> 52) & 0x7FF);
+  if (E == 0 || e < -1000) return;  // zero (or below the FP64 normal range)
+  const long long M = (bits & 0xFFFFFFFFFFFFFLL) | (1LL << 52);
+  const int sh = 1075 + e - 30 - E;  // >= 23 because |x| < 2^e
+  if (sh >= 62) return;
+  long long N = (M + (1LL << (sh - 1))) >> sh;
+  if (bits < 0) N = -N;
+  const long long q0 = (N + (1LL << 23)) >> 24;
+  long long r = N - (q0 << 24);
+  const long long q1 = (r + (1LL << 15)) >> 16;
+  r -= q1 << 16;
+  const long long q2 = (r + (1LL << 7)) >> 8;
+  r -= q2 << 8;
+  d[0] = static_cast<int>(q0);
+  d[1] = static_cast<int>(q1);
+  d[2] = static_cast<int>(q2);
+  d[3] = static_cast<int>(r);
+}
+
+__device__ __forceinline__ float pow2f(int k) {  // 2^k as float, 0 below the normal range
+  return (k < -126) ? 0.0f : __int_as_float((k + 127) << 23);
+}
+
+// ------------------------------------------------------------ kernel
+struct Products {
+  int n;
+  int qa[kMaxProducts];  // A-side (D-scaled) quantity: 0 Phi, 1 X, 2 Y, 3 Z
+  int qb[kMaxProducts];  // B-side quantity
+};
+
+__device__ __forceinline__ Products products_of(int o) {
+  Products P;
+  switch (o) {
+    case 0: P.n = 1; P.qa[0] = 0; P.qb[0] = 0; break;              // V
+    case 1: P.n = 3; P.qa[0] = 1; P.qb[0] = 1; P.qa[1] = 2; P.qb[1] = 2; P.qa[2] = 3; P.qb[2] = 3; break;  // W0
+    case 2: P.n = 1; P.qa[0] = 2; P.qb[0] = 3; break;              // A_yz -> SO_x
+    case 3: P.n = 1; P.qa[0] = 3; P.qb[0] = 1; break;              // A_zx -> SO_y
+    default: P.n = 1; P.qa[0] = 1; P.qb[0] = 2; break;             // A_xy -> SO_z
+  }
+  return P;
+}
+
+__device__ __forceinline__ int local_nf(const DevBasis& B, const DevGrid& G, int a0, int a) {
+  return __ldg(B.sp_nfn + G.atom_sp[G.bat_atoms[a0 + a]]);
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+    k_split_products(DevBasis B, DevGrid G, const int4* __restrict__ items, int n_items, int* counter,
+                     const int64_t* __restrict__ scr_off, const double* __restrict__ scratch,
+                     const int* __restrict__ colexp, const double* __restrict__ v, double* V, double* W0,
+                     double* SOx, double* SOy, double* SOz, unsigned* status) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  unsigned char* sA = smem + kSmemA;
+  unsigned char* sB = smem + kSmemB;
+  double* sD = reinterpret_cast<double*>(smem + kSmemD);
+  int* sExpA = reinterpret_cast<int*>(smem + kSmemExp);
+  int* sExpB = sExpA + kMaxProducts * kTile;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + kSmemBar);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + kSmemBar + 16);
+  int* s_item = reinterpret_cast<int*>(smem + kSmemBar + 32);
+  float* stage = reinterpret_cast<float*>(sB);  // epilogue staging reuses the B tiles (16 KB)
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const uint32_t bar_addr = smem_u32(bar);
+
+  // zero tiles Z of every product slot (never overwritten)
+  for (int i = tid; i < kMaxProducts * kTileBytes / 16; i += kThreads) {
+    const int slot = i / (kTileBytes / 16), off = i - slot * (kTileBytes / 16);
+    reinterpret_cast<uint4*>(sA + slot * kAStride)[off] = make_uint4(0, 0, 0, 0);
+  }
+  if (tid == 0) mbar_init(bar_addr, 1);
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(kTmemCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  uint32_t phase = 0;
+  bool ok = true;
+
+  while (ok) {
+    if (tid == 0) *s_item = atomicAdd(counter, 1);
+    __syncthreads();
+    const int it = *s_item;
+    if (it >= n_items) break;
+    const int4 item = items[it];
+    const int64_t b = item.x;
+    const int o = item.y, ti = item.z, tj = item.w;
+    const int64_t p0 = G.pt_ptr[b];
+    const int np = static_cast<int>(G.pt_ptr[b + 1] - p0);
+    const int ldp = (np + 7) & ~7;
+    const int nb = static_cast<int>(G.bat_fn_ptr[b + 1] - G.bat_fn_ptr[b]);
+    const int64_t plane = static_cast<int64_t>(nb) * ldp;
+    const double* base = scratch + scr_off[b];
+    const int* cexp = colexp + 8 * G.bat_fn_ptr[b];
+    const Products P = products_of(o);
+    const int i0 = ti * kTile, j0 = tj * kTile;
+    const int ncols = min(kTile, nb - j0);
+    const int N = (ncols + 15) & ~15;
+    const uint32_t idesc = make_idesc(128, N);
+
+    for (int k = tid; k < P.n * kTile; k += kThreads) {
+      const int pr = k / kTile, r = k - pr * kTile;
+      sExpA[pr * kTile + r] = (i0 + r < nb) ? cexp[P.qa[pr] * nb + i0 + r] : -30000;
+      sExpB[pr * kTile + r] = (j0 + r < nb) ? cexp[(4 + P.qb[pr]) * nb + j0 + r] : -30000;
+    }
+
+    const int n_chunks = (np + kKc - 1) / kKc;
+    for (int c = 0; c < n_chunks && ok; ++c) {
+      const int kc0 = c * kKc;
+      // the tiles may be overwritten only after the previous chunk's MMAs finished
+      if (c > 0) {
+        ok = __syncthreads_and(mbar_wait(bar_addr, phase & 1, status));
+        ++phase;
+        tc_fence_after();
+        if (!ok) break;
+      }
+      if (tid < kKc) {
+        const int p = kc0 + tid;
+        sD[tid] = p < np ? G.w[p0 + p] * v[p0 + p] : 0.0;
+      }
+      __syncthreads();
+      // slice: one (row r, point pair kp) unit per lane per step, conflict-free stores
+      for (int pr = 0; pr < P.n; ++pr) {
+        for (int side = 0; side < 2; ++side) {
+          const int q = side == 0 ? P.qa[pr] : P.qb[pr];
+          const int row0 = side == 0 ? i0 : j0;
+          const int* ex = (side == 0 ? sExpA : sExpB) + pr * kTile;
+          unsigned char* dst = side == 0 ? sA + pr * kAStride + kTileBytes : sB + pr * kBStride;
+          for (int u = warp; u < 32; u += kThreads / 32) {
+            const int rg = u >> 2, kq = u & 3;
+            const int r = rg * 8 + (lane >> 2), kp = kq * 4 + (lane & 3);
+            const int f = row0 + r, k = 2 * kp, p = kc0 + k;
+            double x0 = 0.0, x1 = 0.0;
+            if (f < nb) {
+              const double* src = base + q * plane + static_cast<int64_t>(f) * ldp + p;
+              if (p < np) x0 = src[0];
+              if (p + 1 < np) x1 = src[1];
+            }
+            if (side == 0) {
+              x0 *= sD[k];
+              x1 *= sD[k + 1];
+            }
+            const int e = ex[r];
+            int d0[4], d1[4];
+            digits4(x0, e, d0);
+            digits4(x1, e, d1);
+            const int off = rg * kSBO + kq * kLBO + (lane >> 2) * 16 + (lane & 3) * 4;
+#pragma unroll
+            for (int s = 0; s < 4; ++s) {
+              const float sc = pow2f(e - 6 - 8 * s);
+              __nv_bfloat162 h = __floats2bfloat162_rn(static_cast<float>(d0[s]) * sc,
+                                                       static_cast<float>(d1[s]) * sc);
+              *reinterpret_cast<__nv_bfloat162*>(dst + s * kTileBytes + off) = h;
+            }
+          }
+        }
+      }
+      fence_async_smem();
+      __syncthreads();
+      if (tid == 0) {
+        tc_fence_after();
+        for (int ks = 0; ks < kKc / 16; ++ks) {
+          const uint32_t koff = ks * 2 * kLBO;
+          for (int pr = 0; pr < P.n; ++pr) {
+            const uint32_t a = smem_u32(sA + pr * kAStride) + koff;  // tile Z; +kTileBytes = A0, ...
+            const uint32_t bb = smem_u32(sB + pr * kBStride) + koff;
+            const bool first = (c == 0 && ks == 0 && pr == 0);
+            const uint32_t t0 = tmem, t1 = tmem + kTile;
+            mma_bf16(t0, make_desc(a + 1 * kTileBytes), make_desc(bb + 0 * kTileBytes), idesc, first ? 0u : 1u);
+            mma_bf16(t0, make_desc(a + 0 * kTileBytes), make_desc(bb + 1 * kTileBytes), idesc, 1u);
+            mma_bf16(t1, make_desc(a + 3 * kTileBytes), make_desc(bb + 0 * kTileBytes), idesc, first ? 0u : 1u);
+            mma_bf16(t1, make_desc(a + 2 * kTileBytes), make_desc(bb + 1 * kTileBytes), idesc, 1u);
+            mma_bf16(t1, make_desc(a + 1 * kTileBytes), make_desc(bb + 2 * kTileBytes), idesc, 1u);
+            mma_bf16(t1, make_desc(a + 1 * kTileBytes), make_desc(bb + 3 * kTileBytes), idesc, 1u);
+          }
+        }
+        mma_commit(bar_addr);
+      }
+      __syncthreads();
+    }
+    if (!ok) break;
+    ok = __syncthreads_and(mbar_wait(bar_addr, phase & 1, status));
+    ++phase;
+    tc_fence_after();
+    if (!ok) break;
+
+    // epilogue: combine [L0;L1] and [L2;L2'] per element, scatter into FP64
+    const int64_t f0 = G.bat_fn_ptr[b];
+    const int a0 = G.bat_atom_ptr[b], na = G.bat_atom_ptr[b + 1] - a0;
+    const int64_t pp = G.bat_pair_ptr[b];
+    double* out = o == 0 ? V : o == 1 ? W0 : o == 2 ? SOx : o == 3 ? SOy : SOz;
+    for (int c0 = 0; c0 < N; c0 += 16) {
+      float v0[16], v1[16];
+      const uint32_t lane_base = static_cast<uint32_t>(warp * 32) << 16;
+      tmem_ld16(tmem + lane_base + c0, v0);
+      tmem_ld16(tmem + lane_base + kTile + c0, v1);
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        stage[(tid * 16 + i) * 2 + 0] = v0[i];
+        stage[(tid * 16 + i) * 2 + 1] = v1[i];
+      }
+      __syncthreads();
+      const int r = tid & 63, half = tid >> 6;
+      const int i = i0 + r;
+      for (int cc = 0; cc < 8; ++cc) {
+        const int col = half * 8 + cc;
+        const int j = j0 + c0 + col;
+        if (i >= nb || j >= nb) continue;
+        const float L0 = stage[(r * 16 + col) * 2], L1 = stage[((r + 64) * 16 + col) * 2];
+        const float L2 = stage[(r * 16 + col) * 2 + 1], L2b = stage[((r + 64) * 16 + col) * 2 + 1];
+        // two-sum of the exact levels, rounded tail on top
+        const float s = L0 + L1;
+        const float bp = s - L0;
+        const float err = (L0 - (s - bp)) + (L1 - bp);
+        const float lo = err + (L2 + L2b);
+        const double val = static_cast<double>(s) + static_cast<double>(lo);
+        int ri = i, rj = j;
+        double sgn = 1.0;
+        if (o <= 1) {
+          if (i > j) continue;
+        } else {
+          if (i == j) continue;
+          if (i > j) { ri = j; rj = i; sgn = -1.0; }
+        }
+        const int ii = G.fn_info[f0 + ri], jj = G.fn_info[f0 + rj];
+        const int ai = ii >> 16, ki = ii & 0xffff, aj = jj >> 16, kj = jj & 0xffff;
+        const int64_t off = G.pair_off[pp + static_cast<int64_t>(ai) * na + aj];
+        if (off < 0) continue;
+        atomicAdd(out + off + static_cast<int64_t>(ki) * local_nf(B, G, a0, aj) + kj, sgn * val);
+      }
+      __syncthreads();
+    }
+    tc_fence_before();
+    __syncthreads();
+  }
+  // on an expired wait give in-flight MMAs one more bounded chance before freeing TMEM
+  if (!ok) (void)__syncthreads_and(mbar_wait(bar_addr, phase & 1, status));
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
+}
+
+}  // namespace split
+
+q4c_status integrate_split(const q4c_tables* t, const q4c_grid* g, const double* v, const q4c_matrices* out,
+                           cudaStream_t s) {
+  if (g->max_np > 341) {
+    set_error("q4c_integrate: the split path needs batches of at most 341 points");
+    return Q4C_EUNSUPPORTED;
+  }
+  double* outs[5] = {out->V, out->W0, out->SOx, out->SOy, out->SOz};
+  for (double* o : outs) Q4C_CUDA(cudaMemsetAsync(o, 0, sizeof(double) * g->nnz, s));
+  const int n_waves = static_cast<int>(g->wave_b0.size()) - 1;
+  Q4C_CUDA(cudaMemsetAsync(g->d_counter, 0, sizeof(int) * std::max(n_waves, 1), s));
+  Q4C_CUDA(cudaFuncSetAttribute(split::k_split_products, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                split::kSmemTotal));
+  int dev = 0, n_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+  for (int wv = 0; wv < n_waves; ++wv) {
+    const int64_t b0 = g->wave_b0[wv], b1 = g->wave_b0[wv + 1];
+    if (b1 <= b0) continue;
+    if (q4c_status st = launch_basis_tiles(t, g, b0, b1, v, g->d_colexp, s)) return st;
+    const int64_t i0 = g->split_w0[wv], i1 = g->split_w0[wv + 1];
+    const int n_items = static_cast<int>(i1 - i0);
+    if (n_items == 0) continue;
+    const int grid = std::min(n_items, 2 * n_sm);
+    {
+      KernelScope ks("split_products", s);
+      split::k_split_products<<<grid, split::kThreads, split::kSmemTotal, s>>>(
+          t->view(), g->view(), g->d_split_items + i0, n_items, g->d_counter + wv, g->d_scr_off, g->d_scratch,
+          g->d_colexp, v, out->V, out->W0, out->SOx, out->SOy, out->SOz, g->d_status);
+    }
+    Q4C_CUDA(cudaGetLastError());
+  }
+  return mirror_and_spinor(g, out, s);
 }
 
 }  // namespace q4c
