@@ -4,23 +4,25 @@
 // Q in {Phi, X, Y, Z}) is computed exactly enough for ~1e-9 relative error
 // from BF16 slices (an Ozaki-type error-free splitting; Ozaki, Ogita, Oishi
 // and Rump 2012):
-//   x = sum_s d_s 2^(e - 6 - 8s),  s = 0..3,  |d_0| <= 64, |d_s| <= 128,
+//   x = sum_s d_s 2^(e - 6 - 8s),  s = 0..4,  |d_0| <= 64, |d_s| <= 128,
 // with e a per-column binary exponent (|x| < 2^e over the batch).  Each digit
 // has <= 8 significant bits, so it is exact in BF16 and every slice product
 // is exact in FP32.  Per output element three FP32 accumulators are kept in
 // tensor memory:
 //   L0 = sum d0 e0          (exact: < 2^24 units for n_p <= 341)
 //   L1 = sum d0 e1 + d1 e0  (exact)
-//   L2 = the s + t in {2, 3} terms (rounded, 2^-16 below L0)
+//   L2 = the 2 <= s + t <= 4 terms (rounded, 2^-16 below L0)
 // and combined as a double-float, then added into the FP64 block pattern.
 //
-// Layout trick: the four slices of one operand set live in shared memory as
-// five consecutive 64-row tiles [Z, A0, A1, A2, A3] (Z = zeros).  An M = 128
-// MMA starting at tile k reads rows [tile_k; tile_k+1], so six MMAs per
-// K-step cover the ten slice pairs with s + t <= 3:
+// Layout trick: the five slices of one operand set live in shared memory as
+// seven consecutive 64-row tiles [Z, A0, A1, A2, A3, A4, Z] (Z = zeros).  An
+// M = 128 MMA starting at tile k reads rows [tile_k; tile_k+1], so ten MMAs
+// per K-step cover the fifteen slice pairs with s + t <= 4:
 //   TMEM block 0 = [L0; L1]:  [A0;A1] x B0,  [Z;A0] x B1
-//   TMEM block 1 = [L2; L2']: [A2;A3] x B0,  [A1;A2] x B1,  [A0;A1] x B2,  [A0;A1] x B3
-// (the bottom halves of block 1 collect level-3 terms and one level-4 term).
+//   TMEM block 1 = [L2; L2']: [A2;A3] x B0, [A4;Z] x B0, [A1;A2] x B1,
+//                             [A3;A4] x B1, [A0;A1] x B2, [A2;A3] x B2,
+//                             [A0;A1] x B3, [A0;A1] x B4
+// (block 1 also collects three level-5 products, which only add accuracy).
 //
 // Outputs per (batch, 64x64 tile): V = (D Phi)^T Phi, W0 = sum_q (D Q)^T Q
 // (three products into one accumulator), and A_yz = (D Y)^T Z,
@@ -36,17 +38,18 @@ namespace q4c {
 namespace split {
 
 constexpr int kTile = 64;          // functions per tile (rows of one half of M)
-constexpr int kKc = 32;            // points per chunk (two K = 16 MMA steps)
-constexpr int kTileBytes = kTile * kKc * 2;  // 4 KB
-constexpr int kSBO = (kKc / 8) * 128;        // 512 B between 8-row groups
+constexpr int kKc = 16;            // points per chunk (one K = 16 MMA step)
+constexpr int kSlices = 5;
+constexpr int kTileBytes = kTile * kKc * 2;  // 2 KB
+constexpr int kSBO = (kKc / 8) * 128;        // 256 B between 8-row groups
 constexpr int kLBO = 128;                    // core matrices adjacent in K
 constexpr int kThreads = 128;
 constexpr int kMaxProducts = 3;
-constexpr int kAStride = 5 * kTileBytes;     // [Z, A0, A1, A2, A3]
-constexpr int kBStride = 4 * kTileBytes;     // [B0, B1, B2, B3]
+constexpr int kAStride = (kSlices + 2) * kTileBytes;  // [Z, A0..A4, Z]
+constexpr int kBStride = kSlices * kTileBytes;        // [B0..B4]
 constexpr int kSmemA = 0;
-constexpr int kSmemB = kSmemA + kMaxProducts * kAStride;        // 60 KB
-constexpr int kSmemD = kSmemB + kMaxProducts * kBStride;        // +48 KB
+constexpr int kSmemB = kSmemA + kMaxProducts * kAStride;        // 42 KB
+constexpr int kSmemD = kSmemB + kMaxProducts * kBStride;        // +30 KB
 constexpr int kSmemExp = kSmemD + kKc * 8;
 constexpr int kSmemBar = kSmemExp + 2 * kMaxProducts * kTile * 4;
 constexpr int kSmemTotal = kSmemBar + 64;
@@ -139,28 +142,28 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
 }
 
 // ------------------------------------------------------------ slicing
-// x = sum_s d_s 2^(e - 6 - 8 s) + O(2^(e-31)), digits from the integer
-// N = round(x 2^(30 - e)) by balanced base-256 extraction (|d_0| <= 64).
-__device__ __forceinline__ void digits4(double x, int e, int d[4]) {
-  d[0] = d[1] = d[2] = d[3] = 0;
+// x = sum_s d_s 2^(e - 6 - 8 s) + O(2^(e-39)), digits from the integer
+// N = round(x 2^(38 - e)) by balanced base-256 extraction (|d_0| <= 64).
+__device__ __forceinline__ void digits5(double x, int e, int d[kSlices]) {
+#pragma unroll
+  for (int s = 0; s < kSlices; ++s) d[s] = 0;
   const long long bits = __double_as_longlong(x);
   const int E = static_cast<int>((bits >> 52) & 0x7FF);
   if (E == 0 || e < -1000) return;  // zero (or below the FP64 normal range)
   const long long M = (bits & 0xFFFFFFFFFFFFFLL) | (1LL << 52);
-  const int sh = 1075 + e - 30 - E;  // >= 23 because |x| < 2^e
+  const int sh = 1075 + e - 38 - E;  // >= 14 because |x| <= 2^e
   if (sh >= 62) return;
   long long N = (M + (1LL << (sh - 1))) >> sh;
   if (bits < 0) N = -N;
-  const long long q0 = (N + (1LL << 23)) >> 24;
-  long long r = N - (q0 << 24);
-  const long long q1 = (r + (1LL << 15)) >> 16;
-  r -= q1 << 16;
-  const long long q2 = (r + (1LL << 7)) >> 8;
-  r -= q2 << 8;
-  d[0] = static_cast<int>(q0);
-  d[1] = static_cast<int>(q1);
-  d[2] = static_cast<int>(q2);
-  d[3] = static_cast<int>(r);
+  long long r = N;
+#pragma unroll
+  for (int s = 0; s < kSlices - 1; ++s) {
+    const int w = 8 * (kSlices - 1 - s);  // 32, 24, 16, 8
+    const long long q = (r + (1LL << (w - 1))) >> w;
+    r -= q << w;
+    d[s] = static_cast<int>(q);
+  }
+  d[kSlices - 1] = static_cast<int>(r);
 }
 
 __device__ __forceinline__ float pow2f(int k) {  // 2^k as float, 0 below the normal range
@@ -190,7 +193,7 @@ __device__ __forceinline__ int local_nf(const DevBasis& B, const DevGrid& G, int
   return __ldg(B.sp_nfn + G.atom_sp[G.bat_atoms[a0 + a]]);
 }
 
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kThreads, 3)
     k_split_products(DevBasis B, DevGrid G, const int4* __restrict__ items, int n_items, int* counter,
                      const int64_t* __restrict__ scr_off, const double* __restrict__ scratch,
                      const int* __restrict__ colexp, const double* __restrict__ v, double* V, double* W0,
@@ -209,10 +212,11 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const uint32_t bar_addr = smem_u32(bar);
 
-  // zero tiles Z of every product slot (never overwritten)
-  for (int i = tid; i < kMaxProducts * kTileBytes / 16; i += kThreads) {
-    const int slot = i / (kTileBytes / 16), off = i - slot * (kTileBytes / 16);
-    reinterpret_cast<uint4*>(sA + slot * kAStride)[off] = make_uint4(0, 0, 0, 0);
+  // zero tiles (first and last of every product slot; never overwritten)
+  for (int i = tid; i < 2 * kMaxProducts * kTileBytes / 16; i += kThreads) {
+    const int z = i / (kTileBytes / 16), off = i - z * (kTileBytes / 16);
+    unsigned char* tile = sA + (z >> 1) * kAStride + ((z & 1) ? (kSlices + 1) * kTileBytes : 0);
+    reinterpret_cast<uint4*>(tile)[off] = make_uint4(0, 0, 0, 0);
   }
   if (tid == 0) mbar_init(bar_addr, 1);
   if (warp == 0) {
@@ -277,8 +281,8 @@ __global__ void __launch_bounds__(kThreads, 1)
           const int row0 = side == 0 ? i0 : j0;
           const int* ex = (side == 0 ? sExpA : sExpB) + pr * kTile;
           unsigned char* dst = side == 0 ? sA + pr * kAStride + kTileBytes : sB + pr * kBStride;
-          for (int u = warp; u < 32; u += kThreads / 32) {
-            const int rg = u >> 2, kq = u & 3;
+          for (int u = warp; u < 16; u += kThreads / 32) {
+            const int rg = u >> 1, kq = u & 1;
             const int r = rg * 8 + (lane >> 2), kp = kq * 4 + (lane & 3);
             const int f = row0 + r, k = 2 * kp, p = kc0 + k;
             double x0 = 0.0, x1 = 0.0;
@@ -292,12 +296,12 @@ __global__ void __launch_bounds__(kThreads, 1)
               x1 *= sD[k + 1];
             }
             const int e = ex[r];
-            int d0[4], d1[4];
-            digits4(x0, e, d0);
-            digits4(x1, e, d1);
+            int d0[kSlices], d1[kSlices];
+            digits5(x0, e, d0);
+            digits5(x1, e, d1);
             const int off = rg * kSBO + kq * kLBO + (lane >> 2) * 16 + (lane & 3) * 4;
 #pragma unroll
-            for (int s = 0; s < 4; ++s) {
+            for (int s = 0; s < kSlices; ++s) {
               const float sc = pow2f(e - 6 - 8 * s);
               __nv_bfloat162 h = __floats2bfloat162_rn(static_cast<float>(d0[s]) * sc,
                                                        static_cast<float>(d1[s]) * sc);
@@ -310,20 +314,24 @@ __global__ void __launch_bounds__(kThreads, 1)
       __syncthreads();
       if (tid == 0) {
         tc_fence_after();
-        for (int ks = 0; ks < kKc / 16; ++ks) {
-          const uint32_t koff = ks * 2 * kLBO;
-          for (int pr = 0; pr < P.n; ++pr) {
-            const uint32_t a = smem_u32(sA + pr * kAStride) + koff;  // tile Z; +kTileBytes = A0, ...
-            const uint32_t bb = smem_u32(sB + pr * kBStride) + koff;
-            const bool first = (c == 0 && ks == 0 && pr == 0);
-            const uint32_t t0 = tmem, t1 = tmem + kTile;
-            mma_bf16(t0, make_desc(a + 1 * kTileBytes), make_desc(bb + 0 * kTileBytes), idesc, first ? 0u : 1u);
-            mma_bf16(t0, make_desc(a + 0 * kTileBytes), make_desc(bb + 1 * kTileBytes), idesc, 1u);
-            mma_bf16(t1, make_desc(a + 3 * kTileBytes), make_desc(bb + 0 * kTileBytes), idesc, first ? 0u : 1u);
-            mma_bf16(t1, make_desc(a + 2 * kTileBytes), make_desc(bb + 1 * kTileBytes), idesc, 1u);
-            mma_bf16(t1, make_desc(a + 1 * kTileBytes), make_desc(bb + 2 * kTileBytes), idesc, 1u);
-            mma_bf16(t1, make_desc(a + 1 * kTileBytes), make_desc(bb + 3 * kTileBytes), idesc, 1u);
-          }
+        for (int pr = 0; pr < P.n; ++pr) {
+          // tile k of the A sequence [Z, A0, A1, A2, A3, A4, Z] starts at a + k * kTileBytes
+          const uint32_t a = smem_u32(sA + pr * kAStride);
+          const uint32_t bb = smem_u32(sB + pr * kBStride);
+          const bool first = (c == 0 && pr == 0);
+          const uint32_t t0 = tmem, t1 = tmem + kTile;
+          auto A = [&](int k) { return make_desc(a + k * kTileBytes); };
+          auto Bt = [&](int t) { return make_desc(bb + t * kTileBytes); };
+          mma_bf16(t0, A(1), Bt(0), idesc, first ? 0u : 1u);  // [A0;A1] x B0 -> L0, L1
+          mma_bf16(t0, A(0), Bt(1), idesc, 1u);                // [Z;A0]  x B1 -> L1
+          mma_bf16(t1, A(3), Bt(0), idesc, first ? 0u : 1u);  // [A2;A3] x B0
+          mma_bf16(t1, A(5), Bt(0), idesc, 1u);                // [A4;Z]  x B0
+          mma_bf16(t1, A(2), Bt(1), idesc, 1u);                // [A1;A2] x B1
+          mma_bf16(t1, A(4), Bt(1), idesc, 1u);                // [A3;A4] x B1
+          mma_bf16(t1, A(1), Bt(2), idesc, 1u);                // [A0;A1] x B2
+          mma_bf16(t1, A(3), Bt(2), idesc, 1u);                // [A2;A3] x B2
+          mma_bf16(t1, A(1), Bt(3), idesc, 1u);                // [A0;A1] x B3
+          mma_bf16(t1, A(1), Bt(4), idesc, 1u);                // [A0;A1] x B4
         }
         mma_commit(bar_addr);
       }
@@ -416,7 +424,7 @@ q4c_status integrate_split(const q4c_tables* t, const q4c_grid* g, const double*
     const int64_t i0 = g->split_w0[wv], i1 = g->split_w0[wv + 1];
     const int n_items = static_cast<int>(i1 - i0);
     if (n_items == 0) continue;
-    const int grid = std::min(n_items, 2 * n_sm);
+    const int grid = std::min(n_items, 3 * n_sm);
     {
       KernelScope ks("split_products", s);
       split::k_split_products<<<grid, split::kThreads, split::kSmemTotal, s>>>(
