@@ -25,7 +25,8 @@
 // (block 1 also collects three level-5 products, which only add accuracy).
 //
 // Outputs per (batch, 64x64 tile): V = (D Phi)^T Phi, W0 = sum_q (D Q)^T Q
-// (three products into one accumulator), and A_yz = (D Y)^T Z,
+// (three products into one accumulator, sliced against a common exponent per
+// function so that the exact levels keep one unit), and A_yz = (D Y)^T Z,
 // A_zx = (D Z)^T X, A_xy = (D X)^T Y with SO_x = A_yz - A_yz^T etc. applied
 // while scattering.  One persistent CTA per SM (128 threads, 128 TMEM
 // columns) loops over work items; every mbarrier wait is bounded and sets a
@@ -253,10 +254,23 @@ __global__ void __launch_bounds__(kThreads, 3)
     const int N = (ncols + 15) & ~15;
     const uint32_t idesc = make_idesc(128, N);
 
+    // Column exponents.  The three products of W0 share one accumulator, so
+    // they must share units: W0 slices each gradient component against the
+    // largest exponent of the three (per function, per side).
     for (int k = tid; k < P.n * kTile; k += kThreads) {
       const int pr = k / kTile, r = k - pr * kTile;
-      sExpA[pr * kTile + r] = (i0 + r < nb) ? cexp[P.qa[pr] * nb + i0 + r] : -30000;
-      sExpB[pr * kTile + r] = (j0 + r < nb) ? cexp[(4 + P.qb[pr]) * nb + j0 + r] : -30000;
+      int ea = -30000, eb = -30000;
+      if (o == 1) {
+        if (i0 + r < nb)
+          ea = max(cexp[1 * nb + i0 + r], max(cexp[2 * nb + i0 + r], cexp[3 * nb + i0 + r]));
+        if (j0 + r < nb)
+          eb = max(cexp[5 * nb + j0 + r], max(cexp[6 * nb + j0 + r], cexp[7 * nb + j0 + r]));
+      } else {
+        if (i0 + r < nb) ea = cexp[P.qa[pr] * nb + i0 + r];
+        if (j0 + r < nb) eb = cexp[(4 + P.qb[pr]) * nb + j0 + r];
+      }
+      sExpA[pr * kTile + r] = ea;
+      sExpB[pr * kTile + r] = eb;
     }
 
     const int n_chunks = (np + kKc - 1) / kKc;

@@ -51,19 +51,31 @@ def test_split_repeatable(pairs):
         assert rel_fro(x, y) <= 1e-14
 
 
-def test_integrate_split_edge_cases():
-    wl1 = single_atom([0, 1, 2, 3], [0.8, 1.1, 1.6, 2.2], Z=6.0, n_rad=20, n_theta=6, n_phi=12)
-    sp = [Species("A", 3.0, [0, 1], [0.9, 1.4]), Species("B", 1.0, [0, 2], [1.2, 0.7])]
-    wl2 = Workload("far-pair", np.array([[0.0, 0, 0], [13.0, 0.5, -0.2]]), np.array([0, 1], np.int32), sp,
-                   n_rad=16, n_theta=6, n_phi=12)
-    wl3 = water(n_rad=8, n_theta=4, n_phi=8, batch_max=1)
-    wl4 = water(n_rad=40, n_theta=10, n_phi=20, batch_max=341)
-    for wl in (wl1, wl2, wl3, wl4):
-        lib, orc = LibCase(wl), OracleCase(wl)
-        got = lib.integrate("split")
-        lib.grid.status()
-        for n, g, r in zip(NAMES, got[:5], orc.mats):
-            assert rel_fro(g, r) <= TOL_SPLIT, (wl.name, n, rel_fro(g, r))
+EDGE = {
+    "single-atom-l0123": lambda: single_atom([0, 1, 2, 3], [0.8, 1.1, 1.6, 2.2], Z=6.0, n_rad=20, n_theta=6,
+                                             n_phi=12),
+    "far-pair": lambda: Workload("far-pair", np.array([[0.0, 0, 0], [13.0, 0.5, -0.2]]), np.array([0, 1], np.int32),
+                                 [Species("A", 3.0, [0, 1], [0.9, 1.4]), Species("B", 1.0, [0, 2], [1.2, 0.7])],
+                                 n_rad=16, n_theta=6, n_phi=12),
+    "one-point-batches": lambda: water(n_rad=8, n_theta=4, n_phi=8, batch_max=1),
+    "341-point-batches": lambda: water(n_rad=40, n_theta=10, n_phi=20, batch_max=341),
+}
+
+
+@pytest.mark.parametrize("case", list(EDGE))
+def test_integrate_split_edge_cases(case):
+    wl = EDGE[case]()
+    lib, orc = LibCase(wl), OracleCase(wl)
+    got = lib.integrate("split")
+    f64 = lib.integrate("fp64")
+    lib.grid.status()
+    errs = {n: rel_fro(g, r) for n, g, r in zip(NAMES, got[:5], orc.mats)}
+    diag = {}
+    for n, g, h, r in zip(NAMES, got[:5], f64[:5], orc.mats):
+        k = int(np.argmax(np.abs(g - r)))
+        diag[n] = dict(split_vs_fp64=rel_fro(g, h), fp64_vs_oracle=rel_fro(h, r), worst_index=k,
+                       worst_abs=float(abs(g[k] - r[k])), ref_there=float(r[k]), max_ref=float(np.abs(r).max()))
+    assert max(errs.values()) <= TOL_SPLIT, (case, errs, diag, int(lib.grid.info.max_np), int(lib.grid.info.max_nb))
 
 
 def test_split_rejects_batches_beyond_exactness_bound():
