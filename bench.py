@@ -311,12 +311,12 @@ def main():
     peaks, peak_src = load_peaks()
     clk = clocks.summary()
     dom_name, (dom_ms, dom_n) = max(kern.items(), key=lambda kv: kv[1][0])
-    S_PAIRS = 15  # slice-pair products (s + t <= 4 of 5 BF16 slices per operand)
+    S_PAIRS = 21  # slice-pair products (s + t <= 5 of 6 BF16 slices per operand)
     if dom_name == "split_products":
         achieved = fl["integrate"] * S_PAIRS * args.steps / (dom_ms * 1e-3) / 1e12
         roof = {"bound": "tensor", "achieved": achieved, "peak": peaks["bf16_tflops_sustained"],
                 "unit": "TFLOP/s", "peak_source": f"{peak_src} bf16 sustained (of measured)",
-                "work": "14 n_p n_b^2 per batch x 15 slice pairs"}
+                "work": "14 n_p n_b^2 per batch x 21 slice pairs"}
     elif dom_name in ("products_fp64", "density_fp64", "backward_fp64"):
         work = {"products_fp64": "integrate", "density_fp64": "density", "backward_fp64": "backward"}[dom_name]
         calls = sum(1 for ph, pr in phase_prec.items() if ph == work and pr == "fp64") or 1

@@ -4,25 +4,29 @@
 // Q in {Phi, X, Y, Z}) is computed exactly enough for ~1e-9 relative error
 // from BF16 slices (an Ozaki-type error-free splitting; Ozaki, Ogita, Oishi
 // and Rump 2012):
-//   x = sum_s d_s 2^(e - 6 - 8s),  s = 0..4,  |d_0| <= 64, |d_s| <= 128,
+//   x = sum_s d_s 2^(e - 6 - 8s),  s = 0..5,  |d_0| <= 64, |d_s| <= 128,
 // with e a per-column binary exponent (|x| < 2^e over the batch).  Each digit
 // has <= 8 significant bits, so it is exact in BF16 and every slice product
 // is exact in FP32.  Per output element three FP32 accumulators are kept in
 // tensor memory:
 //   L0 = sum d0 e0          (exact: < 2^24 units for n_p <= 341)
 //   L1 = sum d0 e1 + d1 e0  (exact)
-//   L2 = the 2 <= s + t <= 4 terms (rounded, 2^-16 below L0)
+//   L2 = the 2 <= s + t <= 5 terms (rounded, 2^-16 below L0)
 // and combined as a double-float, then added into the FP64 block pattern.
 //
-// Layout trick: the five slices of one operand set live in shared memory as
-// seven consecutive 64-row tiles [Z, A0, A1, A2, A3, A4, Z] (Z = zeros).  An
-// M = 128 MMA starting at tile k reads rows [tile_k; tile_k+1], so ten MMAs
-// per K-step cover the fifteen slice pairs with s + t <= 4:
+// The precision is relative to the column maxima of each batch, which near
+// heavy nuclei sit far above the typical values, hence six slices (47 bits).
+//
+// Layout trick: the six slices of one operand set live in shared memory as
+// seven consecutive 64-row tiles [Z, A0, A1, A2, A3, A4, A5] (Z = zeros).  An
+// M = 128 MMA starting at tile k reads rows [tile_k; tile_k+1], so twelve
+// MMAs per K-step cover the twenty-one slice pairs with s + t <= 5:
 //   TMEM block 0 = [L0; L1]:  [A0;A1] x B0,  [Z;A0] x B1
-//   TMEM block 1 = [L2; L2']: [A2;A3] x B0, [A4;Z] x B0, [A1;A2] x B1,
+//   TMEM block 1 = [L2; L2']: [A2;A3] x B0, [A4;A5] x B0, [A1;A2] x B1,
 //                             [A3;A4] x B1, [A0;A1] x B2, [A2;A3] x B2,
-//                             [A0;A1] x B3, [A0;A1] x B4
-// (block 1 also collects three level-5 products, which only add accuracy).
+//                             [A0;A1] x B3, [A2;A3] x B3, [A0;A1] x B4,
+//                             [A0;A1] x B5
+// (block 1 also collects two level-6 products, which only add accuracy).
 //
 // Outputs per (batch, 64x64 tile): V = (D Phi)^T Phi, W0 = sum_q (D Q)^T Q
 // (three products into one accumulator, sliced against a common exponent per
@@ -40,17 +44,17 @@ namespace split {
 
 constexpr int kTile = 64;          // functions per tile (rows of one half of M)
 constexpr int kKc = 16;            // points per chunk (one K = 16 MMA step)
-constexpr int kSlices = 5;
+constexpr int kSlices = 6;
 constexpr int kTileBytes = kTile * kKc * 2;  // 2 KB
 constexpr int kSBO = (kKc / 8) * 128;        // 256 B between 8-row groups
 constexpr int kLBO = 128;                    // core matrices adjacent in K
 constexpr int kThreads = 128;
 constexpr int kMaxProducts = 3;
-constexpr int kAStride = (kSlices + 2) * kTileBytes;  // [Z, A0..A4, Z]
-constexpr int kBStride = kSlices * kTileBytes;        // [B0..B4]
+constexpr int kAStride = (kSlices + 1) * kTileBytes;  // [Z, A0..A5]
+constexpr int kBStride = kSlices * kTileBytes;        // [B0..B5]
 constexpr int kSmemA = 0;
 constexpr int kSmemB = kSmemA + kMaxProducts * kAStride;        // 42 KB
-constexpr int kSmemD = kSmemB + kMaxProducts * kBStride;        // +30 KB
+constexpr int kSmemD = kSmemB + kMaxProducts * kBStride;        // +36 KB
 constexpr int kSmemExp = kSmemD + kKc * 8;
 constexpr int kSmemBar = kSmemExp + 2 * kMaxProducts * kTile * 4;
 constexpr int kSmemTotal = kSmemBar + 64;
@@ -143,23 +147,23 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
 }
 
 // ------------------------------------------------------------ slicing
-// x = sum_s d_s 2^(e - 6 - 8 s) + O(2^(e-39)), digits from the integer
-// N = round(x 2^(38 - e)) by balanced base-256 extraction (|d_0| <= 64).
-__device__ __forceinline__ void digits5(double x, int e, int d[kSlices]) {
+// x = sum_s d_s 2^(e - 6 - 8 s) + O(2^(e-47)), digits from the integer
+// N = round(x 2^(46 - e)) by balanced base-256 extraction (|d_0| <= 64).
+__device__ __forceinline__ void digits6(double x, int e, int d[kSlices]) {
 #pragma unroll
   for (int s = 0; s < kSlices; ++s) d[s] = 0;
   const long long bits = __double_as_longlong(x);
   const int E = static_cast<int>((bits >> 52) & 0x7FF);
   if (E == 0 || e < -1000) return;  // zero (or below the FP64 normal range)
   const long long M = (bits & 0xFFFFFFFFFFFFFLL) | (1LL << 52);
-  const int sh = 1075 + e - 38 - E;  // >= 14 because |x| <= 2^e
+  const int sh = 1075 + e - 46 - E;  // >= 6 because |x| <= 2^e
   if (sh >= 62) return;
   long long N = (M + (1LL << (sh - 1))) >> sh;
   if (bits < 0) N = -N;
   long long r = N;
 #pragma unroll
   for (int s = 0; s < kSlices - 1; ++s) {
-    const int w = 8 * (kSlices - 1 - s);  // 32, 24, 16, 8
+    const int w = 8 * (kSlices - 1 - s);  // 40, 32, 24, 16, 8
     const long long q = (r + (1LL << (w - 1))) >> w;
     r -= q << w;
     d[s] = static_cast<int>(q);
@@ -194,7 +198,7 @@ __device__ __forceinline__ int local_nf(const DevBasis& B, const DevGrid& G, int
   return __ldg(B.sp_nfn + G.atom_sp[G.bat_atoms[a0 + a]]);
 }
 
-__global__ void __launch_bounds__(kThreads, 3)
+__global__ void __launch_bounds__(kThreads, 2)
     k_split_products(DevBasis B, DevGrid G, const int4* __restrict__ items, int n_items, int* counter,
                      const int64_t* __restrict__ scr_off, const double* __restrict__ scratch,
                      const int* __restrict__ colexp, const double* __restrict__ v, double* V, double* W0,
@@ -213,11 +217,10 @@ __global__ void __launch_bounds__(kThreads, 3)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const uint32_t bar_addr = smem_u32(bar);
 
-  // zero tiles (first and last of every product slot; never overwritten)
-  for (int i = tid; i < 2 * kMaxProducts * kTileBytes / 16; i += kThreads) {
+  // zero tile Z at the head of every product slot (never overwritten)
+  for (int i = tid; i < kMaxProducts * kTileBytes / 16; i += kThreads) {
     const int z = i / (kTileBytes / 16), off = i - z * (kTileBytes / 16);
-    unsigned char* tile = sA + (z >> 1) * kAStride + ((z & 1) ? (kSlices + 1) * kTileBytes : 0);
-    reinterpret_cast<uint4*>(tile)[off] = make_uint4(0, 0, 0, 0);
+    reinterpret_cast<uint4*>(sA + z * kAStride)[off] = make_uint4(0, 0, 0, 0);
   }
   if (tid == 0) mbar_init(bar_addr, 1);
   if (warp == 0) {
@@ -311,8 +314,8 @@ __global__ void __launch_bounds__(kThreads, 3)
             }
             const int e = ex[r];
             int d0[kSlices], d1[kSlices];
-            digits5(x0, e, d0);
-            digits5(x1, e, d1);
+            digits6(x0, e, d0);
+            digits6(x1, e, d1);
             const int off = rg * kSBO + kq * kLBO + (lane >> 2) * 16 + (lane & 3) * 4;
 #pragma unroll
             for (int s = 0; s < kSlices; ++s) {
@@ -329,7 +332,7 @@ __global__ void __launch_bounds__(kThreads, 3)
       if (tid == 0) {
         tc_fence_after();
         for (int pr = 0; pr < P.n; ++pr) {
-          // tile k of the A sequence [Z, A0, A1, A2, A3, A4, Z] starts at a + k * kTileBytes
+          // tile k of the A sequence [Z, A0, A1, A2, A3, A4, A5] starts at a + k * kTileBytes
           const uint32_t a = smem_u32(sA + pr * kAStride);
           const uint32_t bb = smem_u32(sB + pr * kBStride);
           const bool first = (c == 0 && pr == 0);
@@ -339,13 +342,15 @@ __global__ void __launch_bounds__(kThreads, 3)
           mma_bf16(t0, A(1), Bt(0), idesc, first ? 0u : 1u);  // [A0;A1] x B0 -> L0, L1
           mma_bf16(t0, A(0), Bt(1), idesc, 1u);                // [Z;A0]  x B1 -> L1
           mma_bf16(t1, A(3), Bt(0), idesc, first ? 0u : 1u);  // [A2;A3] x B0
-          mma_bf16(t1, A(5), Bt(0), idesc, 1u);                // [A4;Z]  x B0
+          mma_bf16(t1, A(5), Bt(0), idesc, 1u);                // [A4;A5] x B0
           mma_bf16(t1, A(2), Bt(1), idesc, 1u);                // [A1;A2] x B1
           mma_bf16(t1, A(4), Bt(1), idesc, 1u);                // [A3;A4] x B1
           mma_bf16(t1, A(1), Bt(2), idesc, 1u);                // [A0;A1] x B2
           mma_bf16(t1, A(3), Bt(2), idesc, 1u);                // [A2;A3] x B2
           mma_bf16(t1, A(1), Bt(3), idesc, 1u);                // [A0;A1] x B3
+          mma_bf16(t1, A(3), Bt(3), idesc, 1u);                // [A2;A3] x B3
           mma_bf16(t1, A(1), Bt(4), idesc, 1u);                // [A0;A1] x B4
+          mma_bf16(t1, A(1), Bt(5), idesc, 1u);                // [A0;A1] x B5
         }
         mma_commit(bar_addr);
       }
@@ -438,7 +443,7 @@ q4c_status integrate_split(const q4c_tables* t, const q4c_grid* g, const double*
     const int64_t i0 = g->split_w0[wv], i1 = g->split_w0[wv + 1];
     const int n_items = static_cast<int>(i1 - i0);
     if (n_items == 0) continue;
-    const int grid = std::min(n_items, 3 * n_sm);
+    const int grid = std::min(n_items, 2 * n_sm);
     {
       KernelScope ks("split_products", s);
       split::k_split_products<<<grid, split::kThreads, split::kSmemTotal, s>>>(
