@@ -7,11 +7,12 @@
 //   x = sum_s d_s 2^(e - 6 - 8s),  s = 0..5,  |d_0| <= 64, |d_s| <= 128,
 // with e a per-column binary exponent (|x| < 2^e over the batch).  Each digit
 // has <= 8 significant bits, so it is exact in BF16 and every slice product
-// is exact in FP32.  Per output element three FP32 accumulators are kept in
-// tensor memory:
-//   L0 = sum d0 e0          (exact: < 2^24 units for n_p <= 341)
-//   L1 = sum d0 e1 + d1 e0  (exact)
-//   L2 = the 2 <= s + t <= 5 terms (rounded, 2^-16 below L0)
+// is exact in FP32.  Per output element six FP32 accumulators (one per level
+// s + t) are kept in tensor memory:
+//   L0 = sum d0 e0, L1 = sum d0 e1 + d1 e0, L2 = sum_{s+t=2} d_s e_t
+//       (exact: integer sums below 2^24 units for n_p <= 341)
+//   L3, L4, L5 (rounded; 2^-24 and further below L0, so the truncating FP32
+//       accumulation of the tensor cores cannot reach the result's bits)
 // and combined as a double-float, then added into the FP64 block pattern.
 //
 // The precision is relative to the column maxima of each batch, which near
@@ -19,21 +20,21 @@
 //
 // Layout trick: the six slices of one operand set live in shared memory as
 // seven consecutive 64-row tiles [Z, A0, A1, A2, A3, A4, A5] (Z = zeros).  An
-// M = 128 MMA starting at tile k reads rows [tile_k; tile_k+1], so twelve
-// MMAs per K-step cover the twenty-one slice pairs with s + t <= 5:
-//   TMEM block 0 = [L0; L1]:  [A0;A1] x B0,  [Z;A0] x B1
-//   TMEM block 1 = [L2; L2']: [A2;A3] x B0, [A4;A5] x B0, [A1;A2] x B1,
-//                             [A3;A4] x B1, [A0;A1] x B2, [A2;A3] x B2,
-//                             [A0;A1] x B3, [A2;A3] x B3, [A0;A1] x B4,
-//                             [A0;A1] x B5
-// (block 1 also collects two level-6 products, which only add accuracy).
+// M = 128 MMA starting at tile k reads rows [tile_k; tile_k+1] and so adds
+// A_s B_t to the top half (level s + t) and A_(s+1) B_t to the bottom half
+// (level s + t + 1) of a TMEM block: twelve MMAs per K-step cover the
+// twenty-one slice pairs with s + t <= 5,
+//   block 0 = [L0; L1]: [A0;A1] x B0, [Z;A0] x B1
+//   block 1 = [L2; L3]: [A2;A3] x B0, [A1;A2] x B1, [A0;A1] x B2, [Z;A0] x B3
+//   block 2 = [L4; L5]: [A4;A5] x B0, [A3;A4] x B1, [A2;A3] x B2,
+//                       [A1;A2] x B3, [A0;A1] x B4, [Z;A0] x B5.
 //
 // Outputs per (batch, 64x64 tile): V = (D Phi)^T Phi, W0 = sum_q (D Q)^T Q
 // (three products into one accumulator, sliced against a common exponent per
 // function so that the exact levels keep one unit), and A_yz = (D Y)^T Z,
 // A_zx = (D Z)^T X, A_xy = (D X)^T Y with SO_x = A_yz - A_yz^T etc. applied
-// while scattering.  One persistent CTA per SM (128 threads, 128 TMEM
-// columns) loops over work items; every mbarrier wait is bounded and sets a
+// while scattering.  Persistent CTAs (128 threads, 256 TMEM columns, two
+// per SM) loop over work items; every mbarrier wait is bounded and sets a
 // status bit instead of hanging.
 #include <cuda_bf16.h>
 
@@ -58,7 +59,7 @@ constexpr int kSmemD = kSmemB + kMaxProducts * kBStride;        // +36 KB
 constexpr int kSmemExp = kSmemD + kKc * 8;
 constexpr int kSmemBar = kSmemExp + 2 * kMaxProducts * kTile * 4;
 constexpr int kSmemTotal = kSmemBar + 64;
-constexpr uint32_t kTmemCols = 128;
+constexpr uint32_t kTmemCols = 256;  // three 64-column blocks
 constexpr uint64_t kWaitLimitNs = 1000000000ull;  // 1 s of wall clock per wait
 
 // ------------------------------------------------------------ PTX helpers
@@ -212,7 +213,7 @@ __global__ void __launch_bounds__(kThreads, 2)
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + kSmemBar);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + kSmemBar + 16);
   int* s_item = reinterpret_cast<int*>(smem + kSmemBar + 32);
-  float* stage = reinterpret_cast<float*>(sB);  // epilogue staging reuses the B tiles (16 KB)
+  float* stage = reinterpret_cast<float*>(sB);  // epilogue staging reuses the B tiles (24 KB)
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const uint32_t bar_addr = smem_u32(bar);
@@ -336,21 +337,22 @@ __global__ void __launch_bounds__(kThreads, 2)
           const uint32_t a = smem_u32(sA + pr * kAStride);
           const uint32_t bb = smem_u32(sB + pr * kBStride);
           const bool first = (c == 0 && pr == 0);
-          const uint32_t t0 = tmem, t1 = tmem + kTile;
+          const uint32_t t0 = tmem, t1 = tmem + kTile, t2 = tmem + 2 * kTile;
+          const uint32_t acc = first ? 0u : 1u;
           auto A = [&](int k) { return make_desc(a + k * kTileBytes); };
           auto Bt = [&](int t) { return make_desc(bb + t * kTileBytes); };
-          mma_bf16(t0, A(1), Bt(0), idesc, first ? 0u : 1u);  // [A0;A1] x B0 -> L0, L1
-          mma_bf16(t0, A(0), Bt(1), idesc, 1u);                // [Z;A0]  x B1 -> L1
-          mma_bf16(t1, A(3), Bt(0), idesc, first ? 0u : 1u);  // [A2;A3] x B0
-          mma_bf16(t1, A(5), Bt(0), idesc, 1u);                // [A4;A5] x B0
-          mma_bf16(t1, A(2), Bt(1), idesc, 1u);                // [A1;A2] x B1
-          mma_bf16(t1, A(4), Bt(1), idesc, 1u);                // [A3;A4] x B1
-          mma_bf16(t1, A(1), Bt(2), idesc, 1u);                // [A0;A1] x B2
-          mma_bf16(t1, A(3), Bt(2), idesc, 1u);                // [A2;A3] x B2
-          mma_bf16(t1, A(1), Bt(3), idesc, 1u);                // [A0;A1] x B3
-          mma_bf16(t1, A(3), Bt(3), idesc, 1u);                // [A2;A3] x B3
-          mma_bf16(t1, A(1), Bt(4), idesc, 1u);                // [A0;A1] x B4
-          mma_bf16(t1, A(1), Bt(5), idesc, 1u);                // [A0;A1] x B5
+          mma_bf16(t0, A(1), Bt(0), idesc, acc);  // [A0;A1] x B0 -> L0, L1
+          mma_bf16(t0, A(0), Bt(1), idesc, 1u);   // [Z;A0]  x B1 -> L1
+          mma_bf16(t1, A(3), Bt(0), idesc, acc);  // [A2;A3] x B0 -> L2, L3
+          mma_bf16(t1, A(2), Bt(1), idesc, 1u);   // [A1;A2] x B1
+          mma_bf16(t1, A(1), Bt(2), idesc, 1u);   // [A0;A1] x B2
+          mma_bf16(t1, A(0), Bt(3), idesc, 1u);   // [Z;A0]  x B3 -> L3
+          mma_bf16(t2, A(5), Bt(0), idesc, acc);  // [A4;A5] x B0 -> L4, L5
+          mma_bf16(t2, A(4), Bt(1), idesc, 1u);   // [A3;A4] x B1
+          mma_bf16(t2, A(3), Bt(2), idesc, 1u);   // [A2;A3] x B2
+          mma_bf16(t2, A(2), Bt(3), idesc, 1u);   // [A1;A2] x B3
+          mma_bf16(t2, A(1), Bt(4), idesc, 1u);   // [A0;A1] x B4
+          mma_bf16(t2, A(0), Bt(5), idesc, 1u);   // [Z;A0]  x B5 -> L5
         }
         mma_commit(bar_addr);
       }
@@ -368,14 +370,13 @@ __global__ void __launch_bounds__(kThreads, 2)
     const int64_t pp = G.bat_pair_ptr[b];
     double* out = o == 0 ? V : o == 1 ? W0 : o == 2 ? SOx : o == 3 ? SOy : SOz;
     for (int c0 = 0; c0 < N; c0 += 16) {
-      float v0[16], v1[16];
       const uint32_t lane_base = static_cast<uint32_t>(warp * 32) << 16;
-      tmem_ld16(tmem + lane_base + c0, v0);
-      tmem_ld16(tmem + lane_base + kTile + c0, v1);
 #pragma unroll
-      for (int i = 0; i < 16; ++i) {
-        stage[(tid * 16 + i) * 2 + 0] = v0[i];
-        stage[(tid * 16 + i) * 2 + 1] = v1[i];
+      for (int blk = 0; blk < 3; ++blk) {
+        float vv[16];
+        tmem_ld16(tmem + lane_base + blk * kTile + c0, vv);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) stage[(tid * 16 + i) * 3 + blk] = vv[i];
       }
       __syncthreads();
       const int r = tid & 63, half = tid >> 6;
@@ -384,13 +385,18 @@ __global__ void __launch_bounds__(kThreads, 2)
         const int col = half * 8 + cc;
         const int j = j0 + c0 + col;
         if (i >= nb || j >= nb) continue;
-        const float L0 = stage[(r * 16 + col) * 2], L1 = stage[((r + 64) * 16 + col) * 2];
-        const float L2 = stage[(r * 16 + col) * 2 + 1], L2b = stage[((r + 64) * 16 + col) * 2 + 1];
-        // two-sum of the exact levels, rounded tail on top
-        const float s = L0 + L1;
-        const float bp = s - L0;
-        const float err = (L0 - (s - bp)) + (L1 - bp);
-        const float lo = err + (L2 + L2b);
+        const float* top = stage + (r * 16 + col) * 3;
+        const float* bot = stage + ((r + 64) * 16 + col) * 3;
+        const float L0 = top[0], L1 = bot[0], L2 = top[1], L3 = bot[1], L4 = top[2], L5 = bot[2];
+        // exact levels by two-sums, rounded tail on top
+        float s = L0 + L1;
+        float bp = s - L0;
+        const float e1 = (L0 - (s - bp)) + (L1 - bp);
+        const float s1 = s;
+        s = s1 + L2;
+        bp = s - s1;
+        const float e2 = (s1 - (s - bp)) + (L2 - bp);
+        const float lo = (e1 + e2) + (L3 + (L4 + L5));
         const double val = static_cast<double>(s) + static_cast<double>(lo);
         int ri = i, rj = j;
         double sgn = 1.0;
