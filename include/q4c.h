@@ -197,6 +197,21 @@ Q4C_API q4c_status q4c_integrate_backward(const q4c_tables* tables, const q4c_gr
                                   const q4c_matrices* G, q4c_precision prec, double* dLdv_dev,
                                   q4c_stream stream);
 
+/* q4c_integrate with prec = Q4C_FP64 for callers that cannot allocate device
+ * memory when they integrate (an application whose own pool owns the device
+ * memory, or a loop that must not pay for cudaMalloc/cudaFree, which can
+ * synchronise the device).  The paper has no counterpart; this is a library
+ * convenience.  It allocates nothing: the per-batch basis-tile workspace is a
+ * statically reserved 64 MiB device array that every GPU loading the library
+ * holds until exit, used in waves of batches.  Same arguments, outputs and
+ * results as q4c_integrate(..., Q4C_FP64, ...).  Q4C_EUNSUPPORTED if one
+ * batch's tiles (4 n_b ceil8(n_p) doubles) exceed 64 MiB.  All calls share
+ * the array: calls that overlap on the GPU race and must be serialised by
+ * the caller.  The first call on each device looks up the array's device
+ * address; make that first call before any stream capture. */
+Q4C_API q4c_status q4c_integrate_noalloc(const q4c_tables* tables, const q4c_grid* grid, const double* v_dev,
+                                         const q4c_matrices* out, q4c_stream stream);
+
 /* Basis values at arbitrary points with the kernels' own evaluation (for
  * parity checks): phi_dev[n_basis][n_pts], grad_dev[n_basis][n_pts][3]
  * (device, overwritten); xyz_dev device [n_pts][3]. */

@@ -25,7 +25,7 @@ STATUS = {0: "Q4C_OK", 1: "Q4C_EINVAL", 2: "Q4C_ENOMEM", 3: "Q4C_ECUDA", 4: "Q4C
 # every symbol include/q4c.h declares
 EXPORTS = ["nao_tabulate", "q4c_tables_destroy", "q4c_tables_export", "grid_partition", "q4c_grid_destroy",
            "q4c_grid_get_info", "q4c_grid_export", "q4c_grid_points", "q4c_integrate", "q4c_density",
-           "q4c_integrate_backward", "q4c_basis_eval", "q4c_grid_status", "q4c_profile", "q4c_profile_read",
+           "q4c_integrate_backward", "q4c_integrate_noalloc", "q4c_basis_eval", "q4c_grid_status", "q4c_profile", "q4c_profile_read",
            "q4c_last_error"]
 
 
@@ -83,6 +83,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     L.q4c_integrate.argtypes = [vp, vp, vp, C.c_int, C.POINTER(Matrices), vp]
     L.q4c_density.argtypes = [vp, vp, vp, C.c_int, vp, vp]
     L.q4c_integrate_backward.argtypes = [vp, vp, C.POINTER(Matrices), C.c_int, vp, vp]
+    L.q4c_integrate_noalloc.argtypes = [vp, vp, vp, C.POINTER(Matrices), vp]
     L.q4c_basis_eval.argtypes = [vp, vp, i64, vp, vp, vp, vp]
     L.q4c_grid_status.argtypes = [vp, vp]
     L.q4c_profile.argtypes = [i32]
@@ -225,6 +226,14 @@ def q4c_integrate(tables: Tables, grid: Grid, v, prec="fp64", out=None, spinor: 
         out.append(torch.empty(8 * grid.nnz, dtype=torch.float64, device=v.device) if spinor else None)
     m = Matrices(*[_ptr(t) for t in out[:5]], _ptr(out[5]) if len(out) > 5 else 0)
     _check(load().q4c_integrate(tables.h, grid.h, _ptr(v), _prec(prec), C.byref(m), _stream(stream)))
+    return out
+
+
+def q4c_integrate_noalloc(tables: Tables, grid: Grid, v, out, stream=None):
+    """FP64 integration into caller-provided outputs with the library's static
+    workspace (no device allocation in the call)."""
+    m = Matrices(*[_ptr(t) for t in out[:5]], _ptr(out[5]) if len(out) > 5 else 0)
+    _check(load().q4c_integrate_noalloc(tables.h, grid.h, _ptr(v), C.byref(m), _stream(stream)))
     return out
 
 
