@@ -49,12 +49,11 @@ extern "C" q4c_status q4c_density(const q4c_tables* t, const q4c_grid* g, const 
   Q4C_CHECK_ARG(prec == Q4C_FP64 || prec == Q4C_SPLIT, "q4c_density: unknown precision");
   try {
     if (prec == Q4C_FP64) return density_fp64(t, g, P, n, reinterpret_cast<cudaStream_t>(stream));
+    return density_split(t, g, P, n, reinterpret_cast<cudaStream_t>(stream));
   } catch (const std::exception& e) {
     set_error(std::string("q4c_density: ") + e.what());
     return Q4C_ENOMEM;
   }
-  set_error("q4c_density: the split-precision density is not built yet");
-  return Q4C_EUNSUPPORTED;
 }
 
 extern "C" q4c_status q4c_integrate_backward(const q4c_tables* t, const q4c_grid* g, const q4c_matrices* G,
@@ -64,12 +63,11 @@ extern "C" q4c_status q4c_integrate_backward(const q4c_tables* t, const q4c_grid
   Q4C_CHECK_ARG(prec == Q4C_FP64 || prec == Q4C_SPLIT, "q4c_integrate_backward: unknown precision");
   try {
     if (prec == Q4C_FP64) return backward_fp64(t, g, G, dLdv, reinterpret_cast<cudaStream_t>(stream));
+    return backward_split(t, g, G, dLdv, reinterpret_cast<cudaStream_t>(stream));
   } catch (const std::exception& e) {
     set_error(std::string("q4c_integrate_backward: ") + e.what());
     return Q4C_ENOMEM;
   }
-  set_error("q4c_integrate_backward: the split-precision adjoint is not built yet");
-  return Q4C_EUNSUPPORTED;
 }
 
 extern "C" q4c_status q4c_basis_eval(const q4c_tables* t, const q4c_grid* g, int64_t n_pts, const double* xyz,

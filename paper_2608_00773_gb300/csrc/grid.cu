@@ -480,6 +480,20 @@ extern "C" q4c_status grid_partition(const q4c_grid_desc* d, const q4c_tables* t
     for (auto& x : lst) sitems.push_back(x.second);
     g->split_w0.push_back(static_cast<int64_t>(sitems.size()));
   }
+  // density/adjoint: (batch, 64-point tile) items per wave, costliest first
+  std::vector<int2> rditems;
+  g->rd_w0.push_back(0);
+  for (size_t wv = 0; wv + 1 < g->wave_b0.size(); ++wv) {
+    std::vector<std::pair<double, int2>> lst;
+    for (int64_t b = g->wave_b0[wv]; b < g->wave_b0[wv + 1]; ++b) {
+      const int64_t np = bptr[b + 1] - bptr[b];
+      const double nb = static_cast<double>(g->h_bat_fn_ptr[b + 1] - g->h_bat_fn_ptr[b]);
+      for (int pt = 0; pt * 64 < np; ++pt) lst.push_back({nb * nb, make_int2(static_cast<int>(b), pt)});
+    }
+    std::stable_sort(lst.begin(), lst.end(), [](const auto& a, const auto& b) { return a.first > b.first; });
+    for (auto& x : lst) rditems.push_back(x.second);
+    g->rd_w0.push_back(static_cast<int64_t>(rditems.size()));
+  }
 
   // ---- schedule for persistent kernels: descending n_p n_b^2
   std::vector<int> sched(nB);
@@ -511,7 +525,7 @@ extern "C" q4c_status grid_partition(const q4c_grid_desc* d, const q4c_tables* t
       (st = up(&g->d_blk_off, g->h_blk_off)) || (st = up(&g->d_blk_row, blk_row)) ||
       (st = up(&g->d_blk_col, g->h_blk_col)) || (st = up(&g->d_blk_T, blk_T)) ||
       (st = up(&g->d_scr_off, g->h_scr_off)) || (st = up(&g->d_tiles, tiles)) || (st = up(&g->d_sched, sched)) ||
-      (st = up(&g->d_split_items, sitems))) {
+      (st = up(&g->d_split_items, sitems)) || (st = up(&g->d_rd_items, rditems))) {
     q4c_grid_destroy(g);
     return st;
   }
@@ -520,9 +534,10 @@ extern "C" q4c_status grid_partition(const q4c_grid_desc* d, const q4c_tables* t
     cudaError_t e = cudaMalloc(&g->d_scratch, sizeof(double) * g->scratch_doubles);
     if (e == cudaSuccess) e = cudaMalloc(&g->d_counter, sizeof(int) * std::max<size_t>(n_waves, 1));
     if (e == cudaSuccess) e = cudaMalloc(&g->d_colexp, sizeof(int) * 8 * std::max<int64_t>(g->h_bat_fn_ptr[nB], 1));
+    if (e == cudaSuccess) e = cudaMalloc(&g->d_rowexp, sizeof(int) * 4 * nP);
     if (e == cudaSuccess) e = cudaMalloc(&g->d_status, sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMemset(g->d_status, 0, sizeof(unsigned));
-    g->split_ws_bytes = static_cast<int64_t>(sizeof(int)) * 8 * g->h_bat_fn_ptr[nB];
+    g->split_ws_bytes = static_cast<int64_t>(sizeof(int)) * (8 * g->h_bat_fn_ptr[nB] + 4 * nP);
     if (e != cudaSuccess) {
       set_error(std::string("grid_partition: workspace: ") + cudaGetErrorString(e));
       q4c_grid_destroy(g);
@@ -539,7 +554,7 @@ extern "C" void q4c_grid_destroy(q4c_grid* g) {
                   g->d_pt_ptr, g->d_bat_atom_ptr, g->d_bat_atoms, g->d_bat_atom_fn0, g->d_bat_fn_ptr,
                   g->d_fn_info, g->d_bat_pair_ptr, g->d_pair_off, g->d_blk_off, g->d_blk_row, g->d_blk_col,
                   g->d_blk_T, g->d_scr_off, g->d_tiles, g->d_scratch, g->d_sched, g->d_counter, g->d_split_ws,
-                  g->d_split_items, g->d_colexp, g->d_status};
+                  g->d_split_items, g->d_colexp, g->d_status, g->d_rd_items, g->d_rowexp};
   for (void* p : ptrs) cudaFree(p);
   delete g;
 }

@@ -131,6 +131,9 @@ struct q4c_grid {
   std::vector<int64_t> split_w0;           // [n_waves+1] ranges into d_split_items
   int4* d_split_items = nullptr;
   int* d_colexp = nullptr;                 // [8 * sum n_b]
+  std::vector<int64_t> rd_w0;              // [n_waves+1] ranges into d_rd_items
+  int2* d_rd_items = nullptr;              // (batch, 64-point tile) for density/adjoint
+  int* d_rowexp = nullptr;                 // [n_points][4] per-point exponents
   unsigned* d_status = nullptr;            // bit 0: a bounded wait expired
   int64_t split_ws_bytes = 0;
   void* d_split_ws = nullptr;
@@ -149,6 +152,10 @@ q4c_status basis_eval(const q4c_tables* t, const q4c_grid* g, int64_t n_pts, con
 q4c_status mirror_and_spinor(const q4c_grid* g, const q4c_matrices* out, cudaStream_t s);
 q4c_status launch_basis_tiles(const q4c_tables* t, const q4c_grid* g, int64_t b0, int64_t b1, const double* v,
                               int* colexp, cudaStream_t s);
+// rowdot.cu
+q4c_status density_split(const q4c_tables* t, const q4c_grid* g, const double* P, double* n, cudaStream_t s);
+q4c_status backward_split(const q4c_tables* t, const q4c_grid* g, const q4c_matrices* G, double* dLdv,
+                          cudaStream_t s);
 // split.cu
 q4c_status integrate_split(const q4c_tables* t, const q4c_grid* g, const double* v, const q4c_matrices* out,
                            cudaStream_t s);

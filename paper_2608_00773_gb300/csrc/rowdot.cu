@@ -1,0 +1,358 @@
+// Split-precision density (Eqs. 39-40) and adjoint of the integration on the
+// tcgen05 tensor cores.
+//
+// Both are row-dot contractions over the batch's active functions:
+//   density   n_p     = sum_j Phi_pj (Phi P)_pj
+//   adjoint   dL/dv_p = w_p [ sum_j Phi_pj (Phi G^V)_pj + sum_{Q=X,Y,Z} sum_j Q_pj (Q G^W)_pj
+//                             + 2 sum_j ( Z_pj (Y Gx)_pj + X_pj (Z Gy)_pj + Y_pj (X Gz)_pj ) ]
+// with Gk the antisymmetric part of G^SOk (the cross product is antisymmetric
+// in i, j, so only that part contributes), i.e. seven products U = F G'
+// (M = points, K = functions i, N = functions j) whose rows are dotted with
+// R in the epilogue, one point per tensor-memory lane.
+//
+// Each U is computed from six BF16 slices of F (per-point exponents) and of
+// G' (per-column exponents) with the same tile sequence and exact-level
+// accumulation as the integration (see split.cu): levels 0-2 are exact
+// integer sums (K = n_b <= 512), levels 3-5 are rounded 2^-24 below.
+#include "internal.h"
+#include "tc.cuh"
+
+namespace q4c {
+namespace rowdot {
+using namespace tc;
+
+constexpr int kTile = 64;                    // points per tile (and functions per j-tile)
+constexpr int kKc = 16;                      // functions i per chunk (one K = 16 MMA step)
+constexpr int kTileBytes = kTile * kKc * 2;  // 2 KB
+constexpr int kSBO = (kKc / 8) * 128;        // 256 B
+constexpr int kThreads = 128;
+constexpr int kSmemA = 0;                                    // [Z, A0..A5]
+constexpr int kSmemB = kSmemA + (kSlices + 1) * kTileBytes;  // [B0..B5]
+constexpr int kSmemStage = kSmemB + kSlices * kTileBytes;    // epilogue staging (24 KB)
+constexpr int kSmemExpF = kSmemStage + kThreads * 16 * 3 * 4;
+constexpr int kSmemExpG = kSmemExpF + kTile * 4;
+constexpr int kSmemY = kSmemExpG + kTile * 4;
+constexpr int kSmemBar = kSmemY + kThreads * 8;
+constexpr int kSmemTotal = kSmemBar + 64;
+constexpr uint32_t kTmemCols = 256;
+constexpr int kMaxNb = 512;
+
+struct Product {
+  int qf, gm, anti, qr;
+  double factor;
+};
+
+__device__ __forceinline__ int local_nf(const DevBasis& B, const DevGrid& G, int a0, int a) {
+  return __ldg(B.sp_nfn + G.atom_sp[G.bat_atoms[a0 + a]]);
+}
+
+// G'_ij of the batch (i, j local), gathered from the block pattern
+__device__ __forceinline__ double gather(const DevBasis& B, const DevGrid& G, const double* M, int64_t f0, int a0,
+                                         int na, int64_t pp, int i, int j) {
+  const int ii = G.fn_info[f0 + i], jj = G.fn_info[f0 + j];
+  const int64_t off = G.pair_off[pp + static_cast<int64_t>(ii >> 16) * na + (jj >> 16)];
+  if (off < 0) return 0.0;
+  return M[off + static_cast<int64_t>(ii & 0xffff) * local_nf(B, G, a0, jj >> 16) + (jj & 0xffff)];
+}
+
+__device__ __forceinline__ double gprime(const DevBasis& B, const DevGrid& G, const double* M, int anti,
+                                         int64_t f0, int a0, int na, int64_t pp, int i, int j) {
+  const double g = gather(B, G, M, f0, a0, na, pp, i, j);
+  if (!anti) return g;
+  return 0.5 * (g - gather(B, G, M, f0, a0, na, pp, j, i));
+}
+
+__device__ __forceinline__ int binexp(double x) {
+  return static_cast<int>((__double_as_longlong(x) >> 52) & 0x7FF) - 1022;
+}
+
+// per point and quantity: exponent of the largest |value| over the batch's functions
+__global__ void k_rowexp(DevGrid G, int64_t b0, const int64_t* __restrict__ scr_off, const double* __restrict__ scratch,
+                         int* __restrict__ rowexp) {
+  const int64_t b = b0 + blockIdx.x;
+  const int64_t p0 = G.pt_ptr[b];
+  const int np = static_cast<int>(G.pt_ptr[b + 1] - p0);
+  const int ldp = (np + 7) & ~7;
+  const int nb = static_cast<int>(G.bat_fn_ptr[b + 1] - G.bat_fn_ptr[b]);
+  const int64_t plane = static_cast<int64_t>(nb) * ldp;
+  const double* base = scratch + scr_off[b];
+  for (int e = threadIdx.x; e < 4 * np; e += blockDim.x) {
+    const int q = e / np, p = e - q * np;
+    int m = -30000;
+    for (int f = 0; f < nb; ++f) {
+      const double x = base[q * plane + static_cast<int64_t>(f) * ldp + p];
+      if (x != 0.0) m = max(m, binexp(x));
+    }
+    rowexp[4 * (p0 + p) + q] = m;
+  }
+}
+
+template <int MODE>  // 0: density, 1: adjoint
+__global__ void __launch_bounds__(kThreads, 2)
+    k_split_rowdot(DevBasis B, DevGrid G, const int2* __restrict__ items, int n_items, int* counter,
+                   const int64_t* __restrict__ scr_off, const double* __restrict__ scratch,
+                   const int* __restrict__ rowexp, const double* M0, const double* M1, const double* M2,
+                   const double* M3, const double* M4, double* __restrict__ out, unsigned* status) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  unsigned char* sA = smem + kSmemA;
+  unsigned char* sB = smem + kSmemB;
+  float* stage = reinterpret_cast<float*>(smem + kSmemStage);
+  int* sExpF = reinterpret_cast<int*>(smem + kSmemExpF);
+  int* sExpG = reinterpret_cast<int*>(smem + kSmemExpG);
+  double* sY = reinterpret_cast<double*>(smem + kSmemY);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + kSmemBar);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + kSmemBar + 16);
+  int* s_item = reinterpret_cast<int*>(smem + kSmemBar + 32);
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const uint32_t bar_addr = smem_u32(bar);
+  const double* mats[5] = {M0, M1, M2, M3, M4};
+  // (F quantity, G matrix, antisymmetric part?, R quantity, factor)
+  const Product prods_adj[7] = {{0, 0, 0, 0, 1.0}, {1, 1, 0, 1, 1.0}, {2, 1, 0, 2, 1.0}, {3, 1, 0, 3, 1.0},
+                                {2, 2, 1, 3, 2.0}, {3, 3, 1, 1, 2.0}, {1, 4, 1, 2, 2.0}};
+  const Product prod_den = {0, 0, 0, 0, 1.0};
+  const int n_prod = MODE == 0 ? 1 : 7;
+
+  for (int i = tid; i < kTileBytes / 16; i += kThreads)
+    reinterpret_cast<uint4*>(sA)[i] = make_uint4(0, 0, 0, 0);  // tile Z
+  if (tid == 0) mbar_init(bar_addr, 1);
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(kTmemCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  uint32_t phase = 0;
+  bool ok = true;
+
+  while (ok) {
+    if (tid == 0) *s_item = atomicAdd(counter, 1);
+    __syncthreads();
+    const int it = *s_item;
+    if (it >= n_items) break;
+    const int2 item = items[it];
+    const int64_t b = item.x;
+    const int pt = item.y;
+    const int64_t bp0 = G.pt_ptr[b];
+    const int np = static_cast<int>(G.pt_ptr[b + 1] - bp0);
+    const int ldp = (np + 7) & ~7;
+    const int nb = static_cast<int>(G.bat_fn_ptr[b + 1] - G.bat_fn_ptr[b]);
+    const int64_t plane = static_cast<int64_t>(nb) * ldp;
+    const double* base = scratch + scr_off[b];
+    const int64_t f0 = G.bat_fn_ptr[b];
+    const int a0 = G.bat_atom_ptr[b], na = G.bat_atom_ptr[b + 1] - a0;
+    const int64_t pp = G.bat_pair_ptr[b];
+    const int r0 = pt * kTile;  // first point of the tile within the batch
+    double y = 0.0;             // partial of point r0 + (tid & 63)
+    const int n_ic = (nb + kKc - 1) / kKc;
+
+    for (int j0 = 0; j0 < nb && ok; j0 += kTile) {
+      const int N = (min(kTile, nb - j0) + 15) & ~15;
+      const uint32_t idesc = make_idesc(128, N);
+      for (int k = 0; k < n_prod && ok; ++k) {
+        const Product P = MODE == 0 ? prod_den : prods_adj[k];
+        const double* Gm = mats[P.gm];
+        if (Gm == nullptr) continue;
+        // exponents: rows of F (per point), columns of G' (per j over all i)
+        if (tid < kTile) {
+          sExpG[tid] = -30000;
+          const int p = r0 + tid;
+          sExpF[tid] = p < np ? rowexp[4 * (bp0 + p) + P.qf] : -30000;
+        }
+        __syncthreads();
+        for (int e = tid; e < kTile * nb; e += kThreads) {
+          const int jr = e & (kTile - 1), i = e >> 6;
+          const int j = j0 + jr;
+          if (j >= nb) continue;
+          const double g = gprime(B, G, Gm, P.anti, f0, a0, na, pp, i, j);
+          if (g != 0.0) atomicMax(&sExpG[jr], binexp(g));
+        }
+        for (int ic = 0; ic < n_ic && ok; ++ic) {
+          const int i0 = ic * kKc;
+          if (ic > 0) {
+            ok = __syncthreads_and(mbar_wait(bar_addr, phase & 1, status));
+            ++phase;
+            tc_fence_after();
+            if (!ok) break;
+          } else {
+            __syncthreads();
+          }
+          // slice F (rows = points, k = functions) and G' (rows = j, k = functions)
+          for (int side = 0; side < 2; ++side) {
+            unsigned char* dst = side == 0 ? sA + kTileBytes : sB;
+            const int* ex = side == 0 ? sExpF : sExpG;
+            for (int u = warp; u < 16; u += kThreads / 32) {
+              const int rg = u >> 1, kq = u & 1;
+              const int r = rg * 8 + (lane >> 2), kp = kq * 4 + (lane & 3);
+              const int i = i0 + 2 * kp;
+              double x0 = 0.0, x1 = 0.0;
+              if (side == 0) {
+                const int p = r0 + r;
+                if (p < np) {
+                  if (i < nb) x0 = base[P.qf * plane + static_cast<int64_t>(i) * ldp + p];
+                  if (i + 1 < nb) x1 = base[P.qf * plane + static_cast<int64_t>(i + 1) * ldp + p];
+                }
+              } else {
+                const int j = j0 + r;
+                if (j < nb) {
+                  if (i < nb) x0 = gprime(B, G, Gm, P.anti, f0, a0, na, pp, i, j);
+                  if (i + 1 < nb) x1 = gprime(B, G, Gm, P.anti, f0, a0, na, pp, i + 1, j);
+                }
+              }
+              const int e = ex[r];
+              int d0[kSlices], d1[kSlices];
+              digits6(x0, e, d0);
+              digits6(x1, e, d1);
+              const int off = rg * kSBO + kq * kLBO + (lane >> 2) * 16 + (lane & 3) * 4;
+#pragma unroll
+              for (int s = 0; s < kSlices; ++s) {
+                const float sc = pow2f(e - 6 - 8 * s);
+                *reinterpret_cast<__nv_bfloat162*>(dst + s * kTileBytes + off) =
+                    __floats2bfloat162_rn(static_cast<float>(d0[s]) * sc, static_cast<float>(d1[s]) * sc);
+              }
+            }
+          }
+          fence_async_smem();
+          __syncthreads();
+          if (tid == 0) {
+            tc_fence_after();
+            const uint32_t a = smem_u32(sA), bb = smem_u32(sB);
+            const uint32_t t0 = tmem, t1 = tmem + kTile, t2 = tmem + 2 * kTile;
+            const uint32_t acc = ic == 0 ? 0u : 1u;
+            auto A = [&](int q) { return make_desc(a + q * kTileBytes, kSBO); };
+            auto Bt = [&](int t) { return make_desc(bb + t * kTileBytes, kSBO); };
+            mma_bf16(t0, A(1), Bt(0), idesc, acc);
+            mma_bf16(t0, A(0), Bt(1), idesc, 1u);
+            mma_bf16(t1, A(3), Bt(0), idesc, acc);
+            mma_bf16(t1, A(2), Bt(1), idesc, 1u);
+            mma_bf16(t1, A(1), Bt(2), idesc, 1u);
+            mma_bf16(t1, A(0), Bt(3), idesc, 1u);
+            mma_bf16(t2, A(5), Bt(0), idesc, acc);
+            mma_bf16(t2, A(4), Bt(1), idesc, 1u);
+            mma_bf16(t2, A(3), Bt(2), idesc, 1u);
+            mma_bf16(t2, A(2), Bt(3), idesc, 1u);
+            mma_bf16(t2, A(1), Bt(4), idesc, 1u);
+            mma_bf16(t2, A(0), Bt(5), idesc, 1u);
+            mma_commit(bar_addr);
+          }
+        }
+        if (!ok) break;
+        ok = __syncthreads_and(mbar_wait(bar_addr, phase & 1, status));
+        ++phase;
+        tc_fence_after();
+        if (!ok) break;
+        // epilogue: U_rj from the six levels, dotted with R_rj
+        const int r = tid & 63, half = tid >> 6;
+        const int p = r0 + r;
+        for (int c0 = 0; c0 < N; c0 += 16) {
+          const uint32_t lane_base = static_cast<uint32_t>(warp * 32) << 16;
+#pragma unroll
+          for (int blk = 0; blk < 3; ++blk) {
+            float vv[16];
+            tmem_ld16(tmem + lane_base + blk * kTile + c0, vv);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) stage[(tid * 16 + i) * 3 + blk] = vv[i];
+          }
+          __syncthreads();
+          if (p < np) {
+            for (int cc = 0; cc < 8; ++cc) {
+              const int col = half * 8 + cc, j = j0 + c0 + col;
+              if (j >= nb) continue;
+              const float* top = stage + (r * 16 + col) * 3;
+              const float* bot = stage + ((r + 64) * 16 + col) * 3;
+              const float L0 = top[0], L1 = bot[0], L2 = top[1], L3 = bot[1], L4 = top[2], L5 = bot[2];
+              float s = L0 + L1;
+              float bp = s - L0;
+              const float e1 = (L0 - (s - bp)) + (L1 - bp);
+              const float s1 = s;
+              s = s1 + L2;
+              bp = s - s1;
+              const float e2 = (s1 - (s - bp)) + (L2 - bp);
+              const float lo = (e1 + e2) + (L3 + (L4 + L5));
+              const double u = static_cast<double>(s) + static_cast<double>(lo);
+              const double R = base[P.qr * plane + static_cast<int64_t>(j) * ldp + p];
+              y = fma(P.factor * R, u, y);
+            }
+          }
+          __syncthreads();
+        }
+        tc_fence_before();
+        __syncthreads();
+      }
+    }
+    // combine the two column halves of each point and write
+    sY[tid] = y;
+    __syncthreads();
+    if (tid < kTile && r0 + tid < np) {
+      const int64_t gp = bp0 + r0 + tid;
+      const double val = sY[tid] + sY[tid + 64];
+      out[gp] = MODE == 0 ? val : G.w[gp] * val;
+    }
+    __syncthreads();
+  }
+  if (!ok) (void)__syncthreads_and(mbar_wait(bar_addr, phase & 1, status));
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
+}
+
+template <int MODE>
+q4c_status run(const q4c_tables* t, const q4c_grid* g, const double* const mats[5], double* out, cudaStream_t s) {
+  if (g->max_nb > kMaxNb) {
+    set_error("the split density/adjoint need at most 512 active functions per batch");
+    return Q4C_EUNSUPPORTED;
+  }
+  const int n_waves = static_cast<int>(g->wave_b0.size()) - 1;
+  Q4C_CUDA(cudaMemsetAsync(g->d_counter, 0, sizeof(int) * std::max(n_waves, 1), s));
+  Q4C_CUDA(cudaFuncSetAttribute(k_split_rowdot<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemTotal));
+  int dev = 0, n_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+  for (int wv = 0; wv < n_waves; ++wv) {
+    const int64_t b0 = g->wave_b0[wv], b1 = g->wave_b0[wv + 1];
+    if (b1 <= b0) continue;
+    if (q4c_status st = launch_basis_tiles(t, g, b0, b1, nullptr, nullptr, s)) return st;
+    {
+      KernelScope ks("split_rowexp", s);
+      k_rowexp<<<static_cast<unsigned>(b1 - b0), 128, 0, s>>>(g->view(), b0, g->d_scr_off, g->d_scratch, g->d_rowexp);
+    }
+    Q4C_CUDA(cudaGetLastError());
+    const int64_t i0 = g->rd_w0[wv], i1 = g->rd_w0[wv + 1];
+    const int n_items = static_cast<int>(i1 - i0);
+    if (n_items == 0) continue;
+    const int grid = std::min(n_items, 2 * n_sm);
+    {
+      KernelScope ks(MODE == 0 ? "split_density" : "split_backward", s);
+      k_split_rowdot<MODE><<<grid, kThreads, kSmemTotal, s>>>(
+          t->view(), g->view(), g->d_rd_items + i0, n_items, g->d_counter + wv, g->d_scr_off, g->d_scratch,
+          g->d_rowexp, mats[0], mats[1], mats[2], mats[3], mats[4], out, g->d_status);
+    }
+    Q4C_CUDA(cudaGetLastError());
+  }
+  return Q4C_OK;
+}
+
+}  // namespace rowdot
+
+q4c_status density_split(const q4c_tables* t, const q4c_grid* g, const double* P, double* n, cudaStream_t s) {
+  const double* mats[5] = {P, nullptr, nullptr, nullptr, nullptr};
+  return rowdot::run<0>(t, g, mats, n, s);
+}
+
+q4c_status backward_split(const q4c_tables* t, const q4c_grid* g, const q4c_matrices* Gm, double* dLdv,
+                          cudaStream_t s) {
+  const double* mats[5] = {Gm->V, Gm->W0, Gm->SOx, Gm->SOy, Gm->SOz};
+  // with every slot NULL the gradient is zero
+  if (!Gm->V && !Gm->W0 && !Gm->SOx && !Gm->SOy && !Gm->SOz) {
+    Q4C_CUDA(cudaMemsetAsync(dLdv, 0, sizeof(double) * g->n_pts, s));
+    return Q4C_OK;
+  }
+  return rowdot::run<1>(t, g, mats, dLdv, s);
+}
+
+}  // namespace q4c

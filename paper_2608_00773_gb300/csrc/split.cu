@@ -36,19 +36,17 @@
 // while scattering.  Persistent CTAs (128 threads, 256 TMEM columns, two
 // per SM) loop over work items; every mbarrier wait is bounded and sets a
 // status bit instead of hanging.
-#include <cuda_bf16.h>
-
 #include "internal.h"
+#include "tc.cuh"
 
 namespace q4c {
 namespace split {
+using namespace tc;
 
 constexpr int kTile = 64;          // functions per tile (rows of one half of M)
 constexpr int kKc = 16;            // points per chunk (one K = 16 MMA step)
-constexpr int kSlices = 6;
 constexpr int kTileBytes = kTile * kKc * 2;  // 2 KB
 constexpr int kSBO = (kKc / 8) * 128;        // 256 B between 8-row groups
-constexpr int kLBO = 128;                    // core matrices adjacent in K
 constexpr int kThreads = 128;
 constexpr int kMaxProducts = 3;
 constexpr int kAStride = (kSlices + 1) * kTileBytes;  // [Z, A0..A5]
@@ -60,121 +58,6 @@ constexpr int kSmemExp = kSmemD + kKc * 8;
 constexpr int kSmemBar = kSmemExp + 2 * kMaxProducts * kTile * 4;
 constexpr int kSmemTotal = kSmemBar + 64;
 constexpr uint32_t kTmemCols = 256;  // three 64-column blocks
-constexpr uint64_t kWaitLimitNs = 1000000000ull;  // 1 s of wall clock per wait
-
-// ------------------------------------------------------------ PTX helpers
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-// K-major, no-swizzle shared-memory matrix descriptor (tcgen05 format)
-__device__ __forceinline__ uint64_t make_desc(uint32_t addr) {
-  uint64_t d = 0;
-  d |= static_cast<uint64_t>((addr >> 4) & 0x3FFF);
-  d |= static_cast<uint64_t>((kLBO >> 4) & 0x3FFF) << 16;
-  d |= static_cast<uint64_t>((kSBO >> 4) & 0x3FFF) << 32;
-  d |= static_cast<uint64_t>(1) << 46;  // descriptor version for tcgen05
-  return d;                              // base offset 0, swizzle none
-}
-
-// kind::f16 instruction descriptor: BF16 x BF16 -> FP32, both K-major
-__device__ __forceinline__ uint32_t make_idesc(int M, int N) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | (static_cast<uint32_t>(N >> 3) << 17) |
-         (static_cast<uint32_t>(M >> 4) << 24);
-}
-
-__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                         uint32_t accumulate) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
-      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
-}
-
-__device__ __forceinline__ void mma_commit(uint32_t bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
-               : "memory");
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}\n"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-__device__ __forceinline__ uint64_t global_ns() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-// bounded wait; returns false (and sets the status bit) once 1 s has passed
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, unsigned* status) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const uint64_t t0 = global_ns();
-  while (true) {
-    if (mbar_try_wait(bar, parity)) return true;
-    if (global_ns() - t0 > kWaitLimitNs) break;
-  }
-  atomicOr(status, 1u);
-  return false;
-}
-
-__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-// ------------------------------------------------------------ slicing
-// x = sum_s d_s 2^(e - 6 - 8 s) + O(2^(e-47)), digits from the integer
-// N = round(x 2^(46 - e)) by balanced base-256 extraction (|d_0| <= 64).
-__device__ __forceinline__ void digits6(double x, int e, int d[kSlices]) {
-#pragma unroll
-  for (int s = 0; s < kSlices; ++s) d[s] = 0;
-  const long long bits = __double_as_longlong(x);
-  const int E = static_cast<int>((bits >> 52) & 0x7FF);
-  if (E == 0 || e < -1000) return;  // zero (or below the FP64 normal range)
-  const long long M = (bits & 0xFFFFFFFFFFFFFLL) | (1LL << 52);
-  const int sh = 1075 + e - 46 - E;  // >= 6 because |x| <= 2^e
-  if (sh >= 62) return;
-  long long N = (M + (1LL << (sh - 1))) >> sh;
-  if (bits < 0) N = -N;
-  long long r = N;
-#pragma unroll
-  for (int s = 0; s < kSlices - 1; ++s) {
-    const int w = 8 * (kSlices - 1 - s);  // 40, 32, 24, 16, 8
-    const long long q = (r + (1LL << (w - 1))) >> w;
-    r -= q << w;
-    d[s] = static_cast<int>(q);
-  }
-  d[kSlices - 1] = static_cast<int>(r);
-}
-
-__device__ __forceinline__ float pow2f(int k) {  // 2^k as float, 0 below the normal range
-  return (k < -126) ? 0.0f : __int_as_float((k + 127) << 23);
-}
 
 // ------------------------------------------------------------ kernel
 struct Products {
@@ -339,8 +222,8 @@ __global__ void __launch_bounds__(kThreads, 2)
           const bool first = (c == 0 && pr == 0);
           const uint32_t t0 = tmem, t1 = tmem + kTile, t2 = tmem + 2 * kTile;
           const uint32_t acc = first ? 0u : 1u;
-          auto A = [&](int k) { return make_desc(a + k * kTileBytes); };
-          auto Bt = [&](int t) { return make_desc(bb + t * kTileBytes); };
+          auto A = [&](int k) { return make_desc(a + k * kTileBytes, kSBO); };
+          auto Bt = [&](int t) { return make_desc(bb + t * kTileBytes, kSBO); };
           mma_bf16(t0, A(1), Bt(0), idesc, acc);  // [A0;A1] x B0 -> L0, L1
           mma_bf16(t0, A(0), Bt(1), idesc, 1u);   // [Z;A0]  x B1 -> L1
           mma_bf16(t1, A(3), Bt(0), idesc, acc);  // [A2;A3] x B0 -> L2, L3

@@ -139,3 +139,73 @@ def test_full_size_sampled_entries(prec, tol, full):
     for n, g, r in zip(NAMES, got[:5], ref):
         s = _sampled(g, pat, pi, pj, first, lib.wl)
         assert np.linalg.norm(s - r) <= tol * np.linalg.norm(r), (prec, n, np.linalg.norm(s - r) / np.linalg.norm(r))
+
+
+# ----------------------------------------------------------------- density / adjoint
+
+
+@pytest.mark.parametrize("name", ["water", "cluster", "cluster12"])
+def test_density_split_matches_oracle(name, pairs):
+    from gpu_helpers import point_map
+    lib, orc = pairs[name]
+    n = q.q4c_density(lib.tables, lib.grid, lib.random(55, "P"), "split").cpu().numpy()
+    lib.grid.status()
+    nref = orc.ob.density(orc.xyz, orc.random(55, "P"), orc.pat)
+    li, oi = point_map(lib.ex["point_id"], orc.ids)
+    assert rel_fro(n[li], nref[oi]) <= TOL_SPLIT, rel_fro(n[li], nref[oi])
+
+
+@pytest.mark.parametrize("name", ["water", "cluster", "cluster12"])
+def test_backward_split_matches_oracle(name, pairs):
+    from gpu_helpers import point_map
+    lib, orc = pairs[name]
+    g = q.q4c_integrate_backward(lib.tables, lib.grid, lib.G(66), "split").cpu().numpy()
+    lib.grid.status()
+    gref = orc.ob.adjoint(orc.xyz, orc.w, orc.G(66), orc.pat)
+    li, oi = point_map(lib.ex["point_id"], orc.ids)
+    assert rel_fro(g[li], gref[oi]) <= TOL_SPLIT, rel_fro(g[li], gref[oi])
+
+
+def test_backward_split_partial_slots_and_autograd(pairs):
+    """NULL G slots count as zero; the autograd wrapper routes through the
+    split adjoint; linearity sum_p v_p dL/dv_p = L holds for the split pair."""
+    import torch
+    lib, orc = pairs["cluster"]
+    G = lib.G(8)
+    only_w = [None, G[1], None, None, None]
+    a = q.q4c_integrate_backward(lib.tables, lib.grid, only_w, "split").cpu().numpy()
+    b = q.q4c_integrate_backward(lib.tables, lib.grid, only_w, "fp64").cpu().numpy()
+    assert rel_fro(a, b) <= TOL_SPLIT
+    v = lib.v.clone().requires_grad_(True)
+    outs = q.integrate(v, lib.tables, lib.grid, "split")
+    L = sum((Gm * M).sum() for Gm, M in zip(G, outs))
+    (gv,) = torch.autograd.grad(L, v)
+    ref = q.q4c_integrate_backward(lib.tables, lib.grid, G, "fp64")
+    assert rel_fro(gv.cpu().numpy(), ref.cpu().numpy()) <= TOL_SPLIT
+    assert abs(float((lib.v * gv).sum()) - float(L)) <= 1e-9 * abs(float(L))
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", TOL_FP64), ("split", TOL_SPLIT)])
+def test_full_size_density_and_adjoint_sampled_points(prec, tol):
+    """Density and adjoint at the full workload against the oracle at 300
+    points of the oracle's own grid (matched by raw point id)."""
+    from workloads import ADJOINT_KINDS, fill_pattern
+    wl = cluster64()
+    lib = LibCase(wl)
+    xyz, w, ids = O.grid(wl)
+    ob = O.OracleBasis(wl)
+    pat = ob.pattern()
+    rng = np.random.default_rng(77)
+    sel = np.sort(rng.choice(len(ids), 300, replace=False))
+    P_o = fill_pattern(pat.blk_ptr, pat.blk_col, pat.blk_off, wl.nf_of_atom, 31, "P")
+    G_o = [fill_pattern(pat.blk_ptr, pat.blk_col, pat.blk_off, wl.nf_of_atom, 32, k, a) for k, a in ADJOINT_KINDS]
+    n_ref = ob.density(xyz[sel], P_o, pat)
+    g_ref = ob.adjoint(xyz[sel], w[sel], G_o, pat)
+    n = q.q4c_density(lib.tables, lib.grid, lib.random(31, "P"), prec).cpu().numpy()
+    g = q.q4c_integrate_backward(lib.tables, lib.grid, [lib.random(32, k, a) for k, a in ADJOINT_KINDS],
+                                 prec).cpu().numpy()
+    lib.grid.status()
+    pos = {int(p): k for k, p in enumerate(lib.ex["point_id"])}
+    li = np.array([pos[int(i)] for i in ids[sel]])
+    assert rel_fro(n[li], n_ref) <= tol, rel_fro(n[li], n_ref)
+    assert rel_fro(g[li], g_ref) <= tol, rel_fro(g[li], g_ref)
