@@ -299,8 +299,8 @@ def main():
     per_step = [a.elapsed_time(b) for a, b in ev]
     t_ms = max_over_ranks(statistics.mean(per_step), world)
     kern = {}
-    for name in ("split_products", "products_fp64", "density_fp64", "backward_fp64", "basis", "mirror", "spinor",
-                 "split_", ""):
+    for name in ("split_products", "split_backward", "split_density", "split_rowexp", "products_fp64",
+                 "density_fp64", "backward_fp64", "basis", "mirror", "spinor", ""):
         ms, n = q.profile_read(name)
         if n:
             kern[name or "other"] = (ms, n)
@@ -312,11 +312,12 @@ def main():
     clk = clocks.summary()
     dom_name, (dom_ms, dom_n) = max(kern.items(), key=lambda kv: kv[1][0])
     S_PAIRS = 21  # slice-pair products (s + t <= 5 of 6 BF16 slices per operand)
-    if dom_name == "split_products":
-        achieved = fl["integrate"] * S_PAIRS * args.steps / (dom_ms * 1e-3) / 1e12
+    if dom_name in ("split_products", "split_backward", "split_density"):
+        work = {"split_products": "integrate", "split_backward": "backward", "split_density": "density"}[dom_name]
+        achieved = fl[work] * S_PAIRS * args.steps / (dom_ms * 1e-3) / 1e12
         roof = {"bound": "tensor", "achieved": achieved, "peak": peaks["bf16_tflops_sustained"],
                 "unit": "TFLOP/s", "peak_source": f"{peak_src} bf16 sustained (of measured)",
-                "work": "14 n_p n_b^2 per batch x 21 slice pairs"}
+                "work": f"algorithmic FLOPs of {work} x {S_PAIRS} slice pairs"}
     elif dom_name in ("products_fp64", "density_fp64", "backward_fp64"):
         work = {"products_fp64": "integrate", "density_fp64": "density", "backward_fp64": "backward"}[dom_name]
         calls = sum(1 for ph, pr in phase_prec.items() if ph == work and pr == "fp64") or 1
