@@ -459,39 +459,45 @@ extern "C" q4c_status grid_partition(const q4c_grid_desc* d, const q4c_tables* t
 
   // ---- split path: (batch, output, ti, tj) items per wave, 64x64 tiles;
   // V and W0 need ti <= tj only, the A_yz/A_zx/A_xy products every tile.
-  // Largest work first inside each wave (persistent CTAs pull in order).
+  // Batches with the most work first; the items of one batch stay adjacent
+  // (W0, three products, leading) so that concurrent CTAs share its tiles in L2.
   std::vector<int4> sitems;
   g->split_w0.push_back(0);
   for (size_t wv = 0; wv + 1 < g->wave_b0.size(); ++wv) {
-    std::vector<std::pair<double, int4>> lst;
+    std::vector<std::pair<double, int64_t>> bl;
     for (int64_t b = g->wave_b0[wv]; b < g->wave_b0[wv + 1]; ++b) {
-      const int64_t np = bptr[b + 1] - bptr[b];
+      const double np = static_cast<double>(bptr[b + 1] - bptr[b]);
+      const double nb = static_cast<double>(g->h_bat_fn_ptr[b + 1] - g->h_bat_fn_ptr[b]);
+      bl.push_back({np * nb * nb, b});
+    }
+    std::stable_sort(bl.begin(), bl.end(), [](const auto& a, const auto& b) { return a.first > b.first; });
+    for (const auto& x : bl) {
+      const int64_t b = x.second;
       const int nb = static_cast<int>(g->h_bat_fn_ptr[b + 1] - g->h_bat_fn_ptr[b]);
       const int nt = (nb + 63) / 64;
-      for (int o = 0; o < 5; ++o)
+      for (int o : {1, 0, 2, 3, 4})
         for (int i = 0; i < nt; ++i)
           for (int j = 0; j < nt; ++j) {
             if (o <= 1 && i > j) continue;
-            const double cost = static_cast<double>(np) * (o == 1 ? 3.0 : 1.0);
-            lst.push_back({cost, make_int4(static_cast<int>(b), o, i, j)});
+            sitems.push_back(make_int4(static_cast<int>(b), o, i, j));
           }
     }
-    std::stable_sort(lst.begin(), lst.end(), [](const auto& a, const auto& b) { return a.first > b.first; });
-    for (auto& x : lst) sitems.push_back(x.second);
     g->split_w0.push_back(static_cast<int64_t>(sitems.size()));
   }
   // density/adjoint: (batch, 64-point tile) items per wave, costliest first
   std::vector<int2> rditems;
   g->rd_w0.push_back(0);
   for (size_t wv = 0; wv + 1 < g->wave_b0.size(); ++wv) {
-    std::vector<std::pair<double, int2>> lst;
+    std::vector<std::pair<double, int64_t>> bl;
     for (int64_t b = g->wave_b0[wv]; b < g->wave_b0[wv + 1]; ++b) {
-      const int64_t np = bptr[b + 1] - bptr[b];
       const double nb = static_cast<double>(g->h_bat_fn_ptr[b + 1] - g->h_bat_fn_ptr[b]);
-      for (int pt = 0; pt * 64 < np; ++pt) lst.push_back({nb * nb, make_int2(static_cast<int>(b), pt)});
+      bl.push_back({nb * nb, b});
     }
-    std::stable_sort(lst.begin(), lst.end(), [](const auto& a, const auto& b) { return a.first > b.first; });
-    for (auto& x : lst) rditems.push_back(x.second);
+    std::stable_sort(bl.begin(), bl.end(), [](const auto& a, const auto& b) { return a.first > b.first; });
+    for (const auto& x : bl) {  // the point tiles of one batch stay adjacent
+      const int64_t b = x.second, np = bptr[b + 1] - bptr[b];
+      for (int pt = 0; pt * 64 < np; ++pt) rditems.push_back(make_int2(static_cast<int>(b), pt));
+    }
     g->rd_w0.push_back(static_cast<int64_t>(rditems.size()));
   }
 
@@ -535,9 +541,10 @@ extern "C" q4c_status grid_partition(const q4c_grid_desc* d, const q4c_tables* t
     if (e == cudaSuccess) e = cudaMalloc(&g->d_counter, sizeof(int) * std::max<size_t>(n_waves, 1));
     if (e == cudaSuccess) e = cudaMalloc(&g->d_colexp, sizeof(int) * 8 * std::max<int64_t>(g->h_bat_fn_ptr[nB], 1));
     if (e == cudaSuccess) e = cudaMalloc(&g->d_rowexp, sizeof(int) * 4 * nP);
+    if (e == cudaSuccess) e = cudaMalloc(&g->d_gexp, sizeof(int) * 5 * std::max<int64_t>(g->h_bat_fn_ptr[nB], 1));
     if (e == cudaSuccess) e = cudaMalloc(&g->d_status, sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMemset(g->d_status, 0, sizeof(unsigned));
-    g->split_ws_bytes = static_cast<int64_t>(sizeof(int)) * (8 * g->h_bat_fn_ptr[nB] + 4 * nP);
+    g->split_ws_bytes = static_cast<int64_t>(sizeof(int)) * (13 * g->h_bat_fn_ptr[nB] + 4 * nP);
     if (e != cudaSuccess) {
       set_error(std::string("grid_partition: workspace: ") + cudaGetErrorString(e));
       q4c_grid_destroy(g);
@@ -554,7 +561,7 @@ extern "C" void q4c_grid_destroy(q4c_grid* g) {
                   g->d_pt_ptr, g->d_bat_atom_ptr, g->d_bat_atoms, g->d_bat_atom_fn0, g->d_bat_fn_ptr,
                   g->d_fn_info, g->d_bat_pair_ptr, g->d_pair_off, g->d_blk_off, g->d_blk_row, g->d_blk_col,
                   g->d_blk_T, g->d_scr_off, g->d_tiles, g->d_scratch, g->d_sched, g->d_counter, g->d_split_ws,
-                  g->d_split_items, g->d_colexp, g->d_status, g->d_rd_items, g->d_rowexp};
+                  g->d_split_items, g->d_colexp, g->d_status, g->d_rd_items, g->d_rowexp, g->d_gexp};
   for (void* p : ptrs) cudaFree(p);
   delete g;
 }

@@ -134,6 +134,7 @@ struct q4c_grid {
   std::vector<int64_t> rd_w0;              // [n_waves+1] ranges into d_rd_items
   int2* d_rd_items = nullptr;              // (batch, 64-point tile) for density/adjoint
   int* d_rowexp = nullptr;                 // [n_points][4] per-point exponents
+  int* d_gexp = nullptr;                   // [5 * sum n_b] per-batch column exponents of G
   unsigned* d_status = nullptr;            // bit 0: a bounded wait expired
   int64_t split_ws_bytes = 0;
   void* d_split_ws = nullptr;

@@ -26,9 +26,8 @@ constexpr int kKc = 16;                      // functions i per chunk (one K = 1
 constexpr int kTileBytes = kTile * kKc * 2;  // 2 KB
 constexpr int kSBO = (kKc / 8) * 128;        // 256 B
 constexpr int kThreads = 128;
-constexpr int kSmemA = 0;                                    // [Z, A0..A5]
-constexpr int kSmemB = kSmemA + (kSlices + 1) * kTileBytes;  // [B0..B5]
-constexpr int kSmemStage = kSmemB + kSlices * kTileBytes;    // epilogue staging (24 KB)
+constexpr int kSmemA = 0;                                      // two stages of [Z, A0..A5][B0..B5]
+constexpr int kSmemStage = kSmemA + 2 * (2 * kSlices + 1) * kTileBytes;  // epilogue staging (24 KB)
 constexpr int kSmemExpF = kSmemStage + kThreads * 16 * 3 * 4;
 constexpr int kSmemExpG = kSmemExpF + kTile * 4;
 constexpr int kSmemY = kSmemExpG + kTile * 4;
@@ -87,15 +86,45 @@ __global__ void k_rowexp(DevGrid G, int64_t b0, const int64_t* __restrict__ scr_
   }
 }
 
+// per batch, matrix and local function j: exponent of max_i |G'_ij|
+// (G' the matrix itself, or its antisymmetric part for the SO seeds)
+__global__ void k_gexp(DevBasis B, DevGrid G, int64_t b0, int n_mats, int anti_from, const double* M0,
+                       const double* M1, const double* M2, const double* M3, const double* M4,
+                       int* __restrict__ gexp) {
+  const int64_t b = b0 + blockIdx.x;
+  const int nb = static_cast<int>(G.bat_fn_ptr[b + 1] - G.bat_fn_ptr[b]);
+  const int64_t f0 = G.bat_fn_ptr[b];
+  const int a0 = G.bat_atom_ptr[b], na = G.bat_atom_ptr[b + 1] - a0;
+  const int64_t pp = G.bat_pair_ptr[b];
+  const double* mats[5] = {M0, M1, M2, M3, M4};
+  for (int e = threadIdx.x; e < n_mats * nb; e += blockDim.x) {
+    const int m = e / nb, j = e - m * nb;
+    int mx = -30000;
+    if (mats[m]) {
+      for (int i = 0; i < nb; ++i) {
+        const double g = gprime(B, G, mats[m], m >= anti_from, f0, a0, na, pp, i, j);
+        if (g != 0.0) mx = max(mx, binexp(g));
+      }
+    }
+    gexp[5 * f0 + m * nb + j] = mx;
+  }
+}
+
+constexpr int kStageA = (kSlices + 1) * kTileBytes;  // [Z, A0..A5]
+constexpr int kStage = kStageA + kSlices * kTileBytes;
+
+// One work item = (batch, 64-point tile).  For every j-tile and product the K
+// dimension (functions i) is a stream of 16-wide steps that alternate between
+// two shared-memory stages: the threads slice step s + 1 while the tensor core
+// runs the twelve MMAs of step s.
 template <int MODE>  // 0: density, 1: adjoint
 __global__ void __launch_bounds__(kThreads, 2)
     k_split_rowdot(DevBasis B, DevGrid G, const int2* __restrict__ items, int n_items, int* counter,
                    const int64_t* __restrict__ scr_off, const double* __restrict__ scratch,
-                   const int* __restrict__ rowexp, const double* M0, const double* M1, const double* M2,
-                   const double* M3, const double* M4, double* __restrict__ out, unsigned* status) {
+                   const int* __restrict__ rowexp, const int* __restrict__ gexp, const double* M0, const double* M1,
+                   const double* M2, const double* M3, const double* M4, double* __restrict__ out,
+                   unsigned* status) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  unsigned char* sA = smem + kSmemA;
-  unsigned char* sB = smem + kSmemB;
   float* stage = reinterpret_cast<float*>(smem + kSmemStage);
   int* sExpF = reinterpret_cast<int*>(smem + kSmemExpF);
   int* sExpG = reinterpret_cast<int*>(smem + kSmemExpG);
@@ -105,7 +134,7 @@ __global__ void __launch_bounds__(kThreads, 2)
   int* s_item = reinterpret_cast<int*>(smem + kSmemBar + 32);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const uint32_t bar_addr = smem_u32(bar);
+  const uint32_t bar_addr[2] = {smem_u32(bar), smem_u32(bar + 1)};
   const double* mats[5] = {M0, M1, M2, M3, M4};
   // (F quantity, G matrix, antisymmetric part?, R quantity, factor)
   const Product prods_adj[7] = {{0, 0, 0, 0, 1.0}, {1, 1, 0, 1, 1.0}, {2, 1, 0, 2, 1.0}, {3, 1, 0, 3, 1.0},
@@ -113,9 +142,14 @@ __global__ void __launch_bounds__(kThreads, 2)
   const Product prod_den = {0, 0, 0, 0, 1.0};
   const int n_prod = MODE == 0 ? 1 : 7;
 
-  for (int i = tid; i < kTileBytes / 16; i += kThreads)
-    reinterpret_cast<uint4*>(sA)[i] = make_uint4(0, 0, 0, 0);  // tile Z
-  if (tid == 0) mbar_init(bar_addr, 1);
+  for (int i = tid; i < 2 * kTileBytes / 16; i += kThreads) {  // tile Z of both stages
+    const int st = i / (kTileBytes / 16), off = i - st * (kTileBytes / 16);
+    reinterpret_cast<uint4*>(smem + kSmemA + st * kStage)[off] = make_uint4(0, 0, 0, 0);
+  }
+  if (tid == 0) {
+    mbar_init(bar_addr[0], 1);
+    mbar_init(bar_addr[1], 1);
+  }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
                  "r"(kTmemCols));
@@ -126,7 +160,9 @@ __global__ void __launch_bounds__(kThreads, 2)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
-  uint32_t phase = 0;
+  uint32_t ph[2] = {0, 0};
+  bool pending[2] = {false, false};  // a commit on this stage not yet waited for
+  int gstep = 0;                     // steps issued by this CTA (stage = gstep & 1)
   bool ok = true;
 
   while (ok) {
@@ -157,56 +193,49 @@ __global__ void __launch_bounds__(kThreads, 2)
         const Product P = MODE == 0 ? prod_den : prods_adj[k];
         const double* Gm = mats[P.gm];
         if (Gm == nullptr) continue;
-        // exponents: rows of F (per point), columns of G' (per j over all i)
         if (tid < kTile) {
-          sExpG[tid] = -30000;
-          const int p = r0 + tid;
+          const int p = r0 + tid, j = j0 + tid;
           sExpF[tid] = p < np ? rowexp[4 * (bp0 + p) + P.qf] : -30000;
+          sExpG[tid] = j < nb ? gexp[5 * f0 + P.gm * nb + j] : -30000;
         }
         __syncthreads();
-        for (int e = tid; e < kTile * nb; e += kThreads) {
-          const int jr = e & (kTile - 1), i = e >> 6;
-          const int j = j0 + jr;
-          if (j >= nb) continue;
-          const double g = gprime(B, G, Gm, P.anti, f0, a0, na, pp, i, j);
-          if (g != 0.0) atomicMax(&sExpG[jr], binexp(g));
-        }
-        for (int ic = 0; ic < n_ic && ok; ++ic) {
-          const int i0 = ic * kKc;
-          if (ic > 0) {
-            ok = __syncthreads_and(mbar_wait(bar_addr, phase & 1, status));
-            ++phase;
-            tc_fence_after();
+        for (int ic = 0; ic < n_ic && ok; ++ic, ++gstep) {
+          const int buf = gstep & 1;
+          if (pending[buf]) {  // the stage is free once the MMAs that read it finished
+            ok = __syncthreads_and(mbar_wait(bar_addr[buf], ph[buf], status));
+            ph[buf] ^= 1;
+            pending[buf] = false;
             if (!ok) break;
-          } else {
-            __syncthreads();
           }
-          // slice F (rows = points, k = functions) and G' (rows = j, k = functions)
+          const int i0 = ic * kKc;
+          unsigned char* sA = smem + kSmemA + buf * kStage;
+          unsigned char* sB = sA + kStageA;
+          // all loads and gathers of the step first, then the splitting
+          double xs[2][4][2];
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const int u = warp + 4 * k;
+            const int r = (u >> 1) * 8 + (lane >> 2), i = i0 + 2 * ((u & 1) * 4 + (lane & 3));
+            const int p = r0 + r, j = j0 + r;
+            const double* src = base + P.qf * plane + static_cast<int64_t>(i) * ldp + p;
+            xs[0][k][0] = (p < np && i < nb) ? src[0] : 0.0;
+            xs[0][k][1] = (p < np && i + 1 < nb) ? src[ldp] : 0.0;
+            xs[1][k][0] = (j < nb && i < nb) ? gprime(B, G, Gm, P.anti, f0, a0, na, pp, i, j) : 0.0;
+            xs[1][k][1] = (j < nb && i + 1 < nb) ? gprime(B, G, Gm, P.anti, f0, a0, na, pp, i + 1, j) : 0.0;
+          }
+#pragma unroll
           for (int side = 0; side < 2; ++side) {
             unsigned char* dst = side == 0 ? sA + kTileBytes : sB;
             const int* ex = side == 0 ? sExpF : sExpG;
-            for (int u = warp; u < 16; u += kThreads / 32) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              const int u = warp + 4 * k;
               const int rg = u >> 1, kq = u & 1;
-              const int r = rg * 8 + (lane >> 2), kp = kq * 4 + (lane & 3);
-              const int i = i0 + 2 * kp;
-              double x0 = 0.0, x1 = 0.0;
-              if (side == 0) {
-                const int p = r0 + r;
-                if (p < np) {
-                  if (i < nb) x0 = base[P.qf * plane + static_cast<int64_t>(i) * ldp + p];
-                  if (i + 1 < nb) x1 = base[P.qf * plane + static_cast<int64_t>(i + 1) * ldp + p];
-                }
-              } else {
-                const int j = j0 + r;
-                if (j < nb) {
-                  if (i < nb) x0 = gprime(B, G, Gm, P.anti, f0, a0, na, pp, i, j);
-                  if (i + 1 < nb) x1 = gprime(B, G, Gm, P.anti, f0, a0, na, pp, i + 1, j);
-                }
-              }
+              const int r = rg * 8 + (lane >> 2);
               const int e = ex[r];
               int d0[kSlices], d1[kSlices];
-              digits6(x0, e, d0);
-              digits6(x1, e, d1);
+              digits_of(fixed46(xs[side][k][0], e), d0);
+              digits_of(fixed46(xs[side][k][1], e), d1);
               const int off = rg * kSBO + kq * kLBO + (lane >> 2) * 16 + (lane & 3) * 4;
 #pragma unroll
               for (int s = 0; s < kSlices; ++s) {
@@ -237,12 +266,19 @@ __global__ void __launch_bounds__(kThreads, 2)
             mma_bf16(t2, A(2), Bt(3), idesc, 1u);
             mma_bf16(t2, A(1), Bt(4), idesc, 1u);
             mma_bf16(t2, A(0), Bt(5), idesc, 1u);
-            mma_commit(bar_addr);
+            mma_commit(bar_addr[buf]);
           }
+          pending[buf] = true;
         }
         if (!ok) break;
-        ok = __syncthreads_and(mbar_wait(bar_addr, phase & 1, status));
-        ++phase;
+        // drain the outstanding commits (oldest first) before reading TMEM
+        for (int d = 0; d < 2 && ok; ++d) {
+          const int buf = (gstep + d) & 1;
+          if (!pending[buf]) continue;
+          ok = __syncthreads_and(mbar_wait(bar_addr[buf], ph[buf], status));
+          ph[buf] ^= 1;
+          pending[buf] = false;
+        }
         tc_fence_after();
         if (!ok) break;
         // epilogue: U_rj from the six levels, dotted with R_rj
@@ -265,15 +301,15 @@ __global__ void __launch_bounds__(kThreads, 2)
               const float* top = stage + (r * 16 + col) * 3;
               const float* bot = stage + ((r + 64) * 16 + col) * 3;
               const float L0 = top[0], L1 = bot[0], L2 = top[1], L3 = bot[1], L4 = top[2], L5 = bot[2];
-              float s = L0 + L1;
-              float bp = s - L0;
-              const float e1 = (L0 - (s - bp)) + (L1 - bp);
-              const float s1 = s;
-              s = s1 + L2;
-              bp = s - s1;
-              const float e2 = (s1 - (s - bp)) + (L2 - bp);
+              float sm = L0 + L1;
+              float bp = sm - L0;
+              const float e1 = (L0 - (sm - bp)) + (L1 - bp);
+              const float s1 = sm;
+              sm = s1 + L2;
+              bp = sm - s1;
+              const float e2 = (s1 - (sm - bp)) + (L2 - bp);
               const float lo = (e1 + e2) + (L3 + (L4 + L5));
-              const double u = static_cast<double>(s) + static_cast<double>(lo);
+              const double u = static_cast<double>(sm) + static_cast<double>(lo);
               const double R = base[P.qr * plane + static_cast<int64_t>(j) * ldp + p];
               y = fma(P.factor * R, u, y);
             }
@@ -294,7 +330,10 @@ __global__ void __launch_bounds__(kThreads, 2)
     }
     __syncthreads();
   }
-  if (!ok) (void)__syncthreads_and(mbar_wait(bar_addr, phase & 1, status));
+  if (!ok) {
+    for (int d = 0; d < 2; ++d)
+      if (pending[d]) (void)__syncthreads_and(mbar_wait(bar_addr[d], ph[d], status));
+  }
   tc_fence_before();
   __syncthreads();
   if (warp == 0)
@@ -322,6 +361,13 @@ q4c_status run(const q4c_tables* t, const q4c_grid* g, const double* const mats[
       k_rowexp<<<static_cast<unsigned>(b1 - b0), 128, 0, s>>>(g->view(), b0, g->d_scr_off, g->d_scratch, g->d_rowexp);
     }
     Q4C_CUDA(cudaGetLastError());
+    {
+      KernelScope ks("split_gexp", s);
+      k_gexp<<<static_cast<unsigned>(b1 - b0), 128, 0, s>>>(t->view(), g->view(), b0, MODE == 0 ? 1 : 5,
+                                                            MODE == 0 ? 5 : 2, mats[0], mats[1], mats[2], mats[3],
+                                                            mats[4], g->d_gexp);
+    }
+    Q4C_CUDA(cudaGetLastError());
     const int64_t i0 = g->rd_w0[wv], i1 = g->rd_w0[wv + 1];
     const int n_items = static_cast<int>(i1 - i0);
     if (n_items == 0) continue;
@@ -330,7 +376,7 @@ q4c_status run(const q4c_tables* t, const q4c_grid* g, const double* const mats[
       KernelScope ks(MODE == 0 ? "split_density" : "split_backward", s);
       k_split_rowdot<MODE><<<grid, kThreads, kSmemTotal, s>>>(
           t->view(), g->view(), g->d_rd_items + i0, n_items, g->d_counter + wv, g->d_scr_off, g->d_scratch,
-          g->d_rowexp, mats[0], mats[1], mats[2], mats[3], mats[4], out, g->d_status);
+          g->d_rowexp, g->d_gexp, mats[0], mats[1], mats[2], mats[3], mats[4], out, g->d_status);
     }
     Q4C_CUDA(cudaGetLastError());
   }

@@ -43,19 +43,21 @@ namespace q4c {
 namespace split {
 using namespace tc;
 
-constexpr int kTile = 64;          // functions per tile (rows of one half of M)
-constexpr int kKc = 16;            // points per chunk (one K = 16 MMA step)
+constexpr int kTile = 64;                    // functions per tile (rows of one half of M)
+constexpr int kKc = 16;                      // points per step (one K = 16 MMA step)
 constexpr int kTileBytes = kTile * kKc * 2;  // 2 KB
 constexpr int kSBO = (kKc / 8) * 128;        // 256 B between 8-row groups
 constexpr int kThreads = 128;
 constexpr int kMaxProducts = 3;
-constexpr int kAStride = (kSlices + 1) * kTileBytes;  // [Z, A0..A5]
-constexpr int kBStride = kSlices * kTileBytes;        // [B0..B5]
-constexpr int kSmemA = 0;
-constexpr int kSmemB = kSmemA + kMaxProducts * kAStride;        // 42 KB
-constexpr int kSmemD = kSmemB + kMaxProducts * kBStride;        // +36 KB
-constexpr int kSmemExp = kSmemD + kKc * 8;
-constexpr int kSmemBar = kSmemExp + 2 * kMaxProducts * kTile * 4;
+constexpr int kStageA = (kSlices + 1) * kTileBytes;  // [Z, A0..A5]
+constexpr int kStageB = kSlices * kTileBytes;        // [B0..B5]
+constexpr int kStage = kStageA + kStageB;            // 26 KB
+constexpr int kSmemStages = 0;                       // two stages (double buffer)
+constexpr int kSmemEpi = kSmemStages + 2 * kStage;   // epilogue staging, 24 KB
+constexpr int kSmemD = kSmemEpi + kThreads * 16 * 3 * 4;
+constexpr int kMaxNp = 344;                          // D values of one batch
+constexpr int kSmemExp = kSmemD + kMaxNp * 8;
+constexpr int kSmemBar = kSmemExp + 2 * kTile * 4;
 constexpr int kSmemTotal = kSmemBar + 64;
 constexpr uint32_t kTmemCols = 256;  // three 64-column blocks
 
@@ -82,31 +84,37 @@ __device__ __forceinline__ int local_nf(const DevBasis& B, const DevGrid& G, int
   return __ldg(B.sp_nfn + G.atom_sp[G.bat_atoms[a0 + a]]);
 }
 
+// One work item = (batch, output, 64x64 tile).  Its K dimension is a stream
+// of steps of 16 points; W0 streams its three gradient products one after
+// the other (a K-concatenation into one accumulator, common exponents).
+// Steps alternate between two shared-memory stages: the 128 threads slice
+// step s + 1 while the tensor core runs the twelve MMAs of step s.
 __global__ void __launch_bounds__(kThreads, 2)
     k_split_products(DevBasis B, DevGrid G, const int4* __restrict__ items, int n_items, int* counter,
                      const int64_t* __restrict__ scr_off, const double* __restrict__ scratch,
                      const int* __restrict__ colexp, const double* __restrict__ v, double* V, double* W0,
                      double* SOx, double* SOy, double* SOz, unsigned* status) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  unsigned char* sA = smem + kSmemA;
-  unsigned char* sB = smem + kSmemB;
+  float* stage = reinterpret_cast<float*>(smem + kSmemEpi);
   double* sD = reinterpret_cast<double*>(smem + kSmemD);
   int* sExpA = reinterpret_cast<int*>(smem + kSmemExp);
-  int* sExpB = sExpA + kMaxProducts * kTile;
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + kSmemBar);
+  int* sExpB = sExpA + kTile;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + kSmemBar);  // two barriers
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + kSmemBar + 16);
   int* s_item = reinterpret_cast<int*>(smem + kSmemBar + 32);
-  float* stage = reinterpret_cast<float*>(sB);  // epilogue staging reuses the B tiles (24 KB)
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const uint32_t bar_addr = smem_u32(bar);
+  const uint32_t bar_addr[2] = {smem_u32(bar), smem_u32(bar + 1)};
 
-  // zero tile Z at the head of every product slot (never overwritten)
-  for (int i = tid; i < kMaxProducts * kTileBytes / 16; i += kThreads) {
-    const int z = i / (kTileBytes / 16), off = i - z * (kTileBytes / 16);
-    reinterpret_cast<uint4*>(sA + z * kAStride)[off] = make_uint4(0, 0, 0, 0);
+  // zero tile Z at the head of each stage (never overwritten)
+  for (int i = tid; i < 2 * kTileBytes / 16; i += kThreads) {
+    const int st = i / (kTileBytes / 16), off = i - st * (kTileBytes / 16);
+    reinterpret_cast<uint4*>(smem + kSmemStages + st * kStage)[off] = make_uint4(0, 0, 0, 0);
   }
-  if (tid == 0) mbar_init(bar_addr, 1);
+  if (tid == 0) {
+    mbar_init(bar_addr[0], 1);
+    mbar_init(bar_addr[1], 1);
+  }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
                  "r"(kTmemCols));
@@ -117,7 +125,8 @@ __global__ void __launch_bounds__(kThreads, 2)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
-  uint32_t phase = 0;
+  uint32_t ph[2] = {0, 0};
+  bool pending[2] = {false, false};  // a commit on this stage not yet waited for
   bool ok = true;
 
   while (ok) {
@@ -141,73 +150,82 @@ __global__ void __launch_bounds__(kThreads, 2)
     const int N = (ncols + 15) & ~15;
     const uint32_t idesc = make_idesc(128, N);
 
-    // Column exponents.  The three products of W0 share one accumulator, so
-    // they must share units: W0 slices each gradient component against the
-    // largest exponent of the three (per function, per side).
-    for (int k = tid; k < P.n * kTile; k += kThreads) {
-      const int pr = k / kTile, r = k - pr * kTile;
+    // Column exponents (W0: one exponent per function over its three gradient
+    // components, so that its K-concatenated products share units) and D.
+    if (tid < kTile) {
+      const int r = tid;
       int ea = -30000, eb = -30000;
       if (o == 1) {
-        if (i0 + r < nb)
-          ea = max(cexp[1 * nb + i0 + r], max(cexp[2 * nb + i0 + r], cexp[3 * nb + i0 + r]));
-        if (j0 + r < nb)
-          eb = max(cexp[5 * nb + j0 + r], max(cexp[6 * nb + j0 + r], cexp[7 * nb + j0 + r]));
+        if (i0 + r < nb) ea = max(cexp[1 * nb + i0 + r], max(cexp[2 * nb + i0 + r], cexp[3 * nb + i0 + r]));
+        if (j0 + r < nb) eb = max(cexp[5 * nb + j0 + r], max(cexp[6 * nb + j0 + r], cexp[7 * nb + j0 + r]));
       } else {
-        if (i0 + r < nb) ea = cexp[P.qa[pr] * nb + i0 + r];
-        if (j0 + r < nb) eb = cexp[(4 + P.qb[pr]) * nb + j0 + r];
+        if (i0 + r < nb) ea = cexp[P.qa[0] * nb + i0 + r];
+        if (j0 + r < nb) eb = cexp[(4 + P.qb[0]) * nb + j0 + r];
       }
-      sExpA[pr * kTile + r] = ea;
-      sExpB[pr * kTile + r] = eb;
+      sExpA[r] = ea;
+      sExpB[r] = eb;
     }
+    for (int p = tid; p < np; p += kThreads) sD[p] = G.w[p0 + p] * v[p0 + p];
+    __syncthreads();
 
     const int n_chunks = (np + kKc - 1) / kKc;
-    for (int c = 0; c < n_chunks && ok; ++c) {
-      const int kc0 = c * kKc;
-      // the tiles may be overwritten only after the previous chunk's MMAs finished
-      if (c > 0) {
-        ok = __syncthreads_and(mbar_wait(bar_addr, phase & 1, status));
-        ++phase;
-        tc_fence_after();
+    const int n_steps = n_chunks * P.n;
+    for (int s = 0; s < n_steps && ok; ++s) {
+      const int buf = s & 1;
+      if (pending[buf]) {  // the stage is free once the MMAs that read it finished
+        ok = __syncthreads_and(mbar_wait(bar_addr[buf], ph[buf], status));
+        ph[buf] ^= 1;
+        pending[buf] = false;
         if (!ok) break;
       }
-      if (tid < kKc) {
-        const int p = kc0 + tid;
-        sD[tid] = p < np ? G.w[p0 + p] * v[p0 + p] : 0.0;
-      }
-      __syncthreads();
-      // slice: one (row r, point pair kp) unit per lane per step, conflict-free stores
-      for (int pr = 0; pr < P.n; ++pr) {
-        for (int side = 0; side < 2; ++side) {
-          const int q = side == 0 ? P.qa[pr] : P.qb[pr];
-          const int row0 = side == 0 ? i0 : j0;
-          const int* ex = (side == 0 ? sExpA : sExpB) + pr * kTile;
-          unsigned char* dst = side == 0 ? sA + pr * kAStride + kTileBytes : sB + pr * kBStride;
-          for (int u = warp; u < 16; u += kThreads / 32) {
-            const int rg = u >> 1, kq = u & 1;
-            const int r = rg * 8 + (lane >> 2), kp = kq * 4 + (lane & 3);
-            const int f = row0 + r, k = 2 * kp, p = kc0 + k;
-            double x0 = 0.0, x1 = 0.0;
-            if (f < nb) {
-              const double* src = base + q * plane + static_cast<int64_t>(f) * ldp + p;
-              if (p < np) x0 = src[0];
-              if (p + 1 < np) x1 = src[1];
-            }
-            if (side == 0) {
-              x0 *= sD[k];
-              x1 *= sD[k + 1];
-            }
-            const int e = ex[r];
-            int d0[kSlices], d1[kSlices];
-            digits6(x0, e, d0);
-            digits6(x1, e, d1);
-            const int off = rg * kSBO + kq * kLBO + (lane >> 2) * 16 + (lane & 3) * 4;
+      const int c = s / P.n, pr = s - c * P.n;
+      const int kc0 = c * kKc;
+      unsigned char* sA = smem + kSmemStages + buf * kStage;
+      unsigned char* sB = sA + kStageA;
+      // all global loads of the step first (eight units per thread: four per
+      // side), then the integer splitting and the shared-memory stores
+      double xs[2][4][2];
 #pragma unroll
-            for (int s = 0; s < kSlices; ++s) {
-              const float sc = pow2f(e - 6 - 8 * s);
-              __nv_bfloat162 h = __floats2bfloat162_rn(static_cast<float>(d0[s]) * sc,
-                                                       static_cast<float>(d1[s]) * sc);
-              *reinterpret_cast<__nv_bfloat162*>(dst + s * kTileBytes + off) = h;
-            }
+      for (int side = 0; side < 2; ++side) {
+        const int q = side == 0 ? P.qa[pr] : P.qb[pr];
+        const int row0 = side == 0 ? i0 : j0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int u = warp + 4 * k;
+          const int r = (u >> 1) * 8 + (lane >> 2), p = kc0 + 2 * ((u & 1) * 4 + (lane & 3));
+          const int f = row0 + r;
+          const double* src = base + q * plane + static_cast<int64_t>(f) * ldp + p;
+          xs[side][k][0] = (f < nb && p < np) ? src[0] : 0.0;
+          xs[side][k][1] = (f < nb && p + 1 < np) ? src[1] : 0.0;
+        }
+      }
+#pragma unroll
+      for (int side = 0; side < 2; ++side) {
+        const int* ex = side == 0 ? sExpA : sExpB;
+        unsigned char* dst = side == 0 ? sA + kTileBytes : sB;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int u = warp + 4 * k;
+          const int rg = u >> 1, kq = u & 1;
+          const int r = rg * 8 + (lane >> 2), p = kc0 + 2 * (kq * 4 + (lane & 3));
+          const int e = ex[r];
+          long long N0, N1;
+          if (side == 0) {
+            N0 = p < np ? fixed46_scaled(xs[0][k][0], sD[p], e) : 0;
+            N1 = p + 1 < np ? fixed46_scaled(xs[0][k][1], sD[p + 1], e) : 0;
+          } else {
+            N0 = fixed46(xs[1][k][0], e);
+            N1 = fixed46(xs[1][k][1], e);
+          }
+          int d0[kSlices], d1[kSlices];
+          digits_of(N0, d0);
+          digits_of(N1, d1);
+          const int off = rg * kSBO + kq * kLBO + (lane >> 2) * 16 + (lane & 3) * 4;
+#pragma unroll
+          for (int t = 0; t < kSlices; ++t) {
+            const float sc = pow2f(e - 6 - 8 * t);
+            *reinterpret_cast<__nv_bfloat162*>(dst + t * kTileBytes + off) =
+                __floats2bfloat162_rn(static_cast<float>(d0[t]) * sc, static_cast<float>(d1[t]) * sc);
           }
         }
       }
@@ -215,39 +233,40 @@ __global__ void __launch_bounds__(kThreads, 2)
       __syncthreads();
       if (tid == 0) {
         tc_fence_after();
-        for (int pr = 0; pr < P.n; ++pr) {
-          // tile k of the A sequence [Z, A0, A1, A2, A3, A4, A5] starts at a + k * kTileBytes
-          const uint32_t a = smem_u32(sA + pr * kAStride);
-          const uint32_t bb = smem_u32(sB + pr * kBStride);
-          const bool first = (c == 0 && pr == 0);
-          const uint32_t t0 = tmem, t1 = tmem + kTile, t2 = tmem + 2 * kTile;
-          const uint32_t acc = first ? 0u : 1u;
-          auto A = [&](int k) { return make_desc(a + k * kTileBytes, kSBO); };
-          auto Bt = [&](int t) { return make_desc(bb + t * kTileBytes, kSBO); };
-          mma_bf16(t0, A(1), Bt(0), idesc, acc);  // [A0;A1] x B0 -> L0, L1
-          mma_bf16(t0, A(0), Bt(1), idesc, 1u);   // [Z;A0]  x B1 -> L1
-          mma_bf16(t1, A(3), Bt(0), idesc, acc);  // [A2;A3] x B0 -> L2, L3
-          mma_bf16(t1, A(2), Bt(1), idesc, 1u);   // [A1;A2] x B1
-          mma_bf16(t1, A(1), Bt(2), idesc, 1u);   // [A0;A1] x B2
-          mma_bf16(t1, A(0), Bt(3), idesc, 1u);   // [Z;A0]  x B3 -> L3
-          mma_bf16(t2, A(5), Bt(0), idesc, acc);  // [A4;A5] x B0 -> L4, L5
-          mma_bf16(t2, A(4), Bt(1), idesc, 1u);   // [A3;A4] x B1
-          mma_bf16(t2, A(3), Bt(2), idesc, 1u);   // [A2;A3] x B2
-          mma_bf16(t2, A(2), Bt(3), idesc, 1u);   // [A1;A2] x B3
-          mma_bf16(t2, A(1), Bt(4), idesc, 1u);   // [A0;A1] x B4
-          mma_bf16(t2, A(0), Bt(5), idesc, 1u);   // [Z;A0]  x B5 -> L5
-        }
-        mma_commit(bar_addr);
+        const uint32_t a = smem_u32(sA), bb = smem_u32(sB);
+        const uint32_t t0 = tmem, t1 = tmem + kTile, t2 = tmem + 2 * kTile;
+        const uint32_t acc = s == 0 ? 0u : 1u;
+        auto A = [&](int k) { return make_desc(a + k * kTileBytes, kSBO); };
+        auto Bt = [&](int t) { return make_desc(bb + t * kTileBytes, kSBO); };
+        mma_bf16(t0, A(1), Bt(0), idesc, acc);  // [A0;A1] x B0 -> L0, L1
+        mma_bf16(t0, A(0), Bt(1), idesc, 1u);   // [Z;A0]  x B1 -> L1
+        mma_bf16(t1, A(3), Bt(0), idesc, acc);  // [A2;A3] x B0 -> L2, L3
+        mma_bf16(t1, A(2), Bt(1), idesc, 1u);   // [A1;A2] x B1
+        mma_bf16(t1, A(1), Bt(2), idesc, 1u);   // [A0;A1] x B2
+        mma_bf16(t1, A(0), Bt(3), idesc, 1u);   // [Z;A0]  x B3 -> L3
+        mma_bf16(t2, A(5), Bt(0), idesc, acc);  // [A4;A5] x B0 -> L4, L5
+        mma_bf16(t2, A(4), Bt(1), idesc, 1u);   // [A3;A4] x B1
+        mma_bf16(t2, A(3), Bt(2), idesc, 1u);   // [A2;A3] x B2
+        mma_bf16(t2, A(2), Bt(3), idesc, 1u);   // [A1;A2] x B3
+        mma_bf16(t2, A(1), Bt(4), idesc, 1u);   // [A0;A1] x B4
+        mma_bf16(t2, A(0), Bt(5), idesc, 1u);   // [Z;A0]  x B5 -> L5
+        mma_commit(bar_addr[buf]);
       }
-      __syncthreads();
+      pending[buf] = true;
     }
     if (!ok) break;
-    ok = __syncthreads_and(mbar_wait(bar_addr, phase & 1, status));
-    ++phase;
+    // drain the outstanding commits (oldest first) before reading TMEM
+    for (int d = 0; d < 2 && ok; ++d) {
+      const int buf = (n_steps + d) & 1;
+      if (!pending[buf]) continue;
+      ok = __syncthreads_and(mbar_wait(bar_addr[buf], ph[buf], status));
+      ph[buf] ^= 1;
+      pending[buf] = false;
+    }
     tc_fence_after();
     if (!ok) break;
 
-    // epilogue: combine [L0;L1] and [L2;L2'] per element, scatter into FP64
+    // epilogue: combine the six levels per element, scatter into FP64
     const int64_t f0 = G.bat_fn_ptr[b];
     const int a0 = G.bat_atom_ptr[b], na = G.bat_atom_ptr[b + 1] - a0;
     const int64_t pp = G.bat_pair_ptr[b];
@@ -272,15 +291,15 @@ __global__ void __launch_bounds__(kThreads, 2)
         const float* bot = stage + ((r + 64) * 16 + col) * 3;
         const float L0 = top[0], L1 = bot[0], L2 = top[1], L3 = bot[1], L4 = top[2], L5 = bot[2];
         // exact levels by two-sums, rounded tail on top
-        float s = L0 + L1;
-        float bp = s - L0;
-        const float e1 = (L0 - (s - bp)) + (L1 - bp);
-        const float s1 = s;
-        s = s1 + L2;
-        bp = s - s1;
-        const float e2 = (s1 - (s - bp)) + (L2 - bp);
+        float sm = L0 + L1;
+        float bp = sm - L0;
+        const float e1 = (L0 - (sm - bp)) + (L1 - bp);
+        const float s1 = sm;
+        sm = s1 + L2;
+        bp = sm - s1;
+        const float e2 = (s1 - (sm - bp)) + (L2 - bp);
         const float lo = (e1 + e2) + (L3 + (L4 + L5));
-        const double val = static_cast<double>(s) + static_cast<double>(lo);
+        const double val = static_cast<double>(sm) + static_cast<double>(lo);
         int ri = i, rj = j;
         double sgn = 1.0;
         if (o <= 1) {
@@ -301,7 +320,10 @@ __global__ void __launch_bounds__(kThreads, 2)
     __syncthreads();
   }
   // on an expired wait give in-flight MMAs one more bounded chance before freeing TMEM
-  if (!ok) (void)__syncthreads_and(mbar_wait(bar_addr, phase & 1, status));
+  if (!ok) {
+    for (int d = 0; d < 2; ++d)
+      if (pending[d]) (void)__syncthreads_and(mbar_wait(bar_addr[d], ph[d], status));
+  }
   tc_fence_before();
   __syncthreads();
   if (warp == 0)
@@ -312,7 +334,7 @@ __global__ void __launch_bounds__(kThreads, 2)
 
 q4c_status integrate_split(const q4c_tables* t, const q4c_grid* g, const double* v, const q4c_matrices* out,
                            cudaStream_t s) {
-  if (g->max_np > 341) {
+  if (g->max_np > 341) {  // exactness bound of the level sums (and the D buffer)
     set_error("q4c_integrate: the split path needs batches of at most 341 points");
     return Q4C_EUNSUPPORTED;
   }

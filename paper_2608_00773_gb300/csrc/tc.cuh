@@ -100,29 +100,59 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
 }
 
 // ------------------------------------------------------------ slicing
-// x = sum_s d_s 2^(e - 6 - 8 s) + O(2^(e-47)), digits from the integer
-// N = round(x 2^(46 - e)) by balanced base-256 extraction (|d_0| <= 64).
-__device__ __forceinline__ void digits6(double x, int e, int d[kSlices]) {
-#pragma unroll
-  for (int s = 0; s < kSlices; ++s) d[s] = 0;
+// The split of x (FP64) against a column exponent e (|x| <= 2^e):
+//   N = round(x 2^(46 - e)),  |N| <= 2^46,
+//   x = sum_s d_s 2^(e - 6 - 8 s) + O(2^(e - 47)),  s = 0..5,
+// with balanced digits |d_0| <= 64, |d_s| <= 128 (each exact in BF16).
+
+// N for x itself
+__device__ __forceinline__ long long fixed46(double x, int e) {
   const long long bits = __double_as_longlong(x);
   const int E = static_cast<int>((bits >> 52) & 0x7FF);
-  if (E == 0 || e < -1000) return;  // zero (or below the FP64 normal range)
-  const long long M = (bits & 0xFFFFFFFFFFFFFLL) | (1LL << 52);
+  if (E == 0 || e < -1000) return 0;  // zero (or below the FP64 normal range)
+  const unsigned long long M = (bits & 0xFFFFFFFFFFFFFULL) | (1ULL << 52);
   const int sh = 1075 + e - 46 - E;  // >= 6 because |x| <= 2^e
-  if (sh >= 62) return;
-  long long N = (M + (1LL << (sh - 1))) >> sh;
-  if (bits < 0) N = -N;
-  long long r = N;
-#pragma unroll
-  for (int s = 0; s < kSlices - 1; ++s) {
-    const int w = 8 * (kSlices - 1 - s);  // 40, 32, 24, 16, 8
-    const long long q = (r + (1LL << (w - 1))) >> w;
-    r -= q << w;
-    d[s] = static_cast<int>(q);
-  }
-  d[kSlices - 1] = static_cast<int>(r);
+  if (sh >= 62) return 0;
+  const long long N = static_cast<long long>(((M >> (sh - 1)) + 1) >> 1);
+  return bits < 0 ? -N : N;
 }
+
+// N for the product x D, from the 106-bit product of the two mantissas
+// (no FP64 multiply: the high 64 bits come from an integer multiply-high)
+__device__ __forceinline__ long long fixed46_scaled(double x, double D, int e) {
+  const long long bx = __double_as_longlong(x), bd = __double_as_longlong(D);
+  const int Ex = static_cast<int>((bx >> 52) & 0x7FF), Ed = static_cast<int>((bd >> 52) & 0x7FF);
+  if (Ex == 0 || Ed == 0 || e < -1000) return 0;
+  const unsigned long long Mx = (bx & 0xFFFFFFFFFFFFFULL) | (1ULL << 52);
+  const unsigned long long Md = (bd & 0xFFFFFFFFFFFFFULL) | (1ULL << 52);
+  const unsigned long long hi = __umul64hi(Mx << 11, Md << 11);  // floor(Mx Md / 2^42)
+  const int sh = 2062 + e - Ex - Ed;  // >= 17 because |x D| <= 2^e
+  if (sh >= 64) return 0;
+  const long long N = static_cast<long long>(((hi >> (sh - 1)) + 1) >> 1);
+  return (bx ^ bd) < 0 ? -N : N;
+}
+
+// six balanced base-256 digits of N (32-bit arithmetic after one split)
+__device__ __forceinline__ void digits_of(long long N, int d[kSlices]) {
+  const long long hi64 = (N + (1LL << 23)) >> 24;
+  const int lo = static_cast<int>(N - (hi64 << 24));  // [-2^23, 2^23)
+  const int h = static_cast<int>(hi64);               // [-2^22, 2^22]
+  int q = (h + (1 << 15)) >> 16;
+  int r = h - (q << 16);
+  d[0] = q;
+  q = (r + 128) >> 8;
+  d[1] = q;
+  d[2] = r - (q << 8);
+  q = (lo + (1 << 15)) >> 16;
+  r = lo - (q << 16);
+  d[3] = q;
+  q = (r + 128) >> 8;
+  d[4] = q;
+  d[5] = r - (q << 8);
+}
+
+// digits of x against exponent e (reference form used by the density/adjoint)
+__device__ __forceinline__ void digits6(double x, int e, int d[kSlices]) { digits_of(fixed46(x, e), d); }
 
 __device__ __forceinline__ float pow2f(int k) {  // 2^k as float, 0 below the normal range
   return (k < -126) ? 0.0f : __int_as_float((k + 127) << 23);
