@@ -140,6 +140,8 @@ DevGrid q4c_grid::view() const {
   v.fn_info = d_fn_info;
   v.bat_pair_ptr = d_bat_pair_ptr;
   v.pair_off = d_pair_off;
+  v.bat_idx_ptr = d_bat_idx_ptr;
+  v.bat_idx = d_bat_idx;
   v.n_atoms = n_atoms;
   return v;
 }
@@ -411,6 +413,14 @@ extern "C" q4c_status grid_partition(const q4c_grid_desc* d, const q4c_tables* t
     g->flops_alg += 14.0 * np * static_cast<double>(nb) * nb;
     g->sum_np_nb += static_cast<double>(np) * nb;
   }
+  // per-batch dense table of pattern offsets: idx[i * n_b + j] = value offset
+  // of element (i, j) (local functions) or -1 outside the pattern
+  std::vector<int64_t> idx_ptr(nB + 1, 0);
+  for (int64_t b = 0; b < nB; ++b) {
+    const int64_t nb = g->h_bat_fn_ptr[b + 1] - g->h_bat_fn_ptr[b];
+    idx_ptr[b + 1] = idx_ptr[b] + nb * nb;
+  }
+  std::vector<int> bat_idx(idx_ptr[nB]);
   std::vector<int> bat_atom_fn0(g->h_bat_atom_ptr[nB]);
   g->h_bat_atoms.resize(g->h_bat_atom_ptr[nB]);
   std::vector<int> fn_info(g->h_bat_fn_ptr[nB]);
@@ -428,7 +438,23 @@ extern "C" q4c_status grid_partition(const q4c_grid_desc* d, const q4c_tables* t
         pair_off[pair_ptr[b] + static_cast<int64_t>(a) * na + c] = q < 0 ? -1 : g->h_blk_off[q];
       }
     }
+    const int nb = f;
+    for (int i = 0; i < nb; ++i) {
+      const int ii = fn_info[g->h_bat_fn_ptr[b] + i];
+      for (int j = 0; j < nb; ++j) {
+        const int jj = fn_info[g->h_bat_fn_ptr[b] + j];
+        const int64_t off = pair_off[pair_ptr[b] + static_cast<int64_t>(ii >> 16) * na + (jj >> 16)];
+        bat_idx[idx_ptr[b] + static_cast<int64_t>(i) * nb + j] =
+            off < 0 ? -1 : static_cast<int>(off + static_cast<int64_t>(ii & 0xffff) *
+                                                       g->h_nf_atom[act[b][jj >> 16]] + (jj & 0xffff));
+      }
+    }
   });
+  if (g->nnz > INT32_MAX) {
+    set_error("grid_partition: more than 2^31 matrix values on the block pattern");
+    delete g;
+    return Q4C_EUNSUPPORTED;
+  }
 
   // ---- FP64 path: waves whose basis tiles fit the scratch cap; 32x32 tiles
   const int64_t cap = scratch_cap_doubles();
@@ -531,7 +557,8 @@ extern "C" q4c_status grid_partition(const q4c_grid_desc* d, const q4c_tables* t
       (st = up(&g->d_blk_off, g->h_blk_off)) || (st = up(&g->d_blk_row, blk_row)) ||
       (st = up(&g->d_blk_col, g->h_blk_col)) || (st = up(&g->d_blk_T, blk_T)) ||
       (st = up(&g->d_scr_off, g->h_scr_off)) || (st = up(&g->d_tiles, tiles)) || (st = up(&g->d_sched, sched)) ||
-      (st = up(&g->d_split_items, sitems)) || (st = up(&g->d_rd_items, rditems))) {
+      (st = up(&g->d_split_items, sitems)) || (st = up(&g->d_rd_items, rditems)) ||
+      (st = up(&g->d_bat_idx_ptr, idx_ptr)) || (st = up(&g->d_bat_idx, bat_idx))) {
     q4c_grid_destroy(g);
     return st;
   }
@@ -561,7 +588,8 @@ extern "C" void q4c_grid_destroy(q4c_grid* g) {
                   g->d_pt_ptr, g->d_bat_atom_ptr, g->d_bat_atoms, g->d_bat_atom_fn0, g->d_bat_fn_ptr,
                   g->d_fn_info, g->d_bat_pair_ptr, g->d_pair_off, g->d_blk_off, g->d_blk_row, g->d_blk_col,
                   g->d_blk_T, g->d_scr_off, g->d_tiles, g->d_scratch, g->d_sched, g->d_counter, g->d_split_ws,
-                  g->d_split_items, g->d_colexp, g->d_status, g->d_rd_items, g->d_rowexp, g->d_gexp};
+                  g->d_split_items, g->d_colexp, g->d_status, g->d_rd_items, g->d_rowexp, g->d_gexp,
+                  g->d_bat_idx_ptr, g->d_bat_idx};
   for (void* p : ptrs) cudaFree(p);
   delete g;
 }

@@ -70,6 +70,8 @@ struct DevGrid {
   const int* fn_info;           // [sum n_b] (local atom << 16) | index within atom
   const int64_t* bat_pair_ptr;  // [n_batches+1] into pair_off (n_a^2 per batch)
   const int64_t* pair_off;      // value offset of block (A_a, A_b) or -1
+  const int64_t* bat_idx_ptr;   // [n_batches+1] into bat_idx (n_b^2 per batch)
+  const int* bat_idx;           // value offset of element (i, j) of the batch, or -1
   int n_atoms;
 };
 
@@ -135,6 +137,8 @@ struct q4c_grid {
   int2* d_rd_items = nullptr;              // (batch, 64-point tile) for density/adjoint
   int* d_rowexp = nullptr;                 // [n_points][4] per-point exponents
   int* d_gexp = nullptr;                   // [5 * sum n_b] per-batch column exponents of G
+  int64_t* d_bat_idx_ptr = nullptr;
+  int* d_bat_idx = nullptr;                // per batch n_b x n_b value offsets (-1 outside)
   unsigned* d_status = nullptr;            // bit 0: a bounded wait expired
   int64_t split_ws_bytes = 0;
   void* d_split_ws = nullptr;

@@ -25,10 +25,11 @@ constexpr int kTile = 64;                    // points per tile (and functions p
 constexpr int kKc = 16;                      // functions i per chunk (one K = 16 MMA step)
 constexpr int kTileBytes = kTile * kKc * 2;  // 2 KB
 constexpr int kSBO = (kKc / 8) * 128;        // 256 B
-constexpr int kThreads = 128;
+constexpr int kThreads = 256;
+constexpr int kUnits = 16 / (kThreads / 32);  // slicing units per side per thread
 constexpr int kSmemA = 0;                                      // two stages of [Z, A0..A5][B0..B5]
 constexpr int kSmemStage = kSmemA + 2 * (2 * kSlices + 1) * kTileBytes;  // epilogue staging (24 KB)
-constexpr int kSmemExpF = kSmemStage + kThreads * 16 * 3 * 4;
+constexpr int kSmemExpF = kSmemStage + 128 * 16 * 3 * 4;
 constexpr int kSmemExpG = kSmemExpF + kTile * 4;
 constexpr int kSmemY = kSmemExpG + kTile * 4;
 constexpr int kSmemBar = kSmemY + kThreads * 8;
@@ -45,20 +46,14 @@ __device__ __forceinline__ int local_nf(const DevBasis& B, const DevGrid& G, int
   return __ldg(B.sp_nfn + G.atom_sp[G.bat_atoms[a0 + a]]);
 }
 
-// G'_ij of the batch (i, j local), gathered from the block pattern
-__device__ __forceinline__ double gather(const DevBasis& B, const DevGrid& G, const double* M, int64_t f0, int a0,
-                                         int na, int64_t pp, int i, int j) {
-  const int ii = G.fn_info[f0 + i], jj = G.fn_info[f0 + j];
-  const int64_t off = G.pair_off[pp + static_cast<int64_t>(ii >> 16) * na + (jj >> 16)];
-  if (off < 0) return 0.0;
-  return M[off + static_cast<int64_t>(ii & 0xffff) * local_nf(B, G, a0, jj >> 16) + (jj & 0xffff)];
-}
-
-__device__ __forceinline__ double gprime(const DevBasis& B, const DevGrid& G, const double* M, int anti,
-                                         int64_t f0, int a0, int na, int64_t pp, int i, int j) {
-  const double g = gather(B, G, M, f0, a0, na, pp, i, j);
+// G'_ij of the batch (i, j local) through the batch's dense offset table
+__device__ __forceinline__ double gprime(const double* M, const int* __restrict__ idx, int nb, int anti, int i,
+                                         int j) {
+  const int o = __ldg(idx + i * nb + j);
+  const double g = o < 0 ? 0.0 : M[o];
   if (!anti) return g;
-  return 0.5 * (g - gather(B, G, M, f0, a0, na, pp, j, i));
+  const int oT = __ldg(idx + j * nb + i);
+  return 0.5 * (g - (oT < 0 ? 0.0 : M[oT]));
 }
 
 __device__ __forceinline__ int binexp(double x) {
@@ -94,15 +89,14 @@ __global__ void k_gexp(DevBasis B, DevGrid G, int64_t b0, int n_mats, int anti_f
   const int64_t b = b0 + blockIdx.x;
   const int nb = static_cast<int>(G.bat_fn_ptr[b + 1] - G.bat_fn_ptr[b]);
   const int64_t f0 = G.bat_fn_ptr[b];
-  const int a0 = G.bat_atom_ptr[b], na = G.bat_atom_ptr[b + 1] - a0;
-  const int64_t pp = G.bat_pair_ptr[b];
+  const int* idx = G.bat_idx + G.bat_idx_ptr[b];
   const double* mats[5] = {M0, M1, M2, M3, M4};
   for (int e = threadIdx.x; e < n_mats * nb; e += blockDim.x) {
     const int m = e / nb, j = e - m * nb;
     int mx = -30000;
     if (mats[m]) {
       for (int i = 0; i < nb; ++i) {
-        const double g = gprime(B, G, mats[m], m >= anti_from, f0, a0, na, pp, i, j);
+        const double g = gprime(mats[m], idx, nb, m >= anti_from, i, j);
         if (g != 0.0) mx = max(mx, binexp(g));
       }
     }
@@ -180,8 +174,7 @@ __global__ void __launch_bounds__(kThreads, 2)
     const int64_t plane = static_cast<int64_t>(nb) * ldp;
     const double* base = scratch + scr_off[b];
     const int64_t f0 = G.bat_fn_ptr[b];
-    const int a0 = G.bat_atom_ptr[b], na = G.bat_atom_ptr[b + 1] - a0;
-    const int64_t pp = G.bat_pair_ptr[b];
+    const int* idx = G.bat_idx + G.bat_idx_ptr[b];
     const int r0 = pt * kTile;  // first point of the tile within the batch
     double y = 0.0;             // partial of point r0 + (tid & 63)
     const int n_ic = (nb + kKc - 1) / kKc;
@@ -211,25 +204,25 @@ __global__ void __launch_bounds__(kThreads, 2)
           unsigned char* sA = smem + kSmemA + buf * kStage;
           unsigned char* sB = sA + kStageA;
           // all loads and gathers of the step first, then the splitting
-          double xs[2][4][2];
+          double xs[2][kUnits][2];
 #pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            const int u = warp + 4 * k;
+          for (int k = 0; k < kUnits; ++k) {
+            const int u = warp + (kThreads / 32) * k;
             const int r = (u >> 1) * 8 + (lane >> 2), i = i0 + 2 * ((u & 1) * 4 + (lane & 3));
             const int p = r0 + r, j = j0 + r;
             const double* src = base + P.qf * plane + static_cast<int64_t>(i) * ldp + p;
             xs[0][k][0] = (p < np && i < nb) ? src[0] : 0.0;
             xs[0][k][1] = (p < np && i + 1 < nb) ? src[ldp] : 0.0;
-            xs[1][k][0] = (j < nb && i < nb) ? gprime(B, G, Gm, P.anti, f0, a0, na, pp, i, j) : 0.0;
-            xs[1][k][1] = (j < nb && i + 1 < nb) ? gprime(B, G, Gm, P.anti, f0, a0, na, pp, i + 1, j) : 0.0;
+            xs[1][k][0] = (j < nb && i < nb) ? gprime(Gm, idx, nb, P.anti, i, j) : 0.0;
+            xs[1][k][1] = (j < nb && i + 1 < nb) ? gprime(Gm, idx, nb, P.anti, i + 1, j) : 0.0;
           }
 #pragma unroll
           for (int side = 0; side < 2; ++side) {
             unsigned char* dst = side == 0 ? sA + kTileBytes : sB;
             const int* ex = side == 0 ? sExpF : sExpG;
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-              const int u = warp + 4 * k;
+            for (int k = 0; k < kUnits; ++k) {
+              const int u = warp + (kThreads / 32) * k;
               const int rg = u >> 1, kq = u & 1;
               const int r = rg * 8 + (lane >> 2);
               const int e = ex[r];
@@ -282,21 +275,23 @@ __global__ void __launch_bounds__(kThreads, 2)
         tc_fence_after();
         if (!ok) break;
         // epilogue: U_rj from the six levels, dotted with R_rj
-        const int r = tid & 63, half = tid >> 6;
+        const int r = tid & 63, part = tid >> 6;
         const int p = r0 + r;
         for (int c0 = 0; c0 < N; c0 += 16) {
-          const uint32_t lane_base = static_cast<uint32_t>(warp * 32) << 16;
+          if (warp < 4) {  // warp w reads TMEM lanes 32w..32w+31
+            const uint32_t lane_base = static_cast<uint32_t>(warp * 32) << 16;
 #pragma unroll
-          for (int blk = 0; blk < 3; ++blk) {
-            float vv[16];
-            tmem_ld16(tmem + lane_base + blk * kTile + c0, vv);
+            for (int blk = 0; blk < 3; ++blk) {
+              float vv[16];
+              tmem_ld16(tmem + lane_base + blk * kTile + c0, vv);
 #pragma unroll
-            for (int i = 0; i < 16; ++i) stage[(tid * 16 + i) * 3 + blk] = vv[i];
+              for (int i = 0; i < 16; ++i) stage[(tid * 16 + i) * 3 + blk] = vv[i];
+            }
           }
           __syncthreads();
           if (p < np) {
-            for (int cc = 0; cc < 8; ++cc) {
-              const int col = half * 8 + cc, j = j0 + c0 + col;
+            for (int cc = 0; cc < 16 / (kThreads / 64); ++cc) {
+              const int col = part * (16 / (kThreads / 64)) + cc, j = j0 + c0 + col;
               if (j >= nb) continue;
               const float* top = stage + (r * 16 + col) * 3;
               const float* bot = stage + ((r + 64) * 16 + col) * 3;
@@ -320,12 +315,13 @@ __global__ void __launch_bounds__(kThreads, 2)
         __syncthreads();
       }
     }
-    // combine the two column halves of each point and write
+    // combine the column parts of each point and write
     sY[tid] = y;
     __syncthreads();
     if (tid < kTile && r0 + tid < np) {
       const int64_t gp = bp0 + r0 + tid;
-      const double val = sY[tid] + sY[tid + 64];
+      double val = 0.0;
+      for (int q = 0; q < kThreads / 64; ++q) val += sY[tid + 64 * q];
       out[gp] = MODE == 0 ? val : G.w[gp] * val;
     }
     __syncthreads();

@@ -47,14 +47,15 @@ constexpr int kTile = 64;                    // functions per tile (rows of one 
 constexpr int kKc = 16;                      // points per step (one K = 16 MMA step)
 constexpr int kTileBytes = kTile * kKc * 2;  // 2 KB
 constexpr int kSBO = (kKc / 8) * 128;        // 256 B between 8-row groups
-constexpr int kThreads = 128;
+constexpr int kThreads = 256;
+constexpr int kUnits = 16 / (kThreads / 32);  // slicing units per side per thread
 constexpr int kMaxProducts = 3;
 constexpr int kStageA = (kSlices + 1) * kTileBytes;  // [Z, A0..A5]
 constexpr int kStageB = kSlices * kTileBytes;        // [B0..B5]
 constexpr int kStage = kStageA + kStageB;            // 26 KB
 constexpr int kSmemStages = 0;                       // two stages (double buffer)
 constexpr int kSmemEpi = kSmemStages + 2 * kStage;   // epilogue staging, 24 KB
-constexpr int kSmemD = kSmemEpi + kThreads * 16 * 3 * 4;
+constexpr int kSmemD = kSmemEpi + 128 * 16 * 3 * 4;
 constexpr int kMaxNp = 344;                          // D values of one batch
 constexpr int kSmemExp = kSmemD + kMaxNp * 8;
 constexpr int kSmemBar = kSmemExp + 2 * kTile * 4;
@@ -184,14 +185,14 @@ __global__ void __launch_bounds__(kThreads, 2)
       unsigned char* sB = sA + kStageA;
       // all global loads of the step first (eight units per thread: four per
       // side), then the integer splitting and the shared-memory stores
-      double xs[2][4][2];
+      double xs[2][kUnits][2];
 #pragma unroll
       for (int side = 0; side < 2; ++side) {
         const int q = side == 0 ? P.qa[pr] : P.qb[pr];
         const int row0 = side == 0 ? i0 : j0;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          const int u = warp + 4 * k;
+        for (int k = 0; k < kUnits; ++k) {
+          const int u = warp + (kThreads / 32) * k;
           const int r = (u >> 1) * 8 + (lane >> 2), p = kc0 + 2 * ((u & 1) * 4 + (lane & 3));
           const int f = row0 + r;
           const double* src = base + q * plane + static_cast<int64_t>(f) * ldp + p;
@@ -204,8 +205,8 @@ __global__ void __launch_bounds__(kThreads, 2)
         const int* ex = side == 0 ? sExpA : sExpB;
         unsigned char* dst = side == 0 ? sA + kTileBytes : sB;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          const int u = warp + 4 * k;
+        for (int k = 0; k < kUnits; ++k) {
+          const int u = warp + (kThreads / 32) * k;
           const int rg = u >> 1, kq = u & 1;
           const int r = rg * 8 + (lane >> 2), p = kc0 + 2 * (kq * 4 + (lane & 3));
           const int e = ex[r];
@@ -272,19 +273,21 @@ __global__ void __launch_bounds__(kThreads, 2)
     const int64_t pp = G.bat_pair_ptr[b];
     double* out = o == 0 ? V : o == 1 ? W0 : o == 2 ? SOx : o == 3 ? SOy : SOz;
     for (int c0 = 0; c0 < N; c0 += 16) {
-      const uint32_t lane_base = static_cast<uint32_t>(warp * 32) << 16;
+      if (warp < 4) {  // warp w reads TMEM lanes 32w..32w+31
+        const uint32_t lane_base = static_cast<uint32_t>(warp * 32) << 16;
 #pragma unroll
-      for (int blk = 0; blk < 3; ++blk) {
-        float vv[16];
-        tmem_ld16(tmem + lane_base + blk * kTile + c0, vv);
+        for (int blk = 0; blk < 3; ++blk) {
+          float vv[16];
+          tmem_ld16(tmem + lane_base + blk * kTile + c0, vv);
 #pragma unroll
-        for (int i = 0; i < 16; ++i) stage[(tid * 16 + i) * 3 + blk] = vv[i];
+          for (int i = 0; i < 16; ++i) stage[(tid * 16 + i) * 3 + blk] = vv[i];
+        }
       }
       __syncthreads();
-      const int r = tid & 63, half = tid >> 6;
+      const int r = tid & 63, part = tid >> 6;
       const int i = i0 + r;
-      for (int cc = 0; cc < 8; ++cc) {
-        const int col = half * 8 + cc;
+      for (int cc = 0; cc < 16 / (kThreads / 64); ++cc) {
+        const int col = part * (16 / (kThreads / 64)) + cc;
         const int j = j0 + c0 + col;
         if (i >= nb || j >= nb) continue;
         const float* top = stage + (r * 16 + col) * 3;
