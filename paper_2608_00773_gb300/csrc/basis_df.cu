@@ -1,0 +1,273 @@
+// Basis tiles for the split-precision path in double-float arithmetic.
+//
+// Same values as k_basis_tiles (phi = g S_lm, grad phi = g' d/r S + g grad S,
+// Eq. 12 and Appendix B), to about 2^-44 relative instead of FP64's 2^-53,
+// computed on the FP32 pipes (GB300's FP64 rate is 1/58 of FP32).  The
+// split path slices every value into 47-bit digits against per-column
+// exponents and reaches ~1e-12 relative error of the matrices with these
+// inputs, far inside its 1e-9 bound.
+//
+// The log-grid coordinate t = ln(r/r_min)/h is split as t = k + s with k from
+// an FP32 logarithm and s = ln(r/r_k)/h from the atanh series
+// ln q = 2 (z + z^3/3 + z^5/5 + ...), z = (q - 1)/(q + 1), |z| < 0.03.
+//
+// One warp handles one active atom and 32 consecutive points of the batch, so
+// the loops over the atom's functions are warp-uniform and the per-function
+// column maxima reduce across the warp before one shared-memory atomic.
+// Outputs (per batch): tiles Phi, X, Y, Z as float2 (hi, lo) in the FP64
+// tile layout [4][n_b][ceil8(n_p)]; column exponents (slots 0..3: upper bounds
+// for the D-scaled values, D = w v; 4..7: the values) and per-point exponents
+// of the four quantities (max over functions).
+#include "df.cuh"
+#include "internal.h"
+
+namespace q4c {
+namespace bdf {
+
+struct cdf {
+  float hi, lo;
+};
+constexpr cdf mk(double c) { return {static_cast<float>(c), static_cast<float>(c - static_cast<double>(static_cast<float>(c)))}; }
+__device__ __forceinline__ df D(cdf c) { return {c.hi, c.lo}; }
+
+constexpr cdf c00 = mk(0.28209479177387814);
+constexpr cdf c1 = mk(0.4886025119029199);
+constexpr cdf c2a = mk(1.0925484305920792);
+constexpr cdf c20 = mk(0.31539156525252005);
+constexpr cdf c22 = mk(0.5462742152960396);
+constexpr cdf c33 = mk(0.5900435899266435);
+constexpr cdf c32a = mk(2.890611442640554);
+constexpr cdf c31 = mk(0.4570457994644658);
+constexpr cdf c30 = mk(0.3731763325901154);
+constexpr cdf c32b = mk(1.445305721320277);
+constexpr cdf two_thirds = mk(2.0 / 3.0);
+
+__device__ __forceinline__ int fexp(float x) {  // |x| < 2^fexp(x) for x != 0
+  return static_cast<int>((__float_as_uint(x) >> 23) & 0xFF) - 126;
+}
+
+__device__ __forceinline__ int dexp(double x) {
+  return static_cast<int>((__double_as_longlong(x) >> 52) & 0x7FF) - 1022;
+}
+
+// S_lm and grad S_lm for l <= lmax (index l*l + m + l), Appendix B signs
+__device__ __forceinline__ void harmonics(df x, df y, df z, int lmax, df* S, df* dS) {
+  const df zero = {0.f, 0.f};
+  S[0] = D(c00);
+  dS[0] = dS[1] = dS[2] = zero;
+  if (lmax < 1) return;
+  const df n1 = df_neg(D(c1));
+  S[1] = df_mul(n1, y); dS[3] = zero; dS[4] = n1; dS[5] = zero;
+  S[2] = df_mul(D(c1), z); dS[6] = zero; dS[7] = zero; dS[8] = D(c1);
+  S[3] = df_mul(n1, x); dS[9] = n1; dS[10] = zero; dS[11] = zero;
+  if (lmax < 2) return;
+  const df xx = df_mul(x, x), yy = df_mul(y, y), zz = df_mul(z, z);
+  const df xy = df_mul(x, y), yz = df_mul(y, z), xz = df_mul(x, z);
+  const df na = df_neg(D(c2a));
+  S[4] = df_mul(D(c2a), xy); dS[12] = df_mul(D(c2a), y); dS[13] = df_mul(D(c2a), x); dS[14] = zero;
+  S[5] = df_mul(na, yz); dS[15] = zero; dS[16] = df_mul(na, z); dS[17] = df_mul(na, y);
+  const df t20 = df_sub(df_mul_f(zz, 2.f), df_add(xx, yy));  // 2 z^2 - x^2 - y^2
+  S[6] = df_mul(D(c20), t20);
+  dS[18] = df_mul_f(df_mul(D(c20), x), -2.f);
+  dS[19] = df_mul_f(df_mul(D(c20), y), -2.f);
+  dS[20] = df_mul_f(df_mul(D(c20), z), 4.f);
+  S[7] = df_mul(na, xz); dS[21] = df_mul(na, z); dS[22] = zero; dS[23] = df_mul(na, x);
+  const df xmy = df_sub(xx, yy);
+  S[8] = df_mul(D(c22), xmy);
+  dS[24] = df_mul_f(df_mul(D(c22), x), 2.f);
+  dS[25] = df_mul_f(df_mul(D(c22), y), -2.f);
+  dS[26] = zero;
+  if (lmax < 3) return;
+  const df n33 = df_neg(D(c33)), n31 = df_neg(D(c31));
+  // m = -3: -c33 y (3x^2 - y^2)
+  const df t3a = df_sub(df_mul_f(xx, 3.f), yy);
+  S[9] = df_mul(n33, df_mul(y, t3a));
+  dS[27] = df_mul_f(df_mul(n33, xy), 6.f);
+  dS[28] = df_mul_f(df_mul(n33, xmy), 3.f);
+  dS[29] = zero;
+  // m = -2: c32a x y z
+  S[10] = df_mul(D(c32a), df_mul(xy, z));
+  dS[30] = df_mul(D(c32a), yz); dS[31] = df_mul(D(c32a), xz); dS[32] = df_mul(D(c32a), xy);
+  // m = -1: -c31 y (4z^2 - x^2 - y^2)
+  const df q4 = df_sub(df_mul_f(zz, 4.f), df_add(xx, yy));
+  S[11] = df_mul(n31, df_mul(y, q4));
+  dS[33] = df_mul_f(df_mul(D(c31), xy), 2.f);
+  dS[34] = df_mul(n31, df_sub(df_sub(df_mul_f(zz, 4.f), xx), df_mul_f(yy, 3.f)));
+  dS[35] = df_mul_f(df_mul(n31, yz), 8.f);
+  // m = 0: c30 z (2z^2 - 3x^2 - 3y^2)
+  const df xy2 = df_add(xx, yy);
+  S[12] = df_mul(D(c30), df_mul(z, df_sub(df_mul_f(zz, 2.f), df_mul_f(xy2, 3.f))));
+  dS[36] = df_mul_f(df_mul(D(c30), xz), -6.f);
+  dS[37] = df_mul_f(df_mul(D(c30), yz), -6.f);
+  dS[38] = df_mul(D(c30), df_sub(df_mul_f(zz, 6.f), df_mul_f(xy2, 3.f)));
+  // m = 1: -c31 x (4z^2 - x^2 - y^2)
+  S[13] = df_mul(n31, df_mul(x, q4));
+  dS[39] = df_mul(n31, df_sub(df_sub(df_mul_f(zz, 4.f), df_mul_f(xx, 3.f)), yy));
+  dS[40] = df_mul_f(df_mul(D(c31), xy), 2.f);
+  dS[41] = df_mul_f(df_mul(n31, xz), 8.f);
+  // m = 2: c32b z (x^2 - y^2)
+  S[14] = df_mul(D(c32b), df_mul(z, xmy));
+  dS[42] = df_mul_f(df_mul(D(c32b), xz), 2.f);
+  dS[43] = df_mul_f(df_mul(D(c32b), yz), -2.f);
+  dS[44] = df_mul(D(c32b), xmy);
+  // m = 3: -c33 x (x^2 - 3y^2)
+  S[15] = df_mul(n33, df_mul(x, df_sub(xx, df_mul_f(yy, 3.f))));
+  dS[45] = df_mul_f(df_mul(n33, xmy), 3.f);
+  dS[46] = df_mul_f(df_mul(D(c33), xy), 6.f);
+  dS[47] = zero;
+}
+
+__global__ void __launch_bounds__(256) k_basis_df(DevBasis B, DevGrid G, DfTables T, int64_t b0,
+                                                  const int64_t* __restrict__ scr_off, float2* __restrict__ scratch,
+                                                  const double* __restrict__ v, int* __restrict__ colexp,
+                                                  int* __restrict__ rowexp) {
+  extern __shared__ int sm[];  // [8][nb] column exponents, then [4][np] point exponents
+  const int64_t b = b0 + blockIdx.x;
+  const int64_t p0 = G.pt_ptr[b];
+  const int np = static_cast<int>(G.pt_ptr[b + 1] - p0);
+  const int ldp = (np + 7) & ~7;
+  const int a0 = G.bat_atom_ptr[b], na = G.bat_atom_ptr[b + 1] - a0;
+  const int nb = static_cast<int>(G.bat_fn_ptr[b + 1] - G.bat_fn_ptr[b]);
+  float2* base = scratch + scr_off[b];
+  const int64_t plane = static_cast<int64_t>(nb) * ldp;
+  int* s_col = sm;
+  int* s_row = sm + 8 * nb;
+  for (int i = threadIdx.x; i < 8 * nb + 4 * np; i += blockDim.x) sm[i] = -30000;
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+  const int n_chunks = (np + 31) / 32;
+  for (int wi = warp; wi < na * n_chunks; wi += nwarps) {
+    const int a = wi / n_chunks, p = (wi - a * n_chunks) * 32 + lane;
+    const bool live = p < np;
+    const int A = G.bat_atoms[a0 + a];
+    const int f0 = G.bat_atom_fn0[a0 + a];
+    const int sp = G.atom_sp[A];
+    const int r0 = __ldg(B.sp_rad0 + sp), nr = __ldg(B.sp_nrad + sp);
+    const int pp = live ? p : 0;
+    const df dx = df_sub(T.pts[3 * (p0 + pp)], T.atoms[3 * A]);
+    const df dy = df_sub(T.pts[3 * (p0 + pp) + 1], T.atoms[3 * A + 1]);
+    const df dz = df_sub(T.pts[3 * (p0 + pp) + 2], T.atoms[3 * A + 2]);
+    const df r2 = df_add(df_add(df_mul(dx, dx), df_mul(dy, dy)), df_mul(dz, dz));
+    const bool in = live && r2.hi < T.rc2;
+    int eD = -30000;
+    if (colexp && live) {
+      const double Dp = G.w[p0 + p] * v[p0 + p];
+      if (Dp != 0.0) eD = dexp(Dp);
+    }
+    int lmax = 0;
+    for (int q = 0; q < nr; ++q) lmax = max(lmax, __ldg(B.rad_l + r0 + q));
+    df S[16], dS[48];
+    harmonics(dx, dy, dz, lmax, S, dS);
+    const bool pos = in && r2.hi > 0.f;  // a point on the nucleus has r = 0 and 1/r taken as 0
+    const df r = pos ? df_sqrt(r2) : df{0.f, 0.f};
+    const df ir = pos ? df_div(df{1.f, 0.f}, r) : df{0.f, 0.f};
+    const df ux = df_mul(dx, ir), uy = df_mul(dy, ir), uz = df_mul(dz, ir);
+    // log-grid interval and local coordinate s (shared by the atom's radials)
+    const bool below = r.hi < T.rmin;
+    int k = 0;
+    df s = {0.f, 0.f};
+    if (in && !below) {
+      const float tf = __logf(r.hi * T.inv_rmin) * T.inv_h;
+      k = min(max(static_cast<int>(tf), 0), B.n_log - 2);
+      const df qv = df_mul(r, T.inv_knot[k]);
+      const df w = df_sub(qv, df{1.f, 0.f});
+      const df zq = df_div(w, df_add(w, df{2.f, 0.f}));
+      const df z2 = df_mul(zq, zq);
+      const float z2f = z2.hi;
+      const float tail = 0.4f + z2f * (0.2857142857f + z2f * 0.2222222222f);  // 2/5 + 2/7 z^2 + 2/9 z^4
+      df ln = df_add(df_mul_f(zq, 2.f), df_mul(df_mul(zq, z2), D(two_thirds)));
+      ln = df_add(ln, df_mul_f(df_mul(zq, z2), z2f * tail));
+      s = df_mul(ln, T.inv_h_df);
+    }
+    int fl = 0;
+    float rmax[4] = {-1.f, -1.f, -1.f, -1.f};  // largest |hi| per quantity over this atom's functions
+    for (int q = 0; q < nr; ++q) {
+      const int rad = r0 + q;
+      const int l = __ldg(B.rad_l + rad);
+      df g = {0.f, 0.f}, gp = {0.f, 0.f};
+      if (in) {
+        if (below) {
+          g = T.g0[rad];
+        } else {
+          const float4* cp = T.coef + (static_cast<int64_t>(rad) * (B.n_log - 1) + k) * 2;
+          const float4 c01 = __ldg(cp), c23 = __ldg(cp + 1);
+          const df C0 = {c01.x, c01.y}, C1 = {c01.z, c01.w}, C2 = {c23.x, c23.y}, C3 = {c23.z, c23.w};
+          const df u = df_add(df_mul(df_add(df_mul(df_add(df_mul(C3, s), C2), s), C1), s), C0);
+          const df du = df_add(df_mul(df_add(df_mul(df_mul_f(C3, 3.f), s), df_mul_f(C2, 2.f)), s), C1);
+          df irl = ir;
+          for (int t = 0; t < l; ++t) irl = df_mul(irl, ir);
+          g = df_mul(u, irl);
+          gp = df_mul(df_mul(df_sub(df_mul(du, T.inv_h_df), df_mul_f(u, static_cast<float>(l + 1))), ir), irl);
+        }
+      }
+      const df gx = df_mul(gp, ux), gy = df_mul(gp, uy), gz = df_mul(gp, uz);
+      for (int m = 0; m < 2 * l + 1; ++m, ++fl) {
+        const int idx = l * l + m;
+        const df ph = df_mul(g, S[idx]);
+        const df vx = df_add(df_mul(gx, S[idx]), df_mul(g, dS[3 * idx]));
+        const df vy = df_add(df_mul(gy, S[idx]), df_mul(g, dS[3 * idx + 1]));
+        const df vz = df_add(df_mul(gz, S[idx]), df_mul(g, dS[3 * idx + 2]));
+        const df vals[4] = {ph, vx, vy, vz};
+        const int f = f0 + fl;
+        if (live) {
+          float2* o = base + static_cast<int64_t>(f) * ldp + p;
+#pragma unroll
+          for (int c = 0; c < 4; ++c) o[c * plane] = make_float2(vals[c].hi, vals[c].lo);
+        }
+#pragma unroll
+        for (int c = 0; c < 4; ++c) rmax[c] = fmaxf(rmax[c], fabsf(vals[c].hi));
+        if (colexp) {
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            const float h = vals[c].hi;
+            const int e = (live && h != 0.f) ? fexp(h) : -30000;
+            const int ea = (e > -30000 && eD > -30000) ? e + eD : -30000;
+            const int mb = __reduce_max_sync(0xffffffffu, e);
+            const int ma = __reduce_max_sync(0xffffffffu, ea);
+            if (lane == 0) {
+              if (mb > -30000) atomicMax(&s_col[(4 + c) * nb + f], mb);
+              if (ma > -30000) atomicMax(&s_col[c * nb + f], ma);
+            }
+          }
+        }
+      }
+    }
+    if (rowexp && live) {
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+        if (rmax[c] > 0.f) atomicMax(&s_row[c * np + p], fexp(rmax[c]));
+    }
+  }
+  __syncthreads();
+  if (colexp) {
+    int* out = colexp + 8 * G.bat_fn_ptr[b];
+    for (int i = threadIdx.x; i < 8 * nb; i += blockDim.x) out[i] = s_col[i];
+  }
+  if (rowexp) {
+    for (int i = threadIdx.x; i < 4 * np; i += blockDim.x) {
+      const int c = i / np, p = i - c * np;
+      rowexp[4 * (p0 + p) + c] = s_row[i];
+    }
+  }
+}
+
+}  // namespace bdf
+
+q4c_status launch_basis_df(const q4c_tables* t, const q4c_grid* g, int64_t b0, int64_t b1, const double* v,
+                           int* colexp, int* rowexp, cudaStream_t s) {
+  const size_t smem = sizeof(int) * (8 * std::max(g->max_nb, 1) + 4 * std::max(g->max_np, 1));
+  if (smem > 48 * 1024)
+    Q4C_CUDA(cudaFuncSetAttribute(bdf::k_basis_df, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  static_cast<int>(smem)));
+  DfTables T = t->df_view();
+  T.pts = g->d_pts_df;
+  T.atoms = g->d_atoms_df;
+  KernelScope ks("basis_df", s);
+  bdf::k_basis_df<<<static_cast<unsigned>(b1 - b0), 256, smem, s>>>(t->view(), g->view(), T, b0, g->d_scr_off,
+                                                                     reinterpret_cast<float2*>(g->d_scratch), v,
+                                                                     colexp, rowexp);
+  Q4C_CUDA(cudaGetLastError());
+  return Q4C_OK;
+}
+
+}  // namespace q4c

@@ -546,8 +546,12 @@ extern "C" q4c_status grid_partition(const q4c_grid_desc* d, const q4c_tables* t
     sy[i] = g->h_xyz[3 * i + 1];
     sz[i] = g->h_xyz[3 * i + 2];
   }
+  auto dsplit = [](double x) { const float h = static_cast<float>(x); return df{h, static_cast<float>(x - h)}; };
+  std::vector<df> pts_df(3 * nP), atoms_df(3 * nA);
+  for (int64_t i = 0; i < 3 * nP; ++i) pts_df[i] = dsplit(g->h_xyz[i]);
+  for (int i = 0; i < 3 * nA; ++i) atoms_df[i] = dsplit(d->xyz[i]);
   q4c_status st;
-  if ((st = up(&g->d_xyz, g->h_xyz)) || (st = up(&g->d_x, sx)) || (st = up(&g->d_y, sy)) ||
+  if ((st = up(&g->d_pts_df, pts_df)) || (st = up(&g->d_atoms_df, atoms_df)) || (st = up(&g->d_xyz, g->h_xyz)) || (st = up(&g->d_x, sx)) || (st = up(&g->d_y, sy)) ||
       (st = up(&g->d_z, sz)) || (st = up(&g->d_w, g->h_w)) || (st = up(&g->d_atom_xyz, g->h_atom_xyz)) ||
       (st = up(&g->d_atom_sp, g->h_atom_sp)) || (st = up(&g->d_atom_fn0, g->h_atom_fn0)) ||
       (st = up(&g->d_pt_ptr, g->h_pt_ptr)) || (st = up(&g->d_bat_atom_ptr, g->h_bat_atom_ptr)) ||
@@ -589,7 +593,7 @@ extern "C" void q4c_grid_destroy(q4c_grid* g) {
                   g->d_fn_info, g->d_bat_pair_ptr, g->d_pair_off, g->d_blk_off, g->d_blk_row, g->d_blk_col,
                   g->d_blk_T, g->d_scr_off, g->d_tiles, g->d_scratch, g->d_sched, g->d_counter, g->d_split_ws,
                   g->d_split_items, g->d_colexp, g->d_status, g->d_rd_items, g->d_rowexp, g->d_gexp,
-                  g->d_bat_idx_ptr, g->d_bat_idx};
+                  g->d_bat_idx_ptr, g->d_bat_idx, g->d_pts_df, g->d_atoms_df};
   for (void* p : ptrs) cudaFree(p);
   delete g;
 }

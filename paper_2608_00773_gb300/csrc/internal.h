@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "../../include/q4c.h"
+#include "df.cuh"
 
 namespace q4c {
 
@@ -57,6 +58,17 @@ struct DevBasis {
   int n_log;
 };
 
+// Double-float views for the split path's basis evaluation.
+struct DfTables {
+  const float4* coef;     // [n_rad_tot][n_log-1][2]: (c0, c1), (c2, c3) as (hi, lo) pairs
+  const df* g0;           // [n_rad_tot]
+  const df* inv_knot;     // [n_log] 1 / r_k
+  const df* pts;          // [n_points][3] kept points (batch order)
+  const df* atoms;        // [n_atoms][3]
+  df inv_h_df;
+  float inv_h, inv_rmin, rmin, rc2;
+};
+
 // Grid, batches and pattern as seen by kernels.
 struct DevGrid {
   const double *x, *y, *z, *w;  // kept points, batch order (SoA)
@@ -91,7 +103,12 @@ struct q4c_tables {
   double* d_g0 = nullptr;
   int *d_rad_l = nullptr, *d_sp_rad0 = nullptr, *d_sp_nrad = nullptr, *d_sp_nfn = nullptr;
   int device = 0;
+  // double-float copies for the split path
+  float4* d_coef_df = nullptr;
+  q4c::df* d_g0_df = nullptr;
+  q4c::df* d_inv_knot_df = nullptr;
   q4c::DevBasis view() const;
+  q4c::DfTables df_view() const;
 };
 
 struct q4c_grid {
@@ -107,6 +124,8 @@ struct q4c_grid {
   std::vector<double> h_atom_xyz;
   // device: points
   double *d_xyz = nullptr, *d_x = nullptr, *d_y = nullptr, *d_z = nullptr, *d_w = nullptr;
+  q4c::df* d_pts_df = nullptr;    // [n_pts][3]
+  q4c::df* d_atoms_df = nullptr;  // [n_atoms][3]
   // device: atoms and batches
   double* d_atom_xyz = nullptr;
   int *d_atom_sp = nullptr, *d_atom_fn0 = nullptr;
@@ -157,6 +176,9 @@ q4c_status basis_eval(const q4c_tables* t, const q4c_grid* g, int64_t n_pts, con
 q4c_status mirror_and_spinor(const q4c_grid* g, const q4c_matrices* out, cudaStream_t s);
 q4c_status launch_basis_tiles(const q4c_tables* t, const q4c_grid* g, int64_t b0, int64_t b1, const double* v,
                               int* colexp, cudaStream_t s);
+// basis_df.cu
+q4c_status launch_basis_df(const q4c_tables* t, const q4c_grid* g, int64_t b0, int64_t b1, const double* v,
+                           int* colexp, int* rowexp, cudaStream_t s);
 // rowdot.cu
 q4c_status density_split(const q4c_tables* t, const q4c_grid* g, const double* P, double* n, cudaStream_t s);
 q4c_status backward_split(const q4c_tables* t, const q4c_grid* g, const q4c_matrices* G, double* dLdv,

@@ -60,27 +60,6 @@ __device__ __forceinline__ int binexp(double x) {
   return static_cast<int>((__double_as_longlong(x) >> 52) & 0x7FF) - 1022;
 }
 
-// per point and quantity: exponent of the largest |value| over the batch's functions
-__global__ void k_rowexp(DevGrid G, int64_t b0, const int64_t* __restrict__ scr_off, const double* __restrict__ scratch,
-                         int* __restrict__ rowexp) {
-  const int64_t b = b0 + blockIdx.x;
-  const int64_t p0 = G.pt_ptr[b];
-  const int np = static_cast<int>(G.pt_ptr[b + 1] - p0);
-  const int ldp = (np + 7) & ~7;
-  const int nb = static_cast<int>(G.bat_fn_ptr[b + 1] - G.bat_fn_ptr[b]);
-  const int64_t plane = static_cast<int64_t>(nb) * ldp;
-  const double* base = scratch + scr_off[b];
-  for (int e = threadIdx.x; e < 4 * np; e += blockDim.x) {
-    const int q = e / np, p = e - q * np;
-    int m = -30000;
-    for (int f = 0; f < nb; ++f) {
-      const double x = base[q * plane + static_cast<int64_t>(f) * ldp + p];
-      if (x != 0.0) m = max(m, binexp(x));
-    }
-    rowexp[4 * (p0 + p) + q] = m;
-  }
-}
-
 // per batch, matrix and local function j: exponent of max_i |G'_ij|
 // (G' the matrix itself, or its antisymmetric part for the SO seeds)
 __global__ void k_gexp(DevBasis B, DevGrid G, int64_t b0, int n_mats, int anti_from, const double* M0,
@@ -172,11 +151,11 @@ __global__ void __launch_bounds__(kThreads, 2)
     const int ldp = (np + 7) & ~7;
     const int nb = static_cast<int>(G.bat_fn_ptr[b + 1] - G.bat_fn_ptr[b]);
     const int64_t plane = static_cast<int64_t>(nb) * ldp;
-    const double* base = scratch + scr_off[b];
+    const float2* base = reinterpret_cast<const float2*>(scratch) + scr_off[b];
     const int64_t f0 = G.bat_fn_ptr[b];
     const int* idx = G.bat_idx + G.bat_idx_ptr[b];
     const int r0 = pt * kTile;  // first point of the tile within the batch
-    double y = 0.0;             // partial of point r0 + (tid & 63)
+    df y = {0.f, 0.f};          // partial of point r0 + (tid & 63)
     const int n_ic = (nb + kKc - 1) / kKc;
 
     for (int j0 = 0; j0 < nb && ok; j0 += kTile) {
@@ -204,17 +183,18 @@ __global__ void __launch_bounds__(kThreads, 2)
           unsigned char* sA = smem + kSmemA + buf * kStage;
           unsigned char* sB = sA + kStageA;
           // all loads and gathers of the step first, then the splitting
-          double xs[2][kUnits][2];
+          float2 xa[kUnits][2];
+          double xs[kUnits][2];
 #pragma unroll
           for (int k = 0; k < kUnits; ++k) {
             const int u = warp + (kThreads / 32) * k;
             const int r = (u >> 1) * 8 + (lane >> 2), i = i0 + 2 * ((u & 1) * 4 + (lane & 3));
             const int p = r0 + r, j = j0 + r;
-            const double* src = base + P.qf * plane + static_cast<int64_t>(i) * ldp + p;
-            xs[0][k][0] = (p < np && i < nb) ? src[0] : 0.0;
-            xs[0][k][1] = (p < np && i + 1 < nb) ? src[ldp] : 0.0;
-            xs[1][k][0] = (j < nb && i < nb) ? gprime(Gm, idx, nb, P.anti, i, j) : 0.0;
-            xs[1][k][1] = (j < nb && i + 1 < nb) ? gprime(Gm, idx, nb, P.anti, i + 1, j) : 0.0;
+            const float2* src = base + P.qf * plane + static_cast<int64_t>(i) * ldp + p;
+            xa[k][0] = (p < np && i < nb) ? src[0] : make_float2(0.f, 0.f);
+            xa[k][1] = (p < np && i + 1 < nb) ? src[ldp] : make_float2(0.f, 0.f);
+            xs[k][0] = (j < nb && i < nb) ? gprime(Gm, idx, nb, P.anti, i, j) : 0.0;
+            xs[k][1] = (j < nb && i + 1 < nb) ? gprime(Gm, idx, nb, P.anti, i + 1, j) : 0.0;
           }
 #pragma unroll
           for (int side = 0; side < 2; ++side) {
@@ -227,8 +207,13 @@ __global__ void __launch_bounds__(kThreads, 2)
               const int r = rg * 8 + (lane >> 2);
               const int e = ex[r];
               int d0[kSlices], d1[kSlices];
-              digits_of(fixed46(xs[side][k][0], e), d0);
-              digits_of(fixed46(xs[side][k][1], e), d1);
+              if (side == 0) {
+                digits_of(fixed46_df(xa[k][0].x, xa[k][0].y, e), d0);
+                digits_of(fixed46_df(xa[k][1].x, xa[k][1].y, e), d1);
+              } else {
+                digits_of(fixed46(xs[k][0], e), d0);
+                digits_of(fixed46(xs[k][1], e), d1);
+              }
               const int off = rg * kSBO + kq * kLBO + (lane >> 2) * 16 + (lane & 3) * 4;
 #pragma unroll
               for (int s = 0; s < kSlices; ++s) {
@@ -304,9 +289,9 @@ __global__ void __launch_bounds__(kThreads, 2)
               bp = sm - s1;
               const float e2 = (s1 - (sm - bp)) + (L2 - bp);
               const float lo = (e1 + e2) + (L3 + (L4 + L5));
-              const double u = static_cast<double>(sm) + static_cast<double>(lo);
-              const double R = base[P.qr * plane + static_cast<int64_t>(j) * ldp + p];
-              y = fma(P.factor * R, u, y);
+              const float2 Rv = base[P.qr * plane + static_cast<int64_t>(j) * ldp + p];
+              const df prod = df_mul(df{Rv.x, Rv.y}, fast_two_sum(sm, lo));
+              y = df_add(y, df_mul_f(prod, static_cast<float>(P.factor)));
             }
           }
           __syncthreads();
@@ -316,7 +301,7 @@ __global__ void __launch_bounds__(kThreads, 2)
       }
     }
     // combine the column parts of each point and write
-    sY[tid] = y;
+    sY[tid] = static_cast<double>(y.hi) + static_cast<double>(y.lo);
     __syncthreads();
     if (tid < kTile && r0 + tid < np) {
       const int64_t gp = bp0 + r0 + tid;
@@ -351,12 +336,7 @@ q4c_status run(const q4c_tables* t, const q4c_grid* g, const double* const mats[
   for (int wv = 0; wv < n_waves; ++wv) {
     const int64_t b0 = g->wave_b0[wv], b1 = g->wave_b0[wv + 1];
     if (b1 <= b0) continue;
-    if (q4c_status st = launch_basis_tiles(t, g, b0, b1, nullptr, nullptr, s)) return st;
-    {
-      KernelScope ks("split_rowexp", s);
-      k_rowexp<<<static_cast<unsigned>(b1 - b0), 128, 0, s>>>(g->view(), b0, g->d_scr_off, g->d_scratch, g->d_rowexp);
-    }
-    Q4C_CUDA(cudaGetLastError());
+    if (q4c_status st = launch_basis_df(t, g, b0, b1, nullptr, nullptr, g->d_rowexp, s)) return st;
     {
       KernelScope ks("split_gexp", s);
       k_gexp<<<static_cast<unsigned>(b1 - b0), 128, 0, s>>>(t->view(), g->view(), b0, MODE == 0 ? 1 : 5,

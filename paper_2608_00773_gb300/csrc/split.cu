@@ -56,7 +56,7 @@ constexpr int kStage = kStageA + kStageB;            // 26 KB
 constexpr int kSmemStages = 0;                       // two stages (double buffer)
 constexpr int kSmemEpi = kSmemStages + 2 * kStage;   // epilogue staging, 24 KB
 constexpr int kSmemD = kSmemEpi + 128 * 16 * 3 * 4;
-constexpr int kMaxNp = 344;                          // D values of one batch
+constexpr int kMaxNp = 344;                          // D values of one batch (double-float)
 constexpr int kSmemExp = kSmemD + kMaxNp * 8;
 constexpr int kSmemBar = kSmemExp + 2 * kTile * 4;
 constexpr int kSmemTotal = kSmemBar + 64;
@@ -97,7 +97,7 @@ __global__ void __launch_bounds__(kThreads, 2)
                      double* SOx, double* SOy, double* SOz, unsigned* status) {
   extern __shared__ __align__(1024) unsigned char smem[];
   float* stage = reinterpret_cast<float*>(smem + kSmemEpi);
-  double* sD = reinterpret_cast<double*>(smem + kSmemD);
+  df* sD = reinterpret_cast<df*>(smem + kSmemD);
   int* sExpA = reinterpret_cast<int*>(smem + kSmemExp);
   int* sExpB = sExpA + kTile;
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + kSmemBar);  // two barriers
@@ -143,7 +143,7 @@ __global__ void __launch_bounds__(kThreads, 2)
     const int ldp = (np + 7) & ~7;
     const int nb = static_cast<int>(G.bat_fn_ptr[b + 1] - G.bat_fn_ptr[b]);
     const int64_t plane = static_cast<int64_t>(nb) * ldp;
-    const double* base = scratch + scr_off[b];
+    const float2* base = reinterpret_cast<const float2*>(scratch) + scr_off[b];
     const int* cexp = colexp + 8 * G.bat_fn_ptr[b];
     const Products P = products_of(o);
     const int i0 = ti * kTile, j0 = tj * kTile;
@@ -166,7 +166,11 @@ __global__ void __launch_bounds__(kThreads, 2)
       sExpA[r] = ea;
       sExpB[r] = eb;
     }
-    for (int p = tid; p < np; p += kThreads) sD[p] = G.w[p0 + p] * v[p0 + p];
+    for (int p = tid; p < np; p += kThreads) {
+      const double Dp = G.w[p0 + p] * v[p0 + p];
+      const float h = static_cast<float>(Dp);
+      sD[p] = df{h, static_cast<float>(Dp - static_cast<double>(h))};
+    }
     __syncthreads();
 
     const int n_chunks = (np + kKc - 1) / kKc;
@@ -185,7 +189,7 @@ __global__ void __launch_bounds__(kThreads, 2)
       unsigned char* sB = sA + kStageA;
       // all global loads of the step first (eight units per thread: four per
       // side), then the integer splitting and the shared-memory stores
-      double xs[2][kUnits][2];
+      float2 xs[2][kUnits][2];
 #pragma unroll
       for (int side = 0; side < 2; ++side) {
         const int q = side == 0 ? P.qa[pr] : P.qb[pr];
@@ -195,9 +199,9 @@ __global__ void __launch_bounds__(kThreads, 2)
           const int u = warp + (kThreads / 32) * k;
           const int r = (u >> 1) * 8 + (lane >> 2), p = kc0 + 2 * ((u & 1) * 4 + (lane & 3));
           const int f = row0 + r;
-          const double* src = base + q * plane + static_cast<int64_t>(f) * ldp + p;
-          xs[side][k][0] = (f < nb && p < np) ? src[0] : 0.0;
-          xs[side][k][1] = (f < nb && p + 1 < np) ? src[1] : 0.0;
+          const float2* src = base + q * plane + static_cast<int64_t>(f) * ldp + p;
+          xs[side][k][0] = (f < nb && p < np) ? src[0] : make_float2(0.f, 0.f);
+          xs[side][k][1] = (f < nb && p + 1 < np) ? src[1] : make_float2(0.f, 0.f);
         }
       }
 #pragma unroll
@@ -211,12 +215,14 @@ __global__ void __launch_bounds__(kThreads, 2)
           const int r = rg * 8 + (lane >> 2), p = kc0 + 2 * (kq * 4 + (lane & 3));
           const int e = ex[r];
           long long N0, N1;
-          if (side == 0) {
-            N0 = p < np ? fixed46_scaled(xs[0][k][0], sD[p], e) : 0;
-            N1 = p + 1 < np ? fixed46_scaled(xs[0][k][1], sD[p + 1], e) : 0;
+          if (side == 0) {  // A side: D-scaled values, the product in double-float
+            const df a0v = p < np ? df_mul(df{xs[0][k][0].x, xs[0][k][0].y}, sD[p]) : df{0.f, 0.f};
+            const df a1v = p + 1 < np ? df_mul(df{xs[0][k][1].x, xs[0][k][1].y}, sD[p + 1]) : df{0.f, 0.f};
+            N0 = fixed46_df(a0v.hi, a0v.lo, e);
+            N1 = fixed46_df(a1v.hi, a1v.lo, e);
           } else {
-            N0 = fixed46(xs[1][k][0], e);
-            N1 = fixed46(xs[1][k][1], e);
+            N0 = fixed46_df(xs[1][k][0].x, xs[1][k][0].y, e);
+            N1 = fixed46_df(xs[1][k][1].x, xs[1][k][1].y, e);
           }
           int d0[kSlices], d1[kSlices];
           digits_of(N0, d0);
@@ -353,7 +359,7 @@ q4c_status integrate_split(const q4c_tables* t, const q4c_grid* g, const double*
   for (int wv = 0; wv < n_waves; ++wv) {
     const int64_t b0 = g->wave_b0[wv], b1 = g->wave_b0[wv + 1];
     if (b1 <= b0) continue;
-    if (q4c_status st = launch_basis_tiles(t, g, b0, b1, v, g->d_colexp, s)) return st;
+    if (q4c_status st = launch_basis_df(t, g, b0, b1, v, g->d_colexp, nullptr, s)) return st;
     const int64_t i0 = g->split_w0[wv], i1 = g->split_w0[wv + 1];
     const int n_items = static_cast<int>(i1 - i0);
     if (n_items == 0) continue;

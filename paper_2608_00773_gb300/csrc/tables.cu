@@ -69,6 +69,20 @@ DevBasis q4c_tables::view() const {
   return b;
 }
 
+DfTables q4c_tables::df_view() const {
+  DfTables d{};
+  d.coef = d_coef_df;
+  d.g0 = d_g0_df;
+  d.inv_knot = d_inv_knot_df;
+  const double ih = 1.0 / h;
+  d.inv_h_df = df{static_cast<float>(ih), static_cast<float>(ih - static_cast<float>(ih))};
+  d.inv_h = static_cast<float>(ih);
+  d.inv_rmin = static_cast<float>(1.0 / r_min);
+  d.rmin = static_cast<float>(r_min);
+  d.rc2 = static_cast<float>(r_c * r_c);
+  return d;
+}
+
 template <typename T>
 static q4c_status upload(T** dst, const std::vector<T>& src) {
   Q4C_CUDA(cudaMalloc(reinterpret_cast<void**>(dst), sizeof(T) * (src.empty() ? 1 : src.size())));
@@ -135,11 +149,25 @@ extern "C" q4c_status nao_tabulate(const q4c_basis_desc* desc, q4c_tables** out)
     natural_spline_coefficients(y, &t->h_coef[static_cast<size_t>(k) * (n - 1) * 4]);
     t->h_g0[k] = y[0] / std::pow(desc->r_min, l + 1);
   }
+  // double-float copies: coefficient pairs, g below r_min, inverse knots
+  auto split = [](double x) { const float h = static_cast<float>(x); return df{h, static_cast<float>(x - h)}; };
+  std::vector<float4> coef_df(static_cast<size_t>(tot) * (n - 1) * 2);
+  for (size_t iv = 0; iv < static_cast<size_t>(tot) * (n - 1); ++iv) {
+    const df c0 = split(t->h_coef[4 * iv]), c1 = split(t->h_coef[4 * iv + 1]), c2 = split(t->h_coef[4 * iv + 2]),
+             c3 = split(t->h_coef[4 * iv + 3]);
+    coef_df[2 * iv] = make_float4(c0.hi, c0.lo, c1.hi, c1.lo);
+    coef_df[2 * iv + 1] = make_float4(c2.hi, c2.lo, c3.hi, c3.lo);
+  }
+  std::vector<df> g0_df(tot), inv_knot(n);
+  for (int k = 0; k < tot; ++k) g0_df[k] = split(t->h_g0[k]);
+  for (int j = 0; j < n; ++j) inv_knot[j] = split(1.0 / (desc->r_min * std::exp(j * t->h)));
   cudaGetDevice(&t->device);
   q4c_status st;
   if ((st = upload(&t->d_coef, t->h_coef)) || (st = upload(&t->d_g0, t->h_g0)) ||
       (st = upload(&t->d_rad_l, t->rad_l)) || (st = upload(&t->d_sp_rad0, t->rad0)) ||
-      (st = upload(&t->d_sp_nrad, t->n_rad)) || (st = upload(&t->d_sp_nfn, t->nfn))) {
+      (st = upload(&t->d_sp_nrad, t->n_rad)) || (st = upload(&t->d_sp_nfn, t->nfn)) ||
+      (st = upload(&t->d_coef_df, coef_df)) || (st = upload(&t->d_g0_df, g0_df)) ||
+      (st = upload(&t->d_inv_knot_df, inv_knot))) {
     q4c_tables_destroy(t);
     return st;
   }
@@ -155,6 +183,9 @@ extern "C" void q4c_tables_destroy(q4c_tables* t) {
   cudaFree(t->d_sp_rad0);
   cudaFree(t->d_sp_nrad);
   cudaFree(t->d_sp_nfn);
+  cudaFree(t->d_coef_df);
+  cudaFree(t->d_g0_df);
+  cudaFree(t->d_inv_knot_df);
   delete t;
 }
 

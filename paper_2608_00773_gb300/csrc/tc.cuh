@@ -132,6 +132,25 @@ __device__ __forceinline__ long long fixed46_scaled(double x, double D, int e) {
   return (bx ^ bd) < 0 ? -N : N;
 }
 
+// round(f 2^(46 - e)) for one FP32 number with |f| < 2^e
+__device__ __forceinline__ long long fixed46_f(float f, int e) {
+  const uint32_t u = __float_as_uint(f);
+  const int E = static_cast<int>((u >> 23) & 0xFF);
+  if (E == 0 || e < -1000) return 0;
+  const uint32_t m = (u & 0x7FFFFFu) | 0x800000u;
+  const int sh = E - 104 - e;  // <= 22 because |f| < 2^e
+  long long N;
+  if (sh >= 0) N = static_cast<long long>(m) << sh;
+  else if (sh > -25) N = static_cast<long long>(((m >> (-sh - 1)) + 1u) >> 1);
+  else N = 0;
+  return (u >> 31) ? -N : N;
+}
+
+// N = round((hi + lo) 2^(46 - e)) within one unit, for a double-float value
+__device__ __forceinline__ long long fixed46_df(float hi, float lo, int e) {
+  return fixed46_f(hi, e) + fixed46_f(lo, e);
+}
+
 // six balanced base-256 digits of N (32-bit arithmetic after one split)
 __device__ __forceinline__ void digits_of(long long N, int d[kSlices]) {
   const long long hi64 = (N + (1LL << 23)) >> 24;
