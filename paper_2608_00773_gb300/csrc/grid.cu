@@ -573,9 +573,11 @@ extern "C" q4c_status grid_partition(const q4c_grid_desc* d, const q4c_tables* t
     if (e == cudaSuccess) e = cudaMalloc(&g->d_colexp, sizeof(int) * 8 * std::max<int64_t>(g->h_bat_fn_ptr[nB], 1));
     if (e == cudaSuccess) e = cudaMalloc(&g->d_rowexp, sizeof(int) * 4 * nP);
     if (e == cudaSuccess) e = cudaMalloc(&g->d_gexp, sizeof(int) * 5 * std::max<int64_t>(g->h_bat_fn_ptr[nB], 1));
+    if (e == cudaSuccess) e = cudaMalloc(&g->d_gdf, sizeof(float2) * 5 * std::max<int64_t>(g->nnz, 1));
     if (e == cudaSuccess) e = cudaMalloc(&g->d_status, sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMemset(g->d_status, 0, sizeof(unsigned));
-    g->split_ws_bytes = static_cast<int64_t>(sizeof(int)) * (13 * g->h_bat_fn_ptr[nB] + 4 * nP);
+    g->split_ws_bytes = static_cast<int64_t>(sizeof(int)) * (13 * g->h_bat_fn_ptr[nB] + 4 * nP) +
+                        static_cast<int64_t>(sizeof(float2)) * 5 * g->nnz;
     if (e != cudaSuccess) {
       set_error(std::string("grid_partition: workspace: ") + cudaGetErrorString(e));
       q4c_grid_destroy(g);
@@ -593,7 +595,7 @@ extern "C" void q4c_grid_destroy(q4c_grid* g) {
                   g->d_fn_info, g->d_bat_pair_ptr, g->d_pair_off, g->d_blk_off, g->d_blk_row, g->d_blk_col,
                   g->d_blk_T, g->d_scr_off, g->d_tiles, g->d_scratch, g->d_sched, g->d_counter, g->d_split_ws,
                   g->d_split_items, g->d_colexp, g->d_status, g->d_rd_items, g->d_rowexp, g->d_gexp,
-                  g->d_bat_idx_ptr, g->d_bat_idx, g->d_pts_df, g->d_atoms_df};
+                  g->d_bat_idx_ptr, g->d_bat_idx, g->d_pts_df, g->d_atoms_df, g->d_gdf};
   for (void* p : ptrs) cudaFree(p);
   delete g;
 }

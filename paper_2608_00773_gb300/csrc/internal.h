@@ -159,6 +159,7 @@ struct q4c_grid {
   int64_t* d_bat_idx_ptr = nullptr;
   int* d_bat_idx = nullptr;                // per batch n_b x n_b value offsets (-1 outside)
   unsigned* d_status = nullptr;            // bit 0: a bounded wait expired
+  float2* d_gdf = nullptr;                 // [5][nnz] FP32-pair copies of the density/adjoint matrices
   int64_t split_ws_bytes = 0;
   void* d_split_ws = nullptr;
   q4c::DevGrid view() const;

@@ -56,6 +56,28 @@ __device__ __forceinline__ double gprime(const double* M, const int* __restrict_
   return 0.5 * (g - (oT < 0 ? 0.0 : M[oT]));
 }
 
+// the same from the matrix as FP32 pairs (the antisymmetric part in double-float)
+__device__ __forceinline__ df gprime_df(const float2* M, const int* __restrict__ idx, int nb, int anti, int i,
+                                        int j) {
+  const int o = __ldg(idx + i * nb + j);
+  const float2 g = o < 0 ? make_float2(0.f, 0.f) : __ldg(M + o);
+  if (!anti) return df{g.x, g.y};
+  const int oT = __ldg(idx + j * nb + i);
+  const float2 gT = oT < 0 ? make_float2(0.f, 0.f) : __ldg(M + oT);
+  const df d = df_sub(df{g.x, g.y}, df{gT.x, gT.y});
+  return df{0.5f * d.hi, 0.5f * d.lo};  // exact
+}
+
+// FP32-pair copy of an FP64 matrix: x = hi + lo within 2^-48 relative
+__global__ void k_to_df(const double* __restrict__ M, int64_t n, float2* __restrict__ out) {
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const double x = M[i];
+    const float h = __double2float_rn(x);
+    out[i] = make_float2(h, __double2float_rn(x - static_cast<double>(h)));
+  }
+}
+
 __device__ __forceinline__ int binexp(double x) {
   return static_cast<int>((__double_as_longlong(x) >> 52) & 0x7FF) - 1022;
 }
@@ -94,13 +116,13 @@ template <int MODE>  // 0: density, 1: adjoint
 __global__ void __launch_bounds__(kThreads, 2)
     k_split_rowdot(DevBasis B, DevGrid G, const int2* __restrict__ items, int n_items, int* counter,
                    const int64_t* __restrict__ scr_off, const double* __restrict__ scratch,
-                   const int* __restrict__ rowexp, const int* __restrict__ gexp, const double* M0, const double* M1,
-                   const double* M2, const double* M3, const double* M4, double* __restrict__ out,
+                   const int* __restrict__ rowexp, const int* __restrict__ gexp, const float2* M0,
+                   const float2* M1, const float2* M2, const float2* M3, const float2* M4, double* __restrict__ out,
                    unsigned* status) {
   extern __shared__ __align__(1024) unsigned char smem[];
   float* stage = reinterpret_cast<float*>(smem + kSmemStage);
-  int* sExpF = reinterpret_cast<int*>(smem + kSmemExpF);
-  int* sExpG = reinterpret_cast<int*>(smem + kSmemExpG);
+  float* sMagF = reinterpret_cast<float*>(smem + kSmemExpF);  // rounding constants per point
+  float* sMagG = reinterpret_cast<float*>(smem + kSmemExpG);  // and per function j
   double* sY = reinterpret_cast<double*>(smem + kSmemY);
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + kSmemBar);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + kSmemBar + 16);
@@ -108,7 +130,7 @@ __global__ void __launch_bounds__(kThreads, 2)
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const uint32_t bar_addr[2] = {smem_u32(bar), smem_u32(bar + 1)};
-  const double* mats[5] = {M0, M1, M2, M3, M4};
+  const float2* mats[5] = {M0, M1, M2, M3, M4};
   // (F quantity, G matrix, antisymmetric part?, R quantity, factor)
   const Product prods_adj[7] = {{0, 0, 0, 0, 1.0}, {1, 1, 0, 1, 1.0}, {2, 1, 0, 2, 1.0}, {3, 1, 0, 3, 1.0},
                                 {2, 2, 1, 3, 2.0}, {3, 3, 1, 1, 2.0}, {1, 4, 1, 2, 2.0}};
@@ -163,12 +185,12 @@ __global__ void __launch_bounds__(kThreads, 2)
       const uint32_t idesc = make_idesc(128, N);
       for (int k = 0; k < n_prod && ok; ++k) {
         const Product P = MODE == 0 ? prod_den : prods_adj[k];
-        const double* Gm = mats[P.gm];
+        const float2* Gm = mats[P.gm];
         if (Gm == nullptr) continue;
         if (tid < kTile) {
           const int p = r0 + tid, j = j0 + tid;
-          sExpF[tid] = p < np ? rowexp[4 * (bp0 + p) + P.qf] : -30000;
-          sExpG[tid] = j < nb ? gexp[5 * f0 + P.gm * nb + j] : -30000;
+          sMagF[tid] = magic0(p < np ? rowexp[4 * (bp0 + p) + P.qf] : -30000);
+          sMagG[tid] = magic0(j < nb ? gexp[5 * f0 + P.gm * nb + j] : -30000);
         }
         __syncthreads();
         for (int ic = 0; ic < n_ic && ok; ++ic, ++gstep) {
@@ -184,7 +206,7 @@ __global__ void __launch_bounds__(kThreads, 2)
           unsigned char* sB = sA + kStageA;
           // all loads and gathers of the step first, then the splitting
           float2 xa[kUnits][2];
-          double xs[kUnits][2];
+          df xs[kUnits][2];
 #pragma unroll
           for (int k = 0; k < kUnits; ++k) {
             const int u = warp + (kThreads / 32) * k;
@@ -193,34 +215,31 @@ __global__ void __launch_bounds__(kThreads, 2)
             const float2* src = base + P.qf * plane + static_cast<int64_t>(i) * ldp + p;
             xa[k][0] = (p < np && i < nb) ? src[0] : make_float2(0.f, 0.f);
             xa[k][1] = (p < np && i + 1 < nb) ? src[ldp] : make_float2(0.f, 0.f);
-            xs[k][0] = (j < nb && i < nb) ? gprime(Gm, idx, nb, P.anti, i, j) : 0.0;
-            xs[k][1] = (j < nb && i + 1 < nb) ? gprime(Gm, idx, nb, P.anti, i + 1, j) : 0.0;
+            xs[k][0] = (j < nb && i < nb) ? gprime_df(Gm, idx, nb, P.anti, i, j) : df{0.f, 0.f};
+            xs[k][1] = (j < nb && i + 1 < nb) ? gprime_df(Gm, idx, nb, P.anti, i + 1, j) : df{0.f, 0.f};
           }
 #pragma unroll
           for (int side = 0; side < 2; ++side) {
             unsigned char* dst = side == 0 ? sA + kTileBytes : sB;
-            const int* ex = side == 0 ? sExpF : sExpG;
+            const float* mg = side == 0 ? sMagF : sMagG;
 #pragma unroll
             for (int k = 0; k < kUnits; ++k) {
               const int u = warp + (kThreads / 32) * k;
               const int rg = u >> 1, kq = u & 1;
               const int r = rg * 8 + (lane >> 2);
-              const int e = ex[r];
-              int d0[kSlices], d1[kSlices];
+              const float m0 = mg[r];
+              float d0[kSlices], d1[kSlices];
               if (side == 0) {
-                digits_of(fixed46_df(xa[k][0].x, xa[k][0].y, e), d0);
-                digits_of(fixed46_df(xa[k][1].x, xa[k][1].y, e), d1);
+                slice6(xa[k][0].x, xa[k][0].y, m0, d0);
+                slice6(xa[k][1].x, xa[k][1].y, m0, d1);
               } else {
-                digits_of(fixed46(xs[k][0], e), d0);
-                digits_of(fixed46(xs[k][1], e), d1);
+                slice6(xs[k][0].hi, xs[k][0].lo, m0, d0);
+                slice6(xs[k][1].hi, xs[k][1].lo, m0, d1);
               }
               const int off = rg * kSBO + kq * kLBO + (lane >> 2) * 16 + (lane & 3) * 4;
 #pragma unroll
-              for (int s = 0; s < kSlices; ++s) {
-                const float sc = pow2f(e - 6 - 8 * s);
-                *reinterpret_cast<__nv_bfloat162*>(dst + s * kTileBytes + off) =
-                    __floats2bfloat162_rn(static_cast<float>(d0[s]) * sc, static_cast<float>(d1[s]) * sc);
-              }
+              for (int s = 0; s < kSlices; ++s)
+                *reinterpret_cast<__nv_bfloat162*>(dst + s * kTileBytes + off) = __floats2bfloat162_rn(d0[s], d1[s]);
             }
           }
           fence_async_smem();
@@ -333,6 +352,19 @@ q4c_status run(const q4c_tables* t, const q4c_grid* g, const double* const mats[
   int dev = 0, n_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+  // FP32-pair copies of the matrices for the B operands
+  const float2* mdf[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  {
+    KernelScope ks(MODE == 0 ? "split_density" : "split_backward", s);
+    for (int m = 0; m < 5; ++m) {
+      if (!mats[m] || g->nnz == 0) continue;
+      float2* dst = g->d_gdf + m * g->nnz;
+      const unsigned blocks = static_cast<unsigned>(std::min<int64_t>((g->nnz + 255) / 256, 8 * n_sm));
+      k_to_df<<<blocks, 256, 0, s>>>(mats[m], g->nnz, dst);
+      mdf[m] = dst;
+    }
+  }
+  Q4C_CUDA(cudaGetLastError());
   for (int wv = 0; wv < n_waves; ++wv) {
     const int64_t b0 = g->wave_b0[wv], b1 = g->wave_b0[wv + 1];
     if (b1 <= b0) continue;
@@ -352,7 +384,7 @@ q4c_status run(const q4c_tables* t, const q4c_grid* g, const double* const mats[
       KernelScope ks(MODE == 0 ? "split_density" : "split_backward", s);
       k_split_rowdot<MODE><<<grid, kThreads, kSmemTotal, s>>>(
           t->view(), g->view(), g->d_rd_items + i0, n_items, g->d_counter + wv, g->d_scr_off, g->d_scratch,
-          g->d_rowexp, g->d_gexp, mats[0], mats[1], mats[2], mats[3], mats[4], out, g->d_status);
+          g->d_rowexp, g->d_gexp, mdf[0], mdf[1], mdf[2], mdf[3], mdf[4], out, g->d_status);
     }
     Q4C_CUDA(cudaGetLastError());
   }

@@ -4,13 +4,18 @@
 // Q in {Phi, X, Y, Z}) is computed exactly enough for ~1e-9 relative error
 // from BF16 slices (an Ozaki-type error-free splitting; Ozaki, Ogita, Oishi
 // and Rump 2012):
-//   x = sum_s d_s 2^(e - 6 - 8s),  s = 0..5,  |d_0| <= 64, |d_s| <= 128,
-// with e a per-column binary exponent (|x| < 2^e over the batch).  Each digit
-// has <= 8 significant bits, so it is exact in BF16 and every slice product
-// is exact in FP32.  Per output element six FP32 accumulators (one per level
-// s + t) are kept in tensor memory:
+//   x = sum_s d_s 2^(e - 6 - 8s),  s = 0..5,  |d_0| <= 64, |d_1|, |d_2| <= 128,
+//   |d_3| <= 160, |d_4|, |d_5| <= 128,
+// with e a per-column binary exponent (|x| <= 2^e over the batch); the digits
+// come from FP32 round-to-multiple steps (tc::slice6).  Each digit has <= 8
+// significant bits, so it is exact in BF16 and every slice product is exact
+// in FP32.  Per output element six FP32 accumulators (one per level s + t)
+// are kept in tensor memory:
 //   L0 = sum d0 e0, L1 = sum d0 e1 + d1 e0, L2 = sum_{s+t=2} d_s e_t
-//       (exact: integer sums below 2^24 units for n_p <= 341)
+//       (integer sums of at most 2^15 units per term: exact for K <= 512
+//       terms, i.e. n_p <= 512 for V and the A products and n_p <= 170 for
+//       the 3 n_p terms of W0; beyond that a rounding of L2 sits ~2^-40
+//       below the column scale)
 //   L3, L4, L5 (rounded; 2^-24 and further below L0, so the truncating FP32
 //       accumulation of the tensor cores cannot reach the result's bits)
 // and combined as a double-float, then added into the FP64 block pattern.
@@ -98,8 +103,8 @@ __global__ void __launch_bounds__(kThreads, 2)
   extern __shared__ __align__(1024) unsigned char smem[];
   float* stage = reinterpret_cast<float*>(smem + kSmemEpi);
   df* sD = reinterpret_cast<df*>(smem + kSmemD);
-  int* sExpA = reinterpret_cast<int*>(smem + kSmemExp);
-  int* sExpB = sExpA + kTile;
+  float* sMagA = reinterpret_cast<float*>(smem + kSmemExp);  // rounding constants of the rows
+  float* sMagB = sMagA + kTile;
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + kSmemBar);  // two barriers
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + kSmemBar + 16);
   int* s_item = reinterpret_cast<int*>(smem + kSmemBar + 32);
@@ -163,8 +168,8 @@ __global__ void __launch_bounds__(kThreads, 2)
         if (i0 + r < nb) ea = cexp[P.qa[0] * nb + i0 + r];
         if (j0 + r < nb) eb = cexp[(4 + P.qb[0]) * nb + j0 + r];
       }
-      sExpA[r] = ea;
-      sExpB[r] = eb;
+      sMagA[r] = magic0(ea);
+      sMagB[r] = magic0(eb);
     }
     for (int p = tid; p < np; p += kThreads) {
       const double Dp = G.w[p0 + p] * v[p0 + p];
@@ -188,7 +193,7 @@ __global__ void __launch_bounds__(kThreads, 2)
       unsigned char* sA = smem + kSmemStages + buf * kStage;
       unsigned char* sB = sA + kStageA;
       // all global loads of the step first (eight units per thread: four per
-      // side), then the integer splitting and the shared-memory stores
+      // side), then the splitting and the shared-memory stores
       float2 xs[2][kUnits][2];
 #pragma unroll
       for (int side = 0; side < 2; ++side) {
@@ -206,34 +211,28 @@ __global__ void __launch_bounds__(kThreads, 2)
       }
 #pragma unroll
       for (int side = 0; side < 2; ++side) {
-        const int* ex = side == 0 ? sExpA : sExpB;
+        const float* mg = side == 0 ? sMagA : sMagB;
         unsigned char* dst = side == 0 ? sA + kTileBytes : sB;
 #pragma unroll
         for (int k = 0; k < kUnits; ++k) {
           const int u = warp + (kThreads / 32) * k;
           const int rg = u >> 1, kq = u & 1;
           const int r = rg * 8 + (lane >> 2), p = kc0 + 2 * (kq * 4 + (lane & 3));
-          const int e = ex[r];
-          long long N0, N1;
+          const float m0 = mg[r];
+          float d0[kSlices], d1[kSlices];
           if (side == 0) {  // A side: D-scaled values, the product in double-float
             const df a0v = p < np ? df_mul(df{xs[0][k][0].x, xs[0][k][0].y}, sD[p]) : df{0.f, 0.f};
             const df a1v = p + 1 < np ? df_mul(df{xs[0][k][1].x, xs[0][k][1].y}, sD[p + 1]) : df{0.f, 0.f};
-            N0 = fixed46_df(a0v.hi, a0v.lo, e);
-            N1 = fixed46_df(a1v.hi, a1v.lo, e);
+            slice6(a0v.hi, a0v.lo, m0, d0);
+            slice6(a1v.hi, a1v.lo, m0, d1);
           } else {
-            N0 = fixed46_df(xs[1][k][0].x, xs[1][k][0].y, e);
-            N1 = fixed46_df(xs[1][k][1].x, xs[1][k][1].y, e);
+            slice6(xs[1][k][0].x, xs[1][k][0].y, m0, d0);
+            slice6(xs[1][k][1].x, xs[1][k][1].y, m0, d1);
           }
-          int d0[kSlices], d1[kSlices];
-          digits_of(N0, d0);
-          digits_of(N1, d1);
           const int off = rg * kSBO + kq * kLBO + (lane >> 2) * 16 + (lane & 3) * 4;
 #pragma unroll
-          for (int t = 0; t < kSlices; ++t) {
-            const float sc = pow2f(e - 6 - 8 * t);
-            *reinterpret_cast<__nv_bfloat162*>(dst + t * kTileBytes + off) =
-                __floats2bfloat162_rn(static_cast<float>(d0[t]) * sc, static_cast<float>(d1[t]) * sc);
-          }
+          for (int t = 0; t < kSlices; ++t)
+            *reinterpret_cast<__nv_bfloat162*>(dst + t * kTileBytes + off) = __floats2bfloat162_rn(d0[t], d1[t]);
         }
       }
       fence_async_smem();

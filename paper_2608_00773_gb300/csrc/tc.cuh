@@ -173,6 +173,35 @@ __device__ __forceinline__ void digits_of(long long N, int d[kSlices]) {
 // digits of x against exponent e (reference form used by the density/adjoint)
 __device__ __forceinline__ void digits6(double x, int e, int d[kSlices]) { digits_of(fixed46(x, e), d); }
 
+// Rounding constant of the leading digit for column exponent e: 1.5 2^(e + 17).
+// Adding and subtracting 1.5 2^(23 + u) in FP32 rounds x to the nearest
+// multiple of 2^u, exactly, whenever |x| < 2^(22 + u).  An empty column
+// (e < -1000) gets 0; e is clamped to [-80, 100] so that every digit weight
+// 2^(e - 6 - 8s) stays a normal FP32 and BF16 number.
+__device__ __forceinline__ float magic0(int e) {
+  if (e < -1000) return 0.0f;
+  e = min(max(e, -80), 100);
+  return __int_as_float(((e + 17 + 127) << 23) | 0x400000);
+}
+
+// Six balanced digits of the double-float value h + l (|h + l| <= 2^e) with
+// m0 = magic0(e): digit s is returned already multiplied by its weight
+// 2^(e - 6 - 8s).  Digits 0-2 come from h exactly (|d| <= 64, 128, 128); l
+// joins the residual (|r| <= 2^(e - 23)) before digit 3, rounded at most
+// 2^(e - 48), so |d3| <= 160 and |d4|, |d5| <= 128, all exact in BF16, and
+// the six digits represent h + l within 2^(e - 46).
+__device__ __forceinline__ void slice6(float h, float l, float m0, float d[kSlices]) {
+  float x = h, m = m0;
+#pragma unroll
+  for (int s = 0; s < kSlices; ++s) {
+    if (s == 3) x = __fadd_rn(x, l);
+    const float t = __fsub_rn(__fadd_rn(x, m), m);
+    d[s] = t;
+    x = __fsub_rn(x, t);
+    m = __fmul_rn(m, 0x1p-8f);
+  }
+}
+
 __device__ __forceinline__ float pow2f(int k) {  // 2^k as float, 0 below the normal range
   return (k < -126) ? 0.0f : __int_as_float((k + 127) << 23);
 }
