@@ -526,6 +526,19 @@ extern "C" q4c_status grid_partition(const q4c_grid_desc* d, const q4c_tables* t
     }
     g->rd_w0.push_back(static_cast<int64_t>(rditems.size()));
   }
+  // G' digit blocks of the density/adjoint, per wave: per batch five matrices
+  // x ceil(nb/64) j-tiles x ceil(nb/16) i-chunks x 12 KB
+  std::vector<int64_t> gsl_off(nB, 0);
+  g->gsl_bytes = 0;
+  for (size_t wv = 0; wv + 1 < g->wave_b0.size(); ++wv) {
+    int64_t used = 0;
+    for (int64_t b = g->wave_b0[wv]; b < g->wave_b0[wv + 1]; ++b) {
+      const int64_t nb = g->h_bat_fn_ptr[b + 1] - g->h_bat_fn_ptr[b];
+      gsl_off[b] = used;
+      used += 5 * ((nb + 63) / 64) * ((nb + 15) / 16) * 12288;
+    }
+    g->gsl_bytes = std::max(g->gsl_bytes, used);
+  }
 
   // ---- schedule for persistent kernels: descending n_p n_b^2
   std::vector<int> sched(nB);
@@ -562,7 +575,8 @@ extern "C" q4c_status grid_partition(const q4c_grid_desc* d, const q4c_tables* t
       (st = up(&g->d_blk_col, g->h_blk_col)) || (st = up(&g->d_blk_T, blk_T)) ||
       (st = up(&g->d_scr_off, g->h_scr_off)) || (st = up(&g->d_tiles, tiles)) || (st = up(&g->d_sched, sched)) ||
       (st = up(&g->d_split_items, sitems)) || (st = up(&g->d_rd_items, rditems)) ||
-      (st = up(&g->d_bat_idx_ptr, idx_ptr)) || (st = up(&g->d_bat_idx, bat_idx))) {
+      (st = up(&g->d_bat_idx_ptr, idx_ptr)) || (st = up(&g->d_bat_idx, bat_idx)) ||
+      (st = up(&g->d_gsl_off, gsl_off))) {
     q4c_grid_destroy(g);
     return st;
   }
@@ -572,12 +586,12 @@ extern "C" q4c_status grid_partition(const q4c_grid_desc* d, const q4c_tables* t
     if (e == cudaSuccess) e = cudaMalloc(&g->d_counter, sizeof(int) * std::max<size_t>(n_waves, 1));
     if (e == cudaSuccess) e = cudaMalloc(&g->d_colexp, sizeof(int) * 8 * std::max<int64_t>(g->h_bat_fn_ptr[nB], 1));
     if (e == cudaSuccess) e = cudaMalloc(&g->d_rowexp, sizeof(int) * 4 * nP);
-    if (e == cudaSuccess) e = cudaMalloc(&g->d_gexp, sizeof(int) * 5 * std::max<int64_t>(g->h_bat_fn_ptr[nB], 1));
+    if (e == cudaSuccess) e = cudaMalloc(&g->d_gsl, static_cast<size_t>(std::max<int64_t>(g->gsl_bytes, 16)));
     if (e == cudaSuccess) e = cudaMalloc(&g->d_gdf, sizeof(float2) * 5 * std::max<int64_t>(g->nnz, 1));
     if (e == cudaSuccess) e = cudaMalloc(&g->d_status, sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMemset(g->d_status, 0, sizeof(unsigned));
-    g->split_ws_bytes = static_cast<int64_t>(sizeof(int)) * (13 * g->h_bat_fn_ptr[nB] + 4 * nP) +
-                        static_cast<int64_t>(sizeof(float2)) * 5 * g->nnz;
+    g->split_ws_bytes = static_cast<int64_t>(sizeof(int)) * (8 * g->h_bat_fn_ptr[nB] + 4 * nP) +
+                        static_cast<int64_t>(sizeof(float2)) * 5 * g->nnz + g->gsl_bytes;
     if (e != cudaSuccess) {
       set_error(std::string("grid_partition: workspace: ") + cudaGetErrorString(e));
       q4c_grid_destroy(g);
@@ -594,7 +608,7 @@ extern "C" void q4c_grid_destroy(q4c_grid* g) {
                   g->d_pt_ptr, g->d_bat_atom_ptr, g->d_bat_atoms, g->d_bat_atom_fn0, g->d_bat_fn_ptr,
                   g->d_fn_info, g->d_bat_pair_ptr, g->d_pair_off, g->d_blk_off, g->d_blk_row, g->d_blk_col,
                   g->d_blk_T, g->d_scr_off, g->d_tiles, g->d_scratch, g->d_sched, g->d_counter, g->d_split_ws,
-                  g->d_split_items, g->d_colexp, g->d_status, g->d_rd_items, g->d_rowexp, g->d_gexp,
+                  g->d_split_items, g->d_colexp, g->d_status, g->d_rd_items, g->d_rowexp, g->d_gsl, g->d_gsl_off,
                   g->d_bat_idx_ptr, g->d_bat_idx, g->d_pts_df, g->d_atoms_df, g->d_gdf};
   for (void* p : ptrs) cudaFree(p);
   delete g;

@@ -155,7 +155,9 @@ struct q4c_grid {
   std::vector<int64_t> rd_w0;              // [n_waves+1] ranges into d_rd_items
   int2* d_rd_items = nullptr;              // (batch, 64-point tile) for density/adjoint
   int* d_rowexp = nullptr;                 // [n_points][4] per-point exponents
-  int* d_gexp = nullptr;                   // [5 * sum n_b] per-batch column exponents of G
+  unsigned char* d_gsl = nullptr;          // G' digit blocks of one wave (density/adjoint)
+  int64_t* d_gsl_off = nullptr;            // [n_batches] byte offsets into d_gsl (per wave)
+  int64_t gsl_bytes = 0;
   int64_t* d_bat_idx_ptr = nullptr;
   int* d_bat_idx = nullptr;                // per batch n_b x n_b value offsets (-1 outside)
   unsigned* d_status = nullptr;            // bit 0: a bounded wait expired

@@ -14,6 +14,11 @@
 // G' (per-column exponents) with the same tile sequence and exact-level
 // accumulation as the integration (see split.cu): levels 0-2 are exact
 // integer sums (K = n_b <= 512), levels 3-5 are rounded 2^-24 below.
+//
+// G' does not depend on the points, so a pre-pass slices every batch's G'
+// once into BF16 digit tiles laid out exactly as the MMA reads them (per
+// matrix, 64-function j-tile and 16-function i-chunk: six 2 KB tiles); the
+// main kernel fetches one 12 KB block per K-step with a bulk copy.
 #include "internal.h"
 #include "tc.cuh"
 
@@ -21,51 +26,54 @@ namespace q4c {
 namespace rowdot {
 using namespace tc;
 
-constexpr int kTile = 64;                    // points per tile (and functions per j-tile)
-constexpr int kKc = 16;                      // functions i per chunk (one K = 16 MMA step)
-constexpr int kTileBytes = kTile * kKc * 2;  // 2 KB
-constexpr int kSBO = (kKc / 8) * 128;        // 256 B
-constexpr int kThreads = 256;
-constexpr int kUnits = 16 / (kThreads / 32);  // slicing units per side per thread
-constexpr int kSmemA = 0;                                      // two stages of [Z, A0..A5][B0..B5]
-constexpr int kSmemStage = kSmemA + 2 * (2 * kSlices + 1) * kTileBytes;  // epilogue staging (24 KB)
-constexpr int kSmemExpF = kSmemStage + 128 * 16 * 3 * 4;
-constexpr int kSmemExpG = kSmemExpF + kTile * 4;
-constexpr int kSmemY = kSmemExpG + kTile * 4;
-constexpr int kSmemBar = kSmemY + kThreads * 8;
-constexpr int kSmemTotal = kSmemBar + 64;
-constexpr uint32_t kTmemCols = 256;
+constexpr int kTile = 64;                      // points per tile (and functions per j-tile)
+constexpr int kKc = 16;                        // functions i per chunk (one K = 16 MMA step)
+constexpr int kTileBytes = kTile * kKc * 2;    // 2 KB
+constexpr int kSBO = (kKc / 8) * 128;          // 256 B
+constexpr int kBlockB = kSlices * kTileBytes;  // one step's G' digits, 12 KB
+constexpr int kSlicers = 256;                  // warps 0-7 slice F
+constexpr int kEpiWarp0 = 8;                   // warps 8-15 drain tensor memory (two groups of four)
+constexpr int kEpiThreads = 256;
+constexpr int kMmaWarp = 16;  // warp 16 owns tensor memory and issues the MMAs
+constexpr int kThreads = 17 * 32;
+constexpr int kUnits = 16 / (kSlicers / 32);         // slicing units per thread (A side only)
+constexpr int kStageA = (kSlices + 1) * kTileBytes;  // [Z, A0..A5]
+constexpr int kStage = kStageA + kBlockB;            // 26 KB
+constexpr int kStages = 4;
+constexpr int kRaw = 4;                               // ring of raw F values (cp.async)
+constexpr int kRawStage = kSlicers * kUnits * 2 * 8;  // 8 KB
+constexpr int kEpiPitch = 17;
+constexpr int kEpiStage = 3 * 128 * kEpiPitch * 4;  // 26 KB per epilogue group
+constexpr int kSmemStages = 0;
+constexpr int kSmemRaw = kSmemStages + kStages * kStage;
+constexpr int kSmemEpi = kSmemRaw + kRaw * kRawStage;
+constexpr int kSmemMag = kSmemEpi + 2 * kEpiStage;  // [4][64] rounding constants per point
+constexpr int kSmemY = kSmemMag + 4 * kTile * 4;    // [4][64] double partials per point
+constexpr int kSmemBar = kSmemY + 4 * kTile * 8;
+constexpr int kNumBars = 2 * kStages + 5;  // full[S], empty[S], accfull[2], accempty[2], drain
+constexpr int kSmemTotal = kSmemBar + kNumBars * 8 + 16;
+constexpr uint32_t kTmemCols = 512;
+constexpr uint32_t kSetCols = 256;
 constexpr int kMaxNb = 512;
 
 struct Product {
-  int qf, gm, anti, qr;
-  double factor;
+  int qf, gm, qr;
+  float factor;
 };
 
-__device__ __forceinline__ int local_nf(const DevBasis& B, const DevGrid& G, int a0, int a) {
-  return __ldg(B.sp_nfn + G.atom_sp[G.bat_atoms[a0 + a]]);
-}
-
-// G'_ij of the batch (i, j local) through the batch's dense offset table
-__device__ __forceinline__ double gprime(const double* M, const int* __restrict__ idx, int nb, int anti, int i,
-                                         int j) {
-  const int o = __ldg(idx + i * nb + j);
-  const double g = o < 0 ? 0.0 : M[o];
-  if (!anti) return g;
-  const int oT = __ldg(idx + j * nb + i);
-  return 0.5 * (g - (oT < 0 ? 0.0 : M[oT]));
-}
-
-// the same from the matrix as FP32 pairs (the antisymmetric part in double-float)
-__device__ __forceinline__ df gprime_df(const float2* M, const int* __restrict__ idx, int nb, int anti, int i,
-                                        int j) {
-  const int o = __ldg(idx + i * nb + j);
-  const float2 g = o < 0 ? make_float2(0.f, 0.f) : __ldg(M + o);
-  if (!anti) return df{g.x, g.y};
-  const int oT = __ldg(idx + j * nb + i);
-  const float2 gT = oT < 0 ? make_float2(0.f, 0.f) : __ldg(M + oT);
-  const df d = df_sub(df{g.x, g.y}, df{gT.x, gT.y});
-  return df{0.5f * d.hi, 0.5f * d.lo};  // exact
+// (F quantity, G matrix, R quantity, factor); matrices 2-4 enter through their
+// antisymmetric parts, which the pre-pass slices
+__device__ __forceinline__ Product product_of(int mode, int k) {
+  if (mode == 0) return {0, 0, 0, 1.0f};
+  switch (k) {
+    case 0: return {0, 0, 0, 1.0f};
+    case 1: return {1, 1, 1, 1.0f};
+    case 2: return {2, 1, 2, 1.0f};
+    case 3: return {3, 1, 3, 1.0f};
+    case 4: return {2, 2, 3, 2.0f};
+    case 5: return {3, 3, 1, 2.0f};
+    default: return {1, 4, 2, 2.0f};
+  }
 }
 
 // FP32-pair copy of an FP64 matrix: x = hi + lo within 2^-48 relative
@@ -78,74 +86,172 @@ __global__ void k_to_df(const double* __restrict__ M, int64_t n, float2* __restr
   }
 }
 
-__device__ __forceinline__ int binexp(double x) {
-  return static_cast<int>((__double_as_longlong(x) >> 52) & 0x7FF) - 1022;
+// G'_ij of the batch (i, j local) from the FP32-pair matrix through the
+// batch's dense offset table (the antisymmetric part in double-float)
+__device__ __forceinline__ df gprime_df(const float2* M, const int* __restrict__ idx, int nb, int anti, int i,
+                                        int j) {
+  const int o = __ldg(idx + i * nb + j);
+  const float2 g = o < 0 ? make_float2(0.f, 0.f) : __ldg(M + o);
+  if (!anti) return df{g.x, g.y};
+  const int oT = __ldg(idx + j * nb + i);
+  const float2 gT = oT < 0 ? make_float2(0.f, 0.f) : __ldg(M + oT);
+  const df d = df_sub(df{g.x, g.y}, df{gT.x, gT.y});
+  return df{0.5f * d.hi, 0.5f * d.lo};  // exact
 }
 
-// per batch, matrix and local function j: exponent of max_i |G'_ij|
-// (G' the matrix itself, or its antisymmetric part for the SO seeds)
-__global__ void k_gexp(DevBasis B, DevGrid G, int64_t b0, int n_mats, int anti_from, const double* M0,
-                       const double* M1, const double* M2, const double* M3, const double* M4,
-                       int* __restrict__ gexp) {
+__device__ __forceinline__ int fexp(float x) {  // |x| < 2^fexp(x) for x != 0
+  return static_cast<int>((__float_as_uint(x) >> 23) & 0xFF) - 126;
+}
+
+// Pre-pass: one CTA per (batch, matrix).  Column exponents e_j (|G'_ij| <=
+// 2^e_j over i), then the six digits of every G'_ij written as the B operand
+// tiles of the main kernel: block (jt, ic) = six 2 KB tiles of 64 rows (j) x
+// 16 K (i) in the no-swizzle K-major layout; padding rows and columns are 0.
+__global__ void __launch_bounds__(256) k_gslice(DevGrid G, int64_t b0, int anti_from, const float2* M0,
+                                                const float2* M1, const float2* M2, const float2* M3,
+                                                const float2* M4, const int64_t* __restrict__ gsl_off,
+                                                uint32_t* __restrict__ gsl) {
+  __shared__ float sMag[kMaxNb];
   const int64_t b = b0 + blockIdx.x;
+  const int m = blockIdx.y;
+  const float2* mats[5] = {M0, M1, M2, M3, M4};
+  const float2* M = mats[m];
+  if (M == nullptr) return;
+  const int anti = m >= anti_from;
   const int nb = static_cast<int>(G.bat_fn_ptr[b + 1] - G.bat_fn_ptr[b]);
-  const int64_t f0 = G.bat_fn_ptr[b];
   const int* idx = G.bat_idx + G.bat_idx_ptr[b];
-  const double* mats[5] = {M0, M1, M2, M3, M4};
-  for (int e = threadIdx.x; e < n_mats * nb; e += blockDim.x) {
-    const int m = e / nb, j = e - m * nb;
-    int mx = -30000;
-    if (mats[m]) {
-      for (int i = 0; i < nb; ++i) {
-        const double g = gprime(mats[m], idx, nb, m >= anti_from, i, j);
-        if (g != 0.0) mx = max(mx, binexp(g));
-      }
+  const int n_jt = (nb + kTile - 1) / kTile, n_ic = (nb + kKc - 1) / kKc;
+  uint32_t* out = gsl + (gsl_off[b] + static_cast<int64_t>(m) * n_jt * n_ic * kBlockB) / 4;
+  for (int j = threadIdx.x; j < nb; j += blockDim.x) {
+    float mx = 0.f;
+    for (int i = 0; i < nb; ++i) mx = fmaxf(mx, fabsf(gprime_df(M, idx, nb, anti, i, j).hi));
+    sMag[j] = magic0(mx > 0.f ? fexp(mx) : -30000);
+  }
+  __syncthreads();
+  const int words = n_jt * n_ic * (kTileBytes / 4);  // word positions (one per element pair)
+  for (int w = threadIdx.x; w < words; w += blockDim.x) {
+    const int blk = w / (kTileBytes / 4), pos = w - blk * (kTileBytes / 4);
+    const int jt = blk / n_ic, ic = blk - jt * n_ic;
+    // pos -> byte offset rg*SBO + kq*LBO + r8*16 + kp*4
+    const int rg = pos >> 6, kq = (pos >> 5) & 1, r8 = (pos >> 2) & 7, kp = pos & 3;
+    const int j = jt * kTile + rg * 8 + r8, i = ic * kKc + kq * 8 + kp * 2;
+    float d0[kSlices], d1[kSlices];
+    if (j < nb) {
+      const float m0 = sMag[j];
+      const df x0 = i < nb ? gprime_df(M, idx, nb, anti, i, j) : df{0.f, 0.f};
+      const df x1 = i + 1 < nb ? gprime_df(M, idx, nb, anti, i + 1, j) : df{0.f, 0.f};
+      slice6(x0.hi, x0.lo, m0, d0);
+      slice6(x1.hi, x1.lo, m0, d1);
+    } else {
+#pragma unroll
+      for (int s = 0; s < kSlices; ++s) d0[s] = d1[s] = 0.f;
     }
-    gexp[5 * f0 + m * nb + j] = mx;
+    uint32_t* o = out + static_cast<int64_t>(blk) * (kBlockB / 4) + pos;
+#pragma unroll
+    for (int s = 0; s < kSlices; ++s) {
+      const __nv_bfloat162 h2 = __floats2bfloat162_rn(d0[s], d1[s]);
+      o[s * (kTileBytes / 4)] = *reinterpret_cast<const uint32_t*>(&h2);
+    }
   }
 }
 
-constexpr int kStageA = (kSlices + 1) * kTileBytes;  // [Z, A0..A5]
-constexpr int kStage = kStageA + kSlices * kTileBytes;
+__device__ __forceinline__ void expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
 
-// One work item = (batch, 64-point tile).  For every j-tile and product the K
-// dimension (functions i) is a stream of 16-wide steps that alternate between
-// two shared-memory stages: the threads slice step s + 1 while the tensor core
-// runs the twelve MMAs of step s.
+__device__ __forceinline__ void bulk_copy(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+      "l"(src), "r"(bytes), "r"(bar)
+      : "memory");
+}
+
+// 8-byte asynchronous copy (zero-filled past src_bytes)
+__device__ __forceinline__ void cp_async8(uint32_t dst, const void* src, int src_bytes) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+}
+
+// the work of one item (batch, 64-point tile): groups (j-tile, product) in
+// order, each a K-loop of n_ic steps over the functions i
+struct ItemInfo {
+  int64_t b, bp0;
+  int pt, np, ldp, nb, n_jt, n_ic;
+  int64_t plane;
+};
+
+__device__ __forceinline__ ItemInfo item_info(const DevGrid& G, int2 it) {
+  ItemInfo I;
+  I.b = it.x;
+  I.pt = it.y;
+  I.bp0 = G.pt_ptr[I.b];
+  I.np = static_cast<int>(G.pt_ptr[I.b + 1] - I.bp0);
+  I.ldp = (I.np + 7) & ~7;
+  I.nb = static_cast<int>(G.bat_fn_ptr[I.b + 1] - G.bat_fn_ptr[I.b]);
+  I.n_jt = (I.nb + kTile - 1) / kTile;
+  I.n_ic = (I.nb + kKc - 1) / kKc;
+  I.plane = static_cast<int64_t>(I.nb) * I.ldp;
+  return I;
+}
+
+// One work item = (batch, 64-point tile); its groups (j-tile, product) run
+// in order, each a K-loop over the functions i.  Warp roles as in the
+// integration kernel:
+//   warps 0-7   per step: wait empty[stage]; one thread starts the bulk copy
+//               of the step's G' digits into the stage (expect_tx on
+//               full[stage]); all slice the 64 x 16 block of F (raw values
+//               by cp.async three steps ahead) and arrive on full[stage];
+//   warp 16     (one thread) issues the twelve MMAs per step into the group's
+//               accumulator set (groups alternate between two sets), commits
+//               empty[stage] and, after the group's last step, accfull[set];
+//   warps 8-15  combine the six levels of U, dot each column with R (a point
+//               per thread, double-float), keep a running sum per point over
+//               the item's groups and write the point's result at the end.
+// Every wait is bounded; a timeout sets the status bit and an abort flag.
 template <int MODE>  // 0: density, 1: adjoint
-__global__ void __launch_bounds__(kThreads, 2)
-    k_split_rowdot(DevBasis B, DevGrid G, const int2* __restrict__ items, int n_items, int* counter,
+__global__ void __launch_bounds__(kThreads, 1)
+    k_split_rowdot(DevBasis B, DevGrid G, const int2* __restrict__ items, int n_items,
                    const int64_t* __restrict__ scr_off, const double* __restrict__ scratch,
-                   const int* __restrict__ rowexp, const int* __restrict__ gexp, const float2* M0,
-                   const float2* M1, const float2* M2, const float2* M3, const float2* M4, double* __restrict__ out,
+                   const int* __restrict__ rowexp, const int64_t* __restrict__ gsl_off,
+                   const unsigned char* __restrict__ gsl, unsigned present, double* __restrict__ out,
                    unsigned* status) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  float* stage = reinterpret_cast<float*>(smem + kSmemStage);
-  float* sMagF = reinterpret_cast<float*>(smem + kSmemExpF);  // rounding constants per point
-  float* sMagG = reinterpret_cast<float*>(smem + kSmemExpG);  // and per function j
-  double* sY = reinterpret_cast<double*>(smem + kSmemY);
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + kSmemBar);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + kSmemBar + 16);
-  int* s_item = reinterpret_cast<int*>(smem + kSmemBar + 32);
+  float* sMag = reinterpret_cast<float*>(smem + kSmemMag);  // [quantity][point]
+  double* sY = reinterpret_cast<double*>(smem + kSmemY);    // [part][point]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kSmemBar);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + kSmemBar + kNumBars * 8);
+  volatile int* s_abort = reinterpret_cast<volatile int*>(smem + kSmemBar + kNumBars * 8 + 4);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const uint32_t bar_addr[2] = {smem_u32(bar), smem_u32(bar + 1)};
-  const float2* mats[5] = {M0, M1, M2, M3, M4};
-  // (F quantity, G matrix, antisymmetric part?, R quantity, factor)
-  const Product prods_adj[7] = {{0, 0, 0, 0, 1.0}, {1, 1, 0, 1, 1.0}, {2, 1, 0, 2, 1.0}, {3, 1, 0, 3, 1.0},
-                                {2, 2, 1, 3, 2.0}, {3, 3, 1, 1, 2.0}, {1, 4, 1, 2, 2.0}};
-  const Product prod_den = {0, 0, 0, 0, 1.0};
-  const int n_prod = MODE == 0 ? 1 : 7;
+  const uint32_t bar0 = smem_u32(bars);
+  auto full_bar = [&](int st) { return bar0 + 8u * st; };
+  auto empty_bar = [&](int st) { return bar0 + 8u * (kStages + st); };
+  auto accfull_bar = [&](int set) { return bar0 + 8u * (2 * kStages + set); };
+  auto accempty_bar = [&](int set) { return bar0 + 8u * (2 * kStages + 2 + set); };
+  const uint32_t drain_bar = bar0 + 8u * (2 * kStages + 4);
+  // products whose matrix is present, in order
+  const int n_prod_all = MODE == 0 ? 1 : 7;
+  int prods[7];
+  int n_prod = 0;
+  for (int k = 0; k < n_prod_all; ++k)
+    if (present & (1u << product_of(MODE, k).gm)) prods[n_prod++] = k;
 
-  for (int i = tid; i < 2 * kTileBytes / 16; i += kThreads) {  // tile Z of both stages
+  for (int i = tid; i < kStages * kTileBytes / 16; i += kThreads) {  // tile Z of every stage
     const int st = i / (kTileBytes / 16), off = i - st * (kTileBytes / 16);
-    reinterpret_cast<uint4*>(smem + kSmemA + st * kStage)[off] = make_uint4(0, 0, 0, 0);
+    reinterpret_cast<uint4*>(smem + kSmemStages + st * kStage)[off] = make_uint4(0, 0, 0, 0);
   }
   if (tid == 0) {
-    mbar_init(bar_addr[0], 1);
-    mbar_init(bar_addr[1], 1);
+    for (int st = 0; st < kStages; ++st) {
+      mbar_init(full_bar(st), kSlicers);
+      mbar_init(empty_bar(st), 1);
+    }
+    for (int set = 0; set < 2; ++set) {
+      mbar_init(accfull_bar(set), 1);
+      mbar_init(accempty_bar(set), kEpiThreads);
+    }
+    mbar_init(drain_bar, 1);
+    *s_abort = 0;
   }
-  if (warp == 0) {
+  if (warp == kMmaWarp) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
                  "r"(kTmemCols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
@@ -155,99 +261,115 @@ __global__ void __launch_bounds__(kThreads, 2)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
-  uint32_t ph[2] = {0, 0};
-  bool pending[2] = {false, false};  // a commit on this stage not yet waited for
-  int gstep = 0;                     // steps issued by this CTA (stage = gstep & 1)
-  bool ok = true;
 
-  while (ok) {
-    if (tid == 0) *s_item = atomicAdd(counter, 1);
-    __syncthreads();
-    const int it = *s_item;
-    if (it >= n_items) break;
-    const int2 item = items[it];
-    const int64_t b = item.x;
-    const int pt = item.y;
-    const int64_t bp0 = G.pt_ptr[b];
-    const int np = static_cast<int>(G.pt_ptr[b + 1] - bp0);
-    const int ldp = (np + 7) & ~7;
-    const int nb = static_cast<int>(G.bat_fn_ptr[b + 1] - G.bat_fn_ptr[b]);
-    const int64_t plane = static_cast<int64_t>(nb) * ldp;
-    const float2* base = reinterpret_cast<const float2*>(scratch) + scr_off[b];
-    const int64_t f0 = G.bat_fn_ptr[b];
-    const int* idx = G.bat_idx + G.bat_idx_ptr[b];
-    const int r0 = pt * kTile;  // first point of the tile within the batch
-    df y = {0.f, 0.f};          // partial of point r0 + (tid & 63)
-    const int n_ic = (nb + kKc - 1) / kKc;
-
-    for (int j0 = 0; j0 < nb && ok; j0 += kTile) {
-      const int N = (min(kTile, nb - j0) + 15) & ~15;
-      const uint32_t idesc = make_idesc(128, N);
-      for (int k = 0; k < n_prod && ok; ++k) {
-        const Product P = MODE == 0 ? prod_den : prods_adj[k];
-        const float2* Gm = mats[P.gm];
-        if (Gm == nullptr) continue;
-        if (tid < kTile) {
-          const int p = r0 + tid, j = j0 + tid;
-          sMagF[tid] = magic0(p < np ? rowexp[4 * (bp0 + p) + P.qf] : -30000);
-          sMagG[tid] = magic0(j < nb ? gexp[5 * f0 + P.gm * nb + j] : -30000);
+  if (warp < kSlicers / 32) {
+    // ---------------------------------------------------------- slicers
+    bool ok = true;
+    int g = 0;  // steps of this CTA
+    const uint32_t raw0 = smem_u32(smem + kSmemRaw);
+    for (int n = blockIdx.x;; n += gridDim.x) {
+      if (bar_red_or(1, kSlicers, !ok || *s_abort) || n >= n_items) break;
+      const ItemInfo I = item_info(G, items[n]);
+      const float2* base = reinterpret_cast<const float2*>(scratch) + scr_off[I.b];
+      const int r0 = I.pt * kTile;
+      for (int e = tid; e < 4 * kTile; e += kSlicers) {  // per quantity and point
+        const int q = e >> 6, r = e & 63, p = r0 + r;
+        sMag[e] = magic0(p < I.np ? rowexp[4 * (I.bp0 + p) + q] : -30000);
+      }
+      bar_sync(1, kSlicers);
+      const unsigned char* gblk = gsl + gsl_off[I.b];
+      const int n_steps = I.n_jt * n_prod * I.n_ic;  // step s -> group s / n_ic, chunk s mod n_ic
+      auto issue = [&](int s, uint32_t raw) {
+        const int grp = s / I.n_ic, ic = s - grp * I.n_ic;
+        const Product P = product_of(MODE, prods[grp % n_prod]);
+        const int i0 = ic * kKc;
+#pragma unroll
+        for (int k = 0; k < kUnits; ++k) {
+          const int u = warp + (kSlicers / 32) * k;
+          const int r = (u >> 1) * 8 + (lane >> 2), i = i0 + 2 * ((u & 1) * 4 + (lane & 3));
+          const int p = r0 + r;
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const bool live = p < I.np && i + h < I.nb;
+            const float2* src = live ? base + P.qf * I.plane + static_cast<int64_t>(i + h) * I.ldp + p : base;
+            cp_async8(raw + ((k * 2 + h) * kSlicers + tid) * 8, src, live ? 8 : 0);
+          }
         }
-        __syncthreads();
-        for (int ic = 0; ic < n_ic && ok; ++ic, ++gstep) {
-          const int buf = gstep & 1;
-          if (pending[buf]) {  // the stage is free once the MMAs that read it finished
-            ok = __syncthreads_and(mbar_wait(bar_addr[buf], ph[buf], status));
-            ph[buf] ^= 1;
-            pending[buf] = false;
-            if (!ok) break;
+      };
+#pragma unroll
+      for (int q = 0; q < kRaw - 1; ++q) {
+        if (q < n_steps) issue(q, raw0 + q * kRawStage);
+        cp_async_commit();
+      }
+      for (int s = 0; s < n_steps; ++s, ++g) {
+        const int sa = s + kRaw - 1;
+        if (sa < n_steps) issue(sa, raw0 + (sa % kRaw) * kRawStage);
+        cp_async_commit();
+        const int st = g % kStages;
+        if (!mbar_wait_abort(empty_bar(st), ((g / kStages) & 1) ^ 1, s_abort, status)) {
+          ok = false;
+          break;
+        }
+        const int grp = s / I.n_ic, ic = s - grp * I.n_ic;
+        const int jt = grp / n_prod;
+        const Product P = product_of(MODE, prods[grp % n_prod]);
+        unsigned char* sA = smem + kSmemStages + st * kStage;
+        if (tid == 0) {  // this step's G' digits: one 12 KB block
+          const unsigned char* src =
+              gblk + (static_cast<int64_t>(P.gm) * I.n_jt * I.n_ic + static_cast<int64_t>(jt) * I.n_ic + ic) *
+                         kBlockB;
+          expect_tx(full_bar(st), kBlockB);
+          bulk_copy(smem_u32(sA + kStageA), src, kBlockB, full_bar(st));
+        }
+        cp_async_wait<kRaw - 1>();  // this thread's raw values of step s have landed
+        const float2* rawp = reinterpret_cast<const float2*>(smem + kSmemRaw + (s % kRaw) * kRawStage);
+        const float* mg = sMag + P.qf * kTile;
+#pragma unroll
+        for (int k = 0; k < kUnits; ++k) {
+          const int u = warp + (kSlicers / 32) * k;
+          const int rg = u >> 1, kq = u & 1;
+          const int r = rg * 8 + (lane >> 2);
+          const float2 x0 = rawp[(k * 2 + 0) * kSlicers + tid], x1 = rawp[(k * 2 + 1) * kSlicers + tid];
+          float d0[kSlices], d1[kSlices];
+          slice6(x0.x, x0.y, mg[r], d0);
+          slice6(x1.x, x1.y, mg[r], d1);
+          const int off = rg * kSBO + kq * kLBO + (lane >> 2) * 16 + (lane & 3) * 4;
+#pragma unroll
+          for (int t = 0; t < kSlices; ++t)
+            *reinterpret_cast<__nv_bfloat162*>(sA + kTileBytes + t * kTileBytes + off) =
+                __floats2bfloat162_rn(d0[t], d1[t]);
+        }
+        fence_async_smem();
+        mbar_arrive(full_bar(st));
+      }
+      cp_async_wait<0>();
+    }
+  } else if (warp == kMmaWarp) {
+    // ---------------------------------------------------------- MMA issue
+    if (lane == 0) {
+      int g = 0, k = 0;
+      bool ok = true;
+      for (int n = blockIdx.x; n < n_items && ok; n += gridDim.x) {
+        const ItemInfo I = item_info(G, items[n]);
+        for (int grp = 0; grp < I.n_jt * n_prod && ok; ++grp, ++k) {
+          const int jt = grp / n_prod;
+          const int N = (min(kTile, I.nb - jt * kTile) + 15) & ~15;
+          const uint32_t idesc = make_idesc(128, N);
+          const int set = k & 1;
+          if (!mbar_wait_abort(accempty_bar(set), ((k >> 1) & 1) ^ 1, s_abort, status, 64)) {
+            ok = false;
+            break;
           }
-          const int i0 = ic * kKc;
-          unsigned char* sA = smem + kSmemA + buf * kStage;
-          unsigned char* sB = sA + kStageA;
-          // all loads and gathers of the step first, then the splitting
-          float2 xa[kUnits][2];
-          df xs[kUnits][2];
-#pragma unroll
-          for (int k = 0; k < kUnits; ++k) {
-            const int u = warp + (kThreads / 32) * k;
-            const int r = (u >> 1) * 8 + (lane >> 2), i = i0 + 2 * ((u & 1) * 4 + (lane & 3));
-            const int p = r0 + r, j = j0 + r;
-            const float2* src = base + P.qf * plane + static_cast<int64_t>(i) * ldp + p;
-            xa[k][0] = (p < np && i < nb) ? src[0] : make_float2(0.f, 0.f);
-            xa[k][1] = (p < np && i + 1 < nb) ? src[ldp] : make_float2(0.f, 0.f);
-            xs[k][0] = (j < nb && i < nb) ? gprime_df(Gm, idx, nb, P.anti, i, j) : df{0.f, 0.f};
-            xs[k][1] = (j < nb && i + 1 < nb) ? gprime_df(Gm, idx, nb, P.anti, i + 1, j) : df{0.f, 0.f};
-          }
-#pragma unroll
-          for (int side = 0; side < 2; ++side) {
-            unsigned char* dst = side == 0 ? sA + kTileBytes : sB;
-            const float* mg = side == 0 ? sMagF : sMagG;
-#pragma unroll
-            for (int k = 0; k < kUnits; ++k) {
-              const int u = warp + (kThreads / 32) * k;
-              const int rg = u >> 1, kq = u & 1;
-              const int r = rg * 8 + (lane >> 2);
-              const float m0 = mg[r];
-              float d0[kSlices], d1[kSlices];
-              if (side == 0) {
-                slice6(xa[k][0].x, xa[k][0].y, m0, d0);
-                slice6(xa[k][1].x, xa[k][1].y, m0, d1);
-              } else {
-                slice6(xs[k][0].hi, xs[k][0].lo, m0, d0);
-                slice6(xs[k][1].hi, xs[k][1].lo, m0, d1);
-              }
-              const int off = rg * kSBO + kq * kLBO + (lane >> 2) * 16 + (lane & 3) * 4;
-#pragma unroll
-              for (int s = 0; s < kSlices; ++s)
-                *reinterpret_cast<__nv_bfloat162*>(dst + s * kTileBytes + off) = __floats2bfloat162_rn(d0[s], d1[s]);
+          tc_fence_after();
+          const uint32_t t0 = tmem + set * kSetCols, t1 = t0 + kTile, t2 = t0 + 2 * kTile;
+          for (int ic = 0; ic < I.n_ic; ++ic, ++g) {
+            const int st = g % kStages;
+            if (!mbar_wait_abort(full_bar(st), (g / kStages) & 1, s_abort, status, 32)) {
+              ok = false;
+              break;
             }
-          }
-          fence_async_smem();
-          __syncthreads();
-          if (tid == 0) {
             tc_fence_after();
-            const uint32_t a = smem_u32(sA), bb = smem_u32(sB);
-            const uint32_t t0 = tmem, t1 = tmem + kTile, t2 = tmem + 2 * kTile;
+            const uint32_t a = smem_u32(smem + kSmemStages + st * kStage), bb = a + kStageA;
             const uint32_t acc = ic == 0 ? 0u : 1u;
             auto A = [&](int q) { return make_desc(a + q * kTileBytes, kSBO); };
             auto Bt = [&](int t) { return make_desc(bb + t * kTileBytes, kSBO); };
@@ -263,43 +385,59 @@ __global__ void __launch_bounds__(kThreads, 2)
             mma_bf16(t2, A(2), Bt(3), idesc, 1u);
             mma_bf16(t2, A(1), Bt(4), idesc, 1u);
             mma_bf16(t2, A(0), Bt(5), idesc, 1u);
-            mma_commit(bar_addr[buf]);
+            mma_commit(empty_bar(st));
           }
-          pending[buf] = true;
+          if (ok) mma_commit(accfull_bar(set));
         }
-        if (!ok) break;
-        // drain the outstanding commits (oldest first) before reading TMEM
-        for (int d = 0; d < 2 && ok; ++d) {
-          const int buf = (gstep + d) & 1;
-          if (!pending[buf]) continue;
-          ok = __syncthreads_and(mbar_wait(bar_addr[buf], ph[buf], status));
-          ph[buf] ^= 1;
-          pending[buf] = false;
+      }
+      // every MMA issued by this thread has completed before tensor memory is freed
+      mma_commit(drain_bar);
+      (void)mbar_wait(drain_bar, 0, status);
+    }
+    __syncwarp();
+  } else {
+    // ---------------------------------------------------------- epilogue
+    const int eg = (warp - kEpiWarp0) >> 2;  // column group
+    const int et = (warp & 3) * 32 + lane;   // TMEM lane 0..127
+    const uint32_t lane_base = static_cast<uint32_t>((warp & 3) * 32) << 16;
+    float* stg = reinterpret_cast<float*>(smem + kSmemEpi) + eg * (kEpiStage / 4);
+    const int r = et & 63, half = et >> 6;  // combine phase: point r, columns half*8 .. half*8+7
+    int k = 0;
+    bool ok = true;
+    for (int n = blockIdx.x; n < n_items && ok; n += gridDim.x) {
+      const ItemInfo I = item_info(G, items[n]);
+      const float2* base = reinterpret_cast<const float2*>(scratch) + scr_off[I.b];
+      const int p = I.pt * kTile + r;
+      df y = {0.f, 0.f};
+      for (int grp = 0; grp < I.n_jt * n_prod; ++grp, ++k) {
+        const int set = k & 1;
+        ok = mbar_wait_abort(accfull_bar(set), (k >> 1) & 1, s_abort, status, 256);
+        if (bar_red_or(2, kEpiThreads, !ok)) {
+          ok = false;
+          break;
         }
         tc_fence_after();
-        if (!ok) break;
-        // epilogue: U_rj from the six levels, dotted with R_rj
-        const int r = tid & 63, part = tid >> 6;
-        const int p = r0 + r;
-        for (int c0 = 0; c0 < N; c0 += 16) {
-          if (warp < 4) {  // warp w reads TMEM lanes 32w..32w+31
-            const uint32_t lane_base = static_cast<uint32_t>(warp * 32) << 16;
+        const int jt = grp / n_prod, j0 = jt * kTile;
+        const Product P = product_of(MODE, prods[grp % n_prod]);
+        const int N = (min(kTile, I.nb - j0) + 15) & ~15;
+        const float2* Rrow = base + P.qr * I.plane + p;
+        for (int c0 = eg * 16; c0 < N; c0 += 32) {
 #pragma unroll
-            for (int blk = 0; blk < 3; ++blk) {
-              float vv[16];
-              tmem_ld16(tmem + lane_base + blk * kTile + c0, vv);
+          for (int blk = 0; blk < 3; ++blk) {
+            float vv[16];
+            tmem_ld16(tmem + lane_base + set * kSetCols + blk * kTile + c0, vv);
 #pragma unroll
-              for (int i = 0; i < 16; ++i) stage[(tid * 16 + i) * 3 + blk] = vv[i];
-            }
+            for (int i = 0; i < 16; ++i) stg[(blk * 128 + et) * kEpiPitch + i] = vv[i];
           }
-          __syncthreads();
-          if (p < np) {
-            for (int cc = 0; cc < 16 / (kThreads / 64); ++cc) {
-              const int col = part * (16 / (kThreads / 64)) + cc, j = j0 + c0 + col;
-              if (j >= nb) continue;
-              const float* top = stage + (r * 16 + col) * 3;
-              const float* bot = stage + ((r + 64) * 16 + col) * 3;
-              const float L0 = top[0], L1 = bot[0], L2 = top[1], L3 = bot[1], L4 = top[2], L5 = bot[2];
+          bar_sync(3 + eg, 128);
+          if (p < I.np) {
+#pragma unroll 2
+            for (int cc = 0; cc < 8; ++cc) {
+              const int col = half * 8 + cc, j = j0 + c0 + col;
+              if (j >= I.nb) break;
+              const float L0 = stg[r * kEpiPitch + col], L1 = stg[(r + 64) * kEpiPitch + col];
+              const float L2 = stg[(128 + r) * kEpiPitch + col], L3 = stg[(192 + r) * kEpiPitch + col];
+              const float L4 = stg[(256 + r) * kEpiPitch + col], L5 = stg[(320 + r) * kEpiPitch + col];
               float sm = L0 + L1;
               float bp = sm - L0;
               const float e1 = (L0 - (sm - bp)) + (L1 - bp);
@@ -308,35 +446,31 @@ __global__ void __launch_bounds__(kThreads, 2)
               bp = sm - s1;
               const float e2 = (s1 - (sm - bp)) + (L2 - bp);
               const float lo = (e1 + e2) + (L3 + (L4 + L5));
-              const float2 Rv = base[P.qr * plane + static_cast<int64_t>(j) * ldp + p];
+              const float2 Rv = __ldg(Rrow + static_cast<int64_t>(j) * I.ldp);
               const df prod = df_mul(df{Rv.x, Rv.y}, fast_two_sum(sm, lo));
-              y = df_add(y, df_mul_f(prod, static_cast<float>(P.factor)));
+              y = df_add(y, df{P.factor * prod.hi, P.factor * prod.lo});  // factor 1 or 2: exact
             }
           }
-          __syncthreads();
+          bar_sync(3 + eg, 128);
         }
         tc_fence_before();
-        __syncthreads();
+        mbar_arrive(accempty_bar(set));
       }
+      if (!ok) break;
+      // the four partial sums of each point (two column halves x two groups)
+      sY[(eg * 2 + half) * kTile + r] = static_cast<double>(y.hi) + static_cast<double>(y.lo);
+      bar_sync(2, kEpiThreads);
+      if (eg == 0 && half == 0 && p < I.np) {
+        const double val = (sY[r] + sY[kTile + r]) + (sY[2 * kTile + r] + sY[3 * kTile + r]);
+        const int64_t gp = I.bp0 + p;
+        out[gp] = MODE == 0 ? val : G.w[gp] * val;
+      }
+      bar_sync(2, kEpiThreads);
     }
-    // combine the column parts of each point and write
-    sY[tid] = static_cast<double>(y.hi) + static_cast<double>(y.lo);
-    __syncthreads();
-    if (tid < kTile && r0 + tid < np) {
-      const int64_t gp = bp0 + r0 + tid;
-      double val = 0.0;
-      for (int q = 0; q < kThreads / 64; ++q) val += sY[tid + 64 * q];
-      out[gp] = MODE == 0 ? val : G.w[gp] * val;
-    }
-    __syncthreads();
-  }
-  if (!ok) {
-    for (int d = 0; d < 2; ++d)
-      if (pending[d]) (void)__syncthreads_and(mbar_wait(bar_addr[d], ph[d], status));
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == 0)
+  if (warp == kMmaWarp)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
 }
 
@@ -347,44 +481,46 @@ q4c_status run(const q4c_tables* t, const q4c_grid* g, const double* const mats[
     return Q4C_EUNSUPPORTED;
   }
   const int n_waves = static_cast<int>(g->wave_b0.size()) - 1;
-  Q4C_CUDA(cudaMemsetAsync(g->d_counter, 0, sizeof(int) * std::max(n_waves, 1), s));
   Q4C_CUDA(cudaFuncSetAttribute(k_split_rowdot<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemTotal));
   int dev = 0, n_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
-  // FP32-pair copies of the matrices for the B operands
+  const char* name = MODE == 0 ? "split_density" : "split_backward";
+  // FP32-pair copies of the matrices
   const float2* mdf[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  unsigned present = 0;
   {
-    KernelScope ks(MODE == 0 ? "split_density" : "split_backward", s);
+    KernelScope ks("split_gslice", s);
     for (int m = 0; m < 5; ++m) {
       if (!mats[m] || g->nnz == 0) continue;
       float2* dst = g->d_gdf + m * g->nnz;
       const unsigned blocks = static_cast<unsigned>(std::min<int64_t>((g->nnz + 255) / 256, 8 * n_sm));
       k_to_df<<<blocks, 256, 0, s>>>(mats[m], g->nnz, dst);
       mdf[m] = dst;
+      present |= 1u << m;
     }
   }
   Q4C_CUDA(cudaGetLastError());
   for (int wv = 0; wv < n_waves; ++wv) {
     const int64_t b0 = g->wave_b0[wv], b1 = g->wave_b0[wv + 1];
     if (b1 <= b0) continue;
-    if (q4c_status st = launch_basis_df(t, g, b0, b1, nullptr, nullptr, g->d_rowexp, s)) return st;
     {
-      KernelScope ks("split_gexp", s);
-      k_gexp<<<static_cast<unsigned>(b1 - b0), 128, 0, s>>>(t->view(), g->view(), b0, MODE == 0 ? 1 : 5,
-                                                            MODE == 0 ? 5 : 2, mats[0], mats[1], mats[2], mats[3],
-                                                            mats[4], g->d_gexp);
+      KernelScope ks("split_gslice", s);
+      k_gslice<<<dim3(static_cast<unsigned>(b1 - b0), MODE == 0 ? 1 : 5), 256, 0, s>>>(
+          g->view(), b0, MODE == 0 ? 5 : 2, mdf[0], mdf[1], mdf[2], mdf[3], mdf[4], g->d_gsl_off,
+          reinterpret_cast<uint32_t*>(g->d_gsl));
     }
     Q4C_CUDA(cudaGetLastError());
+    if (q4c_status st = launch_basis_df(t, g, b0, b1, nullptr, nullptr, g->d_rowexp, s)) return st;
     const int64_t i0 = g->rd_w0[wv], i1 = g->rd_w0[wv + 1];
     const int n_items = static_cast<int>(i1 - i0);
     if (n_items == 0) continue;
-    const int grid = std::min(n_items, 2 * n_sm);
+    const int grid = std::min(n_items, n_sm);
     {
-      KernelScope ks(MODE == 0 ? "split_density" : "split_backward", s);
+      KernelScope ks(name, s);
       k_split_rowdot<MODE><<<grid, kThreads, kSmemTotal, s>>>(
-          t->view(), g->view(), g->d_rd_items + i0, n_items, g->d_counter + wv, g->d_scr_off, g->d_scratch,
-          g->d_rowexp, g->d_gexp, mdf[0], mdf[1], mdf[2], mdf[3], mdf[4], out, g->d_status);
+          t->view(), g->view(), g->d_rd_items + i0, n_items, g->d_scr_off, g->d_scratch, g->d_rowexp,
+          g->d_gsl_off, reinterpret_cast<const unsigned char*>(g->d_gsl), present, out, g->d_status);
     }
     Q4C_CUDA(cudaGetLastError());
   }

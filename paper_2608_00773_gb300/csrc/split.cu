@@ -38,9 +38,9 @@
 // (three products into one accumulator, sliced against a common exponent per
 // function so that the exact levels keep one unit), and A_yz = (D Y)^T Z,
 // A_zx = (D Z)^T X, A_xy = (D X)^T Y with SO_x = A_yz - A_yz^T etc. applied
-// while scattering.  Persistent CTAs (128 threads, 256 TMEM columns, two
-// per SM) loop over work items; every mbarrier wait is bounded and sets a
-// status bit instead of hanging.
+// while scattering.  One warp-specialised CTA per SM (slicers, one MMA
+// thread, epilogue warps; 512 TMEM columns) loops over the work items; every
+// mbarrier wait is bounded and sets a status bit instead of hanging.
 #include "internal.h"
 #include "tc.cuh"
 
@@ -52,20 +52,32 @@ constexpr int kTile = 64;                    // functions per tile (rows of one 
 constexpr int kKc = 16;                      // points per step (one K = 16 MMA step)
 constexpr int kTileBytes = kTile * kKc * 2;  // 2 KB
 constexpr int kSBO = (kKc / 8) * 128;        // 256 B between 8-row groups
-constexpr int kThreads = 256;
-constexpr int kUnits = 16 / (kThreads / 32);  // slicing units per side per thread
+constexpr int kSlicers = 256;                // warps 0-7 slice the operands
+constexpr int kEpiWarp0 = 8;                 // warps 8-15 drain tensor memory (two groups of four)
+constexpr int kEpiThreads = 256;
+constexpr int kMmaWarp = 16;                 // warp 16 owns tensor memory and issues the MMAs
+constexpr int kThreads = 17 * 32;
+constexpr int kEpiPitch = 17;                // floats per staged TMEM lane (16 columns + pad)
+constexpr int kEpiStage = 3 * 128 * kEpiPitch * 4;  // one group's staging, 26 KB
+constexpr int kUnits = 16 / (kSlicers / 32);  // slicing units per side per thread
 constexpr int kMaxProducts = 3;
 constexpr int kStageA = (kSlices + 1) * kTileBytes;  // [Z, A0..A5]
 constexpr int kStageB = kSlices * kTileBytes;        // [B0..B5]
 constexpr int kStage = kStageA + kStageB;            // 26 KB
-constexpr int kSmemStages = 0;                       // two stages (double buffer)
-constexpr int kSmemEpi = kSmemStages + 2 * kStage;   // epilogue staging, 24 KB
-constexpr int kSmemD = kSmemEpi + 128 * 16 * 3 * 4;
-constexpr int kMaxNp = 344;                          // D values of one batch (double-float)
+constexpr int kStages = 4;                           // ring depth of sliced operands
+constexpr int kRaw = 4;                              // ring depth of raw operand values
+constexpr int kRawStage = kSlicers * 2 * kUnits * 16;  // one step's float2 pairs, 16 KB
+constexpr int kSmemStages = 0;
+constexpr int kSmemEpi = kSmemStages + kStages * kStage;  // epilogue staging, 2 x 26 KB
+constexpr int kSmemRaw = kSmemEpi + 2 * kEpiStage;
+constexpr int kSmemD = kSmemRaw + kRaw * kRawStage;
+constexpr int kMaxNp = 344;  // D values of one batch (double-float)
 constexpr int kSmemExp = kSmemD + kMaxNp * 8;
 constexpr int kSmemBar = kSmemExp + 2 * kTile * 4;
-constexpr int kSmemTotal = kSmemBar + 64;
-constexpr uint32_t kTmemCols = 256;  // three 64-column blocks
+constexpr int kNumBars = 2 * kStages + 5;  // full[S], empty[S], accfull[2], accempty[2], drain
+constexpr int kSmemTotal = kSmemBar + kNumBars * 8 + 16;
+constexpr uint32_t kTmemCols = 512;  // two accumulator sets of three 64-column blocks
+constexpr uint32_t kSetCols = 256;
 
 // ------------------------------------------------------------ kernel
 struct Products {
@@ -90,13 +102,60 @@ __device__ __forceinline__ int local_nf(const DevBasis& B, const DevGrid& G, int
   return __ldg(B.sp_nfn + G.atom_sp[G.bat_atoms[a0 + a]]);
 }
 
+__device__ __forceinline__ int item_steps(const DevGrid& G, int4 item) {
+  const int np = static_cast<int>(G.pt_ptr[item.x + 1] - G.pt_ptr[item.x]);
+  return ((np + kKc - 1) / kKc) * (item.y == 1 ? 3 : 1);
+}
+
+// Issue the asynchronous copies of one K-step's operand values for this
+// thread: per side, kUnits units of two consecutive points (16 bytes each)
+// into its slots of a raw stage (slot (side * kUnits + k) * kSlicers + tid).
+// Values past the batch's points or functions arrive as zeros.
+__device__ __forceinline__ void issue_step(const float2* base, int64_t plane, int ldp, int np, int nb, int i0,
+                                           int j0, const Products& P, int s, int warp, int lane, int tid,
+                                           uint32_t raw) {
+  const int c = s / P.n, pr = s - c * P.n;
+  const int kc0 = c * kKc;
+#pragma unroll
+  for (int side = 0; side < 2; ++side) {
+    const int q = side == 0 ? P.qa[pr] : P.qb[pr];
+    const int row0 = side == 0 ? i0 : j0;
+#pragma unroll
+    for (int k = 0; k < kUnits; ++k) {
+      const int u = warp + (kSlicers / 32) * k;
+      const int r = (u >> 1) * 8 + (lane >> 2), p = kc0 + 2 * ((u & 1) * 4 + (lane & 3));
+      const int f = row0 + r;
+      const bool live = f < nb && p < np;
+      const int bytes = !live ? 0 : (p + 1 < np ? 16 : 8);  // row padding is not written
+      const float2* src = live ? base + q * plane + static_cast<int64_t>(f) * ldp + p : base;
+      cp_async16(raw + ((side * kUnits + k) * kSlicers + tid) * 16, src, bytes);
+    }
+  }
+}
+
 // One work item = (batch, output, 64x64 tile).  Its K dimension is a stream
 // of steps of 16 points; W0 streams its three gradient products one after
 // the other (a K-concatenation into one accumulator, common exponents).
-// Steps alternate between two shared-memory stages: the 128 threads slice
-// step s + 1 while the tensor core runs the twelve MMAs of step s.
-__global__ void __launch_bounds__(kThreads, 2)
-    k_split_products(DevBasis B, DevGrid G, const int4* __restrict__ items, int n_items, int* counter,
+//
+// Warp roles (one CTA per SM, items strided over the CTAs):
+//   warps 0-7   slice step g into ring stage g mod 4 once the MMAs that last
+//               read it have completed (empty[stage], a tcgen05.commit), then
+//               arrive on full[stage]; each thread's raw values arrive by
+//               cp.async three steps ahead, in a ring of its own;
+//   warp 12     (one thread) waits full[stage], issues the twelve MMAs into the
+//               item's accumulator set (items alternate between two sets of
+//               192 TMEM columns), commits empty[stage], and after an item's
+//               last step commits accfull[set];
+//   warps 8-15  wait accfull[set], read the six levels, combine and scatter
+//               (two groups of four warps take alternate 16-column chunks;
+//               the scatter offsets come from the batch's dense offset
+//               table), then arrive on accempty[set] so the set can take
+//               item k + 2.
+// Every wait is bounded; a role that times out sets the status bit and an
+// abort flag that ends the other roles' waits, and the MMA thread drains its
+// outstanding MMAs (bounded) before tensor memory is freed.
+__global__ void __launch_bounds__(kThreads, 1)
+    k_split_products(DevBasis B, DevGrid G, const int4* __restrict__ items, int n_items,
                      const int64_t* __restrict__ scr_off, const double* __restrict__ scratch,
                      const int* __restrict__ colexp, const double* __restrict__ v, double* V, double* W0,
                      double* SOx, double* SOy, double* SOz, unsigned* status) {
@@ -105,23 +164,36 @@ __global__ void __launch_bounds__(kThreads, 2)
   df* sD = reinterpret_cast<df*>(smem + kSmemD);
   float* sMagA = reinterpret_cast<float*>(smem + kSmemExp);  // rounding constants of the rows
   float* sMagB = sMagA + kTile;
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + kSmemBar);  // two barriers
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + kSmemBar + 16);
-  int* s_item = reinterpret_cast<int*>(smem + kSmemBar + 32);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kSmemBar);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + kSmemBar + kNumBars * 8);
+  volatile int* s_abort = reinterpret_cast<volatile int*>(smem + kSmemBar + kNumBars * 8 + 4);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const uint32_t bar_addr[2] = {smem_u32(bar), smem_u32(bar + 1)};
+  const uint32_t bar0 = smem_u32(bars);
+  auto full_bar = [&](int st) { return bar0 + 8u * st; };
+  auto empty_bar = [&](int st) { return bar0 + 8u * (kStages + st); };
+  auto accfull_bar = [&](int set) { return bar0 + 8u * (2 * kStages + set); };
+  auto accempty_bar = [&](int set) { return bar0 + 8u * (2 * kStages + 2 + set); };
+  const uint32_t drain_bar = bar0 + 8u * (2 * kStages + 4);
 
   // zero tile Z at the head of each stage (never overwritten)
-  for (int i = tid; i < 2 * kTileBytes / 16; i += kThreads) {
+  for (int i = tid; i < kStages * kTileBytes / 16; i += kThreads) {
     const int st = i / (kTileBytes / 16), off = i - st * (kTileBytes / 16);
     reinterpret_cast<uint4*>(smem + kSmemStages + st * kStage)[off] = make_uint4(0, 0, 0, 0);
   }
   if (tid == 0) {
-    mbar_init(bar_addr[0], 1);
-    mbar_init(bar_addr[1], 1);
+    for (int st = 0; st < kStages; ++st) {
+      mbar_init(full_bar(st), kSlicers);
+      mbar_init(empty_bar(st), 1);
+    }
+    for (int set = 0; set < 2; ++set) {
+      mbar_init(accfull_bar(set), 1);
+      mbar_init(accempty_bar(set), kEpiThreads);
+    }
+    mbar_init(drain_bar, 1);
+    *s_abort = 0;
   }
-  if (warp == 0) {
+  if (warp == kMmaWarp) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
                  "r"(kTmemCols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
@@ -131,210 +203,223 @@ __global__ void __launch_bounds__(kThreads, 2)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
-  uint32_t ph[2] = {0, 0};
-  bool pending[2] = {false, false};  // a commit on this stage not yet waited for
-  bool ok = true;
 
-  while (ok) {
-    if (tid == 0) *s_item = atomicAdd(counter, 1);
-    __syncthreads();
-    const int it = *s_item;
-    if (it >= n_items) break;
-    const int4 item = items[it];
-    const int64_t b = item.x;
-    const int o = item.y, ti = item.z, tj = item.w;
-    const int64_t p0 = G.pt_ptr[b];
-    const int np = static_cast<int>(G.pt_ptr[b + 1] - p0);
-    const int ldp = (np + 7) & ~7;
-    const int nb = static_cast<int>(G.bat_fn_ptr[b + 1] - G.bat_fn_ptr[b]);
-    const int64_t plane = static_cast<int64_t>(nb) * ldp;
-    const float2* base = reinterpret_cast<const float2*>(scratch) + scr_off[b];
-    const int* cexp = colexp + 8 * G.bat_fn_ptr[b];
-    const Products P = products_of(o);
-    const int i0 = ti * kTile, j0 = tj * kTile;
-    const int ncols = min(kTile, nb - j0);
-    const int N = (ncols + 15) & ~15;
-    const uint32_t idesc = make_idesc(128, N);
-
-    // Column exponents (W0: one exponent per function over its three gradient
-    // components, so that its K-concatenated products share units) and D.
-    if (tid < kTile) {
-      const int r = tid;
-      int ea = -30000, eb = -30000;
-      if (o == 1) {
-        if (i0 + r < nb) ea = max(cexp[1 * nb + i0 + r], max(cexp[2 * nb + i0 + r], cexp[3 * nb + i0 + r]));
-        if (j0 + r < nb) eb = max(cexp[5 * nb + j0 + r], max(cexp[6 * nb + j0 + r], cexp[7 * nb + j0 + r]));
-      } else {
-        if (i0 + r < nb) ea = cexp[P.qa[0] * nb + i0 + r];
-        if (j0 + r < nb) eb = cexp[(4 + P.qb[0]) * nb + j0 + r];
-      }
-      sMagA[r] = magic0(ea);
-      sMagB[r] = magic0(eb);
-    }
-    for (int p = tid; p < np; p += kThreads) {
-      const double Dp = G.w[p0 + p] * v[p0 + p];
-      const float h = static_cast<float>(Dp);
-      sD[p] = df{h, static_cast<float>(Dp - static_cast<double>(h))};
-    }
-    __syncthreads();
-
-    const int n_chunks = (np + kKc - 1) / kKc;
-    const int n_steps = n_chunks * P.n;
-    for (int s = 0; s < n_steps && ok; ++s) {
-      const int buf = s & 1;
-      if (pending[buf]) {  // the stage is free once the MMAs that read it finished
-        ok = __syncthreads_and(mbar_wait(bar_addr[buf], ph[buf], status));
-        ph[buf] ^= 1;
-        pending[buf] = false;
-        if (!ok) break;
-      }
-      const int c = s / P.n, pr = s - c * P.n;
-      const int kc0 = c * kKc;
-      unsigned char* sA = smem + kSmemStages + buf * kStage;
-      unsigned char* sB = sA + kStageA;
-      // all global loads of the step first (eight units per thread: four per
-      // side), then the splitting and the shared-memory stores
-      float2 xs[2][kUnits][2];
-#pragma unroll
-      for (int side = 0; side < 2; ++side) {
-        const int q = side == 0 ? P.qa[pr] : P.qb[pr];
-        const int row0 = side == 0 ? i0 : j0;
-#pragma unroll
-        for (int k = 0; k < kUnits; ++k) {
-          const int u = warp + (kThreads / 32) * k;
-          const int r = (u >> 1) * 8 + (lane >> 2), p = kc0 + 2 * ((u & 1) * 4 + (lane & 3));
-          const int f = row0 + r;
-          const float2* src = base + q * plane + static_cast<int64_t>(f) * ldp + p;
-          xs[side][k][0] = (f < nb && p < np) ? src[0] : make_float2(0.f, 0.f);
-          xs[side][k][1] = (f < nb && p + 1 < np) ? src[1] : make_float2(0.f, 0.f);
+  if (warp < kSlicers / 32) {
+    // ---------------------------------------------------------- slicers
+    bool ok = true;
+    int g = 0;  // steps sliced by this CTA
+    for (int n = blockIdx.x;; n += gridDim.x) {
+      // the previous item's constants are no longer read; agree on stopping
+      if (bar_red_or(1, kSlicers, !ok || *s_abort) || n >= n_items) break;
+      const int4 item = items[n];
+      const int64_t b = item.x;
+      const int o = item.y, ti = item.z, tj = item.w;
+      const int64_t p0 = G.pt_ptr[b];
+      const int np = static_cast<int>(G.pt_ptr[b + 1] - p0);
+      const int ldp = (np + 7) & ~7;
+      const int nb = static_cast<int>(G.bat_fn_ptr[b + 1] - G.bat_fn_ptr[b]);
+      const int64_t plane = static_cast<int64_t>(nb) * ldp;
+      const float2* base = reinterpret_cast<const float2*>(scratch) + scr_off[b];
+      const int* cexp = colexp + 8 * G.bat_fn_ptr[b];
+      const Products P = products_of(o);
+      const int i0 = ti * kTile, j0 = tj * kTile;
+      // Column exponents (W0: one exponent per function over its three gradient
+      // components, so that its K-concatenated products share units) and D.
+      if (tid < kTile) {
+        const int r = tid;
+        int ea = -30000, eb = -30000;
+        if (o == 1) {
+          if (i0 + r < nb) ea = max(cexp[1 * nb + i0 + r], max(cexp[2 * nb + i0 + r], cexp[3 * nb + i0 + r]));
+          if (j0 + r < nb) eb = max(cexp[5 * nb + j0 + r], max(cexp[6 * nb + j0 + r], cexp[7 * nb + j0 + r]));
+        } else {
+          if (i0 + r < nb) ea = cexp[P.qa[0] * nb + i0 + r];
+          if (j0 + r < nb) eb = cexp[(4 + P.qb[0]) * nb + j0 + r];
         }
+        sMagA[r] = magic0(ea);
+        sMagB[r] = magic0(eb);
       }
+      for (int p = tid; p < np; p += kSlicers) {
+        const double Dp = G.w[p0 + p] * v[p0 + p];
+        const float h = static_cast<float>(Dp);
+        sD[p] = df{h, static_cast<float>(Dp - static_cast<double>(h))};
+      }
+      bar_sync(1, kSlicers);
+      const int n_steps = item_steps(G, item);
+      const uint32_t raw0 = smem_u32(smem + kSmemRaw);
+      // copies run kRaw - 1 steps ahead of the slicing (one commit group per step)
 #pragma unroll
-      for (int side = 0; side < 2; ++side) {
-        const float* mg = side == 0 ? sMagA : sMagB;
-        unsigned char* dst = side == 0 ? sA + kTileBytes : sB;
+      for (int q = 0; q < kRaw - 1; ++q) {
+        if (q < n_steps) issue_step(base, plane, ldp, np, nb, i0, j0, P, q, warp, lane, tid, raw0 + q * kRawStage);
+        cp_async_commit();
+      }
+      for (int s = 0; s < n_steps; ++s, ++g) {
+        const int sa = s + kRaw - 1;
+        if (sa < n_steps)
+          issue_step(base, plane, ldp, np, nb, i0, j0, P, sa, warp, lane, tid, raw0 + (sa % kRaw) * kRawStage);
+        cp_async_commit();
+        cp_async_wait<kRaw - 1>();  // this thread's copies of step s have landed
+        const float4* rawp = reinterpret_cast<const float4*>(smem + kSmemRaw + (s % kRaw) * kRawStage);
+        float4 cur[2][kUnits];
 #pragma unroll
-        for (int k = 0; k < kUnits; ++k) {
-          const int u = warp + (kThreads / 32) * k;
-          const int rg = u >> 1, kq = u & 1;
-          const int r = rg * 8 + (lane >> 2), p = kc0 + 2 * (kq * 4 + (lane & 3));
-          const float m0 = mg[r];
-          float d0[kSlices], d1[kSlices];
-          if (side == 0) {  // A side: D-scaled values, the product in double-float
-            const df a0v = p < np ? df_mul(df{xs[0][k][0].x, xs[0][k][0].y}, sD[p]) : df{0.f, 0.f};
-            const df a1v = p + 1 < np ? df_mul(df{xs[0][k][1].x, xs[0][k][1].y}, sD[p + 1]) : df{0.f, 0.f};
-            slice6(a0v.hi, a0v.lo, m0, d0);
-            slice6(a1v.hi, a1v.lo, m0, d1);
-          } else {
-            slice6(xs[1][k][0].x, xs[1][k][0].y, m0, d0);
-            slice6(xs[1][k][1].x, xs[1][k][1].y, m0, d1);
+        for (int side = 0; side < 2; ++side)
+#pragma unroll
+          for (int k = 0; k < kUnits; ++k) cur[side][k] = rawp[(side * kUnits + k) * kSlicers + tid];
+        const int st = g % kStages;
+        if (!mbar_wait_abort(empty_bar(st), ((g / kStages) & 1) ^ 1, s_abort, status)) {
+          ok = false;
+          break;
+        }
+        const int c = s / P.n;
+        const int kc0 = c * kKc;
+        unsigned char* sA = smem + kSmemStages + st * kStage;
+        unsigned char* sB = sA + kStageA;
+#pragma unroll
+        for (int side = 0; side < 2; ++side) {
+          const float* mg = side == 0 ? sMagA : sMagB;
+          unsigned char* dst = side == 0 ? sA + kTileBytes : sB;
+#pragma unroll
+          for (int k = 0; k < kUnits; ++k) {
+            const int u = warp + (kSlicers / 32) * k;
+            const int rg = u >> 1, kq = u & 1;
+            const int r = rg * 8 + (lane >> 2), p = kc0 + 2 * (kq * 4 + (lane & 3));
+            const float m0 = mg[r];
+            const float4 x = cur[side][k];
+            float d0[kSlices], d1[kSlices];
+            if (side == 0) {  // A side: D-scaled values, the product in double-float
+              const df a0v = p < np ? df_mul(df{x.x, x.y}, sD[p]) : df{0.f, 0.f};
+              const df a1v = p + 1 < np ? df_mul(df{x.z, x.w}, sD[p + 1]) : df{0.f, 0.f};
+              slice6(a0v.hi, a0v.lo, m0, d0);
+              slice6(a1v.hi, a1v.lo, m0, d1);
+            } else {
+              slice6(x.x, x.y, m0, d0);
+              slice6(x.z, x.w, m0, d1);
+            }
+            const int off = rg * kSBO + kq * kLBO + (lane >> 2) * 16 + (lane & 3) * 4;
+#pragma unroll
+            for (int t = 0; t < kSlices; ++t)
+              *reinterpret_cast<__nv_bfloat162*>(dst + t * kTileBytes + off) = __floats2bfloat162_rn(d0[t], d1[t]);
           }
-          const int off = rg * kSBO + kq * kLBO + (lane >> 2) * 16 + (lane & 3) * 4;
-#pragma unroll
-          for (int t = 0; t < kSlices; ++t)
-            *reinterpret_cast<__nv_bfloat162*>(dst + t * kTileBytes + off) = __floats2bfloat162_rn(d0[t], d1[t]);
         }
+        fence_async_smem();
+        mbar_arrive(full_bar(st));
       }
-      fence_async_smem();
-      __syncthreads();
-      if (tid == 0) {
+      cp_async_wait<0>();  // no copy of this item outlives it
+    }
+  } else if (warp == kMmaWarp) {
+    // ---------------------------------------------------------- MMA issue
+    if (lane == 0) {
+      int g = 0, k = 0;
+      for (int n = blockIdx.x; n < n_items; n += gridDim.x, ++k) {
+        const int4 item = items[n];
+        const int nb = static_cast<int>(G.bat_fn_ptr[item.x + 1] - G.bat_fn_ptr[item.x]);
+        const int N = (min(kTile, nb - item.w * kTile) + 15) & ~15;
+        const uint32_t idesc = make_idesc(128, N);
+        const int n_steps = item_steps(G, item);
+        const int set = k & 1;
+        if (!mbar_wait_abort(accempty_bar(set), ((k >> 1) & 1) ^ 1, s_abort, status, 64)) break;
         tc_fence_after();
-        const uint32_t a = smem_u32(sA), bb = smem_u32(sB);
-        const uint32_t t0 = tmem, t1 = tmem + kTile, t2 = tmem + 2 * kTile;
-        const uint32_t acc = s == 0 ? 0u : 1u;
-        auto A = [&](int k) { return make_desc(a + k * kTileBytes, kSBO); };
-        auto Bt = [&](int t) { return make_desc(bb + t * kTileBytes, kSBO); };
-        mma_bf16(t0, A(1), Bt(0), idesc, acc);  // [A0;A1] x B0 -> L0, L1
-        mma_bf16(t0, A(0), Bt(1), idesc, 1u);   // [Z;A0]  x B1 -> L1
-        mma_bf16(t1, A(3), Bt(0), idesc, acc);  // [A2;A3] x B0 -> L2, L3
-        mma_bf16(t1, A(2), Bt(1), idesc, 1u);   // [A1;A2] x B1
-        mma_bf16(t1, A(1), Bt(2), idesc, 1u);   // [A0;A1] x B2
-        mma_bf16(t1, A(0), Bt(3), idesc, 1u);   // [Z;A0]  x B3 -> L3
-        mma_bf16(t2, A(5), Bt(0), idesc, acc);  // [A4;A5] x B0 -> L4, L5
-        mma_bf16(t2, A(4), Bt(1), idesc, 1u);   // [A3;A4] x B1
-        mma_bf16(t2, A(3), Bt(2), idesc, 1u);   // [A2;A3] x B2
-        mma_bf16(t2, A(2), Bt(3), idesc, 1u);   // [A1;A2] x B3
-        mma_bf16(t2, A(1), Bt(4), idesc, 1u);   // [A0;A1] x B4
-        mma_bf16(t2, A(0), Bt(5), idesc, 1u);   // [Z;A0]  x B5 -> L5
-        mma_commit(bar_addr[buf]);
+        const uint32_t t0 = tmem + set * kSetCols, t1 = t0 + kTile, t2 = t0 + 2 * kTile;
+        bool ok = true;
+        for (int s = 0; s < n_steps; ++s, ++g) {
+          const int st = g % kStages;
+          if (!mbar_wait_abort(full_bar(st), (g / kStages) & 1, s_abort, status, 32)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t a = smem_u32(smem + kSmemStages + st * kStage), bb = a + kStageA;
+          const uint32_t acc = s == 0 ? 0u : 1u;
+          auto A = [&](int q) { return make_desc(a + q * kTileBytes, kSBO); };
+          auto Bt = [&](int t) { return make_desc(bb + t * kTileBytes, kSBO); };
+          mma_bf16(t0, A(1), Bt(0), idesc, acc);  // [A0;A1] x B0 -> L0, L1
+          mma_bf16(t0, A(0), Bt(1), idesc, 1u);   // [Z;A0]  x B1 -> L1
+          mma_bf16(t1, A(3), Bt(0), idesc, acc);  // [A2;A3] x B0 -> L2, L3
+          mma_bf16(t1, A(2), Bt(1), idesc, 1u);   // [A1;A2] x B1
+          mma_bf16(t1, A(1), Bt(2), idesc, 1u);   // [A0;A1] x B2
+          mma_bf16(t1, A(0), Bt(3), idesc, 1u);   // [Z;A0]  x B3 -> L3
+          mma_bf16(t2, A(5), Bt(0), idesc, acc);  // [A4;A5] x B0 -> L4, L5
+          mma_bf16(t2, A(4), Bt(1), idesc, 1u);   // [A3;A4] x B1
+          mma_bf16(t2, A(3), Bt(2), idesc, 1u);   // [A2;A3] x B2
+          mma_bf16(t2, A(2), Bt(3), idesc, 1u);   // [A1;A2] x B3
+          mma_bf16(t2, A(1), Bt(4), idesc, 1u);   // [A0;A1] x B4
+          mma_bf16(t2, A(0), Bt(5), idesc, 1u);   // [Z;A0]  x B5 -> L5
+          mma_commit(empty_bar(st));
+        }
+        if (!ok) break;
+        mma_commit(accfull_bar(set));
       }
-      pending[buf] = true;
+      // every MMA issued by this thread has completed before tensor memory is freed
+      mma_commit(drain_bar);
+      (void)mbar_wait(drain_bar, 0, status);
     }
-    if (!ok) break;
-    // drain the outstanding commits (oldest first) before reading TMEM
-    for (int d = 0; d < 2 && ok; ++d) {
-      const int buf = (n_steps + d) & 1;
-      if (!pending[buf]) continue;
-      ok = __syncthreads_and(mbar_wait(bar_addr[buf], ph[buf], status));
-      ph[buf] ^= 1;
-      pending[buf] = false;
-    }
-    tc_fence_after();
-    if (!ok) break;
-
-    // epilogue: combine the six levels per element, scatter into FP64
-    const int64_t f0 = G.bat_fn_ptr[b];
-    const int a0 = G.bat_atom_ptr[b], na = G.bat_atom_ptr[b + 1] - a0;
-    const int64_t pp = G.bat_pair_ptr[b];
-    double* out = o == 0 ? V : o == 1 ? W0 : o == 2 ? SOx : o == 3 ? SOy : SOz;
-    for (int c0 = 0; c0 < N; c0 += 16) {
-      if (warp < 4) {  // warp w reads TMEM lanes 32w..32w+31
-        const uint32_t lane_base = static_cast<uint32_t>(warp * 32) << 16;
+    __syncwarp();
+  } else {
+    // ---------------------------------------------------------- epilogue
+    const int eg = (warp - kEpiWarp0) >> 2;        // column group
+    const int et = (warp & 3) * 32 + lane;         // TMEM lane 0..127
+    const uint32_t lane_base = static_cast<uint32_t>((warp & 3) * 32) << 16;
+    float* stg = stage + eg * (kEpiStage / 4);
+    int k = 0;
+    for (int n = blockIdx.x; n < n_items; n += gridDim.x, ++k) {
+      const int set = k & 1;
+      bool ok = mbar_wait_abort(accfull_bar(set), (k >> 1) & 1, s_abort, status, 256);
+      if (bar_red_or(2, kEpiThreads, !ok)) break;
+      tc_fence_after();
+      const int4 item = items[n];
+      const int64_t b = item.x;
+      const int o = item.y, i0 = item.z * kTile, j0 = item.w * kTile;
+      const int nb = static_cast<int>(G.bat_fn_ptr[b + 1] - G.bat_fn_ptr[b]);
+      const int N = (min(kTile, nb - j0) + 15) & ~15;
+      const int* idx = G.bat_idx + G.bat_idx_ptr[b];
+      double* out = o == 0 ? V : o == 1 ? W0 : o == 2 ? SOx : o == 3 ? SOy : SOz;
+      for (int c0 = eg * 16; c0 < N; c0 += 32) {
 #pragma unroll
         for (int blk = 0; blk < 3; ++blk) {
           float vv[16];
-          tmem_ld16(tmem + lane_base + blk * kTile + c0, vv);
+          tmem_ld16(tmem + lane_base + set * kSetCols + blk * kTile + c0, vv);
 #pragma unroll
-          for (int i = 0; i < 16; ++i) stage[(tid * 16 + i) * 3 + blk] = vv[i];
+          for (int i = 0; i < 16; ++i) stg[(blk * 128 + et) * kEpiPitch + i] = vv[i];
         }
-      }
-      __syncthreads();
-      const int r = tid & 63, part = tid >> 6;
-      const int i = i0 + r;
-      for (int cc = 0; cc < 16 / (kThreads / 64); ++cc) {
-        const int col = part * (16 / (kThreads / 64)) + cc;
-        const int j = j0 + c0 + col;
-        if (i >= nb || j >= nb) continue;
-        const float* top = stage + (r * 16 + col) * 3;
-        const float* bot = stage + ((r + 64) * 16 + col) * 3;
-        const float L0 = top[0], L1 = bot[0], L2 = top[1], L3 = bot[1], L4 = top[2], L5 = bot[2];
-        // exact levels by two-sums, rounded tail on top
-        float sm = L0 + L1;
-        float bp = sm - L0;
-        const float e1 = (L0 - (sm - bp)) + (L1 - bp);
-        const float s1 = sm;
-        sm = s1 + L2;
-        bp = sm - s1;
-        const float e2 = (s1 - (sm - bp)) + (L2 - bp);
-        const float lo = (e1 + e2) + (L3 + (L4 + L5));
-        const double val = static_cast<double>(sm) + static_cast<double>(lo);
-        int ri = i, rj = j;
-        double sgn = 1.0;
-        if (o <= 1) {
-          if (i > j) continue;
-        } else {
-          if (i == j) continue;
-          if (i > j) { ri = j; rj = i; sgn = -1.0; }
+        bar_sync(3 + eg, 128);
+        // thread -> (column, rows): a warp covers 16 consecutive columns of two rows
+        const int col = et & 15, j = j0 + c0 + col;
+#pragma unroll 2
+        for (int q = 0; q < 8; ++q) {
+          const int r = (et >> 4) + 8 * q, i = i0 + r;
+          if (i >= nb || j >= nb) continue;
+          const float L0 = stg[r * kEpiPitch + col], L1 = stg[(r + 64) * kEpiPitch + col];
+          const float L2 = stg[(128 + r) * kEpiPitch + col], L3 = stg[(192 + r) * kEpiPitch + col];
+          const float L4 = stg[(256 + r) * kEpiPitch + col], L5 = stg[(320 + r) * kEpiPitch + col];
+          // exact levels by two-sums, rounded tail on top
+          float sm = L0 + L1;
+          float bp = sm - L0;
+          const float e1 = (L0 - (sm - bp)) + (L1 - bp);
+          const float s1 = sm;
+          sm = s1 + L2;
+          bp = sm - s1;
+          const float e2 = (s1 - (sm - bp)) + (L2 - bp);
+          const float lo = (e1 + e2) + (L3 + (L4 + L5));
+          const double val = static_cast<double>(sm) + static_cast<double>(lo);
+          int ri = i, rj = j;
+          double sgn = 1.0;
+          if (o <= 1) {
+            if (i > j) continue;
+          } else {
+            if (i == j) continue;
+            if (i > j) { ri = j; rj = i; sgn = -1.0; }
+          }
+          const int off = __ldg(idx + ri * nb + rj);
+          if (off >= 0) atomicAdd(out + off, sgn * val);
         }
-        const int ii = G.fn_info[f0 + ri], jj = G.fn_info[f0 + rj];
-        const int ai = ii >> 16, ki = ii & 0xffff, aj = jj >> 16, kj = jj & 0xffff;
-        const int64_t off = G.pair_off[pp + static_cast<int64_t>(ai) * na + aj];
-        if (off < 0) continue;
-        atomicAdd(out + off + static_cast<int64_t>(ki) * local_nf(B, G, a0, aj) + kj, sgn * val);
+        bar_sync(3 + eg, 128);
       }
-      __syncthreads();
+      tc_fence_before();
+      mbar_arrive(accempty_bar(set));
     }
-    tc_fence_before();
-    __syncthreads();
-  }
-  // on an expired wait give in-flight MMAs one more bounded chance before freeing TMEM
-  if (!ok) {
-    for (int d = 0; d < 2; ++d)
-      if (pending[d]) (void)__syncthreads_and(mbar_wait(bar_addr[d], ph[d], status));
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == 0)
+  if (warp == kMmaWarp)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
 }
 
@@ -349,7 +434,6 @@ q4c_status integrate_split(const q4c_tables* t, const q4c_grid* g, const double*
   double* outs[5] = {out->V, out->W0, out->SOx, out->SOy, out->SOz};
   for (double* o : outs) Q4C_CUDA(cudaMemsetAsync(o, 0, sizeof(double) * g->nnz, s));
   const int n_waves = static_cast<int>(g->wave_b0.size()) - 1;
-  Q4C_CUDA(cudaMemsetAsync(g->d_counter, 0, sizeof(int) * std::max(n_waves, 1), s));
   Q4C_CUDA(cudaFuncSetAttribute(split::k_split_products, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 split::kSmemTotal));
   int dev = 0, n_sm = 0;
@@ -362,11 +446,11 @@ q4c_status integrate_split(const q4c_tables* t, const q4c_grid* g, const double*
     const int64_t i0 = g->split_w0[wv], i1 = g->split_w0[wv + 1];
     const int n_items = static_cast<int>(i1 - i0);
     if (n_items == 0) continue;
-    const int grid = std::min(n_items, 2 * n_sm);
+    const int grid = std::min(n_items, n_sm);
     {
       KernelScope ks("split_products", s);
       split::k_split_products<<<grid, split::kThreads, split::kSmemTotal, s>>>(
-          t->view(), g->view(), g->d_split_items + i0, n_items, g->d_counter + wv, g->d_scr_off, g->d_scratch,
+          t->view(), g->view(), g->d_split_items + i0, n_items, g->d_scr_off, g->d_scratch,
           g->d_colexp, v, out->V, out->W0, out->SOx, out->SOy, out->SOz, g->d_status);
     }
     Q4C_CUDA(cudaGetLastError());
