@@ -42,12 +42,9 @@ constexpr int kStage = kStageA + kBlockB;            // 26 KB
 constexpr int kStages = 4;
 constexpr int kRaw = 4;                               // ring of raw F values (cp.async)
 constexpr int kRawStage = kSlicers * kUnits * 2 * 8;  // 8 KB
-constexpr int kEpiPitch = 17;
-constexpr int kEpiStage = 3 * 128 * kEpiPitch * 4;  // 26 KB per epilogue group
 constexpr int kSmemStages = 0;
 constexpr int kSmemRaw = kSmemStages + kStages * kStage;
-constexpr int kSmemEpi = kSmemRaw + kRaw * kRawStage;
-constexpr int kSmemMag = kSmemEpi + 2 * kEpiStage;  // [4][64] rounding constants per point
+constexpr int kSmemMag = kSmemRaw + kRaw * kRawStage;  // [4][64] rounding constants per point
 constexpr int kSmemY = kSmemMag + 4 * kTile * 4;    // [4][64] double partials per point
 constexpr int kSmemBar = kSmemY + 4 * kTile * 8;
 constexpr int kNumBars = 2 * kStages + 5;  // full[S], empty[S], accfull[2], accempty[2], drain
@@ -61,19 +58,17 @@ struct Product {
   float factor;
 };
 
-// (F quantity, G matrix, R quantity, factor); matrices 2-4 enter through their
-// antisymmetric parts, which the pre-pass slices
-__device__ __forceinline__ Product product_of(int mode, int k) {
-  if (mode == 0) return {0, 0, 0, 1.0f};
-  switch (k) {
-    case 0: return {0, 0, 0, 1.0f};
-    case 1: return {1, 1, 1, 1.0f};
-    case 2: return {2, 1, 2, 1.0f};
-    case 3: return {3, 1, 3, 1.0f};
-    case 4: return {2, 2, 3, 2.0f};
-    case 5: return {3, 3, 1, 2.0f};
-    default: return {1, 4, 2, 2.0f};
-  }
+// (F quantity, G matrix, R quantity, factor) of adjoint product k, packed one
+// byte per product (qf | gm << 2 | qr << 5 | (factor == 2) << 7) so that the
+// lookup stays in registers; matrices 2-4 enter through their antisymmetric
+// parts, which the pre-pass slices.  The density is product 0.
+constexpr uint64_t kProducts = 0x00ull | (0x25ull << 8) | (0x46ull << 16) | (0x67ull << 24) | (0xEAull << 32) |
+                               (0xAFull << 40) | (0xD1ull << 48);
+
+__device__ __forceinline__ Product product_of(int k) {
+  const unsigned c = static_cast<unsigned>(kProducts >> (8 * k)) & 0xFFu;
+  return {static_cast<int>(c & 3u), static_cast<int>((c >> 2) & 7u), static_cast<int>((c >> 5) & 3u),
+          (c >> 7) ? 2.0f : 1.0f};
 }
 
 // FP32-pair copy of an FP64 matrix: x = hi + lo within 2^-48 relative
@@ -193,6 +188,21 @@ __device__ __forceinline__ ItemInfo item_info(const DevGrid& G, int2 it) {
   return I;
 }
 
+// position in an item's step sequence (j-tile, product, i-chunk), advanced
+// without divisions
+struct StepIter {
+  int ic = 0, kk = 0, jt = 0;
+  __device__ __forceinline__ void next(int n_ic, int n_prod) {
+    if (++ic == n_ic) {
+      ic = 0;
+      if (++kk == n_prod) {
+        kk = 0;
+        ++jt;
+      }
+    }
+  }
+};
+
 // One work item = (batch, 64-point tile); its groups (j-tile, product) run
 // in order, each a K-loop over the functions i.  Warp roles as in the
 // integration kernel:
@@ -203,9 +213,10 @@ __device__ __forceinline__ ItemInfo item_info(const DevGrid& G, int2 it) {
 //   warp 16     (one thread) issues the twelve MMAs per step into the group's
 //               accumulator set (groups alternate between two sets), commits
 //               empty[stage] and, after the group's last step, accfull[set];
-//   warps 8-15  combine the six levels of U, dot each column with R (a point
-//               per thread, double-float), keep a running sum per point over
-//               the item's groups and write the point's result at the end.
+//   warps 8-15  read U's levels from tensor memory, dot each column with R
+//               (a lane per thread, double-float), keep a running sum per lane
+//               over the item's groups and write each point's result at the
+//               end of the item.
 // Every wait is bounded; a timeout sets the status bit and an abort flag.
 template <int MODE>  // 0: density, 1: adjoint
 __global__ void __launch_bounds__(kThreads, 1)
@@ -228,12 +239,12 @@ __global__ void __launch_bounds__(kThreads, 1)
   auto accfull_bar = [&](int set) { return bar0 + 8u * (2 * kStages + set); };
   auto accempty_bar = [&](int set) { return bar0 + 8u * (2 * kStages + 2 + set); };
   const uint32_t drain_bar = bar0 + 8u * (2 * kStages + 4);
-  // products whose matrix is present, in order
-  const int n_prod_all = MODE == 0 ? 1 : 7;
-  int prods[7];
+  // the products whose matrix is present, in order, 3 bits each (registers only)
+  unsigned plist = 0;
   int n_prod = 0;
-  for (int k = 0; k < n_prod_all; ++k)
-    if (present & (1u << product_of(MODE, k).gm)) prods[n_prod++] = k;
+  for (int k = 0; k < (MODE == 0 ? 1 : 7); ++k)
+    if (present & (1u << product_of(k).gm)) plist |= static_cast<unsigned>(k) << (3 * n_prod++);
+  auto prod_at = [&](int kk) { return product_of(static_cast<int>((plist >> (3 * kk)) & 7u)); };
 
   for (int i = tid; i < kStages * kTileBytes / 16; i += kThreads) {  // tile Z of every stage
     const int st = i / (kTileBytes / 16), off = i - st * (kTileBytes / 16);
@@ -278,11 +289,12 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       bar_sync(1, kSlicers);
       const unsigned char* gblk = gsl + gsl_off[I.b];
-      const int n_steps = I.n_jt * n_prod * I.n_ic;  // step s -> group s / n_ic, chunk s mod n_ic
-      auto issue = [&](int s, uint32_t raw) {
-        const int grp = s / I.n_ic, ic = s - grp * I.n_ic;
-        const Product P = product_of(MODE, prods[grp % n_prod]);
-        const int i0 = ic * kKc;
+      const int n_steps = I.n_jt * n_prod * I.n_ic;
+      // the raw copies of step t (t = s + 3): (j-tile, product, chunk) advanced incrementally
+      StepIter it_issue;
+      auto issue = [&](uint32_t raw) {
+        const int qf = prod_at(it_issue.kk).qf;
+        const int i0 = it_issue.ic * kKc;
 #pragma unroll
         for (int k = 0; k < kUnits; ++k) {
           const int u = warp + (kSlicers / 32) * k;
@@ -291,32 +303,32 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
           for (int h = 0; h < 2; ++h) {
             const bool live = p < I.np && i + h < I.nb;
-            const float2* src = live ? base + P.qf * I.plane + static_cast<int64_t>(i + h) * I.ldp + p : base;
+            const float2* src = live ? base + qf * I.plane + static_cast<int64_t>(i + h) * I.ldp + p : base;
             cp_async8(raw + ((k * 2 + h) * kSlicers + tid) * 8, src, live ? 8 : 0);
           }
         }
+        it_issue.next(I.n_ic, n_prod);
       };
 #pragma unroll
       for (int q = 0; q < kRaw - 1; ++q) {
-        if (q < n_steps) issue(q, raw0 + q * kRawStage);
+        if (q < n_steps) issue(raw0 + q * kRawStage);
         cp_async_commit();
       }
+      StepIter it;
       for (int s = 0; s < n_steps; ++s, ++g) {
         const int sa = s + kRaw - 1;
-        if (sa < n_steps) issue(sa, raw0 + (sa % kRaw) * kRawStage);
+        if (sa < n_steps) issue(raw0 + (sa % kRaw) * kRawStage);
         cp_async_commit();
         const int st = g % kStages;
         if (!mbar_wait_abort(empty_bar(st), ((g / kStages) & 1) ^ 1, s_abort, status)) {
           ok = false;
           break;
         }
-        const int grp = s / I.n_ic, ic = s - grp * I.n_ic;
-        const int jt = grp / n_prod;
-        const Product P = product_of(MODE, prods[grp % n_prod]);
+        const Product P = prod_at(it.kk);
         unsigned char* sA = smem + kSmemStages + st * kStage;
         if (tid == 0) {  // this step's G' digits: one 12 KB block
           const unsigned char* src =
-              gblk + (static_cast<int64_t>(P.gm) * I.n_jt * I.n_ic + static_cast<int64_t>(jt) * I.n_ic + ic) *
+              gblk + (static_cast<int64_t>(P.gm) * I.n_jt * I.n_ic + static_cast<int64_t>(it.jt) * I.n_ic + it.ic) *
                          kBlockB;
           expect_tx(full_bar(st), kBlockB);
           bulk_copy(smem_u32(sA + kStageA), src, kBlockB, full_bar(st));
@@ -341,6 +353,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         fence_async_smem();
         mbar_arrive(full_bar(st));
+        it.next(I.n_ic, n_prod);
       }
       cp_async_wait<0>();
     }
@@ -397,70 +410,74 @@ __global__ void __launch_bounds__(kThreads, 1)
     __syncwarp();
   } else {
     // ---------------------------------------------------------- epilogue
-    const int eg = (warp - kEpiWarp0) >> 2;  // column group
-    const int et = (warp & 3) * 32 + lane;   // TMEM lane 0..127
-    const uint32_t lane_base = static_cast<uint32_t>((warp & 3) * 32) << 16;
-    float* stg = reinterpret_cast<float*>(smem + kSmemEpi) + eg * (kEpiStage / 4);
-    const int r = et & 63, half = et >> 6;  // combine phase: point r, columns half*8 .. half*8+7
+    // Thread = one TMEM lane: lanes 0-63 hold levels 0, 2, 4 and lanes 64-127
+    // levels 1, 3, 5 of the same 64 points.  The dot with R is linear in the
+    // levels, so each lane keeps its own double-float partial sum; the two
+    // halves and the two column groups meet once per item.
+    const int eg = (warp - kEpiWarp0) >> 2;  // column group: 8-column chunks eg, eg + 2, ...
+    const int quarter = warp & 3;            // TMEM lanes 32 quarter .. +31
+    const int r = (quarter & 1) * 32 + lane, lvl = quarter >> 1;
+    const uint32_t lane_base = static_cast<uint32_t>(quarter * 32) << 16;
     int k = 0;
     bool ok = true;
     for (int n = blockIdx.x; n < n_items && ok; n += gridDim.x) {
       const ItemInfo I = item_info(G, items[n]);
       const float2* base = reinterpret_cast<const float2*>(scratch) + scr_off[I.b];
       const int p = I.pt * kTile + r;
+      const bool live = p < I.np;
       df y = {0.f, 0.f};
+      int kk = 0, jt = 0;
       for (int grp = 0; grp < I.n_jt * n_prod; ++grp, ++k) {
         const int set = k & 1;
+        const int j0 = jt * kTile;
+        const Product P = prod_at(kk);
+        const int N = (min(kTile, I.nb - j0) + 15) & ~15;
+        const float2* Rrow = base + P.qr * I.plane + p;
+        // R of this thread's point, 8 columns per chunk; the first chunk's
+        // values load while the MMAs finish, later ones one chunk ahead
+        auto load_R = [&](int c0, float2* R) {
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            const int j = j0 + c0 + i;
+            R[i] = (live && j < I.nb) ? __ldg(Rrow + static_cast<int64_t>(j) * I.ldp) : make_float2(0.f, 0.f);
+          }
+        };
+        float2 Rc[8], Rn[8];
+        if (eg * 8 < N) load_R(eg * 8, Rc);
         ok = mbar_wait_abort(accfull_bar(set), (k >> 1) & 1, s_abort, status, 256);
         if (bar_red_or(2, kEpiThreads, !ok)) {
           ok = false;
           break;
         }
         tc_fence_after();
-        const int jt = grp / n_prod, j0 = jt * kTile;
-        const Product P = product_of(MODE, prods[grp % n_prod]);
-        const int N = (min(kTile, I.nb - j0) + 15) & ~15;
-        const float2* Rrow = base + P.qr * I.plane + p;
-        for (int c0 = eg * 16; c0 < N; c0 += 32) {
+        for (int c0 = eg * 8; c0 < N; c0 += 16) {
+          if (c0 + 16 < N) load_R(c0 + 16, Rn);
+          float v0[8], v1[8], v2[8];
+          tmem_ld8(tmem + lane_base + set * kSetCols + c0, v0);
+          tmem_ld8(tmem + lane_base + set * kSetCols + kTile + c0, v1);
+          tmem_ld8(tmem + lane_base + set * kSetCols + 2 * kTile + c0, v2);
 #pragma unroll
-          for (int blk = 0; blk < 3; ++blk) {
-            float vv[16];
-            tmem_ld16(tmem + lane_base + set * kSetCols + blk * kTile + c0, vv);
+          for (int i = 0; i < 8; ++i) {
+            // top: L0 + L2 + L4 (L0, L2 exact); bottom: L1 + L3 + L5 (L1 exact)
+            const df u = df_add(two_sum(v0[i], v1[i]), df{v2[i], 0.f});
+            const df pr = df_mul(df{Rc[i].x, Rc[i].y}, u);
+            y = df_add(y, df{P.factor * pr.hi, P.factor * pr.lo});  // factor 1 or 2: exact
+          }
 #pragma unroll
-            for (int i = 0; i < 16; ++i) stg[(blk * 128 + et) * kEpiPitch + i] = vv[i];
-          }
-          bar_sync(3 + eg, 128);
-          if (p < I.np) {
-#pragma unroll 2
-            for (int cc = 0; cc < 8; ++cc) {
-              const int col = half * 8 + cc, j = j0 + c0 + col;
-              if (j >= I.nb) break;
-              const float L0 = stg[r * kEpiPitch + col], L1 = stg[(r + 64) * kEpiPitch + col];
-              const float L2 = stg[(128 + r) * kEpiPitch + col], L3 = stg[(192 + r) * kEpiPitch + col];
-              const float L4 = stg[(256 + r) * kEpiPitch + col], L5 = stg[(320 + r) * kEpiPitch + col];
-              float sm = L0 + L1;
-              float bp = sm - L0;
-              const float e1 = (L0 - (sm - bp)) + (L1 - bp);
-              const float s1 = sm;
-              sm = s1 + L2;
-              bp = sm - s1;
-              const float e2 = (s1 - (sm - bp)) + (L2 - bp);
-              const float lo = (e1 + e2) + (L3 + (L4 + L5));
-              const float2 Rv = __ldg(Rrow + static_cast<int64_t>(j) * I.ldp);
-              const df prod = df_mul(df{Rv.x, Rv.y}, fast_two_sum(sm, lo));
-              y = df_add(y, df{P.factor * prod.hi, P.factor * prod.lo});  // factor 1 or 2: exact
-            }
-          }
-          bar_sync(3 + eg, 128);
+          for (int i = 0; i < 8; ++i) Rc[i] = Rn[i];
         }
         tc_fence_before();
         mbar_arrive(accempty_bar(set));
+        if (++kk == n_prod) {
+          kk = 0;
+          ++jt;
+        }
       }
       if (!ok) break;
-      // the four partial sums of each point (two column halves x two groups)
-      sY[(eg * 2 + half) * kTile + r] = static_cast<double>(y.hi) + static_cast<double>(y.lo);
+      // the four partial sums of each point (two level halves x two column groups)
+      sY[(eg * 2 + lvl) * kTile + r] = static_cast<double>(y.hi) + static_cast<double>(y.lo);
       bar_sync(2, kEpiThreads);
-      if (eg == 0 && half == 0 && p < I.np) {
+      if (eg == 0 && lvl == 0 && live) {
         const double val = (sY[r] + sY[kTile + r]) + (sY[2 * kTile + r] + sY[3 * kTile + r]);
         const int64_t gp = I.bp0 + p;
         out[gp] = MODE == 0 ? val : G.w[gp] * val;

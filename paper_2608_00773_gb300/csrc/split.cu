@@ -80,22 +80,24 @@ constexpr uint32_t kTmemCols = 512;  // two accumulator sets of three 64-column 
 constexpr uint32_t kSetCols = 256;
 
 // ------------------------------------------------------------ kernel
+// The products of one output, in registers: n of them, the A-side (D-scaled)
+// and B-side quantities of product pr in bits 2pr..2pr+1 of qa and qb
+// (0 Phi, 1 X, 2 Y, 3 Z).
 struct Products {
   int n;
-  int qa[kMaxProducts];  // A-side (D-scaled) quantity: 0 Phi, 1 X, 2 Y, 3 Z
-  int qb[kMaxProducts];  // B-side quantity
+  unsigned qa, qb;
+  __device__ __forceinline__ int a(int pr) const { return static_cast<int>((qa >> (2 * pr)) & 3u); }
+  __device__ __forceinline__ int b(int pr) const { return static_cast<int>((qb >> (2 * pr)) & 3u); }
 };
 
 __device__ __forceinline__ Products products_of(int o) {
-  Products P;
   switch (o) {
-    case 0: P.n = 1; P.qa[0] = 0; P.qb[0] = 0; break;              // V
-    case 1: P.n = 3; P.qa[0] = 1; P.qb[0] = 1; P.qa[1] = 2; P.qb[1] = 2; P.qa[2] = 3; P.qb[2] = 3; break;  // W0
-    case 2: P.n = 1; P.qa[0] = 2; P.qb[0] = 3; break;              // A_yz -> SO_x
-    case 3: P.n = 1; P.qa[0] = 3; P.qb[0] = 1; break;              // A_zx -> SO_y
-    default: P.n = 1; P.qa[0] = 1; P.qb[0] = 2; break;             // A_xy -> SO_z
+    case 0: return {1, 0u, 0u};                // V
+    case 1: return {3, 0x39u, 0x39u};          // W0: (X, X), (Y, Y), (Z, Z)
+    case 2: return {1, 2u, 3u};                // A_yz -> SO_x
+    case 3: return {1, 3u, 1u};                // A_zx -> SO_y
+    default: return {1, 1u, 2u};               // A_xy -> SO_z
   }
-  return P;
 }
 
 __device__ __forceinline__ int local_nf(const DevBasis& B, const DevGrid& G, int a0, int a) {
@@ -114,11 +116,11 @@ __device__ __forceinline__ int item_steps(const DevGrid& G, int4 item) {
 __device__ __forceinline__ void issue_step(const float2* base, int64_t plane, int ldp, int np, int nb, int i0,
                                            int j0, const Products& P, int s, int warp, int lane, int tid,
                                            uint32_t raw) {
-  const int c = s / P.n, pr = s - c * P.n;
+  const int c = P.n == 1 ? s : s / 3, pr = s - c * P.n;
   const int kc0 = c * kKc;
 #pragma unroll
   for (int side = 0; side < 2; ++side) {
-    const int q = side == 0 ? P.qa[pr] : P.qb[pr];
+    const int q = side == 0 ? P.a(pr) : P.b(pr);
     const int row0 = side == 0 ? i0 : j0;
 #pragma unroll
     for (int k = 0; k < kUnits; ++k) {
@@ -232,8 +234,8 @@ __global__ void __launch_bounds__(kThreads, 1)
           if (i0 + r < nb) ea = max(cexp[1 * nb + i0 + r], max(cexp[2 * nb + i0 + r], cexp[3 * nb + i0 + r]));
           if (j0 + r < nb) eb = max(cexp[5 * nb + j0 + r], max(cexp[6 * nb + j0 + r], cexp[7 * nb + j0 + r]));
         } else {
-          if (i0 + r < nb) ea = cexp[P.qa[0] * nb + i0 + r];
-          if (j0 + r < nb) eb = cexp[(4 + P.qb[0]) * nb + j0 + r];
+          if (i0 + r < nb) ea = cexp[P.a(0) * nb + i0 + r];
+          if (j0 + r < nb) eb = cexp[(4 + P.b(0)) * nb + j0 + r];
         }
         sMagA[r] = magic0(ea);
         sMagB[r] = magic0(eb);
@@ -269,7 +271,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           ok = false;
           break;
         }
-        const int c = s / P.n;
+        const int c = P.n == 1 ? s : s / 3;
         const int kc0 = c * kKc;
         unsigned char* sA = smem + kSmemStages + st * kStage;
         unsigned char* sB = sA + kStageA;
