@@ -106,7 +106,7 @@ __global__ void __launch_bounds__(256) k_gslice(DevGrid G, int64_t b0, int anti_
                                                 const float2* M1, const float2* M2, const float2* M3,
                                                 const float2* M4, const int64_t* __restrict__ gsl_off,
                                                 uint32_t* __restrict__ gsl) {
-  __shared__ float sMag[kMaxNb];
+  __shared__ unsigned sMax[kMaxNb];  // bits of max_i |hi(G'_ij)| (non-negative floats order as integers)
   const int64_t b = b0 + blockIdx.x;
   const int m = blockIdx.y;
   const float2* mats[5] = {M0, M1, M2, M3, M4};
@@ -117,12 +117,19 @@ __global__ void __launch_bounds__(256) k_gslice(DevGrid G, int64_t b0, int anti_
   const int* idx = G.bat_idx + G.bat_idx_ptr[b];
   const int n_jt = (nb + kTile - 1) / kTile, n_ic = (nb + kKc - 1) / kKc;
   uint32_t* out = gsl + (gsl_off[b] + static_cast<int64_t>(m) * n_jt * n_ic * kBlockB) / 4;
-  for (int j = threadIdx.x; j < nb; j += blockDim.x) {
-    float mx = 0.f;
-    for (int i = 0; i < nb; ++i) mx = fmaxf(mx, fabsf(gprime_df(M, idx, nb, anti, i, j).hi));
-    sMag[j] = magic0(mx > 0.f ? fexp(mx) : -30000);
+  for (int j = threadIdx.x; j < nb; j += blockDim.x) sMax[j] = 0u;
+  __syncthreads();
+  // pass 1: column maxima, element-parallel (pairs (i, i+1) of one column per thread step)
+  const int half = (nb + 1) / 2;
+  for (int e = threadIdx.x; e < nb * half; e += blockDim.x) {
+    const int j = e / half, i = 2 * (e - j * half);
+    const float h0 = fabsf(gprime_df(M, idx, nb, anti, i, j).hi);
+    const float h1 = i + 1 < nb ? fabsf(gprime_df(M, idx, nb, anti, i + 1, j).hi) : 0.f;
+    const float mx = fmaxf(h0, h1);
+    if (mx > 0.f) atomicMax(&sMax[j], __float_as_uint(mx));
   }
   __syncthreads();
+  // pass 2: the six digits of every element, in the B-operand tile layout
   const int words = n_jt * n_ic * (kTileBytes / 4);  // word positions (one per element pair)
   for (int w = threadIdx.x; w < words; w += blockDim.x) {
     const int blk = w / (kTileBytes / 4), pos = w - blk * (kTileBytes / 4);
@@ -132,7 +139,8 @@ __global__ void __launch_bounds__(256) k_gslice(DevGrid G, int64_t b0, int anti_
     const int j = jt * kTile + rg * 8 + r8, i = ic * kKc + kq * 8 + kp * 2;
     float d0[kSlices], d1[kSlices];
     if (j < nb) {
-      const float m0 = sMag[j];
+      const unsigned mb = sMax[j];
+      const float m0 = magic0(mb ? fexp(__uint_as_float(mb)) : -30000);
       const df x0 = i < nb ? gprime_df(M, idx, nb, anti, i, j) : df{0.f, 0.f};
       const df x1 = i + 1 < nb ? gprime_df(M, idx, nb, anti, i + 1, j) : df{0.f, 0.f};
       slice6(x0.hi, x0.lo, m0, d0);
