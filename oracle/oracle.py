@@ -40,6 +40,7 @@ class _Basis(C.Structure):
         ("n_species", C.c_int), ("n_rad", C.c_void_p), ("rad_l", C.c_void_p), ("rad_alpha", C.c_void_p),
         ("n_log", C.c_int), ("r_min", C.c_double), ("r_c", C.c_double), ("r_on", C.c_double),
         ("tab_u", C.c_void_p), ("tab_M", C.c_void_p), ("analytic", C.c_int),
+        ("lattice", C.c_void_p), ("n_shell", C.c_int),
     ]
 
 
@@ -71,16 +72,19 @@ def lib() -> C.CDLL:
             L.orc_grid.argtypes = [C.c_int, _dp, C.c_int, C.c_double, C.c_int, C.c_int, C.c_double,
                                    C.c_double, C.c_longlong, _dp, _dp, _lp]
             L.orc_grid.restype = C.c_long
-            L.orc_pattern.argtypes = [bp, C.c_void_p, C.c_void_p, C.c_void_p]
+            L.orc_grid_cell.argtypes = [C.c_int, _dp, C.c_void_p, C.c_int, C.c_int, C.c_double, C.c_int,
+                                        C.c_int, C.c_double, C.c_double, C.c_longlong, _dp, _dp, _lp]
+            L.orc_grid_cell.restype = C.c_long
+            L.orc_pattern.argtypes = [bp, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
             L.orc_pattern.restype = C.c_long
             L.orc_matrix_pairs.argtypes = [bp, C.c_long, _dp, _dp, _dp, C.c_long, _ip, _ip,
                                            _dp, _dp, _dp, _dp, _dp]
-            L.orc_matrix_blocks.argtypes = [bp, C.c_long, _dp, _dp, _dp, _lp, _ip, _lp,
+            L.orc_matrix_blocks.argtypes = [bp, C.c_long, _dp, _dp, _dp, _lp, _ip, _ip, _lp,
                                             _dp, _dp, _dp, _dp, _dp]
             L.orc_matrix_blocks.restype = C.c_int
-            L.orc_density.argtypes = [bp, C.c_long, _dp, _lp, _ip, _lp, _dp, _dp]
+            L.orc_density.argtypes = [bp, C.c_long, _dp, _lp, _ip, _ip, _lp, _dp, _dp]
             vp = C.c_void_p
-            L.orc_adjoint.argtypes = [bp, C.c_long, _dp, _dp, _lp, _ip, _lp, vp, vp, vp, vp, vp, _dp]
+            L.orc_adjoint.argtypes = [bp, C.c_long, _dp, _dp, _lp, _ip, _ip, _lp, vp, vp, vp, vp, vp, _dp]
             L.orc_spinor_ss.argtypes = [bp, _lp, _ip, _lp, _dp, _dp, _dp, _dp, _dp]
             _lib = L
         return _lib
@@ -149,11 +153,14 @@ def becke_weight(centres: np.ndarray, owner: int, p, r_nb: float = 1e300) -> flo
 
 def grid(wl, stride: int = 1):
     """Kept grid points of a workload: (xyz (n,3), w (n,), raw id (n,)).
-    stride > 1 evaluates only the raw points whose id is a multiple of it."""
+    stride > 1 evaluates only the raw points whose id is a multiple of it.
+    A periodic workload (wl.lattice set) partitions over the atoms' images too."""
     n_raw = (wl.n_raw_points + stride - 1) // stride
     xyz = np.zeros(3 * n_raw); w = np.zeros(n_raw); ids = np.zeros(n_raw, dtype=np.int64)
-    n = lib().orc_grid(wl.n_atoms, _f64(wl.xyz).reshape(-1), wl.n_rad, wl.R, wl.n_theta, wl.n_phi,
-                       wl.r_c, wl.r_nb, stride, xyz, w, ids)
+    lat = None if wl.lattice is None else _f64(wl.lattice).reshape(-1)
+    n = lib().orc_grid_cell(wl.n_atoms, _f64(wl.xyz).reshape(-1), None if lat is None else lat.ctypes.data,
+                            wl.n_shell, wl.n_rad, wl.R, wl.n_theta, wl.n_phi, wl.r_c, wl.r_nb, stride, xyz, w,
+                            ids)
     return xyz[:3 * n].reshape(n, 3).copy(), w[:n].copy(), ids[:n].copy()
 
 
@@ -162,12 +169,15 @@ def grid(wl, stride: int = 1):
 # --------------------------------------------------------------------------
 
 class Pattern:
-    """CSR block pattern over atoms: block (A, B) iff |R_A - R_B| < 2 r_c."""
+    """CSR block pattern over atoms: block (A, B, T) iff |R_A - R_B - T.L| < 2 r_c
+    (T = 0 for a molecule); blk_T holds the integer shifts, [n_blocks][3]."""
 
-    def __init__(self, blk_ptr, blk_col, blk_off):
+    def __init__(self, blk_ptr, blk_col, blk_off, blk_T=None):
         self.blk_ptr = blk_ptr
         self.blk_col = blk_col
         self.blk_off = blk_off
+        self.blk_T = (np.zeros((len(blk_col), 3), np.int32) if blk_T is None
+                      else np.ascontiguousarray(blk_T, np.int32).reshape(-1, 3))
 
     @property
     def nnz(self) -> int:
@@ -190,10 +200,12 @@ class OracleBasis:
         for k in range(nr):
             r, u, M = tabulate(int(self._l[k]), float(self._alpha[k]), wl.n_log, wl.r_min, wl.r_c, wl.r_on)
             self.tab_r[k] = r; self.tab_u[k] = u; self.tab_M[k] = M
+        self._lat = None if wl.lattice is None else _f64(wl.lattice).reshape(-1)
         self.s = _Basis(wl.n_atoms, self._xyz.ctypes.data, self._species.ctypes.data, len(wl.species),
                         self._n_rad.ctypes.data, self._l.ctypes.data, self._alpha.ctypes.data, wl.n_log,
                         wl.r_min, wl.r_c, wl.r_on, self.tab_u.ctypes.data, self.tab_M.ctypes.data,
-                        1 if analytic else 0)
+                        1 if analytic else 0, None if self._lat is None else self._lat.ctypes.data,
+                        wl.n_shell)
         self.n_fn = lib().orc_count_functions(C.byref(self.s))
         self.fn_atom = np.zeros(self.n_fn, np.int32); self.fn_rad = np.zeros(self.n_fn, np.int32)
         self.fn_l = np.zeros(self.n_fn, np.int32); self.fn_m = np.zeros(self.n_fn, np.int32)
@@ -208,11 +220,11 @@ class OracleBasis:
         return phi.reshape(len(fns), len(pts)), grad.reshape(len(fns), len(pts), 3)
 
     def pattern(self) -> Pattern:
-        nb = lib().orc_pattern(C.byref(self.s), None, None, None)
+        nb = lib().orc_pattern(C.byref(self.s), None, None, None, None)
         ptr = np.zeros(self.wl.n_atoms + 1, np.int64); col = np.zeros(max(nb, 1), np.int32)
-        off = np.zeros(nb + 1, np.int64)
-        lib().orc_pattern(C.byref(self.s), ptr.ctypes.data, col.ctypes.data, off.ctypes.data)
-        return Pattern(ptr, col[:nb].copy(), off)
+        T = np.zeros(3 * max(nb, 1), np.int32); off = np.zeros(nb + 1, np.int64)
+        lib().orc_pattern(C.byref(self.s), ptr.ctypes.data, col.ctypes.data, T.ctypes.data, off.ctypes.data)
+        return Pattern(ptr, col[:nb].copy(), off, T[:3 * nb].copy())
 
     def matrix_pairs(self, xyz, w, v, pi, pj):
         """V, W0, SOx, SOy, SOz at listed (i, j) pairs (Eqs. 29-30 + the SS reading)."""
@@ -227,7 +239,7 @@ class OracleBasis:
         xyz = _f64(xyz).reshape(-1); w = _f64(w); v = _f64(v)
         outs = [np.zeros(pat.nnz) for _ in range(5)]
         miss = lib().orc_matrix_blocks(C.byref(self.s), len(w), xyz, w, v, pat.blk_ptr, pat.blk_col,
-                                       pat.blk_off, *outs)
+                                       pat.blk_T.reshape(-1), pat.blk_off, *outs)
         if miss:
             raise RuntimeError("active atom pair outside the block pattern")
         return outs
@@ -236,7 +248,8 @@ class OracleBasis:
         """n_p = sum_ij P_ij phi_i phi_j (Eqs. 39-40)."""
         xyz = _f64(xyz).reshape(-1)
         n = np.zeros(len(xyz) // 3)
-        lib().orc_density(C.byref(self.s), len(n), xyz, pat.blk_ptr, pat.blk_col, pat.blk_off, _f64(P), n)
+        lib().orc_density(C.byref(self.s), len(n), xyz, pat.blk_ptr, pat.blk_col, pat.blk_T.reshape(-1),
+                          pat.blk_off, _f64(P), n)
         return n
 
     def adjoint(self, xyz, w, G, pat: Pattern):
@@ -245,8 +258,8 @@ class OracleBasis:
         keep = [None if g is None else _f64(g) for g in G]
         ptrs = [None if g is None else g.ctypes.data for g in keep]
         out = np.zeros(len(w))
-        lib().orc_adjoint(C.byref(self.s), len(w), xyz, w, pat.blk_ptr, pat.blk_col, pat.blk_off,
-                          *ptrs, out)
+        lib().orc_adjoint(C.byref(self.s), len(w), xyz, w, pat.blk_ptr, pat.blk_col, pat.blk_T.reshape(-1),
+                          pat.blk_off, *ptrs, out)
         return out
 
     def spinor_ss(self, W0, SOx, SOy, SOz, pat: Pattern):

@@ -286,7 +286,47 @@ typedef struct {
   const double* tab_u;      /* [sum n_rad][n_log] knot values (spline mode) */
   const double* tab_M;      /* [sum n_rad][n_log] second derivatives */
   int analytic;             /* 1: u = r^(l+1) exp(-alpha r^2), no cutoff (closed-form pins) */
+  const double* lattice;    /* [3][3] lattice vectors as rows (periodic cell), NULL for a molecule */
+  int n_shell;              /* periodic images T in [-n_shell, n_shell]^3 */
 } orc_basis;
+
+/* ------------------------------------------------------------------ */
+/* centres: the atoms and, in a periodic cell, their images (Eqs. 24-25) */
+/* ------------------------------------------------------------------ */
+/* Centre c = cell * n_atoms + A, cells in lexicographic order of
+ * T = (t1, t2, t3) in [-s, s]^3 (s = n_shell; s = 0 for a molecule), at
+ * R_A + t1 a1 + t2 a2 + t3 a3. */
+static int orc_cell_side(const double* lattice, int n_shell) { return lattice ? 2 * n_shell + 1 : 1; }
+
+static void orc_cell_T(int side, int cell, int T[3]) {
+  int s = side / 2;
+  T[0] = cell / (side * side) - s;
+  T[1] = (cell / side) % side - s;
+  T[2] = cell % side - s;
+}
+
+static void orc_shift(const double* lattice, const int T[3], double out[3]) {
+  out[0] = out[1] = out[2] = 0.0;
+  if (!lattice) return;
+  for (int k = 0; k < 3; ++k)
+    for (int d = 0; d < 3; ++d) out[d] += T[k] * lattice[3 * k + d];
+}
+
+/* positions of all centres: out [side^3 * n_atoms][3]; returns their number */
+static int orc_centres(int n_atoms, const double* xyz, const double* lattice, int n_shell, double** out) {
+  int side = orc_cell_side(lattice, n_shell), nc = side * side * side * n_atoms;
+  double* c = (double*)malloc(sizeof(double) * 3 * (size_t)nc);
+  for (int cell = 0; cell < side * side * side; ++cell) {
+    int T[3];
+    double sh[3];
+    orc_cell_T(side, cell, T);
+    orc_shift(lattice, T, sh);
+    for (int A = 0; A < n_atoms; ++A)
+      for (int d = 0; d < 3; ++d) c[3 * ((size_t)cell * n_atoms + A) + d] = xyz[3 * A + d] + sh[d];
+  }
+  *out = c;
+  return nc;
+}
 
 /* Function table: atom a, radial k of its species, m = -l..l (radial-major). */
 int orc_count_functions(const orc_basis* b) {
@@ -413,22 +453,29 @@ double orc_becke_weight(int n_c, const double* centres, int owner, const double 
   return result;
 }
 
-/* Raw grid of every atom, Becke weights, pruning.
+/* Raw grid of every (0-cell) atom, Becke weights, pruning.
  * Raw point id = ((atom*n_rad + i)*n_theta + a)*n_phi + b; i radial shell
  * (ascending x_i order, i.e. decreasing r), a Gauss-Legendre node in cos(theta)
  * (ascending), b azimuth phi_b = (b + 1/2) 2 pi / n_phi.
- * Keep p iff some atom lies strictly within r_c of p and w_p != 0.
+ * The Becke partition runs over all centres (atoms and, in a periodic cell,
+ * their images) within r_nb; the owner is the generating atom in cell 0.
+ * Keep p iff some centre lies strictly within r_c of p and w_p != 0.
  * stride > 1 keeps only raw ids divisible by stride (a uniform sample used
  * to time the oracle on a bounded share of a large workload).
  * Returns the number of kept points; out arrays must hold the raw count. */
-long orc_grid(int n_atoms, const double* xyz, int n_rad, double R, int n_theta, int n_phi,
-              double r_c, double r_nb, long long stride, double* out_xyz, double* out_w, long long* out_id) {
+long orc_grid_cell(int n_atoms, const double* xyz, const double* lattice, int n_shell, int n_rad, double R,
+                   int n_theta, int n_phi, double r_c, double r_nb, long long stride, double* out_xyz,
+                   double* out_w, long long* out_id) {
   double* rr = (double*)malloc(sizeof(double) * n_rad);
   double* wr = (double*)malloc(sizeof(double) * n_rad);
   double* ct = (double*)malloc(sizeof(double) * n_theta);
   double* wt = (double*)malloc(sizeof(double) * n_theta);
   orc_radial_shells(n_rad, R, rr, wr);
   orc_gauss_legendre(n_theta, ct, wt);
+  double* cen = NULL;
+  int side = orc_cell_side(lattice, n_shell);
+  int nc = orc_centres(n_atoms, xyz, lattice, n_shell, &cen);
+  int cell0 = (side * side * side - 1) / 2; /* T = (0, 0, 0) */
   long kept = 0;
   for (int A = 0; A < n_atoms; ++A) {
     for (int i = 0; i < n_rad; ++i) {
@@ -441,12 +488,13 @@ long orc_grid(int n_atoms, const double* xyz, int n_rad, double R, int n_theta, 
           double p[3] = {xyz[3 * A] + rr[i] * st * cos(ph), xyz[3 * A + 1] + rr[i] * st * sin(ph),
                          xyz[3 * A + 2] + rr[i] * ct[a]};
           int near = 0;
-          for (int B = 0; B < n_atoms && !near; ++B) {
-            double dx = p[0] - xyz[3 * B], dy = p[1] - xyz[3 * B + 1], dz = p[2] - xyz[3 * B + 2];
+          for (int B = 0; B < nc && !near; ++B) {
+            double dx = p[0] - cen[3 * B], dy = p[1] - cen[3 * B + 1], dz = p[2] - cen[3 * B + 2];
             if (sqrt(dx * dx + dy * dy + dz * dz) < r_c) near = 1;
           }
           if (!near) continue;
-          double w = wr[i] * wt[a] * (2.0 * M_PI / n_phi) * orc_becke_weight(n_atoms, xyz, A, p, r_nb);
+          double w = wr[i] * wt[a] * (2.0 * M_PI / n_phi) *
+                     orc_becke_weight(nc, cen, cell0 * n_atoms + A, p, r_nb);
           if (w == 0.0) continue;
           out_xyz[3 * kept] = p[0]; out_xyz[3 * kept + 1] = p[1]; out_xyz[3 * kept + 2] = p[2];
           out_w[kept] = w;
@@ -456,8 +504,15 @@ long orc_grid(int n_atoms, const double* xyz, int n_rad, double R, int n_theta, 
       }
     }
   }
-  free(rr); free(wr); free(ct); free(wt);
+  free(rr); free(wr); free(ct); free(wt); free(cen);
   return kept;
+}
+
+/* the molecular grid (no lattice) */
+long orc_grid(int n_atoms, const double* xyz, int n_rad, double R, int n_theta, int n_phi,
+              double r_c, double r_nb, long long stride, double* out_xyz, double* out_w, long long* out_id) {
+  return orc_grid_cell(n_atoms, xyz, NULL, 0, n_rad, R, n_theta, n_phi, r_c, r_nb, stride, out_xyz, out_w,
+                       out_id);
 }
 
 /* ------------------------------------------------------------------ */
@@ -471,23 +526,34 @@ static int species_nfn(const orc_basis* b, int s) {
   return n;
 }
 
-/* returns number of blocks; if blk_ptr != NULL fills CSR (blk_ptr[n_atoms+1],
- * blk_col[nb], blk_off[nb+1]) */
-long orc_pattern(const orc_basis* b, long long* blk_ptr, int* blk_col, long long* blk_off) {
+/* Block (A, B, T) exists iff |R_A - R_B - T.L| < 2 r_c (strict), T an
+ * integer lattice triple in [-2s, 2s]^3 (T = 0 for a molecule): the real-space
+ * H(T) blocks <phi_(A,0)| . |phi_(B,T)> (Eqs. 24-25).  Rows A, then B, then T
+ * lexicographic.  Returns the number of blocks; if blk_ptr != NULL fills CSR
+ * (blk_ptr[n_atoms+1], blk_col[nb], blk_T[nb][3] if not NULL, blk_off[nb+1]). */
+long orc_pattern(const orc_basis* b, long long* blk_ptr, int* blk_col, int* blk_T, long long* blk_off) {
   long nb = 0;
   long long off = 0;
+  int s2 = b->lattice ? 2 * b->n_shell : 0, side = 2 * s2 + 1;
   if (blk_ptr) blk_ptr[0] = 0;
   for (int A = 0; A < b->n_atoms; ++A) {
     for (int B = 0; B < b->n_atoms; ++B) {
-      double dx = b->xyz[3 * A] - b->xyz[3 * B], dy = b->xyz[3 * A + 1] - b->xyz[3 * B + 1],
-             dz = b->xyz[3 * A + 2] - b->xyz[3 * B + 2];
-      if (sqrt(dx * dx + dy * dy + dz * dz) < 2.0 * b->r_c) {
-        if (blk_col) {
-          blk_col[nb] = B;
-          blk_off[nb] = off;
+      for (int cell = 0; cell < side * side * side; ++cell) {
+        int T[3];
+        double sh[3];
+        orc_cell_T(side, cell, T);
+        orc_shift(b->lattice, T, sh);
+        double dx = b->xyz[3 * A] - b->xyz[3 * B] - sh[0], dy = b->xyz[3 * A + 1] - b->xyz[3 * B + 1] - sh[1],
+               dz = b->xyz[3 * A + 2] - b->xyz[3 * B + 2] - sh[2];
+        if (sqrt(dx * dx + dy * dy + dz * dz) < 2.0 * b->r_c) {
+          if (blk_col) {
+            blk_col[nb] = B;
+            blk_off[nb] = off;
+            if (blk_T) { blk_T[3 * nb] = T[0]; blk_T[3 * nb + 1] = T[1]; blk_T[3 * nb + 2] = T[2]; }
+          }
+          off += (long long)species_nfn(b, b->species[A]) * species_nfn(b, b->species[B]);
+          ++nb;
         }
-        off += (long long)species_nfn(b, b->species[A]) * species_nfn(b, b->species[B]);
-        ++nb;
       }
     }
     if (blk_ptr) blk_ptr[A + 1] = nb;
@@ -520,10 +586,6 @@ static void ftab_init(const orc_basis* b, ftab* t) {
 }
 static void ftab_free(ftab* t) { free(t->fa); free(t->fr); free(t->fl); free(t->fm); free(t->afirst); }
 
-static void eval_all(const orc_basis* b, const ftab* t, const double p[3], double* phi, double* grad) {
-  for (int i = 0; i < t->nf; ++i)
-    phi_at(b, t->fr[i], t->fl[i], t->fm[i], b->xyz + 3 * t->fa[i], p, &phi[i], &grad[3 * i]);
-}
 
 /* ------------------------------------------------------------------ */
 /* matrix elements                                                      */
@@ -573,50 +635,105 @@ void orc_matrix_pairs(const orc_basis* b, long n_pts, const double* xyz, const d
   ftab_free(&t);
 }
 
-/* locate block (A,B) in the CSR pattern, -1 if absent */
-static long find_block(const long long* blk_ptr, const int* blk_col, int A, int B) {
-  for (long long q = blk_ptr[A]; q < blk_ptr[A + 1]; ++q)
-    if (blk_col[q] == B) return (long)q;
+/* locate block (A, B, T) in the CSR pattern, -1 if absent (blk_T NULL: all T = 0) */
+static long find_block(const long long* blk_ptr, const int* blk_col, const int* blk_T, int A, int B,
+                       const int T[3]) {
+  for (long long q = blk_ptr[A]; q < blk_ptr[A + 1]; ++q) {
+    if (blk_col[q] != B) continue;
+    if (!blk_T) {
+      if (T[0] == 0 && T[1] == 0 && T[2] == 0) return (long)q;
+      continue;
+    }
+    if (blk_T[3 * q] == T[0] && blk_T[3 * q + 1] == T[1] && blk_T[3 * q + 2] == T[2]) return (long)q;
+  }
   return -1;
 }
 
-/* Full matrices on the block pattern: outputs [blk_off[nb]] each. */
+/* centres within r_c of X: their indices, atoms and cells; the values and
+ * gradients of their functions at X (phi[slot*nmax + k], grad[3*(...)]) */
+typedef struct {
+  int n, nc, side, nmax;
+  double* cen;
+  int *c, *atom, *cell;
+  double *phi, *grad;
+} orc_active;
+
+static void active_init(const orc_basis* b, orc_active* a) {
+  a->side = orc_cell_side(b->lattice, b->n_shell);
+  a->nc = orc_centres(b->n_atoms, b->xyz, b->lattice, b->n_shell, &a->cen);
+  a->nmax = 0;
+  for (int A = 0; A < b->n_atoms; ++A) {
+    int nf = species_nfn(b, b->species[A]);
+    if (nf > a->nmax) a->nmax = nf;
+  }
+  a->c = (int*)malloc(sizeof(int) * a->nc);
+  a->atom = (int*)malloc(sizeof(int) * a->nc);
+  a->cell = (int*)malloc(sizeof(int) * a->nc);
+  a->phi = (double*)calloc((size_t)a->nc * a->nmax, sizeof(double));
+  a->grad = (double*)calloc(3 * (size_t)a->nc * a->nmax, sizeof(double));
+}
+static void active_free(orc_active* a) {
+  free(a->cen); free(a->c); free(a->atom); free(a->cell); free(a->phi); free(a->grad);
+}
+
+static void active_at(const orc_basis* b, const ftab* t, orc_active* a, const double X[3]) {
+  a->n = 0;
+  for (int c = 0; c < a->nc; ++c) {
+    double dx = X[0] - a->cen[3 * c], dy = X[1] - a->cen[3 * c + 1], dz = X[2] - a->cen[3 * c + 2];
+    if (sqrt(dx * dx + dy * dy + dz * dz) >= b->r_c) continue;
+    int A = c % b->n_atoms, s = a->n++;
+    a->c[s] = c; a->atom[s] = A; a->cell[s] = c / b->n_atoms;
+    for (int i = t->afirst[A]; i < t->afirst[A + 1]; ++i) {
+      int k = i - t->afirst[A];
+      phi_at(b, t->fr[i], t->fl[i], t->fm[i], a->cen + 3 * c, X, &a->phi[(size_t)s * a->nmax + k],
+             &a->grad[3 * ((size_t)s * a->nmax + k)]);
+    }
+  }
+}
+
+/* block of the centre pair (slot sa, slot sb): (A, B, T_b - T_a) */
+static long pair_block(const orc_active* a, int sa, int sb, const long long* blk_ptr, const int* blk_col,
+                       const int* blk_T) {
+  int Ta[3], Tb[3], T[3];
+  orc_cell_T(a->side, a->cell[sa], Ta);
+  orc_cell_T(a->side, a->cell[sb], Tb);
+  for (int k = 0; k < 3; ++k) T[k] = Tb[k] - Ta[k];
+  return find_block(blk_ptr, blk_col, blk_T, a->atom[sa], a->atom[sb], T);
+}
+
+/* Full matrices on the block pattern (Eqs. 29-30 with F = v and the SS
+ * reading): outputs [blk_off[nb]] each.  Every pair of centres active at a
+ * point adds into its block (A, B, T_b - T_a) (the restricted real-space sum
+ * of Eqs. 24-25; one block (A, B, 0) per pair for a molecule). */
 int orc_matrix_blocks(const orc_basis* b, long n_pts, const double* xyz, const double* w, const double* v,
-                      const long long* blk_ptr, const int* blk_col, const long long* blk_off,
+                      const long long* blk_ptr, const int* blk_col, const int* blk_T, const long long* blk_off,
                       double* V, double* W0, double* SOx, double* SOy, double* SOz) {
   ftab t;
   ftab_init(b, &t);
+  orc_active a;
+  active_init(b, &a);
   long long nnz = blk_off[blk_ptr[b->n_atoms]];
   orc_acc* acc = (orc_acc*)calloc(5 * (size_t)nnz, sizeof(orc_acc));
-  double* phi = (double*)calloc(t.nf, sizeof(double));
-  double* grad = (double*)calloc(3 * (size_t)t.nf, sizeof(double));
-  int* act = (int*)malloc(sizeof(int) * b->n_atoms);
   int missing = 0;
   for (long p = 0; p < n_pts; ++p) {
-    const double* P = xyz + 3 * p;
-    eval_all(b, &t, P, phi, grad);
-    int na = 0;
-    for (int A = 0; A < b->n_atoms; ++A) {
-      double dx = P[0] - b->xyz[3 * A], dy = P[1] - b->xyz[3 * A + 1], dz = P[2] - b->xyz[3 * A + 2];
-      if (sqrt(dx * dx + dy * dy + dz * dz) < b->r_c) act[na++] = A;
-    }
+    active_at(b, &t, &a, xyz + 3 * p);
     double wv = w[p] * v[p];
-    for (int ia = 0; ia < na; ++ia) {
-      for (int ib = 0; ib < na; ++ib) {
-        int A = act[ia], B = act[ib];
-        long q = find_block(blk_ptr, blk_col, A, B);
+    for (int sa = 0; sa < a.n; ++sa) {
+      for (int sb = 0; sb < a.n; ++sb) {
+        long q = pair_block(&a, sa, sb, blk_ptr, blk_col, blk_T);
         if (q < 0) { missing = 1; continue; }
-        int nfB = t.afirst[B + 1] - t.afirst[B];
-        for (int i = t.afirst[A]; i < t.afirst[A + 1]; ++i) {
-          for (int j = t.afirst[B]; j < t.afirst[B + 1]; ++j) {
-            long long e = blk_off[q] + (long long)(i - t.afirst[A]) * nfB + (j - t.afirst[B]);
-            const double* a = &grad[3 * i];
-            const double* c = &grad[3 * j];
-            acc_add(&acc[5 * e + 0], wv * (phi[i] * phi[j]));
-            acc_add(&acc[5 * e + 1], wv * (a[0] * c[0] + a[1] * c[1] + a[2] * c[2]));
-            acc_add(&acc[5 * e + 2], wv * (a[1] * c[2] - a[2] * c[1]));
-            acc_add(&acc[5 * e + 3], wv * (a[2] * c[0] - a[0] * c[2]));
-            acc_add(&acc[5 * e + 4], wv * (a[0] * c[1] - a[1] * c[0]));
+        int nfA = species_nfn(b, b->species[a.atom[sa]]), nfB = species_nfn(b, b->species[a.atom[sb]]);
+        for (int i = 0; i < nfA; ++i) {
+          for (int j = 0; j < nfB; ++j) {
+            long long e = blk_off[q] + (long long)i * nfB + j;
+            double pi = a.phi[(size_t)sa * a.nmax + i], pj = a.phi[(size_t)sb * a.nmax + j];
+            const double* gi = &a.grad[3 * ((size_t)sa * a.nmax + i)];
+            const double* gj = &a.grad[3 * ((size_t)sb * a.nmax + j)];
+            acc_add(&acc[5 * e + 0], wv * (pi * pj));
+            acc_add(&acc[5 * e + 1], wv * (gi[0] * gj[0] + gi[1] * gj[1] + gi[2] * gj[2]));
+            acc_add(&acc[5 * e + 2], wv * (gi[1] * gj[2] - gi[2] * gj[1]));
+            acc_add(&acc[5 * e + 3], wv * (gi[2] * gj[0] - gi[0] * gj[2]));
+            acc_add(&acc[5 * e + 4], wv * (gi[0] * gj[1] - gi[1] * gj[0]));
           }
         }
       }
@@ -629,97 +746,77 @@ int orc_matrix_blocks(const orc_basis* b, long n_pts, const double* xyz, const d
     SOy[e] = acc_get(&acc[5 * e + 3]);
     SOz[e] = acc_get(&acc[5 * e + 4]);
   }
-  free(acc); free(phi); free(grad); free(act);
+  free(acc);
+  active_free(&a);
   ftab_free(&t);
   return missing;
 }
 
-/* Density n_p = sum_ij P_ij phi_i phi_j with P on the block pattern (Eq. 39). */
+/* Density n_p = sum_ij P_ij phi_i phi_j with P on the block pattern (Eq. 39),
+ * the pairs of active centres taking P from their block (A, B, T_b - T_a). */
 void orc_density(const orc_basis* b, long n_pts, const double* xyz,
-                 const long long* blk_ptr, const int* blk_col, const long long* blk_off,
+                 const long long* blk_ptr, const int* blk_col, const int* blk_T, const long long* blk_off,
                  const double* P, double* n_out) {
   ftab t;
   ftab_init(b, &t);
-  double* phi = (double*)calloc(t.nf, sizeof(double));
-  double* grad = (double*)calloc(3 * (size_t)t.nf, sizeof(double));
-  int* act = (int*)malloc(sizeof(int) * b->n_atoms);
+  orc_active a;
+  active_init(b, &a);
   for (long p = 0; p < n_pts; ++p) {
-    const double* X = xyz + 3 * p;
-    int na = 0;
-    for (int A = 0; A < b->n_atoms; ++A) {
-      double dx = X[0] - b->xyz[3 * A], dy = X[1] - b->xyz[3 * A + 1], dz = X[2] - b->xyz[3 * A + 2];
-      if (sqrt(dx * dx + dy * dy + dz * dz) < b->r_c) act[na++] = A;
-    }
-    for (int ia = 0; ia < na; ++ia) {
-      int A = act[ia];
-      for (int i = t.afirst[A]; i < t.afirst[A + 1]; ++i)
-        phi_at(b, t.fr[i], t.fl[i], t.fm[i], b->xyz + 3 * A, X, &phi[i], &grad[3 * i]);
-    }
+    active_at(b, &t, &a, xyz + 3 * p);
     orc_acc acc = {0.0, 0.0};
-    for (int ia = 0; ia < na; ++ia) {
-      for (int ib = 0; ib < na; ++ib) {
-        int A = act[ia], B = act[ib];
-        long q = find_block(blk_ptr, blk_col, A, B);
+    for (int sa = 0; sa < a.n; ++sa) {
+      for (int sb = 0; sb < a.n; ++sb) {
+        long q = pair_block(&a, sa, sb, blk_ptr, blk_col, blk_T);
         if (q < 0) continue;
-        int nfB = t.afirst[B + 1] - t.afirst[B];
-        for (int i = t.afirst[A]; i < t.afirst[A + 1]; ++i)
-          for (int j = t.afirst[B]; j < t.afirst[B + 1]; ++j)
-            acc_add(&acc, P[blk_off[q] + (long long)(i - t.afirst[A]) * nfB + (j - t.afirst[B])] * phi[i] * phi[j]);
+        int nfA = species_nfn(b, b->species[a.atom[sa]]), nfB = species_nfn(b, b->species[a.atom[sb]]);
+        for (int i = 0; i < nfA; ++i)
+          for (int j = 0; j < nfB; ++j)
+            acc_add(&acc, P[blk_off[q] + (long long)i * nfB + j] * a.phi[(size_t)sa * a.nmax + i] *
+                              a.phi[(size_t)sb * a.nmax + j]);
       }
     }
     n_out[p] = acc_get(&acc);
   }
-  free(phi); free(grad); free(act);
+  active_free(&a);
   ftab_free(&t);
 }
 
 /* Adjoint: dL/dv_p = w_p sum_M sum_ij G^M_ij f^M_ij(p), M = V, W0, SOx, SOy, SOz,
  * each G^M on the block pattern (a NULL slot counts as zero). */
 void orc_adjoint(const orc_basis* b, long n_pts, const double* xyz, const double* w,
-                 const long long* blk_ptr, const int* blk_col, const long long* blk_off,
+                 const long long* blk_ptr, const int* blk_col, const int* blk_T, const long long* blk_off,
                  const double* GV, const double* GW, const double* Gx, const double* Gy, const double* Gz,
                  double* dLdv) {
   ftab t;
   ftab_init(b, &t);
-  double* phi = (double*)calloc(t.nf, sizeof(double));
-  double* grad = (double*)calloc(3 * (size_t)t.nf, sizeof(double));
-  int* act = (int*)malloc(sizeof(int) * b->n_atoms);
+  orc_active a;
+  active_init(b, &a);
   for (long p = 0; p < n_pts; ++p) {
-    const double* X = xyz + 3 * p;
-    int na = 0;
-    for (int A = 0; A < b->n_atoms; ++A) {
-      double dx = X[0] - b->xyz[3 * A], dy = X[1] - b->xyz[3 * A + 1], dz = X[2] - b->xyz[3 * A + 2];
-      if (sqrt(dx * dx + dy * dy + dz * dz) < b->r_c) act[na++] = A;
-    }
-    for (int ia = 0; ia < na; ++ia) {
-      int A = act[ia];
-      for (int i = t.afirst[A]; i < t.afirst[A + 1]; ++i)
-        phi_at(b, t.fr[i], t.fl[i], t.fm[i], b->xyz + 3 * A, X, &phi[i], &grad[3 * i]);
-    }
+    active_at(b, &t, &a, xyz + 3 * p);
     orc_acc acc = {0.0, 0.0};
-    for (int ia = 0; ia < na; ++ia) {
-      for (int ib = 0; ib < na; ++ib) {
-        int A = act[ia], B = act[ib];
-        long q = find_block(blk_ptr, blk_col, A, B);
+    for (int sa = 0; sa < a.n; ++sa) {
+      for (int sb = 0; sb < a.n; ++sb) {
+        long q = pair_block(&a, sa, sb, blk_ptr, blk_col, blk_T);
         if (q < 0) continue;
-        int nfB = t.afirst[B + 1] - t.afirst[B];
-        for (int i = t.afirst[A]; i < t.afirst[A + 1]; ++i) {
-          for (int j = t.afirst[B]; j < t.afirst[B + 1]; ++j) {
-            long long e = blk_off[q] + (long long)(i - t.afirst[A]) * nfB + (j - t.afirst[B]);
-            const double* a = &grad[3 * i];
-            const double* c = &grad[3 * j];
-            if (GV) acc_add(&acc, GV[e] * phi[i] * phi[j]);
-            if (GW) acc_add(&acc, GW[e] * (a[0] * c[0] + a[1] * c[1] + a[2] * c[2]));
-            if (Gx) acc_add(&acc, Gx[e] * (a[1] * c[2] - a[2] * c[1]));
-            if (Gy) acc_add(&acc, Gy[e] * (a[2] * c[0] - a[0] * c[2]));
-            if (Gz) acc_add(&acc, Gz[e] * (a[0] * c[1] - a[1] * c[0]));
+        int nfA = species_nfn(b, b->species[a.atom[sa]]), nfB = species_nfn(b, b->species[a.atom[sb]]);
+        for (int i = 0; i < nfA; ++i) {
+          for (int j = 0; j < nfB; ++j) {
+            long long e = blk_off[q] + (long long)i * nfB + j;
+            double pi = a.phi[(size_t)sa * a.nmax + i], pj = a.phi[(size_t)sb * a.nmax + j];
+            const double* gi = &a.grad[3 * ((size_t)sa * a.nmax + i)];
+            const double* gj = &a.grad[3 * ((size_t)sb * a.nmax + j)];
+            if (GV) acc_add(&acc, GV[e] * pi * pj);
+            if (GW) acc_add(&acc, GW[e] * (gi[0] * gj[0] + gi[1] * gj[1] + gi[2] * gj[2]));
+            if (Gx) acc_add(&acc, Gx[e] * (gi[1] * gj[2] - gi[2] * gj[1]));
+            if (Gy) acc_add(&acc, Gy[e] * (gi[2] * gj[0] - gi[0] * gj[2]));
+            if (Gz) acc_add(&acc, Gz[e] * (gi[0] * gj[1] - gi[1] * gj[0]));
           }
         }
       }
     }
     dLdv[p] = w[p] * acc_get(&acc);
   }
-  free(phi); free(grad); free(act);
+  active_free(&a);
   ftab_free(&t);
 }
 

@@ -58,6 +58,10 @@ class Workload:
     n_phi: int = 16
     r_nb: float = 12.0
     batch_max: int = 128
+    # periodic cell: lattice vectors as rows (Bohr) and the image shell
+    # T in [-n_shell, n_shell]^3; None for a molecule
+    lattice: Optional[np.ndarray] = None
+    n_shell: int = 0
 
     @property
     def n_atoms(self) -> int:
@@ -186,6 +190,34 @@ def single_atom(l_list=(0, 1, 2, 3), alphas=None, Z: float = 8.0, n_rad: int = 6
 # input potential
 # --------------------------------------------------------------------------
 
+def periodic_cell(seed: int = 1005, cell=(9.0, 10.0, 11.0), n_atoms: int = 3, n_rad: int = 16,
+                  n_theta: int = 6, n_phi: int = 12, r_nb: float = 8.0, n_shell: int = 2,
+                  batch_max: int = 64) -> Workload:
+    """A small orthorhombic periodic cell (the periodic-slab configuration in
+    miniature): one heavier atom (2s2p1d) and light ones (2s1p) placed
+    uniformly with a minimum image separation of 3 Bohr.  r_nb = 8 keeps the
+    Becke neighbour sets small; n_shell = 2 covers every image within
+    r_nb + r_c of the cell."""
+    rng = np.random.default_rng(seed)
+    L = np.diag(np.asarray(cell, dtype=np.float64))
+    heavy = Species("Pb", 82.0, [0, 0, 1, 1, 2], _draw_alphas(rng, 5))
+    light = Species("H", 1.0, [0, 0, 1], _draw_alphas(rng, 3))
+    pts = []
+    while len(pts) < n_atoms:
+        p = rng.uniform(0.0, 1.0, 3) @ L
+        ok = True
+        for q in pts:
+            d = p - q
+            d = d - np.round(d / np.asarray(cell)) * np.asarray(cell)  # minimum image
+            if np.linalg.norm(d) < 3.0:
+                ok = False
+        if ok:
+            pts.append(p)
+    kinds = np.array([0] + [1] * (n_atoms - 1), dtype=np.int32)
+    return Workload("periodic-cell", np.array(pts), kinds, [heavy, light], n_rad=n_rad, n_theta=n_theta,
+                    n_phi=n_phi, r_nb=r_nb, batch_max=batch_max, lattice=L, n_shell=n_shell)
+
+
 def _erf(x: np.ndarray) -> np.ndarray:
     try:
         from scipy.special import erf
@@ -194,20 +226,47 @@ def _erf(x: np.ndarray) -> np.ndarray:
         return np.vectorize(math.erf)(x)
 
 
+def _images(wl: Workload, reach: float) -> np.ndarray:
+    """Lattice translations T.L of a periodic workload (rows), T in [-k, k]^3
+    with k chosen so that every image within `reach` of the cell's atoms is
+    present (the lattice vectors of the workloads here are orthogonal)."""
+    L = np.asarray(wl.lattice, dtype=np.float64).reshape(3, 3)
+    k = [int(math.ceil(reach / np.linalg.norm(L[d]))) + 1 for d in range(3)]
+    T = np.array([(a, b, c) for a in range(-k[0], k[0] + 1) for b in range(-k[1], k[1] + 1)
+                  for c in range(-k[2], k[2] + 1)], dtype=np.float64)
+    return T @ L
+
+
+def _smoothstep_cut(d: np.ndarray, r_on: float, r_off: float) -> np.ndarray:
+    s = np.clip((d - r_on) / (r_off - r_on), 0.0, 1.0)
+    return 1.0 - s * s * s * (10.0 - 15.0 * s + 6.0 * s * s)
+
+
 def potential(points: np.ndarray, wl: Workload, chunk: int = 65536) -> np.ndarray:
     """v(r) = sum_A -Z_A erf(d_A)/d_A, d_A = |r - R_A|, with
-    erf(d)/d -> 2/sqrt(pi) (1 - d^2/3 + d^4/10) for d < 1e-4."""
+    erf(d)/d -> 2/sqrt(pi) (1 - d^2/3 + d^4/10) for d < 1e-4.
+    Periodic workloads sum over the images within 2 r_c, each term times a
+    quintic smoothstep that goes from 1 at 2 r_c - 1 to 0 at 2 r_c (the bare
+    lattice sum of -Z/r diverges)."""
     points = np.ascontiguousarray(points, dtype=np.float64).reshape(-1, 3)
     Z = wl.Z_of_atom
+    centres, Zc = wl.xyz, Z
+    periodic = wl.lattice is not None
+    if periodic:
+        sh = _images(wl, 2.0 * wl.r_c + wl.r_nb)
+        centres = (wl.xyz[None, :, :] + sh[:, None, :]).reshape(-1, 3)
+        Zc = np.tile(Z, len(sh))
     out = np.empty(points.shape[0], dtype=np.float64)
     c = 2.0 / math.sqrt(math.pi)
     for s in range(0, points.shape[0], chunk):
         P = points[s:s + chunk]
-        d = np.sqrt(((P[:, None, :] - wl.xyz[None, :, :]) ** 2).sum(-1))
+        d = np.sqrt(((P[:, None, :] - centres[None, :, :]) ** 2).sum(-1))
         small = d < 1e-4
         ds = np.where(small, 1.0, d)
         f = np.where(small, c * (1.0 - d * d / 3.0 + d ** 4 / 10.0), _erf(ds) / ds)
-        out[s:s + chunk] = -(f * Z[None, :]).sum(-1)
+        if periodic:
+            f = f * _smoothstep_cut(d, 2.0 * wl.r_c - 1.0, 2.0 * wl.r_c)
+        out[s:s + chunk] = -(f * Zc[None, :]).sum(-1)
     return out
 
 
@@ -218,34 +277,46 @@ def potential(points: np.ndarray, wl: Workload, chunk: int = 65536) -> np.ndarra
 KINDS = {"P": 1, "GV": 2, "GW0": 3, "GSOx": 4, "GSOy": 5, "GSOz": 6}
 
 
-def _block_rng(seed: int, kind: str, A: int, B: int) -> np.random.Generator:
+def _block_rng(seed: int, kind: str, A: int, B: int, T=(0, 0, 0)) -> np.random.Generator:
     key = [(int(seed) << 8) | KINDS[kind], (int(A) << 32) | int(B)]
-    return np.random.Generator(np.random.Philox(key=key))
+    if tuple(T) == (0, 0, 0):
+        return np.random.Generator(np.random.Philox(key=key))
+    ctr = [((int(T[0]) + 512) << 20) | ((int(T[1]) + 512) << 10) | (int(T[2]) + 512), 0, 0, 1]
+    return np.random.Generator(np.random.Philox(key=key, counter=ctr))
 
 
-def block_values(seed: int, kind: str, A: int, B: int, nfA: int, nfB: int, antisym: bool) -> np.ndarray:
-    """Block (A, B) of a random matrix that is symmetric (antisym=False) or
-    antisymmetric (antisym=True) as a whole: the pair's block is drawn once,
-    keyed by (min, max), and transposed (and negated) for the other order."""
-    if A == B:
-        R = _block_rng(seed, kind, A, A).standard_normal((nfA, nfA))
+def block_values(seed: int, kind: str, A: int, B: int, nfA: int, nfB: int, antisym: bool,
+                 T=(0, 0, 0)) -> np.ndarray:
+    """Block (A, B, T) of a random matrix that is symmetric (antisym=False) or
+    antisymmetric (antisym=True) as a whole, pairing block (A, B, T) with
+    (B, A, -T): the pair is drawn once, keyed by the lexicographically smaller
+    of the two, and transposed (and negated) for the other.  A block that is
+    its own partner (A = B, T = 0) is symmetrised (antisymmetrised)."""
+    T = tuple(int(t) for t in T)
+    mT = tuple(-t for t in T)
+    if (A, T) == (B, mT):
+        R = _block_rng(seed, kind, A, A, T).standard_normal((nfA, nfA))
         return 0.5 * (R - R.T) if antisym else 0.5 * (R + R.T)
-    if A < B:
-        return _block_rng(seed, kind, A, B).standard_normal((nfA, nfB))
-    R = _block_rng(seed, kind, B, A).standard_normal((nfB, nfA))
+    if (A, B, T) < (B, A, mT):
+        return _block_rng(seed, kind, A, B, T).standard_normal((nfA, nfB))
+    R = _block_rng(seed, kind, B, A, mT).standard_normal((nfB, nfA))
     return -R.T if antisym else R.T.copy()
 
 
 def fill_pattern(blk_ptr: np.ndarray, blk_col: np.ndarray, blk_off: np.ndarray,
-                 nf_of_atom: np.ndarray, seed: int, kind: str, antisym: bool = False) -> np.ndarray:
+                 nf_of_atom: np.ndarray, seed: int, kind: str, antisym: bool = False,
+                 blk_T: Optional[np.ndarray] = None) -> np.ndarray:
     """Values of a random matrix on a CSR block pattern (rows = atoms,
-    blocks dense row-major nf_A x nf_B at blk_off)."""
+    blocks dense row-major nf_A x nf_B at blk_off; blk_T the lattice shift of
+    each block, [n_blocks][3], None for a molecule)."""
     n_atoms = len(blk_ptr) - 1
     out = np.zeros(int(blk_off[int(blk_ptr[-1])]), dtype=np.float64)
+    Ts = None if blk_T is None else np.asarray(blk_T).reshape(-1, 3)
     for A in range(n_atoms):
         for q in range(int(blk_ptr[A]), int(blk_ptr[A + 1])):
             B = int(blk_col[q])
-            blk = block_values(seed, kind, A, B, int(nf_of_atom[A]), int(nf_of_atom[B]), antisym)
+            T = (0, 0, 0) if Ts is None else tuple(int(t) for t in Ts[q])
+            blk = block_values(seed, kind, A, B, int(nf_of_atom[A]), int(nf_of_atom[B]), antisym, T)
             out[int(blk_off[q]):int(blk_off[q]) + blk.size] = blk.ravel()
     return out
 
