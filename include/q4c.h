@@ -106,6 +106,17 @@ Q4C_API q4c_status q4c_tables_export(const q4c_tables* tables, int32_t radial, d
  * split into batches by recursive median bisection along the longest
  * bounding-box axis until a batch holds <= batch_max points; the raw point
  * id ((atom*n_rad + shell)*n_theta + theta)*n_phi + phi is kept.
+ *
+ * Periodic cells (Eqs. 24-25, the real-space H(T) before any k-phase): with
+ * a lattice, the centres are the atoms and their images R_A + T.L, T an
+ * integer triple in [-n_shell, n_shell]^3 (n_shell must cover r_nb + r_cut
+ * around the cell).  Grid points come from the cell-0 atoms only; the
+ * partition, the pruning and the active-function sets run over all centres.
+ * The block pattern becomes (A, B, T) for cell-0 atoms A, B with
+ * |R_A - R_B - T.L| < 2 r_cut, T in [-2 n_shell, 2 n_shell]^3, sorted by
+ * (A, B, T); a pair of centres (A, Ta), (B, Tb) active at a point adds into
+ * block (A, B, Tb - Ta).  Without a lattice everything reduces to the
+ * molecule (T = 0).
  * ---------------------------------------------------------------------- */
 typedef struct q4c_grid_desc {
   int32_t n_atoms;
@@ -116,6 +127,8 @@ typedef struct q4c_grid_desc {
   int32_t n_theta, n_phi;  /* angular product grid (>= 1 each) */
   double r_nb;             /* Becke neighbour radius, Bohr (> 0) */
   int32_t batch_max;       /* maximum points per batch (1..1024) */
+  const double* lattice;   /* host [3][3] lattice vectors as rows (Bohr), or NULL for a molecule */
+  int32_t n_shell;         /* image shell of a periodic cell (0..8); ignored without a lattice */
 } q4c_grid_desc;
 
 /* Builds the grid (raw points and base weights on the host, Becke weights in
@@ -149,6 +162,12 @@ Q4C_API q4c_status q4c_grid_get_info(const q4c_grid* grid, q4c_grid_info* info);
 Q4C_API q4c_status q4c_grid_export(const q4c_grid* grid, double* xyz, double* w, int64_t* point_id,
                            int64_t* batch_ptr, int64_t* batch_atom_ptr, int32_t* batch_atoms,
                            int64_t* blk_ptr, int32_t* blk_col, int64_t* blk_off);
+
+/* Host copy of the lattice shift T of every pattern block, shifts[n_blocks][3]
+ * (all zero for a molecule).  In a periodic grid the batch_atoms of
+ * q4c_grid_export are centre indices, cell * n_atoms + atom with the cells in
+ * lexicographic order of T in [-n_shell, n_shell]^3.  Synchronous. */
+Q4C_API q4c_status q4c_grid_export_shifts(const q4c_grid* grid, int32_t* shifts);
 
 /* Device pointers (grid-owned, read-only) to the kept points in batch order:
  * xyz[n_points][3] and w[n_points], so callers can build v on the device. */

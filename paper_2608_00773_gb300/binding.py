@@ -24,7 +24,7 @@ STATUS = {0: "Q4C_OK", 1: "Q4C_EINVAL", 2: "Q4C_ENOMEM", 3: "Q4C_ECUDA", 4: "Q4C
 
 # every symbol include/q4c.h declares
 EXPORTS = ["nao_tabulate", "q4c_tables_destroy", "q4c_tables_export", "grid_partition", "q4c_grid_destroy",
-           "q4c_grid_get_info", "q4c_grid_export", "q4c_grid_points", "q4c_integrate", "q4c_density",
+           "q4c_grid_get_info", "q4c_grid_export", "q4c_grid_export_shifts", "q4c_grid_points", "q4c_integrate", "q4c_density",
            "q4c_integrate_backward", "q4c_integrate_noalloc", "q4c_basis_eval", "q4c_grid_status", "q4c_profile", "q4c_profile_read",
            "q4c_last_error"]
 
@@ -43,7 +43,7 @@ class BasisDesc(C.Structure):
 class GridDesc(C.Structure):
     _fields_ = [("n_atoms", C.c_int32), ("xyz", C.c_void_p), ("species", C.c_void_p),
                 ("n_rad_shells", C.c_int32), ("R", C.c_double), ("n_theta", C.c_int32), ("n_phi", C.c_int32),
-                ("r_nb", C.c_double), ("batch_max", C.c_int32)]
+                ("r_nb", C.c_double), ("batch_max", C.c_int32), ("lattice", C.c_void_p), ("n_shell", C.c_int32)]
 
 
 class GridInfo(C.Structure):
@@ -79,6 +79,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     L.q4c_grid_destroy.restype = None
     L.q4c_grid_get_info.argtypes = [vp, C.POINTER(GridInfo)]
     L.q4c_grid_export.argtypes = [vp] + [vp] * 9
+    L.q4c_grid_export_shifts.argtypes = [vp, vp]
     L.q4c_grid_points.argtypes = [vp, C.POINTER(vp), C.POINTER(vp), C.POINTER(i64)]
     L.q4c_integrate.argtypes = [vp, vp, vp, C.c_int, C.POINTER(Matrices), vp]
     L.q4c_density.argtypes = [vp, vp, vp, C.c_int, vp, vp]
@@ -148,13 +149,15 @@ class Tables:
 class Grid:
     """q4c_grid handle (grid_partition)."""
 
-    def __init__(self, tables: Tables, xyz, species, n_rad_shells, R, n_theta, n_phi, r_nb, batch_max):
+    def __init__(self, tables: Tables, xyz, species, n_rad_shells, R, n_theta, n_phi, r_nb, batch_max,
+                 lattice=None, n_shell: int = 0):
         L = load()
         self.tables = tables
         self._xyz = np.ascontiguousarray(xyz, np.float64).reshape(-1)
         self._sp = np.ascontiguousarray(species, np.int32)
+        self._lat = None if lattice is None else np.ascontiguousarray(lattice, np.float64).reshape(-1)
         d = GridDesc(len(self._sp), self._xyz.ctypes.data, self._sp.ctypes.data, n_rad_shells, R, n_theta, n_phi,
-                     r_nb, batch_max)
+                     r_nb, batch_max, None if self._lat is None else self._lat.ctypes.data, int(n_shell))
         h = C.c_void_p()
         _check(L.grid_partition(C.byref(d), tables.h, C.byref(h)))
         self.h = h
@@ -182,9 +185,11 @@ class Grid:
         _check(load().q4c_grid_export(self.h, xyz.ctypes.data, w.ctypes.data, pid.ctypes.data, bptr.ctypes.data,
                                       baptr.ctypes.data, batoms.ctypes.data, blk_ptr.ctypes.data,
                                       blk_col.ctypes.data, blk_off.ctypes.data))
+        blk_T = np.zeros(3 * max(i.n_blocks, 1), np.int32)
+        _check(load().q4c_grid_export_shifts(self.h, blk_T.ctypes.data))
         return dict(xyz=xyz, w=w, point_id=pid, batch_ptr=bptr, batch_atom_ptr=baptr,
                     batch_atoms=batoms[:int(baptr[-1])], blk_ptr=blk_ptr, blk_col=blk_col[:i.n_blocks],
-                    blk_off=blk_off)
+                    blk_off=blk_off, blk_T=blk_T[:3 * i.n_blocks].reshape(-1, 3))
 
     def status(self, stream=None):
         """Synchronise and raise Q4CError(Q4C_ETIMEOUT) if a bounded wait expired."""
@@ -210,8 +215,9 @@ def nao_tabulate(n_rad, l, alpha, r_cut=6.0, r_on=5.0, r_min=1e-4, n_log=200) ->
     return Tables(n_rad, l, alpha, r_cut, r_on, r_min, n_log)
 
 
-def grid_partition(tables: Tables, xyz, species, n_rad_shells, R, n_theta, n_phi, r_nb, batch_max) -> Grid:
-    return Grid(tables, xyz, species, n_rad_shells, R, n_theta, n_phi, r_nb, batch_max)
+def grid_partition(tables: Tables, xyz, species, n_rad_shells, R, n_theta, n_phi, r_nb, batch_max,
+                   lattice=None, n_shell: int = 0) -> Grid:
+    return Grid(tables, xyz, species, n_rad_shells, R, n_theta, n_phi, r_nb, batch_max, lattice, n_shell)
 
 
 def _prec(prec) -> int:

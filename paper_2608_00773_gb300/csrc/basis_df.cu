@@ -141,7 +141,7 @@ __global__ void __launch_bounds__(256) k_basis_df(DevBasis B, DevGrid G, DfTable
     const bool live = p < np;
     const int A = G.bat_atoms[a0 + a];
     const int f0 = G.bat_atom_fn0[a0 + a];
-    const int sp = G.atom_sp[A];
+    const int sp = G.c_sp[A];
     const int r0 = __ldg(B.sp_rad0 + sp), nr = __ldg(B.sp_nrad + sp);
     const int pp = live ? p : 0;
     const df dx = df_sub(T.pts[3 * (p0 + pp)], T.atoms[3 * A]);

@@ -38,14 +38,14 @@ __global__ void k_basis_tiles(DevBasis B, DevGrid G, int64_t b0, const int64_t* 
     const int a = item / np, p = item - a * np;
     const int A = G.bat_atoms[a0 + a];
     const int f0 = G.bat_atom_fn0[a0 + a];
-    const double dx = G.x[p0 + p] - G.atom_xyz[3 * A], dy = G.y[p0 + p] - G.atom_xyz[3 * A + 1],
-                 dz = G.z[p0 + p] - G.atom_xyz[3 * A + 2];
+    const double dx = G.x[p0 + p] - G.c_xyz[3 * A], dy = G.y[p0 + p] - G.c_xyz[3 * A + 1],
+                 dz = G.z[p0 + p] - G.c_xyz[3 * A + 2];
     int eD = kNoExp;
     if (colexp) {
       const double D = G.w[p0 + p] * v[p0 + p];
       if (D != 0.0) eD = binexp(D);
     }
-    atom_functions(B, G.atom_sp[A], dx, dy, dz, [&](int k, double phi, double gx, double gy, double gz) {
+    atom_functions(B, G.c_sp[A], dx, dy, dz, [&](int k, double phi, double gx, double gy, double gz) {
       double* q = base + static_cast<int64_t>(f0 + k) * ldp + p;
       q[0] = phi;
       q[plane] = gx;
@@ -84,7 +84,7 @@ q4c_status launch_basis_tiles(const q4c_tables* t, const q4c_grid* g, int64_t b0
 
 // nf of the atom behind local atom a of a batch
 __device__ __forceinline__ int local_nf(const DevBasis& B, const DevGrid& G, int a0, int a) {
-  return __ldg(B.sp_nfn + G.atom_sp[G.bat_atoms[a0 + a]]);
+  return __ldg(B.sp_nfn + G.c_sp[G.bat_atoms[a0 + a]]);
 }
 
 // ------------------------------------------------------------ products
@@ -183,21 +183,29 @@ __global__ void __launch_bounds__(256) k_products_fp64(DevBasis B, DevGrid G, co
 }
 
 // ------------------------------------------------- mirror + spinor blocks
-// One CTA per block.  Upper blocks (A < B) are copied transposed into
-// (B, A) (negated for SO); diagonal blocks fill i > j from (j, i).
+// One CTA per block.  The batch kernels accumulate only the canonical half
+// of the pattern: local functions are ordered by centre (cell, atom) with the
+// cells lexicographic in T, so a pair i <= j always lands in a block (A, B, T)
+// with T > 0, or T = 0 and A <= B.  Canonical blocks (role 1) are copied
+// transposed into their partner (B, A, -T) (negated for SO); a block that is
+// its own partner (A = B, T = 0; role 2) fills i > j from (j, i); role 0
+// blocks are the copy targets.
 __global__ void k_mirror(const int* __restrict__ blk_row, const int* __restrict__ blk_col,
-                         const int* __restrict__ blk_T, const int64_t* __restrict__ blk_off, const int* atom_sp,
-                         const int* sp_nfn, double* V, double* W0, double* SOx, double* SOy, double* SOz) {
+                         const int* __restrict__ blk_T, const int* __restrict__ blk_role,
+                         const int64_t* __restrict__ blk_off, const int* atom_sp, const int* sp_nfn, double* V,
+                         double* W0, double* SOx, double* SOy, double* SOz) {
   const int q = blockIdx.x;
+  const int role = blk_role[q];
+  if (role == 0) return;
   const int A = blk_row[q], Bc = blk_col[q];
-  if (A > Bc) return;
   const int nfA = sp_nfn[atom_sp[A]], nfB = sp_nfn[atom_sp[Bc]];
+  const bool self = role == 2;
   const int64_t o = blk_off[q], oT = blk_off[blk_T[q]];
   for (int e = threadIdx.x; e < nfA * nfB; e += blockDim.x) {
     const int i = e / nfB, j = e - i * nfB;
-    if (A == Bc && i <= j) continue;
-    const int64_t src = (A == Bc) ? o + static_cast<int64_t>(j) * nfB + i : o + e;
-    const int64_t dst = (A == Bc) ? o + e : oT + static_cast<int64_t>(j) * nfA + i;
+    if (self && i <= j) continue;
+    const int64_t src = self ? o + static_cast<int64_t>(j) * nfB + i : o + e;
+    const int64_t dst = self ? o + e : oT + static_cast<int64_t>(j) * nfA + i;
     V[dst] = V[src];
     W0[dst] = W0[src];
     SOx[dst] = -SOx[src];
@@ -233,7 +241,8 @@ q4c_status mirror_and_spinor(const q4c_grid* g, const q4c_matrices* out, cudaStr
   {
   KernelScope ks("mirror", s);
   k_mirror<<<static_cast<unsigned>(g->n_blocks), 128, 0, s>>>(g->d_blk_row, g->d_blk_col, g->d_blk_T,
-                                                             g->d_blk_off, g->d_atom_sp, t->d_sp_nfn, out->V,
+                                                             g->d_blk_role, g->d_blk_off, g->d_atom_sp,
+                                                             t->d_sp_nfn, out->V,
                                                              out->W0, out->SOx, out->SOy, out->SOz);
   }
   Q4C_CUDA(cudaGetLastError());

@@ -64,12 +64,12 @@ __device__ __forceinline__ double becke_s(double mu) {
 // p_owner = P_owner / sum_{C in N} P_C with P_A = prod_{B in N, B != A} s(mu_AB),
 // mu_AB = (|r - R_A| - |r - R_B|)/|R_A - R_B|.  near = some atom within r_c.
 __global__ void k_becke(const double* __restrict__ raw, const double* __restrict__ base_w, int64_t n_raw,
-                        int pts_per_atom, const double* __restrict__ atom_xyz, int n_atoms, double r_c,
-                        double r_nb, double* __restrict__ w_out, unsigned char* __restrict__ near_out,
+                        int pts_per_atom, int owner_base, const double* __restrict__ atom_xyz, int n_atoms,
+                        double r_c, double r_nb, double* __restrict__ w_out, unsigned char* __restrict__ near_out,
                         int* __restrict__ overflow) {
   const int64_t p = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
   if (p >= n_raw) return;
-  const int owner = static_cast<int>(p / pts_per_atom);
+  const int owner = owner_base + static_cast<int>(p / pts_per_atom);
   const double px = raw[3 * p], py = raw[3 * p + 1], pz = raw[3 * p + 2];
   int nb_idx[kMaxNeighbours];
   double nb_d[kMaxNeighbours];
@@ -132,6 +132,8 @@ DevGrid q4c_grid::view() const {
   v.w = d_w;
   v.atom_xyz = d_atom_xyz;
   v.atom_sp = d_atom_sp;
+  v.c_xyz = d_c_xyz;
+  v.c_sp = d_c_sp;
   v.pt_ptr = d_pt_ptr;
   v.bat_atom_ptr = d_bat_atom_ptr;
   v.bat_atoms = d_bat_atoms;
@@ -199,6 +201,47 @@ extern "C" q4c_status grid_partition(const q4c_grid_desc* d, const q4c_tables* t
   }
   g->n_basis = nb_tot;
 
+  // ---- centres: the atoms and, in a periodic cell, their images R_A + T.L
+  // (c = cell * n_atoms + A, cells in lexicographic order of T)
+  const bool periodic = d->lattice != nullptr;
+  if (periodic) {
+    const double* L = d->lattice;
+    const double det = L[0] * (L[4] * L[8] - L[5] * L[7]) - L[1] * (L[3] * L[8] - L[5] * L[6]) +
+                       L[2] * (L[3] * L[7] - L[4] * L[6]);
+    if (!(d->n_shell >= 0 && d->n_shell <= 8) || !std::isfinite(det) || std::fabs(det) < 1e-6) {
+      set_error("grid_partition: a lattice needs n_shell in 0..8 and three independent vectors");
+      delete g;
+      return Q4C_EINVAL;
+    }
+  }
+  g->n_shell = periodic ? d->n_shell : 0;
+  g->cell_side = 2 * g->n_shell + 1;
+  const int n_cells = g->cell_side * g->cell_side * g->cell_side;
+  const int cell0 = (n_cells - 1) / 2;  // T = (0, 0, 0)
+  g->n_centres = n_cells * nA;
+  const int nC = g->n_centres;
+  auto cell_T = [&](int cell, int T[3]) {
+    const int sd = g->cell_side, sh = g->n_shell;
+    T[0] = cell / (sd * sd) - sh;
+    T[1] = (cell / sd) % sd - sh;
+    T[2] = cell % sd - sh;
+  };
+  g->h_c_xyz.resize(3 * static_cast<size_t>(nC));
+  g->h_c_sp.resize(nC);
+  for (int cell = 0; cell < n_cells; ++cell) {
+    int T[3];
+    cell_T(cell, T);
+    double sh[3] = {0, 0, 0};
+    if (periodic)
+      for (int k = 0; k < 3; ++k)
+        for (int dd = 0; dd < 3; ++dd) sh[dd] += T[k] * d->lattice[3 * k + dd];
+    for (int A = 0; A < nA; ++A) {
+      const int c = cell * nA + A;
+      for (int dd = 0; dd < 3; ++dd) g->h_c_xyz[3 * c + dd] = d->xyz[3 * A + dd] + sh[dd];
+      g->h_c_sp[c] = d->species[A];
+    }
+  }
+
   // ---- raw points and base weights (w_rad * w_GL * 2 pi / n_phi)
   std::vector<double> rr(d->n_rad_shells), wr(d->n_rad_shells), ct, wt;
   for (int i = 1; i <= d->n_rad_shells; ++i) {
@@ -243,17 +286,17 @@ extern "C" q4c_status grid_partition(const q4c_grid_desc* d, const q4c_tables* t
       if ((e = cudaMalloc(&d_raw, sizeof(double) * 3 * n_raw))) break;
       if ((e = cudaMalloc(&d_base, sizeof(double) * n_raw))) break;
       if ((e = cudaMalloc(&d_w, sizeof(double) * n_raw))) break;
-      if ((e = cudaMalloc(&d_axyz, sizeof(double) * 3 * nA))) break;
+      if ((e = cudaMalloc(&d_axyz, sizeof(double) * 3 * nC))) break;
       if ((e = cudaMalloc(&d_near, n_raw))) break;
       if ((e = cudaMalloc(&d_ovf, sizeof(int)))) break;
       if ((e = cudaMemset(d_ovf, 0, sizeof(int)))) break;
       if ((e = cudaMemcpy(d_raw, raw.data(), sizeof(double) * 3 * n_raw, cudaMemcpyHostToDevice))) break;
       if ((e = cudaMemcpy(d_base, base.data(), sizeof(double) * n_raw, cudaMemcpyHostToDevice))) break;
-      if ((e = cudaMemcpy(d_axyz, d->xyz, sizeof(double) * 3 * nA, cudaMemcpyHostToDevice))) break;
+      if ((e = cudaMemcpy(d_axyz, g->h_c_xyz.data(), sizeof(double) * 3 * nC, cudaMemcpyHostToDevice))) break;
       const int threads = 128;
       const int64_t blocks = (n_raw + threads - 1) / threads;
-      k_becke<<<static_cast<unsigned>(blocks), threads>>>(d_raw, d_base, n_raw, ppa, d_axyz, nA, r_c, d->r_nb,
-                                                          d_w, d_near, d_ovf);
+      k_becke<<<static_cast<unsigned>(blocks), threads>>>(d_raw, d_base, n_raw, ppa, cell0 * nA, d_axyz, nC, r_c,
+                                                          d->r_nb, d_w, d_near, d_ovf);
       if ((e = cudaGetLastError())) break;
       if ((e = cudaMemcpy(wfull.data(), d_w, sizeof(double) * n_raw, cudaMemcpyDeviceToHost))) break;
       if ((e = cudaMemcpy(nearv.data(), d_near, n_raw, cudaMemcpyDeviceToHost))) break;
@@ -266,7 +309,7 @@ extern "C" q4c_status grid_partition(const q4c_grid_desc* d, const q4c_tables* t
       return e == cudaErrorMemoryAllocation ? Q4C_ENOMEM : Q4C_ECUDA;
     }
     if (ovf) {
-      set_error("grid_partition: more than 512 atoms within r_nb of a grid point");
+      set_error("grid_partition: more than 512 centres within r_nb of a grid point");
       delete g;
       return Q4C_EUNSUPPORTED;
     }
@@ -337,7 +380,7 @@ extern "C" q4c_status grid_partition(const q4c_grid_desc* d, const q4c_tables* t
   }
   raw.clear(); raw.shrink_to_fit();
 
-  // ---- active atoms per batch: some point strictly within r_c
+  // ---- active centres per batch: some point strictly within r_c
   std::vector<std::vector<int>> act(nB);
   parallel_for(nB, [&](int64_t b) {
     const int64_t p0 = bptr[b], p1 = bptr[b + 1];
@@ -351,13 +394,14 @@ extern "C" q4c_status grid_partition(const q4c_grid_desc* d, const q4c_tables* t
       for (int k = 0; k < 3; ++k) s += (g->h_xyz[3 * i + k] - c[k]) * (g->h_xyz[3 * i + k] - c[k]);
       rad = std::max(rad, std::sqrt(s));
     }
-    for (int A = 0; A < nA; ++A) {
+    const double* cx = g->h_c_xyz.data();
+    for (int A = 0; A < nC; ++A) {
       double s = 0;
-      for (int k = 0; k < 3; ++k) s += (d->xyz[3 * A + k] - c[k]) * (d->xyz[3 * A + k] - c[k]);
+      for (int k = 0; k < 3; ++k) s += (cx[3 * A + k] - c[k]) * (cx[3 * A + k] - c[k]);
       if (std::sqrt(s) >= rad + r_c + 1e-9) continue;
       for (int64_t i = p0; i < p1; ++i) {
-        const double dx = g->h_xyz[3 * i] - d->xyz[3 * A], dy = g->h_xyz[3 * i + 1] - d->xyz[3 * A + 1],
-                     dz = g->h_xyz[3 * i + 2] - d->xyz[3 * A + 2];
+        const double dx = g->h_xyz[3 * i] - cx[3 * A], dy = g->h_xyz[3 * i + 1] - cx[3 * A + 1],
+                     dz = g->h_xyz[3 * i + 2] - cx[3 * A + 2];
         if (std::sqrt(dx * dx + dy * dy + dz * dz) < r_c) {
           act[b].push_back(A);
           break;
@@ -366,19 +410,29 @@ extern "C" q4c_status grid_partition(const q4c_grid_desc* d, const q4c_tables* t
     }
   });
 
-  // ---- block pattern: (A, B) iff |R_A - R_B| < 2 r_c; CSR sorted by B
+  // ---- block pattern: (A, B, T) iff |R_A - R_B - T.L| < 2 r_c, T in
+  // [-2 n_shell, 2 n_shell]^3 (T = 0 for a molecule); CSR over A, sorted by (B, T)
   g->h_blk_ptr.assign(nA + 1, 0);
   std::vector<int> blk_row;
   int64_t off = 0;
+  const int s2 = 2 * g->n_shell, side2 = 2 * s2 + 1;
   for (int A = 0; A < nA; ++A) {
     for (int B = 0; B < nA; ++B) {
-      const double dx = d->xyz[3 * A] - d->xyz[3 * B], dy = d->xyz[3 * A + 1] - d->xyz[3 * B + 1],
-                   dz = d->xyz[3 * A + 2] - d->xyz[3 * B + 2];
-      if (std::sqrt(dx * dx + dy * dy + dz * dz) < 2.0 * r_c) {
-        g->h_blk_col.push_back(B);
-        blk_row.push_back(A);
-        g->h_blk_off.push_back(off);
-        off += static_cast<int64_t>(g->h_nf_atom[A]) * g->h_nf_atom[B];
+      for (int cell = 0; cell < side2 * side2 * side2; ++cell) {
+        const int T[3] = {cell / (side2 * side2) - s2, (cell / side2) % side2 - s2, cell % side2 - s2};
+        double sh[3] = {0, 0, 0};
+        if (periodic)
+          for (int k = 0; k < 3; ++k)
+            for (int dd = 0; dd < 3; ++dd) sh[dd] += T[k] * d->lattice[3 * k + dd];
+        const double dx = d->xyz[3 * A] - d->xyz[3 * B] - sh[0], dy = d->xyz[3 * A + 1] - d->xyz[3 * B + 1] - sh[1],
+                     dz = d->xyz[3 * A + 2] - d->xyz[3 * B + 2] - sh[2];
+        if (std::sqrt(dx * dx + dy * dy + dz * dz) < 2.0 * r_c) {
+          g->h_blk_col.push_back(B);
+          g->h_blk_shift.insert(g->h_blk_shift.end(), {T[0], T[1], T[2]});
+          blk_row.push_back(A);
+          g->h_blk_off.push_back(off);
+          off += static_cast<int64_t>(g->h_nf_atom[A]) * g->h_nf_atom[B];
+        }
       }
     }
     g->h_blk_ptr[A + 1] = static_cast<int64_t>(g->h_blk_col.size());
@@ -386,23 +440,50 @@ extern "C" q4c_status grid_partition(const q4c_grid_desc* d, const q4c_tables* t
   g->h_blk_off.push_back(off);
   g->n_blocks = static_cast<int64_t>(g->h_blk_col.size());
   g->nnz = off;
-  auto find_block = [&](int A, int B) -> int64_t {
-    const int* b0 = g->h_blk_col.data() + g->h_blk_ptr[A];
-    const int* b1 = g->h_blk_col.data() + g->h_blk_ptr[A + 1];
-    const int* it = std::lower_bound(b0, b1, B);
-    return (it != b1 && *it == B) ? (it - g->h_blk_col.data()) : -1;
+  // block (A, B, T) or -1; rows are sorted by (B, T) lexicographically
+  auto find_block = [&](int A, int B, const int T[3]) -> int64_t {
+    int64_t lo = g->h_blk_ptr[A], hi = g->h_blk_ptr[A + 1];
+    auto key_less = [&](int64_t q) {  // block q before (B, T)?
+      const int* t = g->h_blk_shift.data() + 3 * q;
+      if (g->h_blk_col[q] != B) return g->h_blk_col[q] < B;
+      if (t[0] != T[0]) return t[0] < T[0];
+      if (t[1] != T[1]) return t[1] < T[1];
+      return t[2] < T[2];
+    };
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) / 2;
+      if (key_less(mid)) lo = mid + 1;
+      else hi = mid;
+    }
+    if (lo < g->h_blk_ptr[A + 1] && g->h_blk_col[lo] == B) {
+      const int* t = g->h_blk_shift.data() + 3 * lo;
+      if (t[0] == T[0] && t[1] == T[1] && t[2] == T[2]) return lo;
+    }
+    return -1;
   };
-  std::vector<int> blk_T(g->n_blocks);
-  for (int64_t q = 0; q < g->n_blocks; ++q) blk_T[q] = static_cast<int>(find_block(g->h_blk_col[q], blk_row[q]));
+  // transpose partner (B, A, -T) of every block, and its role in the mirror:
+  // the canonical half is T > 0 (lexicographic) or T = 0 and A <= B
+  std::vector<int> blk_T(g->n_blocks), blk_role(g->n_blocks);
+  for (int64_t q = 0; q < g->n_blocks; ++q) {
+    const int* t = g->h_blk_shift.data() + 3 * q;
+    const int mT[3] = {-t[0], -t[1], -t[2]};
+    blk_T[q] = static_cast<int>(find_block(g->h_blk_col[q], blk_row[q], mT));
+    const bool zero = t[0] == 0 && t[1] == 0 && t[2] == 0;
+    const bool pos = t[0] > 0 || (t[0] == 0 && (t[1] > 0 || (t[1] == 0 && t[2] > 0)));
+    const int A = blk_row[q], B = g->h_blk_col[q];
+    blk_role[q] = (zero && A == B) ? 2 : ((pos || (zero && A < B)) ? 1 : 0);
+  }
 
-  // ---- per-batch tables
+  // ---- per-batch tables (over the batch's active centres)
+  auto c_atom = [&](int c) { return c % nA; };
+  auto c_cell = [&](int c) { return c / nA; };
   g->h_bat_atom_ptr.assign(nB + 1, 0);
   g->h_bat_fn_ptr.assign(nB + 1, 0);
   std::vector<int64_t> pair_ptr(nB + 1, 0);
   for (int64_t b = 0; b < nB; ++b) {
     const int na = static_cast<int>(act[b].size());
     int nb = 0;
-    for (int A : act[b]) nb += g->h_nf_atom[A];
+    for (int A : act[b]) nb += g->h_nf_atom[c_atom(A)];
     g->h_bat_atom_ptr[b + 1] = g->h_bat_atom_ptr[b] + na;
     g->h_bat_fn_ptr[b + 1] = g->h_bat_fn_ptr[b] + nb;
     pair_ptr[b + 1] = pair_ptr[b] + static_cast<int64_t>(na) * na;
@@ -432,9 +513,17 @@ extern "C" q4c_status grid_partition(const q4c_grid_desc* d, const q4c_tables* t
       const int A = act[b][a];
       g->h_bat_atoms[g->h_bat_atom_ptr[b] + a] = A;
       bat_atom_fn0[g->h_bat_atom_ptr[b] + a] = f;
-      for (int k = 0; k < g->h_nf_atom[A]; ++k) fn_info[g->h_bat_fn_ptr[b] + f++] = (a << 16) | k;
+      for (int k = 0; k < g->h_nf_atom[c_atom(A)]; ++k) fn_info[g->h_bat_fn_ptr[b] + f++] = (a << 16) | k;
+      int Ta[3];
+      cell_T(c_cell(A), Ta);
       for (int c = 0; c < na; ++c) {
-        const int64_t q = find_block(A, act[b][c]);
+        const int Cc = act[b][c];
+        int Tb[3];
+        cell_T(c_cell(Cc), Tb);
+        const int T[3] = {Tb[0] - Ta[0], Tb[1] - Ta[1], Tb[2] - Ta[2]};
+        // no block: the two centres are never within r_c of one point of
+        // the batch (active at opposite ends of it), so the pair adds nothing
+        const int64_t q = find_block(c_atom(A), c_atom(Cc), T);
         pair_off[pair_ptr[b] + static_cast<int64_t>(a) * na + c] = q < 0 ? -1 : g->h_blk_off[q];
       }
     }
@@ -445,8 +534,9 @@ extern "C" q4c_status grid_partition(const q4c_grid_desc* d, const q4c_tables* t
         const int jj = fn_info[g->h_bat_fn_ptr[b] + j];
         const int64_t off = pair_off[pair_ptr[b] + static_cast<int64_t>(ii >> 16) * na + (jj >> 16)];
         bat_idx[idx_ptr[b] + static_cast<int64_t>(i) * nb + j] =
-            off < 0 ? -1 : static_cast<int>(off + static_cast<int64_t>(ii & 0xffff) *
-                                                       g->h_nf_atom[act[b][jj >> 16]] + (jj & 0xffff));
+            off < 0 ? -1
+                    : static_cast<int>(off + static_cast<int64_t>(ii & 0xffff) *
+                                                 g->h_nf_atom[c_atom(act[b][jj >> 16])] + (jj & 0xffff));
       }
     }
   });
@@ -560,11 +650,12 @@ extern "C" q4c_status grid_partition(const q4c_grid_desc* d, const q4c_tables* t
     sz[i] = g->h_xyz[3 * i + 2];
   }
   auto dsplit = [](double x) { const float h = static_cast<float>(x); return df{h, static_cast<float>(x - h)}; };
-  std::vector<df> pts_df(3 * nP), atoms_df(3 * nA);
+  std::vector<df> pts_df(3 * nP), atoms_df(3 * static_cast<size_t>(nC));
   for (int64_t i = 0; i < 3 * nP; ++i) pts_df[i] = dsplit(g->h_xyz[i]);
-  for (int i = 0; i < 3 * nA; ++i) atoms_df[i] = dsplit(d->xyz[i]);
+  for (int i = 0; i < 3 * nC; ++i) atoms_df[i] = dsplit(g->h_c_xyz[i]);
   q4c_status st;
-  if ((st = up(&g->d_pts_df, pts_df)) || (st = up(&g->d_atoms_df, atoms_df)) || (st = up(&g->d_xyz, g->h_xyz)) || (st = up(&g->d_x, sx)) || (st = up(&g->d_y, sy)) ||
+  if ((st = up(&g->d_pts_df, pts_df)) || (st = up(&g->d_atoms_df, atoms_df)) ||
+      (st = up(&g->d_c_xyz, g->h_c_xyz)) || (st = up(&g->d_c_sp, g->h_c_sp)) || (st = up(&g->d_xyz, g->h_xyz)) || (st = up(&g->d_x, sx)) || (st = up(&g->d_y, sy)) ||
       (st = up(&g->d_z, sz)) || (st = up(&g->d_w, g->h_w)) || (st = up(&g->d_atom_xyz, g->h_atom_xyz)) ||
       (st = up(&g->d_atom_sp, g->h_atom_sp)) || (st = up(&g->d_atom_fn0, g->h_atom_fn0)) ||
       (st = up(&g->d_pt_ptr, g->h_pt_ptr)) || (st = up(&g->d_bat_atom_ptr, g->h_bat_atom_ptr)) ||
@@ -572,7 +663,7 @@ extern "C" q4c_status grid_partition(const q4c_grid_desc* d, const q4c_tables* t
       (st = up(&g->d_bat_fn_ptr, g->h_bat_fn_ptr)) || (st = up(&g->d_fn_info, fn_info)) ||
       (st = up(&g->d_bat_pair_ptr, pair_ptr)) || (st = up(&g->d_pair_off, pair_off)) ||
       (st = up(&g->d_blk_off, g->h_blk_off)) || (st = up(&g->d_blk_row, blk_row)) ||
-      (st = up(&g->d_blk_col, g->h_blk_col)) || (st = up(&g->d_blk_T, blk_T)) ||
+      (st = up(&g->d_blk_col, g->h_blk_col)) || (st = up(&g->d_blk_T, blk_T)) || (st = up(&g->d_blk_role, blk_role)) ||
       (st = up(&g->d_scr_off, g->h_scr_off)) || (st = up(&g->d_tiles, tiles)) || (st = up(&g->d_sched, sched)) ||
       (st = up(&g->d_split_items, sitems)) || (st = up(&g->d_rd_items, rditems)) ||
       (st = up(&g->d_bat_idx_ptr, idx_ptr)) || (st = up(&g->d_bat_idx, bat_idx)) ||
@@ -609,7 +700,8 @@ extern "C" void q4c_grid_destroy(q4c_grid* g) {
                   g->d_fn_info, g->d_bat_pair_ptr, g->d_pair_off, g->d_blk_off, g->d_blk_row, g->d_blk_col,
                   g->d_blk_T, g->d_scr_off, g->d_tiles, g->d_scratch, g->d_sched, g->d_counter, g->d_split_ws,
                   g->d_split_items, g->d_colexp, g->d_status, g->d_rd_items, g->d_rowexp, g->d_gsl, g->d_gsl_off,
-                  g->d_bat_idx_ptr, g->d_bat_idx, g->d_pts_df, g->d_atoms_df, g->d_gdf};
+                  g->d_bat_idx_ptr, g->d_bat_idx, g->d_pts_df, g->d_atoms_df, g->d_gdf,
+                  g->d_c_xyz, g->d_c_sp, g->d_blk_role};
   for (void* p : ptrs) cudaFree(p);
   delete g;
 }
@@ -644,6 +736,12 @@ extern "C" q4c_status q4c_grid_export(const q4c_grid* g, double* xyz, double* w,
   if (blk_ptr) std::copy(g->h_blk_ptr.begin(), g->h_blk_ptr.end(), blk_ptr);
   if (blk_col) std::copy(g->h_blk_col.begin(), g->h_blk_col.end(), blk_col);
   if (blk_off) std::copy(g->h_blk_off.begin(), g->h_blk_off.end(), blk_off);
+  return Q4C_OK;
+}
+
+extern "C" q4c_status q4c_grid_export_shifts(const q4c_grid* g, int32_t* shifts) {
+  Q4C_CHECK_ARG(g && shifts, "q4c_grid_export_shifts: NULL argument");
+  std::copy(g->h_blk_shift.begin(), g->h_blk_shift.end(), shifts);
   return Q4C_OK;
 }
 

@@ -64,7 +64,7 @@ struct DfTables {
   const df* g0;           // [n_rad_tot]
   const df* inv_knot;     // [n_log] 1 / r_k
   const df* pts;          // [n_points][3] kept points (batch order)
-  const df* atoms;        // [n_atoms][3]
+  const df* atoms;        // [n_centres][3] centre positions (atoms and periodic images)
   df inv_h_df;
   float inv_h, inv_rmin, rmin, rc2;
 };
@@ -72,16 +72,18 @@ struct DfTables {
 // Grid, batches and pattern as seen by kernels.
 struct DevGrid {
   const double *x, *y, *z, *w;  // kept points, batch order (SoA)
-  const double* atom_xyz;       // [n_atoms][3]
+  const double* atom_xyz;       // [n_atoms][3] cell-0 atoms
   const int* atom_sp;           // [n_atoms]
+  const double* c_xyz;          // [n_centres][3] centres: atoms and, in a periodic cell, images
+  const int* c_sp;              // [n_centres] species of each centre
   const int64_t* pt_ptr;        // [n_batches+1]
   const int* bat_atom_ptr;      // [n_batches+1] into bat_atoms
-  const int* bat_atoms;         // active atoms, ascending
-  const int* bat_atom_fn0;      // local index of each active atom's first function
+  const int* bat_atoms;         // active centres, ascending
+  const int* bat_atom_fn0;      // local index of each active centre's first function
   const int64_t* bat_fn_ptr;    // [n_batches+1] prefix of n_b
-  const int* fn_info;           // [sum n_b] (local atom << 16) | index within atom
+  const int* fn_info;           // [sum n_b] (local centre << 16) | index within its atom
   const int64_t* bat_pair_ptr;  // [n_batches+1] into pair_off (n_a^2 per batch)
-  const int64_t* pair_off;      // value offset of block (A_a, A_b) or -1
+  const int64_t* pair_off;      // value offset of the block of the centre pair (a, b) or -1
   const int64_t* bat_idx_ptr;   // [n_batches+1] into bat_idx (n_b^2 per batch)
   const int* bat_idx;           // value offset of element (i, j) of the batch, or -1
   int n_atoms;
@@ -122,10 +124,17 @@ struct q4c_grid {
   std::vector<int64_t> h_pid, h_pt_ptr, h_blk_ptr, h_blk_off, h_bat_fn_ptr;
   std::vector<int> h_blk_col, h_bat_atom_ptr, h_bat_atoms, h_atom_sp, h_atom_fn0, h_nf_atom;
   std::vector<double> h_atom_xyz;
+  // centres: c = cell * n_atoms + atom, cells in lexicographic order of
+  // T in [-n_shell, n_shell]^3 (one cell, T = 0, for a molecule)
+  int n_centres = 0, n_shell = 0, cell_side = 1;
+  std::vector<double> h_c_xyz;
+  std::vector<int> h_c_sp, h_blk_shift;  // h_blk_shift [n_blocks][3]
+  double* d_c_xyz = nullptr;
+  int* d_c_sp = nullptr;
   // device: points
   double *d_xyz = nullptr, *d_x = nullptr, *d_y = nullptr, *d_z = nullptr, *d_w = nullptr;
   q4c::df* d_pts_df = nullptr;    // [n_pts][3]
-  q4c::df* d_atoms_df = nullptr;  // [n_atoms][3]
+  q4c::df* d_atoms_df = nullptr;  // [n_centres][3]
   // device: atoms and batches
   double* d_atom_xyz = nullptr;
   int *d_atom_sp = nullptr, *d_atom_fn0 = nullptr;
@@ -137,6 +146,7 @@ struct q4c_grid {
   // device: pattern
   int64_t* d_blk_off = nullptr;
   int *d_blk_row = nullptr, *d_blk_col = nullptr, *d_blk_T = nullptr;
+  int* d_blk_role = nullptr;  // mirror role: 1 canonical (copied to its partner), 2 own partner, 0 target
   // FP64 path: waves of batches whose basis tiles fit the scratch buffer
   std::vector<int64_t> wave_b0;            // [n_waves+1] batch ranges
   std::vector<int64_t> h_scr_off;          // [n_batches] offset (doubles) within its wave

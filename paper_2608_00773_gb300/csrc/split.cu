@@ -100,10 +100,6 @@ __device__ __forceinline__ Products products_of(int o) {
   }
 }
 
-__device__ __forceinline__ int local_nf(const DevBasis& B, const DevGrid& G, int a0, int a) {
-  return __ldg(B.sp_nfn + G.atom_sp[G.bat_atoms[a0 + a]]);
-}
-
 __device__ __forceinline__ int item_steps(const DevGrid& G, int4 item) {
   const int np = static_cast<int>(G.pt_ptr[item.x + 1] - G.pt_ptr[item.x]);
   return ((np + kKc - 1) / kKc) * (item.y == 1 ? 3 : 1);

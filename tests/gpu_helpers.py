@@ -32,7 +32,7 @@ class LibCase:
 
     def random(self, seed, kind, antisym=False):
         import torch
-        vals = fill_pattern(*self.pat, self.wl.nf_of_atom, seed, kind, antisym)
+        vals = fill_pattern(*self.pat, self.wl.nf_of_atom, seed, kind, antisym, blk_T=self.ex["blk_T"])
         return torch.tensor(vals, device="cuda")
 
     def G(self, seed):
@@ -59,7 +59,7 @@ class OracleCase:
 
     def random(self, seed, kind, antisym=False):
         return fill_pattern(self.pat.blk_ptr, self.pat.blk_col, self.pat.blk_off, self.wl.nf_of_atom, seed, kind,
-                            antisym)
+                            antisym, blk_T=self.pat.blk_T)
 
     def G(self, seed):
         return [self.random(seed, k, a) for k, a in ADJOINT_KINDS]
