@@ -117,6 +117,15 @@ Q4C_API q4c_status q4c_tables_export(const q4c_tables* tables, int32_t radial, d
  * (A, B, T); a pair of centres (A, Ta), (B, Tb) active at a point adds into
  * block (A, B, Tb - Ta).  Without a lattice everything reduces to the
  * molecule (T = 0).
+ *
+ * Batched molecules (many independent molecules in one grid and one call):
+ * with mol_atom_ptr the atoms form n_molecules consecutive ranges.  Each
+ * molecule is partitioned, pruned, batched and screened on its own atoms
+ * only (its Becke neighbour sets, active sets and pattern blocks never
+ * include another molecule's atoms, wherever the molecules sit), so every
+ * batch holds one molecule's points and the molecule's blocks (its atom
+ * rows of the pattern) are what integrating it alone would give.  Not
+ * combined with a lattice.
  * ---------------------------------------------------------------------- */
 typedef struct q4c_grid_desc {
   int32_t n_atoms;
@@ -129,6 +138,9 @@ typedef struct q4c_grid_desc {
   int32_t batch_max;       /* maximum points per batch (1..1024) */
   const double* lattice;   /* host [3][3] lattice vectors as rows (Bohr), or NULL for a molecule */
   int32_t n_shell;         /* image shell of a periodic cell (0..8); ignored without a lattice */
+  int32_t n_molecules;     /* independent molecules (0 or 1: one system) */
+  const int32_t* mol_atom_ptr; /* host [n_molecules+1]: atom ranges, 0 = p[0] < p[1] < ... = n_atoms;
+                                  NULL when n_molecules <= 1 */
 } q4c_grid_desc;
 
 /* Builds the grid (raw points and base weights on the host, Becke weights in

@@ -43,7 +43,8 @@ class BasisDesc(C.Structure):
 class GridDesc(C.Structure):
     _fields_ = [("n_atoms", C.c_int32), ("xyz", C.c_void_p), ("species", C.c_void_p),
                 ("n_rad_shells", C.c_int32), ("R", C.c_double), ("n_theta", C.c_int32), ("n_phi", C.c_int32),
-                ("r_nb", C.c_double), ("batch_max", C.c_int32), ("lattice", C.c_void_p), ("n_shell", C.c_int32)]
+                ("r_nb", C.c_double), ("batch_max", C.c_int32), ("lattice", C.c_void_p), ("n_shell", C.c_int32),
+                ("n_molecules", C.c_int32), ("mol_atom_ptr", C.c_void_p)]
 
 
 class GridInfo(C.Structure):
@@ -150,14 +151,17 @@ class Grid:
     """q4c_grid handle (grid_partition)."""
 
     def __init__(self, tables: Tables, xyz, species, n_rad_shells, R, n_theta, n_phi, r_nb, batch_max,
-                 lattice=None, n_shell: int = 0):
+                 lattice=None, n_shell: int = 0, mol_atom_ptr=None):
         L = load()
         self.tables = tables
         self._xyz = np.ascontiguousarray(xyz, np.float64).reshape(-1)
         self._sp = np.ascontiguousarray(species, np.int32)
         self._lat = None if lattice is None else np.ascontiguousarray(lattice, np.float64).reshape(-1)
+        self._mol = None if mol_atom_ptr is None else np.ascontiguousarray(mol_atom_ptr, np.int32)
         d = GridDesc(len(self._sp), self._xyz.ctypes.data, self._sp.ctypes.data, n_rad_shells, R, n_theta, n_phi,
-                     r_nb, batch_max, None if self._lat is None else self._lat.ctypes.data, int(n_shell))
+                     r_nb, batch_max, None if self._lat is None else self._lat.ctypes.data, int(n_shell),
+                     0 if self._mol is None else len(self._mol) - 1,
+                     None if self._mol is None else self._mol.ctypes.data)
         h = C.c_void_p()
         _check(L.grid_partition(C.byref(d), tables.h, C.byref(h)))
         self.h = h
@@ -216,8 +220,9 @@ def nao_tabulate(n_rad, l, alpha, r_cut=6.0, r_on=5.0, r_min=1e-4, n_log=200) ->
 
 
 def grid_partition(tables: Tables, xyz, species, n_rad_shells, R, n_theta, n_phi, r_nb, batch_max,
-                   lattice=None, n_shell: int = 0) -> Grid:
-    return Grid(tables, xyz, species, n_rad_shells, R, n_theta, n_phi, r_nb, batch_max, lattice, n_shell)
+                   lattice=None, n_shell: int = 0, mol_atom_ptr=None) -> Grid:
+    return Grid(tables, xyz, species, n_rad_shells, R, n_theta, n_phi, r_nb, batch_max, lattice, n_shell,
+                mol_atom_ptr)
 
 
 def _prec(prec) -> int:

@@ -64,18 +64,21 @@ __device__ __forceinline__ double becke_s(double mu) {
 // p_owner = P_owner / sum_{C in N} P_C with P_A = prod_{B in N, B != A} s(mu_AB),
 // mu_AB = (|r - R_A| - |r - R_B|)/|R_A - R_B|.  near = some atom within r_c.
 __global__ void k_becke(const double* __restrict__ raw, const double* __restrict__ base_w, int64_t n_raw,
-                        int pts_per_atom, int owner_base, const double* __restrict__ atom_xyz, int n_atoms,
-                        double r_c, double r_nb, double* __restrict__ w_out, unsigned char* __restrict__ near_out,
-                        int* __restrict__ overflow) {
+                        int pts_per_atom, int owner_base, const double* __restrict__ atom_xyz,
+                        const int2* __restrict__ cand, double r_c, double r_nb, double* __restrict__ w_out,
+                        unsigned char* __restrict__ near_out, int* __restrict__ overflow) {
   const int64_t p = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
   if (p >= n_raw) return;
-  const int owner = owner_base + static_cast<int>(p / pts_per_atom);
+  const int gen = static_cast<int>(p / pts_per_atom);  // generating (cell-0) atom
+  const int owner = owner_base + gen;
+  // centres that can take part: the generating atom's molecule, or all
+  const int2 range = cand[gen];
   const double px = raw[3 * p], py = raw[3 * p + 1], pz = raw[3 * p + 2];
   int nb_idx[kMaxNeighbours];
   double nb_d[kMaxNeighbours];
   int nn = 0, own_slot = -1;
   bool near = false;
-  for (int B = 0; B < n_atoms; ++B) {
+  for (int B = range.x; B < range.y; ++B) {
     const double dx = px - atom_xyz[3 * B], dy = py - atom_xyz[3 * B + 1], dz = pz - atom_xyz[3 * B + 2];
     const double d = sqrt(dx * dx + dy * dy + dz * dz);
     if (d < r_c) near = true;
@@ -167,6 +170,36 @@ static void parallel_for(int64_t n, F&& f) {
   for (auto& x : th) x.join();
 }
 
+namespace q4c {
+
+// Dense offset tables of one wave's batches (one CTA per batch) from the
+// centre-pair offsets: element (i, j) -> pair_off[a_i, a_j] + k_i nf(a_j) + k_j.
+__global__ void k_fill_idx(DevBasis B, DevGrid G, int64_t b0) {
+  const int64_t b = b0 + blockIdx.x;
+  const int64_t f0 = G.bat_fn_ptr[b];
+  const int nb = static_cast<int>(G.bat_fn_ptr[b + 1] - f0);
+  const int a0 = G.bat_atom_ptr[b], na = G.bat_atom_ptr[b + 1] - a0;
+  const int64_t pp = G.bat_pair_ptr[b];
+  int* idx = G.bat_idx + G.bat_idx_ptr[b];
+  for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
+    const int i = e / nb, j = e - i * nb;
+    const int ii = G.fn_info[f0 + i], jj = G.fn_info[f0 + j];
+    const int64_t off = G.pair_off[pp + static_cast<int64_t>(ii >> 16) * na + (jj >> 16)];
+    const int nfj = __ldg(B.sp_nfn + G.c_sp[G.bat_atoms[a0 + (jj >> 16)]]);
+    idx[e] = off < 0 ? -1 : static_cast<int>(off + static_cast<int64_t>(ii & 0xffff) * nfj + (jj & 0xffff));
+  }
+}
+
+q4c_status launch_fill_idx(const q4c_tables* t, const q4c_grid* g, int64_t b0, int64_t b1, cudaStream_t s) {
+  if (b1 <= b0) return Q4C_OK;
+  KernelScope ks("fill_idx", s);
+  k_fill_idx<<<static_cast<unsigned>(b1 - b0), 256, 0, s>>>(t->view(), g->view(), b0);
+  Q4C_CUDA(cudaGetLastError());
+  return Q4C_OK;
+}
+
+}  // namespace q4c
+
 static int64_t scratch_cap_doubles() {
   int64_t mb = 2048;
   if (const char* e = std::getenv("Q4C_SCRATCH_MB")) mb = std::max<int64_t>(16, std::atoll(e));
@@ -226,6 +259,26 @@ extern "C" q4c_status grid_partition(const q4c_grid_desc* d, const q4c_tables* t
     T[1] = (cell / sd) % sd - sh;
     T[2] = cell % sd - sh;
   };
+  // ---- molecules: atom ranges; every atom's candidate centres
+  const int n_mol = d->n_molecules > 1 ? d->n_molecules : 1;
+  std::vector<int> mol_ptr{0, nA};
+  if (n_mol > 1) {
+    bool ok = d->mol_atom_ptr != nullptr && !periodic && d->mol_atom_ptr[0] == 0 && d->mol_atom_ptr[n_mol] == nA;
+    for (int m = 0; ok && m < n_mol; ++m) ok = d->mol_atom_ptr[m] < d->mol_atom_ptr[m + 1];
+    if (!ok) {
+      set_error("grid_partition: mol_atom_ptr must rise strictly from 0 to n_atoms (and no lattice)");
+      delete g;
+      return Q4C_EINVAL;
+    }
+    mol_ptr.assign(d->mol_atom_ptr, d->mol_atom_ptr + n_mol + 1);
+  }
+  std::vector<int2> cand(nA);  // candidate centre range of each cell-0 atom
+  std::vector<int> atom_mol(nA);
+  for (int m = 0; m < n_mol; ++m)
+    for (int A = mol_ptr[m]; A < mol_ptr[m + 1]; ++A) {
+      atom_mol[A] = m;
+      cand[A] = n_mol > 1 ? make_int2(mol_ptr[m], mol_ptr[m + 1]) : make_int2(0, nC);
+    }
   g->h_c_xyz.resize(3 * static_cast<size_t>(nC));
   g->h_c_sp.resize(nC);
   for (int cell = 0; cell < n_cells; ++cell) {
@@ -277,8 +330,10 @@ extern "C" q4c_status grid_partition(const q4c_grid_desc* d, const q4c_tables* t
     double *d_raw = nullptr, *d_base = nullptr, *d_w = nullptr, *d_axyz = nullptr;
     unsigned char* d_near = nullptr;
     int* d_ovf = nullptr;
+    int2* d_cand = nullptr;
     auto cleanup = [&] {
       cudaFree(d_raw); cudaFree(d_base); cudaFree(d_w); cudaFree(d_axyz); cudaFree(d_near); cudaFree(d_ovf);
+      cudaFree(d_cand);
     };
     cudaError_t e = cudaSuccess;
     int ovf = 0;
@@ -289,14 +344,16 @@ extern "C" q4c_status grid_partition(const q4c_grid_desc* d, const q4c_tables* t
       if ((e = cudaMalloc(&d_axyz, sizeof(double) * 3 * nC))) break;
       if ((e = cudaMalloc(&d_near, n_raw))) break;
       if ((e = cudaMalloc(&d_ovf, sizeof(int)))) break;
+      if ((e = cudaMalloc(&d_cand, sizeof(int2) * nA))) break;
+      if ((e = cudaMemcpy(d_cand, cand.data(), sizeof(int2) * nA, cudaMemcpyHostToDevice))) break;
       if ((e = cudaMemset(d_ovf, 0, sizeof(int)))) break;
       if ((e = cudaMemcpy(d_raw, raw.data(), sizeof(double) * 3 * n_raw, cudaMemcpyHostToDevice))) break;
       if ((e = cudaMemcpy(d_base, base.data(), sizeof(double) * n_raw, cudaMemcpyHostToDevice))) break;
       if ((e = cudaMemcpy(d_axyz, g->h_c_xyz.data(), sizeof(double) * 3 * nC, cudaMemcpyHostToDevice))) break;
       const int threads = 128;
       const int64_t blocks = (n_raw + threads - 1) / threads;
-      k_becke<<<static_cast<unsigned>(blocks), threads>>>(d_raw, d_base, n_raw, ppa, cell0 * nA, d_axyz, nC, r_c,
-                                                          d->r_nb, d_w, d_near, d_ovf);
+      k_becke<<<static_cast<unsigned>(blocks), threads>>>(d_raw, d_base, n_raw, ppa, cell0 * nA, d_axyz, d_cand,
+                                                          r_c, d->r_nb, d_w, d_near, d_ovf);
       if ((e = cudaGetLastError())) break;
       if ((e = cudaMemcpy(wfull.data(), d_w, sizeof(double) * n_raw, cudaMemcpyDeviceToHost))) break;
       if ((e = cudaMemcpy(nearv.data(), d_near, n_raw, cudaMemcpyDeviceToHost))) break;
@@ -332,8 +389,20 @@ extern "C" q4c_status grid_partition(const q4c_grid_desc* d, const q4c_tables* t
   std::vector<int64_t> bptr{0};
   {
     struct Range { int64_t lo, hi; };
-    std::vector<Range> stack{{0, static_cast<int64_t>(order.size())}};
-    std::vector<Range> leaves;
+    // one root range per molecule (kept points are atom-major, so each
+    // molecule's points are contiguous); the roots pushed in reverse so that
+    // the molecules' batches come out in molecule order
+    std::vector<Range> stack, leaves;
+    {
+      std::vector<Range> roots;
+      int64_t i = 0;
+      for (int m = 0; m < n_mol; ++m) {
+        const int64_t lo = i;
+        while (i < static_cast<int64_t>(order.size()) && atom_mol[order[i] / ppa] == m) ++i;
+        if (i > lo) roots.push_back({lo, i});
+      }
+      stack.assign(roots.rbegin(), roots.rend());
+    }
     while (!stack.empty()) {
       Range r = stack.back();
       stack.pop_back();
@@ -395,7 +464,8 @@ extern "C" q4c_status grid_partition(const q4c_grid_desc* d, const q4c_tables* t
       rad = std::max(rad, std::sqrt(s));
     }
     const double* cx = g->h_c_xyz.data();
-    for (int A = 0; A < nC; ++A) {
+    const int2 range = cand[g->h_pid[p0] / ppa];  // the batch's molecule
+    for (int A = range.x; A < range.y; ++A) {
       double s = 0;
       for (int k = 0; k < 3; ++k) s += (cx[3 * A + k] - c[k]) * (cx[3 * A + k] - c[k]);
       if (std::sqrt(s) >= rad + r_c + 1e-9) continue;
@@ -417,7 +487,7 @@ extern "C" q4c_status grid_partition(const q4c_grid_desc* d, const q4c_tables* t
   int64_t off = 0;
   const int s2 = 2 * g->n_shell, side2 = 2 * s2 + 1;
   for (int A = 0; A < nA; ++A) {
-    for (int B = 0; B < nA; ++B) {
+    for (int B = mol_ptr[atom_mol[A]]; B < mol_ptr[atom_mol[A] + 1]; ++B) {
       for (int cell = 0; cell < side2 * side2 * side2; ++cell) {
         const int T[3] = {cell / (side2 * side2) - s2, (cell / side2) % side2 - s2, cell % side2 - s2};
         double sh[3] = {0, 0, 0};
@@ -494,14 +564,6 @@ extern "C" q4c_status grid_partition(const q4c_grid_desc* d, const q4c_tables* t
     g->flops_alg += 14.0 * np * static_cast<double>(nb) * nb;
     g->sum_np_nb += static_cast<double>(np) * nb;
   }
-  // per-batch dense table of pattern offsets: idx[i * n_b + j] = value offset
-  // of element (i, j) (local functions) or -1 outside the pattern
-  std::vector<int64_t> idx_ptr(nB + 1, 0);
-  for (int64_t b = 0; b < nB; ++b) {
-    const int64_t nb = g->h_bat_fn_ptr[b + 1] - g->h_bat_fn_ptr[b];
-    idx_ptr[b + 1] = idx_ptr[b] + nb * nb;
-  }
-  std::vector<int> bat_idx(idx_ptr[nB]);
   std::vector<int> bat_atom_fn0(g->h_bat_atom_ptr[nB]);
   g->h_bat_atoms.resize(g->h_bat_atom_ptr[nB]);
   std::vector<int> fn_info(g->h_bat_fn_ptr[nB]);
@@ -525,18 +587,6 @@ extern "C" q4c_status grid_partition(const q4c_grid_desc* d, const q4c_tables* t
         // the batch (active at opposite ends of it), so the pair adds nothing
         const int64_t q = find_block(c_atom(A), c_atom(Cc), T);
         pair_off[pair_ptr[b] + static_cast<int64_t>(a) * na + c] = q < 0 ? -1 : g->h_blk_off[q];
-      }
-    }
-    const int nb = f;
-    for (int i = 0; i < nb; ++i) {
-      const int ii = fn_info[g->h_bat_fn_ptr[b] + i];
-      for (int j = 0; j < nb; ++j) {
-        const int jj = fn_info[g->h_bat_fn_ptr[b] + j];
-        const int64_t off = pair_off[pair_ptr[b] + static_cast<int64_t>(ii >> 16) * na + (jj >> 16)];
-        bat_idx[idx_ptr[b] + static_cast<int64_t>(i) * nb + j] =
-            off < 0 ? -1
-                    : static_cast<int>(off + static_cast<int64_t>(ii & 0xffff) *
-                                                 g->h_nf_atom[c_atom(act[b][jj >> 16])] + (jj & 0xffff));
       }
     }
   });
@@ -572,6 +622,22 @@ extern "C" q4c_status grid_partition(const q4c_grid_desc* d, const q4c_tables* t
   g->wave_b0.push_back(nB);
   g->wave_t0.push_back(static_cast<int64_t>(tiles.size()));
   g->scratch_doubles = std::max<int64_t>(peak, 1);
+
+  // per-batch dense tables of pattern offsets, idx[i * n_b + j] = value
+  // offset of element (i, j) (local functions) or -1 outside the pattern;
+  // filled on the device for one wave at a time (sum n_b^2 of a whole grid
+  // can be far larger than a wave's)
+  std::vector<int64_t> idx_ptr(nB + 1, 0);
+  g->idx_entries = 1;
+  for (size_t wv = 0; wv + 1 < g->wave_b0.size(); ++wv) {
+    int64_t used = 0;
+    for (int64_t b = g->wave_b0[wv]; b < g->wave_b0[wv + 1]; ++b) {
+      const int64_t nb = g->h_bat_fn_ptr[b + 1] - g->h_bat_fn_ptr[b];
+      idx_ptr[b] = used;
+      used += nb * nb;
+    }
+    g->idx_entries = std::max(g->idx_entries, used);
+  }
 
   // ---- split path: (batch, output, ti, tj) items per wave, 64x64 tiles;
   // V and W0 need ti <= tj only, the A_yz/A_zx/A_xy products every tile.
@@ -666,7 +732,7 @@ extern "C" q4c_status grid_partition(const q4c_grid_desc* d, const q4c_tables* t
       (st = up(&g->d_blk_col, g->h_blk_col)) || (st = up(&g->d_blk_T, blk_T)) || (st = up(&g->d_blk_role, blk_role)) ||
       (st = up(&g->d_scr_off, g->h_scr_off)) || (st = up(&g->d_tiles, tiles)) || (st = up(&g->d_sched, sched)) ||
       (st = up(&g->d_split_items, sitems)) || (st = up(&g->d_rd_items, rditems)) ||
-      (st = up(&g->d_bat_idx_ptr, idx_ptr)) || (st = up(&g->d_bat_idx, bat_idx)) ||
+      (st = up(&g->d_bat_idx_ptr, idx_ptr)) ||
       (st = up(&g->d_gsl_off, gsl_off))) {
     q4c_grid_destroy(g);
     return st;
@@ -679,6 +745,7 @@ extern "C" q4c_status grid_partition(const q4c_grid_desc* d, const q4c_tables* t
     if (e == cudaSuccess) e = cudaMalloc(&g->d_rowexp, sizeof(int) * 4 * nP);
     if (e == cudaSuccess) e = cudaMalloc(&g->d_gsl, static_cast<size_t>(std::max<int64_t>(g->gsl_bytes, 16)));
     if (e == cudaSuccess) e = cudaMalloc(&g->d_gdf, sizeof(float2) * 5 * std::max<int64_t>(g->nnz, 1));
+    if (e == cudaSuccess) e = cudaMalloc(&g->d_bat_idx, sizeof(int) * g->idx_entries);
     if (e == cudaSuccess) e = cudaMalloc(&g->d_status, sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMemset(g->d_status, 0, sizeof(unsigned));
     g->split_ws_bytes = static_cast<int64_t>(sizeof(int)) * (8 * g->h_bat_fn_ptr[nB] + 4 * nP) +
@@ -718,7 +785,7 @@ extern "C" q4c_status q4c_grid_get_info(const q4c_grid* g, q4c_grid_info* info) 
   info->max_np = g->max_np;
   info->flops_alg = g->flops_alg;
   info->sum_np_nb = g->sum_np_nb;
-  info->scratch_bytes = 8 * g->scratch_doubles + g->split_ws_bytes;
+  info->scratch_bytes = 8 * g->scratch_doubles + g->split_ws_bytes + 4 * g->idx_entries;
   return Q4C_OK;
 }
 

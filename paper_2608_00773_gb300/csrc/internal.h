@@ -85,7 +85,7 @@ struct DevGrid {
   const int64_t* bat_pair_ptr;  // [n_batches+1] into pair_off (n_a^2 per batch)
   const int64_t* pair_off;      // value offset of the block of the centre pair (a, b) or -1
   const int64_t* bat_idx_ptr;   // [n_batches+1] into bat_idx (n_b^2 per batch)
-  const int* bat_idx;           // value offset of element (i, j) of the batch, or -1
+  int* bat_idx;                 // value offset of element (i, j) of the batch, or -1 (one wave, filled per call)
   int n_atoms;
 };
 
@@ -168,6 +168,7 @@ struct q4c_grid {
   unsigned char* d_gsl = nullptr;          // G' digit blocks of one wave (density/adjoint)
   int64_t* d_gsl_off = nullptr;            // [n_batches] byte offsets into d_gsl (per wave)
   int64_t gsl_bytes = 0;
+  int64_t idx_entries = 0;                 // size of the per-wave dense offset tables
   int64_t* d_bat_idx_ptr = nullptr;
   int* d_bat_idx = nullptr;                // per batch n_b x n_b value offsets (-1 outside)
   unsigned* d_status = nullptr;            // bit 0: a bounded wait expired
@@ -189,6 +190,9 @@ q4c_status basis_eval(const q4c_tables* t, const q4c_grid* g, int64_t n_pts, con
 q4c_status mirror_and_spinor(const q4c_grid* g, const q4c_matrices* out, cudaStream_t s);
 q4c_status launch_basis_tiles(const q4c_tables* t, const q4c_grid* g, int64_t b0, int64_t b1, const double* v,
                               int* colexp, cudaStream_t s);
+// grid.cu: dense per-batch offset tables of the batches [b0, b1) (one wave)
+q4c_status launch_fill_idx(const q4c_tables* t, const q4c_grid* g, int64_t b0, int64_t b1, cudaStream_t s);
+
 // basis_df.cu
 q4c_status launch_basis_df(const q4c_tables* t, const q4c_grid* g, int64_t b0, int64_t b1, const double* v,
                            int* colexp, int* rowexp, cudaStream_t s);

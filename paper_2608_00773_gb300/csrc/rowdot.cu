@@ -529,6 +529,7 @@ q4c_status run(const q4c_tables* t, const q4c_grid* g, const double* const mats[
   for (int wv = 0; wv < n_waves; ++wv) {
     const int64_t b0 = g->wave_b0[wv], b1 = g->wave_b0[wv + 1];
     if (b1 <= b0) continue;
+    if (q4c_status st = launch_fill_idx(t, g, b0, b1, s)) return st;
     {
       KernelScope ks("split_gslice", s);
       k_gslice<<<dim3(static_cast<unsigned>(b1 - b0), MODE == 0 ? 1 : 5), 256, 0, s>>>(

@@ -62,6 +62,8 @@ class Workload:
     # T in [-n_shell, n_shell]^3; None for a molecule
     lattice: Optional[np.ndarray] = None
     n_shell: int = 0
+    # batched independent molecules: atom ranges [n_molecules + 1]; None for one system
+    mol_atom_ptr: Optional[np.ndarray] = None
 
     @property
     def n_atoms(self) -> int:
@@ -95,6 +97,16 @@ class Workload:
     @property
     def n_raw_points(self) -> int:
         return self.n_atoms * self.n_rad * self.n_theta * self.n_phi
+
+    @property
+    def n_molecules(self) -> int:
+        return 1 if self.mol_atom_ptr is None else len(self.mol_atom_ptr) - 1
+
+    def molecule(self, m: int) -> "Workload":
+        """Molecule m of a batched workload as a workload of its own."""
+        a0, a1 = int(self.mol_atom_ptr[m]), int(self.mol_atom_ptr[m + 1])
+        return dataclasses.replace(self, name=f"{self.name}-mol{m}", xyz=self.xyz[a0:a1].copy(),
+                                   species_of_atom=self.species_of_atom[a0:a1].copy(), mol_atom_ptr=None)
 
     def translated(self, shift) -> "Workload":
         return dataclasses.replace(self, xyz=self.xyz + np.asarray(shift, dtype=np.float64)[None, :])
@@ -190,6 +202,28 @@ def single_atom(l_list=(0, 1, 2, 3), alphas=None, Z: float = 8.0, n_rad: int = 6
 # input potential
 # --------------------------------------------------------------------------
 
+def molecule_batch(n_mol: int = 2000, seed: int = 1003, n_min: int = 3, n_max: int = 40, n_rad: int = 40,
+                   n_theta: int = 10, n_phi: int = 20, batch_max: int = 128) -> Workload:
+    """Many independent molecules integrated together: sizes N uniform in
+    n_min..n_max, atoms O (probability 1/3, 3s2p1d) or H (2s1p) with the basis
+    of the water workload, placed uniformly in a cube of side 3 N^(1/3) + 2
+    Bohr with a minimum separation of 1.8 Bohr (drawn in order from `seed`).
+    Every molecule keeps its own coordinates; they are independent through
+    mol_atom_ptr, not through distance.  40 x (10 x 20) points per atom."""
+    base = water()
+    rng = np.random.default_rng(seed)
+    xyz, kinds, ptr = [], [], [0]
+    for _ in range(n_mol):
+        n = int(rng.integers(n_min, n_max + 1))
+        box = 3.0 * n ** (1.0 / 3.0) + 2.0
+        xyz.append(_place(rng, n, box, 1.8))
+        kinds.append((rng.uniform(size=n) >= 1.0 / 3.0).astype(np.int32))  # 0 = O, 1 = H
+        ptr.append(ptr[-1] + n)
+    return Workload(f"molecules-{n_mol}", np.vstack(xyz), np.concatenate(kinds), base.species, n_rad=n_rad,
+                    n_theta=n_theta, n_phi=n_phi, batch_max=batch_max,
+                    mol_atom_ptr=np.array(ptr, dtype=np.int32))
+
+
 def periodic_cell(seed: int = 1005, cell=(9.0, 10.0, 11.0), n_atoms: int = 3, n_rad: int = 16,
                   n_theta: int = 6, n_phi: int = 12, r_nb: float = 8.0, n_shell: int = 2,
                   batch_max: int = 64) -> Workload:
@@ -267,6 +301,21 @@ def potential(points: np.ndarray, wl: Workload, chunk: int = 65536) -> np.ndarra
         if periodic:
             f = f * _smoothstep_cut(d, 2.0 * wl.r_c - 1.0, 2.0 * wl.r_c)
         out[s:s + chunk] = -(f * Zc[None, :]).sum(-1)
+    return out
+
+
+def molecule_potential(points: np.ndarray, point_atom: np.ndarray, wl: Workload) -> np.ndarray:
+    """v of a batched workload: each point feels only its own molecule (the
+    molecule of the atom that generated it, point_atom)."""
+    points = np.ascontiguousarray(points, dtype=np.float64).reshape(-1, 3)
+    mol = np.searchsorted(wl.mol_atom_ptr, np.asarray(point_atom), side="right") - 1
+    order = np.argsort(mol, kind="stable")
+    bounds = np.searchsorted(mol[order], np.arange(wl.n_molecules + 1))
+    out = np.empty(points.shape[0], dtype=np.float64)
+    for m in range(wl.n_molecules):
+        sel = order[bounds[m]:bounds[m + 1]]
+        if len(sel):
+            out[sel] = potential(points[sel], wl.molecule(m))
     return out
 
 
