@@ -217,7 +217,7 @@ def main():
     ap.add_argument("--prec", default="split", choices=["split", "fp64"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="cluster64", choices=["cluster64", "water"])
-    ap.add_argument("--cpu-stride", type=int, default=11)
+    ap.add_argument("--cpu-stride", type=int, default=4)
     ap.add_argument("--ref-stride", type=int, default=61)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

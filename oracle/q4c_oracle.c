@@ -455,7 +455,7 @@ double orc_becke_weight(int n_c, const double* centres, int owner, const double 
 
 /* Raw grid of every (0-cell) atom, Becke weights, pruning.
  * Raw point id = ((atom*n_rad + i)*n_theta + a)*n_phi + b; i radial shell
- * (ascending x_i order, i.e. decreasing r), a Gauss-Legendre node in cos(theta)
+ * (i = 1..N of x_i = cos(i pi/(N+1)), so decreasing r), a Gauss-Legendre node in cos(theta)
  * (ascending), b azimuth phi_b = (b + 1/2) 2 pi / n_phi.
  * The Becke partition runs over all centres (atoms and, in a periodic cell,
  * their images) within r_nb; the owner is the generating atom in cell 0.

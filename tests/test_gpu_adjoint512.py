@@ -1,0 +1,92 @@
+"""The adjoint at the 512-atom configuration (~6,400 functions, 20M raw grid
+points, batches <= 128): dL/dv on every point through the autograd function,
+checked at sampled points against the oracle (its own Becke weights and
+basis at those points), by central differences of L (L is linear in v, so
+a large step is exact up to rounding), and along a random direction."""
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_2608_00773_gb300 as q
+from workloads import ADJOINT_KINDS, cluster512, fill_pattern, potential
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def big():
+    import torch
+    from paper_2608_00773_gb300 import _build
+    _build.build()
+    O.build()
+    wl = cluster512()
+    tables, grid = q.setup(wl)
+    ex = grid.export()
+    pat = (ex["blk_ptr"], ex["blk_col"], ex["blk_off"])
+    G_h = [fill_pattern(*pat, wl.nf_of_atom, 2004, k, a) for k, a in ADJOINT_KINDS]
+    G = [torch.tensor(g, device="cuda") for g in G_h]
+    v = torch.tensor(potential(ex["xyz"], wl), device="cuda")
+    return wl, tables, grid, ex, G_h, G, v
+
+
+def _L(tables, grid, v, G, prec):
+    mats = q.q4c_integrate(tables, grid, v, prec)[:5]
+    return sum(float((m * g).sum()) for m, g in zip(mats, G))
+
+
+def test_sizes(big):
+    wl, tables, grid, ex, *_ = big
+    assert wl.n_raw_points == 20070400 and 6000 < wl.n_basis < 6800
+    assert grid.info.max_np <= 128
+
+
+def test_autograd_equals_backward_and_oracle_samples(big):
+    import torch
+    wl, tables, grid, ex, G_h, G, v = big
+    vv = v.clone().requires_grad_(True)
+    outs = q.integrate(vv, tables, grid, "split")
+    L = sum((o * g).sum() for o, g in zip(outs, G))
+    L.backward()
+    g_auto = vv.grad.detach().cpu().numpy()
+    g_direct = q.q4c_integrate_backward(tables, grid, G, "split").cpu().numpy()
+    grid.status()
+    assert np.array_equal(g_auto, g_direct)
+    # the oracle at 64 sampled points: its own Becke weights there and its own basis
+    rng = np.random.default_rng(2004)
+    idx = rng.choice(len(ex["w"]), 64, replace=False)
+    ppa = wl.n_rad * wl.n_theta * wl.n_phi
+    owner = ex["point_id"][idx] // ppa
+    ob = O.OracleBasis(wl)
+    pat = ob.pattern()
+    assert np.array_equal(pat.blk_off, ex["blk_off"])
+    w_orc = np.array([O.becke_weight(wl.xyz, int(a), ex["xyz"][i], wl.r_nb) for i, a in zip(idx, owner)])
+    # base weights (radial x angular) are the library's w / its Becke factor; compare
+    # the ratio structure instead: w_lib / p_orc is a product-grid weight, the same
+    # for every point of one (shell, theta) pair
+    shell_theta = (ex["point_id"][idx] % ppa) // wl.n_phi
+    base = ex["w"][idx] / w_orc
+    r, wr = O.radial_shells(wl.n_rad, wl.R)
+    ct, wt = O.gauss_legendre(wl.n_theta)
+    ref_base = wr[shell_theta // wl.n_theta] * wt[shell_theta % wl.n_theta] * 2 * np.pi / wl.n_phi
+    assert np.allclose(base, ref_base, rtol=1e-12, atol=0)
+    gref = ob.adjoint(ex["xyz"][idx], ex["w"][idx], G_h, pat)
+    err = np.abs(g_direct[idx] - gref).max() / np.abs(gref).max()
+    assert err <= 1e-9, err
+
+
+def test_central_differences_and_direction(big):
+    """(L(v + h e_p) - L(v - h e_p)) / 2h = dL/dv_p for any h (L is linear in v)."""
+    import torch
+    wl, tables, grid, ex, G_h, G, v = big
+    g = q.q4c_integrate_backward(tables, grid, G, "fp64").cpu().numpy()
+    rng = np.random.default_rng(7)
+    h = 1e4
+    scale = np.abs(g).max()
+    for p in rng.choice(len(g), 12, replace=False):
+        e = torch.zeros_like(v)
+        e[int(p)] = h
+        fd = (_L(tables, grid, v + e, G, "fp64") - _L(tables, grid, v - e, G, "fp64")) / (2 * h)
+        assert abs(fd - g[p]) <= 1e-9 * scale, (p, fd, g[p])
+    u = torch.tensor(rng.standard_normal(len(g)), device="cuda")
+    dd = (_L(tables, grid, v + u, G, "fp64") - _L(tables, grid, v - u, G, "fp64")) / 2
+    assert abs(dd - float(np.dot(u.cpu().numpy(), g))) <= 1e-10 * abs(dd)

@@ -178,6 +178,14 @@ def cluster64() -> Workload:
     return heavy_light_cluster(64, 24.0, 4.0, seed=1002, name="cluster-64atom")
 
 
+def cluster512() -> Workload:
+    """The 512-atom adjoint configuration: the 64-atom rules in a 64 Bohr cube
+    (minimum separation 4, ~6,400 functions), 100 x (14 x 28) points per atom
+    (20.07M raw), batches <= 128, seed 1004."""
+    return heavy_light_cluster(512, 64.0, 4.0, seed=1004, n_rad=100, n_theta=14, n_phi=28, batch_max=128,
+                               name="cluster-512atom")
+
+
 def small_cluster(n_atoms: int = 8, seed: int = 7, n_rad: int = 24, n_theta: int = 8,
                   n_phi: int = 16, batch_max: int = 200) -> Workload:
     """A reduced heavy/light cluster that the oracle finishes in seconds but
