@@ -6,6 +6,7 @@
 // partition weights, the only arithmetic-heavy setup step (O(|N(r)|^2) per
 // point), run in one kernel.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdlib>
 #include <numeric>
@@ -389,27 +390,8 @@ extern "C" q4c_status grid_partition(const q4c_grid_desc* d, const q4c_tables* t
   std::vector<int64_t> bptr{0};
   {
     struct Range { int64_t lo, hi; };
-    // one root range per molecule (kept points are atom-major, so each
-    // molecule's points are contiguous); the roots pushed in reverse so that
-    // the molecules' batches come out in molecule order
-    std::vector<Range> stack, leaves;
-    {
-      std::vector<Range> roots;
-      int64_t i = 0;
-      for (int m = 0; m < n_mol; ++m) {
-        const int64_t lo = i;
-        while (i < static_cast<int64_t>(order.size()) && atom_mol[order[i] / ppa] == m) ++i;
-        if (i > lo) roots.push_back({lo, i});
-      }
-      stack.assign(roots.rbegin(), roots.rend());
-    }
-    while (!stack.empty()) {
-      Range r = stack.back();
-      stack.pop_back();
-      if (r.hi - r.lo <= d->batch_max) {
-        leaves.push_back(r);
-        continue;
-      }
+    // split r at the median of its longest bounding-box axis (in place)
+    auto split = [&](const Range& r) -> int64_t {
       double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
       for (int64_t i = r.lo; i < r.hi; ++i)
         for (int k = 0; k < 3; ++k) {
@@ -426,11 +408,65 @@ extern "C" q4c_status grid_partition(const q4c_grid_desc* d, const q4c_tables* t
                          const double ca = raw[3 * a + ax], cb = raw[3 * b + ax];
                          return ca < cb || (ca == cb && a < b);
                        });
-      // right half pushed first so the left half is emitted first (DFS order)
-      stack.push_back({mid, r.hi});
-      stack.push_back({r.lo, mid});
+      return mid;
+    };
+    // one root range per molecule (kept points are atom-major, so each
+    // molecule's points are contiguous), then a few breadth-first levels so
+    // that there are enough independent subtrees for the host threads; the
+    // leaves of every subtree come out depth-first, left half first, and the
+    // subtrees are concatenated left to right: the same batches as one
+    // depth-first pass
+    std::vector<Range> front;
+    {
+      int64_t i = 0;
+      for (int m = 0; m < n_mol; ++m) {
+        const int64_t lo = i;
+        while (i < static_cast<int64_t>(order.size()) && atom_mol[order[i] / ppa] == m) ++i;
+        if (i > lo) front.push_back({lo, i});
+      }
     }
-    for (const Range& r : leaves) bptr.push_back(r.hi);
+    for (int level = 0; level < 12 && front.size() < 64; ++level) {
+      std::vector<Range> next;
+      bool any = false;
+      for (const Range& r : front) {
+        if (r.hi - r.lo <= d->batch_max) {
+          next.push_back(r);
+          continue;
+        }
+        const int64_t mid = split(r);
+        next.push_back({r.lo, mid});
+        next.push_back({mid, r.hi});
+        any = true;
+      }
+      front.swap(next);
+      if (!any) break;
+    }
+    std::vector<std::vector<Range>> leaves(front.size());
+    std::atomic<int64_t> next_sub{0};
+    auto worker = [&] {
+      for (int64_t f; (f = next_sub.fetch_add(1)) < static_cast<int64_t>(front.size());) {
+        std::vector<Range> stack{front[f]};
+        while (!stack.empty()) {
+          Range r = stack.back();
+          stack.pop_back();
+          if (r.hi - r.lo <= d->batch_max) {
+            leaves[f].push_back(r);
+            continue;
+          }
+          const int64_t mid = split(r);
+          stack.push_back({mid, r.hi});  // right half pushed first: left half emitted first
+          stack.push_back({r.lo, mid});
+        }
+      }
+    };
+    {
+      const unsigned nt = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+      std::vector<std::thread> th;
+      for (unsigned t = 0; t < nt; ++t) th.emplace_back(worker);
+      for (auto& x : th) x.join();
+    }
+    for (const auto& lv : leaves)
+      for (const Range& r : lv) bptr.push_back(r.hi);
   }
   const int64_t nB = static_cast<int64_t>(bptr.size()) - 1;
   const int64_t nP = static_cast<int64_t>(order.size());

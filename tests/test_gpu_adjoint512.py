@@ -19,13 +19,18 @@ def big():
     from paper_2608_00773_gb300 import _build
     _build.build()
     O.build()
+    import time
+    t0 = time.time()
     wl = cluster512()
     tables, grid = q.setup(wl)
+    t1 = time.time()
     ex = grid.export()
     pat = (ex["blk_ptr"], ex["blk_col"], ex["blk_off"])
     G_h = [fill_pattern(*pat, wl.nf_of_atom, 2004, k, a) for k, a in ADJOINT_KINDS]
     G = [torch.tensor(g, device="cuda") for g in G_h]
-    v = torch.tensor(potential(ex["xyz"], wl), device="cuda")
+    t2 = time.time()
+    v = torch.tensor(potential(ex["xyz"], wl, device="cuda"), device="cuda")
+    print(f"grid {t1 - t0:.1f} s, export + G {t2 - t1:.1f} s, v {time.time() - t2:.1f} s")
     return wl, tables, grid, ex, G_h, G, v
 
 

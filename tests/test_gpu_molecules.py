@@ -16,11 +16,15 @@ TOL = {"fp64": 1e-12, "split": 1e-9}
 
 
 def _lib(wl):
+    import time
     import torch
+    t0 = time.time()
     tables, grid = q.setup(wl)
+    t1 = time.time()
     ex = grid.export()
     ppa = wl.n_rad * wl.n_theta * wl.n_phi
-    v = torch.tensor(molecule_potential(ex["xyz"], ex["point_id"] // ppa, wl), device="cuda")
+    v = torch.tensor(molecule_potential(ex["xyz"], ex["point_id"] // ppa, wl, device="cuda"), device="cuda")
+    print(f"grid {t1 - t0:.1f} s, export + v {time.time() - t1:.1f} s")
     return tables, grid, ex, v
 
 

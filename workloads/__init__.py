@@ -284,12 +284,13 @@ def _smoothstep_cut(d: np.ndarray, r_on: float, r_off: float) -> np.ndarray:
     return 1.0 - s * s * s * (10.0 - 15.0 * s + 6.0 * s * s)
 
 
-def potential(points: np.ndarray, wl: Workload, chunk: int = 65536) -> np.ndarray:
+def potential(points: np.ndarray, wl: Workload, chunk: int = 65536, device=None) -> np.ndarray:
     """v(r) = sum_A -Z_A erf(d_A)/d_A, d_A = |r - R_A|, with
     erf(d)/d -> 2/sqrt(pi) (1 - d^2/3 + d^4/10) for d < 1e-4.
     Periodic workloads sum over the images within 2 r_c, each term times a
     quintic smoothstep that goes from 1 at 2 r_c - 1 to 0 at 2 r_c (the bare
-    lattice sum of -Z/r diverges)."""
+    lattice sum of -Z/r diverges).  device (a torch device) evaluates the same
+    expression in FP64 with torch there, for inputs of many million points."""
     points = np.ascontiguousarray(points, dtype=np.float64).reshape(-1, 3)
     Z = wl.Z_of_atom
     centres, Zc = wl.xyz, Z
@@ -298,6 +299,8 @@ def potential(points: np.ndarray, wl: Workload, chunk: int = 65536) -> np.ndarra
         sh = _images(wl, 2.0 * wl.r_c + wl.r_nb)
         centres = (wl.xyz[None, :, :] + sh[:, None, :]).reshape(-1, 3)
         Zc = np.tile(Z, len(sh))
+    if device is not None:
+        return _potential_torch(points, centres, Zc, wl, periodic, device)
     out = np.empty(points.shape[0], dtype=np.float64)
     c = 2.0 / math.sqrt(math.pi)
     for s in range(0, points.shape[0], chunk):
@@ -312,7 +315,28 @@ def potential(points: np.ndarray, wl: Workload, chunk: int = 65536) -> np.ndarra
     return out
 
 
-def molecule_potential(points: np.ndarray, point_atom: np.ndarray, wl: Workload) -> np.ndarray:
+def _potential_torch(points, centres, Zc, wl, periodic, device) -> np.ndarray:
+    import torch
+    C = torch.tensor(centres, dtype=torch.float64, device=device)
+    Zt = torch.tensor(Zc, dtype=torch.float64, device=device)
+    out = np.empty(points.shape[0], dtype=np.float64)
+    c = 2.0 / math.sqrt(math.pi)
+    step = max(1, (1 << 26) // max(len(Zc), 1))
+    for s in range(0, points.shape[0], step):
+        P = torch.tensor(points[s:s + step], dtype=torch.float64, device=device)
+        d = torch.sqrt(((P[:, None, :] - C[None, :, :]) ** 2).sum(-1))
+        small = d < 1e-4
+        ds = torch.where(small, torch.ones_like(d), d)
+        f = torch.where(small, c * (1.0 - d * d / 3.0 + d ** 4 / 10.0), torch.special.erf(ds) / ds)
+        if periodic:
+            r_on, r_off = 2.0 * wl.r_c - 1.0, 2.0 * wl.r_c
+            t = torch.clamp((d - r_on) / (r_off - r_on), 0.0, 1.0)
+            f = f * (1.0 - t * t * t * (10.0 - 15.0 * t + 6.0 * t * t))
+        out[s:s + step] = (-(f * Zt[None, :]).sum(-1)).cpu().numpy()
+    return out
+
+
+def molecule_potential(points: np.ndarray, point_atom: np.ndarray, wl: Workload, device=None) -> np.ndarray:
     """v of a batched workload: each point feels only its own molecule (the
     molecule of the atom that generated it, point_atom)."""
     points = np.ascontiguousarray(points, dtype=np.float64).reshape(-1, 3)
@@ -323,7 +347,7 @@ def molecule_potential(points: np.ndarray, point_atom: np.ndarray, wl: Workload)
     for m in range(wl.n_molecules):
         sel = order[bounds[m]:bounds[m + 1]]
         if len(sel):
-            out[sel] = potential(points[sel], wl.molecule(m))
+            out[sel] = potential(points[sel], wl.molecule(m), device=device)
     return out
 
 
