@@ -153,7 +153,7 @@ __global__ void __launch_bounds__(256) k_gslice(DevGrid G, int64_t b0, int anti_
 #pragma unroll
     for (int s = 0; s < kSlices; ++s) {
       const __nv_bfloat162 h2 = __floats2bfloat162_rn(d0[s], d1[s]);
-      o[s * (kTileBytes / 4)] = *reinterpret_cast<const uint32_t*>(&h2);
+      o[b_tile(s) * (kTileBytes / 4)] = *reinterpret_cast<const uint32_t*>(&h2);  // [B0, B2, B4, B1, B3, B5]
     }
   }
 }
@@ -218,7 +218,7 @@ struct StepIter {
 //               of the step's G' digits into the stage (expect_tx on
 //               full[stage]); all slice the 64 x 16 block of F (raw values
 //               by cp.async three steps ahead) and arrive on full[stage];
-//   warp 16     (one thread) issues the twelve MMAs per step into the group's
+//   warp 16     (one thread) issues the six MMAs per step into the group's
 //               accumulator set (groups alternate between two sets), commits
 //               empty[stage] and, after the group's last step, accfull[set];
 //   warps 8-15  read U's levels from tensor memory, dot each column with R
@@ -373,16 +373,13 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int n = blockIdx.x; n < n_items && ok; n += gridDim.x) {
         const ItemInfo I = item_info(G, items[n]);
         for (int grp = 0; grp < I.n_jt * n_prod && ok; ++grp, ++k) {
-          const int jt = grp / n_prod;
-          const int N = (min(kTile, I.nb - jt * kTile) + 15) & ~15;
-          const uint32_t idesc = make_idesc(128, N);
           const int set = k & 1;
           if (!mbar_wait_abort(accempty_bar(set), ((k >> 1) & 1) ^ 1, s_abort, status, 64)) {
             ok = false;
             break;
           }
           tc_fence_after();
-          const uint32_t t0 = tmem + set * kSetCols, t1 = t0 + kTile, t2 = t0 + 2 * kTile;
+          const uint32_t t0 = tmem + set * kSetCols;
           for (int ic = 0; ic < I.n_ic; ++ic, ++g) {
             const int st = g % kStages;
             if (!mbar_wait_abort(full_bar(st), (g / kStages) & 1, s_abort, status, 32)) {
@@ -391,21 +388,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             tc_fence_after();
             const uint32_t a = smem_u32(smem + kSmemStages + st * kStage), bb = a + kStageA;
-            const uint32_t acc = ic == 0 ? 0u : 1u;
-            auto A = [&](int q) { return make_desc(a + q * kTileBytes, kSBO); };
-            auto Bt = [&](int t) { return make_desc(bb + t * kTileBytes, kSBO); };
-            mma_bf16(t0, A(1), Bt(0), idesc, acc);
-            mma_bf16(t0, A(0), Bt(1), idesc, 1u);
-            mma_bf16(t1, A(3), Bt(0), idesc, acc);
-            mma_bf16(t1, A(2), Bt(1), idesc, 1u);
-            mma_bf16(t1, A(1), Bt(2), idesc, 1u);
-            mma_bf16(t1, A(0), Bt(3), idesc, 1u);
-            mma_bf16(t2, A(5), Bt(0), idesc, acc);
-            mma_bf16(t2, A(4), Bt(1), idesc, 1u);
-            mma_bf16(t2, A(3), Bt(2), idesc, 1u);
-            mma_bf16(t2, A(2), Bt(3), idesc, 1u);
-            mma_bf16(t2, A(1), Bt(4), idesc, 1u);
-            mma_bf16(t2, A(0), Bt(5), idesc, 1u);
+            mma_levels(t0, a, bb, ic == 0 ? 0u : 1u);
             mma_commit(empty_bar(st));
           }
           if (ok) mma_commit(accfull_bar(set));

@@ -23,16 +23,14 @@
 // The precision is relative to the column maxima of each batch, which near
 // heavy nuclei sit far above the typical values, hence six slices (47 bits).
 //
-// Layout trick: the six slices of one operand set live in shared memory as
-// seven consecutive 64-row tiles [Z, A0, A1, A2, A3, A4, A5] (Z = zeros).  An
-// M = 128 MMA starting at tile k reads rows [tile_k; tile_k+1] and so adds
-// A_s B_t to the top half (level s + t) and A_(s+1) B_t to the bottom half
-// (level s + t + 1) of a TMEM block: twelve MMAs per K-step cover the
-// twenty-one slice pairs with s + t <= 5,
-//   block 0 = [L0; L1]: [A0;A1] x B0, [Z;A0] x B1
-//   block 1 = [L2; L3]: [A2;A3] x B0, [A1;A2] x B1, [A0;A1] x B2, [Z;A0] x B3
-//   block 2 = [L4; L5]: [A4;A5] x B0, [A3;A4] x B1, [A2;A3] x B2,
-//                       [A1;A2] x B3, [A0;A1] x B4, [Z;A0] x B5.
+// Layout trick: the six slices of the A operand live in shared memory as
+// seven consecutive 64-row tiles [Z, A0, A1, A2, A3, A4, A5] (Z = zeros), so an
+// M = 128 MMA starting at tile k reads rows [A_(k-1); A_k] and adds A_s B_t to
+// the top half (level s + t) and A_(s+1) B_t to the bottom half (level
+// s + t + 1) of a TMEM block; the B slices are stored [B0, B2, B4, B1, B3, B5],
+// so one MMA with N = 64, 128 or 192 covers B_t, B_(t+2), ... and lands in
+// consecutive blocks [L0;L1], [L2;L3], [L4;L5].  Six MMAs per K-step cover the
+// twenty-one slice pairs with s + t <= 5 (tc::mma_levels lists them).
 //
 // Outputs per (batch, 64x64 tile): V = (D Phi)^T Phi, W0 = sum_q (D Q)^T Q
 // (three products into one accumulator, sliced against a common exponent per
@@ -140,7 +138,7 @@ __device__ __forceinline__ void issue_step(const float2* base, int64_t plane, in
 //               read it have completed (empty[stage], a tcgen05.commit), then
 //               arrive on full[stage]; each thread's raw values arrive by
 //               cp.async three steps ahead, in a ring of its own;
-//   warp 12     (one thread) waits full[stage], issues the twelve MMAs into the
+//   warp 16     (one thread) waits full[stage], issues the six MMAs into the
 //               item's accumulator set (items alternate between two sets of
 //               192 TMEM columns), commits empty[stage], and after an item's
 //               last step commits accfull[set];
@@ -294,8 +292,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             const int off = rg * kSBO + kq * kLBO + (lane >> 2) * 16 + (lane & 3) * 4;
 #pragma unroll
-            for (int t = 0; t < kSlices; ++t)
-              *reinterpret_cast<__nv_bfloat162*>(dst + t * kTileBytes + off) = __floats2bfloat162_rn(d0[t], d1[t]);
+            for (int t = 0; t < kSlices; ++t)  // A: [Z, A0..A5]; B: [B0, B2, B4, B1, B3, B5]
+              *reinterpret_cast<__nv_bfloat162*>(dst + (side == 0 ? t : b_tile(t)) * kTileBytes + off) =
+                  __floats2bfloat162_rn(d0[t], d1[t]);
           }
         }
         fence_async_smem();
@@ -309,14 +308,11 @@ __global__ void __launch_bounds__(kThreads, 1)
       int g = 0, k = 0;
       for (int n = blockIdx.x; n < n_items; n += gridDim.x, ++k) {
         const int4 item = items[n];
-        const int nb = static_cast<int>(G.bat_fn_ptr[item.x + 1] - G.bat_fn_ptr[item.x]);
-        const int N = (min(kTile, nb - item.w * kTile) + 15) & ~15;
-        const uint32_t idesc = make_idesc(128, N);
         const int n_steps = item_steps(G, item);
         const int set = k & 1;
         if (!mbar_wait_abort(accempty_bar(set), ((k >> 1) & 1) ^ 1, s_abort, status, 64)) break;
         tc_fence_after();
-        const uint32_t t0 = tmem + set * kSetCols, t1 = t0 + kTile, t2 = t0 + 2 * kTile;
+        const uint32_t t0 = tmem + set * kSetCols;
         bool ok = true;
         for (int s = 0; s < n_steps; ++s, ++g) {
           const int st = g % kStages;
@@ -326,21 +322,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           tc_fence_after();
           const uint32_t a = smem_u32(smem + kSmemStages + st * kStage), bb = a + kStageA;
-          const uint32_t acc = s == 0 ? 0u : 1u;
-          auto A = [&](int q) { return make_desc(a + q * kTileBytes, kSBO); };
-          auto Bt = [&](int t) { return make_desc(bb + t * kTileBytes, kSBO); };
-          mma_bf16(t0, A(1), Bt(0), idesc, acc);  // [A0;A1] x B0 -> L0, L1
-          mma_bf16(t0, A(0), Bt(1), idesc, 1u);   // [Z;A0]  x B1 -> L1
-          mma_bf16(t1, A(3), Bt(0), idesc, acc);  // [A2;A3] x B0 -> L2, L3
-          mma_bf16(t1, A(2), Bt(1), idesc, 1u);   // [A1;A2] x B1
-          mma_bf16(t1, A(1), Bt(2), idesc, 1u);   // [A0;A1] x B2
-          mma_bf16(t1, A(0), Bt(3), idesc, 1u);   // [Z;A0]  x B3 -> L3
-          mma_bf16(t2, A(5), Bt(0), idesc, acc);  // [A4;A5] x B0 -> L4, L5
-          mma_bf16(t2, A(4), Bt(1), idesc, 1u);   // [A3;A4] x B1
-          mma_bf16(t2, A(3), Bt(2), idesc, 1u);   // [A2;A3] x B2
-          mma_bf16(t2, A(2), Bt(3), idesc, 1u);   // [A1;A2] x B3
-          mma_bf16(t2, A(1), Bt(4), idesc, 1u);   // [A0;A1] x B4
-          mma_bf16(t2, A(0), Bt(5), idesc, 1u);   // [Z;A0]  x B5 -> L5
+          mma_levels(t0, a, bb, s == 0 ? 0u : 1u);
           mma_commit(empty_bar(st));
         }
         if (!ok) break;

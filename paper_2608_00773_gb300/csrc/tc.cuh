@@ -49,6 +49,39 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
                : "memory");
 }
 
+// ---- the 21 slice products of one K-step (s + t <= 5) as six MMAs
+// Operand tiles are 64 rows x 16 K BF16 (2 KB, no-swizzle K-major).  A is
+// stored as seven tiles [Z, A0..A5] (Z zeros), so the M = 128 operand starting
+// at tile q is [A_(q-1); A_q]; B is stored as [B0, B2, B4, B1, B3, B5].  An MMA
+// of [A_a; A_(a+1)] with the consecutive B tiles B_t, B_(t+2), ... (a + t even)
+// adds level a + t + 2c to the top lanes and level a + t + 2c + 1 to the bottom
+// lanes of the 64-column block (a + t)/2 + c, so the three blocks [L0;L1],
+// [L2;L3], [L4;L5] at tmem receive exactly the pairs of their levels:
+//   [A0;A1] x [B0,B2,B4]  -> blocks 0-2   (6 pairs)
+//   [Z;A0]  x [B1,B3,B5]  -> blocks 0-2   (3 pairs, bottom lanes)
+//   [A2;A3] x [B0,B2]     -> blocks 1-2   (4 pairs)
+//   [A1;A2] x [B1,B3]     -> blocks 1-2   (4 pairs)
+//   [A4;A5] x B0          -> block 2      (2 pairs)
+//   [A3;A4] x B1          -> block 2      (2 pairs)
+constexpr int kLevelTile = 2048;     // bytes per operand tile
+constexpr uint32_t kLevelSBO = 256;  // bytes between 8-row groups
+
+// tile position of B slice t in the stage
+__host__ __device__ constexpr int b_tile(int t) { return (t & 1) ? 3 + (t >> 1) : (t >> 1); }
+
+// a, b: shared addresses of tile Z of A and of the first B tile; acc = 0 starts
+// the accumulators (the first MMA covers all three blocks)
+__device__ __forceinline__ void mma_levels(uint32_t tmem, uint32_t a, uint32_t b, uint32_t acc) {
+  auto A = [&](int q) { return make_desc(a + q * kLevelTile, kLevelSBO); };
+  auto Bt = [&](int pos) { return make_desc(b + pos * kLevelTile, kLevelSBO); };
+  mma_bf16(tmem, A(1), Bt(0), make_idesc(128, 192), acc);
+  mma_bf16(tmem, A(0), Bt(3), make_idesc(128, 192), 1u);
+  mma_bf16(tmem + 64, A(3), Bt(0), make_idesc(128, 128), 1u);
+  mma_bf16(tmem + 64, A(2), Bt(3), make_idesc(128, 128), 1u);
+  mma_bf16(tmem + 128, A(5), Bt(0), make_idesc(128, 64), 1u);
+  mma_bf16(tmem + 128, A(4), Bt(3), make_idesc(128, 64), 1u);
+}
+
 __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
 }
