@@ -202,7 +202,7 @@ q4c_status launch_fill_idx(const q4c_tables* t, const q4c_grid* g, int64_t b0, i
 }  // namespace q4c
 
 static int64_t scratch_cap_doubles() {
-  int64_t mb = 2048;
+  int64_t mb = 4096;
   if (const char* e = std::getenv("Q4C_SCRATCH_MB")) mb = std::max<int64_t>(16, std::atoll(e));
   return mb * (1 << 20) / 8;
 }

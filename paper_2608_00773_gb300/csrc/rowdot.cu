@@ -119,14 +119,23 @@ __global__ void __launch_bounds__(256) k_gslice(DevGrid G, int64_t b0, int anti_
   uint32_t* out = gsl + (gsl_off[b] + static_cast<int64_t>(m) * n_jt * n_ic * kBlockB) / 4;
   for (int j = threadIdx.x; j < nb; j += blockDim.x) sMax[j] = 0u;
   __syncthreads();
-  // pass 1: column maxima, element-parallel (pairs (i, i+1) of one column per thread step)
-  const int half = (nb + 1) / 2;
-  for (int e = threadIdx.x; e < nb * half; e += blockDim.x) {
-    const int j = e / half, i = 2 * (e - j * half);
-    const float h0 = fabsf(gprime_df(M, idx, nb, anti, i, j).hi);
-    const float h1 = i + 1 < nb ? fabsf(gprime_df(M, idx, nb, anti, i + 1, j).hi) : 0.f;
-    const float mx = fmaxf(h0, h1);
-    if (mx > 0.f) atomicMax(&sMax[j], __float_as_uint(mx));
+  // pass 1: column maxima, element-parallel, four gathers in flight per thread
+  constexpr int kU = 4;
+  const int nn = nb * nb;
+  for (int e0 = threadIdx.x; e0 < nn; e0 += kU * blockDim.x) {
+    df x[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int e = e0 + u * blockDim.x;
+      x[u] = e < nn ? gprime_df(M, idx, nb, anti, e / nb, e - (e / nb) * nb) : df{0.f, 0.f};
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int e = e0 + u * blockDim.x;
+      if (e >= nn) break;
+      const float a = fabsf(x[u].hi);
+      if (a > 0.f) atomicMax(&sMax[e - (e / nb) * nb], __float_as_uint(a));
+    }
   }
   __syncthreads();
   // pass 2: the six digits of every element, in the B-operand tile layout
@@ -156,17 +165,6 @@ __global__ void __launch_bounds__(256) k_gslice(DevGrid G, int64_t b0, int anti_
       o[b_tile(s) * (kTileBytes / 4)] = *reinterpret_cast<const uint32_t*>(&h2);  // [B0, B2, B4, B1, B3, B5]
     }
   }
-}
-
-__device__ __forceinline__ void expect_tx(uint32_t bar, uint32_t bytes) {
-  asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-
-__device__ __forceinline__ void bulk_copy(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-      "l"(src), "r"(bytes), "r"(bar)
-      : "memory");
 }
 
 // 8-byte asynchronous copy (zero-filled past src_bytes)
