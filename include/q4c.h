@@ -218,6 +218,18 @@ Q4C_API q4c_status q4c_integrate(const q4c_tables* tables, const q4c_grid* grid,
 Q4C_API q4c_status q4c_density(const q4c_tables* tables, const q4c_grid* grid, const double* P_dev,
                        q4c_precision prec, double* n_dev, q4c_stream stream);
 
+/* Density with the gradient (small-component) terms (the density counterpart
+ * of the W0 and W_SO integrands, Eqs. 4, 21, 39-40 with the kinetic-balance
+ * small component of R1):
+ *   n_p = sum_ij [ P^V_ij phi_i phi_j + P^W0_ij grad phi_i . grad phi_j
+ *                  + sum_k P^SOk_ij (grad phi_i x grad phi_j)_k ](p)
+ * P->V..P->SOz device [nnz] on the block pattern, NULL slots count as zero
+ * (only the symmetric part of P^V, P^W0 and the antisymmetric part of P^SOk
+ * contribute); spinor_SS is ignored.  n_dev device [n_points], overwritten.
+ * With only the V slot it equals q4c_density. */
+Q4C_API q4c_status q4c_density_full(const q4c_tables* tables, const q4c_grid* grid, const q4c_matrices* P,
+                            q4c_precision prec, double* n_dev, q4c_stream stream);
+
 /* Adjoint of q4c_integrate for L = <G^V,V> + <G^W0,W0> + sum_k <G^SOk,SOk>:
  *   dLdv_p = w_p sum_M sum_ij G^M_ij f^M_ij(p)
  * with f^V = phi_i phi_j, f^W0 = grad phi_i . grad phi_j,

@@ -262,6 +262,12 @@ class OracleBasis:
                           pat.blk_off, *ptrs, out)
         return out
 
+    def density_full(self, xyz, P, pat: Pattern):
+        """n_p = sum_M sum_ij P^M_ij f^M_ij(p), P = [PV, PW0, PSOx, PSOy, PSOz] (None = 0):
+        the density with the gradient terms, i.e. the adjoint's sum with unit weights."""
+        n = len(_f64(xyz).reshape(-1)) // 3
+        return self.adjoint(xyz, np.ones(n), P, pat)
+
     def spinor_ss(self, W0, SOx, SOy, SOz, pat: Pattern):
         """Complex SS spinor blocks (Eq. 16, kinetic-balance reading), complex128 [4*nnz]."""
         out = np.zeros(8 * pat.nnz)

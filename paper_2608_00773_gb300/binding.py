@@ -24,7 +24,7 @@ STATUS = {0: "Q4C_OK", 1: "Q4C_EINVAL", 2: "Q4C_ENOMEM", 3: "Q4C_ECUDA", 4: "Q4C
 
 # every symbol include/q4c.h declares
 EXPORTS = ["nao_tabulate", "q4c_tables_destroy", "q4c_tables_export", "grid_partition", "q4c_grid_destroy",
-           "q4c_grid_get_info", "q4c_grid_export", "q4c_grid_export_shifts", "q4c_grid_points", "q4c_integrate", "q4c_density",
+           "q4c_grid_get_info", "q4c_grid_export", "q4c_grid_export_shifts", "q4c_grid_points", "q4c_integrate", "q4c_density", "q4c_density_full",
            "q4c_integrate_backward", "q4c_integrate_noalloc", "q4c_basis_eval", "q4c_grid_status", "q4c_profile", "q4c_profile_read",
            "q4c_last_error"]
 
@@ -85,6 +85,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     L.q4c_integrate.argtypes = [vp, vp, vp, C.c_int, C.POINTER(Matrices), vp]
     L.q4c_density.argtypes = [vp, vp, vp, C.c_int, vp, vp]
     L.q4c_integrate_backward.argtypes = [vp, vp, C.POINTER(Matrices), C.c_int, vp, vp]
+    L.q4c_density_full.argtypes = [vp, vp, C.POINTER(Matrices), C.c_int, vp, vp]
     L.q4c_integrate_noalloc.argtypes = [vp, vp, vp, C.POINTER(Matrices), vp]
     L.q4c_basis_eval.argtypes = [vp, vp, i64, vp, vp, vp, vp]
     L.q4c_grid_status.argtypes = [vp, vp]
@@ -253,6 +254,17 @@ def q4c_density(tables: Tables, grid: Grid, P, prec="fp64", out=None, stream=Non
     if out is None:
         out = torch.empty(grid.n_points, dtype=torch.float64, device=P.device)
     _check(load().q4c_density(tables.h, grid.h, _ptr(P), _prec(prec), _ptr(out), _stream(stream)))
+    return out
+
+
+def q4c_density_full(tables: Tables, grid: Grid, P: Sequence, prec="fp64", out=None, stream=None):
+    """n_p = sum_M sum_ij P^M_ij f^M_ij(p) for P = [PV, PW0, PSOx, PSOy, PSOz], None = 0."""
+    import torch
+    dev = next(x for x in P if x is not None).device
+    if out is None:
+        out = torch.empty(grid.n_points, dtype=torch.float64, device=dev)
+    m = Matrices(*[_ptr(x) for x in P], 0)
+    _check(load().q4c_density_full(tables.h, grid.h, C.byref(m), _prec(prec), _ptr(out), _stream(stream)))
     return out
 
 

@@ -70,6 +70,25 @@ extern "C" q4c_status q4c_integrate_backward(const q4c_tables* t, const q4c_grid
   }
 }
 
+extern "C" q4c_status q4c_density_full(const q4c_tables* t, const q4c_grid* g, const q4c_matrices* P,
+                                       q4c_precision prec, double* n, q4c_stream stream) {
+  if (q4c_status st = check_pair(t, g, "q4c_density_full")) return st;
+  Q4C_CHECK_ARG(P && n, "q4c_density_full: NULL argument");
+  Q4C_CHECK_ARG(prec == Q4C_FP64 || prec == Q4C_SPLIT, "q4c_density_full: unknown precision");
+  auto s = reinterpret_cast<cudaStream_t>(stream);
+  try {
+    if (!P->V && !P->W0 && !P->SOx && !P->SOy && !P->SOz) {
+      Q4C_CUDA(cudaMemsetAsync(n, 0, sizeof(double) * g->n_pts, s));
+      return Q4C_OK;
+    }
+    if (prec == Q4C_FP64) return backward_fp64(t, g, P, n, s, false);
+    return backward_split(t, g, P, n, s, false);
+  } catch (const std::exception& e) {
+    set_error(std::string("q4c_density_full: ") + e.what());
+    return Q4C_ENOMEM;
+  }
+}
+
 extern "C" q4c_status q4c_basis_eval(const q4c_tables* t, const q4c_grid* g, int64_t n_pts, const double* xyz,
                                      double* phi, double* grad, q4c_stream stream) {
   if (q4c_status st = check_pair(t, g, "q4c_basis_eval")) return st;

@@ -353,7 +353,8 @@ q4c_status density_fp64(const q4c_tables* t, const q4c_grid* g, const double* P,
 constexpr int kRowsB = 8;
 __global__ void k_backward_fp64(DevBasis B, DevGrid G, int64_t b0, const int64_t* __restrict__ scr_off,
                                 const double* __restrict__ scratch, const double* GV, const double* GW,
-                                const double* Gx, const double* Gy, const double* Gz, double* __restrict__ dLdv) {
+                                const double* Gx, const double* Gy, const double* Gz, double* __restrict__ dLdv,
+                                int weighted) {
   extern __shared__ double sG[];  // [5][kRowsB][nb]
   const int64_t b = b0 + blockIdx.x;
   const int64_t p0 = G.pt_ptr[b];
@@ -407,12 +408,12 @@ __global__ void k_backward_fp64(DevBasis B, DevGrid G, int64_t b0, const int64_t
         }
       }
     }
-    if (p < np) dLdv[p0 + p] = G.w[p0 + p] * acc;
+    if (p < np) dLdv[p0 + p] = weighted ? G.w[p0 + p] * acc : acc;
   }
 }
 
 q4c_status backward_fp64(const q4c_tables* t, const q4c_grid* g, const q4c_matrices* Gm, double* dLdv,
-                         cudaStream_t s) {
+                         cudaStream_t s, bool weighted) {
   const DevBasis B = t->view();
   const DevGrid G = g->view();
   const size_t smem = sizeof(double) * 5 * kRowsB * std::max(g->max_nb, 1);
@@ -424,7 +425,8 @@ q4c_status backward_fp64(const q4c_tables* t, const q4c_grid* g, const q4c_matri
     if (q4c_status st = launch_basis_tiles(t, g, b0, b1, nullptr, nullptr, s)) return st;
     KernelScope ks("backward_fp64", s);
     k_backward_fp64<<<static_cast<unsigned>(b1 - b0), 128, smem, s>>>(B, G, b0, g->d_scr_off, g->d_scratch, Gm->V,
-                                                                      Gm->W0, Gm->SOx, Gm->SOy, Gm->SOz, dLdv);
+                                                                      Gm->W0, Gm->SOx, Gm->SOy, Gm->SOz, dLdv,
+                                                                      weighted ? 1 : 0);
     Q4C_CUDA(cudaGetLastError());
   }
   return Q4C_OK;

@@ -184,7 +184,7 @@ q4c_status integrate_fp64(const q4c_tables* t, const q4c_grid* g, const double* 
                           cudaStream_t s);
 q4c_status density_fp64(const q4c_tables* t, const q4c_grid* g, const double* P, double* n, cudaStream_t s);
 q4c_status backward_fp64(const q4c_tables* t, const q4c_grid* g, const q4c_matrices* G, double* dLdv,
-                         cudaStream_t s);
+                         cudaStream_t s, bool weighted = true);
 q4c_status basis_eval(const q4c_tables* t, const q4c_grid* g, int64_t n_pts, const double* xyz, double* phi,
                       double* grad, cudaStream_t s);
 q4c_status mirror_and_spinor(const q4c_grid* g, const q4c_matrices* out, cudaStream_t s);
@@ -199,7 +199,7 @@ q4c_status launch_basis_df(const q4c_tables* t, const q4c_grid* g, int64_t b0, i
 // rowdot.cu
 q4c_status density_split(const q4c_tables* t, const q4c_grid* g, const double* P, double* n, cudaStream_t s);
 q4c_status backward_split(const q4c_tables* t, const q4c_grid* g, const q4c_matrices* G, double* dLdv,
-                          cudaStream_t s);
+                          cudaStream_t s, bool weighted = true);
 // split.cu
 q4c_status integrate_split(const q4c_tables* t, const q4c_grid* g, const double* v, const q4c_matrices* out,
                            cudaStream_t s);

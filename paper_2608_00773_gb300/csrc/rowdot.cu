@@ -229,8 +229,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     k_split_rowdot(DevBasis B, DevGrid G, const int2* __restrict__ items, int n_items,
                    const int64_t* __restrict__ scr_off, const double* __restrict__ scratch,
                    const int* __restrict__ rowexp, const int64_t* __restrict__ gsl_off,
-                   const unsigned char* __restrict__ gsl, unsigned present, double* __restrict__ out,
-                   unsigned* status) {
+                   const unsigned char* __restrict__ gsl, unsigned present, int weighted,
+                   double* __restrict__ out, unsigned* status) {
   extern __shared__ __align__(1024) unsigned char smem[];
   float* sMag = reinterpret_cast<float*>(smem + kSmemMag);  // [quantity][point]
   double* sY = reinterpret_cast<double*>(smem + kSmemY);    // [part][point]
@@ -469,7 +469,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (eg == 0 && lvl == 0 && live) {
         const double val = (sY[r] + sY[kTile + r]) + (sY[2 * kTile + r] + sY[3 * kTile + r]);
         const int64_t gp = I.bp0 + p;
-        out[gp] = MODE == 0 ? val : G.w[gp] * val;
+        out[gp] = weighted ? G.w[gp] * val : val;
       }
       bar_sync(2, kEpiThreads);
     }
@@ -481,7 +481,8 @@ __global__ void __launch_bounds__(kThreads, 1)
 }
 
 template <int MODE>
-q4c_status run(const q4c_tables* t, const q4c_grid* g, const double* const mats[5], double* out, cudaStream_t s) {
+q4c_status run(const q4c_tables* t, const q4c_grid* g, const double* const mats[5], double* out, cudaStream_t s,
+               bool weighted) {
   if (g->max_nb > kMaxNb) {
     set_error("the split density/adjoint need at most 512 active functions per batch");
     return Q4C_EUNSUPPORTED;
@@ -527,7 +528,8 @@ q4c_status run(const q4c_tables* t, const q4c_grid* g, const double* const mats[
       KernelScope ks(name, s);
       k_split_rowdot<MODE><<<grid, kThreads, kSmemTotal, s>>>(
           t->view(), g->view(), g->d_rd_items + i0, n_items, g->d_scr_off, g->d_scratch, g->d_rowexp,
-          g->d_gsl_off, reinterpret_cast<const unsigned char*>(g->d_gsl), present, out, g->d_status);
+          g->d_gsl_off, reinterpret_cast<const unsigned char*>(g->d_gsl), present, weighted ? 1 : 0, out,
+          g->d_status);
     }
     Q4C_CUDA(cudaGetLastError());
   }
@@ -538,18 +540,18 @@ q4c_status run(const q4c_tables* t, const q4c_grid* g, const double* const mats[
 
 q4c_status density_split(const q4c_tables* t, const q4c_grid* g, const double* P, double* n, cudaStream_t s) {
   const double* mats[5] = {P, nullptr, nullptr, nullptr, nullptr};
-  return rowdot::run<0>(t, g, mats, n, s);
+  return rowdot::run<0>(t, g, mats, n, s, false);
 }
 
 q4c_status backward_split(const q4c_tables* t, const q4c_grid* g, const q4c_matrices* Gm, double* dLdv,
-                          cudaStream_t s) {
+                          cudaStream_t s, bool weighted) {
   const double* mats[5] = {Gm->V, Gm->W0, Gm->SOx, Gm->SOy, Gm->SOz};
   // with every slot NULL the gradient is zero
   if (!Gm->V && !Gm->W0 && !Gm->SOx && !Gm->SOy && !Gm->SOz) {
     Q4C_CUDA(cudaMemsetAsync(dLdv, 0, sizeof(double) * g->n_pts, s));
     return Q4C_OK;
   }
-  return rowdot::run<1>(t, g, mats, dLdv, s);
+  return rowdot::run<1>(t, g, mats, dLdv, s, weighted);
 }
 
 }  // namespace q4c
