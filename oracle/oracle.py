@@ -86,6 +86,9 @@ def lib() -> C.CDLL:
             vp = C.c_void_p
             L.orc_adjoint.argtypes = [bp, C.c_long, _dp, _dp, _lp, _ip, _ip, _lp, vp, vp, vp, vp, vp, _dp]
             L.orc_spinor_ss.argtypes = [bp, _lp, _ip, _lp, _dp, _dp, _dp, _dp, _dp]
+            L.orc_kpattern.argtypes = [bp, _lp, _ip, C.c_void_p, C.c_void_p, C.c_void_p]
+            L.orc_kpattern.restype = C.c_long
+            L.orc_kfold.argtypes = [bp, _lp, _ip, _ip, _lp, _dp, C.c_int, _dp, _lp, _ip, _lp, _dp]
             _lib = L
         return _lib
 
@@ -274,6 +277,25 @@ class OracleBasis:
         lib().orc_spinor_ss(C.byref(self.s), pat.blk_ptr, pat.blk_col, pat.blk_off, _f64(W0), _f64(SOx),
                             _f64(SOy), _f64(SOz), out)
         return out.view(np.complex128)
+
+    def kpattern(self, pat: Pattern):
+        """(kblk_ptr, kblk_col, kblk_off): the atom pairs with some block (A, B, T)."""
+        nkb = lib().orc_kpattern(C.byref(self.s), pat.blk_ptr, pat.blk_col, None, None, None)
+        ptr = np.zeros(self.wl.n_atoms + 1, np.int64); col = np.zeros(max(nkb, 1), np.int32)
+        off = np.zeros(nkb + 1, np.int64)
+        lib().orc_kpattern(C.byref(self.s), pat.blk_ptr, pat.blk_col, ptr.ctypes.data, col.ctypes.data,
+                           off.ctypes.data)
+        return ptr, col[:nkb].copy(), off
+
+    def kfold(self, H, k, pat: Pattern):
+        """H(k)_AB = sum_T exp(2 pi i k.T) H(T)_AB (Eqs. 24-26), k [n_k][3] reduced
+        coordinates; complex128 [n_k][nnz_k] on the k-pattern."""
+        kptr, kcol, koff = self.kpattern(pat)
+        k = _f64(k).reshape(-1, 3)
+        out = np.zeros(2 * len(k) * int(koff[-1]))
+        lib().orc_kfold(C.byref(self.s), pat.blk_ptr, pat.blk_col, pat.blk_T.reshape(-1), pat.blk_off, _f64(H),
+                        len(k), k.reshape(-1), kptr, kcol, koff, out)
+        return out.view(np.complex128).reshape(len(k), -1)
 
     def dense(self, vals, pat: Pattern) -> np.ndarray:
         """Scatter a block-pattern array into a dense n_fn x n_fn matrix."""

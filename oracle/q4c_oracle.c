@@ -820,6 +820,65 @@ void orc_adjoint(const orc_basis* b, long n_pts, const double* xyz, const double
   ftab_free(&t);
 }
 
+/* k-pattern: the atom pairs (A, B) that have at least one block (A, B, T);
+ * returns their number; if kblk_ptr != NULL fills CSR (kblk_ptr[n_atoms+1],
+ * kblk_col[], kblk_off[nkb+1]). */
+long orc_kpattern(const orc_basis* b, const long long* blk_ptr, const int* blk_col, long long* kblk_ptr,
+                  int* kblk_col, long long* kblk_off) {
+  long nkb = 0;
+  long long off = 0;
+  if (kblk_ptr) kblk_ptr[0] = 0;
+  for (int A = 0; A < b->n_atoms; ++A) {
+    for (int B = 0; B < b->n_atoms; ++B) {
+      int present = 0;
+      for (long long q = blk_ptr[A]; q < blk_ptr[A + 1] && !present; ++q) present = blk_col[q] == B;
+      if (!present) continue;
+      if (kblk_col) {
+        kblk_col[nkb] = B;
+        kblk_off[nkb] = off;
+      }
+      off += (long long)species_nfn(b, b->species[A]) * species_nfn(b, b->species[B]);
+      ++nkb;
+    }
+    if (kblk_ptr) kblk_ptr[A + 1] = nkb;
+  }
+  if (kblk_off) kblk_off[nkb] = off;
+  return nkb;
+}
+
+/* k-phase fold of real-space blocks (Eqs. 24-26): for each k in reduced
+ * coordinates (fractions of the reciprocal lattice vectors),
+ *   H(k)_AB = sum_T exp(2 pi i k.T) H(T)_AB
+ * over the pattern blocks (A, B, T) (blk_T NULL: T = 0).  out: complex
+ * interleaved (re, im) [n_k][nnz_k] on the k-pattern. */
+void orc_kfold(const orc_basis* b, const long long* blk_ptr, const int* blk_col, const int* blk_T,
+               const long long* blk_off, const double* H, int n_k, const double* k, const long long* kblk_ptr,
+               const int* kblk_col, const long long* kblk_off, double* out) {
+  long long nnz_k = kblk_off[kblk_ptr[b->n_atoms]];
+  for (int ik = 0; ik < n_k; ++ik) {
+    double* o = out + 2 * (size_t)ik * nnz_k;
+    for (long long e = 0; e < 2 * nnz_k; ++e) o[e] = 0.0;
+    for (int A = 0; A < b->n_atoms; ++A) {
+      int nfA = species_nfn(b, b->species[A]);
+      for (long long q = blk_ptr[A]; q < blk_ptr[A + 1]; ++q) {
+        int B = blk_col[q], nfB = species_nfn(b, b->species[B]);
+        long long kq = -1;
+        for (long long r = kblk_ptr[A]; r < kblk_ptr[A + 1]; ++r)
+          if (kblk_col[r] == B) kq = r;
+        double t = 0.0;
+        if (blk_T)
+          t = k[3 * ik] * blk_T[3 * q] + k[3 * ik + 1] * blk_T[3 * q + 1] + k[3 * ik + 2] * blk_T[3 * q + 2];
+        double c = cos(2.0 * M_PI * t), sn = sin(2.0 * M_PI * t);
+        for (long long e = 0; e < (long long)nfA * nfB; ++e) {
+          double h = H[blk_off[q] + e];
+          o[2 * (kblk_off[kq] + e)] += h * c;
+          o[2 * (kblk_off[kq] + e) + 1] += h * sn;
+        }
+      }
+    }
+  }
+}
+
 /* Spinor SS block assembly (Eq. 16 with the kinetic-balance reading):
  * each scalar element (i,j) becomes the 2x2 complex block
  *   [[W0 + i SOz,  SOy + i SOx], [-SOy + i SOx, W0 - i SOz]],

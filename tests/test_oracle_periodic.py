@@ -179,3 +179,33 @@ def test_periodic_inputs():
             qt = blk[(B, A, tuple(-t for t in T))]
             X, Y = _block(G, pat, q, nf[A], nf[B]), _block(G, pat, qt, nf[B], nf[A]).T
             assert np.array_equal(X, -Y if anti else Y)
+
+
+def test_kfold_equals_bloch_sum_matrix_elements(cell_case):
+    """H(k)_ij = sum_T exp(2 pi i k.T) H(T)_ij must equal the matrix element
+    between Bloch sums, sum_p w_p v_p conj(chi_i(p)) chi_j(p) with
+    chi_i(p) = sum_T exp(2 pi i k.T) phi_i(p - T.L), evaluated directly from
+    the basis at the grid points (Eqs. 24-26); this fixes the sign of the
+    phase and of T."""
+    wl, xyz, w, ids, ob, pat, v, mats = cell_case
+    L = np.asarray(wl.lattice)
+    ks = np.array([[0.0, 0.0, 0.0], [0.25, 0.1, -0.3], [0.5, 0.5, 0.5]])
+    s = wl.n_shell
+    Ts = np.array([(a, b, c) for a in range(-s, s + 1) for b in range(-s, s + 1) for c in range(-s, s + 1)])
+    phi_T = [ob.eval(xyz - T @ L)[0] for T in Ts]  # (n_fn, n_pts) per shift
+    kptr, kcol, koff = ob.kpattern(pat)
+    nf = wl.nf_of_atom
+    first = np.concatenate([[0], np.cumsum(nf)])
+    Hk = ob.kfold(mats[0], ks, pat)
+    for ik, k in enumerate(ks):
+        ph = np.exp(2j * np.pi * (Ts @ k))
+        chi = sum(p * f for p, f in zip(ph, phi_T))
+        direct = (np.conj(chi) * (w * v)) @ chi.T
+        dense = np.zeros_like(direct)
+        for A in range(wl.n_atoms):
+            for r in range(int(kptr[A]), int(kptr[A + 1])):
+                B = int(kcol[r])
+                o = int(koff[r])
+                dense[first[A]:first[A + 1], first[B]:first[B + 1]] = Hk[ik, o:o + nf[A] * nf[B]].reshape(nf[A], nf[B])
+        assert np.abs(dense - direct).max() <= 1e-12 * np.abs(direct).max(), ik
+        assert np.abs(dense - dense.conj().T).max() <= 1e-13 * np.abs(dense).max()  # Hermitian
