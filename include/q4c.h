@@ -181,6 +181,23 @@ Q4C_API q4c_status q4c_grid_export(const q4c_grid* grid, double* xyz, double* w,
  * lexicographic order of T in [-n_shell, n_shell]^3.  Synchronous. */
 Q4C_API q4c_status q4c_grid_export_shifts(const q4c_grid* grid, int32_t* shifts);
 
+/* k-pattern of a grid: the atom pairs (A, B) that have at least one pattern
+ * block (A, B, T), CSR by atom rows (kblk_ptr[n_atoms+1], kblk_col[],
+ * kblk_off[n+1] value offsets of dense nf_A x nf_B blocks); *nnz_k = values
+ * per k-point.  Any pointer may be NULL.  Synchronous.  For a molecule it is
+ * the pattern itself. */
+Q4C_API q4c_status q4c_grid_kpattern(const q4c_grid* grid, int64_t* nnz_k, int64_t* kblk_ptr, int32_t* kblk_col,
+                             int64_t* kblk_off);
+
+/* k-phase fold of a real-space matrix on the pattern (Eqs. 24-26, 36):
+ *   H(k)_AB = sum_T exp(2 pi i k.T) H(T)_AB
+ * for n_k k-points in reduced coordinates (k_host[n_k][3], fractions of the
+ * reciprocal lattice vectors; T the integer shifts of q4c_grid_export_shifts).
+ * H_dev device [nnz]; Hk_dev device complex128 [n_k][nnz_k] (interleaved re,
+ * im) on the k-pattern, overwritten.  FP64.  Stream-ordered. */
+Q4C_API q4c_status q4c_kfold(const q4c_grid* grid, const double* H_dev, int32_t n_k, const double* k_host,
+                     double* Hk_dev, q4c_stream stream);
+
 /* Device pointers (grid-owned, read-only) to the kept points in batch order:
  * xyz[n_points][3] and w[n_points], so callers can build v on the device. */
 Q4C_API q4c_status q4c_grid_points(const q4c_grid* grid, const double** xyz_dev, const double** w_dev,

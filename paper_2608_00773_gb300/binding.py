@@ -24,7 +24,7 @@ STATUS = {0: "Q4C_OK", 1: "Q4C_EINVAL", 2: "Q4C_ENOMEM", 3: "Q4C_ECUDA", 4: "Q4C
 
 # every symbol include/q4c.h declares
 EXPORTS = ["nao_tabulate", "q4c_tables_destroy", "q4c_tables_export", "grid_partition", "q4c_grid_destroy",
-           "q4c_grid_get_info", "q4c_grid_export", "q4c_grid_export_shifts", "q4c_grid_points", "q4c_integrate", "q4c_density", "q4c_density_full",
+           "q4c_grid_get_info", "q4c_grid_export", "q4c_grid_export_shifts", "q4c_grid_kpattern", "q4c_kfold", "q4c_grid_points", "q4c_integrate", "q4c_density", "q4c_density_full",
            "q4c_integrate_backward", "q4c_integrate_noalloc", "q4c_basis_eval", "q4c_grid_status", "q4c_profile", "q4c_profile_read",
            "q4c_last_error"]
 
@@ -81,6 +81,8 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     L.q4c_grid_get_info.argtypes = [vp, C.POINTER(GridInfo)]
     L.q4c_grid_export.argtypes = [vp] + [vp] * 9
     L.q4c_grid_export_shifts.argtypes = [vp, vp]
+    L.q4c_grid_kpattern.argtypes = [vp, vp, vp, vp, vp]
+    L.q4c_kfold.argtypes = [vp, vp, i32, vp, vp, vp]
     L.q4c_grid_points.argtypes = [vp, C.POINTER(vp), C.POINTER(vp), C.POINTER(i64)]
     L.q4c_integrate.argtypes = [vp, vp, vp, C.c_int, C.POINTER(Matrices), vp]
     L.q4c_density.argtypes = [vp, vp, vp, C.c_int, vp, vp]
@@ -196,6 +198,16 @@ class Grid:
                     batch_atoms=batoms[:int(baptr[-1])], blk_ptr=blk_ptr, blk_col=blk_col[:i.n_blocks],
                     blk_off=blk_off, blk_T=blk_T[:3 * i.n_blocks].reshape(-1, 3))
 
+    def kpattern(self):
+        """(kblk_ptr, kblk_col, kblk_off) of the atom pairs with some block (A, B, T)."""
+        n = C.c_int64()
+        _check(load().q4c_grid_kpattern(self.h, C.byref(n), None, None, None))
+        ptr = np.zeros(self.info.n_atoms + 1, np.int64)
+        _check(load().q4c_grid_kpattern(self.h, None, ptr.ctypes.data, None, None))
+        col = np.zeros(max(int(ptr[-1]), 1), np.int32); off = np.zeros(int(ptr[-1]) + 1, np.int64)
+        _check(load().q4c_grid_kpattern(self.h, None, None, col.ctypes.data, off.ctypes.data))
+        return ptr, col[:int(ptr[-1])], off
+
     def status(self, stream=None):
         """Synchronise and raise Q4CError(Q4C_ETIMEOUT) if a bounded wait expired."""
         _check(load().q4c_grid_status(self.h, _stream(stream)))
@@ -265,6 +277,18 @@ def q4c_density_full(tables: Tables, grid: Grid, P: Sequence, prec="fp64", out=N
         out = torch.empty(grid.n_points, dtype=torch.float64, device=dev)
     m = Matrices(*[_ptr(x) for x in P], 0)
     _check(load().q4c_density_full(tables.h, grid.h, C.byref(m), _prec(prec), _ptr(out), _stream(stream)))
+    return out
+
+
+def q4c_kfold(grid: Grid, H, k, out=None, stream=None):
+    """H(k)_AB = sum_T exp(2 pi i k.T) H(T)_AB on the k-pattern: complex128 [n_k][nnz_k]."""
+    import torch
+    k = np.ascontiguousarray(k, np.float64).reshape(-1, 3)
+    n = C.c_int64()
+    _check(load().q4c_grid_kpattern(grid.h, C.byref(n), None, None, None))
+    if out is None:
+        out = torch.empty((len(k), n.value), dtype=torch.complex128, device=H.device)
+    _check(load().q4c_kfold(grid.h, _ptr(H), len(k), k.ctypes.data, _ptr(out), _stream(stream)))
     return out
 
 

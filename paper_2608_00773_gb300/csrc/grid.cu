@@ -580,6 +580,28 @@ extern "C" q4c_status grid_partition(const q4c_grid_desc* d, const q4c_tables* t
     blk_role[q] = (zero && A == B) ? 2 : ((pos || (zero && A < B)) ? 1 : 0);
   }
 
+  // ---- k-pattern: atom pairs (A, B) with some block (A, B, T); the blocks of
+  // one pair are a contiguous run of the pattern (rows sorted by (B, T))
+  g->h_kblk_ptr.assign(nA + 1, 0);
+  {
+    int64_t koff = 0;
+    for (int A = 0; A < nA; ++A) {
+      for (int64_t q = g->h_blk_ptr[A]; q < g->h_blk_ptr[A + 1];) {
+        int64_t q1 = q + 1;
+        while (q1 < g->h_blk_ptr[A + 1] && g->h_blk_col[q1] == g->h_blk_col[q]) ++q1;
+        g->h_kblk_col.push_back(g->h_blk_col[q]);
+        g->h_kblk_off.push_back(koff);
+        g->h_kblk_q0.push_back(q);
+        g->h_kblk_q1.push_back(q1);
+        koff += static_cast<int64_t>(g->h_nf_atom[A]) * g->h_nf_atom[g->h_blk_col[q]];
+        q = q1;
+      }
+      g->h_kblk_ptr[A + 1] = static_cast<int64_t>(g->h_kblk_col.size());
+    }
+    g->h_kblk_off.push_back(koff);
+    g->nnz_k = koff;
+  }
+
   // ---- per-batch tables (over the batch's active centres)
   auto c_atom = [&](int c) { return c % nA; };
   auto c_cell = [&](int c) { return c / nA; };
@@ -766,6 +788,8 @@ extern "C" q4c_status grid_partition(const q4c_grid_desc* d, const q4c_tables* t
       (st = up(&g->d_bat_pair_ptr, pair_ptr)) || (st = up(&g->d_pair_off, pair_off)) ||
       (st = up(&g->d_blk_off, g->h_blk_off)) || (st = up(&g->d_blk_row, blk_row)) ||
       (st = up(&g->d_blk_col, g->h_blk_col)) || (st = up(&g->d_blk_T, blk_T)) || (st = up(&g->d_blk_role, blk_role)) ||
+      (st = up(&g->d_blk_shift, g->h_blk_shift)) || (st = up(&g->d_kblk_q0, g->h_kblk_q0)) ||
+      (st = up(&g->d_kblk_q1, g->h_kblk_q1)) || (st = up(&g->d_kblk_off, g->h_kblk_off)) ||
       (st = up(&g->d_scr_off, g->h_scr_off)) || (st = up(&g->d_tiles, tiles)) || (st = up(&g->d_sched, sched)) ||
       (st = up(&g->d_split_items, sitems)) || (st = up(&g->d_rd_items, rditems)) ||
       (st = up(&g->d_bat_idx_ptr, idx_ptr)) ||
@@ -804,7 +828,8 @@ extern "C" void q4c_grid_destroy(q4c_grid* g) {
                   g->d_blk_T, g->d_scr_off, g->d_tiles, g->d_scratch, g->d_sched, g->d_counter, g->d_split_ws,
                   g->d_split_items, g->d_colexp, g->d_status, g->d_rd_items, g->d_rowexp, g->d_gsl, g->d_gsl_off,
                   g->d_bat_idx_ptr, g->d_bat_idx, g->d_pts_df, g->d_atoms_df, g->d_gdf,
-                  g->d_c_xyz, g->d_c_sp, g->d_blk_role};
+                  g->d_c_xyz, g->d_c_sp, g->d_blk_role, g->d_blk_shift, g->d_kblk_q0, g->d_kblk_q1,
+                  g->d_kblk_off};
   for (void* p : ptrs) cudaFree(p);
   delete g;
 }
@@ -845,6 +870,58 @@ extern "C" q4c_status q4c_grid_export(const q4c_grid* g, double* xyz, double* w,
 extern "C" q4c_status q4c_grid_export_shifts(const q4c_grid* g, int32_t* shifts) {
   Q4C_CHECK_ARG(g && shifts, "q4c_grid_export_shifts: NULL argument");
   std::copy(g->h_blk_shift.begin(), g->h_blk_shift.end(), shifts);
+  return Q4C_OK;
+}
+
+extern "C" q4c_status q4c_grid_kpattern(const q4c_grid* g, int64_t* nnz_k, int64_t* kblk_ptr, int32_t* kblk_col,
+                                        int64_t* kblk_off) {
+  Q4C_CHECK_ARG(g, "q4c_grid_kpattern: NULL grid");
+  if (nnz_k) *nnz_k = g->nnz_k;
+  if (kblk_ptr) std::copy(g->h_kblk_ptr.begin(), g->h_kblk_ptr.end(), kblk_ptr);
+  if (kblk_col) std::copy(g->h_kblk_col.begin(), g->h_kblk_col.end(), kblk_col);
+  if (kblk_off) std::copy(g->h_kblk_off.begin(), g->h_kblk_off.end(), kblk_off);
+  return Q4C_OK;
+}
+
+namespace q4c {
+// One CTA per k-pattern block (A, B): the sum over its run of pattern blocks
+// (A, B, T) with the phase exp(2 pi i k.T) (FP64 sincospi of the reduced phase).
+__global__ void k_kfold(const int64_t* __restrict__ q0, const int64_t* __restrict__ q1,
+                        const int64_t* __restrict__ koff, const int64_t* __restrict__ blk_off,
+                        const int* __restrict__ shift, const double* __restrict__ H, double k1, double k2, double k3,
+                        double2* __restrict__ out) {
+  const int kb = blockIdx.x;
+  const int64_t a = q0[kb], z = q1[kb];
+  const int64_t n_el = blk_off[a + 1] - blk_off[a];
+  for (int64_t e = threadIdx.x; e < n_el; e += blockDim.x) {
+    double re = 0.0, im = 0.0;
+    for (int64_t q = a; q < z; ++q) {
+      const double t = k1 * shift[3 * q] + k2 * shift[3 * q + 1] + k3 * shift[3 * q + 2];
+      double sn, cs;
+      sincospi(2.0 * t, &sn, &cs);
+      const double h = H[blk_off[q] + e];
+      re = fma(h, cs, re);
+      im = fma(h, sn, im);
+    }
+    out[koff[kb] + e] = make_double2(re, im);
+  }
+}
+}  // namespace q4c
+
+extern "C" q4c_status q4c_kfold(const q4c_grid* g, const double* H, int32_t n_k, const double* k,
+                                double* Hk, q4c_stream stream) {
+  Q4C_CHECK_ARG(g && (n_k == 0 || (H && k && Hk)), "q4c_kfold: NULL argument");
+  Q4C_CHECK_ARG(n_k >= 0, "q4c_kfold: negative number of k-points");
+  auto s = reinterpret_cast<cudaStream_t>(stream);
+  const auto nkb = static_cast<unsigned>(g->h_kblk_col.size());
+  if (nkb == 0) return Q4C_OK;
+  for (int ik = 0; ik < n_k; ++ik) {
+    KernelScope ks("kfold", s);
+    k_kfold<<<nkb, 128, 0, s>>>(g->d_kblk_q0, g->d_kblk_q1, g->d_kblk_off, g->d_blk_off, g->d_blk_shift, H,
+                                k[3 * ik], k[3 * ik + 1], k[3 * ik + 2],
+                                reinterpret_cast<double2*>(Hk) + static_cast<int64_t>(ik) * g->nnz_k);
+    Q4C_CUDA(cudaGetLastError());
+  }
   return Q4C_OK;
 }
 

@@ -129,6 +129,12 @@ struct q4c_grid {
   int n_centres = 0, n_shell = 0, cell_side = 1;
   std::vector<double> h_c_xyz;
   std::vector<int> h_c_sp, h_blk_shift;  // h_blk_shift [n_blocks][3]
+  // k-pattern: atom pairs with some block; each covers the pattern blocks [q0, q1)
+  std::vector<int64_t> h_kblk_ptr, h_kblk_off, h_kblk_q0, h_kblk_q1;
+  std::vector<int> h_kblk_col;
+  int64_t nnz_k = 0;
+  int* d_blk_shift = nullptr;
+  int64_t *d_kblk_q0 = nullptr, *d_kblk_q1 = nullptr, *d_kblk_off = nullptr;
   double* d_c_xyz = nullptr;
   int* d_c_sp = nullptr;
   // device: points
