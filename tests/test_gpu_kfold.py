@@ -33,9 +33,9 @@ def test_kpattern_bit_exact(cell):
 
 def test_kfold_of_pattern_values(cell):
     lib, orc = cell
-    H = lib.random(81, "V")
+    H = lib.random(81, "P")
     got = q.q4c_kfold(lib.grid, H, KS).cpu().numpy()
-    ref = orc.ob.kfold(orc.random(81, "V"), KS, orc.pat)
+    ref = orc.ob.kfold(orc.random(81, "P"), KS, orc.pat)
     assert got.shape == ref.shape
     for ik in range(len(KS)):
         assert np.linalg.norm(got[ik] - ref[ik]) <= 1e-13 * np.linalg.norm(ref[ik]), ik
@@ -52,7 +52,7 @@ def test_kfold_of_integrated_matrix(cell):
 
 def test_kfold_zero_kpoints(cell):
     lib, _ = cell
-    out = q.q4c_kfold(lib.grid, lib.random(82, "V"), np.zeros((0, 3)))
+    out = q.q4c_kfold(lib.grid, lib.random(82, "P"), np.zeros((0, 3)))
     assert out.shape[0] == 0
 
 
@@ -61,7 +61,7 @@ def test_molecule_kfold_is_identity():
     ptr, col, off = lib.grid.kpattern()
     assert np.array_equal(ptr, lib.ex["blk_ptr"]) and np.array_equal(col, lib.ex["blk_col"])
     assert np.array_equal(off, lib.ex["blk_off"])
-    H = lib.random(83, "V")
+    H = lib.random(83, "P")
     got = q.q4c_kfold(lib.grid, H, KS[1:3]).cpu().numpy()
     for ik in range(2):
         assert np.array_equal(got[ik].real, H.cpu().numpy()) and not got[ik].imag.any()
