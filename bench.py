@@ -44,6 +44,51 @@ def load_peaks():
         "fallback"
 
 
+# DRAM traffic per launch of a kernel group, from the committed ncu summary
+# of that kernel; trusted only while the sources it was captured from are
+# unchanged (the summary records their sha256).
+TRAFFIC_PROFILES = {
+    "split_products": ("k_split_products_cluster64.md", ["split.cu", "tc.cuh", "df.cuh", "internal.h"]),
+    "split_backward": ("k_split_rowdot_cluster64.md", ["rowdot.cu", "tc.cuh", "df.cuh", "internal.h"]),
+    "split_density": ("k_split_rowdot_cluster64.md", ["rowdot.cu", "tc.cuh", "df.cuh", "internal.h"]),
+}
+
+
+def kernel_source_hash(name: str):
+    import hashlib
+    ent = TRAFFIC_PROFILES.get(name)
+    if ent is None:
+        return None
+    h = hashlib.sha256()
+    for f in ent[1]:
+        with open(os.path.join(ROOT, "paper_2608_00773_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def measured_traffic(name: str):
+    """(bytes per launch, summary file) if the summary matches the current sources, else (None, why)."""
+    ent = TRAFFIC_PROFILES.get(name)
+    if ent is None:
+        return None, "no ncu summary for this kernel"
+    path = os.path.join(ROOT, "profiles", ent[0])
+    if not os.path.exists(path):
+        return None, f"profiles/{ent[0]} missing"
+    want, val = None, None
+    with open(path) as f:
+        for line in f:
+            line = line.strip()
+            if line.startswith(f"source_sha256[{name}]:"):
+                want = line.split(":", 1)[1].strip()
+            elif line.startswith(f"traffic_bytes_per_launch[{name}]:"):
+                val = float(line.split(":", 1)[1].strip())
+    if val is None or want is None:
+        return None, f"profiles/{ent[0]} has no traffic line for {name}"
+    if want != kernel_source_hash(name):
+        return None, f"sources changed since profiles/{ent[0]} was captured"
+    return val, f"profiles/{ent[0]}"
+
+
 # FP64 FMA rate of GB300: 2 DFMA per SM per clock -> 4 flop/clk/SM
 def fp64_peak_tflops(sm_mhz: float) -> float:
     return 152 * sm_mhz * 1e6 * 4 / 1e12
@@ -67,13 +112,22 @@ class ClockSampler:
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            t0 = time.perf_counter()
+            while not self.lines and time.perf_counter() - t0 < 5.0 and self.proc.poll() is None:
+                time.sleep(0.01)  # sampling runs before the timed region starts
         except (FileNotFoundError, OSError):
             self.proc = None
+        self.t_start = time.perf_counter()
+        self.t_end = None
         return self
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.perf_counter(), line.strip()))
+
+    def stop_window(self):
+        """End of the timed region: later samples are not counted."""
+        self.t_end = time.perf_counter()
 
     def __exit__(self, *a):
         if self.proc:
@@ -86,7 +140,10 @@ class ClockSampler:
     def summary(self):
         sm, mx, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in self.lines:
+        t_end = self.t_end if self.t_end is not None else float("inf")
+        for t, line in self.lines:
+            if not (self.t_start <= t <= t_end):
+                continue
             f = [x.strip() for x in line.split(",")]
             if len(f) < 9:
                 continue
@@ -212,7 +269,7 @@ def workload_flops(wl) -> float:
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=60)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--prec", default="split", choices=["split", "fp64"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
@@ -220,7 +277,13 @@ def main():
     ap.add_argument("--cpu-stride", type=int, default=4)
     ap.add_argument("--ref-stride", type=int, default=61)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--print-source-hash", action="store_true",
+                    help="print the sha256 of each profiled kernel's sources and exit")
     args = ap.parse_args()
+    if args.print_source_hash:
+        for name in TRAFFIC_PROFILES:
+            print(f"source_sha256[{name}]: {kernel_source_hash(name)}")
+        return
 
     from workloads import cluster64, water
     wl = cluster64() if args.workload == "cluster64" else water()
@@ -294,6 +357,7 @@ def main():
             step(prec)
             ev[k][1].record(stream)
         torch.cuda.synchronize()
+        clocks.stop_window()
     barrier(world)
     q.profile(False)
     per_step = [a.elapsed_time(b) for a, b in ev]
@@ -328,7 +392,7 @@ def main():
     else:
         roof = {"bound": "alu", "achieved": None, "peak": None, "unit": "TFLOP/s"}
     roof["frac"] = (roof["achieved"] / roof["peak"]) if roof.get("achieved") and roof.get("peak") else None
-    roof["traffic"] = None
+    roof["traffic"], roof["traffic_source"] = measured_traffic(dom_name)
     roof["kernel"] = dom_name
     roof["kernel_ms_per_launch"] = dom_ms / dom_n
     roof["share_of_step"] = dom_ms / (t_ms * args.steps)

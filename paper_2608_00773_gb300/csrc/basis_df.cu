@@ -17,7 +17,8 @@
 // Outputs (per batch): tiles Phi, X, Y, Z as float2 (hi, lo) in the FP64
 // tile layout [4][n_b][ceil8(n_p)]; column exponents (slots 0..3: upper bounds
 // for the D-scaled values, D = w v; 4..7: the values) and per-point exponents
-// of the four quantities (max over functions).
+// of the four quantities (max over functions).  NQ = 1 computes and stores
+// Phi alone (the density contracts Phi only).
 #include "df.cuh"
 #include "internal.h"
 
@@ -117,6 +118,37 @@ __device__ __forceinline__ void harmonics(df x, df y, df z, int lmax, df* S, df*
   dS[47] = zero;
 }
 
+// S_lm alone for l <= lmax (the same polynomials as harmonics)
+__device__ __forceinline__ void harmonics_s(df x, df y, df z, int lmax, df* S) {
+  S[0] = D(c00);
+  if (lmax < 1) return;
+  const df n1 = df_neg(D(c1));
+  S[1] = df_mul(n1, y);
+  S[2] = df_mul(D(c1), z);
+  S[3] = df_mul(n1, x);
+  if (lmax < 2) return;
+  const df xx = df_mul(x, x), yy = df_mul(y, y), zz = df_mul(z, z);
+  const df xy = df_mul(x, y), yz = df_mul(y, z), xz = df_mul(x, z);
+  const df na = df_neg(D(c2a));
+  S[4] = df_mul(D(c2a), xy);
+  S[5] = df_mul(na, yz);
+  S[6] = df_mul(D(c20), df_sub(df_mul_f(zz, 2.f), df_add(xx, yy)));
+  S[7] = df_mul(na, xz);
+  const df xmy = df_sub(xx, yy);
+  S[8] = df_mul(D(c22), xmy);
+  if (lmax < 3) return;
+  const df n33 = df_neg(D(c33)), n31 = df_neg(D(c31));
+  S[9] = df_mul(n33, df_mul(y, df_sub(df_mul_f(xx, 3.f), yy)));
+  S[10] = df_mul(D(c32a), df_mul(xy, z));
+  const df q4 = df_sub(df_mul_f(zz, 4.f), df_add(xx, yy));
+  S[11] = df_mul(n31, df_mul(y, q4));
+  S[12] = df_mul(D(c30), df_mul(z, df_sub(df_mul_f(zz, 2.f), df_mul_f(df_add(xx, yy), 3.f))));
+  S[13] = df_mul(n31, df_mul(x, q4));
+  S[14] = df_mul(D(c32b), df_mul(z, xmy));
+  S[15] = df_mul(n33, df_mul(x, df_sub(xx, df_mul_f(yy, 3.f))));
+}
+
+template <int NQ>
 __global__ void __launch_bounds__(256) k_basis_df(DevBasis B, DevGrid G, DfTables T, int64_t b0,
                                                   const int64_t* __restrict__ scr_off, float2* __restrict__ scratch,
                                                   const double* __restrict__ v, int* __restrict__ colexp,
@@ -156,8 +188,11 @@ __global__ void __launch_bounds__(256) k_basis_df(DevBasis B, DevGrid G, DfTable
     }
     int lmax = 0;
     for (int q = 0; q < nr; ++q) lmax = max(lmax, __ldg(B.rad_l + r0 + q));
-    df S[16], dS[48];
-    harmonics(dx, dy, dz, lmax, S, dS);
+    df S[16], dS[NQ == 1 ? 1 : 48];
+    if (NQ == 1)
+      harmonics_s(dx, dy, dz, lmax, S);
+    else
+      harmonics(dx, dy, dz, lmax, S, dS);
     const bool pos = in && r2.hi > 0.f;  // a point on the nucleus has r = 0 and 1/r taken as 0
     const df r = pos ? df_sqrt(r2) : df{0.f, 0.f};
     const df ir = pos ? df_div(df{1.f, 0.f}, r) : df{0.f, 0.f};
@@ -197,28 +232,31 @@ __global__ void __launch_bounds__(256) k_basis_df(DevBasis B, DevGrid G, DfTable
           df irl = ir;
           for (int t = 0; t < l; ++t) irl = df_mul(irl, ir);
           g = df_mul(u, irl);
-          gp = df_mul(df_mul(df_sub(df_mul(du, T.inv_h_df), df_mul_f(u, static_cast<float>(l + 1))), ir), irl);
+          if (NQ > 1)
+            gp = df_mul(df_mul(df_sub(df_mul(du, T.inv_h_df), df_mul_f(u, static_cast<float>(l + 1))), ir), irl);
         }
       }
       const df gx = df_mul(gp, ux), gy = df_mul(gp, uy), gz = df_mul(gp, uz);
       for (int m = 0; m < 2 * l + 1; ++m, ++fl) {
         const int idx = l * l + m;
-        const df ph = df_mul(g, S[idx]);
-        const df vx = df_add(df_mul(gx, S[idx]), df_mul(g, dS[3 * idx]));
-        const df vy = df_add(df_mul(gy, S[idx]), df_mul(g, dS[3 * idx + 1]));
-        const df vz = df_add(df_mul(gz, S[idx]), df_mul(g, dS[3 * idx + 2]));
-        const df vals[4] = {ph, vx, vy, vz};
+        df vals[4];
+        vals[0] = df_mul(g, S[idx]);
+        if (NQ > 1) {
+          vals[1] = df_add(df_mul(gx, S[idx]), df_mul(g, dS[3 * idx]));
+          vals[2] = df_add(df_mul(gy, S[idx]), df_mul(g, dS[3 * idx + 1]));
+          vals[3] = df_add(df_mul(gz, S[idx]), df_mul(g, dS[3 * idx + 2]));
+        }
         const int f = f0 + fl;
         if (live) {
           float2* o = base + static_cast<int64_t>(f) * ldp + p;
 #pragma unroll
-          for (int c = 0; c < 4; ++c) o[c * plane] = make_float2(vals[c].hi, vals[c].lo);
+          for (int c = 0; c < NQ; ++c) o[c * plane] = make_float2(vals[c].hi, vals[c].lo);
         }
 #pragma unroll
-        for (int c = 0; c < 4; ++c) rmax[c] = fmaxf(rmax[c], fabsf(vals[c].hi));
+        for (int c = 0; c < NQ; ++c) rmax[c] = fmaxf(rmax[c], fabsf(vals[c].hi));
         if (colexp) {
 #pragma unroll
-          for (int c = 0; c < 4; ++c) {
+          for (int c = 0; c < NQ; ++c) {
             const float h = vals[c].hi;
             const int e = (live && h != 0.f) ? fexp(h) : -30000;
             const int ea = (e > -30000 && eD > -30000) ? e + eD : -30000;
@@ -234,7 +272,7 @@ __global__ void __launch_bounds__(256) k_basis_df(DevBasis B, DevGrid G, DfTable
     }
     if (rowexp && live) {
 #pragma unroll
-      for (int c = 0; c < 4; ++c)
+      for (int c = 0; c < NQ; ++c)
         if (rmax[c] > 0.f) atomicMax(&s_row[c * np + p], fexp(rmax[c]));
     }
   }
@@ -254,16 +292,20 @@ __global__ void __launch_bounds__(256) k_basis_df(DevBasis B, DevGrid G, DfTable
 }  // namespace bdf
 
 q4c_status launch_basis_df(const q4c_tables* t, const q4c_grid* g, int64_t b0, int64_t b1, const double* v,
-                           int* colexp, int* rowexp, cudaStream_t s) {
+                           int* colexp, int* rowexp, int nq, cudaStream_t s) {
   const size_t smem = sizeof(int) * (8 * std::max(g->max_nb, 1) + 4 * std::max(g->max_np, 1));
+  auto kern = nq == 1 ? bdf::k_basis_df<1> : bdf::k_basis_df<4>;
+  if (nq != 1 && nq != 4) {
+    set_error("launch_basis_df: nq must be 1 or 4");
+    return Q4C_EINVAL;
+  }
   if (smem > 48 * 1024)
-    Q4C_CUDA(cudaFuncSetAttribute(bdf::k_basis_df, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  static_cast<int>(smem)));
+    Q4C_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
   DfTables T = t->df_view();
   T.pts = g->d_pts_df;
   T.atoms = g->d_atoms_df;
   KernelScope ks("basis_df", s);
-  bdf::k_basis_df<<<static_cast<unsigned>(b1 - b0), 256, smem, s>>>(t->view(), g->view(), T, b0, g->d_scr_off,
+  kern<<<static_cast<unsigned>(b1 - b0), 256, smem, s>>>(t->view(), g->view(), T, b0, g->d_scr_off,
                                                                      reinterpret_cast<float2*>(g->d_scratch), v,
                                                                      colexp, rowexp);
   Q4C_CUDA(cudaGetLastError());

@@ -200,8 +200,9 @@ q4c_status launch_basis_tiles(const q4c_tables* t, const q4c_grid* g, int64_t b0
 q4c_status launch_fill_idx(const q4c_tables* t, const q4c_grid* g, int64_t b0, int64_t b1, cudaStream_t s);
 
 // basis_df.cu
+// nq = 4: Phi, X, Y, Z tiles; nq = 1: Phi alone
 q4c_status launch_basis_df(const q4c_tables* t, const q4c_grid* g, int64_t b0, int64_t b1, const double* v,
-                           int* colexp, int* rowexp, cudaStream_t s);
+                           int* colexp, int* rowexp, int nq, cudaStream_t s);
 // rowdot.cu
 q4c_status density_split(const q4c_tables* t, const q4c_grid* g, const double* P, double* n, cudaStream_t s);
 q4c_status backward_split(const q4c_tables* t, const q4c_grid* g, const q4c_matrices* G, double* dLdv,

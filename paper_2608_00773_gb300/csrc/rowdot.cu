@@ -519,7 +519,7 @@ q4c_status run(const q4c_tables* t, const q4c_grid* g, const double* const mats[
           reinterpret_cast<uint32_t*>(g->d_gsl));
     }
     Q4C_CUDA(cudaGetLastError());
-    if (q4c_status st = launch_basis_df(t, g, b0, b1, nullptr, nullptr, g->d_rowexp, s)) return st;
+    if (q4c_status st = launch_basis_df(t, g, b0, b1, nullptr, nullptr, g->d_rowexp, MODE == 0 ? 1 : 4, s)) return st;
     const int64_t i0 = g->rd_w0[wv], i1 = g->rd_w0[wv + 1];
     const int n_items = static_cast<int>(i1 - i0);
     if (n_items == 0) continue;

@@ -423,7 +423,7 @@ q4c_status integrate_split(const q4c_tables* t, const q4c_grid* g, const double*
     const int64_t b0 = g->wave_b0[wv], b1 = g->wave_b0[wv + 1];
     if (b1 <= b0) continue;
     if (q4c_status st = launch_fill_idx(t, g, b0, b1, s)) return st;
-    if (q4c_status st = launch_basis_df(t, g, b0, b1, v, g->d_colexp, nullptr, s)) return st;
+    if (q4c_status st = launch_basis_df(t, g, b0, b1, v, g->d_colexp, nullptr, 4, s)) return st;
     const int64_t i0 = g->split_w0[wv], i1 = g->split_w0[wv + 1];
     const int n_items = static_cast<int>(i1 - i0);
     if (n_items == 0) continue;
