@@ -363,7 +363,8 @@ def main():
     per_step = [a.elapsed_time(b) for a, b in ev]
     t_ms = max_over_ranks(statistics.mean(per_step), world)
     kern = {}
-    for name in ("split_products", "split_backward", "split_density", "split_gslice", "fill_idx", "basis_df", "products_fp64",
+    for name in ("split_products", "split_prep", "split_backward", "split_density", "split_gslice", "fill_idx", "basis_df",
+                 "products_fp64",
                  "density_fp64", "backward_fp64", "basis", "mirror", "spinor", ""):
         ms, n = q.profile_read(name)
         if n:

@@ -152,7 +152,7 @@ template <int NQ>
 __global__ void __launch_bounds__(256) k_basis_df(DevBasis B, DevGrid G, DfTables T, int64_t b0,
                                                   const int64_t* __restrict__ scr_off, float2* __restrict__ scratch,
                                                   const double* __restrict__ v, int* __restrict__ colexp,
-                                                  int* __restrict__ rowexp) {
+                                                  int* __restrict__ rowexp, float2* __restrict__ dpad) {
   extern __shared__ int sm[];  // [8][nb] column exponents, then [4][np] point exponents
   const int64_t b = b0 + blockIdx.x;
   const int64_t p0 = G.pt_ptr[b];
@@ -185,6 +185,12 @@ __global__ void __launch_bounds__(256) k_basis_df(DevBasis B, DevGrid G, DfTable
     if (colexp && live) {
       const double Dp = G.w[p0 + p] * v[p0 + p];
       if (Dp != 0.0) eD = dexp(Dp);
+      if (dpad && a == 0) {  // D = w v as (hi, lo), once per point
+        const float h = static_cast<float>(Dp);
+        dpad[b * kDPitch + p] = make_float2(h, static_cast<float>(Dp - static_cast<double>(h)));
+      }
+    } else if (dpad && a == 0 && p < ((np + 15) & ~15)) {
+      dpad[b * kDPitch + p] = make_float2(0.f, 0.f);  // the K-step of 16 points reads zeros past n_p
     }
     int lmax = 0;
     for (int q = 0; q < nr; ++q) lmax = max(lmax, __ldg(B.rad_l + r0 + q));
@@ -292,7 +298,7 @@ __global__ void __launch_bounds__(256) k_basis_df(DevBasis B, DevGrid G, DfTable
 }  // namespace bdf
 
 q4c_status launch_basis_df(const q4c_tables* t, const q4c_grid* g, int64_t b0, int64_t b1, const double* v,
-                           int* colexp, int* rowexp, int nq, cudaStream_t s) {
+                           int* colexp, int* rowexp, int nq, cudaStream_t s, float2* dpad) {
   const size_t smem = sizeof(int) * (8 * std::max(g->max_nb, 1) + 4 * std::max(g->max_np, 1));
   auto kern = nq == 1 ? bdf::k_basis_df<1> : bdf::k_basis_df<4>;
   if (nq != 1 && nq != 4) {
@@ -307,7 +313,7 @@ q4c_status launch_basis_df(const q4c_tables* t, const q4c_grid* g, int64_t b0, i
   KernelScope ks("basis_df", s);
   kern<<<static_cast<unsigned>(b1 - b0), 256, smem, s>>>(t->view(), g->view(), T, b0, g->d_scr_off,
                                                                      reinterpret_cast<float2*>(g->d_scratch), v,
-                                                                     colexp, rowexp);
+                                                                     colexp, rowexp, dpad);
   Q4C_CUDA(cudaGetLastError());
   return Q4C_OK;
 }

@@ -9,8 +9,12 @@
 #include <atomic>
 #include <cmath>
 #include <cstdlib>
+#include <cstring>
 #include <numeric>
 #include <thread>
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
 
 #include "internal.h"
 
@@ -200,6 +204,58 @@ q4c_status launch_fill_idx(const q4c_tables* t, const q4c_grid* g, int64_t b0, i
 }
 
 }  // namespace q4c
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// dependency on the driver library)
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static const PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      p = nullptr;
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }();
+  return fn;
+}
+
+// One TMA map per batch over its basis tiles in the scratch buffer: a 3-D
+// tensor (point, function, quantity) of 8-byte (hi, lo) pairs with extents
+// (n_p, n_b, 4) and row pitch ceil8(n_p), read in boxes of 16 points x 64
+// functions with the 128-byte swizzle.  Points past n_p and functions past
+// n_b read as zeros.
+static q4c_status encode_tile_maps(q4c_grid* g) {
+  const int64_t nB = g->n_batches;
+  std::vector<CUtensorMap> maps(static_cast<size_t>(std::max<int64_t>(nB, 1)));
+  std::memset(maps.data(), 0, sizeof(CUtensorMap) * maps.size());
+  auto enc = tensor_map_encoder();
+  if (!enc) {
+    set_error("grid_partition: cuTensorMapEncodeTiled is not available from the driver");
+    return Q4C_ECUDA;
+  }
+  for (int64_t b = 0; b < nB; ++b) {
+    const int64_t np = g->h_pt_ptr[b + 1] - g->h_pt_ptr[b];
+    const int64_t nb = g->h_bat_fn_ptr[b + 1] - g->h_bat_fn_ptr[b];
+    if (np <= 0 || nb <= 0) continue;  // no items read this batch
+    const int64_t ldp = (np + 7) / 8 * 8;
+    void* base = g->d_scratch + g->h_scr_off[b];
+    const cuuint64_t dims[3] = {static_cast<cuuint64_t>(np), static_cast<cuuint64_t>(nb), 4};
+    const cuuint64_t strides[2] = {static_cast<cuuint64_t>(ldp * 8), static_cast<cuuint64_t>(nb * ldp * 8)};
+    const cuuint32_t box[3] = {16, 64, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    const CUresult r = enc(&maps[b], CU_TENSOR_MAP_DATA_TYPE_INT64, 3, base, dims, strides, box, estr,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+      set_error("grid_partition: cuTensorMapEncodeTiled failed for batch " + std::to_string(b) + " (CUresult " +
+                std::to_string(static_cast<int>(r)) + ")");
+      return Q4C_ECUDA;
+    }
+  }
+  Q4C_CUDA(cudaMemcpy(g->d_tmaps, maps.data(), sizeof(CUtensorMap) * maps.size(), cudaMemcpyHostToDevice));
+  return Q4C_OK;
+}
 
 static int64_t scratch_cap_doubles() {
   int64_t mb = 4096;
@@ -702,6 +758,8 @@ extern "C" q4c_status grid_partition(const q4c_grid_desc* d, const q4c_tables* t
   // Batches with the most work first; the items of one batch stay adjacent
   // (W0, three products, leading) so that concurrent CTAs share its tiles in L2.
   std::vector<int4> sitems;
+  std::vector<int> ssteps;
+  int64_t max_wave_items = 1;
   g->split_w0.push_back(0);
   for (size_t wv = 0; wv + 1 < g->wave_b0.size(); ++wv) {
     std::vector<std::pair<double, int64_t>> bl;
@@ -720,8 +778,10 @@ extern "C" q4c_status grid_partition(const q4c_grid_desc* d, const q4c_tables* t
           for (int j = 0; j < nt; ++j) {
             if (o <= 1 && i > j) continue;
             sitems.push_back(make_int4(static_cast<int>(b), o, i, j));
+            ssteps.push_back(static_cast<int>((bptr[b + 1] - bptr[b] + 15) / 16) * (o == 1 ? 3 : 1));
           }
     }
+    max_wave_items = std::max(max_wave_items, static_cast<int64_t>(sitems.size()) - g->split_w0.back());
     g->split_w0.push_back(static_cast<int64_t>(sitems.size()));
   }
   // density/adjoint: (batch, 64-point tile) items per wave, costliest first
@@ -791,7 +851,8 @@ extern "C" q4c_status grid_partition(const q4c_grid_desc* d, const q4c_tables* t
       (st = up(&g->d_blk_shift, g->h_blk_shift)) || (st = up(&g->d_kblk_q0, g->h_kblk_q0)) ||
       (st = up(&g->d_kblk_q1, g->h_kblk_q1)) || (st = up(&g->d_kblk_off, g->h_kblk_off)) ||
       (st = up(&g->d_scr_off, g->h_scr_off)) || (st = up(&g->d_tiles, tiles)) || (st = up(&g->d_sched, sched)) ||
-      (st = up(&g->d_split_items, sitems)) || (st = up(&g->d_rd_items, rditems)) ||
+      (st = up(&g->d_split_items, sitems)) || (st = up(&g->d_split_steps, ssteps)) ||
+      (st = up(&g->d_rd_items, rditems)) ||
       (st = up(&g->d_bat_idx_ptr, idx_ptr)) ||
       (st = up(&g->d_gsl_off, gsl_off))) {
     q4c_grid_destroy(g);
@@ -806,6 +867,9 @@ extern "C" q4c_status grid_partition(const q4c_grid_desc* d, const q4c_tables* t
     if (e == cudaSuccess) e = cudaMalloc(&g->d_gsl, static_cast<size_t>(std::max<int64_t>(g->gsl_bytes, 16)));
     if (e == cudaSuccess) e = cudaMalloc(&g->d_gdf, sizeof(float2) * 5 * std::max<int64_t>(g->nnz, 1));
     if (e == cudaSuccess) e = cudaMalloc(&g->d_bat_idx, sizeof(int) * g->idx_entries);
+    if (e == cudaSuccess) e = cudaMalloc(&g->d_split_mag, sizeof(float) * 128 * max_wave_items);
+    if (e == cudaSuccess) e = cudaMalloc(&g->d_dpad, sizeof(float2) * kDPitch * std::max<int64_t>(nB, 1));
+    if (e == cudaSuccess) e = cudaMalloc(&g->d_tmaps, sizeof(CUtensorMap) * std::max<int64_t>(nB, 1));
     if (e == cudaSuccess) e = cudaMalloc(&g->d_status, sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMemset(g->d_status, 0, sizeof(unsigned));
     g->split_ws_bytes = static_cast<int64_t>(sizeof(int)) * (8 * g->h_bat_fn_ptr[nB] + 4 * nP) +
@@ -815,6 +879,10 @@ extern "C" q4c_status grid_partition(const q4c_grid_desc* d, const q4c_tables* t
       q4c_grid_destroy(g);
       return e == cudaErrorMemoryAllocation ? Q4C_ENOMEM : Q4C_ECUDA;
     }
+  }
+  if (q4c_status st2 = encode_tile_maps(g)) {
+    q4c_grid_destroy(g);
+    return st2;
   }
   *out = g;
   return Q4C_OK;
@@ -826,7 +894,7 @@ extern "C" void q4c_grid_destroy(q4c_grid* g) {
                   g->d_pt_ptr, g->d_bat_atom_ptr, g->d_bat_atoms, g->d_bat_atom_fn0, g->d_bat_fn_ptr,
                   g->d_fn_info, g->d_bat_pair_ptr, g->d_pair_off, g->d_blk_off, g->d_blk_row, g->d_blk_col,
                   g->d_blk_T, g->d_scr_off, g->d_tiles, g->d_scratch, g->d_sched, g->d_counter, g->d_split_ws,
-                  g->d_split_items, g->d_colexp, g->d_status, g->d_rd_items, g->d_rowexp, g->d_gsl, g->d_gsl_off,
+                  g->d_split_items, g->d_split_steps, g->d_split_mag, g->d_dpad, g->d_tmaps, g->d_colexp, g->d_status, g->d_rd_items, g->d_rowexp, g->d_gsl, g->d_gsl_off,
                   g->d_bat_idx_ptr, g->d_bat_idx, g->d_pts_df, g->d_atoms_df, g->d_gdf,
                   g->d_c_xyz, g->d_c_sp, g->d_blk_role, g->d_blk_shift, g->d_kblk_q0, g->d_kblk_q1,
                   g->d_kblk_off};

@@ -14,6 +14,7 @@ namespace q4c {
 
 constexpr int kMaxL = 3;
 constexpr int kMaxBatch = 1024;
+constexpr int kDPitch = 352;  // points per batch row of the D = w v table (>= 16 * ceil(341 / 16))
 
 // ---------------------------------------------------------------- errors
 void set_error(const std::string& msg);
@@ -167,6 +168,10 @@ struct q4c_grid {
   int* d_counter = nullptr;                // [n_waves]
   std::vector<int64_t> split_w0;           // [n_waves+1] ranges into d_split_items
   int4* d_split_items = nullptr;
+  int* d_split_steps = nullptr;            // K-steps of 16 points per item (3x for W0)
+  float* d_split_mag = nullptr;            // [items of the largest wave][128] rounding constants
+  void* d_tmaps = nullptr;                 // [n_batches] 3-D TMA maps (points, functions, quantity) of the tiles
+  float2* d_dpad = nullptr;                // [n_batches][kDPitch] D = w v as (hi, lo), zero past n_p
   int* d_colexp = nullptr;                 // [8 * sum n_b]
   std::vector<int64_t> rd_w0;              // [n_waves+1] ranges into d_rd_items
   int2* d_rd_items = nullptr;              // (batch, 64-point tile) for density/adjoint
@@ -202,7 +207,7 @@ q4c_status launch_fill_idx(const q4c_tables* t, const q4c_grid* g, int64_t b0, i
 // basis_df.cu
 // nq = 4: Phi, X, Y, Z tiles; nq = 1: Phi alone
 q4c_status launch_basis_df(const q4c_tables* t, const q4c_grid* g, int64_t b0, int64_t b1, const double* v,
-                           int* colexp, int* rowexp, int nq, cudaStream_t s);
+                           int* colexp, int* rowexp, int nq, cudaStream_t s, float2* dpad = nullptr);
 // rowdot.cu
 q4c_status density_split(const q4c_tables* t, const q4c_grid* g, const double* P, double* n, cudaStream_t s);
 q4c_status backward_split(const q4c_tables* t, const q4c_grid* g, const q4c_matrices* G, double* dLdv,

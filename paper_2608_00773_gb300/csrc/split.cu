@@ -39,6 +39,8 @@
 // while scattering.  One warp-specialised CTA per SM (slicers, one MMA
 // thread, epilogue warps; 512 TMEM columns) loops over the work items; every
 // mbarrier wait is bounded and sets a status bit instead of hanging.
+#include <cuda.h>
+
 #include "internal.h"
 #include "tc.cuh"
 
@@ -54,33 +56,37 @@ constexpr int kSlicers = 256;                // warps 0-7 slice the operands
 constexpr int kEpiWarp0 = 8;                 // warps 8-15 drain tensor memory (two groups of four)
 constexpr int kEpiThreads = 256;
 constexpr int kMmaWarp = 16;                 // warp 16 owns tensor memory and issues the MMAs
-constexpr int kThreads = 17 * 32;
+constexpr int kProdWarp = 17;                // warp 17 issues the TMA loads of the raw operands
+constexpr int kThreads = 18 * 32;
 constexpr int kEpiPitch = 17;                // floats per staged TMEM lane (16 columns + pad)
 constexpr int kEpiStage = 3 * 128 * kEpiPitch * 4;  // one group's staging, 26 KB
-constexpr int kUnits = 16 / (kSlicers / 32);  // slicing units per side per thread
-constexpr int kMaxProducts = 3;
 constexpr int kStageA = (kSlices + 1) * kTileBytes;  // [Z, A0..A5]
 constexpr int kStageB = kSlices * kTileBytes;        // [B0..B5]
 constexpr int kStage = kStageA + kStageB;            // 26 KB
 constexpr int kStages = 4;                           // ring depth of sliced operands
-constexpr int kRaw = 4;                              // ring depth of raw operand values
-constexpr int kRawStage = kSlicers * 2 * kUnits * 16;  // one step's float2 pairs, 16 KB
-constexpr int kSmemStages = 0;
+// raw ring: per K-step the A and B boxes (64 functions x 16 points of (hi, lo),
+// 128-byte rows, swizzled), the step's D values and, on an item's first step,
+// the item's 128 rounding constants
+constexpr int kRaw = 4;
+constexpr int kRawTile = kTile * kKc * 8;            // 8 KB
+constexpr int kRawD = 2 * kRawTile;                  // offset of D (16 x 8 B)
+constexpr int kRawMag = kRawD + kKc * 8;             // offset of the rounding constants (128 x 4 B)
+constexpr int kRawStage = 17 * 1024;                 // 1024-aligned stages (swizzle atoms)
+constexpr int kSmemRaw = 0;
+constexpr int kSmemStages = kSmemRaw + kRaw * kRawStage;
 constexpr int kSmemEpi = kSmemStages + kStages * kStage;  // epilogue staging, 2 x 26 KB
-constexpr int kSmemRaw = kSmemEpi + 2 * kEpiStage;
-constexpr int kSmemD = kSmemRaw + kRaw * kRawStage;
-constexpr int kMaxNp = 344;  // D values of one batch (double-float)
-constexpr int kSmemExp = kSmemD + kMaxNp * 8;
-constexpr int kSmemBar = kSmemExp + 2 * kTile * 4;
-constexpr int kNumBars = 2 * kStages + 5;  // full[S], empty[S], accfull[2], accempty[2], drain
+constexpr int kSmemBar = kSmemEpi + 2 * kEpiStage;
+constexpr int kNumBars = 2 * kStages + 5 + 2 * kRaw;  // full, empty, accfull[2], accempty[2], drain, raw full/empty
 constexpr int kSmemTotal = kSmemBar + kNumBars * 8 + 16;
 constexpr uint32_t kTmemCols = 512;  // two accumulator sets of three 64-column blocks
 constexpr uint32_t kSetCols = 256;
+static_assert(kRawMag + 128 * 4 <= kRawStage, "raw stage overflow");
+static_assert(kSmemTotal <= 232448, "shared memory per CTA");
 
 // ------------------------------------------------------------ kernel
-// The products of one output, in registers: n of them, the A-side (D-scaled)
-// and B-side quantities of product pr in bits 2pr..2pr+1 of qa and qb
-// (0 Phi, 1 X, 2 Y, 3 Z).
+// The products of one output: n of them, the A-side (D-scaled) and B-side
+// quantities of product pr in bits 2pr..2pr+1 of qa and qb (0 Phi, 1 X, 2 Y,
+// 3 Z).
 struct Products {
   int n;
   unsigned qa, qb;
@@ -98,35 +104,42 @@ __device__ __forceinline__ Products products_of(int o) {
   }
 }
 
-__device__ __forceinline__ int item_steps(const DevGrid& G, int4 item) {
-  const int np = static_cast<int>(G.pt_ptr[item.x + 1] - G.pt_ptr[item.x]);
-  return ((np + kKc - 1) / kKc) * (item.y == 1 ? 3 : 1);
-}
-
-// Issue the asynchronous copies of one K-step's operand values for this
-// thread: per side, kUnits units of two consecutive points (16 bytes each)
-// into its slots of a raw stage (slot (side * kUnits + k) * kSlicers + tid).
-// Values past the batch's points or functions arrive as zeros.
-__device__ __forceinline__ void issue_step(const float2* base, int64_t plane, int ldp, int np, int nb, int i0,
-                                           int j0, const Products& P, int s, int warp, int lane, int tid,
-                                           uint32_t raw) {
-  const int c = P.n == 1 ? s : s / 3, pr = s - c * P.n;
-  const int kc0 = c * kKc;
-#pragma unroll
-  for (int side = 0; side < 2; ++side) {
-    const int q = side == 0 ? P.a(pr) : P.b(pr);
-    const int row0 = side == 0 ? i0 : j0;
-#pragma unroll
-    for (int k = 0; k < kUnits; ++k) {
-      const int u = warp + (kSlicers / 32) * k;
-      const int r = (u >> 1) * 8 + (lane >> 2), p = kc0 + 2 * ((u & 1) * 4 + (lane & 3));
-      const int f = row0 + r;
-      const bool live = f < nb && p < np;
-      const int bytes = !live ? 0 : (p + 1 < np ? 16 : 8);  // row padding is not written
-      const float2* src = live ? base + q * plane + static_cast<int64_t>(f) * ldp + p : base;
-      cp_async16(raw + ((side * kUnits + k) * kSlicers + tid) * 16, src, bytes);
+// Rounding constants of one item's rows: 0..63 the A side (column exponents
+// of the D-scaled quantity), 64..127 the B side.  W0 slices its three
+// gradient products against one exponent per function (the maximum over x,
+// y, z), so that its K-concatenated products share units.
+__global__ void k_item_prep(DevGrid G, const int4* __restrict__ items, const int* __restrict__ colexp,
+                            float* __restrict__ mag) {
+  const int n = blockIdx.x;
+  const int4 item = items[n];
+  const int64_t b = item.x;
+  const int o = item.y, t = threadIdx.x, side = t >> 6, r = t & 63;
+  const int64_t fn0 = G.bat_fn_ptr[b];
+  const int nb = static_cast<int>(G.bat_fn_ptr[b + 1] - fn0);
+  const int* cexp = colexp + 8 * fn0;
+  const int f = (side ? item.w : item.z) * kTile + r;
+  int e = -30000;
+  if (f < nb) {
+    const int base = side ? 4 : 0;
+    if (o == 1) {
+      e = max(cexp[(base + 1) * nb + f], max(cexp[(base + 2) * nb + f], cexp[(base + 3) * nb + f]));
+    } else {
+      const Products P = products_of(o);
+      e = cexp[(base + (side ? P.b(0) : P.a(0))) * nb + f];
     }
   }
+  mag[static_cast<int64_t>(n) * 128 + t] = magic0(e);
+}
+
+__device__ __forceinline__ float4 lds128(const unsigned char* p) { return *reinterpret_cast<const float4*>(p); }
+
+__device__ __forceinline__ void sts64(unsigned char* p, uint32_t a, uint32_t b) {
+  asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(smem_u32(p)), "r"(a), "r"(b) : "memory");
+}
+
+__device__ __forceinline__ uint32_t bf2(float lo, float hi) {
+  const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<const uint32_t*>(&v);
 }
 
 // One work item = (batch, output, 64x64 tile).  Its K dimension is a stream
@@ -134,10 +147,18 @@ __device__ __forceinline__ void issue_step(const float2* base, int64_t plane, in
 // the other (a K-concatenation into one accumulator, common exponents).
 //
 // Warp roles (one CTA per SM, items strided over the CTAs):
-//   warps 0-7   slice step g into ring stage g mod 4 once the MMAs that last
-//               read it have completed (empty[stage], a tcgen05.commit), then
-//               arrive on full[stage]; each thread's raw values arrive by
-//               cp.async three steps ahead, in a ring of its own;
+//   warp 17     (one thread) loads step g's raw operands into raw stage
+//               g mod 4 once the slicers have read it (raw_empty): two TMA
+//               boxes (A and B rows of the step's quantities, zeros past n_p
+//               and n_b), the step's 16 D values and, on an item's first
+//               step, the item's rounding constants; one mbarrier (raw_full)
+//               counts the bytes;
+//   warps 0-7   thread (row r, points 4q..4q+3) reads its raw values, frees
+//               the raw stage, forms the D-scaled A values in double-float,
+//               slices both sides into six BF16 digits and stores them (8
+//               bytes per slice and side) into operand stage g mod 4 once the
+//               MMAs that last read it have completed (empty[stage], a
+//               tcgen05.commit), then arrives on full[stage];
 //   warp 16     (one thread) waits full[stage], issues the six MMAs into the
 //               item's accumulator set (items alternate between two sets of
 //               192 TMEM columns), commits empty[stage], and after an item's
@@ -151,26 +172,29 @@ __device__ __forceinline__ void issue_step(const float2* base, int64_t plane, in
 // abort flag that ends the other roles' waits, and the MMA thread drains its
 // outstanding MMAs (bounded) before tensor memory is freed.
 __global__ void __launch_bounds__(kThreads, 1)
-    k_split_products(DevBasis B, DevGrid G, const int4* __restrict__ items, int n_items,
-                     const int64_t* __restrict__ scr_off, const double* __restrict__ scratch,
-                     const int* __restrict__ colexp, const double* __restrict__ v, double* V, double* W0,
-                     double* SOx, double* SOy, double* SOz, unsigned* status) {
+    k_split_products(DevGrid G, const int4* __restrict__ items, const int* __restrict__ steps, int n_items,
+                     const CUtensorMap* __restrict__ maps, const float2* __restrict__ dpad,
+                     const float* __restrict__ mag, double* V, double* W0, double* SOx, double* SOy, double* SOz,
+                     unsigned* status) {
   extern __shared__ __align__(1024) unsigned char smem[];
   float* stage = reinterpret_cast<float*>(smem + kSmemEpi);
-  df* sD = reinterpret_cast<df*>(smem + kSmemD);
-  float* sMagA = reinterpret_cast<float*>(smem + kSmemExp);  // rounding constants of the rows
-  float* sMagB = sMagA + kTile;
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kSmemBar);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + kSmemBar + kNumBars * 8);
   volatile int* s_abort = reinterpret_cast<volatile int*>(smem + kSmemBar + kNumBars * 8 + 4);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (smem_u32(smem) & 1023u) {  // the swizzled TMA boxes need 1024-byte aligned stages
+    if (tid == 0) atomicOr(status, 2u);
+    return;
+  }
   const uint32_t bar0 = smem_u32(bars);
   auto full_bar = [&](int st) { return bar0 + 8u * st; };
   auto empty_bar = [&](int st) { return bar0 + 8u * (kStages + st); };
   auto accfull_bar = [&](int set) { return bar0 + 8u * (2 * kStages + set); };
   auto accempty_bar = [&](int set) { return bar0 + 8u * (2 * kStages + 2 + set); };
   const uint32_t drain_bar = bar0 + 8u * (2 * kStages + 4);
+  auto rawfull_bar = [&](int rs) { return bar0 + 8u * (2 * kStages + 5 + rs); };
+  auto rawempty_bar = [&](int rs) { return bar0 + 8u * (2 * kStages + 5 + kRaw + rs); };
 
   // zero tile Z at the head of each stage (never overwritten)
   for (int i = tid; i < kStages * kTileBytes / 16; i += kThreads) {
@@ -187,6 +211,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_init(accempty_bar(set), kEpiThreads);
     }
     mbar_init(drain_bar, 1);
+    for (int rs = 0; rs < kRaw; ++rs) {
+      mbar_init(rawfull_bar(rs), 1);
+      mbar_init(rawempty_bar(rs), kSlicers / 32);
+    }
     *s_abort = 0;
   }
   if (warp == kMmaWarp) {
@@ -202,113 +230,110 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   if (warp < kSlicers / 32) {
     // ---------------------------------------------------------- slicers
-    bool ok = true;
+    const int r = warp * 8 + (lane >> 2), q = lane & 3;  // row, points 4q..4q+3 of the step
+    // byte offsets: swizzled 16-byte chunks 2q, 2q+1 of row r in a raw box;
+    // the 8-byte slot of (r, 4q) in a K-major core-matrix operand tile
+    const int rc0 = r * 128 + (((2 * q) ^ (r & 7)) << 4), rc1 = r * 128 + (((2 * q + 1) ^ (r & 7)) << 4);
+    const int dst_off = (r >> 3) * kSBO + (q >> 1) * kLBO + (r & 7) * 16 + (q & 1) * 8;
     int g = 0;  // steps sliced by this CTA
-    for (int n = blockIdx.x;; n += gridDim.x) {
-      // the previous item's constants are no longer read; agree on stopping
-      if (bar_red_or(1, kSlicers, !ok || *s_abort) || n >= n_items) break;
-      const int4 item = items[n];
-      const int64_t b = item.x;
-      const int o = item.y, ti = item.z, tj = item.w;
-      const int64_t p0 = G.pt_ptr[b];
-      const int np = static_cast<int>(G.pt_ptr[b + 1] - p0);
-      const int ldp = (np + 7) & ~7;
-      const int nb = static_cast<int>(G.bat_fn_ptr[b + 1] - G.bat_fn_ptr[b]);
-      const int64_t plane = static_cast<int64_t>(nb) * ldp;
-      const float2* base = reinterpret_cast<const float2*>(scratch) + scr_off[b];
-      const int* cexp = colexp + 8 * G.bat_fn_ptr[b];
-      const Products P = products_of(o);
-      const int i0 = ti * kTile, j0 = tj * kTile;
-      // Column exponents (W0: one exponent per function over its three gradient
-      // components, so that its K-concatenated products share units) and D.
-      if (tid < kTile) {
-        const int r = tid;
-        int ea = -30000, eb = -30000;
-        if (o == 1) {
-          if (i0 + r < nb) ea = max(cexp[1 * nb + i0 + r], max(cexp[2 * nb + i0 + r], cexp[3 * nb + i0 + r]));
-          if (j0 + r < nb) eb = max(cexp[5 * nb + j0 + r], max(cexp[6 * nb + j0 + r], cexp[7 * nb + j0 + r]));
-        } else {
-          if (i0 + r < nb) ea = cexp[P.a(0) * nb + i0 + r];
-          if (j0 + r < nb) eb = cexp[(4 + P.b(0)) * nb + j0 + r];
-        }
-        sMagA[r] = magic0(ea);
-        sMagB[r] = magic0(eb);
-      }
-      for (int p = tid; p < np; p += kSlicers) {
-        const double Dp = G.w[p0 + p] * v[p0 + p];
-        const float h = static_cast<float>(Dp);
-        sD[p] = df{h, static_cast<float>(Dp - static_cast<double>(h))};
-      }
-      bar_sync(1, kSlicers);
-      const int n_steps = item_steps(G, item);
-      const uint32_t raw0 = smem_u32(smem + kSmemRaw);
-      // copies run kRaw - 1 steps ahead of the slicing (one commit group per step)
-#pragma unroll
-      for (int q = 0; q < kRaw - 1; ++q) {
-        if (q < n_steps) issue_step(base, plane, ldp, np, nb, i0, j0, P, q, warp, lane, tid, raw0 + q * kRawStage);
-        cp_async_commit();
-      }
+    int n_steps_next = blockIdx.x < n_items ? steps[blockIdx.x] : 0;
+    for (int n = blockIdx.x; n < n_items; n += gridDim.x) {
+      const int n_steps = n_steps_next;
+      if (n + static_cast<int>(gridDim.x) < n_items) n_steps_next = steps[n + gridDim.x];
+      float mA = 0.f, mB = 0.f;
+      bool ok = true;
       for (int s = 0; s < n_steps; ++s, ++g) {
-        const int sa = s + kRaw - 1;
-        if (sa < n_steps)
-          issue_step(base, plane, ldp, np, nb, i0, j0, P, sa, warp, lane, tid, raw0 + (sa % kRaw) * kRawStage);
-        cp_async_commit();
-        cp_async_wait<kRaw - 1>();  // this thread's copies of step s have landed
-        const float4* rawp = reinterpret_cast<const float4*>(smem + kSmemRaw + (s % kRaw) * kRawStage);
-        float4 cur[2][kUnits];
-#pragma unroll
-        for (int side = 0; side < 2; ++side)
-#pragma unroll
-          for (int k = 0; k < kUnits; ++k) cur[side][k] = rawp[(side * kUnits + k) * kSlicers + tid];
-        const int st = g % kStages;
+        const int rs = g % kRaw, st = g % kStages;
+        if (!mbar_wait_abort(rawfull_bar(rs), (g / kRaw) & 1, s_abort, status)) {
+          ok = false;
+          break;
+        }
+        const unsigned char* raw = smem + kSmemRaw + rs * kRawStage;
+        if (s == 0) {
+          mA = reinterpret_cast<const float*>(raw + kRawMag)[r];
+          mB = reinterpret_cast<const float*>(raw + kRawMag)[64 + r];
+        }
+        const float4 a01 = lds128(raw + rc0), a23 = lds128(raw + rc1);
+        const float4 b01 = lds128(raw + kRawTile + rc0), b23 = lds128(raw + kRawTile + rc1);
+        const float4 d01 = lds128(raw + kRawD + q * 32), d23 = lds128(raw + kRawD + q * 32 + 16);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(rawempty_bar(rs));
         if (!mbar_wait_abort(empty_bar(st), ((g / kStages) & 1) ^ 1, s_abort, status)) {
           ok = false;
           break;
         }
-        const int c = P.n == 1 ? s : s / 3;
-        const int kc0 = c * kKc;
         unsigned char* sA = smem + kSmemStages + st * kStage;
         unsigned char* sB = sA + kStageA;
+        {  // A side: D-scaled values in double-float
+          const df x0 = df_mul(df{a01.x, a01.y}, df{d01.x, d01.y});
+          const df x1 = df_mul(df{a01.z, a01.w}, df{d01.z, d01.w});
+          const df x2 = df_mul(df{a23.x, a23.y}, df{d23.x, d23.y});
+          const df x3 = df_mul(df{a23.z, a23.w}, df{d23.z, d23.w});
+          float e0[kSlices], e1[kSlices], e2[kSlices], e3[kSlices];
+          slice6(x0.hi, x0.lo, mA, e0);
+          slice6(x1.hi, x1.lo, mA, e1);
+          slice6(x2.hi, x2.lo, mA, e2);
+          slice6(x3.hi, x3.lo, mA, e3);
 #pragma unroll
-        for (int side = 0; side < 2; ++side) {
-          const float* mg = side == 0 ? sMagA : sMagB;
-          unsigned char* dst = side == 0 ? sA + kTileBytes : sB;
+          for (int t = 0; t < kSlices; ++t)  // A: [Z, A0..A5]
+            sts64(sA + (1 + t) * kTileBytes + dst_off, bf2(e0[t], e1[t]), bf2(e2[t], e3[t]));
+        }
+        {  // B side
+          float e0[kSlices], e1[kSlices], e2[kSlices], e3[kSlices];
+          slice6(b01.x, b01.y, mB, e0);
+          slice6(b01.z, b01.w, mB, e1);
+          slice6(b23.x, b23.y, mB, e2);
+          slice6(b23.z, b23.w, mB, e3);
 #pragma unroll
-          for (int k = 0; k < kUnits; ++k) {
-            const int u = warp + (kSlicers / 32) * k;
-            const int rg = u >> 1, kq = u & 1;
-            const int r = rg * 8 + (lane >> 2), p = kc0 + 2 * (kq * 4 + (lane & 3));
-            const float m0 = mg[r];
-            const float4 x = cur[side][k];
-            float d0[kSlices], d1[kSlices];
-            if (side == 0) {  // A side: D-scaled values, the product in double-float
-              const df a0v = p < np ? df_mul(df{x.x, x.y}, sD[p]) : df{0.f, 0.f};
-              const df a1v = p + 1 < np ? df_mul(df{x.z, x.w}, sD[p + 1]) : df{0.f, 0.f};
-              slice6(a0v.hi, a0v.lo, m0, d0);
-              slice6(a1v.hi, a1v.lo, m0, d1);
-            } else {
-              slice6(x.x, x.y, m0, d0);
-              slice6(x.z, x.w, m0, d1);
-            }
-            const int off = rg * kSBO + kq * kLBO + (lane >> 2) * 16 + (lane & 3) * 4;
-#pragma unroll
-            for (int t = 0; t < kSlices; ++t)  // A: [Z, A0..A5]; B: [B0, B2, B4, B1, B3, B5]
-              *reinterpret_cast<__nv_bfloat162*>(dst + (side == 0 ? t : b_tile(t)) * kTileBytes + off) =
-                  __floats2bfloat162_rn(d0[t], d1[t]);
-          }
+          for (int t = 0; t < kSlices; ++t)  // B: [B0, B2, B4, B1, B3, B5]
+            sts64(sB + b_tile(t) * kTileBytes + dst_off, bf2(e0[t], e1[t]), bf2(e2[t], e3[t]));
         }
         fence_async_smem();
         mbar_arrive(full_bar(st));
       }
-      cp_async_wait<0>();  // no copy of this item outlives it
+      // agree on stopping (a wait that gave up in one warp ends every role)
+      if (bar_red_or(1, kSlicers, !ok || *s_abort)) break;
     }
+  } else if (warp == kProdWarp) {
+    // ---------------------------------------------------------- TMA producer
+    if (lane == 0) {
+      int g = 0;
+      for (int n = blockIdx.x; n < n_items; n += gridDim.x) {
+        const int4 item = items[n];
+        const int n_steps = steps[n];
+        const Products P = products_of(item.y);
+        const CUtensorMap* map = maps + item.x;
+        const float2* drow = dpad + static_cast<int64_t>(item.x) * kDPitch;
+        const int i0 = item.z * kTile, j0 = item.w * kTile;
+        bool ok = true;
+        for (int s = 0; s < n_steps; ++s, ++g) {
+          const int rs = g % kRaw;
+          if (!mbar_wait_abort(rawempty_bar(rs), ((g / kRaw) & 1) ^ 1, s_abort, status, 32)) {
+            ok = false;
+            break;
+          }
+          const int c = P.n == 1 ? s : s / 3, pr = s - c * P.n;
+          const uint32_t dst = smem_u32(smem + kSmemRaw + rs * kRawStage);
+          const uint32_t fb = rawfull_bar(rs);
+          arrive_expect_tx(fb, 2 * kRawTile + kKc * 8 + (s == 0 ? 128 * 4 : 0));
+          tma_load_3d(dst, map, c * kKc, i0, P.a(pr), fb);
+          tma_load_3d(dst + kRawTile, map, c * kKc, j0, P.b(pr), fb);
+          bulk_copy(dst + kRawD, drow + c * kKc, kKc * 8, fb);
+          if (s == 0) bulk_copy(dst + kRawMag, mag + static_cast<int64_t>(n) * 128, 128 * 4, fb);
+        }
+        if (!ok) break;
+      }
+      // no copy outlives the CTA: the last kRaw issued steps have landed
+      // (immediately true unless a wait gave up; bounded either way)
+      for (int h = max(0, g - kRaw); h < g; ++h) (void)mbar_wait(rawfull_bar(h % kRaw), (h / kRaw) & 1, status);
+    }
+    __syncwarp();
   } else if (warp == kMmaWarp) {
     // ---------------------------------------------------------- MMA issue
     if (lane == 0) {
       int g = 0, k = 0;
       for (int n = blockIdx.x; n < n_items; n += gridDim.x, ++k) {
-        const int4 item = items[n];
-        const int n_steps = item_steps(G, item);
+        const int n_steps = steps[n];
         const int set = k & 1;
         if (!mbar_wait_abort(accempty_bar(set), ((k >> 1) & 1) ^ 1, s_abort, status, 64)) break;
         tc_fence_after();
@@ -364,8 +389,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         // thread -> (column, rows): a warp covers 16 consecutive columns of two rows
         const int col = et & 15, j = j0 + c0 + col;
 #pragma unroll 2
-        for (int q = 0; q < 8; ++q) {
-          const int r = (et >> 4) + 8 * q, i = i0 + r;
+        for (int qr = 0; qr < 8; ++qr) {
+          const int r = (et >> 4) + 8 * qr, i = i0 + r;
           if (i >= nb || j >= nb) continue;
           const float L0 = stg[r * kEpiPitch + col], L1 = stg[(r + 64) * kEpiPitch + col];
           const float L2 = stg[(128 + r) * kEpiPitch + col], L3 = stg[(192 + r) * kEpiPitch + col];
@@ -423,16 +448,22 @@ q4c_status integrate_split(const q4c_tables* t, const q4c_grid* g, const double*
     const int64_t b0 = g->wave_b0[wv], b1 = g->wave_b0[wv + 1];
     if (b1 <= b0) continue;
     if (q4c_status st = launch_fill_idx(t, g, b0, b1, s)) return st;
-    if (q4c_status st = launch_basis_df(t, g, b0, b1, v, g->d_colexp, nullptr, 4, s)) return st;
+    if (q4c_status st = launch_basis_df(t, g, b0, b1, v, g->d_colexp, nullptr, 4, s, g->d_dpad)) return st;
     const int64_t i0 = g->split_w0[wv], i1 = g->split_w0[wv + 1];
     const int n_items = static_cast<int>(i1 - i0);
     if (n_items == 0) continue;
+    {
+      KernelScope ks("split_prep", s);
+      split::k_item_prep<<<n_items, 128, 0, s>>>(g->view(), g->d_split_items + i0, g->d_colexp, g->d_split_mag);
+    }
+    Q4C_CUDA(cudaGetLastError());
     const int grid = std::min(n_items, n_sm);
     {
       KernelScope ks("split_products", s);
       split::k_split_products<<<grid, split::kThreads, split::kSmemTotal, s>>>(
-          t->view(), g->view(), g->d_split_items + i0, n_items, g->d_scr_off, g->d_scratch,
-          g->d_colexp, v, out->V, out->W0, out->SOx, out->SOy, out->SOz, g->d_status);
+          g->view(), g->d_split_items + i0, g->d_split_steps + i0, n_items,
+          reinterpret_cast<const CUtensorMap*>(g->d_tmaps), g->d_dpad, g->d_split_mag, out->V, out->W0, out->SOx,
+          out->SOy, out->SOz, g->d_status);
     }
     Q4C_CUDA(cudaGetLastError());
   }
