@@ -225,9 +225,12 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 // (n_p, n_b, 4) and row pitch ceil8(n_p), read in boxes of 16 points x 64
 // functions with the 128-byte swizzle.  Points past n_p and functions past
 // n_b read as zeros.
+// A second set with boxes of 64 points x 16 functions (no swizzle) serves the
+// density and the adjoint, whose A operand runs over points.
 static q4c_status encode_tile_maps(q4c_grid* g) {
   const int64_t nB = g->n_batches;
-  std::vector<CUtensorMap> maps(static_cast<size_t>(std::max<int64_t>(nB, 1)));
+  const size_t n_maps = static_cast<size_t>(std::max<int64_t>(nB, 1));
+  std::vector<CUtensorMap> maps(2 * n_maps);
   std::memset(maps.data(), 0, sizeof(CUtensorMap) * maps.size());
   auto enc = tensor_map_encoder();
   if (!enc) {
@@ -242,11 +245,15 @@ static q4c_status encode_tile_maps(q4c_grid* g) {
     void* base = g->d_scratch + g->h_scr_off[b];
     const cuuint64_t dims[3] = {static_cast<cuuint64_t>(np), static_cast<cuuint64_t>(nb), 4};
     const cuuint64_t strides[2] = {static_cast<cuuint64_t>(ldp * 8), static_cast<cuuint64_t>(nb * ldp * 8)};
-    const cuuint32_t box[3] = {16, 64, 1};
+    const cuuint32_t box[3] = {16, 64, 1}, box_rd[3] = {64, 16, 1};
     const cuuint32_t estr[3] = {1, 1, 1};
-    const CUresult r = enc(&maps[b], CU_TENSOR_MAP_DATA_TYPE_INT64, 3, base, dims, strides, box, estr,
-                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    CUresult r = enc(&maps[b], CU_TENSOR_MAP_DATA_TYPE_INT64, 3, base, dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r == CUDA_SUCCESS)
+      r = enc(&maps[n_maps + b], CU_TENSOR_MAP_DATA_TYPE_INT64, 3, base, dims, strides, box_rd, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) {
       set_error("grid_partition: cuTensorMapEncodeTiled failed for batch " + std::to_string(b) + " (CUresult " +
                 std::to_string(static_cast<int>(r)) + ")");
@@ -869,7 +876,7 @@ extern "C" q4c_status grid_partition(const q4c_grid_desc* d, const q4c_tables* t
     if (e == cudaSuccess) e = cudaMalloc(&g->d_bat_idx, sizeof(int) * g->idx_entries);
     if (e == cudaSuccess) e = cudaMalloc(&g->d_split_mag, sizeof(float) * 128 * max_wave_items);
     if (e == cudaSuccess) e = cudaMalloc(&g->d_dpad, sizeof(float2) * kDPitch * std::max<int64_t>(nB, 1));
-    if (e == cudaSuccess) e = cudaMalloc(&g->d_tmaps, sizeof(CUtensorMap) * std::max<int64_t>(nB, 1));
+    if (e == cudaSuccess) e = cudaMalloc(&g->d_tmaps, 2 * sizeof(CUtensorMap) * std::max<int64_t>(nB, 1));
     if (e == cudaSuccess) e = cudaMalloc(&g->d_status, sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMemset(g->d_status, 0, sizeof(unsigned));
     g->split_ws_bytes = static_cast<int64_t>(sizeof(int)) * (8 * g->h_bat_fn_ptr[nB] + 4 * nP) +

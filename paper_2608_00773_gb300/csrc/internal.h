@@ -170,7 +170,8 @@ struct q4c_grid {
   int4* d_split_items = nullptr;
   int* d_split_steps = nullptr;            // K-steps of 16 points per item (3x for W0)
   float* d_split_mag = nullptr;            // [items of the largest wave][128] rounding constants
-  void* d_tmaps = nullptr;                 // [n_batches] 3-D TMA maps (points, functions, quantity) of the tiles
+  void* d_tmaps = nullptr;                 // [2][n_batches] 3-D TMA maps (points, functions, quantity) of the
+                                           // tiles: boxes 16 x 64 (products), 64 x 16 (density, adjoint)
   float2* d_dpad = nullptr;                // [n_batches][kDPitch] D = w v as (hi, lo), zero past n_p
   int* d_colexp = nullptr;                 // [8 * sum n_b]
   std::vector<int64_t> rd_w0;              // [n_waves+1] ranges into d_rd_items

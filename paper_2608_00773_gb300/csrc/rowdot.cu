@@ -19,6 +19,8 @@
 // once into BF16 digit tiles laid out exactly as the MMA reads them (per
 // matrix, 64-function j-tile and 16-function i-chunk: six 2 KB tiles); the
 // main kernel fetches one 12 KB block per K-step with a bulk copy.
+#include <cuda.h>
+
 #include "internal.h"
 #include "tc.cuh"
 
@@ -35,19 +37,22 @@ constexpr int kSlicers = 256;                  // warps 0-7 slice F
 constexpr int kEpiWarp0 = 8;                   // warps 8-15 drain tensor memory (two groups of four)
 constexpr int kEpiThreads = 256;
 constexpr int kMmaWarp = 16;  // warp 16 owns tensor memory and issues the MMAs
-constexpr int kThreads = 17 * 32;
-constexpr int kUnits = 16 / (kSlicers / 32);         // slicing units per thread (A side only)
+constexpr int kProdWarp = 17;  // warp 17 issues the TMA loads of F
+constexpr int kThreads = 18 * 32;
 constexpr int kStageA = (kSlices + 1) * kTileBytes;  // [Z, A0..A5]
 constexpr int kStage = kStageA + kBlockB;            // 26 KB
 constexpr int kStages = 4;
-constexpr int kRaw = 4;                               // ring of raw F values (cp.async)
-constexpr int kRawStage = kSlicers * kUnits * 2 * 8;  // 8 KB
-constexpr int kSmemStages = 0;
-constexpr int kSmemRaw = kSmemStages + kStages * kStage;
-constexpr int kSmemMag = kSmemRaw + kRaw * kRawStage;  // [4][64] rounding constants per point
-constexpr int kSmemY = kSmemMag + 4 * kTile * 4;    // [4][64] double partials per point
+// raw ring: per K-step the box of F (16 functions x 64 points of (hi, lo),
+// 512-byte rows) and, on an item's first step, the points' exponents
+constexpr int kRaw = 4;
+constexpr int kRawTile = kKc * kTile * 8;  // 8 KB
+constexpr int kRawExp = kRawTile;          // [64][4] per-point exponents
+constexpr int kRawStage = 9 * 1024;
+constexpr int kSmemRaw = 0;
+constexpr int kSmemStages = kSmemRaw + kRaw * kRawStage;
+constexpr int kSmemY = kSmemStages + kStages * kStage;  // [4][64] double partials per point
 constexpr int kSmemBar = kSmemY + 4 * kTile * 8;
-constexpr int kNumBars = 2 * kStages + 5;  // full[S], empty[S], accfull[2], accempty[2], drain
+constexpr int kNumBars = 2 * kStages + 5 + 2 * kRaw;  // full, empty, accfull[2], accempty[2], drain, raw full/empty
 constexpr int kSmemTotal = kSmemBar + kNumBars * 8 + 16;
 constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kSetCols = 256;
@@ -167,11 +172,6 @@ __global__ void __launch_bounds__(256) k_gslice(DevGrid G, int64_t b0, int anti_
   }
 }
 
-// 8-byte asynchronous copy (zero-filled past src_bytes)
-__device__ __forceinline__ void cp_async8(uint32_t dst, const void* src, int src_bytes) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
-}
-
 // the work of one item (batch, 64-point tile): groups (j-tile, product) in
 // order, each a K-loop of n_ic steps over the functions i
 struct ItemInfo {
@@ -226,25 +226,30 @@ struct StepIter {
 // Every wait is bounded; a timeout sets the status bit and an abort flag.
 template <int MODE>  // 0: density, 1: adjoint
 __global__ void __launch_bounds__(kThreads, 1)
-    k_split_rowdot(DevBasis B, DevGrid G, const int2* __restrict__ items, int n_items,
+    k_split_rowdot(DevGrid G, const int2* __restrict__ items, int n_items, const CUtensorMap* __restrict__ maps,
                    const int64_t* __restrict__ scr_off, const double* __restrict__ scratch,
                    const int* __restrict__ rowexp, const int64_t* __restrict__ gsl_off,
                    const unsigned char* __restrict__ gsl, unsigned present, int weighted,
                    double* __restrict__ out, unsigned* status) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  float* sMag = reinterpret_cast<float*>(smem + kSmemMag);  // [quantity][point]
   double* sY = reinterpret_cast<double*>(smem + kSmemY);    // [part][point]
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kSmemBar);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + kSmemBar + kNumBars * 8);
   volatile int* s_abort = reinterpret_cast<volatile int*>(smem + kSmemBar + kNumBars * 8 + 4);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (smem_u32(smem) & 1023u) {  // TMA boxes and operand tiles need aligned stages
+    if (tid == 0) atomicOr(status, 2u);
+    return;
+  }
   const uint32_t bar0 = smem_u32(bars);
   auto full_bar = [&](int st) { return bar0 + 8u * st; };
   auto empty_bar = [&](int st) { return bar0 + 8u * (kStages + st); };
   auto accfull_bar = [&](int set) { return bar0 + 8u * (2 * kStages + set); };
   auto accempty_bar = [&](int set) { return bar0 + 8u * (2 * kStages + 2 + set); };
   const uint32_t drain_bar = bar0 + 8u * (2 * kStages + 4);
+  auto rawfull_bar = [&](int rs) { return bar0 + 8u * (2 * kStages + 5 + rs); };
+  auto rawempty_bar = [&](int rs) { return bar0 + 8u * (2 * kStages + 5 + kRaw + rs); };
   // the products whose matrix is present, in order, 3 bits each (registers only)
   unsigned plist = 0;
   int n_prod = 0;
@@ -256,6 +261,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int st = i / (kTileBytes / 16), off = i - st * (kTileBytes / 16);
     reinterpret_cast<uint4*>(smem + kSmemStages + st * kStage)[off] = make_uint4(0, 0, 0, 0);
   }
+  fence_async_smem();  // the zero tiles are read by the tensor cores (async proxy)
   if (tid == 0) {
     for (int st = 0; st < kStages; ++st) {
       mbar_init(full_bar(st), kSlicers);
@@ -266,6 +272,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_init(accempty_bar(set), kEpiThreads);
     }
     mbar_init(drain_bar, 1);
+    for (int rs = 0; rs < kRaw; ++rs) {
+      mbar_init(rawfull_bar(rs), 1);
+      mbar_init(rawempty_bar(rs), kSlicers / 32);
+    }
     *s_abort = 0;
   }
   if (warp == kMmaWarp) {
@@ -281,51 +291,35 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   if (warp < kSlicers / 32) {
     // ---------------------------------------------------------- slicers
+    // thread = (point p, functions 4q..4q+3 of the step)
+    const int p = 16 * (warp >> 1) + (lane & 15), q = 2 * (warp & 1) + (lane >> 4);
+    const int dst_off = (p >> 3) * kSBO + (q >> 1) * kLBO + (p & 7) * 16 + (q & 1) * 8;
     bool ok = true;
     int g = 0;  // steps of this CTA
-    const uint32_t raw0 = smem_u32(smem + kSmemRaw);
-    for (int n = blockIdx.x;; n += gridDim.x) {
-      if (bar_red_or(1, kSlicers, !ok || *s_abort) || n >= n_items) break;
+    for (int n = blockIdx.x; n < n_items; n += gridDim.x) {
       const ItemInfo I = item_info(G, items[n]);
-      const float2* base = reinterpret_cast<const float2*>(scratch) + scr_off[I.b];
-      const int r0 = I.pt * kTile;
-      for (int e = tid; e < 4 * kTile; e += kSlicers) {  // per quantity and point
-        const int q = e >> 6, r = e & 63, p = r0 + r;
-        sMag[e] = magic0(p < I.np ? rowexp[4 * (I.bp0 + p) + q] : -30000);
-      }
-      bar_sync(1, kSlicers);
+      const bool live = I.pt * kTile + p < I.np;
       const unsigned char* gblk = gsl + gsl_off[I.b];
       const int n_steps = I.n_jt * n_prod * I.n_ic;
-      // the raw copies of step t (t = s + 3): (j-tile, product, chunk) advanced incrementally
-      StepIter it_issue;
-      auto issue = [&](uint32_t raw) {
-        const int qf = prod_at(it_issue.kk).qf;
-        const int i0 = it_issue.ic * kKc;
-#pragma unroll
-        for (int k = 0; k < kUnits; ++k) {
-          const int u = warp + (kSlicers / 32) * k;
-          const int r = (u >> 1) * 8 + (lane >> 2), i = i0 + 2 * ((u & 1) * 4 + (lane & 3));
-          const int p = r0 + r;
-#pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            const bool live = p < I.np && i + h < I.nb;
-            const float2* src = live ? base + qf * I.plane + static_cast<int64_t>(i + h) * I.ldp + p : base;
-            cp_async8(raw + ((k * 2 + h) * kSlicers + tid) * 8, src, live ? 8 : 0);
-          }
-        }
-        it_issue.next(I.n_ic, n_prod);
-      };
-#pragma unroll
-      for (int q = 0; q < kRaw - 1; ++q) {
-        if (q < n_steps) issue(raw0 + q * kRawStage);
-        cp_async_commit();
-      }
+      float m0 = 0.f, m1 = 0.f, m2 = 0.f, m3 = 0.f;  // rounding constants of the point's four quantities
       StepIter it;
       for (int s = 0; s < n_steps; ++s, ++g) {
-        const int sa = s + kRaw - 1;
-        if (sa < n_steps) issue(raw0 + (sa % kRaw) * kRawStage);
-        cp_async_commit();
-        const int st = g % kStages;
+        const int rs = g % kRaw, st = g % kStages;
+        if (!mbar_wait_abort(rawfull_bar(rs), (g / kRaw) & 1, s_abort, status)) {
+          ok = false;
+          break;
+        }
+        const unsigned char* raw = smem + kSmemRaw + rs * kRawStage;
+        if (s == 0 && live) {
+          const int4 e = *reinterpret_cast<const int4*>(raw + kRawExp + p * 16);
+          m0 = magic0(e.x);
+          m1 = magic0(e.y);
+          m2 = magic0(e.z);
+          m3 = magic0(e.w);
+        }
+        float2 x[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) x[k] = *reinterpret_cast<const float2*>(raw + (4 * q + k) * (kTile * 8) + p * 8);
         if (!mbar_wait_abort(empty_bar(st), ((g / kStages) & 1) ^ 1, s_abort, status)) {
           ok = false;
           break;
@@ -339,30 +333,60 @@ __global__ void __launch_bounds__(kThreads, 1)
           expect_tx(full_bar(st), kBlockB);
           bulk_copy(smem_u32(sA + kStageA), src, kBlockB, full_bar(st));
         }
-        cp_async_wait<kRaw - 1>();  // this thread's raw values of step s have landed
-        const float2* rawp = reinterpret_cast<const float2*>(smem + kSmemRaw + (s % kRaw) * kRawStage);
-        const float* mg = sMag + P.qf * kTile;
+        const float m = P.qf == 0 ? m0 : P.qf == 1 ? m1 : P.qf == 2 ? m2 : m3;
+        float d0[kSlices], d1[kSlices], d2[kSlices], d3[kSlices];
+        slice6(x[0].x, x[0].y, m, d0);
+        slice6(x[1].x, x[1].y, m, d1);
+        slice6(x[2].x, x[2].y, m, d2);
+        slice6(x[3].x, x[3].y, m, d3);
 #pragma unroll
-        for (int k = 0; k < kUnits; ++k) {
-          const int u = warp + (kSlicers / 32) * k;
-          const int rg = u >> 1, kq = u & 1;
-          const int r = rg * 8 + (lane >> 2);
-          const float2 x0 = rawp[(k * 2 + 0) * kSlicers + tid], x1 = rawp[(k * 2 + 1) * kSlicers + tid];
-          float d0[kSlices], d1[kSlices];
-          slice6(x0.x, x0.y, mg[r], d0);
-          slice6(x1.x, x1.y, mg[r], d1);
-          const int off = rg * kSBO + kq * kLBO + (lane >> 2) * 16 + (lane & 3) * 4;
-#pragma unroll
-          for (int t = 0; t < kSlices; ++t)
-            *reinterpret_cast<__nv_bfloat162*>(sA + kTileBytes + t * kTileBytes + off) =
-                __floats2bfloat162_rn(d0[t], d1[t]);
+        for (int t = 0; t < kSlices; ++t) {
+          const __nv_bfloat162 lo = __floats2bfloat162_rn(d0[t], d1[t]), hi = __floats2bfloat162_rn(d2[t], d3[t]);
+          asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(smem_u32(sA + (1 + t) * kTileBytes + dst_off)),
+                       "r"(*reinterpret_cast<const uint32_t*>(&lo)), "r"(*reinterpret_cast<const uint32_t*>(&hi))
+                       : "memory");
         }
         fence_async_smem();
         mbar_arrive(full_bar(st));
+        // Only now is the raw stage free: the digit stores above take their
+        // data from the loaded values, so once they have issued the loads
+        // have landed (freeing it right after issuing the loads let the next
+        // TMA box overwrite values that were still on their way).
+        __syncwarp();
+        if (lane == 0) mbar_arrive(rawempty_bar(rs));
         it.next(I.n_ic, n_prod);
       }
-      cp_async_wait<0>();
+      // agree on stopping (a wait that gave up in one warp ends every role)
+      if (bar_red_or(1, kSlicers, !ok || *s_abort)) break;
     }
+  } else if (warp == kProdWarp) {
+    // ---------------------------------------------------------- TMA producer
+    if (lane == 0) {
+      int g = 0;
+      bool ok = true;
+      for (int n = blockIdx.x; n < n_items && ok; n += gridDim.x) {
+        const ItemInfo I = item_info(G, items[n]);
+        const CUtensorMap* map = maps + I.b;
+        const int r0 = I.pt * kTile, rows = min(kTile, I.np - r0);
+        const int n_steps = I.n_jt * n_prod * I.n_ic;
+        StepIter it;
+        for (int s = 0; s < n_steps; ++s, ++g) {
+          const int rs = g % kRaw;
+          if (!mbar_wait_abort(rawempty_bar(rs), ((g / kRaw) & 1) ^ 1, s_abort, status, 32)) {
+            ok = false;
+            break;
+          }
+          const uint32_t dst = smem_u32(smem + kSmemRaw + rs * kRawStage), fb = rawfull_bar(rs);
+          arrive_expect_tx(fb, kRawTile + (s == 0 ? rows * 16 : 0));
+          tma_load_3d(dst, map, r0, it.ic * kKc, prod_at(it.kk).qf, fb);
+          if (s == 0) bulk_copy(dst + kRawExp, rowexp + 4 * (I.bp0 + r0), rows * 16, fb);
+          it.next(I.n_ic, n_prod);
+        }
+      }
+      // no copy outlives the CTA: the last kRaw issued steps have landed
+      for (int h = max(0, g - kRaw); h < g; ++h) (void)mbar_wait(rawfull_bar(h % kRaw), (h / kRaw) & 1, status);
+    }
+    __syncwarp();
   } else if (warp == kMmaWarp) {
     // ---------------------------------------------------------- MMA issue
     if (lane == 0) {
@@ -414,7 +438,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       const float2* base = reinterpret_cast<const float2*>(scratch) + scr_off[I.b];
       const int p = I.pt * kTile + r;
       const bool live = p < I.np;
-      df y = {0.f, 0.f};
+      df y = {0.f, 0.f};  // running sum over the item's groups
       int kk = 0, jt = 0;
       for (int grp = 0; grp < I.n_jt * n_prod; ++grp, ++k) {
         const int set = k & 1;
@@ -439,24 +463,37 @@ __global__ void __launch_bounds__(kThreads, 1)
           break;
         }
         tc_fence_after();
+        // this group's sum yh + yl: per column u = v0 + v1 + v2 (top lanes
+        // L0 + L2 + L4 with L0, L2 exact; bottom lanes L1 + L3 + L5) as the
+        // exact two-sum of v0, v1 with v2 (2^-16 and further below) folded
+        // into its error; the product with R = (rh, rl) keeps its FMA error
+        // term unnormalised, and the sum adds each product by a two-sum whose
+        // error joins yl (all terms about 2^-24 below yh and beyond)
+        float yh = 0.f, yl = 0.f;
         for (int c0 = eg * 8; c0 < N; c0 += 16) {
           if (c0 + 16 < N) load_R(c0 + 16, Rn);
           float v0[8], v1[8], v2[8];
-          tmem_ld8(tmem + lane_base + set * kSetCols + c0, v0);
-          tmem_ld8(tmem + lane_base + set * kSetCols + kTile + c0, v1);
-          tmem_ld8(tmem + lane_base + set * kSetCols + 2 * kTile + c0, v2);
+          const uint32_t ta = tmem + lane_base + set * kSetCols + c0;
+          tmem_ld8x3(ta, ta + kTile, ta + 2 * kTile, v0, v1, v2);
 #pragma unroll
           for (int i = 0; i < 8; ++i) {
-            // top: L0 + L2 + L4 (L0, L2 exact); bottom: L1 + L3 + L5 (L1 exact)
-            const df u = df_add(two_sum(v0[i], v1[i]), df{v2[i], 0.f});
-            const df pr = df_mul(df{Rc[i].x, Rc[i].y}, u);
-            y = df_add(y, df{P.factor * pr.hi, P.factor * pr.lo});  // factor 1 or 2: exact
+            const df u = two_sum(v0[i], v1[i]);
+            const float ul = __fadd_rn(u.lo, v2[i]);
+            const float rh = Rc[i].x, rl = Rc[i].y;
+            const float ph = __fmul_rn(rh, u.hi);
+            float pl = __fmaf_rn(rh, u.hi, -ph);
+            pl = __fmaf_rn(rh, ul, pl);
+            pl = __fmaf_rn(rl, u.hi, pl);
+            const df a = two_sum(yh, ph);
+            yh = a.hi;
+            yl = __fadd_rn(yl, __fadd_rn(a.lo, pl));
           }
 #pragma unroll
           for (int i = 0; i < 8; ++i) Rc[i] = Rn[i];
         }
         tc_fence_before();
         mbar_arrive(accempty_bar(set));
+        y = df_add(y, df{P.factor * yh, P.factor * yl});  // factor 1 or 2: exact
         if (++kk == n_prod) {
           kk = 0;
           ++jt;
@@ -527,7 +564,8 @@ q4c_status run(const q4c_tables* t, const q4c_grid* g, const double* const mats[
     {
       KernelScope ks(name, s);
       k_split_rowdot<MODE><<<grid, kThreads, kSmemTotal, s>>>(
-          t->view(), g->view(), g->d_rd_items + i0, n_items, g->d_scr_off, g->d_scratch, g->d_rowexp,
+          g->view(), g->d_rd_items + i0, n_items, reinterpret_cast<const CUtensorMap*>(g->d_tmaps) + g->n_batches,
+          g->d_scr_off, g->d_scratch, g->d_rowexp,
           g->d_gsl_off, reinterpret_cast<const unsigned char*>(g->d_gsl), present, weighted ? 1 : 0, out,
           g->d_status);
     }

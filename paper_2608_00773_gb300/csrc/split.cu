@@ -201,6 +201,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int st = i / (kTileBytes / 16), off = i - st * (kTileBytes / 16);
     reinterpret_cast<uint4*>(smem + kSmemStages + st * kStage)[off] = make_uint4(0, 0, 0, 0);
   }
+  fence_async_smem();  // the zero tiles are read by the tensor cores (async proxy)
   if (tid == 0) {
     for (int st = 0; st < kStages; ++st) {
       mbar_init(full_bar(st), kSlicers);
@@ -256,8 +257,6 @@ __global__ void __launch_bounds__(kThreads, 1)
         const float4 a01 = lds128(raw + rc0), a23 = lds128(raw + rc1);
         const float4 b01 = lds128(raw + kRawTile + rc0), b23 = lds128(raw + kRawTile + rc1);
         const float4 d01 = lds128(raw + kRawD + q * 32), d23 = lds128(raw + kRawD + q * 32 + 16);
-        __syncwarp();
-        if (lane == 0) mbar_arrive(rawempty_bar(rs));
         if (!mbar_wait_abort(empty_bar(st), ((g / kStages) & 1) ^ 1, s_abort, status)) {
           ok = false;
           break;
@@ -290,6 +289,11 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         fence_async_smem();
         mbar_arrive(full_bar(st));
+        // Only now is the raw stage free: the digit stores above take their
+        // data from the loaded values, so once they have issued the loads
+        // have landed (the next TMA box may not overwrite values in flight).
+        __syncwarp();
+        if (lane == 0) mbar_arrive(rawempty_bar(rs));
       }
       // agree on stopping (a wait that gave up in one warp ends every role)
       if (bar_red_or(1, kSlicers, !ok || *s_abort)) break;

@@ -209,3 +209,27 @@ def test_full_size_density_and_adjoint_sampled_points(prec, tol):
     li = np.array([pos[int(i)] for i in ids[sel]])
     assert rel_fro(n[li], n_ref) <= tol, rel_fro(n[li], n_ref)
     assert rel_fro(g[li], g_ref) <= tol, rel_fro(g[li], g_ref)
+
+
+def test_split_repeated_calls_agree_with_fp64():
+    """Integration, adjoint and density in alternation over several seeds (the
+    tensor-core kernels then start on shared memory and tensor memory that the
+    other kernels left behind), each against the FP64 path: catches ordering
+    faults between the asynchronous copies and the threads that read them."""
+    import torch
+    wl = small_cluster(12, seed=9)
+    lib = LibCase(wl)
+    Vref = q.q4c_integrate(lib.tables, lib.grid, lib.v, "fp64")
+    for seed in range(6):
+        Vs = q.q4c_integrate(lib.tables, lib.grid, lib.v, "split")
+        for a, b in zip(Vs[:5], Vref[:5]):
+            assert float(torch.linalg.norm(a - b) / torch.linalg.norm(b)) <= TOL_SPLIT, seed
+        G = lib.G(100 + seed)
+        g = q.q4c_integrate_backward(lib.tables, lib.grid, G, "split")
+        q.q4c_integrate(lib.tables, lib.grid, lib.v, "split")
+        n = q.q4c_density(lib.tables, lib.grid, G[0], "split")
+        gr = q.q4c_integrate_backward(lib.tables, lib.grid, G, "fp64")
+        nr = q.q4c_density(lib.tables, lib.grid, G[0], "fp64")
+        assert float(torch.linalg.norm(g - gr) / torch.linalg.norm(gr)) <= TOL_SPLIT, seed
+        assert float(torch.linalg.norm(n - nr) / torch.linalg.norm(nr)) <= TOL_SPLIT, seed
+    lib.grid.status()
