@@ -247,6 +247,59 @@ Q4C_API q4c_status q4c_density(const q4c_tables* tables, const q4c_grid* grid, c
 Q4C_API q4c_status q4c_density_full(const q4c_tables* tables, const q4c_grid* grid, const q4c_matrices* P,
                             q4c_precision prec, double* n_dev, q4c_stream stream);
 
+/* ---------------------------------------------------------------- spinors
+ * Scalar -> spinor transformation (Section II, Eqs. 9-14; Section III A,
+ * Eqs. 33-34, 37-38; Appendix A).  Spinor basis of an atom: per radial
+ * function (angular momentum l) in the species' order, j = l - 1/2
+ * (kappa = l, only for l > 0) then j = l + 1/2 (kappa = -l - 1), m_j = -j..j
+ * ascending; 2 (2l + 1) spinor functions per radial function, twice the
+ * atom's scalar functions.  Spinor function mu = sum G_(2t+s),mu phi_t eta_s
+ * with the Clebsch-Gordan coefficients of Eq. 10 and the complex harmonics
+ * Y~_l^m (Condon-Shortley phase) written in the real harmonics of
+ * Appendix B.  Spinor blocks are complex128 (re, im), block q of the pattern
+ * a row-major (2 nf_A) x (2 nf_B) matrix at 4*blk_off[q] (the layout of
+ * q4c_matrices.spinor_SS, rows spinor functions of atom A). */
+
+/* Quantum numbers of the spinor functions of one species: *n = 2 x its
+ * scalar function count; radial[i] (index of the radial function within the
+ * species), kappa[i], two_mj[i] = 2 m_j, host arrays of *n entries, any may
+ * be NULL.  Synchronous, no device work. */
+Q4C_API q4c_status q4c_spinor_basis(const q4c_tables* tables, int32_t species, int32_t* n, int32_t* radial,
+                            int32_t* kappa, int32_t* two_mj);
+
+/* Eqs. 33-34, per pattern block (A, B, T):
+ *   HL = G_A^dagger (V x 1) G_B               (large component, from F->V)
+ *   HS = G_A^dagger (W0 1 + i SO.sigma) G_B   (kinetic-balance small component,
+ *                                              from F->W0, F->SOx..SOz; NULL
+ *                                              slots count as zero)
+ * F: real device arrays [nnz] on the grid's pattern (q4c_integrate's output);
+ * HL_dev, HS_dev: device double [8*nnz] (complex128 [4*nnz]) or NULL to skip,
+ * overwritten.  EINVAL if HL is asked without F->V or HS without any of the
+ * small-component slots.  Stream-ordered. */
+Q4C_API q4c_status q4c_spinor_transform(const q4c_tables* tables, const q4c_grid* grid, const q4c_matrices* F,
+                                double* HL_dev, double* HS_dev, q4c_stream stream);
+
+/* Eqs. 37-38, the reverse map of a spinor density matrix D (device double
+ * [8*nnz], complex128 blocks as above, normally Hermitian: block (B, A, -T)
+ * = block (A, B, T)^dagger) to the scalar density matrices of the large and
+ * small components:
+ *   D'_ab = sum_mu,nu conj(G_a,mu) D_mu,nu G_b,nu,
+ *   P->V = P->W0 = Re tr_s D'_ij,  P->SOk = Re(i sum_ss' (sigma_k)_ss' D'_(is)(js'))
+ * so that q4c_density(P->V) gives the large-component density and
+ * q4c_density_full with (NULL, P->W0, P->SOx, P->SOy, P->SOz) the small one.
+ * P slots: device [nnz], overwritten; NULL slots are skipped.  Stream-ordered. */
+Q4C_API q4c_status q4c_spinor_density_matrices(const q4c_tables* tables, const q4c_grid* grid, const double* D_dev,
+                                       const q4c_matrices* P, q4c_stream stream);
+
+/* Algorithm 1 for one batch: the spinor functions present on the batch's
+ * local scalar functions (those of its active centres), in ascending global
+ * order (centre, then spinor index within the centre's atom).  *n gets the
+ * count (twice the batch's n_b); centre[] and spinor[] (host, *n entries,
+ * either may be NULL) the pairs.  Synchronous, no device work. */
+Q4C_API q4c_status q4c_grid_batch_spinors(const q4c_grid* grid, int64_t batch, int32_t* n, int32_t* centre,
+                                  int32_t* spinor);
+
+
 /* Adjoint of q4c_integrate for L = <G^V,V> + <G^W0,W0> + sum_k <G^SOk,SOk>:
  *   dLdv_p = w_p sum_M sum_ij G^M_ij f^M_ij(p)
  * with f^V = phi_i phi_j, f^W0 = grad phi_i . grad phi_j,

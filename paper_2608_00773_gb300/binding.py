@@ -25,6 +25,7 @@ STATUS = {0: "Q4C_OK", 1: "Q4C_EINVAL", 2: "Q4C_ENOMEM", 3: "Q4C_ECUDA", 4: "Q4C
 # every symbol include/q4c.h declares
 EXPORTS = ["nao_tabulate", "q4c_tables_destroy", "q4c_tables_export", "grid_partition", "q4c_grid_destroy",
            "q4c_grid_get_info", "q4c_grid_export", "q4c_grid_export_shifts", "q4c_grid_kpattern", "q4c_kfold", "q4c_grid_points", "q4c_integrate", "q4c_density", "q4c_density_full",
+           "q4c_spinor_basis", "q4c_spinor_transform", "q4c_spinor_density_matrices", "q4c_grid_batch_spinors",
            "q4c_integrate_backward", "q4c_integrate_noalloc", "q4c_basis_eval", "q4c_grid_status", "q4c_profile", "q4c_profile_read",
            "q4c_last_error"]
 
@@ -88,6 +89,10 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     L.q4c_density.argtypes = [vp, vp, vp, C.c_int, vp, vp]
     L.q4c_integrate_backward.argtypes = [vp, vp, C.POINTER(Matrices), C.c_int, vp, vp]
     L.q4c_density_full.argtypes = [vp, vp, C.POINTER(Matrices), C.c_int, vp, vp]
+    L.q4c_spinor_basis.argtypes = [vp, i32, vp, vp, vp, vp]
+    L.q4c_spinor_transform.argtypes = [vp, vp, C.POINTER(Matrices), vp, vp, vp]
+    L.q4c_spinor_density_matrices.argtypes = [vp, vp, vp, C.POINTER(Matrices), vp]
+    L.q4c_grid_batch_spinors.argtypes = [vp, i64, vp, vp, vp]
     L.q4c_integrate_noalloc.argtypes = [vp, vp, vp, C.POINTER(Matrices), vp]
     L.q4c_basis_eval.argtypes = [vp, vp, i64, vp, vp, vp, vp]
     L.q4c_grid_status.argtypes = [vp, vp]
@@ -198,6 +203,15 @@ class Grid:
                     batch_atoms=batoms[:int(baptr[-1])], blk_ptr=blk_ptr, blk_col=blk_col[:i.n_blocks],
                     blk_off=blk_off, blk_T=blk_T[:3 * i.n_blocks].reshape(-1, 3))
 
+    def batch_spinors(self, batch: int):
+        """(centre, spinor index within the centre's atom) of the spinor
+        functions present on a batch (Algorithm 1)."""
+        n = C.c_int32()
+        _check(load().q4c_grid_batch_spinors(self.h, batch, C.byref(n), None, None))
+        c, m = np.zeros(max(n.value, 1), np.int32), np.zeros(max(n.value, 1), np.int32)
+        _check(load().q4c_grid_batch_spinors(self.h, batch, C.byref(n), c.ctypes.data, m.ctypes.data))
+        return c[:n.value], m[:n.value]
+
     def kpattern(self):
         """(kblk_ptr, kblk_col, kblk_off) of the atom pairs with some block (A, B, T)."""
         n = C.c_int64()
@@ -278,6 +292,37 @@ def q4c_density_full(tables: Tables, grid: Grid, P: Sequence, prec="fp64", out=N
     m = Matrices(*[_ptr(x) for x in P], 0)
     _check(load().q4c_density_full(tables.h, grid.h, C.byref(m), _prec(prec), _ptr(out), _stream(stream)))
     return out
+
+
+def q4c_spinor_basis(tables: Tables, species: int):
+    """(radial, kappa, two_mj) of the spinor functions of one species."""
+    n = C.c_int32()
+    _check(load().q4c_spinor_basis(tables.h, species, C.byref(n), None, None, None))
+    rad, kap, mj = (np.zeros(n.value, np.int32) for _ in range(3))
+    _check(load().q4c_spinor_basis(tables.h, species, C.byref(n), rad.ctypes.data, kap.ctypes.data, mj.ctypes.data))
+    return rad, kap, mj
+
+
+def q4c_spinor_transform(tables: Tables, grid: Grid, F: Sequence, large=True, small=True, stream=None):
+    """(HL, HS): complex128 [4 nnz] spinor blocks G^dagger (V x 1) G and
+    G^dagger (W0 1 + i SO.sigma) G of F = [V, W0, SOx, SOy, SOz] (None = 0)."""
+    import torch
+    dev = next(x for x in F if x is not None).device
+    HL = torch.empty(4 * grid.nnz, dtype=torch.complex128, device=dev) if large else None
+    HS = torch.empty(4 * grid.nnz, dtype=torch.complex128, device=dev) if small else None
+    m = Matrices(*[_ptr(x) for x in F], 0)
+    _check(load().q4c_spinor_transform(tables.h, grid.h, C.byref(m), _ptr(HL), _ptr(HS), _stream(stream)))
+    return HL, HS
+
+
+def q4c_spinor_density_matrices(tables: Tables, grid: Grid, D, stream=None):
+    """[P^V, P^W0, P^SOx, P^SOy, P^SOz] (real [nnz]) of a spinor density matrix D
+    (complex128 [4 nnz] blocks)."""
+    import torch
+    P = [torch.empty(grid.nnz, dtype=torch.float64, device=D.device) for _ in range(5)]
+    m = Matrices(*[_ptr(x) for x in P], 0)
+    _check(load().q4c_spinor_density_matrices(tables.h, grid.h, _ptr(D), C.byref(m), _stream(stream)))
+    return P
 
 
 def q4c_kfold(grid: Grid, H, k, out=None, stream=None):

@@ -110,6 +110,13 @@ struct q4c_tables {
   float4* d_coef_df = nullptr;
   q4c::df* d_g0_df = nullptr;
   q4c::df* d_inv_knot_df = nullptr;
+  // scalar -> spinor relation tables (spinor.cu): per species the first
+  // spinor index (twice the first scalar function), and per spinor function
+  // its radial index, kappa and 2 m_j; device column and row views of G
+  std::vector<int> h_spn0, h_spn_radial, h_spn_kappa, h_spn_two_mj;
+  int* d_spn0 = nullptr;
+  void* d_spn_col = nullptr;
+  void* d_spn_row = nullptr;
   q4c::DevBasis view() const;
   q4c::DfTables df_view() const;
 };
@@ -206,6 +213,8 @@ q4c_status launch_basis_tiles(const q4c_tables* t, const q4c_grid* g, int64_t b0
 q4c_status launch_fill_idx(const q4c_tables* t, const q4c_grid* g, int64_t b0, int64_t b1, cudaStream_t s);
 
 // basis_df.cu
+// spinor.cu: scalar -> spinor relation tables of a set of species
+q4c_status build_spinor_tables(q4c_tables* t);
 // nq = 4: Phi, X, Y, Z tiles; nq = 1: Phi alone
 q4c_status launch_basis_df(const q4c_tables* t, const q4c_grid* g, int64_t b0, int64_t b1, const double* v,
                            int* colexp, int* rowexp, int nq, cudaStream_t s, float2* dpad = nullptr);

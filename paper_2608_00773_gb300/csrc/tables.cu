@@ -167,7 +167,7 @@ extern "C" q4c_status nao_tabulate(const q4c_basis_desc* desc, q4c_tables** out)
       (st = upload(&t->d_rad_l, t->rad_l)) || (st = upload(&t->d_sp_rad0, t->rad0)) ||
       (st = upload(&t->d_sp_nrad, t->n_rad)) || (st = upload(&t->d_sp_nfn, t->nfn)) ||
       (st = upload(&t->d_coef_df, coef_df)) || (st = upload(&t->d_g0_df, g0_df)) ||
-      (st = upload(&t->d_inv_knot_df, inv_knot))) {
+      (st = upload(&t->d_inv_knot_df, inv_knot)) || (st = build_spinor_tables(t))) {
     q4c_tables_destroy(t);
     return st;
   }
@@ -186,6 +186,9 @@ extern "C" void q4c_tables_destroy(q4c_tables* t) {
   cudaFree(t->d_coef_df);
   cudaFree(t->d_g0_df);
   cudaFree(t->d_inv_knot_df);
+  cudaFree(t->d_spn0);
+  cudaFree(t->d_spn_col);
+  cudaFree(t->d_spn_row);
   delete t;
 }
 
