@@ -100,8 +100,9 @@ Q4C_API q4c_status q4c_tables_export(const q4c_tables* tables, int32_t radial, d
  * Per atom: n_rad_shells Gauss-Chebyshev (second kind) radial shells mapped
  * by r = R (1+x)/(1-x), times Gauss-Legendre(n_theta) in cos(theta) times
  * n_phi uniform azimuths phi_b = (b + 1/2) 2 pi / n_phi.  Point weights
- * w = w_rad w_ang p_A(r), p_A the Becke partition (three iterations, no size
- * adjustment) over the atoms within r_nb of the point.  Points farther than
+ * w = w_rad w_ang p_A(r), p_A the Becke (or, by the descriptor's partition
+ * field, Stratmann) partition, no size adjustment, over the atoms within
+ * r_nb of the point.  Points farther than
  * r_cut from every atom, or with w = 0, are dropped.  The kept points are
  * split into batches by recursive median bisection along the longest
  * bounding-box axis until a batch holds <= batch_max points; the raw point
@@ -141,6 +142,10 @@ typedef struct q4c_grid_desc {
   int32_t n_molecules;     /* independent molecules (0 or 1: one system) */
   const int32_t* mol_atom_ptr; /* host [n_molecules+1]: atom ranges, 0 = p[0] < p[1] < ... = n_atoms;
                                   NULL when n_molecules <= 1 */
+  int32_t partition;       /* cell function of the partition of unity: 0 Becke (1988, three
+                              iterations; a zeroed descriptor), 1 Stratmann, Scuseria and Frisch
+                              (1996: odd degree-7 polynomial, a = 0.64, exactly 1 and 0 beyond);
+                              no size adjustment in either */
 } q4c_grid_desc;
 
 /* Builds the grid (raw points and base weights on the host, Becke weights in

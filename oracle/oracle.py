@@ -69,11 +69,13 @@ def lib() -> C.CDLL:
             L.orc_basis_eval.argtypes = [bp, C.c_int, _dp, C.c_int, _ip, _dp, _dp]
             L.orc_becke_weight.argtypes = [C.c_int, _dp, C.c_int, _dp, C.c_double]
             L.orc_becke_weight.restype = C.c_double
+            L.orc_partition_weight.argtypes = [C.c_int, _dp, C.c_int, _dp, C.c_double, C.c_int]
+            L.orc_partition_weight.restype = C.c_double
             L.orc_grid.argtypes = [C.c_int, _dp, C.c_int, C.c_double, C.c_int, C.c_int, C.c_double,
                                    C.c_double, C.c_longlong, _dp, _dp, _lp]
             L.orc_grid.restype = C.c_long
             L.orc_grid_cell.argtypes = [C.c_int, _dp, C.c_void_p, C.c_int, C.c_int, C.c_double, C.c_int,
-                                        C.c_int, C.c_double, C.c_double, C.c_longlong, _dp, _dp, _lp]
+                                        C.c_int, C.c_double, C.c_double, C.c_int, C.c_longlong, _dp, _dp, _lp]
             L.orc_grid_cell.restype = C.c_long
             L.orc_pattern.argtypes = [bp, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
             L.orc_pattern.restype = C.c_long
@@ -154,6 +156,15 @@ def becke_weight(centres: np.ndarray, owner: int, p, r_nb: float = 1e300) -> flo
     return lib().orc_becke_weight(len(c) // 3, c, owner, _f64(p), r_nb)
 
 
+PARTITIONS = {"becke": 0, "stratmann": 1}
+
+
+def partition_weight(centres: np.ndarray, owner: int, p, r_nb: float = 1e300, scheme: str = "becke") -> float:
+    """p_owner(r) with Becke's (1988) or Stratmann, Scuseria and Frisch's (1996) cell function."""
+    c = _f64(centres).reshape(-1)
+    return lib().orc_partition_weight(len(c) // 3, c, owner, _f64(p), r_nb, PARTITIONS[scheme])
+
+
 def grid(wl, stride: int = 1):
     """Kept grid points of a workload: (xyz (n,3), w (n,), raw id (n,)).
     stride > 1 evaluates only the raw points whose id is a multiple of it.
@@ -162,8 +173,8 @@ def grid(wl, stride: int = 1):
     xyz = np.zeros(3 * n_raw); w = np.zeros(n_raw); ids = np.zeros(n_raw, dtype=np.int64)
     lat = None if wl.lattice is None else _f64(wl.lattice).reshape(-1)
     n = lib().orc_grid_cell(wl.n_atoms, _f64(wl.xyz).reshape(-1), None if lat is None else lat.ctypes.data,
-                            wl.n_shell, wl.n_rad, wl.R, wl.n_theta, wl.n_phi, wl.r_c, wl.r_nb, stride, xyz, w,
-                            ids)
+                            wl.n_shell, wl.n_rad, wl.R, wl.n_theta, wl.n_phi, wl.r_c, wl.r_nb,
+                            PARTITIONS[wl.partition], stride, xyz, w, ids)
     return xyz[:3 * n].reshape(n, 3).copy(), w[:n].copy(), ids[:n].copy()
 
 

@@ -419,9 +419,25 @@ static double becke_s(double mu) {
   return 0.5 * (1.0 - f);
 }
 
-/* Becke weight p_owner(r) over the neighbour set N(r) = {B : |r - R_B| < r_nb}.
+/* Stratmann, Scuseria and Frisch (1996) cell function, without size
+ * adjustment: s(mu) = (1 - g(mu))/2 with the odd degree-7 polynomial
+ * g(x) = (35 x - 35 x^3 + 21 x^5 - 5 x^7)/16 of x = mu/a, a = 0.64, on
+ * |mu| <= a, and g = -1 below, +1 above (so s is exactly 1 near its own
+ * centre and 0 near the other). */
+static double stratmann_s(double mu) {
+  const double a = 0.64;
+  if (mu <= -a) return 1.0;
+  if (mu >= a) return 0.0;
+  const double x = mu / a, x2 = x * x;
+  const double g = x * (35.0 - x2 * (35.0 - x2 * (21.0 - 5.0 * x2))) / 16.0;
+  return 0.5 * (1.0 - g);
+}
+
+/* Partition weight p_owner(r) over the neighbour set N(r) = {B : |r - R_B| < r_nb},
+ * scheme 0 Becke's cell function, 1 Stratmann's.
  * centres: [n_c][3] (atoms, and periodic images if any). */
-double orc_becke_weight(int n_c, const double* centres, int owner, const double p[3], double r_nb) {
+double orc_partition_weight(int n_c, const double* centres, int owner, const double p[3], double r_nb,
+                            int scheme) {
   if (owner < 0 || owner >= n_c) return 0.0;
   double* dist = (double*)malloc(sizeof(double) * n_c);
   int* in = (int*)calloc(n_c, sizeof(int));
@@ -441,7 +457,8 @@ double orc_becke_weight(int n_c, const double* centres, int owner, const double 
         double dx = centres[3 * A] - centres[3 * B], dy = centres[3 * A + 1] - centres[3 * B + 1],
                dz = centres[3 * A + 2] - centres[3 * B + 2];
         double RAB = sqrt(dx * dx + dy * dy + dz * dz);
-        PA *= becke_s((dist[A] - dist[B]) / RAB);
+        const double mu = (dist[A] - dist[B]) / RAB;
+        PA *= scheme == 1 ? stratmann_s(mu) : becke_s(mu);
       }
       sum += PA;
       if (A == owner) Pown = PA;
@@ -453,7 +470,11 @@ double orc_becke_weight(int n_c, const double* centres, int owner, const double 
   return result;
 }
 
-/* Raw grid of every (0-cell) atom, Becke weights, pruning.
+double orc_becke_weight(int n_c, const double* centres, int owner, const double p[3], double r_nb) {
+  return orc_partition_weight(n_c, centres, owner, p, r_nb, 0);
+}
+
+/* Raw grid of every (0-cell) atom, partition weights, pruning.
  * Raw point id = ((atom*n_rad + i)*n_theta + a)*n_phi + b; i radial shell
  * (i = 1..N of x_i = cos(i pi/(N+1)), so decreasing r), a Gauss-Legendre node in cos(theta)
  * (ascending), b azimuth phi_b = (b + 1/2) 2 pi / n_phi.
@@ -464,8 +485,8 @@ double orc_becke_weight(int n_c, const double* centres, int owner, const double 
  * to time the oracle on a bounded share of a large workload).
  * Returns the number of kept points; out arrays must hold the raw count. */
 long orc_grid_cell(int n_atoms, const double* xyz, const double* lattice, int n_shell, int n_rad, double R,
-                   int n_theta, int n_phi, double r_c, double r_nb, long long stride, double* out_xyz,
-                   double* out_w, long long* out_id) {
+                   int n_theta, int n_phi, double r_c, double r_nb, int scheme, long long stride,
+                   double* out_xyz, double* out_w, long long* out_id) {
   double* rr = (double*)malloc(sizeof(double) * n_rad);
   double* wr = (double*)malloc(sizeof(double) * n_rad);
   double* ct = (double*)malloc(sizeof(double) * n_theta);
@@ -494,7 +515,7 @@ long orc_grid_cell(int n_atoms, const double* xyz, const double* lattice, int n_
           }
           if (!near) continue;
           double w = wr[i] * wt[a] * (2.0 * M_PI / n_phi) *
-                     orc_becke_weight(nc, cen, cell0 * n_atoms + A, p, r_nb);
+                     orc_partition_weight(nc, cen, cell0 * n_atoms + A, p, r_nb, scheme);
           if (w == 0.0) continue;
           out_xyz[3 * kept] = p[0]; out_xyz[3 * kept + 1] = p[1]; out_xyz[3 * kept + 2] = p[2];
           out_w[kept] = w;
@@ -511,7 +532,7 @@ long orc_grid_cell(int n_atoms, const double* xyz, const double* lattice, int n_
 /* the molecular grid (no lattice) */
 long orc_grid(int n_atoms, const double* xyz, int n_rad, double R, int n_theta, int n_phi,
               double r_c, double r_nb, long long stride, double* out_xyz, double* out_w, long long* out_id) {
-  return orc_grid_cell(n_atoms, xyz, NULL, 0, n_rad, R, n_theta, n_phi, r_c, r_nb, stride, out_xyz, out_w,
+  return orc_grid_cell(n_atoms, xyz, NULL, 0, n_rad, R, n_theta, n_phi, r_c, r_nb, 0, stride, out_xyz, out_w,
                        out_id);
 }
 

@@ -45,7 +45,10 @@ class GridDesc(C.Structure):
     _fields_ = [("n_atoms", C.c_int32), ("xyz", C.c_void_p), ("species", C.c_void_p),
                 ("n_rad_shells", C.c_int32), ("R", C.c_double), ("n_theta", C.c_int32), ("n_phi", C.c_int32),
                 ("r_nb", C.c_double), ("batch_max", C.c_int32), ("lattice", C.c_void_p), ("n_shell", C.c_int32),
-                ("n_molecules", C.c_int32), ("mol_atom_ptr", C.c_void_p)]
+                ("n_molecules", C.c_int32), ("mol_atom_ptr", C.c_void_p), ("partition", C.c_int32)]
+
+
+PARTITIONS = {"becke": 0, "stratmann": 1}
 
 
 class GridInfo(C.Structure):
@@ -159,7 +162,7 @@ class Grid:
     """q4c_grid handle (grid_partition)."""
 
     def __init__(self, tables: Tables, xyz, species, n_rad_shells, R, n_theta, n_phi, r_nb, batch_max,
-                 lattice=None, n_shell: int = 0, mol_atom_ptr=None):
+                 lattice=None, n_shell: int = 0, mol_atom_ptr=None, partition: str = "becke"):
         L = load()
         self.tables = tables
         self._xyz = np.ascontiguousarray(xyz, np.float64).reshape(-1)
@@ -169,7 +172,7 @@ class Grid:
         d = GridDesc(len(self._sp), self._xyz.ctypes.data, self._sp.ctypes.data, n_rad_shells, R, n_theta, n_phi,
                      r_nb, batch_max, None if self._lat is None else self._lat.ctypes.data, int(n_shell),
                      0 if self._mol is None else len(self._mol) - 1,
-                     None if self._mol is None else self._mol.ctypes.data)
+                     None if self._mol is None else self._mol.ctypes.data, PARTITIONS[partition])
         h = C.c_void_p()
         _check(L.grid_partition(C.byref(d), tables.h, C.byref(h)))
         self.h = h

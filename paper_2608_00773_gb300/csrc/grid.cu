@@ -65,13 +65,25 @@ __device__ __forceinline__ double becke_s(double mu) {
   return 0.5 * (1.0 - f);
 }
 
+// Stratmann, Scuseria and Frisch (1996) cell function without size
+// adjustment: s(mu) = (1 - g(mu))/2, g(x) = (35 x - 35 x^3 + 21 x^5 - 5 x^7)/16
+// of x = mu/a on |mu| <= a = 0.64, g = -1 below and +1 above
+__device__ __forceinline__ double stratmann_s(double mu) {
+  constexpr double a = 0.64;
+  if (mu <= -a) return 1.0;
+  if (mu >= a) return 0.0;
+  const double x = mu / a, x2 = x * x;
+  return 0.5 - x * (35.0 + x2 * (-35.0 + x2 * (21.0 - 5.0 * x2))) * (1.0 / 32.0);
+}
+
 // One thread per raw point: neighbour set N(r) = atoms within r_nb, then
 // p_owner = P_owner / sum_{C in N} P_C with P_A = prod_{B in N, B != A} s(mu_AB),
 // mu_AB = (|r - R_A| - |r - R_B|)/|R_A - R_B|.  near = some atom within r_c.
 __global__ void k_becke(const double* __restrict__ raw, const double* __restrict__ base_w, int64_t n_raw,
                         int pts_per_atom, int owner_base, const double* __restrict__ atom_xyz,
-                        const int2* __restrict__ cand, double r_c, double r_nb, double* __restrict__ w_out,
-                        unsigned char* __restrict__ near_out, int* __restrict__ overflow) {
+                        const int2* __restrict__ cand, double r_c, double r_nb, int scheme,
+                        double* __restrict__ w_out, unsigned char* __restrict__ near_out,
+                        int* __restrict__ overflow) {
   const int64_t p = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
   if (p >= n_raw) return;
   const int gen = static_cast<int>(p / pts_per_atom);  // generating (cell-0) atom
@@ -114,7 +126,8 @@ __global__ void k_becke(const double* __restrict__ raw, const double* __restrict
       const int B = nb_idx[b];
       const double dx = ax - atom_xyz[3 * B], dy = ay - atom_xyz[3 * B + 1], dz = az - atom_xyz[3 * B + 2];
       const double rab = sqrt(dx * dx + dy * dy + dz * dz);
-      P *= becke_s((nb_d[a] - nb_d[b]) / rab);
+      const double mu = (nb_d[a] - nb_d[b]) / rab;
+      P *= scheme == 1 ? stratmann_s(mu) : becke_s(mu);
     }
     return P;
   };
@@ -277,6 +290,7 @@ extern "C" q4c_status grid_partition(const q4c_grid_desc* d, const q4c_tables* t
   Q4C_CHECK_ARG(d->n_rad_shells >= 1 && d->n_theta >= 1 && d->n_phi >= 1 && d->R > 0 && d->r_nb > 0,
                 "grid_partition: bad grid parameters");
   Q4C_CHECK_ARG(d->batch_max >= 1 && d->batch_max <= kMaxBatch, "grid_partition: batch_max must be in 1..1024");
+  Q4C_CHECK_ARG(d->partition == 0 || d->partition == 1, "grid_partition: partition must be 0 (Becke) or 1 (Stratmann)");
   for (int a = 0; a < d->n_atoms; ++a)
     Q4C_CHECK_ARG(d->species[a] >= 0 && d->species[a] < t->n_species, "grid_partition: species out of range");
   const int nA = d->n_atoms;
@@ -417,7 +431,7 @@ extern "C" q4c_status grid_partition(const q4c_grid_desc* d, const q4c_tables* t
       const int threads = 128;
       const int64_t blocks = (n_raw + threads - 1) / threads;
       k_becke<<<static_cast<unsigned>(blocks), threads>>>(d_raw, d_base, n_raw, ppa, cell0 * nA, d_axyz, d_cand,
-                                                          r_c, d->r_nb, d_w, d_near, d_ovf);
+                                                          r_c, d->r_nb, d->partition, d_w, d_near, d_ovf);
       if ((e = cudaGetLastError())) break;
       if ((e = cudaMemcpy(wfull.data(), d_w, sizeof(double) * n_raw, cudaMemcpyDeviceToHost))) break;
       if ((e = cudaMemcpy(nearv.data(), d_near, n_raw, cudaMemcpyDeviceToHost))) break;

@@ -64,6 +64,8 @@ class Workload:
     n_shell: int = 0
     # batched independent molecules: atom ranges [n_molecules + 1]; None for one system
     mol_atom_ptr: Optional[np.ndarray] = None
+    # partition of unity: "becke" (Becke 1988) or "stratmann" (Stratmann et al. 1996)
+    partition: str = "becke"
 
     @property
     def n_atoms(self) -> int:
