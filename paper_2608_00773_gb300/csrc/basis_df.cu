@@ -149,7 +149,7 @@ __device__ __forceinline__ void harmonics_s(df x, df y, df z, int lmax, df* S) {
 }
 
 template <int NQ>
-__global__ void __launch_bounds__(256) k_basis_df(DevBasis B, DevGrid G, DfTables T, int64_t b0,
+__global__ void __launch_bounds__(256, 4) k_basis_df(DevBasis B, DevGrid G, DfTables T, int64_t b0,
                                                   const int64_t* __restrict__ scr_off, float2* __restrict__ scratch,
                                                   const double* __restrict__ v, int* __restrict__ colexp,
                                                   int* __restrict__ rowexp, float2* __restrict__ dpad) {
