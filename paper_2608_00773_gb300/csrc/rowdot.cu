@@ -212,10 +212,15 @@ struct StepIter {
 // One work item = (batch, 64-point tile); its groups (j-tile, product) run
 // in order, each a K-loop over the functions i.  Warp roles as in the
 // integration kernel:
-//   warps 0-7   per step: wait empty[stage]; one thread starts the bulk copy
-//               of the step's G' digits into the stage (expect_tx on
-//               full[stage]); all slice the 64 x 16 block of F (raw values
-//               by cp.async three steps ahead) and arrive on full[stage];
+//   warp 17     (one thread) loads each step's box of F (64 points x 16
+//               functions of the step's quantity) and, on an item's first
+//               step, the points' exponents into the raw ring (raw_full
+//               counts the bytes; raw_empty hands a stage back);
+//   warps 0-7   per step: thread (point, 4 functions) reads its raw values,
+//               waits empty[stage]; one thread starts the bulk copy of the
+//               step's G' digits into the stage (expect_tx on full[stage]);
+//               all slice their F values, store the digits, arrive on
+//               full[stage] and hand the raw stage back;
 //   warp 16     (one thread) issues the six MMAs per step into the group's
 //               accumulator set (groups alternate between two sets), commits
 //               empty[stage] and, after the group's last step, accfull[set];

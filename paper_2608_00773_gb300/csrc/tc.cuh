@@ -187,16 +187,6 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const void* map, int x
       : "memory");
 }
 
-// 16-byte asynchronous global -> shared copy; bytes past src_bytes are zero
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, int src_bytes) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
-}
-
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
@@ -240,78 +230,9 @@ __device__ __forceinline__ void tmem_ld8x3(uint32_t t0, uint32_t t1, uint32_t t2
 }
 
 // ------------------------------------------------------------ slicing
-// The split of x (FP64) against a column exponent e (|x| <= 2^e):
-//   N = round(x 2^(46 - e)),  |N| <= 2^46,
+// The split of a value x against a column exponent e (|x| <= 2^e):
 //   x = sum_s d_s 2^(e - 6 - 8 s) + O(2^(e - 47)),  s = 0..5,
-// with balanced digits |d_0| <= 64, |d_s| <= 128 (each exact in BF16).
-
-// N for x itself
-__device__ __forceinline__ long long fixed46(double x, int e) {
-  const long long bits = __double_as_longlong(x);
-  const int E = static_cast<int>((bits >> 52) & 0x7FF);
-  if (E == 0 || e < -1000) return 0;  // zero (or below the FP64 normal range)
-  const unsigned long long M = (bits & 0xFFFFFFFFFFFFFULL) | (1ULL << 52);
-  const int sh = 1075 + e - 46 - E;  // >= 6 because |x| <= 2^e
-  if (sh >= 62) return 0;
-  const long long N = static_cast<long long>(((M >> (sh - 1)) + 1) >> 1);
-  return bits < 0 ? -N : N;
-}
-
-// N for the product x D, from the 106-bit product of the two mantissas
-// (no FP64 multiply: the high 64 bits come from an integer multiply-high)
-__device__ __forceinline__ long long fixed46_scaled(double x, double D, int e) {
-  const long long bx = __double_as_longlong(x), bd = __double_as_longlong(D);
-  const int Ex = static_cast<int>((bx >> 52) & 0x7FF), Ed = static_cast<int>((bd >> 52) & 0x7FF);
-  if (Ex == 0 || Ed == 0 || e < -1000) return 0;
-  const unsigned long long Mx = (bx & 0xFFFFFFFFFFFFFULL) | (1ULL << 52);
-  const unsigned long long Md = (bd & 0xFFFFFFFFFFFFFULL) | (1ULL << 52);
-  const unsigned long long hi = __umul64hi(Mx << 11, Md << 11);  // floor(Mx Md / 2^42)
-  const int sh = 2062 + e - Ex - Ed;  // >= 17 because |x D| <= 2^e
-  if (sh >= 64) return 0;
-  const long long N = static_cast<long long>(((hi >> (sh - 1)) + 1) >> 1);
-  return (bx ^ bd) < 0 ? -N : N;
-}
-
-// round(f 2^(46 - e)) for one FP32 number with |f| < 2^e
-__device__ __forceinline__ long long fixed46_f(float f, int e) {
-  const uint32_t u = __float_as_uint(f);
-  const int E = static_cast<int>((u >> 23) & 0xFF);
-  if (E == 0 || e < -1000) return 0;
-  const uint32_t m = (u & 0x7FFFFFu) | 0x800000u;
-  const int sh = E - 104 - e;  // <= 22 because |f| < 2^e
-  long long N;
-  if (sh >= 0) N = static_cast<long long>(m) << sh;
-  else if (sh > -25) N = static_cast<long long>(((m >> (-sh - 1)) + 1u) >> 1);
-  else N = 0;
-  return (u >> 31) ? -N : N;
-}
-
-// N = round((hi + lo) 2^(46 - e)) within one unit, for a double-float value
-__device__ __forceinline__ long long fixed46_df(float hi, float lo, int e) {
-  return fixed46_f(hi, e) + fixed46_f(lo, e);
-}
-
-// six balanced base-256 digits of N (32-bit arithmetic after one split)
-__device__ __forceinline__ void digits_of(long long N, int d[kSlices]) {
-  const long long hi64 = (N + (1LL << 23)) >> 24;
-  const int lo = static_cast<int>(N - (hi64 << 24));  // [-2^23, 2^23)
-  const int h = static_cast<int>(hi64);               // [-2^22, 2^22]
-  int q = (h + (1 << 15)) >> 16;
-  int r = h - (q << 16);
-  d[0] = q;
-  q = (r + 128) >> 8;
-  d[1] = q;
-  d[2] = r - (q << 8);
-  q = (lo + (1 << 15)) >> 16;
-  r = lo - (q << 16);
-  d[3] = q;
-  q = (r + 128) >> 8;
-  d[4] = q;
-  d[5] = r - (q << 8);
-}
-
-// digits of x against exponent e (reference form used by the density/adjoint)
-__device__ __forceinline__ void digits6(double x, int e, int d[kSlices]) { digits_of(fixed46(x, e), d); }
+// with balanced digits, each exact in BF16.
 
 // Rounding constant of the leading digit for column exponent e: 1.5 2^(e + 17).
 // Adding and subtracting 1.5 2^(23 + u) in FP32 rounds x to the nearest
@@ -341,11 +262,6 @@ __device__ __forceinline__ void slice6(float h, float l, float m0, float d[kSlic
     m = __fmul_rn(m, 0x1p-8f);
   }
 }
-
-__device__ __forceinline__ float pow2f(int k) {  // 2^k as float, 0 below the normal range
-  return (k < -126) ? 0.0f : __int_as_float((k + 127) << 23);
-}
-
 
 }  // namespace tc
 }  // namespace q4c
