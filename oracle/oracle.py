@@ -88,6 +88,8 @@ def lib() -> C.CDLL:
             vp = C.c_void_p
             L.orc_adjoint.argtypes = [bp, C.c_long, _dp, _dp, _lp, _ip, _ip, _lp, vp, vp, vp, vp, vp, _dp]
             L.orc_spinor_ss.argtypes = [bp, _lp, _ip, _lp, _dp, _dp, _dp, _dp, _dp]
+            L.orc_matrix_columns.argtypes = [bp, C.c_long, _dp, _dp, _dp, _dp, _dp, _lp, _ip, _ip, _lp, _dp]
+            L.orc_matrix_columns.restype = None
             L.orc_kpattern.argtypes = [bp, _lp, _ip, C.c_void_p, C.c_void_p, C.c_void_p]
             L.orc_kpattern.restype = C.c_long
             L.orc_kfold.argtypes = [bp, _lp, _ip, _ip, _lp, _dp, C.c_int, _dp, _lp, _ip, _lp, _dp]
@@ -257,6 +259,16 @@ class OracleBasis:
         if miss:
             raise RuntimeError("active atom pair outside the block pattern")
         return outs
+
+    def matrix_columns(self, xyz, w, v, eps, knots, pat: Pattern):
+        """F_ij = sum_p w phi_i (eps_j - V_j(|p - R_j|) + v) phi_j (Eq. 19, large component,
+        per-column operator): eps [n_rad_tot], knots [n_rad_tot][n_log] values of V at the
+        radial knots; flat array on the block pattern (not symmetric)."""
+        xyz = _f64(xyz).reshape(-1); w = _f64(w); v = _f64(v)
+        out = np.zeros(pat.nnz)
+        lib().orc_matrix_columns(C.byref(self.s), len(w), xyz, w, v, _f64(eps), _f64(knots).reshape(-1),
+                                 pat.blk_ptr, pat.blk_col, pat.blk_T.reshape(-1), pat.blk_off, out)
+        return out
 
     def density(self, xyz, P, pat: Pattern):
         """n_p = sum_ij P_ij phi_i phi_j (Eqs. 39-40)."""

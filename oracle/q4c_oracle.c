@@ -124,14 +124,10 @@ double orc_cutoff(double r, double r_on, double r_c) {
  * t = k (unit spacing): M_{k-1} + 4 M_k + M_{k+1} = 6 (u_{k+1} - 2u_k + u_{k-1}),
  * M_0 = M_{n-1} = 0, solved by plain Gaussian elimination of the
  * tridiagonal system. */
-int orc_tabulate(int l, double alpha, int n, double r_min, double r_c, double r_on,
-                 double* r, double* u, double* M) {
-  if (n < 3) return -1;
-  for (int k = 0; k < n; ++k) {
-    double rk = r_min * pow(r_c / r_min, (double)k / (double)(n - 1));
-    r[k] = rk;
-    u[k] = pow(rk, l + 1) * exp(-alpha * rk * rk) * orc_cutoff(rk, r_on, r_c);
-  }
+/* Second derivatives M_k (in the knot index) of the natural cubic spline
+ * through u_0..u_{n-1}: M_0 = M_{n-1} = 0, M_{k-1} + 4 M_k + M_{k+1} =
+ * 6 (u_{k+1} - 2 u_k + u_{k-1}). */
+static void orc_natural_M(int n, const double* u, double* M) {
   int m = n - 2; /* unknowns M_1..M_{n-2} */
   double* diag = (double*)malloc(sizeof(double) * m);
   double* rhs = (double*)malloc(sizeof(double) * m);
@@ -152,6 +148,17 @@ int orc_tabulate(int l, double alpha, int n, double r_min, double r_c, double r_
   for (int i = m - 2; i >= 0; --i) M[i + 1] = (rhs[i] - M[i + 2]) / diag[i];
   free(diag);
   free(rhs);
+}
+
+int orc_tabulate(int l, double alpha, int n, double r_min, double r_c, double r_on,
+                 double* r, double* u, double* M) {
+  if (n < 3) return -1;
+  for (int k = 0; k < n; ++k) {
+    double rk = r_min * pow(r_c / r_min, (double)k / (double)(n - 1));
+    r[k] = rk;
+    u[k] = pow(rk, l + 1) * exp(-alpha * rk * rk) * orc_cutoff(rk, r_on, r_c);
+  }
+  orc_natural_M(n, u, M);
   return 0;
 }
 
@@ -771,6 +778,74 @@ int orc_matrix_blocks(const orc_basis* b, long n_pts, const double* xyz, const d
   active_free(&a);
   ftab_free(&t);
   return missing;
+}
+
+/* The per-column operator of Eq. 19 (large component, scalar form):
+ *   F_ij = sum_p w_p phi_i(p) [eps_j - V_j(|p - R_j|) + v_p] phi_j(p)
+ * with eps_j and V_j those of the radial function of column function j
+ * (eps[rad], knots[rad][n_log]: V at the log knots r_k of the radial
+ * tables; natural cubic spline in the knot index, the first knot's value
+ * below r_min, the last one's from r_c on, where phi_j vanishes anyway) and
+ * R_j the centre of j.  Not symmetric.  Output F[blk_off[nb]]. */
+void orc_matrix_columns(const orc_basis* b, long n_pts, const double* xyz, const double* w, const double* v,
+                        const double* eps, const double* knots, const long long* blk_ptr, const int* blk_col,
+                        const int* blk_T, const long long* blk_off, double* F) {
+  ftab t;
+  ftab_init(b, &t);
+  orc_active a;
+  active_init(b, &a);
+  int n_rad_tot = 0;
+  for (int s = 0; s < b->n_species; ++s) n_rad_tot += b->n_rad[s];
+  const int n = b->n_log;
+  double* M = (double*)malloc(sizeof(double) * (size_t)n_rad_tot * n);
+  for (int k = 0; k < n_rad_tot; ++k) orc_natural_M(n, knots + (size_t)k * n, M + (size_t)k * n);
+  const double h = log(b->r_c / b->r_min) / (n - 1);
+  long long nnz = blk_off[blk_ptr[b->n_atoms]];
+  orc_acc* acc = (orc_acc*)calloc((size_t)nnz, sizeof(orc_acc));
+  double* col = (double*)malloc(sizeof(double) * (size_t)a.nmax);
+  for (long p = 0; p < n_pts; ++p) {
+    const double* X = xyz + 3 * p;
+    active_at(b, &t, &a, X);
+    for (int sb = 0; sb < a.n; ++sb) {
+      int B = a.atom[sb], nfB = species_nfn(b, b->species[B]);
+      const double* cB = a.cen + 3 * a.c[sb];
+      double dx = X[0] - cB[0], dy = X[1] - cB[1], dz = X[2] - cB[2];
+      double r = sqrt(dx * dx + dy * dy + dz * dz);
+      /* the column factor w (eps_j - V_j(r) + v) phi_j of every function of centre sb */
+      for (int j = 0; j < nfB; ++j) {
+        int rad = t.fr[t.afirst[B] + j];
+        const double* u = knots + (size_t)rad * n;
+        const double* Mk = M + (size_t)rad * n;
+        double Vr;
+        if (r < b->r_min) {
+          Vr = u[0];
+        } else if (r >= b->r_c) {
+          Vr = u[n - 1];
+        } else {
+          double tt = log(r / b->r_min) / h;
+          int k = (int)floor(tt);
+          if (k > n - 2) k = n - 2;
+          if (k < 0) k = 0;
+          double s = tt - k, q = 1.0 - s;
+          Vr = q * u[k] + s * u[k + 1] + (q * q * q - q) * Mk[k] / 6.0 + (s * s * s - s) * Mk[k + 1] / 6.0;
+        }
+        col[j] = w[p] * (eps[rad] - Vr + v[p]) * a.phi[(size_t)sb * a.nmax + j];
+      }
+      for (int sa = 0; sa < a.n; ++sa) {
+        long q = pair_block(&a, sa, sb, blk_ptr, blk_col, blk_T);
+        if (q < 0) continue;
+        int nfA = species_nfn(b, b->species[a.atom[sa]]);
+        for (int i = 0; i < nfA; ++i) {
+          double pi = a.phi[(size_t)sa * a.nmax + i];
+          for (int j = 0; j < nfB; ++j) acc_add(&acc[blk_off[q] + (long long)i * nfB + j], pi * col[j]);
+        }
+      }
+    }
+  }
+  for (long long e = 0; e < nnz; ++e) F[e] = acc_get(&acc[e]);
+  free(acc); free(col); free(M);
+  active_free(&a);
+  ftab_free(&t);
 }
 
 /* Density n_p = sum_ij P_ij phi_i phi_j with P on the block pattern (Eq. 39),

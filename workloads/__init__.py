@@ -209,6 +209,33 @@ def single_atom(l_list=(0, 1, 2, 3), alphas=None, Z: float = 8.0, n_rad: int = 6
 
 
 # --------------------------------------------------------------------------
+# per-column operator inputs (eigenvalue and defining potential per radial)
+# --------------------------------------------------------------------------
+
+def column_operator(wl: Workload, seed: int = 1201):
+    """(eps [n_rad_tot], knots [n_rad_tot][n_log]): per radial function a seeded
+    eigenvalue in [-3, -0.1] Hartree and a free-atom-like potential
+    V(r) = -Z erf(a r)/r (a in [0.8, 1.5], -2 Z a / sqrt(pi) at r = 0) given at the
+    radial knots r_k = r_min (r_c/r_min)^(k/(n_log-1))."""
+    rng = np.random.default_rng(seed)
+    n_tot = int(sum(len(sp.l) for sp in wl.species))
+    eps = rng.uniform(-3.0, -0.1, n_tot)
+    a = rng.uniform(0.8, 1.5, n_tot)
+    Z = np.array([sp.Z for sp in wl.species for _ in sp.l], dtype=np.float64)
+    r = wl.r_min * (wl.r_c / wl.r_min) ** (np.arange(wl.n_log) / (wl.n_log - 1))
+    knots = np.empty((n_tot, wl.n_log))
+    for k in range(n_tot):
+        x = a[k] * r
+        knots[k] = -Z[k] * a[k] * np.where(x > 1e-8, _erf(x) / np.maximum(x, 1e-300), 2.0 / math.sqrt(math.pi))
+    return eps, knots
+
+
+def _erf(x):
+    from scipy.special import erf
+    return erf(x)
+
+
+# --------------------------------------------------------------------------
 # input potential
 # --------------------------------------------------------------------------
 
