@@ -252,6 +252,27 @@ Q4C_API q4c_status q4c_density(const q4c_tables* tables, const q4c_grid* grid, c
 Q4C_API q4c_status q4c_density_full(const q4c_tables* tables, const q4c_grid* grid, const q4c_matrices* P,
                             q4c_precision prec, double* n_dev, q4c_stream stream);
 
+/* ------------------------------------------------- per-column operator
+ * The large-component matrix of Eq. 19 in the scalar form, where every
+ * element carries the eigenvalue and defining potential of the radial
+ * function of its column function j:
+ *   F_ij = sum_p w_p phi_i(p) [eps_j - V_j(|p - R_j|) + v_p] phi_j(p)
+ * (R_j the centre of j, an atom or a periodic image).  F is not symmetric. */
+
+/* Stores eps (host [sum n_rad], species-major, Hartree) and V (host
+ * [sum n_rad][n_log]: values at the radial knots r_k = r_min (r_cut/r_min)^(k/(n_log-1)),
+ * interpolated by a natural cubic spline in the knot index; below r_min the
+ * first knot's value, from r_cut on the last one's) with the tables,
+ * replacing earlier ones.  Synchronous.  EINVAL on NULL arguments. */
+Q4C_API q4c_status q4c_tables_set_columns(q4c_tables* tables, const double* eps, const double* knots);
+
+/* F on the grid's block pattern (device [nnz], overwritten; every element
+ * of every block, no symmetry used) in FP64, v_dev device [n_points] in
+ * batch order.  EINVAL without q4c_tables_set_columns.  Stream-ordered,
+ * with one host synchronisation per wave of batches. */
+Q4C_API q4c_status q4c_integrate_columns(const q4c_tables* tables, const q4c_grid* grid, const double* v_dev,
+                                 double* F_dev, q4c_stream stream);
+
 /* ---------------------------------------------------------------- spinors
  * Scalar -> spinor transformation (Section II, Eqs. 9-14; Section III A,
  * Eqs. 33-34, 37-38; Appendix A).  Spinor basis of an atom: per radial

@@ -26,6 +26,7 @@ STATUS = {0: "Q4C_OK", 1: "Q4C_EINVAL", 2: "Q4C_ENOMEM", 3: "Q4C_ECUDA", 4: "Q4C
 EXPORTS = ["nao_tabulate", "q4c_tables_destroy", "q4c_tables_export", "grid_partition", "q4c_grid_destroy",
            "q4c_grid_get_info", "q4c_grid_export", "q4c_grid_export_shifts", "q4c_grid_kpattern", "q4c_kfold", "q4c_grid_points", "q4c_integrate", "q4c_density", "q4c_density_full",
            "q4c_spinor_basis", "q4c_spinor_transform", "q4c_spinor_density_matrices", "q4c_grid_batch_spinors",
+           "q4c_tables_set_columns", "q4c_integrate_columns",
            "q4c_integrate_backward", "q4c_integrate_noalloc", "q4c_basis_eval", "q4c_grid_status", "q4c_profile", "q4c_profile_read",
            "q4c_last_error"]
 
@@ -93,6 +94,8 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     L.q4c_integrate_backward.argtypes = [vp, vp, C.POINTER(Matrices), C.c_int, vp, vp]
     L.q4c_density_full.argtypes = [vp, vp, C.POINTER(Matrices), C.c_int, vp, vp]
     L.q4c_spinor_basis.argtypes = [vp, i32, vp, vp, vp, vp]
+    L.q4c_tables_set_columns.argtypes = [vp, vp, vp]
+    L.q4c_integrate_columns.argtypes = [vp, vp, vp, vp, vp]
     L.q4c_spinor_transform.argtypes = [vp, vp, C.POINTER(Matrices), vp, vp, vp]
     L.q4c_spinor_density_matrices.argtypes = [vp, vp, vp, C.POINTER(Matrices), vp]
     L.q4c_grid_batch_spinors.argtypes = [vp, i64, vp, vp, vp]
@@ -294,6 +297,22 @@ def q4c_density_full(tables: Tables, grid: Grid, P: Sequence, prec="fp64", out=N
         out = torch.empty(grid.n_points, dtype=torch.float64, device=dev)
     m = Matrices(*[_ptr(x) for x in P], 0)
     _check(load().q4c_density_full(tables.h, grid.h, C.byref(m), _prec(prec), _ptr(out), _stream(stream)))
+    return out
+
+
+def q4c_tables_set_columns(tables: Tables, eps, knots):
+    """eps [sum n_rad] and V at the radial knots [sum n_rad][n_log] of the per-column operator."""
+    e = np.ascontiguousarray(eps, np.float64).reshape(-1)
+    k = np.ascontiguousarray(knots, np.float64).reshape(-1)
+    _check(load().q4c_tables_set_columns(tables.h, e.ctypes.data, k.ctypes.data))
+
+
+def q4c_integrate_columns(tables: Tables, grid: Grid, v, out=None, stream=None):
+    """F_ij = sum_p w phi_i (eps_j - V_j + v) phi_j on the block pattern (FP64)."""
+    import torch
+    if out is None:
+        out = torch.empty(grid.nnz, dtype=torch.float64, device=v.device)
+    _check(load().q4c_integrate_columns(tables.h, grid.h, _ptr(v), _ptr(out), _stream(stream)))
     return out
 
 

@@ -279,6 +279,146 @@ q4c_status integrate_fp64(const q4c_tables* t, const q4c_grid* g, const double* 
   return mirror_and_spinor(g, out, s);
 }
 
+// ------------------------------------------------------ per-column operator
+// Eq. 19 in the scalar form of the large component: every element carries
+// the eigenvalue and defining potential of its COLUMN's radial function,
+//   F_ij = sum_p phi_i(p) theta_pj,  theta_pj = w_p (v_p + eps_j - V_j(|p - R_j|)) phi_j(p),
+// so F is not symmetric: one CTA per 32x32 tile over all tile pairs of a
+// batch, the column factors built while loading the j side, every element
+// scattered (no mirror).  V_j: cubic in the knot index on each interval,
+// the first knot's value below r_min and the last one's from r_c on.
+__device__ __forceinline__ double column_potential(const DevBasis& B, const double* __restrict__ vcoef, int rad,
+                                                   double r) {
+  const double* c = vcoef + static_cast<int64_t>(rad) * (B.n_log - 1) * 4;
+  if (r < B.r_min) return c[0];
+  if (r >= B.r_c) {
+    const double* e = c + (B.n_log - 2) * 4;
+    return e[0] + e[1] + e[2] + e[3];
+  }
+  const double t = log(r * B.inv_rmin) * B.inv_h;
+  const int k = min(max(static_cast<int>(t), 0), B.n_log - 2);
+  const double s = t - k;
+  const double* e = c + k * 4;
+  return e[0] + s * (e[1] + s * (e[2] + s * e[3]));
+}
+
+__global__ void __launch_bounds__(256) k_columns_fp64(DevBasis B, DevGrid G, const int4* __restrict__ tiles,
+                                                      const int64_t* __restrict__ scr_off,
+                                                      const double* __restrict__ scratch,
+                                                      const double* __restrict__ v, const double* __restrict__ eps,
+                                                      const double* __restrict__ vcoef, double* F) {
+  __shared__ double sa[kK][kT], sb[kK][kT];
+  __shared__ double s_c[3][kT], s_eps[kT];
+  __shared__ int s_rad[kT];
+  const int4 tile = tiles[blockIdx.x];
+  const int64_t b = tile.x;
+  const int ti = tile.y, tj = tile.z;
+  const int64_t p0 = G.pt_ptr[b];
+  const int np = static_cast<int>(G.pt_ptr[b + 1] - p0);
+  const int ldp = (np + 7) & ~7;
+  const int64_t f0 = G.bat_fn_ptr[b];
+  const int nb = static_cast<int>(G.bat_fn_ptr[b + 1] - f0);
+  const int a0 = G.bat_atom_ptr[b], na = G.bat_atom_ptr[b + 1] - a0;
+  const double* base = scratch + scr_off[b];
+  if (threadIdx.x < kT) {  // centre, radial and eigenvalue of each column function of the tile
+    const int fj = tj * kT + threadIdx.x;
+    int rad = -1;
+    if (fj < nb) {
+      const int info = G.fn_info[f0 + fj];
+      const int c = G.bat_atoms[a0 + (info >> 16)], k = info & 0xffff;
+      const int sp = G.c_sp[c], r0 = __ldg(B.sp_rad0 + sp), nr = __ldg(B.sp_nrad + sp);
+      for (int q = 0, first = 0; q < nr; ++q) {
+        const int n = 2 * __ldg(B.rad_l + r0 + q) + 1;
+        if (k < first + n) {
+          rad = r0 + q;
+          break;
+        }
+        first += n;
+      }
+      s_c[0][threadIdx.x] = G.c_xyz[3 * c];
+      s_c[1][threadIdx.x] = G.c_xyz[3 * c + 1];
+      s_c[2][threadIdx.x] = G.c_xyz[3 * c + 2];
+      s_eps[threadIdx.x] = rad >= 0 ? eps[rad] : 0.0;
+    }
+    s_rad[threadIdx.x] = rad;
+  }
+  __syncthreads();
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  double acc[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
+  for (int k0 = 0; k0 < np; k0 += kK) {
+    for (int e = threadIdx.x; e < kK * kT; e += blockDim.x) {
+      const int f = e / kK, kk = e - f * kK, p = k0 + kk;
+      const int fi = ti * kT + f, fj = tj * kT + f;
+      sa[kk][f] = (p < np && fi < nb) ? base[static_cast<int64_t>(fi) * ldp + p] : 0.0;
+      double th = 0.0;
+      if (p < np && fj < nb && s_rad[f] >= 0) {
+        const int64_t gp = p0 + p;
+        const double dx = G.x[gp] - s_c[0][f], dy = G.y[gp] - s_c[1][f], dz = G.z[gp] - s_c[2][f];
+        const double Vr = column_potential(B, vcoef, s_rad[f], sqrt(dx * dx + dy * dy + dz * dz));
+        th = base[static_cast<int64_t>(fj) * ldp + p] * G.w[gp] * (v[gp] + s_eps[f] - Vr);
+      }
+      sb[kk][f] = th;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < kK; ++kk) {
+      const double a0v = sa[kk][2 * ty], a1v = sa[kk][2 * ty + 1];
+      const double c0v = sb[kk][2 * tx], c1v = sb[kk][2 * tx + 1];
+      acc[0][0] = fma(a0v, c0v, acc[0][0]);
+      acc[0][1] = fma(a0v, c1v, acc[0][1]);
+      acc[1][0] = fma(a1v, c0v, acc[1][0]);
+      acc[1][1] = fma(a1v, c1v, acc[1][1]);
+    }
+    __syncthreads();
+  }
+  const int64_t pp = G.bat_pair_ptr[b];
+#pragma unroll
+  for (int u = 0; u < 2; ++u)
+#pragma unroll
+    for (int w = 0; w < 2; ++w) {
+      const int i = ti * kT + 2 * ty + u, j = tj * kT + 2 * tx + w;
+      if (i >= nb || j >= nb) continue;
+      const int ii = G.fn_info[f0 + i], jj = G.fn_info[f0 + j];
+      const int64_t off = G.pair_off[pp + static_cast<int64_t>(ii >> 16) * na + (jj >> 16)];
+      if (off < 0) continue;
+      atomicAdd(F + off + static_cast<int64_t>(ii & 0xffff) * local_nf(B, G, a0, jj >> 16) + (jj & 0xffff),
+                acc[u][w]);
+    }
+}
+
+q4c_status integrate_columns_fp64(const q4c_tables* t, const q4c_grid* g, const double* v, double* F,
+                                  cudaStream_t s) {
+  Q4C_CUDA(cudaMemsetAsync(F, 0, sizeof(double) * g->nnz, s));
+  const DevBasis B = t->view();
+  const DevGrid G = g->view();
+  for (size_t wv = 0; wv + 1 < g->wave_b0.size(); ++wv) {
+    const int64_t b0 = g->wave_b0[wv], b1 = g->wave_b0[wv + 1];
+    if (b1 <= b0) continue;
+    std::vector<int4> tiles;  // every tile pair (ti, tj) of the wave's batches
+    for (int64_t b = b0; b < b1; ++b) {
+      const int nt = static_cast<int>((g->h_bat_fn_ptr[b + 1] - g->h_bat_fn_ptr[b] + kT - 1) / kT);
+      for (int i = 0; i < nt; ++i)
+        for (int j = 0; j < nt; ++j) tiles.push_back(make_int4(static_cast<int>(b), i, j, 0));
+    }
+    if (tiles.empty()) continue;
+    if (q4c_status st = launch_basis_tiles(t, g, b0, b1, nullptr, nullptr, s)) return st;
+    int4* d_tiles = nullptr;
+    Q4C_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&d_tiles), sizeof(int4) * tiles.size(), s));
+    Q4C_CUDA(cudaMemcpyAsync(d_tiles, tiles.data(), sizeof(int4) * tiles.size(), cudaMemcpyHostToDevice, s));
+    {
+      KernelScope ks("columns_fp64", s);
+      k_columns_fp64<<<static_cast<unsigned>(tiles.size()), 256, 0, s>>>(B, G, d_tiles, g->d_scr_off, g->d_scratch,
+                                                                          v, t->d_col_eps, t->d_col_coef, F);
+    }
+    const cudaError_t e = cudaGetLastError();
+    // the host list must outlive the asynchronous copy
+    Q4C_CUDA(cudaStreamSynchronize(s));
+    Q4C_CUDA(cudaFreeAsync(d_tiles, s));
+    Q4C_CUDA(e);
+  }
+  return Q4C_OK;
+}
+
 // ------------------------------------------------------------- density
 // One CTA per batch, one thread per point; P rows gathered into shared
 // memory kRows at a time: n_p = sum_i Phi_pi sum_j P_ij Phi_pj.

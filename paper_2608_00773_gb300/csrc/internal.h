@@ -101,6 +101,10 @@ struct q4c_tables {
   int n_log = 0;
   std::vector<double> h_coef;  // host copy [n_rad_tot][n_log-1][4]
   std::vector<double> h_g0;
+  // per-column operator (q4c_tables_set_columns): eps and the spline
+  // coefficients of V per radial function, [n_rad_tot] and [n_rad_tot][n_log-1][4]
+  double* d_col_eps = nullptr;
+  double* d_col_coef = nullptr;
   // device
   double* d_coef = nullptr;
   double* d_g0 = nullptr;
@@ -209,6 +213,9 @@ q4c_status basis_eval(const q4c_tables* t, const q4c_grid* g, int64_t n_pts, con
 q4c_status mirror_and_spinor(const q4c_grid* g, const q4c_matrices* out, cudaStream_t s);
 q4c_status launch_basis_tiles(const q4c_tables* t, const q4c_grid* g, int64_t b0, int64_t b1, const double* v,
                               int* colexp, cudaStream_t s);
+// fp64.cu: the per-column operator of Eq. 19 in FP64
+q4c_status integrate_columns_fp64(const q4c_tables* t, const q4c_grid* g, const double* v, double* F,
+                                  cudaStream_t s);
 // grid.cu: dense per-batch offset tables of the batches [b0, b1) (one wave)
 q4c_status launch_fill_idx(const q4c_tables* t, const q4c_grid* g, int64_t b0, int64_t b1, cudaStream_t s);
 

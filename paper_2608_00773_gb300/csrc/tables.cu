@@ -186,10 +186,29 @@ extern "C" void q4c_tables_destroy(q4c_tables* t) {
   cudaFree(t->d_coef_df);
   cudaFree(t->d_g0_df);
   cudaFree(t->d_inv_knot_df);
+  cudaFree(t->d_col_eps);
+  cudaFree(t->d_col_coef);
   cudaFree(t->d_spn0);
   cudaFree(t->d_spn_col);
   cudaFree(t->d_spn_row);
   delete t;
+}
+
+extern "C" q4c_status q4c_tables_set_columns(q4c_tables* t, const double* eps, const double* knots) {
+  Q4C_CHECK_ARG(t && eps && knots, "q4c_tables_set_columns: NULL argument");
+  const int n_tot = static_cast<int>(t->rad_l.size()), n = t->n_log;
+  std::vector<double> coef(static_cast<size_t>(n_tot) * (n - 1) * 4), y(n);
+  for (int k = 0; k < n_tot; ++k) {
+    for (int j = 0; j < n; ++j) y[j] = knots[static_cast<size_t>(k) * n + j];
+    natural_spline_coefficients(y, &coef[static_cast<size_t>(k) * (n - 1) * 4]);
+  }
+  std::vector<double> e(eps, eps + n_tot);
+  cudaFree(t->d_col_eps);
+  cudaFree(t->d_col_coef);
+  t->d_col_eps = nullptr;
+  t->d_col_coef = nullptr;
+  if (q4c_status st = upload(&t->d_col_eps, e)) return st;
+  return upload(&t->d_col_coef, coef);
 }
 
 extern "C" q4c_status q4c_tables_export(const q4c_tables* t, int32_t radial, double* coef_host) {
