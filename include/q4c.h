@@ -86,6 +86,15 @@ typedef struct q4c_basis_desc {
  * current device.  *out receives a new handle.  EINVAL on a bad descriptor,
  * EUNSUPPORTED for l > 3, ENOMEM/ECUDA on allocation/copy failure. */
 Q4C_API q4c_status nao_tabulate(const q4c_basis_desc* desc, q4c_tables** out);
+
+/* The same tables from radial functions given by their values at the knots
+ * instead of (l, alpha): knots host [sum n_rad][n_log], u(r_k) with
+ * r_k = r_min (r_cut/r_min)^(k/(n_log-1)) (phi = u(r)/r Y_lm, so u ~ r^(l+1)
+ * at small r; below r_min u = u(r_min) (r/r_min)^(l+1)); desc->alpha may be
+ * NULL.  This is how the small-component functions phi^S = Q(r)/r Y_(l~m~)
+ * (Eq. 12b) enter: a tables handle of the Q radials with l~ = l +- 1.
+ * Errors as nao_tabulate. */
+Q4C_API q4c_status nao_tabulate_knots(const q4c_basis_desc* desc, const double* knots, q4c_tables** out);
 Q4C_API void q4c_tables_destroy(q4c_tables* tables);
 
 /* Host copy of the cubic coefficients of radial function k (species-major

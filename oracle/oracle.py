@@ -55,6 +55,7 @@ def lib() -> C.CDLL:
             L.orc_cutoff.restype = C.c_double
             L.orc_tabulate.argtypes = [C.c_int, C.c_double, C.c_int, C.c_double, C.c_double, C.c_double,
                                        _dp, _dp, _dp]
+            L.orc_spline_second.argtypes = [C.c_int, _dp, _dp]
             L.orc_spline_eval.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, _dp, _dp, C.c_double,
                                           C.POINTER(C.c_double), C.POINTER(C.c_double)]
             L.orc_K.argtypes = [C.c_int, C.c_int]
@@ -203,7 +204,9 @@ class Pattern:
 class OracleBasis:
     """Basis of a workload with radial tables built by the oracle itself."""
 
-    def __init__(self, wl, analytic: bool = False):
+    def __init__(self, wl, analytic: bool = False, knots: Optional[np.ndarray] = None):
+        """knots [n_rad_tot][n_log]: radial values u(r_k) at the knots instead of
+        r^(l+1) exp(-alpha r^2) c(r) (the small-component Q radials, Eq. 12b)."""
         self.wl = wl
         self._xyz = _f64(wl.xyz).reshape(-1)
         self._species = np.ascontiguousarray(wl.species_of_atom, dtype=np.int32)
@@ -214,7 +217,14 @@ class OracleBasis:
         self.tab_r = np.zeros((nr, wl.n_log)); self.tab_u = np.zeros((nr, wl.n_log))
         self.tab_M = np.zeros((nr, wl.n_log))
         for k in range(nr):
-            r, u, M = tabulate(int(self._l[k]), float(self._alpha[k]), wl.n_log, wl.r_min, wl.r_c, wl.r_on)
+            if knots is None:
+                r, u, M = tabulate(int(self._l[k]), float(self._alpha[k]), wl.n_log, wl.r_min, wl.r_c, wl.r_on)
+            else:
+                if analytic:
+                    raise ValueError("knot values and the analytic radial exclude each other")
+                r = wl.r_min * (wl.r_c / wl.r_min) ** (np.arange(wl.n_log) / (wl.n_log - 1))
+                u = _f64(knots[k]).copy(); M = np.zeros(wl.n_log)
+                lib().orc_spline_second(wl.n_log, u, M)
             self.tab_r[k] = r; self.tab_u[k] = u; self.tab_M[k] = M
         self._lat = None if wl.lattice is None else _f64(wl.lattice).reshape(-1)
         self.s = _Basis(wl.n_atoms, self._xyz.ctypes.data, self._species.ctypes.data, len(wl.species),

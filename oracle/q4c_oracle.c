@@ -150,6 +150,14 @@ static void orc_natural_M(int n, const double* u, double* M) {
   free(rhs);
 }
 
+/* The same second derivatives for radial values given at the knots (the
+ * small-component radials Q(r) of Eq. 12b enter this way). */
+int orc_spline_second(int n, const double* u, double* M) {
+  if (n < 3) return -1;
+  orc_natural_M(n, u, M);
+  return 0;
+}
+
 int orc_tabulate(int l, double alpha, int n, double r_min, double r_c, double r_on,
                  double* r, double* u, double* M) {
   if (n < 3) return -1;

@@ -23,7 +23,7 @@ PRECISIONS = {"fp64": Q4C_FP64, "split": Q4C_SPLIT}
 STATUS = {0: "Q4C_OK", 1: "Q4C_EINVAL", 2: "Q4C_ENOMEM", 3: "Q4C_ECUDA", 4: "Q4C_ETIMEOUT", 5: "Q4C_EUNSUPPORTED"}
 
 # every symbol include/q4c.h declares
-EXPORTS = ["nao_tabulate", "q4c_tables_destroy", "q4c_tables_export", "grid_partition", "q4c_grid_destroy",
+EXPORTS = ["nao_tabulate", "nao_tabulate_knots", "q4c_tables_destroy", "q4c_tables_export", "grid_partition", "q4c_grid_destroy",
            "q4c_grid_get_info", "q4c_grid_export", "q4c_grid_export_shifts", "q4c_grid_kpattern", "q4c_kfold", "q4c_grid_points", "q4c_integrate", "q4c_density", "q4c_density_full",
            "q4c_spinor_basis", "q4c_spinor_transform", "q4c_spinor_density_matrices", "q4c_grid_batch_spinors",
            "q4c_tables_set_columns", "q4c_integrate_columns",
@@ -77,6 +77,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     L = C.CDLL(path)
     vp, i64, i32 = C.c_void_p, C.c_int64, C.c_int32
     L.nao_tabulate.argtypes = [C.POINTER(BasisDesc), C.POINTER(vp)]
+    L.nao_tabulate_knots.argtypes = [C.POINTER(BasisDesc), vp, C.POINTER(vp)]
     L.q4c_tables_destroy.argtypes = [vp]
     L.q4c_tables_destroy.restype = None
     L.q4c_tables_export.argtypes = [vp, i32, vp]
@@ -137,16 +138,24 @@ def _stream(stream) -> int:
 class Tables:
     """q4c_tables handle (nao_tabulate)."""
 
-    def __init__(self, n_rad: Sequence[int], l: Sequence[int], alpha: Sequence[float], r_cut=6.0, r_on=5.0,
-                 r_min=1e-4, n_log=200):
+    def __init__(self, n_rad: Sequence[int], l: Sequence[int], alpha: Optional[Sequence[float]], r_cut=6.0,
+                 r_on=5.0, r_min=1e-4, n_log=200, knots: Optional[np.ndarray] = None):
+        """Radials u = r^(l+1) exp(-alpha r^2) c(r) (nao_tabulate), or, with knots
+        [sum n_rad][n_log], the given values at the knots (nao_tabulate_knots)."""
         L = load()
         self._n_rad = np.ascontiguousarray(n_rad, np.int32)
         self._l = np.ascontiguousarray(l, np.int32)
-        self._alpha = np.ascontiguousarray(alpha, np.float64)
-        d = BasisDesc(len(self._n_rad), self._n_rad.ctypes.data, self._l.ctypes.data, self._alpha.ctypes.data,
-                      r_cut, r_on, r_min, n_log)
+        self._alpha = None if alpha is None else np.ascontiguousarray(alpha, np.float64)
+        d = BasisDesc(len(self._n_rad), self._n_rad.ctypes.data, self._l.ctypes.data,
+                      None if self._alpha is None else self._alpha.ctypes.data, r_cut, r_on, r_min, n_log)
         h = C.c_void_p()
-        _check(L.nao_tabulate(C.byref(d), C.byref(h)))
+        if knots is None:
+            _check(L.nao_tabulate(C.byref(d), C.byref(h)))
+        else:
+            kn = np.ascontiguousarray(knots, np.float64)
+            if kn.shape != (len(self._l), n_log):
+                raise ValueError("knots must be [sum n_rad][n_log]")
+            _check(L.nao_tabulate_knots(C.byref(d), kn.ctypes.data, C.byref(h)))
         self.h = h
         self.n_log = n_log
 
@@ -250,6 +259,10 @@ class Grid:
 
 def nao_tabulate(n_rad, l, alpha, r_cut=6.0, r_on=5.0, r_min=1e-4, n_log=200) -> Tables:
     return Tables(n_rad, l, alpha, r_cut, r_on, r_min, n_log)
+
+
+def nao_tabulate_knots(n_rad, l, knots, r_cut=6.0, r_on=5.0, r_min=1e-4, n_log=200) -> Tables:
+    return Tables(n_rad, l, None, r_cut, r_on, r_min, n_log, knots=knots)
 
 
 def grid_partition(tables: Tables, xyz, species, n_rad_shells, R, n_theta, n_phi, r_nb, batch_max,

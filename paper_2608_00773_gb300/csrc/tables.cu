@@ -90,10 +90,13 @@ static q4c_status upload(T** dst, const std::vector<T>& src) {
   return Q4C_OK;
 }
 
-extern "C" q4c_status nao_tabulate(const q4c_basis_desc* desc, q4c_tables** out) {
+// Radial functions from (l, alpha) (knots == NULL) or from their values at
+// the knots (knots [sum n_rad][n_log], alpha unused).
+static q4c_status tabulate(const q4c_basis_desc* desc, const double* knots, q4c_tables** out) {
   Q4C_CHECK_ARG(desc && out, "nao_tabulate: NULL argument");
   *out = nullptr;
-  Q4C_CHECK_ARG(desc->n_species >= 1 && desc->n_rad && desc->l && desc->alpha, "nao_tabulate: empty basis");
+  Q4C_CHECK_ARG(desc->n_species >= 1 && desc->n_rad && desc->l && (desc->alpha || knots),
+                "nao_tabulate: empty basis");
   Q4C_CHECK_ARG(desc->n_log >= 4, "nao_tabulate: n_log must be >= 4");
   Q4C_CHECK_ARG(desc->r_min > 0 && desc->r_on > desc->r_min && desc->r_cut > desc->r_on,
                 "nao_tabulate: need 0 < r_min < r_on < r_cut");
@@ -111,8 +114,8 @@ extern "C" q4c_status nao_tabulate(const q4c_basis_desc* desc, q4c_tables** out)
     int nf = 0;
     for (int k = 0; k < desc->n_rad[s]; ++k) {
       const int l = desc->l[tot + k];
-      const double a = desc->alpha[tot + k];
-      if (l < 0 || !(a > 0.0)) {
+      const double a = knots ? 0.0 : desc->alpha[tot + k];
+      if (l < 0 || (!knots && !(a > 0.0))) {
         delete t;
         set_error("nao_tabulate: need l >= 0 and alpha > 0");
         return Q4C_EINVAL;
@@ -144,7 +147,8 @@ extern "C" q4c_status nao_tabulate(const q4c_basis_desc* desc, q4c_tables** out)
       const double r = desc->r_min * std::exp(j * t->h);
       // the last knot is r_c itself, where the cutoff vanishes
       const double rr = (j == n - 1) ? desc->r_cut : r;
-      y[j] = std::pow(rr, l + 1) * std::exp(-t->alpha[k] * rr * rr) * smooth_cut(rr, desc->r_on, desc->r_cut);
+      y[j] = knots ? knots[static_cast<size_t>(k) * n + j]
+                   : std::pow(rr, l + 1) * std::exp(-t->alpha[k] * rr * rr) * smooth_cut(rr, desc->r_on, desc->r_cut);
     }
     natural_spline_coefficients(y, &t->h_coef[static_cast<size_t>(k) * (n - 1) * 4]);
     t->h_g0[k] = y[0] / std::pow(desc->r_min, l + 1);
@@ -173,6 +177,15 @@ extern "C" q4c_status nao_tabulate(const q4c_basis_desc* desc, q4c_tables** out)
   }
   *out = t;
   return Q4C_OK;
+}
+
+extern "C" q4c_status nao_tabulate(const q4c_basis_desc* desc, q4c_tables** out) {
+  return tabulate(desc, nullptr, out);
+}
+
+extern "C" q4c_status nao_tabulate_knots(const q4c_basis_desc* desc, const double* knots, q4c_tables** out) {
+  Q4C_CHECK_ARG(knots, "nao_tabulate_knots: NULL knots");
+  return tabulate(desc, knots, out);
 }
 
 extern "C" void q4c_tables_destroy(q4c_tables* t) {

@@ -21,10 +21,10 @@ def rel_fro(a, b) -> float:
 class LibCase:
     """Library side: tables, grid, v on the library's points."""
 
-    def __init__(self, wl):
+    def __init__(self, wl, knots=None):
         import torch
         self.wl = wl
-        self.tables, self.grid = q.setup(wl)
+        self.tables, self.grid = q.setup(wl, knots)
         self.ex = self.grid.export()
         self.v_host = potential(self.ex["xyz"], wl)
         self.v = torch.tensor(self.v_host, device="cuda")
@@ -46,10 +46,10 @@ class LibCase:
 class OracleCase:
     """Oracle side: its own grid, pattern and v."""
 
-    def __init__(self, wl):
+    def __init__(self, wl, knots=None):
         self.wl = wl
         self.xyz, self.w, self.ids = O.grid(wl)
-        self.ob = O.OracleBasis(wl)
+        self.ob = O.OracleBasis(wl, knots=knots)
         self.pat = self.ob.pattern()
         self.v = potential(self.xyz, wl)
 

@@ -230,9 +230,59 @@ def column_operator(wl: Workload, seed: int = 1201):
     return eps, knots
 
 
-def _erf(x):
-    from scipy.special import erf
-    return erf(x)
+# --------------------------------------------------------------------------
+# small-component radial functions (synthetic stand-ins for the free-atom Dirac
+# solutions, which are inputs of the integration)
+# --------------------------------------------------------------------------
+
+C_LIGHT = 137.035999084  # speed of light in Hartree atomic units
+
+
+def _taper(r, r_on, r_c):
+    """(c(r), c'(r)) of the quintic taper 1 - (10 s^3 - 15 s^4 + 6 s^5),
+    s = (r - r_on)/(r_c - r_on), that the large-component radials carry."""
+    s = np.clip((r - r_on) / (r_c - r_on), 0.0, 1.0)
+    c = 1.0 - s ** 3 * (10.0 - 15.0 * s + 6.0 * s * s)
+    dc = -30.0 * s * s * (1.0 - s) ** 2 / (r_c - r_on)
+    return c, dc
+
+
+def small_radial(r, l: int, alpha: float, kappa: int, V, r_on: float, r_c: float, c: float = C_LIGHT):
+    """Q(r) = c / (2c^2 - V) (P' + kappa P/r) for P(r) = r^(l+1) exp(-alpha r^2) c(r)
+    at radii r > 0 (V: the potential at r, or a constant)."""
+    r = np.asarray(r, dtype=np.float64)
+    cut, dcut = _taper(r, r_on, r_c)
+    e = np.exp(-alpha * r * r)
+    P = r ** (l + 1) * e * cut
+    dP = ((l + 1) * r ** l - 2.0 * alpha * r ** (l + 2)) * e * cut + r ** (l + 1) * e * dcut
+    return c / (2.0 * c * c - V) * (dP + kappa * P / r)
+
+
+def small_component(wl: Workload, knots_V: np.ndarray, c: float = C_LIGHT):
+    """The small-component basis of a workload: per large-component radial
+    P(r) = r^(l+1) exp(-alpha r^2) c(r) and each kappa of its shell
+    (kappa = -l-1, small-component l~ = l+1; kappa = l for l >= 1, l~ = l-1),
+    Q(r) = c / (2c^2 - V(r)) (P'(r) + kappa P(r)/r) (the atomic-ZORA balance of
+    Eq. 8b; V the radial's potential, given at the knots).  Returns
+    (workload with the l~ per radial, Q at the knots [n_rad_S][n_log], index of
+    the parent large-component radial [n_rad_S], kappa [n_rad_S])."""
+    r = wl.r_min * (wl.r_c / wl.r_min) ** (np.arange(wl.n_log) / (wl.n_log - 1))
+    r[-1] = wl.r_c
+    species, Q, parent, kappas = [], [], [], []
+    k = 0
+    for sp in wl.species:
+        l_s, a_s = [], []
+        for l, alpha in zip(sp.l, sp.alpha):
+            for kappa in ([-l - 1, l] if l >= 1 else [-1]):
+                Q.append(small_radial(r, l, alpha, kappa, knots_V[k], wl.r_on, wl.r_c, c))
+                l_s.append(l + 1 if kappa < 0 else l - 1)
+                a_s.append(alpha)
+                parent.append(k)
+                kappas.append(kappa)
+            k += 1
+        species.append(Species(sp.name + "~", sp.Z, l_s, a_s))
+    wl_s = dataclasses.replace(wl, name=wl.name + "-small", species=species)
+    return wl_s, np.array(Q), np.array(parent, dtype=np.int64), np.array(kappas, dtype=np.int64)
 
 
 # --------------------------------------------------------------------------
