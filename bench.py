@@ -272,6 +272,8 @@ def main():
     ap.add_argument("--steps", type=int, default=60)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--prec", default="split", choices=["split", "fp64"])
+    ap.add_argument("--fp64-steps", type=int, default=3,
+                    help="FP64-path steps timed after the split run for the speedup (0: skip)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="cluster64", choices=["cluster64", "water"])
     ap.add_argument("--cpu-stride", type=int, default=4)
@@ -433,13 +435,36 @@ def main():
 
     # ---- FP64 comparison path and split error (reported beside the value)
     extra = {}
-    if prec == "split":
+    if prec == "split" and args.fp64_steps > 0:
         ref = [torch.empty_like(m) for m in mats[:5]]
         q.q4c_integrate(tables, grid, v, "fp64", out=ref + [None], stream=stream)
         q.q4c_integrate(tables, grid, v, "split", out=mats, stream=stream)
         torch.cuda.synchronize()
         extra["split_rel_err_vs_fp64"] = {n: float(torch.linalg.norm(a - b) / torch.linalg.norm(b))
                                           for n, a, b in zip(["V", "W0", "SOx", "SOy", "SOz"], mats[:5], ref)}
+        # the same step on the FP64 path (device time, L2 flushed), for the split/FP64 speedup
+        fp64_phase = {"integrate": "fp64", "density": "fp64", "backward": "fp64"}
+
+        def step64():
+            q.q4c_integrate(tables, grid, v, "fp64", out=mats, stream=stream)
+            q.q4c_density(tables, grid, P, "fp64", out=n_out, stream=stream)
+            q.q4c_integrate_backward(tables, grid, G, "fp64", out=g_out, stream=stream)
+        step64()
+        ev64 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                for _ in range(args.fp64_steps)]
+        for a_, b_ in ev64:
+            flush.zero_()
+            a_.record(stream)
+            step64()
+            b_.record(stream)
+        torch.cuda.synchronize()
+        t64 = max_over_ranks(statistics.mean(a_.elapsed_time(b_) for a_, b_ in ev64), world)
+        p64 = fp64_peak_tflops(peaks.get("sm_max_mhz", 2070.0))
+        extra["fp64_path"] = {"ms_per_step": t64, "tflops": world * F_step / (t64 * 1e-3) / 1e12,
+                              "peak": p64, "peak_source": "derived: 152 SM x 2 DFMA/clk x sm_max_mhz",
+                              "frac": world * F_step / (t64 * 1e-3) / 1e12 / p64,
+                              "speedup_split_vs_fp64": t64 / t_ms, "steps": args.fp64_steps,
+                              "phase_precision": fp64_phase}
 
     if rank != 0:
         return

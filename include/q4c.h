@@ -293,10 +293,33 @@ Q4C_API q4c_status q4c_integrate_columns(const q4c_tables* tables, const q4c_gri
  * Y~_l^m (Condon-Shortley phase) written in the real harmonics of
  * Appendix B.  Spinor blocks are complex128 (re, im), block q of the pattern
  * a row-major (2 nf_A) x (2 nf_B) matrix at 4*blk_off[q] (the layout of
- * q4c_matrices.spinor_SS, rows spinor functions of atom A). */
+ * q4c_matrices.spinor_SS, rows spinor functions of atom A).
+ *
+ * With a kappa selection (q4c_tables_set_kappa) a radial function carries the
+ * spinor functions of one kappa only (2|kappa| of them); the spinor blocks are
+ * then n_spinor(A) x n_spinor(B) matrices laid out consecutively in pattern
+ * order (q4c_spinor_nnz gives the total), and the row view of G keeps the
+ * scalar-spin index 2t + s of these tables.  Small-component tables (radials
+ * Q, Eq. 12b; nao_tabulate_knots) with kappa~ = -kappa of each parent,
+ * ordered per parent as kappa = l then kappa = -l - 1, have exactly the
+ * spinor functions of the large-component tables in the same order (the
+ * small component of spinor (kappa, m_j) is i Q/r Upsilon_(-kappa, m_j),
+ * Eq. 11), so their blocks share the large component's layout. */
+
+/* Per radial function (host [sum n_rad], species-major) the kappa whose
+ * spinors it carries: 0 for both (the default), -l-1 (j = l + 1/2) or, for
+ * l > 0, l (j = l - 1/2); kappa = NULL (or all zeros) restores the default.
+ * Rebuilds the tables' spinor relation tables; synchronous.  Grids keep
+ * working with the new selection.  EINVAL on a kappa that does not belong to
+ * its radial function's l. */
+Q4C_API q4c_status q4c_tables_set_kappa(q4c_tables* tables, const int32_t* kappa);
+
+/* Number of complex spinor elements of the grid's pattern under the tables'
+ * spinor basis (4 nnz without a kappa selection).  Synchronous. */
+Q4C_API q4c_status q4c_spinor_nnz(const q4c_tables* tables, const q4c_grid* grid, int64_t* n);
 
 /* Quantum numbers of the spinor functions of one species: *n = 2 x its
- * scalar function count; radial[i] (index of the radial function within the
+ * scalar function count (without a kappa selection); radial[i] (index of the radial function within the
  * species), kappa[i], two_mj[i] = 2 m_j, host arrays of *n entries, any may
  * be NULL.  Synchronous, no device work. */
 Q4C_API q4c_status q4c_spinor_basis(const q4c_tables* tables, int32_t species, int32_t* n, int32_t* radial,
@@ -307,21 +330,29 @@ Q4C_API q4c_status q4c_spinor_basis(const q4c_tables* tables, int32_t species, i
  *   HS = G_A^dagger (W0 1 + i SO.sigma) G_B   (kinetic-balance small component,
  *                                              from F->W0, F->SOx..SOz; NULL
  *                                              slots count as zero)
- * F: real device arrays [nnz] on the grid's pattern (q4c_integrate's output);
- * HL_dev, HS_dev: device double [8*nnz] (complex128 [4*nnz]) or NULL to skip,
- * overwritten.  EINVAL if HL is asked without F->V or HS without any of the
+ * F: real device arrays [nnz] on the grid's pattern (q4c_integrate's output,
+ * or any real matrix on the pattern, symmetric or not: F->V may be
+ * q4c_integrate_columns' F); HL_dev, HS_dev: device double [2 x spinor nnz]
+ * (complex128 [4*nnz] without a kappa selection) or NULL to skip,
+ * overwritten.  For small-component tables (kappa selection above) HL with
+ * F->V = their scalar matrix is the SS spinor block of Eq. 19, e.g.
+ * G^S^dagger (F^S x 1) G^S; adding it to the large component's HL gives H+
+ * (and with overlap matrices S+).  EINVAL if HL is asked without F->V or HS without any of the
  * small-component slots.  Stream-ordered. */
 Q4C_API q4c_status q4c_spinor_transform(const q4c_tables* tables, const q4c_grid* grid, const q4c_matrices* F,
                                 double* HL_dev, double* HS_dev, q4c_stream stream);
 
 /* Eqs. 37-38, the reverse map of a spinor density matrix D (device double
- * [8*nnz], complex128 blocks as above, normally Hermitian: block (B, A, -T)
+ * [2 x spinor nnz], complex128 blocks as above, normally Hermitian: block (B, A, -T)
  * = block (A, B, T)^dagger) to the scalar density matrices of the large and
  * small components:
  *   D'_ab = sum_mu,nu conj(G_a,mu) D_mu,nu G_b,nu,
  *   P->V = P->W0 = Re tr_s D'_ij,  P->SOk = Re(i sum_ss' (sigma_k)_ss' D'_(is)(js'))
  * so that q4c_density(P->V) gives the large-component density and
- * q4c_density_full with (NULL, P->W0, P->SOx, P->SOy, P->SOz) the small one.
+ * q4c_density_full with (NULL, P->W0, P->SOx, P->SOy, P->SOz) the small one
+ * (kinetic-balance reading).  With small-component tables (kappa selection)
+ * P->V is the scalar density matrix of the Q functions, and q4c_density on
+ * those tables gives the small-component density of Eq. 21.
  * P slots: device [nnz], overwritten; NULL slots are skipped.  Stream-ordered. */
 Q4C_API q4c_status q4c_spinor_density_matrices(const q4c_tables* tables, const q4c_grid* grid, const double* D_dev,
                                        const q4c_matrices* P, q4c_stream stream);
@@ -329,7 +360,7 @@ Q4C_API q4c_status q4c_spinor_density_matrices(const q4c_tables* tables, const q
 /* Algorithm 1 for one batch: the spinor functions present on the batch's
  * local scalar functions (those of its active centres), in ascending global
  * order (centre, then spinor index within the centre's atom).  *n gets the
- * count (twice the batch's n_b); centre[] and spinor[] (host, *n entries,
+ * count (twice the batch's n_b without a kappa selection); centre[] and spinor[] (host, *n entries,
  * either may be NULL) the pairs.  Synchronous, no device work. */
 Q4C_API q4c_status q4c_grid_batch_spinors(const q4c_grid* grid, int64_t batch, int32_t* n, int32_t* centre,
                                   int32_t* spinor);

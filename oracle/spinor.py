@@ -29,11 +29,15 @@ What it follows:
   matrices P^V = P^W0 = Re tr_s D'_ij and P^SOk = Re(i sum_ss' (sigma_k)_ss' D'_(is)(js')).
 * Algorithm 1: the local-to-global spinor index map of a set of local scalar
   functions.
+* Eqs. 11-12b, 14: the small component of spinor (kappa, m_j) is
+  i Q(r)/r Upsilon_(-kappa, m_j); a basis of Q radials carries, per radial,
+  the spinors of one kappa~ = -kappa (`kappas` below), so its G is G^S of
+  Eq. 14 and G^S^dagger (F^S x 1) G^S is the SS block of Eq. 19.
 """
 from __future__ import annotations
 
 import math
-from typing import Dict, List, Sequence, Tuple
+from typing import Dict, List, Optional, Sequence, Tuple
 
 import numpy as np
 
@@ -89,30 +93,36 @@ def complex_harmonic_in_real(l: int, m: int, phase: str = "cs") -> Dict[int, com
     return {a: 1 / SQ2, -a: -1j / SQ2}
 
 
-def spinor_functions(l_list: Sequence[int]) -> List[Tuple[int, int, int, int, int]]:
+def spinor_functions(l_list: Sequence[int], kappas: Optional[Sequence[int]] = None
+                     ) -> List[Tuple[int, int, int, int, int]]:
     """(radial q, l, 2j, 2m_j, kappa) of one atom's spinor functions: per radial
     function in order, j = l - 1/2 (kappa = l, only for l > 0) then j = l + 1/2
-    (kappa = -l - 1), m_j ascending (Eqs. 9-11)."""
+    (kappa = -l - 1), m_j ascending (Eqs. 9-11).  kappas[q] != 0 keeps only
+    that kappa of radial q (its j = |kappa| - 1/2)."""
     out = []
     for q, l in enumerate(l_list):
         for jx2 in ((2 * l - 1, 2 * l + 1) if l > 0 else (1,)):
             kappa = l if jx2 == 2 * l - 1 else -l - 1
+            if kappas is not None and kappas[q] != 0 and kappas[q] != kappa:
+                continue
             for mjx2 in range(-jx2, jx2 + 1, 2):
                 out.append((q, l, jx2, mjx2, kappa))
     return out
 
 
-def transformation_matrix(l_list: Sequence[int], phase: str = "cs") -> np.ndarray:
-    """G of one atom (Eq. 14): (2 n_fn, 2 n_fn) complex, rows 2t + s (scalar
+def transformation_matrix(l_list: Sequence[int], phase: str = "cs",
+                          kappas: Optional[Sequence[int]] = None) -> np.ndarray:
+    """G of one atom (Eq. 14): (2 n_fn, n_spinor) complex, rows 2t + s (scalar
     function t in radial-then-m order, spin s = 0 up, 1 down), columns the
-    spinor functions of `spinor_functions`."""
+    spinor functions of `spinor_functions` (n_spinor = 2 n_fn without kappas)."""
     first, t0 = [], 0
     for l in l_list:
         first.append(t0)
         t0 += 2 * l + 1
     n = t0
-    G = np.zeros((2 * n, 2 * n), complex)
-    for mu, (q, l, jx2, mjx2, _) in enumerate(spinor_functions(l_list)):
+    fns = spinor_functions(l_list, kappas)
+    G = np.zeros((2 * n, len(fns)), complex)
+    for mu, (q, l, jx2, mjx2, _) in enumerate(fns):
         for s, msx2 in ((0, 1), (1, -1)):
             mlx2 = mjx2 - msx2  # m_l = m_j - m_s
             if abs(mlx2) > 2 * l:
@@ -124,9 +134,14 @@ def transformation_matrix(l_list: Sequence[int], phase: str = "cs") -> np.ndarra
     return G
 
 
-def atom_matrices(wl, phase: str = "cs") -> List[np.ndarray]:
-    """G of each atom of a workload."""
-    per_species = [transformation_matrix(sp.l, phase) for sp in wl.species]
+def atom_matrices(wl, phase: str = "cs", kappas: Optional[Sequence[int]] = None) -> List[np.ndarray]:
+    """G of each atom of a workload; kappas: per radial function, species-major
+    (the selection of `spinor_functions`)."""
+    per_species, r0 = [], 0
+    for sp in wl.species:
+        ks = None if kappas is None else list(kappas[r0:r0 + len(sp.l)])
+        per_species.append(transformation_matrix(sp.l, phase, ks))
+        r0 += len(sp.l)
     return [per_species[s] for s in wl.species_of_atom]
 
 

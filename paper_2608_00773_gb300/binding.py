@@ -26,7 +26,7 @@ STATUS = {0: "Q4C_OK", 1: "Q4C_EINVAL", 2: "Q4C_ENOMEM", 3: "Q4C_ECUDA", 4: "Q4C
 EXPORTS = ["nao_tabulate", "nao_tabulate_knots", "q4c_tables_destroy", "q4c_tables_export", "grid_partition", "q4c_grid_destroy",
            "q4c_grid_get_info", "q4c_grid_export", "q4c_grid_export_shifts", "q4c_grid_kpattern", "q4c_kfold", "q4c_grid_points", "q4c_integrate", "q4c_density", "q4c_density_full",
            "q4c_spinor_basis", "q4c_spinor_transform", "q4c_spinor_density_matrices", "q4c_grid_batch_spinors",
-           "q4c_tables_set_columns", "q4c_integrate_columns",
+           "q4c_tables_set_columns", "q4c_integrate_columns", "q4c_tables_set_kappa", "q4c_spinor_nnz",
            "q4c_integrate_backward", "q4c_integrate_noalloc", "q4c_basis_eval", "q4c_grid_status", "q4c_profile", "q4c_profile_read",
            "q4c_last_error"]
 
@@ -78,6 +78,8 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     vp, i64, i32 = C.c_void_p, C.c_int64, C.c_int32
     L.nao_tabulate.argtypes = [C.POINTER(BasisDesc), C.POINTER(vp)]
     L.nao_tabulate_knots.argtypes = [C.POINTER(BasisDesc), vp, C.POINTER(vp)]
+    L.q4c_tables_set_kappa.argtypes = [vp, vp]
+    L.q4c_spinor_nnz.argtypes = [vp, vp, C.POINTER(i64)]
     L.q4c_tables_destroy.argtypes = [vp]
     L.q4c_tables_destroy.restype = None
     L.q4c_tables_export.argtypes = [vp, i32, vp]
@@ -338,13 +340,27 @@ def q4c_spinor_basis(tables: Tables, species: int):
     return rad, kap, mj
 
 
+def q4c_tables_set_kappa(tables: Tables, kappa=None):
+    """Per radial function the kappa whose spinors it carries (0: both; None: default)."""
+    k = None if kappa is None else np.ascontiguousarray(kappa, np.int32)
+    _check(load().q4c_tables_set_kappa(tables.h, None if k is None else k.ctypes.data))
+
+
+def q4c_spinor_nnz(tables: Tables, grid: Grid) -> int:
+    """Complex spinor elements of the grid's pattern (4 nnz without a kappa selection)."""
+    n = C.c_int64()
+    _check(load().q4c_spinor_nnz(tables.h, grid.h, C.byref(n)))
+    return n.value
+
+
 def q4c_spinor_transform(tables: Tables, grid: Grid, F: Sequence, large=True, small=True, stream=None):
-    """(HL, HS): complex128 [4 nnz] spinor blocks G^dagger (V x 1) G and
+    """(HL, HS): complex128 [spinor nnz] spinor blocks G^dagger (V x 1) G and
     G^dagger (W0 1 + i SO.sigma) G of F = [V, W0, SOx, SOy, SOz] (None = 0)."""
     import torch
     dev = next(x for x in F if x is not None).device
-    HL = torch.empty(4 * grid.nnz, dtype=torch.complex128, device=dev) if large else None
-    HS = torch.empty(4 * grid.nnz, dtype=torch.complex128, device=dev) if small else None
+    ns = q4c_spinor_nnz(tables, grid)
+    HL = torch.empty(ns, dtype=torch.complex128, device=dev) if large else None
+    HS = torch.empty(ns, dtype=torch.complex128, device=dev) if small else None
     m = Matrices(*[_ptr(x) for x in F], 0)
     _check(load().q4c_spinor_transform(tables.h, grid.h, C.byref(m), _ptr(HL), _ptr(HS), _stream(stream)))
     return HL, HS

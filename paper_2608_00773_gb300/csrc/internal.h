@@ -118,6 +118,13 @@ struct q4c_tables {
   // spinor index (twice the first scalar function), and per spinor function
   // its radial index, kappa and 2 m_j; device column and row views of G
   std::vector<int> h_spn0, h_spn_radial, h_spn_kappa, h_spn_two_mj;
+  // per radial function the one kappa whose spinors it carries, 0 for both
+  // (q4c_tables_set_kappa; empty: both for every radial); with a selection
+  // the spinor counts differ from twice the scalar counts, so the row view
+  // is indexed by the scalar-spin offsets h_ss0 and spinor blocks are laid
+  // out by their own offsets
+  std::vector<int> h_kappa_sel, h_ss0;
+  int* d_ss0 = nullptr;
   int* d_spn0 = nullptr;
   void* d_spn_col = nullptr;
   void* d_spn_row = nullptr;

@@ -22,6 +22,16 @@
 // Reverse (Eqs. 37-38): D'_ab = sum_mu,nu conj(G_a,mu) D_mu,nu G_b,nu and
 //   P^V = P^W0 = Re tr_s D'_ij,  P^SOk = Re(i sum_ss' (sigma_k)_ss' D'_(is)(js')),
 // the inputs of q4c_density_full.
+//
+// Kappa selection (q4c_tables_set_kappa): a radial function may carry the
+// spinors of one kappa only, j = |kappa| - 1/2 with the coupling of the
+// spin-angular function of that kappa.  Tables of the small-component radials
+// Q (Eq. 12b) select kappa~ = -kappa of their large-component parent: the
+// small component of spinor (kappa, m_j) is i Q/r Upsilon_(-kappa, m_j)
+// (Eq. 11), so G of these tables is G^S of Eq. 14, its spinor functions line
+// up one to one with those of the large-component tables when the radials
+// come per parent in the order kappa = l, kappa = -l - 1, and
+// G^S^dagger (F^S x 1) G^S is the SS block of Eq. 19.
 #include <cmath>
 
 #include "internal.h"
@@ -40,21 +50,26 @@ __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
 }
 
 // One CTA per pattern block; thread per spinor element (mu, nu).
+// Spinor block q starts at spin_off[q] (complex elements), or at 4 blk_off[q]
+// when spin_off is NULL (no kappa selection: twice the scalar counts).
 __global__ void k_forward(const int* __restrict__ blk_row, const int* __restrict__ blk_col,
-                          const int64_t* __restrict__ blk_off, const int* __restrict__ atom_sp,
-                          const int* __restrict__ sp_nfn, const int* __restrict__ spn0,
-                          const Ent* __restrict__ col, const double* __restrict__ V, const double* __restrict__ W0,
-                          const double* __restrict__ SOx, const double* __restrict__ SOy,
-                          const double* __restrict__ SOz, double2* __restrict__ HL, double2* __restrict__ HS) {
+                          const int64_t* __restrict__ blk_off, const int64_t* __restrict__ spin_off,
+                          const int* __restrict__ atom_sp, const int* __restrict__ sp_nfn,
+                          const int* __restrict__ spn0, const Ent* __restrict__ col, const double* __restrict__ V,
+                          const double* __restrict__ W0, const double* __restrict__ SOx,
+                          const double* __restrict__ SOy, const double* __restrict__ SOz, double2* __restrict__ HL,
+                          double2* __restrict__ HS) {
   const int q = blockIdx.x;
   const int A = blk_row[q], B = blk_col[q];
   const int sa = atom_sp[A], sb = atom_sp[B];
-  const int nfA = sp_nfn[sa], nfB = sp_nfn[sb], n2A = 2 * nfA, n2B = 2 * nfB;
+  const int nfB = sp_nfn[sb];
+  const int nsA = spn0[sa + 1] - spn0[sa], nsB = spn0[sb + 1] - spn0[sb];
   const int64_t off = blk_off[q];
+  const int64_t so = spin_off ? spin_off[q] : 4 * off;
   const Ent* cA = col + 4 * spn0[sa];
   const Ent* cB = col + 4 * spn0[sb];
-  for (int e = threadIdx.x; e < n2A * n2B; e += blockDim.x) {
-    const int mu = e / n2B, nu = e - mu * n2B;
+  for (int e = threadIdx.x; e < nsA * nsB; e += blockDim.x) {
+    const int mu = e / nsB, nu = e - mu * nsB;
     double2 hl = make_double2(0.0, 0.0), hs = make_double2(0.0, 0.0);
 #pragma unroll
     for (int ea = 0; ea < 4; ++ea) {
@@ -88,7 +103,7 @@ __global__ void k_forward(const int* __restrict__ blk_row, const int* __restrict
         }
       }
     }
-    const int64_t o = 4 * off + e;
+    const int64_t o = so + e;
     if (HL) HL[o] = hl;
     if (HS) HS[o] = hs;
   }
@@ -96,19 +111,20 @@ __global__ void k_forward(const int* __restrict__ blk_row, const int* __restrict
 
 // One CTA per pattern block; thread per scalar element (t, u).
 __global__ void k_reverse(const int* __restrict__ blk_row, const int* __restrict__ blk_col,
-                          const int64_t* __restrict__ blk_off, const int* __restrict__ atom_sp,
-                          const int* __restrict__ sp_nfn, const int* __restrict__ spn0,
-                          const Ent* __restrict__ row, const double2* __restrict__ D, double* __restrict__ PV,
-                          double* __restrict__ PW0, double* __restrict__ PSOx, double* __restrict__ PSOy,
-                          double* __restrict__ PSOz) {
+                          const int64_t* __restrict__ blk_off, const int64_t* __restrict__ spin_off,
+                          const int* __restrict__ atom_sp, const int* __restrict__ sp_nfn,
+                          const int* __restrict__ spn0, const int* __restrict__ ss0, const Ent* __restrict__ row,
+                          const double2* __restrict__ D, double* __restrict__ PV, double* __restrict__ PW0,
+                          double* __restrict__ PSOx, double* __restrict__ PSOy, double* __restrict__ PSOz) {
   const int q = blockIdx.x;
   const int A = blk_row[q], B = blk_col[q];
   const int sa = atom_sp[A], sb = atom_sp[B];
-  const int nfA = sp_nfn[sa], nfB = sp_nfn[sb], n2B = 2 * nfB;
+  const int nfA = sp_nfn[sa], nfB = sp_nfn[sb];
+  const int nsB = spn0[sb + 1] - spn0[sb];
   const int64_t off = blk_off[q];
-  const double2* Dq = D + 4 * off;
-  const Ent* rA = row + 4 * spn0[sa];
-  const Ent* rB = row + 4 * spn0[sb];
+  const double2* Dq = D + (spin_off ? spin_off[q] : 4 * off);
+  const Ent* rA = row + 4 * ss0[sa];
+  const Ent* rB = row + 4 * ss0[sb];
   for (int e = threadIdx.x; e < nfA * nfB; e += blockDim.x) {
     const int t = e / nfB, u = e - t * nfB;
     double2 Dp[2][2];
@@ -126,7 +142,7 @@ __global__ void k_reverse(const int* __restrict__ blk_row, const int* __restrict
             const Ent b = rB[4 * (2 * u + s2) + eb];
             if (b.idx < 0) continue;
             const double2 g = cmul(make_double2(a.re, -a.im), make_double2(b.re, b.im));
-            const double2 d = cmul(g, Dq[static_cast<int64_t>(a.idx) * n2B + b.idx]);
+            const double2 d = cmul(g, Dq[static_cast<int64_t>(a.idx) * nsB + b.idx]);
             acc.x += d.x;
             acc.y += d.y;
           }
@@ -150,11 +166,21 @@ __global__ void k_reverse(const int* __restrict__ blk_row, const int* __restrict
 q4c_status build_spinor_tables(q4c_tables* t) {
   using spinor::Ent;
   const int ns = t->n_species;
-  std::vector<int> spn0(ns + 1, 0);
-  for (int s = 0; s < ns; ++s) spn0[s + 1] = spn0[s] + 2 * t->nfn[s];
-  const int total = spn0[ns];
+  const bool sel = !t->h_kappa_sel.empty();
+  auto kappa_sel = [&](int s, int k) { return sel ? t->h_kappa_sel[t->rad0[s] + k] : 0; };
+  std::vector<int> spn0(ns + 1, 0), ss0(ns + 1, 0);
+  for (int s = 0; s < ns; ++s) {
+    ss0[s + 1] = ss0[s] + 2 * t->nfn[s];
+    int n = 0;
+    for (int k = 0; k < t->n_rad[s]; ++k) {
+      const int l = t->rad_l[t->rad0[s] + k], kp = kappa_sel(s, k);
+      n += kp ? 2 * std::abs(kp) : 2 * (2 * l + 1);
+    }
+    spn0[s + 1] = spn0[s] + n;
+  }
+  const int total = spn0[ns], total_ss = ss0[ns];
   std::vector<Ent> col(4 * static_cast<size_t>(total), Ent{-1, 0, 0.0, 0.0});
-  std::vector<Ent> row(4 * static_cast<size_t>(total), Ent{-1, 0, 0.0, 0.0});
+  std::vector<Ent> row(4 * static_cast<size_t>(total_ss), Ent{-1, 0, 0.0, 0.0});
   t->h_spn_radial.assign(total, 0);
   t->h_spn_kappa.assign(total, 0);
   t->h_spn_two_mj.assign(total, 0);
@@ -162,10 +188,11 @@ q4c_status build_spinor_tables(q4c_tables* t) {
   for (int s = 0; s < ns; ++s) {
     int t0 = 0, mu = 0;  // first scalar function of the shell, spinor index within the atom
     for (int k = 0; k < t->n_rad[s]; ++k) {
-      const int l = t->rad_l[t->rad0[s] + k];
+      const int l = t->rad_l[t->rad0[s] + k], kp = kappa_sel(s, k);
       for (int jx2 : {2 * l - 1, 2 * l + 1}) {
         if (jx2 < 0) continue;
         const int a = jx2 == 2 * l + 1 ? 1 : -1;
+        if (kp && kp != (a > 0 ? -l - 1 : l)) continue;
         for (int mjx2 = -jx2; mjx2 <= jx2; mjx2 += 2, ++mu) {
           const int g = spn0[s] + mu;
           t->h_spn_radial[g] = k;
@@ -199,7 +226,7 @@ q4c_status build_spinor_tables(q4c_tables* t) {
               if (ne < 4) col[4 * static_cast<size_t>(g) + ne] = e;
               ++ne;
               // row view: the spinor functions of scalar-spin row rowi
-              Ent* rv = &row[4 * static_cast<size_t>(spn0[s] + rowi)];
+              Ent* rv = &row[4 * static_cast<size_t>(ss0[s] + rowi)];
               int slot = 0;
               while (slot < 4 && rv[slot].idx >= 0) ++slot;
               if (slot == 4 || ne > 4) {  // at most two m_l x two j per row, two spins x two terms per column
@@ -215,8 +242,18 @@ q4c_status build_spinor_tables(q4c_tables* t) {
     }
   }
   t->h_spn0 = spn0;
+  t->h_ss0 = ss0;
+  // a rebuild (new kappa selection) replaces the device views
+  cudaFree(t->d_spn0);
+  cudaFree(t->d_ss0);
+  cudaFree(t->d_spn_col);
+  cudaFree(t->d_spn_row);
+  t->d_spn0 = t->d_ss0 = nullptr;
+  t->d_spn_col = t->d_spn_row = nullptr;
   Q4C_CUDA(cudaMalloc(&t->d_spn0, sizeof(int) * spn0.size()));
   Q4C_CUDA(cudaMemcpy(t->d_spn0, spn0.data(), sizeof(int) * spn0.size(), cudaMemcpyHostToDevice));
+  Q4C_CUDA(cudaMalloc(&t->d_ss0, sizeof(int) * ss0.size()));
+  Q4C_CUDA(cudaMemcpy(t->d_ss0, ss0.data(), sizeof(int) * ss0.size(), cudaMemcpyHostToDevice));
   Q4C_CUDA(cudaMalloc(&t->d_spn_col, sizeof(Ent) * col.size()));
   Q4C_CUDA(cudaMemcpy(t->d_spn_col, col.data(), sizeof(Ent) * col.size(), cudaMemcpyHostToDevice));
   Q4C_CUDA(cudaMalloc(&t->d_spn_row, sizeof(Ent) * row.size()));
@@ -224,9 +261,64 @@ q4c_status build_spinor_tables(q4c_tables* t) {
   return Q4C_OK;
 }
 
+// Offsets of the spinor blocks of a grid's pattern under tables with a kappa
+// selection (prefix sums of n_spinor(A) n_spinor(B)); total in *n.
+static std::vector<int64_t> spinor_block_offsets(const q4c_tables* t, const q4c_grid* g, int64_t* n) {
+  std::vector<int64_t> off(static_cast<size_t>(g->n_blocks) + 1, 0);
+  for (int A = 0; A < g->n_atoms; ++A) {
+    const int sa = g->h_atom_sp[A];
+    const int64_t nsA = t->h_spn0[sa + 1] - t->h_spn0[sa];
+    for (int64_t q = g->h_blk_ptr[A]; q < g->h_blk_ptr[A + 1]; ++q) {
+      const int sb = g->h_atom_sp[g->h_blk_col[q]];
+      off[q + 1] = off[q] + nsA * (t->h_spn0[sb + 1] - t->h_spn0[sb]);
+    }
+  }
+  *n = off.back();
+  return off;
+}
+
+// Device copy of the spinor block offsets for one call (NULL without a
+// kappa selection); the caller frees it on the stream.
+static q4c_status upload_spinor_offsets(const q4c_tables* t, const q4c_grid* g, cudaStream_t s, int64_t** d) {
+  *d = nullptr;
+  if (t->h_kappa_sel.empty()) return Q4C_OK;
+  int64_t n = 0;
+  const std::vector<int64_t> off = spinor_block_offsets(t, g, &n);
+  Q4C_CUDA(cudaMallocAsync(reinterpret_cast<void**>(d), sizeof(int64_t) * off.size(), s));
+  // pageable source: the copy is staged before the call returns
+  Q4C_CUDA(cudaMemcpyAsync(*d, off.data(), sizeof(int64_t) * off.size(), cudaMemcpyHostToDevice, s));
+  return Q4C_OK;
+}
+
 }  // namespace q4c
 
 using namespace q4c;
+
+extern "C" q4c_status q4c_tables_set_kappa(q4c_tables* t, const int32_t* kappa) {
+  Q4C_CHECK_ARG(t, "q4c_tables_set_kappa: NULL tables");
+  const int n = static_cast<int>(t->rad_l.size());
+  std::vector<int> sel;
+  if (kappa) {
+    sel.assign(kappa, kappa + n);
+    for (int k = 0; k < n; ++k) {
+      const int kp = sel[k], l = t->rad_l[k];
+      Q4C_CHECK_ARG(kp == 0 || kp == -l - 1 || (l > 0 && kp == l),
+                    "q4c_tables_set_kappa: kappa must be 0, -l-1 or l (l > 0) of its radial function");
+    }
+    bool any = false;
+    for (int kp : sel) any = any || kp != 0;
+    if (!any) sel.clear();
+  }
+  t->h_kappa_sel = sel;
+  return build_spinor_tables(t);
+}
+
+extern "C" q4c_status q4c_spinor_nnz(const q4c_tables* t, const q4c_grid* g, int64_t* n) {
+  Q4C_CHECK_ARG(t && g && n, "q4c_spinor_nnz: NULL argument");
+  Q4C_CHECK_ARG(g->tables == t, "q4c_spinor_nnz: grid was partitioned with different tables");
+  spinor_block_offsets(t, g, n);
+  return Q4C_OK;
+}
 
 extern "C" q4c_status q4c_spinor_basis(const q4c_tables* t, int32_t species, int32_t* n, int32_t* radial,
                                        int32_t* kappa, int32_t* two_mj) {
@@ -251,12 +343,19 @@ extern "C" q4c_status q4c_spinor_transform(const q4c_tables* t, const q4c_grid* 
                 "q4c_spinor_transform: the small component needs F->W0 or an SO slot");
   if ((!HL && !HS) || g->n_blocks == 0) return Q4C_OK;
   auto s = reinterpret_cast<cudaStream_t>(stream);
-  KernelScope ks("spinor_transform", s);
-  spinor::k_forward<<<static_cast<unsigned>(g->n_blocks), 256, 0, s>>>(
-      g->d_blk_row, g->d_blk_col, g->d_blk_off, g->d_atom_sp, t->d_sp_nfn, t->d_spn0,
-      reinterpret_cast<const spinor::Ent*>(t->d_spn_col), HL ? F->V : nullptr, F->W0, F->SOx, F->SOy, F->SOz,
-      reinterpret_cast<double2*>(HL), reinterpret_cast<double2*>(HS));
-  Q4C_CUDA(cudaGetLastError());
+  int64_t* d_so = nullptr;
+  q4c_status st = upload_spinor_offsets(t, g, s, &d_so);
+  if (st) return st;
+  {
+    KernelScope ks("spinor_transform", s);
+    spinor::k_forward<<<static_cast<unsigned>(g->n_blocks), 256, 0, s>>>(
+        g->d_blk_row, g->d_blk_col, g->d_blk_off, d_so, g->d_atom_sp, t->d_sp_nfn, t->d_spn0,
+        reinterpret_cast<const spinor::Ent*>(t->d_spn_col), HL ? F->V : nullptr, F->W0, F->SOx, F->SOy, F->SOz,
+        reinterpret_cast<double2*>(HL), reinterpret_cast<double2*>(HS));
+  }
+  const cudaError_t e = cudaGetLastError();
+  if (d_so) cudaFreeAsync(d_so, s);
+  Q4C_CUDA(e);
   return Q4C_OK;
 }
 
@@ -266,12 +365,19 @@ extern "C" q4c_status q4c_spinor_density_matrices(const q4c_tables* t, const q4c
   Q4C_CHECK_ARG(g->tables == t, "q4c_spinor_density_matrices: grid was partitioned with different tables");
   if (g->n_blocks == 0) return Q4C_OK;
   auto s = reinterpret_cast<cudaStream_t>(stream);
-  KernelScope ks("spinor_reverse", s);
-  spinor::k_reverse<<<static_cast<unsigned>(g->n_blocks), 256, 0, s>>>(
-      g->d_blk_row, g->d_blk_col, g->d_blk_off, g->d_atom_sp, t->d_sp_nfn, t->d_spn0,
-      reinterpret_cast<const spinor::Ent*>(t->d_spn_row), reinterpret_cast<const double2*>(D), P->V, P->W0,
-      P->SOx, P->SOy, P->SOz);
-  Q4C_CUDA(cudaGetLastError());
+  int64_t* d_so = nullptr;
+  q4c_status st = upload_spinor_offsets(t, g, s, &d_so);
+  if (st) return st;
+  {
+    KernelScope ks("spinor_reverse", s);
+    spinor::k_reverse<<<static_cast<unsigned>(g->n_blocks), 256, 0, s>>>(
+        g->d_blk_row, g->d_blk_col, g->d_blk_off, d_so, g->d_atom_sp, t->d_sp_nfn, t->d_spn0, t->d_ss0,
+        reinterpret_cast<const spinor::Ent*>(t->d_spn_row), reinterpret_cast<const double2*>(D), P->V, P->W0,
+        P->SOx, P->SOy, P->SOz);
+  }
+  const cudaError_t e = cudaGetLastError();
+  if (d_so) cudaFreeAsync(d_so, s);
+  Q4C_CUDA(e);
   return Q4C_OK;
 }
 

@@ -204,6 +204,7 @@ extern "C" void q4c_tables_destroy(q4c_tables* t) {
   cudaFree(t->d_spn0);
   cudaFree(t->d_spn_col);
   cudaFree(t->d_spn_row);
+  cudaFree(t->d_ss0);
   delete t;
 }
 

@@ -260,8 +260,9 @@ def small_radial(r, l: int, alpha: float, kappa: int, V, r_on: float, r_c: float
 
 def small_component(wl: Workload, knots_V: np.ndarray, c: float = C_LIGHT):
     """The small-component basis of a workload: per large-component radial
-    P(r) = r^(l+1) exp(-alpha r^2) c(r) and each kappa of its shell
-    (kappa = -l-1, small-component l~ = l+1; kappa = l for l >= 1, l~ = l-1),
+    P(r) = r^(l+1) exp(-alpha r^2) c(r) and each kappa of its shell, in the
+    order of its spinor functions (kappa = l for l >= 1, small-component
+    l~ = l-1; then kappa = -l-1, l~ = l+1),
     Q(r) = c / (2c^2 - V(r)) (P'(r) + kappa P(r)/r) (the atomic-ZORA balance of
     Eq. 8b; V the radial's potential, given at the knots).  Returns
     (workload with the l~ per radial, Q at the knots [n_rad_S][n_log], index of
@@ -273,7 +274,7 @@ def small_component(wl: Workload, knots_V: np.ndarray, c: float = C_LIGHT):
     for sp in wl.species:
         l_s, a_s = [], []
         for l, alpha in zip(sp.l, sp.alpha):
-            for kappa in ([-l - 1, l] if l >= 1 else [-1]):
+            for kappa in ([l, -l - 1] if l >= 1 else [-1]):
                 Q.append(small_radial(r, l, alpha, kappa, knots_V[k], wl.r_on, wl.r_c, c))
                 l_s.append(l + 1 if kappa < 0 else l - 1)
                 a_s.append(alpha)
