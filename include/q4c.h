@@ -74,7 +74,7 @@ typedef struct q4c_grid q4c_grid;
 typedef struct q4c_basis_desc {
   int32_t n_species;
   const int32_t* n_rad;  /* host [n_species]: radial functions per species (>= 1) */
-  const int32_t* l;      /* host [sum n_rad]: species-major angular momenta, 0 <= l <= 3 */
+  const int32_t* l;      /* host [sum n_rad]: species-major angular momenta, 0 <= l <= 4 */
   const double* alpha;   /* host [sum n_rad]: Gaussian exponents (> 0) */
   double r_cut;          /* support radius of every function (> r_on) */
   double r_on;           /* start of the cutoff ramp (> r_min) */
@@ -84,7 +84,7 @@ typedef struct q4c_basis_desc {
 
 /* Builds the spline tables on the host in FP64 and uploads them to the
  * current device.  *out receives a new handle.  EINVAL on a bad descriptor,
- * EUNSUPPORTED for l > 3, ENOMEM/ECUDA on allocation/copy failure. */
+ * EUNSUPPORTED for l > 4, ENOMEM/ECUDA on allocation/copy failure. */
 Q4C_API q4c_status nao_tabulate(const q4c_basis_desc* desc, q4c_tables** out);
 
 /* The same tables from radial functions given by their values at the knots

@@ -34,7 +34,7 @@ __device__ __forceinline__ void radial_g(const DevBasis& B, int rad, int l, doub
   gp = (du_ds * B.inv_h - (l + 1) * u) * inv_r * irl1;
 }
 
-// S_lm and grad S_lm for l <= lmax (lmax <= 3), index l*l + (m + l)
+// S_lm and grad S_lm for l <= lmax (lmax <= 4), index l*l + (m + l)
 __device__ __forceinline__ void solid_harmonics(double x, double y, double z, int lmax, double* S, double* dS) {
   constexpr double c00 = 0.28209479177387814;   // 1/(2 sqrt(pi))
   constexpr double c1 = 0.4886025119029199;     // sqrt(3/(4 pi))
@@ -46,6 +46,13 @@ __device__ __forceinline__ void solid_harmonics(double x, double y, double z, in
   constexpr double c31 = 0.4570457994644658;    // sqrt(21/(2 pi))/4
   constexpr double c30 = 0.3731763325901154;    // sqrt(7/pi)/4
   constexpr double c32b = 1.445305721320277;    // sqrt(105/pi)/4
+  constexpr double c44a = 2.5033429417967046;   // (3/4) sqrt(35/pi)
+  constexpr double c43 = 1.7701307697799304;    // (3/4) sqrt(35/(2 pi))
+  constexpr double c42a = 0.9461746957575601;   // (3/4) sqrt(5/pi)
+  constexpr double c41 = 0.6690465435572892;    // (3/4) sqrt(5/(2 pi))
+  constexpr double c40 = 0.10578554691520431;   // (3/16) / sqrt(pi)
+  constexpr double c42b = 0.47308734787878004;  // (3/8) sqrt(5/pi)
+  constexpr double c44b = 0.6258357354491761;   // (3/16) sqrt(35/pi)
   S[0] = c00;
   dS[0] = dS[1] = dS[2] = 0.0;
   if (lmax < 1) return;
@@ -77,6 +84,30 @@ __device__ __forceinline__ void solid_harmonics(double x, double y, double z, in
   dS[42] = c32b * 2.0 * x * z; dS[43] = -c32b * 2.0 * y * z; dS[44] = c32b * (xx - yy);
   S[15] = -c33 * x * (xx - 3.0 * yy);
   dS[45] = -c33 * 3.0 * (xx - yy); dS[46] = c33 * 6.0 * x * y; dS[47] = 0.0;
+  if (lmax < 4) return;
+  // l = 4 (rho = r^2); the sign (-1)^|m| of Appendix B on every m != 0 term
+  const double rho = xx + yy + zz, xyz = x * y * z;
+  const double q2 = 7.0 * zz - rho, q1 = 7.0 * zz - 3.0 * rho, q5 = 5.0 * zz - rho;
+  S[16] = c44a * x * y * (xx - yy);
+  dS[48] = c44a * y * (3.0 * xx - yy); dS[49] = c44a * x * (xx - 3.0 * yy); dS[50] = 0.0;
+  S[17] = -c43 * y * z * (3.0 * xx - yy);
+  dS[51] = -6.0 * c43 * xyz; dS[52] = -3.0 * c43 * z * (xx - yy); dS[53] = -c43 * y * (3.0 * xx - yy);
+  S[18] = c42a * x * y * q2;
+  dS[54] = c42a * y * (6.0 * zz - 3.0 * xx - yy); dS[55] = c42a * x * (6.0 * zz - xx - 3.0 * yy);
+  dS[56] = 12.0 * c42a * xyz;
+  S[19] = -c41 * y * z * q1;
+  dS[57] = 6.0 * c41 * xyz; dS[58] = -c41 * z * (q1 - 6.0 * yy); dS[59] = -3.0 * c41 * y * q5;
+  S[20] = c40 * (35.0 * zz * zz - 30.0 * zz * rho + 3.0 * rho * rho);
+  dS[60] = -12.0 * c40 * x * q5; dS[61] = -12.0 * c40 * y * q5; dS[62] = 16.0 * c40 * z * (5.0 * zz - 3.0 * rho);
+  S[21] = -c41 * x * z * q1;
+  dS[63] = -c41 * z * (q1 - 6.0 * xx); dS[64] = 6.0 * c41 * xyz; dS[65] = -3.0 * c41 * x * q5;
+  S[22] = c42b * (xx - yy) * q2;
+  dS[66] = 4.0 * c42b * x * (3.0 * zz - xx); dS[67] = -4.0 * c42b * y * (3.0 * zz - yy);
+  dS[68] = 12.0 * c42b * z * (xx - yy);
+  S[23] = -c43 * x * z * (xx - 3.0 * yy);
+  dS[69] = -3.0 * c43 * z * (xx - yy); dS[70] = 6.0 * c43 * xyz; dS[71] = -c43 * x * (xx - 3.0 * yy);
+  S[24] = c44b * (xx * xx - 6.0 * xx * yy + yy * yy);
+  dS[72] = 4.0 * c44b * x * (xx - 3.0 * yy); dS[73] = 4.0 * c44b * y * (yy - 3.0 * xx); dS[74] = 0.0;
 }
 
 // Evaluates every function of one atom at one point.  out(k, phi, gx, gy, gz)
@@ -96,7 +127,7 @@ __device__ __forceinline__ void atom_functions(const DevBasis& B, int species, d
   }
   int lmax = 0;
   for (int q = 0; q < nr; ++q) lmax = max(lmax, __ldg(B.rad_l + r0 + q));
-  double S[16], dS[48];
+  double S[(kMaxL + 1) * (kMaxL + 1)], dS[3 * (kMaxL + 1) * (kMaxL + 1)];
   solid_harmonics(dx, dy, dz, lmax, S, dS);
   const double r = sqrt(r2);
   const double inv_r = r > 0.0 ? 1.0 / r : 0.0;

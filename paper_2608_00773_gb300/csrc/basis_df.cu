@@ -19,6 +19,8 @@
 // for the D-scaled values, D = w v; 4..7: the values) and per-point exponents
 // of the four quantities (max over functions).  NQ = 1 computes and stores
 // Phi alone (the density contracts Phi only).
+#include <algorithm>
+
 #include "df.cuh"
 #include "internal.h"
 
@@ -41,6 +43,13 @@ constexpr cdf c32a = mk(2.890611442640554);
 constexpr cdf c31 = mk(0.4570457994644658);
 constexpr cdf c30 = mk(0.3731763325901154);
 constexpr cdf c32b = mk(1.445305721320277);
+constexpr cdf c44a = mk(2.5033429417967046);   // (3/4) sqrt(35/pi)
+constexpr cdf c43 = mk(1.7701307697799304);    // (3/4) sqrt(35/(2 pi))
+constexpr cdf c42a = mk(0.9461746957575601);   // (3/4) sqrt(5/pi)
+constexpr cdf c41 = mk(0.6690465435572892);    // (3/4) sqrt(5/(2 pi))
+constexpr cdf c40 = mk(0.10578554691520431);   // (3/16) / sqrt(pi)
+constexpr cdf c42b = mk(0.47308734787878004);  // (3/8) sqrt(5/pi)
+constexpr cdf c44b = mk(0.6258357354491761);   // (3/16) sqrt(35/pi)
 constexpr cdf two_thirds = mk(2.0 / 3.0);
 
 __device__ __forceinline__ int fexp(float x) {  // |x| < 2^fexp(x) for x != 0
@@ -51,7 +60,9 @@ __device__ __forceinline__ int dexp(double x) {
   return static_cast<int>((__double_as_longlong(x) >> 52) & 0x7FF) - 1022;
 }
 
-// S_lm and grad S_lm for l <= lmax (index l*l + m + l), Appendix B signs
+// S_lm and grad S_lm for l <= lmax (index l*l + m + l), Appendix B signs;
+// LM is the largest l the caller's arrays hold (3 or 4)
+template <int LM>
 __device__ __forceinline__ void harmonics(df x, df y, df z, int lmax, df* S, df* dS) {
   const df zero = {0.f, 0.f};
   S[0] = D(c00);
@@ -116,9 +127,58 @@ __device__ __forceinline__ void harmonics(df x, df y, df z, int lmax, df* S, df*
   dS[45] = df_mul_f(df_mul(n33, xmy), 3.f);
   dS[46] = df_mul_f(df_mul(D(c33), xy), 6.f);
   dS[47] = zero;
+  if constexpr (LM >= 4) {
+    if (lmax < 4) return;
+    // l = 4 (rho = r^2), the same polynomials as the FP64 path
+    const df n43 = df_neg(D(c43)), n41 = df_neg(D(c41));
+    const df rho = df_add(xy2, zz), xyz = df_mul(xy, z);
+    const df q2 = df_sub(df_mul_f(zz, 7.f), rho);                    // 7 z^2 - rho
+    const df q1 = df_sub(df_mul_f(zz, 7.f), df_mul_f(rho, 3.f));     // 7 z^2 - 3 rho
+    const df q5 = df_sub(df_mul_f(zz, 5.f), rho);                    // 5 z^2 - rho
+    const df t3b = df_sub(xx, df_mul_f(yy, 3.f));                    // x^2 - 3 y^2
+    const df z3 = df_mul_f(zz, 3.f), z6 = df_mul_f(zz, 6.f);
+    S[16] = df_mul(D(c44a), df_mul(xy, xmy));
+    dS[48] = df_mul(D(c44a), df_mul(y, t3a));
+    dS[49] = df_mul(D(c44a), df_mul(x, t3b));
+    dS[50] = zero;
+    S[17] = df_mul(n43, df_mul(yz, t3a));
+    dS[51] = df_mul_f(df_mul(n43, xyz), 6.f);
+    dS[52] = df_mul_f(df_mul(n43, df_mul(z, xmy)), 3.f);
+    dS[53] = df_mul(n43, df_mul(y, t3a));
+    S[18] = df_mul(D(c42a), df_mul(xy, q2));
+    dS[54] = df_mul(D(c42a), df_mul(y, df_sub(df_sub(z6, df_mul_f(xx, 3.f)), yy)));
+    dS[55] = df_mul(D(c42a), df_mul(x, df_sub(df_sub(z6, xx), df_mul_f(yy, 3.f))));
+    dS[56] = df_mul_f(df_mul(D(c42a), xyz), 12.f);
+    S[19] = df_mul(n41, df_mul(yz, q1));
+    dS[57] = df_mul_f(df_mul(D(c41), xyz), 6.f);
+    dS[58] = df_mul(n41, df_mul(z, df_sub(q1, df_mul_f(yy, 6.f))));
+    dS[59] = df_mul_f(df_mul(n41, df_mul(y, q5)), 3.f);
+    S[20] = df_mul(D(c40), df_add(df_sub(df_mul_f(df_mul(zz, zz), 35.f), df_mul_f(df_mul(zz, rho), 30.f)),
+                                  df_mul_f(df_mul(rho, rho), 3.f)));
+    dS[60] = df_mul_f(df_mul(D(c40), df_mul(x, q5)), -12.f);
+    dS[61] = df_mul_f(df_mul(D(c40), df_mul(y, q5)), -12.f);
+    dS[62] = df_mul_f(df_mul(D(c40), df_mul(z, df_sub(df_mul_f(zz, 5.f), df_mul_f(rho, 3.f)))), 16.f);
+    S[21] = df_mul(n41, df_mul(xz, q1));
+    dS[63] = df_mul(n41, df_mul(z, df_sub(q1, df_mul_f(xx, 6.f))));
+    dS[64] = df_mul_f(df_mul(D(c41), xyz), 6.f);
+    dS[65] = df_mul_f(df_mul(n41, df_mul(x, q5)), 3.f);
+    S[22] = df_mul(D(c42b), df_mul(xmy, q2));
+    dS[66] = df_mul_f(df_mul(D(c42b), df_mul(x, df_sub(z3, xx))), 4.f);
+    dS[67] = df_mul_f(df_mul(D(c42b), df_mul(y, df_sub(z3, yy))), -4.f);
+    dS[68] = df_mul_f(df_mul(D(c42b), df_mul(z, xmy)), 12.f);
+    S[23] = df_mul(n43, df_mul(xz, t3b));
+    dS[69] = df_mul_f(df_mul(n43, df_mul(z, xmy)), 3.f);
+    dS[70] = df_mul_f(df_mul(D(c43), xyz), 6.f);
+    dS[71] = df_mul(n43, df_mul(x, t3b));
+    S[24] = df_mul(D(c44b), df_add(df_sub(df_mul(xx, xx), df_mul_f(df_mul(xx, yy), 6.f)), df_mul(yy, yy)));
+    dS[72] = df_mul_f(df_mul(D(c44b), df_mul(x, t3b)), 4.f);
+    dS[73] = df_mul_f(df_mul(D(c44b), df_mul(y, df_sub(yy, df_mul_f(xx, 3.f)))), 4.f);
+    dS[74] = zero;
+  }
 }
 
 // S_lm alone for l <= lmax (the same polynomials as harmonics)
+template <int LM>
 __device__ __forceinline__ void harmonics_s(df x, df y, df z, int lmax, df* S) {
   S[0] = D(c00);
   if (lmax < 1) return;
@@ -146,9 +206,26 @@ __device__ __forceinline__ void harmonics_s(df x, df y, df z, int lmax, df* S) {
   S[13] = df_mul(n31, df_mul(x, q4));
   S[14] = df_mul(D(c32b), df_mul(z, xmy));
   S[15] = df_mul(n33, df_mul(x, df_sub(xx, df_mul_f(yy, 3.f))));
+  if constexpr (LM >= 4) {
+    if (lmax < 4) return;
+    const df n43 = df_neg(D(c43)), n41 = df_neg(D(c41));
+    const df rho = df_add(df_add(xx, yy), zz);
+    const df q2 = df_sub(df_mul_f(zz, 7.f), rho);
+    const df q1 = df_sub(df_mul_f(zz, 7.f), df_mul_f(rho, 3.f));
+    S[16] = df_mul(D(c44a), df_mul(xy, xmy));
+    S[17] = df_mul(n43, df_mul(yz, df_sub(df_mul_f(xx, 3.f), yy)));
+    S[18] = df_mul(D(c42a), df_mul(xy, q2));
+    S[19] = df_mul(n41, df_mul(yz, q1));
+    S[20] = df_mul(D(c40), df_add(df_sub(df_mul_f(df_mul(zz, zz), 35.f), df_mul_f(df_mul(zz, rho), 30.f)),
+                                  df_mul_f(df_mul(rho, rho), 3.f)));
+    S[21] = df_mul(n41, df_mul(xz, q1));
+    S[22] = df_mul(D(c42b), df_mul(xmy, q2));
+    S[23] = df_mul(n43, df_mul(xz, df_sub(xx, df_mul_f(yy, 3.f))));
+    S[24] = df_mul(D(c44b), df_add(df_sub(df_mul(xx, xx), df_mul_f(df_mul(xx, yy), 6.f)), df_mul(yy, yy)));
+  }
 }
 
-template <int NQ>
+template <int NQ, int LM>
 __global__ void __launch_bounds__(256, 4) k_basis_df(DevBasis B, DevGrid G, DfTables T, int64_t b0,
                                                   const int64_t* __restrict__ scr_off, float2* __restrict__ scratch,
                                                   const double* __restrict__ v, int* __restrict__ colexp,
@@ -194,11 +271,11 @@ __global__ void __launch_bounds__(256, 4) k_basis_df(DevBasis B, DevGrid G, DfTa
     }
     int lmax = 0;
     for (int q = 0; q < nr; ++q) lmax = max(lmax, __ldg(B.rad_l + r0 + q));
-    df S[16], dS[NQ == 1 ? 1 : 48];
+    df S[(LM + 1) * (LM + 1)], dS[NQ == 1 ? 1 : 3 * (LM + 1) * (LM + 1)];
     if (NQ == 1)
-      harmonics_s(dx, dy, dz, lmax, S);
+      harmonics_s<LM>(dx, dy, dz, lmax, S);
     else
-      harmonics(dx, dy, dz, lmax, S, dS);
+      harmonics<LM>(dx, dy, dz, lmax, S, dS);
     const bool pos = in && r2.hi > 0.f;  // a point on the nucleus has r = 0 and 1/r taken as 0
     const df r = pos ? df_sqrt(r2) : df{0.f, 0.f};
     const df ir = pos ? df_div(df{1.f, 0.f}, r) : df{0.f, 0.f};
@@ -300,7 +377,10 @@ __global__ void __launch_bounds__(256, 4) k_basis_df(DevBasis B, DevGrid G, DfTa
 q4c_status launch_basis_df(const q4c_tables* t, const q4c_grid* g, int64_t b0, int64_t b1, const double* v,
                            int* colexp, int* rowexp, int nq, cudaStream_t s, float2* dpad) {
   const size_t smem = sizeof(int) * (8 * std::max(g->max_nb, 1) + 4 * std::max(g->max_np, 1));
-  auto kern = nq == 1 ? bdf::k_basis_df<1> : bdf::k_basis_df<4>;
+  // the l <= 3 instantiations keep the smaller harmonic arrays (registers and stack)
+  const bool l4 = !t->rad_l.empty() && *std::max_element(t->rad_l.begin(), t->rad_l.end()) >= 4;
+  auto kern = nq == 1 ? (l4 ? bdf::k_basis_df<1, 4> : bdf::k_basis_df<1, 3>)
+                      : (l4 ? bdf::k_basis_df<4, 4> : bdf::k_basis_df<4, 3>);
   if (nq != 1 && nq != 4) {
     set_error("launch_basis_df: nq must be 1 or 4");
     return Q4C_EINVAL;

@@ -12,7 +12,7 @@
 
 namespace q4c {
 
-constexpr int kMaxL = 3;
+constexpr int kMaxL = 4;
 constexpr int kMaxBatch = 1024;
 constexpr int kDPitch = 352;  // points per batch row of the D = w v table (>= 16 * ceil(341 / 16))
 

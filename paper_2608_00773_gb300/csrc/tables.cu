@@ -122,7 +122,7 @@ static q4c_status tabulate(const q4c_basis_desc* desc, const double* knots, q4c_
       }
       if (l > kMaxL) {
         delete t;
-        set_error("nao_tabulate: l > 3 is not supported");
+        set_error("nao_tabulate: l > 4 is not supported");
         return Q4C_EUNSUPPORTED;
       }
       nf += 2 * l + 1;

@@ -57,9 +57,9 @@ def test_status_codes_on_bad_arguments(lib):
     d = B.BasisDesc(1, n_rad.ctypes.data, l.ctypes.data, a.ctypes.data, 5.0, 6.0, 1e-4, 200)
     assert lib.nao_tabulate(C.byref(d), C.byref(h)) == 1
     assert b"r_min < r_on < r_cut" in lib.q4c_last_error()
-    # l > 3 is outside what the kernels expand
-    l4 = np.array([4], np.int32)
-    d = B.BasisDesc(1, n_rad.ctypes.data, l4.ctypes.data, a.ctypes.data, 6.0, 5.0, 1e-4, 200)
+    # l > 4 is outside what the kernels expand
+    l5 = np.array([5], np.int32)
+    d = B.BasisDesc(1, n_rad.ctypes.data, l5.ctypes.data, a.ctypes.data, 6.0, 5.0, 1e-4, 200)
     assert lib.nao_tabulate(C.byref(d), C.byref(h)) == 5
     # too few knots, negative exponent
     d = B.BasisDesc(1, n_rad.ctypes.data, l.ctypes.data, a.ctypes.data, 6.0, 5.0, 1e-4, 3)
@@ -75,6 +75,11 @@ def test_status_codes_on_bad_arguments(lib):
     assert lib.grid_partition(None, None, C.byref(h)) == 1
     info = B.GridInfo()
     assert lib.q4c_grid_get_info(None, C.byref(info)) == 1
+    # knot-value tables without knots, kappa selection and spinor counts without handles
+    assert lib.nao_tabulate_knots(C.byref(d), None, C.byref(h)) == 1
+    assert lib.q4c_tables_set_kappa(None, None) == 1
+    n = C.c_int64()
+    assert lib.q4c_spinor_nnz(None, None, C.byref(n)) == 1
 
 
 def test_no_device_fails_loudly(lib):

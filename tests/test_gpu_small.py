@@ -5,26 +5,17 @@ Eq. 19 in the scalar form, F^S_ij = sum_p w phi^S_i (eps_j - V_j + v) phi^S_j
 (the i of phi^S cancels against its conjugate), against the oracle within
 1e-12 relative Frobenius on a molecule, a cluster and a periodic cell; the
 split path on the same tables within 1e-9 of FP64; knot-value tables of the
-large-component radials against the (l, alpha) tables; and l~ = 4 (from f
-shells) refused."""
-import dataclasses
-
+large-component radials against the (l, alpha) tables; l = 4 (g shells, and
+the l~ = 4 small components of f shells) on both paths; l = 5 refused."""
 import numpy as np
 import pytest
 
 import oracle as O
 import paper_2608_00773_gb300 as q
 from gpu_helpers import LibCase, OracleCase, rel_fro
-from workloads import Species, column_operator, periodic_cell, small_cluster, small_component, water
+from workloads import column_operator, periodic_cell, single_atom, small_cluster, small_component, water
 
 pytestmark = pytest.mark.gpu
-
-
-def up_to_d(wl):
-    """The workload with its f shells dropped (their small components need l~ = 4)."""
-    sp = [Species(s.name, s.Z, [l for l in s.l if l <= 2], [a for l, a in zip(s.l, s.alpha) if l <= 2])
-          for s in wl.species]
-    return dataclasses.replace(wl, species=sp)
 
 
 @pytest.fixture(scope="module", params=["water", "cluster", "cell"])
@@ -32,8 +23,8 @@ def case(request):
     from paper_2608_00773_gb300 import _build
     _build.build()
     O.build()
-    wl = {"water": water, "cluster": lambda: up_to_d(small_cluster(8, seed=7)),
-          "cell": lambda: up_to_d(periodic_cell())}[request.param]()
+    # the cluster's f shells give small components with l~ = 4
+    wl = {"water": water, "cluster": lambda: small_cluster(8, seed=7), "cell": periodic_cell}[request.param]()
     eps, Vk = column_operator(wl, 41)
     ws, Q, parent, _ = small_component(wl, Vk)
     return LibCase(ws, Q), OracleCase(ws, Q), eps[parent], Vk[parent]
@@ -76,12 +67,23 @@ def test_knot_tables_match_analytic_tables():
         assert np.abs(a - b).max() <= 1e-13 * np.abs(a).max()
 
 
-def test_l_tilde_4_is_refused():
+def test_g_shells_of_the_large_component():
+    """l = 4 as a large-component radial (the basis evaluation has no
+    small-component special case): FP64 against the oracle, split against FP64."""
     from paper_2608_00773_gb300 import _build
     _build.build()
-    wl = small_cluster(8, seed=7)
-    _, Vk = column_operator(wl, 3)
-    ws, Q, _, _ = small_component(wl, Vk)
-    assert ws.rad_l.max() == 4
+    O.build()
+    wl = single_atom([0, 2, 4, 4], [1.3, 0.9, 2.1, 0.6], Z=6.0, n_rad=40)
+    lib, orc = LibCase(wl), OracleCase(wl)
+    got = lib.integrate("fp64")
+    for g, r in zip(got[:5], orc.mats):
+        assert rel_fro(g, r) <= 1e-12
+    for g, r in zip(lib.integrate("split")[:5], got[:5]):
+        assert rel_fro(g, r) <= 1e-9
+
+
+def test_l_5_is_refused():
+    from paper_2608_00773_gb300 import _build
+    _build.build()
     with pytest.raises(q.Q4CError):
-        q.nao_tabulate_knots(ws.n_rad_per_species, ws.rad_l, Q, ws.r_c, ws.r_on, ws.r_min, ws.n_log)
+        q.nao_tabulate([1], [5], [1.0])

@@ -4,8 +4,8 @@ give the spinor basis of the large component, bit-exact against the oracle;
 their forward map of the per-column operator F^S is the SS block of Eq. 19,
 and with the large component's block the whole H+ (and S+), within 1e-12 of
 the oracle; the reverse map and the small-component density of Eq. 21 on
-seeded spinor density matrices within 1e-12; on a molecule and a periodic
-cell."""
+seeded spinor density matrices within 1e-12; on a molecule, a cluster with f
+shells (l~ = 4) and a periodic cell."""
 import numpy as np
 import pytest
 
@@ -13,7 +13,7 @@ import oracle as O
 import paper_2608_00773_gb300 as q
 from gpu_helpers import LibCase, OracleCase, point_map, rel_fro
 from oracle import spinor as S
-from workloads import column_operator, periodic_cell, small_component, water
+from workloads import column_operator, periodic_cell, small_cluster, small_component, water
 
 pytestmark = pytest.mark.gpu
 
@@ -31,12 +31,13 @@ class Case:
         self.GS = S.atom_matrices(self.ws, kappas=self.kS)
 
 
-@pytest.fixture(scope="module", params=["water", "cell"])
+@pytest.fixture(scope="module", params=["water", "cluster", "cell"])
 def case(request):
     from paper_2608_00773_gb300 import _build
     _build.build()
     O.build()
-    return Case(water() if request.param == "water" else periodic_cell())
+    # the cluster's f shells carry small components with l~ = 4
+    return Case({"water": water, "cluster": lambda: small_cluster(8, seed=7), "cell": periodic_cell}[request.param]())
 
 
 def _flat(blocks, pat):

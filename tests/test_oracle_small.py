@@ -59,7 +59,7 @@ def test_small_r_power_law_fixes_l_tilde_and_kappa():
 
 @pytest.fixture(scope="module")
 def atom():
-    wl = single_atom([0, 1, 2], [1.4, 1.6, 1.9], Z=3.0, n_rad=80)
+    wl = single_atom([0, 1, 2, 3], [1.4, 1.6, 1.9, 2.2], Z=3.0, n_rad=80)  # l~ up to 4
     xyz, w, _ = O.grid(wl)
     return wl, xyz, w
 
