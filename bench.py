@@ -295,7 +295,7 @@ def main():
     import torch
 
     import paper_2608_00773_gb300 as q
-    from workloads import ADJOINT_KINDS, fill_pattern, potential
+    from workloads import ADJOINT_KINDS, column_operator, fill_pattern, potential
 
     rank, world, local = dist_init()
     torch.cuda.set_device(local)
@@ -465,6 +465,32 @@ def main():
                               "frac": world * F_step / (t64 * 1e-3) / 1e12 / p64,
                               "speedup_split_vs_fp64": t64 / t_ms, "steps": args.fp64_steps,
                               "phase_precision": fp64_phase}
+        # the per-column operator of Eq. 19 (one non-symmetric product per
+        # batch: 2 n_p n_b^2 algorithmic FLOPs) on both paths, same workload
+        eps_c, knots_c = column_operator(wl, 1201)
+        q.q4c_tables_set_columns(tables, eps_c, knots_c)
+        F_split = torch.empty(nnz, dtype=torch.float64, device=dev)
+        F_64 = torch.empty(nnz, dtype=torch.float64, device=dev)
+        q.q4c_integrate_columns(tables, grid, v, "split", out=F_split, stream=stream)
+        evc = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(5)]
+        for a_, b_ in evc:
+            flush.zero_()
+            a_.record(stream)
+            q.q4c_integrate_columns(tables, grid, v, "split", out=F_split, stream=stream)
+            b_.record(stream)
+        e64 = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+        flush.zero_()
+        e64[0].record(stream)
+        q.q4c_integrate_columns(tables, grid, v, "fp64", out=F_64, stream=stream)
+        e64[1].record(stream)
+        torch.cuda.synchronize()
+        tc = statistics.mean(a_.elapsed_time(b_) for a_, b_ in evc)
+        Fc = fl["integrate"] / 7.0
+        extra["columns_operator"] = {
+            "what": "F_ij = sum_p w phi_i (eps_j - V_j + v) phi_j (Eq. 19), q4c_integrate_columns",
+            "split_ms": tc, "split_tflops": Fc / (tc * 1e-3) / 1e12, "fp64_ms": e64[0].elapsed_time(e64[1]),
+            "rel_err_split_vs_fp64": float(torch.linalg.norm(F_split - F_64) / torch.linalg.norm(F_64)),
+            "steps": len(evc)}
 
     if rank != 0:
         return

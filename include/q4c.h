@@ -276,11 +276,15 @@ Q4C_API q4c_status q4c_density_full(const q4c_tables* tables, const q4c_grid* gr
 Q4C_API q4c_status q4c_tables_set_columns(q4c_tables* tables, const double* eps, const double* knots);
 
 /* F on the grid's block pattern (device [nnz], overwritten; every element
- * of every block, no symmetry used) in FP64, v_dev device [n_points] in
- * batch order.  EINVAL without q4c_tables_set_columns.  Stream-ordered,
- * with one host synchronisation per wave of batches. */
+ * of every block, no symmetry used), v_dev device [n_points] in batch order.
+ * prec Q4C_FP64: FP64 tiles and products.  Q4C_SPLIT: the tensor-core path
+ * of q4c_integrate, F = (w Phi)^T Psi per batch with
+ * Psi_pj = (v_p + eps_j - V_j(r_pj)) phi_j(p) formed in double-float and
+ * sliced into six BF16 digits (~1e-12 relative; EUNSUPPORTED above 341
+ * points per batch).  EINVAL without q4c_tables_set_columns.
+ * Stream-ordered, with one host synchronisation per wave of batches. */
 Q4C_API q4c_status q4c_integrate_columns(const q4c_tables* tables, const q4c_grid* grid, const double* v_dev,
-                                 double* F_dev, q4c_stream stream);
+                                 q4c_precision prec, double* F_dev, q4c_stream stream);
 
 /* ---------------------------------------------------------------- spinors
  * Scalar -> spinor transformation (Section II, Eqs. 9-14; Section III A,

@@ -98,7 +98,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     L.q4c_density_full.argtypes = [vp, vp, C.POINTER(Matrices), C.c_int, vp, vp]
     L.q4c_spinor_basis.argtypes = [vp, i32, vp, vp, vp, vp]
     L.q4c_tables_set_columns.argtypes = [vp, vp, vp]
-    L.q4c_integrate_columns.argtypes = [vp, vp, vp, vp, vp]
+    L.q4c_integrate_columns.argtypes = [vp, vp, vp, i32, vp, vp]
     L.q4c_spinor_transform.argtypes = [vp, vp, C.POINTER(Matrices), vp, vp, vp]
     L.q4c_spinor_density_matrices.argtypes = [vp, vp, vp, C.POINTER(Matrices), vp]
     L.q4c_grid_batch_spinors.argtypes = [vp, i64, vp, vp, vp]
@@ -322,12 +322,12 @@ def q4c_tables_set_columns(tables: Tables, eps, knots):
     _check(load().q4c_tables_set_columns(tables.h, e.ctypes.data, k.ctypes.data))
 
 
-def q4c_integrate_columns(tables: Tables, grid: Grid, v, out=None, stream=None):
-    """F_ij = sum_p w phi_i (eps_j - V_j + v) phi_j on the block pattern (FP64)."""
+def q4c_integrate_columns(tables: Tables, grid: Grid, v, prec="fp64", out=None, stream=None):
+    """F_ij = sum_p w phi_i (eps_j - V_j + v) phi_j on the block pattern ("fp64" or "split")."""
     import torch
     if out is None:
         out = torch.empty(grid.nnz, dtype=torch.float64, device=v.device)
-    _check(load().q4c_integrate_columns(tables.h, grid.h, _ptr(v), _ptr(out), _stream(stream)))
+    _check(load().q4c_integrate_columns(tables.h, grid.h, _ptr(v), _prec(prec), _ptr(out), _stream(stream)))
     return out
 
 

@@ -18,7 +18,10 @@
 // tile layout [4][n_b][ceil8(n_p)]; column exponents (slots 0..3: upper bounds
 // for the D-scaled values, D = w v; 4..7: the values) and per-point exponents
 // of the four quantities (max over functions).  NQ = 1 computes and stores
-// Phi alone (the density contracts Phi only).
+// Phi alone (the density contracts Phi only).  NQ = 2 is the per-column
+// operator of Eq. 19: Phi and Psi_pj = (v_p + eps_j - V_j(r_pj)) phi_j(p) in
+// the planes of Phi and X, with D = w (V_j the column potential splined on
+// the radial knots, eps_j its eigenvalue, per radial function).
 #include <algorithm>
 
 #include "df.cuh"
@@ -54,6 +57,11 @@ constexpr cdf two_thirds = mk(2.0 / 3.0);
 
 __device__ __forceinline__ int fexp(float x) {  // |x| < 2^fexp(x) for x != 0
   return static_cast<int>((__float_as_uint(x) >> 23) & 0xFF) - 126;
+}
+
+__device__ __forceinline__ df split_d(double x) {  // x as an FP32 pair
+  const float h = static_cast<float>(x);
+  return {h, static_cast<float>(x - static_cast<double>(h))};
 }
 
 __device__ __forceinline__ int dexp(double x) {
@@ -229,7 +237,8 @@ template <int NQ, int LM>
 __global__ void __launch_bounds__(256, 4) k_basis_df(DevBasis B, DevGrid G, DfTables T, int64_t b0,
                                                   const int64_t* __restrict__ scr_off, float2* __restrict__ scratch,
                                                   const double* __restrict__ v, int* __restrict__ colexp,
-                                                  int* __restrict__ rowexp, float2* __restrict__ dpad) {
+                                                  int* __restrict__ rowexp, float2* __restrict__ dpad,
+                                                  const float4* __restrict__ ccoef, const double* __restrict__ ceps) {
   extern __shared__ int sm[];  // [8][nb] column exponents, then [4][np] point exponents
   const int64_t b = b0 + blockIdx.x;
   const int64_t p0 = G.pt_ptr[b];
@@ -260,7 +269,7 @@ __global__ void __launch_bounds__(256, 4) k_basis_df(DevBasis B, DevGrid G, DfTa
     const bool in = live && r2.hi < T.rc2;
     int eD = -30000;
     if (colexp && live) {
-      const double Dp = G.w[p0 + p] * v[p0 + p];
+      const double Dp = NQ == 2 ? G.w[p0 + p] : G.w[p0 + p] * v[p0 + p];
       if (Dp != 0.0) eD = dexp(Dp);
       if (dpad && a == 0) {  // D = w v as (hi, lo), once per point
         const float h = static_cast<float>(Dp);
@@ -269,10 +278,11 @@ __global__ void __launch_bounds__(256, 4) k_basis_df(DevBasis B, DevGrid G, DfTa
     } else if (dpad && a == 0 && p < ((np + 15) & ~15)) {
       dpad[b * kDPitch + p] = make_float2(0.f, 0.f);  // the K-step of 16 points reads zeros past n_p
     }
+    const df vdf = (NQ == 2 && live) ? split_d(v[p0 + p]) : df{0.f, 0.f};
     int lmax = 0;
     for (int q = 0; q < nr; ++q) lmax = max(lmax, __ldg(B.rad_l + r0 + q));
-    df S[(LM + 1) * (LM + 1)], dS[NQ == 1 ? 1 : 3 * (LM + 1) * (LM + 1)];
-    if (NQ == 1)
+    df S[(LM + 1) * (LM + 1)], dS[NQ == 4 ? 3 * (LM + 1) * (LM + 1) : 1];
+    if (NQ != 4)
       harmonics_s<LM>(dx, dy, dz, lmax, S);
     else
       harmonics<LM>(dx, dy, dz, lmax, S, dS);
@@ -303,6 +313,14 @@ __global__ void __launch_bounds__(256, 4) k_basis_df(DevBasis B, DevGrid G, DfTa
       const int rad = r0 + q;
       const int l = __ldg(B.rad_l + rad);
       df g = {0.f, 0.f}, gp = {0.f, 0.f};
+      df psi = {0.f, 0.f};  // NQ = 2: v_p + eps_j - V_j(r)
+      if (NQ == 2 && in) {
+        const float4* vp = ccoef + (static_cast<int64_t>(rad) * (B.n_log - 1) + (below ? 0 : k)) * 2;
+        const float4 v01 = __ldg(vp), v23 = __ldg(vp + 1);
+        const df V0 = {v01.x, v01.y}, V1 = {v01.z, v01.w}, V2 = {v23.x, v23.y}, V3 = {v23.z, v23.w};
+        const df Vr = below ? V0 : df_add(df_mul(df_add(df_mul(df_add(df_mul(V3, s), V2), s), V1), s), V0);
+        psi = df_sub(df_add(vdf, split_d(__ldg(ceps + rad))), Vr);
+      }
       if (in) {
         if (below) {
           g = T.g0[rad];
@@ -315,7 +333,7 @@ __global__ void __launch_bounds__(256, 4) k_basis_df(DevBasis B, DevGrid G, DfTa
           df irl = ir;
           for (int t = 0; t < l; ++t) irl = df_mul(irl, ir);
           g = df_mul(u, irl);
-          if (NQ > 1)
+          if (NQ == 4)
             gp = df_mul(df_mul(df_sub(df_mul(du, T.inv_h_df), df_mul_f(u, static_cast<float>(l + 1))), ir), irl);
         }
       }
@@ -324,10 +342,12 @@ __global__ void __launch_bounds__(256, 4) k_basis_df(DevBasis B, DevGrid G, DfTa
         const int idx = l * l + m;
         df vals[4];
         vals[0] = df_mul(g, S[idx]);
-        if (NQ > 1) {
+        if (NQ == 4) {
           vals[1] = df_add(df_mul(gx, S[idx]), df_mul(g, dS[3 * idx]));
           vals[2] = df_add(df_mul(gy, S[idx]), df_mul(g, dS[3 * idx + 1]));
           vals[3] = df_add(df_mul(gz, S[idx]), df_mul(g, dS[3 * idx + 2]));
+        } else if (NQ == 2) {
+          vals[1] = df_mul(psi, vals[0]);
         }
         const int f = f0 + fl;
         if (live) {
@@ -376,13 +396,18 @@ __global__ void __launch_bounds__(256, 4) k_basis_df(DevBasis B, DevGrid G, DfTa
 
 q4c_status launch_basis_df(const q4c_tables* t, const q4c_grid* g, int64_t b0, int64_t b1, const double* v,
                            int* colexp, int* rowexp, int nq, cudaStream_t s, float2* dpad) {
+  if (nq == 2 && !(t->d_col_coef_df && t->d_col_eps && v)) {
+    set_error("launch_basis_df: the per-column operator needs the column potentials and v");
+    return Q4C_EINVAL;
+  }
   const size_t smem = sizeof(int) * (8 * std::max(g->max_nb, 1) + 4 * std::max(g->max_np, 1));
   // the l <= 3 instantiations keep the smaller harmonic arrays (registers and stack)
   const bool l4 = !t->rad_l.empty() && *std::max_element(t->rad_l.begin(), t->rad_l.end()) >= 4;
-  auto kern = nq == 1 ? (l4 ? bdf::k_basis_df<1, 4> : bdf::k_basis_df<1, 3>)
-                      : (l4 ? bdf::k_basis_df<4, 4> : bdf::k_basis_df<4, 3>);
-  if (nq != 1 && nq != 4) {
-    set_error("launch_basis_df: nq must be 1 or 4");
+  auto kern = nq == 1   ? (l4 ? bdf::k_basis_df<1, 4> : bdf::k_basis_df<1, 3>)
+              : nq == 2 ? (l4 ? bdf::k_basis_df<2, 4> : bdf::k_basis_df<2, 3>)
+                        : (l4 ? bdf::k_basis_df<4, 4> : bdf::k_basis_df<4, 3>);
+  if (nq != 1 && nq != 2 && nq != 4) {
+    set_error("launch_basis_df: nq must be 1, 2 or 4");
     return Q4C_EINVAL;
   }
   if (smem > 48 * 1024)
@@ -393,7 +418,8 @@ q4c_status launch_basis_df(const q4c_tables* t, const q4c_grid* g, int64_t b0, i
   KernelScope ks("basis_df", s);
   kern<<<static_cast<unsigned>(b1 - b0), 256, smem, s>>>(t->view(), g->view(), T, b0, g->d_scr_off,
                                                                      reinterpret_cast<float2*>(g->d_scratch), v,
-                                                                     colexp, rowexp, dpad);
+                                                                     colexp, rowexp, dpad, t->d_col_coef_df,
+                                                                     t->d_col_eps);
   Q4C_CUDA(cudaGetLastError());
   return Q4C_OK;
 }

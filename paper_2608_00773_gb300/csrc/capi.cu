@@ -97,13 +97,15 @@ extern "C" q4c_status q4c_basis_eval(const q4c_tables* t, const q4c_grid* g, int
   return basis_eval(t, g, n_pts, xyz, phi, grad, reinterpret_cast<cudaStream_t>(stream));
 }
 
-extern "C" q4c_status q4c_integrate_columns(const q4c_tables* t, const q4c_grid* g, const double* v, double* F,
-                                            q4c_stream stream) {
+extern "C" q4c_status q4c_integrate_columns(const q4c_tables* t, const q4c_grid* g, const double* v,
+                                            q4c_precision prec, double* F, q4c_stream stream) {
   if (q4c_status st = check_pair(t, g, "q4c_integrate_columns")) return st;
   Q4C_CHECK_ARG(v && F, "q4c_integrate_columns: NULL input or output array");
+  Q4C_CHECK_ARG(prec == Q4C_FP64 || prec == Q4C_SPLIT, "q4c_integrate_columns: unknown precision");
   Q4C_CHECK_ARG(t->d_col_eps && t->d_col_coef,
                 "q4c_integrate_columns: no column potentials (call q4c_tables_set_columns first)");
   try {
+    if (prec == Q4C_SPLIT) return integrate_columns_split(t, g, v, F, reinterpret_cast<cudaStream_t>(stream));
     return integrate_columns_fp64(t, g, v, F, reinterpret_cast<cudaStream_t>(stream));
   } catch (const std::exception& e) {
     set_error(std::string("q4c_integrate_columns: ") + e.what());

@@ -805,6 +805,21 @@ extern "C" q4c_status grid_partition(const q4c_grid_desc* d, const q4c_tables* t
     max_wave_items = std::max(max_wave_items, static_cast<int64_t>(sitems.size()) - g->split_w0.back());
     g->split_w0.push_back(static_cast<int64_t>(sitems.size()));
   }
+  // per-column operator (output 5): one product on every tile pair, in the
+  // same batch order (never more items per wave than the list above, so the
+  // rounding-constant buffer fits both)
+  std::vector<int4> citems;
+  std::vector<int> csteps;
+  g->col_w0.push_back(0);
+  for (size_t wv = 0; wv + 1 < g->wave_b0.size(); ++wv) {
+    for (int64_t n = g->split_w0[wv]; n < g->split_w0[wv + 1]; ++n) {
+      const int4 it = sitems[n];
+      if (it.y != 4) continue;  // the A_xy items visit every tile pair of their batch once
+      citems.push_back(make_int4(it.x, 5, it.z, it.w));
+      csteps.push_back(ssteps[n]);
+    }
+    g->col_w0.push_back(static_cast<int64_t>(citems.size()));
+  }
   // density/adjoint: (batch, 64-point tile) items per wave, costliest first
   std::vector<int2> rditems;
   g->rd_w0.push_back(0);
@@ -873,6 +888,7 @@ extern "C" q4c_status grid_partition(const q4c_grid_desc* d, const q4c_tables* t
       (st = up(&g->d_kblk_q1, g->h_kblk_q1)) || (st = up(&g->d_kblk_off, g->h_kblk_off)) ||
       (st = up(&g->d_scr_off, g->h_scr_off)) || (st = up(&g->d_tiles, tiles)) || (st = up(&g->d_sched, sched)) ||
       (st = up(&g->d_split_items, sitems)) || (st = up(&g->d_split_steps, ssteps)) ||
+      (st = up(&g->d_col_items, citems)) || (st = up(&g->d_col_steps, csteps)) ||
       (st = up(&g->d_rd_items, rditems)) ||
       (st = up(&g->d_bat_idx_ptr, idx_ptr)) ||
       (st = up(&g->d_gsl_off, gsl_off))) {
@@ -915,7 +931,7 @@ extern "C" void q4c_grid_destroy(q4c_grid* g) {
                   g->d_pt_ptr, g->d_bat_atom_ptr, g->d_bat_atoms, g->d_bat_atom_fn0, g->d_bat_fn_ptr,
                   g->d_fn_info, g->d_bat_pair_ptr, g->d_pair_off, g->d_blk_off, g->d_blk_row, g->d_blk_col,
                   g->d_blk_T, g->d_scr_off, g->d_tiles, g->d_scratch, g->d_sched, g->d_counter, g->d_split_ws,
-                  g->d_split_items, g->d_split_steps, g->d_split_mag, g->d_dpad, g->d_tmaps, g->d_colexp, g->d_status, g->d_rd_items, g->d_rowexp, g->d_gsl, g->d_gsl_off,
+                  g->d_split_items, g->d_split_steps, g->d_col_items, g->d_col_steps, g->d_split_mag, g->d_dpad, g->d_tmaps, g->d_colexp, g->d_status, g->d_rd_items, g->d_rowexp, g->d_gsl, g->d_gsl_off,
                   g->d_bat_idx_ptr, g->d_bat_idx, g->d_pts_df, g->d_atoms_df, g->d_gdf,
                   g->d_c_xyz, g->d_c_sp, g->d_blk_role, g->d_blk_shift, g->d_kblk_q0, g->d_kblk_q1,
                   g->d_kblk_off};

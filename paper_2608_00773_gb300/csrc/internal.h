@@ -105,6 +105,7 @@ struct q4c_tables {
   // coefficients of V per radial function, [n_rad_tot] and [n_rad_tot][n_log-1][4]
   double* d_col_eps = nullptr;
   double* d_col_coef = nullptr;
+  float4* d_col_coef_df = nullptr;  // the same coefficients as FP32 pairs (split path)
   // device
   double* d_coef = nullptr;
   double* d_g0 = nullptr;
@@ -187,6 +188,9 @@ struct q4c_grid {
   std::vector<int64_t> split_w0;           // [n_waves+1] ranges into d_split_items
   int4* d_split_items = nullptr;
   int* d_split_steps = nullptr;            // K-steps of 16 points per item (3x for W0)
+  std::vector<int64_t> col_w0;             // [n_waves+1] ranges into d_col_items
+  int4* d_col_items = nullptr;             // per-column operator: (batch, 5, ti, tj), every tile pair
+  int* d_col_steps = nullptr;
   float* d_split_mag = nullptr;            // [items of the largest wave][128] rounding constants
   void* d_tmaps = nullptr;                 // [2][n_batches] 3-D TMA maps (points, functions, quantity) of the
                                            // tiles: boxes 16 x 64 (products), 64 x 16 (density, adjoint)
@@ -229,7 +233,8 @@ q4c_status launch_fill_idx(const q4c_tables* t, const q4c_grid* g, int64_t b0, i
 // basis_df.cu
 // spinor.cu: scalar -> spinor relation tables of a set of species
 q4c_status build_spinor_tables(q4c_tables* t);
-// nq = 4: Phi, X, Y, Z tiles; nq = 1: Phi alone
+// nq = 4: Phi, X, Y, Z tiles; nq = 1: Phi alone; nq = 2: Phi and the
+// per-column operator's Psi = (v + eps_j - V_j) phi_j with D = w
 q4c_status launch_basis_df(const q4c_tables* t, const q4c_grid* g, int64_t b0, int64_t b1, const double* v,
                            int* colexp, int* rowexp, int nq, cudaStream_t s, float2* dpad = nullptr);
 // rowdot.cu
@@ -239,6 +244,8 @@ q4c_status backward_split(const q4c_tables* t, const q4c_grid* g, const q4c_matr
 // split.cu
 q4c_status integrate_split(const q4c_tables* t, const q4c_grid* g, const double* v, const q4c_matrices* out,
                            cudaStream_t s);
+q4c_status integrate_columns_split(const q4c_tables* t, const q4c_grid* g, const double* v, double* F,
+                                   cudaStream_t s);
 // grid.cu
 q4c_status becke_weights(const double* d_raw_xyz, const double* d_base_w, int64_t n_raw, int pts_per_atom,
                          const double* d_atom_xyz, const double* d_inv_rab, int n_atoms, double r_c, double r_nb,

@@ -36,7 +36,9 @@
 // (three products into one accumulator, sliced against a common exponent per
 // function so that the exact levels keep one unit), and A_yz = (D Y)^T Z,
 // A_zx = (D Z)^T X, A_xy = (D X)^T Y with SO_x = A_yz - A_yz^T etc. applied
-// while scattering.  One warp-specialised CTA per SM (slicers, one MMA
+// while scattering; and, as its own launch, the per-column operator of
+// Eq. 19, F = (w Phi)^T Psi with Psi_pj = (v_p + eps_j - V_j) phi_j (output 5,
+// every tile pair, every element into its own block).  One warp-specialised CTA per SM (slicers, one MMA
 // thread, epilogue warps; 512 TMEM columns) loops over the work items; every
 // mbarrier wait is bounded and sets a status bit instead of hanging.
 #include <cuda.h>
@@ -100,7 +102,8 @@ __device__ __forceinline__ Products products_of(int o) {
     case 1: return {3, 0x39u, 0x39u};          // W0: (X, X), (Y, Y), (Z, Z)
     case 2: return {1, 2u, 3u};                // A_yz -> SO_x
     case 3: return {1, 3u, 1u};                // A_zx -> SO_y
-    default: return {1, 1u, 2u};               // A_xy -> SO_z
+    case 4: return {1, 1u, 2u};                // A_xy -> SO_z
+    default: return {1, 0u, 1u};               // per-column operator: (w Phi)^T Psi
   }
 }
 
@@ -380,7 +383,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int nb = static_cast<int>(G.bat_fn_ptr[b + 1] - G.bat_fn_ptr[b]);
       const int N = (min(kTile, nb - j0) + 15) & ~15;
       const int* idx = G.bat_idx + G.bat_idx_ptr[b];
-      double* out = o == 0 ? V : o == 1 ? W0 : o == 2 ? SOx : o == 3 ? SOy : SOz;
+      double* out = (o == 0 || o == 5) ? V : o == 1 ? W0 : o == 2 ? SOx : o == 3 ? SOy : SOz;
       for (int c0 = eg * 16; c0 < N; c0 += 32) {
 #pragma unroll
         for (int blk = 0; blk < 3; ++blk) {
@@ -411,7 +414,9 @@ __global__ void __launch_bounds__(kThreads, 1)
           const double val = static_cast<double>(sm) + static_cast<double>(lo);
           int ri = i, rj = j;
           double sgn = 1.0;
-          if (o <= 1) {
+          if (o == 5) {
+            // not symmetric: every (i, j) into its own block
+          } else if (o <= 1) {
             if (i > j) continue;
           } else {
             if (i == j) continue;
@@ -472,6 +477,49 @@ q4c_status integrate_split(const q4c_tables* t, const q4c_grid* g, const double*
     Q4C_CUDA(cudaGetLastError());
   }
   return mirror_and_spinor(g, out, s);
+}
+
+// The per-column operator of Eq. 19 on the split path: per wave the offset
+// tables, the tiles Phi and Psi with D = w (k_basis_df<2>), the rounding
+// constants and one products launch over every tile pair; F is written
+// element by element (no mirror: it is not symmetric).
+q4c_status integrate_columns_split(const q4c_tables* t, const q4c_grid* g, const double* v, double* F,
+                                   cudaStream_t s) {
+  if (g->max_np > 341) {
+    set_error("q4c_integrate_columns: the split path needs batches of at most 341 points");
+    return Q4C_EUNSUPPORTED;
+  }
+  Q4C_CUDA(cudaMemsetAsync(F, 0, sizeof(double) * g->nnz, s));
+  const int n_waves = static_cast<int>(g->wave_b0.size()) - 1;
+  Q4C_CUDA(cudaFuncSetAttribute(split::k_split_products, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                split::kSmemTotal));
+  int dev = 0, n_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+  for (int wv = 0; wv < n_waves; ++wv) {
+    const int64_t b0 = g->wave_b0[wv], b1 = g->wave_b0[wv + 1];
+    if (b1 <= b0) continue;
+    if (q4c_status st = launch_fill_idx(t, g, b0, b1, s)) return st;
+    if (q4c_status st = launch_basis_df(t, g, b0, b1, v, g->d_colexp, nullptr, 2, s, g->d_dpad)) return st;
+    const int64_t i0 = g->col_w0[wv], i1 = g->col_w0[wv + 1];
+    const int n_items = static_cast<int>(i1 - i0);
+    if (n_items == 0) continue;
+    {
+      KernelScope ks("split_prep", s);
+      split::k_item_prep<<<n_items, 128, 0, s>>>(g->view(), g->d_col_items + i0, g->d_colexp, g->d_split_mag);
+    }
+    Q4C_CUDA(cudaGetLastError());
+    const int grid = std::min(n_items, n_sm);
+    {
+      KernelScope ks("split_columns", s);
+      split::k_split_products<<<grid, split::kThreads, split::kSmemTotal, s>>>(
+          g->view(), g->d_col_items + i0, g->d_col_steps + i0, n_items,
+          reinterpret_cast<const CUtensorMap*>(g->d_tmaps), g->d_dpad, g->d_split_mag, F, nullptr, nullptr,
+          nullptr, nullptr, g->d_status);
+    }
+    Q4C_CUDA(cudaGetLastError());
+  }
+  return Q4C_OK;
 }
 
 }  // namespace q4c

@@ -205,6 +205,7 @@ extern "C" void q4c_tables_destroy(q4c_tables* t) {
   cudaFree(t->d_spn_col);
   cudaFree(t->d_spn_row);
   cudaFree(t->d_ss0);
+  cudaFree(t->d_col_coef_df);
   delete t;
 }
 
@@ -217,11 +218,22 @@ extern "C" q4c_status q4c_tables_set_columns(q4c_tables* t, const double* eps, c
     natural_spline_coefficients(y, &coef[static_cast<size_t>(k) * (n - 1) * 4]);
   }
   std::vector<double> e(eps, eps + n_tot);
+  auto split = [](double x) { const float h = static_cast<float>(x); return std::make_pair(h, static_cast<float>(x - h)); };
+  std::vector<float4> coef_df(static_cast<size_t>(n_tot) * (n - 1) * 2);
+  for (size_t iv = 0; iv < static_cast<size_t>(n_tot) * (n - 1); ++iv) {
+    const auto c0 = split(coef[4 * iv]), c1 = split(coef[4 * iv + 1]), c2 = split(coef[4 * iv + 2]),
+               c3 = split(coef[4 * iv + 3]);
+    coef_df[2 * iv] = make_float4(c0.first, c0.second, c1.first, c1.second);
+    coef_df[2 * iv + 1] = make_float4(c2.first, c2.second, c3.first, c3.second);
+  }
   cudaFree(t->d_col_eps);
   cudaFree(t->d_col_coef);
+  cudaFree(t->d_col_coef_df);
   t->d_col_eps = nullptr;
   t->d_col_coef = nullptr;
+  t->d_col_coef_df = nullptr;
   if (q4c_status st = upload(&t->d_col_eps, e)) return st;
+  if (q4c_status st = upload(&t->d_col_coef_df, coef_df)) return st;
   return upload(&t->d_col_coef, coef);
 }
 

@@ -48,11 +48,16 @@ def test_small_columns_match_oracle(case):
 
 
 def test_small_split_matches_fp64(case):
-    lib, _, _, _ = case
+    lib, _, eps, Vk = case
     ref = lib.integrate("fp64")
     got = lib.integrate("split")
     for g, r in zip(got[:5], ref[:5]):
         assert rel_fro(g, r) <= 1e-9
+    q.q4c_tables_set_columns(lib.tables, eps, Vk)
+    Fs = q.q4c_integrate_columns(lib.tables, lib.grid, lib.v, "split").cpu().numpy()
+    F64 = q.q4c_integrate_columns(lib.tables, lib.grid, lib.v, "fp64").cpu().numpy()
+    lib.grid.status()
+    assert rel_fro(Fs, F64) <= 1e-9
 
 
 def test_knot_tables_match_analytic_tables():
