@@ -296,8 +296,13 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   if (warp < kSlicers / 32) {
     // ---------------------------------------------------------- slicers
-    // thread = (point p, functions 4q..4q+3 of the step)
-    const int p = 16 * (warp >> 1) + (lane & 15), q = 2 * (warp & 1) + (lane >> 4);
+    // thread = (point p, functions 4q..4q+3 of the step); a warp takes 16
+    // points and one pair of q.  Each half warp holds points 0-7 of one q and
+    // points 8-15 of the other, so its 8-byte raw loads cover 128 distinct
+    // bytes and its 8-byte digit stores land in distinct banks of the two
+    // 8-row core matrices.
+    const int sub = (lane >> 3) & 1;
+    const int p = 16 * (warp >> 1) + 8 * (sub ^ (lane >> 4)) + (lane & 7), q = 2 * (warp & 1) + sub;
     const int dst_off = (p >> 3) * kSBO + (q >> 1) * kLBO + (p & 7) * 16 + (q & 1) * 8;
     bool ok = true;
     int g = 0;  // steps of this CTA

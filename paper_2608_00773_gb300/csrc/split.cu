@@ -234,7 +234,11 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   if (warp < kSlicers / 32) {
     // ---------------------------------------------------------- slicers
-    const int r = warp * 8 + (lane >> 2), q = lane & 3;  // row, points 4q..4q+3 of the step
+    // row, points 4q..4q+3 of the step.  A quarter warp takes one q on rows
+    // 0-7 (its 16-byte raw chunks 2q ^ row are then eight distinct banks
+    // groups) and a half warp one K-half on rows 0-7 (its 8-byte digit slots
+    // fill one 128-byte core-matrix pair without a bank conflict).
+    const int r = warp * 8 + (lane & 7), q = lane >> 3;
     // byte offsets: swizzled 16-byte chunks 2q, 2q+1 of row r in a raw box;
     // the 8-byte slot of (r, 4q) in a K-major core-matrix operand tile
     const int rc0 = r * 128 + (((2 * q) ^ (r & 7)) << 4), rc1 = r * 128 + (((2 * q + 1) ^ (r & 7)) << 4);
