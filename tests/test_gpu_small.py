@@ -72,6 +72,34 @@ def test_knot_tables_match_analytic_tables():
         assert np.abs(a - b).max() <= 1e-13 * np.abs(a).max()
 
 
+def test_small_component_of_the_64_atom_cluster():
+    """The bench's workload in the small-component basis (f shells give l~ = 4;
+    ~2x the large component's functions per batch): split within 1e-9 of FP64
+    for V, W0, SO and the per-column operator, and the spinor functions line up
+    with the large component's."""
+    from paper_2608_00773_gb300 import _build
+    from workloads import cluster64
+    _build.build()
+    wl = cluster64()
+    eps, Vk = column_operator(wl, 61)
+    ws, Q, parent, kappa = small_component(wl, Vk)
+    lib = LibCase(ws, Q)
+    assert lib.grid.info.max_nb > 175
+    ref = lib.integrate("fp64")
+    got = lib.integrate("split")
+    lib.grid.status()
+    for g, r in zip(got[:5], ref[:5]):
+        assert rel_fro(g, r) <= 1e-9
+    q.q4c_tables_set_columns(lib.tables, eps[parent], Vk[parent])
+    Fs = q.q4c_integrate_columns(lib.tables, lib.grid, lib.v, "split").cpu().numpy()
+    F64 = q.q4c_integrate_columns(lib.tables, lib.grid, lib.v, "fp64").cpu().numpy()
+    lib.grid.status()
+    assert rel_fro(Fs, F64) <= 1e-9
+    q.q4c_tables_set_kappa(lib.tables, -kappa)
+    for s, sp in enumerate(wl.species):
+        assert len(q.q4c_spinor_basis(lib.tables, s)[0]) == 2 * sp.n_fn
+
+
 def test_g_shells_of_the_large_component():
     """l = 4 as a large-component radial (the basis evaluation has no
     small-component special case): FP64 against the oracle, split against FP64."""
