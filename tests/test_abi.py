@@ -91,3 +91,33 @@ def test_no_device_fails_loudly(lib):
     with pytest.raises(q.Q4CError) as e:
         q.nao_tabulate([1], [0], [1.0])
     assert e.value.status in (2, 3)
+
+
+def test_header_is_plain_c_and_links(lib, tmp_path):
+    """include/q4c.h compiles as C99 (-pedantic-errors) and a C program links
+    against the library and gets EINVAL plus a message for a NULL descriptor;
+    no device call."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    from paper_2608_00773_gb300 import binding
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    src = tmp_path / "abi.c"
+    src.write_text(
+        "#include <stdio.h>\n#include \"q4c.h\"\n"
+        "int main(void) {\n"
+        "  q4c_tables* t = NULL;\n"
+        "  q4c_status st = nao_tabulate(NULL, &t);\n"
+        "  const char* msg = q4c_last_error();\n"
+        "  printf(\"%d %s\\n\", (int)st, msg);\n"
+        "  return (st == Q4C_EINVAL && t == NULL && msg && msg[0]) ? 0 : 1;\n"
+        "}\n")
+    exe = tmp_path / "abi"
+    libdir = os.path.dirname(binding.LIB_PATH)
+    subprocess.run([gcc, "-std=c99", "-pedantic-errors", "-Wall", "-Werror", "-I", os.path.join(root, "include"),
+                    str(src), "-o", str(exe), "-L", libdir, "-lq4c", "-Wl,-rpath," + libdir], check=True)
+    r = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stdout + r.stderr
+
