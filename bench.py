@@ -189,9 +189,21 @@ def max_over_ranks(x: float, world: int) -> float:
 # the oracle on a bounded sample (cpu_baseline and the reference arm)
 # ---------------------------------------------------------------------------
 
-def oracle_step_sample(wl, stride: int):
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def oracle_step_sample(wl, stride: int, threads: int = 1):
     """One oracle step (matrices, density, adjoint) on the raw grid points with
-    id % stride == 0; returns (seconds, fraction of the workload)."""
+    id % stride == 0, the points dealt round-robin to `threads` parts that run
+    concurrently (the oracle's C calls release the GIL; each part's sums are
+    its own, as in a split of the grid); returns (wall seconds, fraction of
+    the workload)."""
+    from concurrent.futures import ThreadPoolExecutor
+
     import oracle as O
     from workloads import ADJOINT_KINDS, fill_pattern, potential
     xyz, w, ids = O.grid(wl, stride=stride)
@@ -200,10 +212,20 @@ def oracle_step_sample(wl, stride: int):
     v = potential(xyz, wl)
     P = fill_pattern(pat.blk_ptr, pat.blk_col, pat.blk_off, wl.nf_of_atom, 11, "P")
     G = [fill_pattern(pat.blk_ptr, pat.blk_col, pat.blk_off, wl.nf_of_atom, 12, k, a) for k, a in ADJOINT_KINDS]
+    parts = [np.arange(k, len(w), threads) for k in range(threads)]  # interleaved: even cost per thread
+
+    def chunk(k):
+        i = parts[k]
+        ob.matrix_blocks(xyz[i], w[i], v[i], pat)
+        ob.density(xyz[i], P, pat)
+        ob.adjoint(xyz[i], w[i], G, pat)
+
     t0 = time.perf_counter()
-    ob.matrix_blocks(xyz, w, v, pat)
-    ob.density(xyz, P, pat)
-    ob.adjoint(xyz, w, G, pat)
+    if threads == 1:
+        chunk(0)
+    else:
+        with ThreadPoolExecutor(max_workers=threads) as ex:
+            list(ex.map(chunk, range(threads)))
     return time.perf_counter() - t0, 1.0 / stride
 
 
@@ -219,21 +241,22 @@ def run_reference(args, wl):
     if rank != 0:
         return
     flops = workload_flops(wl)
+    cores = host_cores()
     times = []
     for _ in range(args.warmup):
-        oracle_step_sample(wl, args.ref_stride)
+        oracle_step_sample(wl, args.ref_stride, cores)
     for _ in range(args.steps):
-        t, frac = oracle_step_sample(wl, args.ref_stride)
+        t, frac = oracle_step_sample(wl, args.ref_stride, cores)
         times.append(t / frac)
     t_step = statistics.mean(times)
     val = flops / t_step / 1e12
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "TFLOP/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": wl.name, "note": "oracle (plain FP64 C, one host core) on a uniform "
+            "config": {"workload": wl.name, "note": f"oracle (plain FP64 C, {cores} host threads) on a uniform "
                        f"1/{args.ref_stride} sample of the raw grid, time scaled to the full workload"},
-            "cpu_baseline": {"value": val, "unit": "TFLOP/s", "cores": 1, "kind": "oracle",
-                             "sample": f"raw grid ids divisible by {args.ref_stride}"},
+            "cpu_baseline": {"value": val, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
+                             "sample": f"raw grid ids divisible by {args.ref_stride}, split over {cores} threads"},
             "e2e": {"value": val, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
@@ -276,8 +299,9 @@ def main():
                     help="FP64-path steps timed after the split run for the speedup (0: skip)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="cluster64", choices=["cluster64", "water"])
-    ap.add_argument("--cpu-stride", type=int, default=4)
-    ap.add_argument("--ref-stride", type=int, default=61)
+    ap.add_argument("--cpu-stride", type=int, default=16, help="one-core sample of the cpu baseline")
+    ap.add_argument("--cpu-stride-all", type=int, default=2, help="all-core sample of the cpu baseline")
+    ap.add_argument("--ref-stride", type=int, default=7)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--print-source-hash", action="store_true",
                     help="print the sha256 of each profiled kernel's sources and exit")
@@ -362,6 +386,7 @@ def main():
         clocks.stop_window()
     barrier(world)
     q.profile(False)
+    grid.status()  # raises if a bounded wait of a tensor kernel ran out (incomplete outputs)
     per_step = [a.elapsed_time(b) for a, b in ev]
     t_ms = max_over_ranks(statistics.mean(per_step), world)
     kern = {}
@@ -382,8 +407,8 @@ def main():
     if dom_name in ("split_products", "split_backward", "split_density"):
         work = {"split_products": "integrate", "split_backward": "backward", "split_density": "density"}[dom_name]
         achieved = fl[work] * S_PAIRS * args.steps / (dom_ms * 1e-3) / 1e12
-        roof = {"bound": "tensor", "achieved": achieved, "peak": peaks["bf16_tflops_sustained"],
-                "unit": "TFLOP/s", "peak_source": f"{peak_src} bf16 sustained (of measured)",
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peaks["bf16_tflops"],
+                "unit": "TFLOP/s", "peak_source": f"{peak_src} bf16 burst (of {peak_src})",
                 "work": f"algorithmic FLOPs of {work} x {S_PAIRS} slice pairs"}
     elif dom_name in ("products_fp64", "density_fp64", "backward_fp64"):
         work = {"products_fp64": "integrate", "density_fp64": "density", "backward_fp64": "backward"}[dom_name]
@@ -430,11 +455,29 @@ def main():
     for _ in range(args.steps):
         e2e_step()
     t_e2e = max_over_ranks((time.perf_counter() - t0) / args.steps, world)
+    grid.status()
     e2e = {"value": world * F_step / t_e2e / 1e12, "unit": "TFLOP/s", "h2d_bytes_per_step": bi,
            "d2h_bytes_per_step": bo}
 
-    # ---- FP64 comparison path and split error (reported beside the value)
+    # ---- the integration alone (q4c_integrate, device time, L2 flushed)
     extra = {}
+    evi = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for a_, b_ in evi:
+        flush.zero_()
+        a_.record(stream)
+        q.q4c_integrate(tables, grid, v, phase_prec["integrate"], out=mats, stream=stream)
+        b_.record(stream)
+    torch.cuda.synchronize()
+    grid.status()
+    t_int = max_over_ranks(statistics.mean(a_.elapsed_time(b_) for a_, b_ in evi), world)
+    tf_int = world * fl["integrate"] / (t_int * 1e-3) / 1e12
+    extra["integration_only"] = {
+        "what": "q4c_integrate alone (V, W0, SO x,y,z and the SS spinor blocks), algorithmic 14 sum n_p n_b^2",
+        "ms_per_call": t_int, "tflops": tf_int,
+        "tensor_frac": tf_int * S_PAIRS / peaks["bf16_tflops"] if phase_prec["integrate"] == "split" else None,
+        "tensor_frac_note": f"x {S_PAIRS} slice pairs / {peak_src} bf16 burst, whole call incl. basis and scatter"}
+
+    # ---- FP64 comparison path and split error (reported beside the value)
     if prec == "split" and args.fp64_steps > 0:
         ref = [torch.empty_like(m) for m in mats[:5]]
         q.q4c_integrate(tables, grid, v, "fp64", out=ref + [None], stream=stream)
@@ -496,10 +539,15 @@ def main():
         return
     cpu = None
     if not args.no_cpu_baseline and world == 1:
-        t_cpu, frac = oracle_step_sample(wl, args.cpu_stride)
-        cpu = {"value": F_step * frac / t_cpu / 1e12, "unit": "TFLOP/s", "cores": 1, "kind": "oracle",
-               "sample": f"raw grid ids divisible by {args.cpu_stride} ({frac:.4f} of the workload), "
-                         f"{t_cpu:.1f} s of one host core"}
+        cores = host_cores()
+        t1, f1 = oracle_step_sample(wl, args.cpu_stride, 1)
+        tn, fn_ = oracle_step_sample(wl, args.cpu_stride_all, cores)
+        cpu = {"value": F_step * fn_ / tn / 1e12, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
+               "sample": f"raw grid ids divisible by {args.cpu_stride_all} ({fn_:.4f} of the workload) split over "
+                         f"{cores} threads, {tn:.1f} s wall",
+               "single_core": {"value": F_step * f1 / t1 / 1e12, "cores": 1,
+                               "sample": f"raw grid ids divisible by {args.cpu_stride} ({f1:.4f} of the workload), "
+                                         f"{t1:.1f} s of one core"}}
     line = {
         "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_ms, "higher_is_better": True, "scaling": "weak",

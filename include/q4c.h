@@ -391,7 +391,9 @@ Q4C_API q4c_status q4c_integrate_backward(const q4c_tables* tables, const q4c_gr
  * batch's tiles (4 n_b ceil8(n_p) doubles) exceed 64 MiB.  All calls share
  * the array: calls that overlap on the GPU race and must be serialised by
  * the caller.  The first call on each device looks up the array's device
- * address; make that first call before any stream capture. */
+ * address and keeps it for the rest of the process; make that first call
+ * before any stream capture, and do not call this entry point again on a
+ * device whose primary context the process has destroyed (cudaDeviceReset). */
 Q4C_API q4c_status q4c_integrate_noalloc(const q4c_tables* tables, const q4c_grid* grid, const double* v_dev,
                                          const q4c_matrices* out, q4c_stream stream);
 
@@ -408,6 +410,18 @@ Q4C_API q4c_status q4c_basis_eval(const q4c_tables* tables, const q4c_grid* grid
  * Q4C_OK.  Such a kernel stops early instead of hanging, so its outputs are
  * incomplete. */
 Q4C_API q4c_status q4c_grid_status(const q4c_grid* grid, q4c_stream stream);
+
+/* Limit, in nanoseconds of wall clock, of each bounded wait of the working
+ * roles of the tensor-core kernels (the split path), for kernels launched
+ * after the call, from any thread, on any device; 0 restores the default of
+ * one second.  A wait that runs out sets the grid's status flag (reported by
+ * q4c_grid_status) and stops the kernel early, so its outputs are
+ * incomplete; the waits with which a stopping kernel drains its own copies
+ * and tensor-core operations keep the fixed one-second limit.  Meant for
+ * tests of the failure path (a tiny limit makes the first wait that is not
+ * already satisfied give up) and for callers that want a stall reported
+ * sooner.  Always Q4C_OK.  Not in the paper: a library control. */
+Q4C_API q4c_status q4c_set_wait_limit_ns(uint64_t ns);
 
 /* Kernel instrumentation.  q4c_profile(1) makes every later compute call
  * record a pair of CUDA events on its stream around each kernel it launches

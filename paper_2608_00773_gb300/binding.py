@@ -27,7 +27,7 @@ EXPORTS = ["nao_tabulate", "nao_tabulate_knots", "q4c_tables_destroy", "q4c_tabl
            "q4c_grid_get_info", "q4c_grid_export", "q4c_grid_export_shifts", "q4c_grid_kpattern", "q4c_kfold", "q4c_grid_points", "q4c_integrate", "q4c_density", "q4c_density_full",
            "q4c_spinor_basis", "q4c_spinor_transform", "q4c_spinor_density_matrices", "q4c_grid_batch_spinors",
            "q4c_tables_set_columns", "q4c_integrate_columns", "q4c_tables_set_kappa", "q4c_spinor_nnz",
-           "q4c_integrate_backward", "q4c_integrate_noalloc", "q4c_basis_eval", "q4c_grid_status", "q4c_profile", "q4c_profile_read",
+           "q4c_integrate_backward", "q4c_integrate_noalloc", "q4c_basis_eval", "q4c_grid_status", "q4c_set_wait_limit_ns", "q4c_profile", "q4c_profile_read",
            "q4c_last_error"]
 
 
@@ -105,6 +105,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     L.q4c_integrate_noalloc.argtypes = [vp, vp, vp, C.POINTER(Matrices), vp]
     L.q4c_basis_eval.argtypes = [vp, vp, i64, vp, vp, vp, vp]
     L.q4c_grid_status.argtypes = [vp, vp]
+    L.q4c_set_wait_limit_ns.argtypes = [C.c_uint64]
     L.q4c_profile.argtypes = [i32]
     L.q4c_profile_read.argtypes = [C.c_char_p, C.POINTER(C.c_double), C.POINTER(i64)]
     L.q4c_last_error.restype = C.c_char_p
@@ -409,6 +410,11 @@ def q4c_basis_eval(tables: Tables, grid: Grid, xyz, stream=None):
     return phi, grad
 
 
+def q4c_set_wait_limit_ns(ns: int):
+    """Limit of the tensor kernels' bounded work waits for later launches (0: 1 s)."""
+    _check(load().q4c_set_wait_limit_ns(int(ns)))
+
+
 def profile(enable: bool):
     """Record CUDA events around every kernel of later compute calls."""
     _check(load().q4c_profile(1 if enable else 0))
@@ -436,6 +442,8 @@ def _make_function():
         def forward(ctx, v, tables, grid, prec):
             ctx.tables, ctx.grid, ctx.prec = tables, grid, prec
             outs = q4c_integrate(tables, grid, v.contiguous(), prec)[:5]
+            if _prec(prec) == Q4C_SPLIT:
+                grid.status()  # a bounded wait that ran out leaves incomplete outputs: raise
             return tuple(outs)
 
         @staticmethod
@@ -443,7 +451,10 @@ def _make_function():
             G = [None if g is None else g.contiguous() for g in (gV, gW, gx, gy, gz)]
             if all(g is None for g in G):
                 return None, None, None, None
-            return q4c_integrate_backward(ctx.tables, ctx.grid, G, ctx.prec), None, None, None
+            dv = q4c_integrate_backward(ctx.tables, ctx.grid, G, ctx.prec)
+            if _prec(ctx.prec) == Q4C_SPLIT:
+                ctx.grid.status()
+            return dv, None, None, None
 
     return Q4CIntegrate
 
@@ -452,7 +463,9 @@ _fn = None
 
 
 def integrate(v, tables: Tables, grid: Grid, prec="fp64"):
-    """Differentiable integration: returns (V, W0, SOx, SOy, SOz)."""
+    """Differentiable integration: returns (V, W0, SOx, SOy, SOz).  On the
+    split path forward and backward synchronise and raise Q4CError
+    (Q4C_ETIMEOUT) if a bounded wait of a tensor kernel ran out."""
     global _fn
     if _fn is None:
         _fn = _make_function()

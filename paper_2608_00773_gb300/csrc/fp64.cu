@@ -19,8 +19,11 @@ __device__ __forceinline__ int binexp(double x) {  // |x| < 2^binexp(x), x != 0
   return E - 1022;
 }
 constexpr int kNoExp = -30000;
+// scr_base: subtracted from the batch offsets (the first offset of a sub-wave
+// whose tiles start at `scratch`; 0 for the grid's own workspace)
 __global__ void k_basis_tiles(DevBasis B, DevGrid G, int64_t b0, const int64_t* __restrict__ scr_off,
-                              double* __restrict__ scratch, const double* __restrict__ v, int* __restrict__ colexp) {
+                              int64_t scr_base, double* __restrict__ scratch, const double* __restrict__ v,
+                              int* __restrict__ colexp) {
   extern __shared__ int s_exp[];  // [8][nb] when colexp != NULL
   const int64_t b = b0 + blockIdx.x;
   const int64_t p0 = G.pt_ptr[b];
@@ -28,7 +31,7 @@ __global__ void k_basis_tiles(DevBasis B, DevGrid G, int64_t b0, const int64_t* 
   const int ldp = (np + 7) & ~7;
   const int a0 = G.bat_atom_ptr[b], na = G.bat_atom_ptr[b + 1] - a0;
   const int nb = static_cast<int>(G.bat_fn_ptr[b + 1] - G.bat_fn_ptr[b]);
-  double* base = scratch + scr_off[b];
+  double* base = scratch + (scr_off[b] - scr_base);
   const int64_t plane = static_cast<int64_t>(nb) * ldp;
   if (colexp) {
     for (int i = threadIdx.x; i < 8 * nb; i += blockDim.x) s_exp[i] = kNoExp;
@@ -76,7 +79,7 @@ q4c_status launch_basis_tiles(const q4c_tables* t, const q4c_grid* g, int64_t b0
   if (smem > 48 * 1024)
     Q4C_CUDA(cudaFuncSetAttribute(k_basis_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
   KernelScope ks("basis", s);
-  k_basis_tiles<<<static_cast<unsigned>(b1 - b0), 256, smem, s>>>(t->view(), g->view(), b0, g->d_scr_off,
+  k_basis_tiles<<<static_cast<unsigned>(b1 - b0), 256, smem, s>>>(t->view(), g->view(), b0, g->d_scr_off, 0,
                                                                    g->d_scratch, v, colexp);
   Q4C_CUDA(cudaGetLastError());
   return Q4C_OK;
@@ -94,7 +97,7 @@ __device__ __forceinline__ int local_nf(const DevBasis& B, const DevGrid& G, int
 constexpr int kT = 32, kK = 16;
 __global__ void __launch_bounds__(256) k_products_fp64(DevBasis B, DevGrid G, const int4* __restrict__ tiles,
                                                        int64_t t0, const int64_t* __restrict__ scr_off,
-                                                       const double* __restrict__ scratch,
+                                                       int64_t scr_base, const double* __restrict__ scratch,
                                                        const double* __restrict__ v, double* V, double* W0,
                                                        double* SOx, double* SOy, double* SOz) {
   __shared__ double sa[4][kK][kT];  // D-scaled i side
@@ -108,7 +111,7 @@ __global__ void __launch_bounds__(256) k_products_fp64(DevBasis B, DevGrid G, co
   const int ldp = (np + 7) & ~7;
   const int nb = static_cast<int>(G.bat_fn_ptr[b + 1] - G.bat_fn_ptr[b]);
   const int64_t plane = static_cast<int64_t>(nb) * ldp;
-  const double* base = scratch + scr_off[b];
+  const double* base = scratch + (scr_off[b] - scr_base);
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   double acc[2][2][5];
 #pragma unroll
@@ -270,7 +273,7 @@ q4c_status integrate_fp64(const q4c_tables* t, const q4c_grid* g, const double* 
     const int64_t t0 = g->wave_t0[wv], t1 = g->wave_t0[wv + 1];
     if (t1 > t0) {
       KernelScope ks("products_fp64", s);
-      k_products_fp64<<<static_cast<unsigned>(t1 - t0), 256, 0, s>>>(B, G, g->d_tiles, t0, g->d_scr_off,
+      k_products_fp64<<<static_cast<unsigned>(t1 - t0), 256, 0, s>>>(B, G, g->d_tiles, t0, g->d_scr_off, 0,
                                                                        g->d_scratch, v, out->V, out->W0, out->SOx,
                                                                        out->SOy, out->SOz);
       Q4C_CUDA(cudaGetLastError());

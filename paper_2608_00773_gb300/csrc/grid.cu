@@ -166,6 +166,7 @@ DevGrid q4c_grid::view() const {
   v.bat_idx_ptr = d_bat_idx_ptr;
   v.bat_idx = d_bat_idx;
   v.n_atoms = n_atoms;
+  v.wait_ns = q4c::work_wait_limit_ns();
   return v;
 }
 
@@ -1036,6 +1037,17 @@ extern "C" q4c_status q4c_grid_points(const q4c_grid* g, const double** xyz_dev,
   if (xyz_dev) *xyz_dev = g->d_xyz;
   if (w_dev) *w_dev = g->d_w;
   if (n_points) *n_points = g->n_pts;
+  return Q4C_OK;
+}
+
+namespace {
+std::atomic<unsigned long long> g_work_wait_ns{1000000000ull};
+}  // namespace
+
+unsigned long long q4c::work_wait_limit_ns() { return g_work_wait_ns.load(std::memory_order_relaxed); }
+
+extern "C" q4c_status q4c_set_wait_limit_ns(uint64_t ns) {
+  g_work_wait_ns.store(ns ? static_cast<unsigned long long>(ns) : 1000000000ull, std::memory_order_relaxed);
   return Q4C_OK;
 }
 

@@ -88,7 +88,11 @@ struct DevGrid {
   const int64_t* bat_idx_ptr;   // [n_batches+1] into bat_idx (n_b^2 per batch)
   int* bat_idx;                 // value offset of element (i, j) of the batch, or -1 (one wave, filled per call)
   int n_atoms;
+  unsigned long long wait_ns;   // limit of the tensor kernels' bounded work waits (q4c_set_wait_limit_ns)
 };
+
+// the work-wait limit that q4c_set_wait_limit_ns last set (1 s by default)
+unsigned long long work_wait_limit_ns();
 
 }  // namespace q4c
 

@@ -19,8 +19,10 @@
 //
 // Host code cannot use the array's name as a device address; the first call
 // on each device resolves it with cudaGetSymbolAddress (with that device
-// current) and caches it.  That first call should therefore come before any
-// stream capture.
+// current) and caches it for the rest of the process.  That first call should
+// therefore come before any stream capture, and a process that destroys a
+// device's primary context (cudaDeviceReset) must not call this entry point
+// on that device again: the cached address belonged to the old context.
 #include <cstdint>
 #include <mutex>
 
@@ -36,9 +38,11 @@ static __device__ __align__(256) double g_noalloc_scratch[kNoAllocDoubles];
 
 // kernels of the FP64 path (fp64.cu)
 __global__ void k_basis_tiles(DevBasis B, DevGrid G, int64_t b0, const int64_t* __restrict__ scr_off,
-                              double* __restrict__ scratch, const double* __restrict__ v, int* __restrict__ colexp);
+                              int64_t scr_base, double* __restrict__ scratch, const double* __restrict__ v,
+                              int* __restrict__ colexp);
 __global__ void k_products_fp64(DevBasis B, DevGrid G, const int4* __restrict__ tiles, int64_t t0,
-                                const int64_t* __restrict__ scr_off, const double* __restrict__ scratch,
+                                const int64_t* __restrict__ scr_off, int64_t scr_base,
+                                const double* __restrict__ scratch,
                                 const double* __restrict__ v, double* V, double* W0, double* SOx, double* SOy,
                                 double* SOz);
 
@@ -94,8 +98,8 @@ extern "C" q4c_status q4c_integrate_noalloc(const q4c_tables* t, const q4c_grid*
   const DevBasis B = t->view();
   const DevGrid G = g->view();
   // the grid's own waves keep per-batch tile offsets cumulative in batch
-  // order; sub-waves of them that fit the static array reuse those offsets
-  // shifted by the sub-wave's first offset
+  // order; sub-waves of them that fit the static array reuse those offsets,
+  // and the kernels subtract the sub-wave's first offset (base)
   int64_t tile = 0;
   for (size_t wv = 0; wv + 1 < g->wave_b0.size(); ++wv) {
     int64_t b = g->wave_b0[wv];
@@ -112,18 +116,16 @@ extern "C" q4c_status q4c_integrate_noalloc(const q4c_tables* t, const q4c_grid*
         tile += nt * (nt + 1) / 2;
         ++b;
       }
-      double* shifted = reinterpret_cast<double*>(reinterpret_cast<uintptr_t>(ws) -
-                                                  static_cast<uintptr_t>(base) * sizeof(double));
       {
         KernelScope ks("basis", s);
-        k_basis_tiles<<<static_cast<unsigned>(b - b_first), 256, 0, s>>>(B, G, b_first, g->d_scr_off, shifted,
-                                                                         nullptr, nullptr);
+        k_basis_tiles<<<static_cast<unsigned>(b - b_first), 256, 0, s>>>(B, G, b_first, g->d_scr_off, base,
+                                                                         ws, nullptr, nullptr);
       }
       Q4C_CUDA(cudaGetLastError());
       if (tile > t_first) {
         KernelScope ks("products_fp64", s);
         k_products_fp64<<<static_cast<unsigned>(tile - t_first), 256, 0, s>>>(
-            B, G, g->d_tiles, t_first, g->d_scr_off, shifted, v, out->V, out->W0, out->SOx, out->SOy, out->SOz);
+            B, G, g->d_tiles, t_first, g->d_scr_off, base, ws, v, out->V, out->W0, out->SOx, out->SOy, out->SOz);
       }
       Q4C_CUDA(cudaGetLastError());
     }

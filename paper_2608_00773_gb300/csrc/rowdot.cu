@@ -52,7 +52,8 @@ constexpr int kSmemRaw = 0;
 constexpr int kSmemStages = kSmemRaw + kRaw * kRawStage;
 constexpr int kSmemY = kSmemStages + kStages * kStage;  // [4][64] double partials per point
 constexpr int kSmemBar = kSmemY + 4 * kTile * 8;
-constexpr int kNumBars = 2 * kStages + 5 + 2 * kRaw;  // full, empty, accfull[2], accempty[2], drain, raw full/empty
+// full, empty, accfull[2], accempty[2], drain, raw full/empty, G' copy full
+constexpr int kNumBars = 3 * kStages + 5 + 2 * kRaw;
 constexpr int kSmemTotal = kSmemBar + kNumBars * 8 + 16;
 constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kSetCols = 256;
@@ -218,7 +219,8 @@ struct StepIter {
 //               counts the bytes; raw_empty hands a stage back);
 //   warps 0-7   per step: thread (point, 4 functions) reads its raw values,
 //               waits empty[stage]; one thread starts the bulk copy of the
-//               step's G' digits into the stage (expect_tx on full[stage]);
+//               step's G' digits into the stage (its bytes complete
+//               gfull[stage]);
 //               all slice their F values, store the digits, arrive on
 //               full[stage] and hand the raw stage back;
 //   warp 16     (one thread) issues the six MMAs per step into the group's
@@ -255,6 +257,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   const uint32_t drain_bar = bar0 + 8u * (2 * kStages + 4);
   auto rawfull_bar = [&](int rs) { return bar0 + 8u * (2 * kStages + 5 + rs); };
   auto rawempty_bar = [&](int rs) { return bar0 + 8u * (2 * kStages + 5 + kRaw + rs); };
+  auto gfull_bar = [&](int st) { return bar0 + 8u * (2 * kStages + 5 + 2 * kRaw + st); };
   // the products whose matrix is present, in order, 3 bits each (registers only)
   unsigned plist = 0;
   int n_prod = 0;
@@ -281,6 +284,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_init(rawfull_bar(rs), 1);
       mbar_init(rawempty_bar(rs), kSlicers / 32);
     }
+    for (int st = 0; st < kStages; ++st) mbar_init(gfull_bar(st), 1);
     *s_abort = 0;
   }
   if (warp == kMmaWarp) {
@@ -315,7 +319,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       StepIter it;
       for (int s = 0; s < n_steps; ++s, ++g) {
         const int rs = g % kRaw, st = g % kStages;
-        if (!mbar_wait_abort(rawfull_bar(rs), (g / kRaw) & 1, s_abort, status)) {
+        if (!mbar_wait_abort(rawfull_bar(rs), (g / kRaw) & 1, s_abort, status, G.wait_ns)) {
           ok = false;
           break;
         }
@@ -330,7 +334,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         float2 x[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) x[k] = *reinterpret_cast<const float2*>(raw + (4 * q + k) * (kTile * 8) + p * 8);
-        if (!mbar_wait_abort(empty_bar(st), ((g / kStages) & 1) ^ 1, s_abort, status)) {
+        if (!mbar_wait_abort(empty_bar(st), ((g / kStages) & 1) ^ 1, s_abort, status, G.wait_ns)) {
           ok = false;
           break;
         }
@@ -340,8 +344,8 @@ __global__ void __launch_bounds__(kThreads, 1)
           const unsigned char* src =
               gblk + (static_cast<int64_t>(P.gm) * I.n_jt * I.n_ic + static_cast<int64_t>(it.jt) * I.n_ic + it.ic) *
                          kBlockB;
-          expect_tx(full_bar(st), kBlockB);
-          bulk_copy(smem_u32(sA + kStageA), src, kBlockB, full_bar(st));
+          arrive_expect_tx(gfull_bar(st), kBlockB);
+          bulk_copy(smem_u32(sA + kStageA), src, kBlockB, gfull_bar(st));
         }
         const float m = P.qf == 0 ? m0 : P.qf == 1 ? m1 : P.qf == 2 ? m2 : m3;
         float d0[kSlices], d1[kSlices], d2[kSlices], d3[kSlices];
@@ -369,6 +373,11 @@ __global__ void __launch_bounds__(kThreads, 1)
       // agree on stopping (a wait that gave up in one warp ends every role)
       if (bar_red_or(1, kSlicers, !ok || *s_abort)) break;
     }
+    // no G' copy outlives the CTA: thread 0 issued one per completed step;
+    // the last kStages of them may not have been consumed after an abort
+    if (tid == 0)
+      for (int h = max(0, g - kStages); h < g; ++h)
+        (void)mbar_wait(gfull_bar(h % kStages), (h / kStages) & 1, status);
   } else if (warp == kProdWarp) {
     // ---------------------------------------------------------- TMA producer
     if (lane == 0) {
@@ -382,7 +391,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         StepIter it;
         for (int s = 0; s < n_steps; ++s, ++g) {
           const int rs = g % kRaw;
-          if (!mbar_wait_abort(rawempty_bar(rs), ((g / kRaw) & 1) ^ 1, s_abort, status, 32)) {
+          if (!mbar_wait_abort(rawempty_bar(rs), ((g / kRaw) & 1) ^ 1, s_abort, status, G.wait_ns, 32)) {
             ok = false;
             break;
           }
@@ -406,7 +415,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const ItemInfo I = item_info(G, items[n]);
         for (int grp = 0; grp < I.n_jt * n_prod && ok; ++grp, ++k) {
           const int set = k & 1;
-          if (!mbar_wait_abort(accempty_bar(set), ((k >> 1) & 1) ^ 1, s_abort, status, 64)) {
+          if (!mbar_wait_abort(accempty_bar(set), ((k >> 1) & 1) ^ 1, s_abort, status, G.wait_ns, 64)) {
             ok = false;
             break;
           }
@@ -414,7 +423,8 @@ __global__ void __launch_bounds__(kThreads, 1)
           const uint32_t t0 = tmem + set * kSetCols;
           for (int ic = 0; ic < I.n_ic; ++ic, ++g) {
             const int st = g % kStages;
-            if (!mbar_wait_abort(full_bar(st), (g / kStages) & 1, s_abort, status, 32)) {
+            if (!mbar_wait_abort(full_bar(st), (g / kStages) & 1, s_abort, status, G.wait_ns, 32) ||
+                !mbar_wait_abort(gfull_bar(st), (g / kStages) & 1, s_abort, status, G.wait_ns, 32)) {
               ok = false;
               break;
             }
@@ -467,7 +477,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         };
         float2 Rc[8], Rn[8];
         if (eg * 8 < N) load_R(eg * 8, Rc);
-        ok = mbar_wait_abort(accfull_bar(set), (k >> 1) & 1, s_abort, status, 256);
+        ok = mbar_wait_abort(accfull_bar(set), (k >> 1) & 1, s_abort, status, G.wait_ns, 256);
         if (bar_red_or(2, kEpiThreads, !ok)) {
           ok = false;
           break;

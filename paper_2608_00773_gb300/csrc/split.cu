@@ -252,7 +252,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       bool ok = true;
       for (int s = 0; s < n_steps; ++s, ++g) {
         const int rs = g % kRaw, st = g % kStages;
-        if (!mbar_wait_abort(rawfull_bar(rs), (g / kRaw) & 1, s_abort, status)) {
+        if (!mbar_wait_abort(rawfull_bar(rs), (g / kRaw) & 1, s_abort, status, G.wait_ns)) {
           ok = false;
           break;
         }
@@ -264,7 +264,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const float4 a01 = lds128(raw + rc0), a23 = lds128(raw + rc1);
         const float4 b01 = lds128(raw + kRawTile + rc0), b23 = lds128(raw + kRawTile + rc1);
         const float4 d01 = lds128(raw + kRawD + q * 32), d23 = lds128(raw + kRawD + q * 32 + 16);
-        if (!mbar_wait_abort(empty_bar(st), ((g / kStages) & 1) ^ 1, s_abort, status)) {
+        if (!mbar_wait_abort(empty_bar(st), ((g / kStages) & 1) ^ 1, s_abort, status, G.wait_ns)) {
           ok = false;
           break;
         }
@@ -319,7 +319,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         bool ok = true;
         for (int s = 0; s < n_steps; ++s, ++g) {
           const int rs = g % kRaw;
-          if (!mbar_wait_abort(rawempty_bar(rs), ((g / kRaw) & 1) ^ 1, s_abort, status, 32)) {
+          if (!mbar_wait_abort(rawempty_bar(rs), ((g / kRaw) & 1) ^ 1, s_abort, status, G.wait_ns, 32)) {
             ok = false;
             break;
           }
@@ -346,13 +346,13 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int n = blockIdx.x; n < n_items; n += gridDim.x, ++k) {
         const int n_steps = steps[n];
         const int set = k & 1;
-        if (!mbar_wait_abort(accempty_bar(set), ((k >> 1) & 1) ^ 1, s_abort, status, 64)) break;
+        if (!mbar_wait_abort(accempty_bar(set), ((k >> 1) & 1) ^ 1, s_abort, status, G.wait_ns, 64)) break;
         tc_fence_after();
         const uint32_t t0 = tmem + set * kSetCols;
         bool ok = true;
         for (int s = 0; s < n_steps; ++s, ++g) {
           const int st = g % kStages;
-          if (!mbar_wait_abort(full_bar(st), (g / kStages) & 1, s_abort, status, 32)) {
+          if (!mbar_wait_abort(full_bar(st), (g / kStages) & 1, s_abort, status, G.wait_ns, 32)) {
             ok = false;
             break;
           }
@@ -378,7 +378,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     int k = 0;
     for (int n = blockIdx.x; n < n_items; n += gridDim.x, ++k) {
       const int set = k & 1;
-      bool ok = mbar_wait_abort(accfull_bar(set), (k >> 1) & 1, s_abort, status, 256);
+      bool ok = mbar_wait_abort(accfull_bar(set), (k >> 1) & 1, s_abort, status, G.wait_ns, 256);
       if (bar_red_or(2, kEpiThreads, !ok)) break;
       tc_fence_after();
       const int4 item = items[n];

@@ -12,7 +12,7 @@ namespace tc {
 
 constexpr int kSlices = 6;
 constexpr int kLBO = 128;                         // core matrices adjacent in K
-constexpr uint64_t kWaitLimitNs = 1000000000ull;  // 1 s of wall clock per wait
+constexpr uint64_t kWaitLimitNs = 1000000000ull;  // 1 s of wall clock per drain wait
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -116,19 +116,21 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, unsigne
   return false;
 }
 
-// bounded wait that also gives up as soon as another role of the CTA has
-// set *abort (a role that times out sets it and the status bit)
+// bounded wait of a working role (limit_ns of wall clock, the grid's work
+// wait limit) that also gives up as soon as another role of the CTA has set
+// *abort (a role that times out sets it and the status bit); the drain waits
+// before a CTA exits keep the fixed 1 s limit of mbar_wait
 // (sleep_ns > 0: back off between polls, for roles whose waits are long and
 // whose polling would take issue slots from the working warps)
 __device__ __forceinline__ bool mbar_wait_abort(uint32_t bar, uint32_t parity, volatile int* abort,
-                                                unsigned* status, unsigned sleep_ns = 0) {
+                                                unsigned* status, uint64_t limit_ns, unsigned sleep_ns = 0) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = global_ns();
   while (true) {
     if (sleep_ns) __nanosleep(sleep_ns);
     if (mbar_try_wait(bar, parity)) return true;
     if (*abort) return false;
-    if (global_ns() - t0 > kWaitLimitNs) {
+    if (global_ns() - t0 > limit_ns) {
       *abort = 1;
       atomicOr(status, 1u);
       return false;

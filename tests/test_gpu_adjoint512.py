@@ -1,8 +1,9 @@
 """The adjoint at the 512-atom configuration (~6,400 functions, 20M raw grid
 points, batches <= 128): dL/dv on every point through the autograd function,
-checked at sampled points against the oracle (its own Becke weights and
-basis at those points), by central differences of L (L is linear in v, so
-a large step is exact up to rounding), and along a random direction."""
+checked at sampled points against the oracle (points, Becke weights and
+basis of its own grid, matched by raw id), by central differences of L (L is
+linear in v, so a large step is exact up to rounding), and along a random
+direction."""
 import numpy as np
 import pytest
 
@@ -56,26 +57,21 @@ def test_autograd_equals_backward_and_oracle_samples(big):
     g_direct = q.q4c_integrate_backward(tables, grid, G, "split").cpu().numpy()
     grid.status()
     assert np.array_equal(g_auto, g_direct)
-    # the oracle at 64 sampled points: its own Becke weights there and its own basis
-    rng = np.random.default_rng(2004)
-    idx = rng.choice(len(ex["w"]), 64, replace=False)
-    ppa = wl.n_rad * wl.n_theta * wl.n_phi
-    owner = ex["point_id"][idx] // ppa
+    # the oracle at 64 sampled points of its own grid (its own coordinates,
+    # Becke weights and basis), matched to the library's points by raw id
     ob = O.OracleBasis(wl)
     pat = ob.pattern()
     assert np.array_equal(pat.blk_off, ex["blk_off"])
-    w_orc = np.array([O.becke_weight(wl.xyz, int(a), ex["xyz"][i], wl.r_nb) for i, a in zip(idx, owner)])
-    # base weights (radial x angular) are the library's w / its Becke factor; compare
-    # the ratio structure instead: w_lib / p_orc is a product-grid weight, the same
-    # for every point of one (shell, theta) pair
-    shell_theta = (ex["point_id"][idx] % ppa) // wl.n_phi
-    base = ex["w"][idx] / w_orc
-    r, wr = O.radial_shells(wl.n_rad, wl.R)
-    ct, wt = O.gauss_legendre(wl.n_theta)
-    ref_base = wr[shell_theta // wl.n_theta] * wt[shell_theta % wl.n_theta] * 2 * np.pi / wl.n_phi
-    assert np.allclose(base, ref_base, rtol=1e-12, atol=0)
-    gref = ob.adjoint(ex["xyz"][idx], ex["w"][idx], G_h, pat)
-    err = np.abs(g_direct[idx] - gref).max() / np.abs(gref).max()
+    oxyz, ow, oids = O.grid(wl, stride=9973)  # a uniform ~2,000-point sample of the raw grid
+    pos = {int(p): k for k, p in enumerate(ex["point_id"])}
+    both = np.array([k for k, i in enumerate(oids) if int(i) in pos])
+    assert len(both) >= 64
+    rng = np.random.default_rng(2004)
+    sel = np.sort(rng.choice(both, 64, replace=False))
+    li = np.array([pos[int(i)] for i in oids[sel]])
+    assert np.allclose(ex["w"][li], ow[sel], rtol=1e-12, atol=0)
+    gref = ob.adjoint(oxyz[sel], ow[sel], G_h, pat)
+    err = np.abs(g_direct[li] - gref).max() / np.abs(gref).max()
     assert err <= 1e-9, err
 
 

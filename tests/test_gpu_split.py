@@ -79,13 +79,52 @@ def test_integrate_split_edge_cases(case):
 
 
 def test_split_rejects_batches_beyond_exactness_bound():
-    wl = water(n_rad=40, n_theta=10, n_phi=20, batch_max=400)
+    # ~18k kept points; median bisection down to <= 1000 points per batch
+    # leaves batches of ~560 points, past the split path's 341-point bound
+    wl = water(n_rad=40, n_theta=10, n_phi=20, batch_max=1000)
     lib = LibCase(wl)
-    if lib.grid.info.max_np <= 341:
-        pytest.skip("bisection produced small batches")
+    assert lib.grid.info.max_np > 341
     with pytest.raises(q.Q4CError) as e:
         lib.integrate("split")
     assert e.value.status == 5
+
+
+def test_bounded_wait_timeout_is_reported_and_recovers():
+    """A work-wait limit of 1 ns makes the tensor kernels' first unsatisfied
+    wait give up: the call returns, q4c_grid_status reports Q4C_ETIMEOUT once
+    and clears it, and with the default limit restored the same calls give
+    the normal results on the same context."""
+    wl = water()
+    lib = LibCase(wl)
+    G = lib.G(31)
+    ref = lib.integrate("split")
+    gref = q.q4c_integrate_backward(lib.tables, lib.grid, G, "split").cpu().numpy()
+    lib.grid.status()
+    try:
+        q.q4c_set_wait_limit_ns(1)
+        q.q4c_integrate(lib.tables, lib.grid, lib.v, "split")
+        with pytest.raises(q.Q4CError) as e:
+            lib.grid.status()
+        assert e.value.status == 4
+        lib.grid.status()  # the flag was cleared
+        q.q4c_integrate_backward(lib.tables, lib.grid, G, "split")
+        with pytest.raises(q.Q4CError) as e:
+            lib.grid.status()
+        assert e.value.status == 4
+        # the autograd function raises instead of returning incomplete outputs
+        import torch
+        v = lib.v.clone().requires_grad_(True)
+        with pytest.raises(q.Q4CError):
+            q.integrate(v, lib.tables, lib.grid, "split")
+    finally:
+        q.q4c_set_wait_limit_ns(0)
+    lib.grid.status()
+    again = lib.integrate("split")
+    gagain = q.q4c_integrate_backward(lib.tables, lib.grid, G, "split").cpu().numpy()
+    lib.grid.status()
+    for a, b in zip(again[:5], ref[:5]):
+        assert rel_fro(a, b) <= 1e-13
+    assert rel_fro(gagain, gref) <= 1e-13
 
 
 # ----------------------------------------------------------------- full size
