@@ -775,8 +775,9 @@ extern "C" q4c_status grid_partition(const q4c_grid_desc* d, const q4c_tables* t
     g->idx_entries = std::max(g->idx_entries, used);
   }
 
-  // ---- split path: (batch, output, ti, tj) items per wave, 64x64 tiles;
-  // V and W0 need ti <= tj only, the A_yz/A_zx/A_xy products every tile.
+  // ---- split path: (batch, output, ti, tj) items per wave, tiles of 64
+  // functions, tile pairs ti <= tj only (SO: the antisymmetric part of A_k on
+  // diagonal pairs, two K-concatenated products on off-diagonal ones).
   // Batches with the most work first; the items of one batch stay adjacent
   // (W0, three products, leading) so that concurrent CTAs share its tiles in L2.
   std::vector<int4> sitems;
@@ -797,28 +798,33 @@ extern "C" q4c_status grid_partition(const q4c_grid_desc* d, const q4c_tables* t
       const int nt = (nb + 63) / 64;
       for (int o : {1, 0, 2, 3, 4})
         for (int i = 0; i < nt; ++i)
-          for (int j = 0; j < nt; ++j) {
-            if (o <= 1 && i > j) continue;
+          for (int j = i; j < nt; ++j) {
             sitems.push_back(make_int4(static_cast<int>(b), o, i, j));
-            ssteps.push_back(static_cast<int>((bptr[b + 1] - bptr[b] + 15) / 16) * (o == 1 ? 3 : 1));
+            const int n_prod = o == 1 ? 3 : (o >= 2 && i != j) ? 2 : 1;
+            ssteps.push_back(static_cast<int>((bptr[b + 1] - bptr[b] + 15) / 16) * n_prod);
           }
     }
     max_wave_items = std::max(max_wave_items, static_cast<int64_t>(sitems.size()) - g->split_w0.back());
     g->split_w0.push_back(static_cast<int64_t>(sitems.size()));
   }
-  // per-column operator (output 5): one product on every tile pair, in the
-  // same batch order (never more items per wave than the list above, so the
-  // rounding-constant buffer fits both)
+  // per-column operator (output 5): one product on every tile pair (it is
+  // not symmetric), in the same batch order
   std::vector<int4> citems;
   std::vector<int> csteps;
   g->col_w0.push_back(0);
   for (size_t wv = 0; wv + 1 < g->wave_b0.size(); ++wv) {
     for (int64_t n = g->split_w0[wv]; n < g->split_w0[wv + 1]; ++n) {
       const int4 it = sitems[n];
-      if (it.y != 4) continue;  // the A_xy items visit every tile pair of their batch once
-      citems.push_back(make_int4(it.x, 5, it.z, it.w));
-      csteps.push_back(ssteps[n]);
+      if (it.y != 0 || it.z != 0 || it.w != 0) continue;  // once per batch (its first V item)
+      const int64_t b = it.x;
+      const int nt = static_cast<int>((g->h_bat_fn_ptr[b + 1] - g->h_bat_fn_ptr[b] + 63) / 64);
+      for (int i = 0; i < nt; ++i)
+        for (int j = 0; j < nt; ++j) {
+          citems.push_back(make_int4(static_cast<int>(b), 5, i, j));
+          csteps.push_back(static_cast<int>((bptr[b + 1] - bptr[b] + 15) / 16));
+        }
     }
+    max_wave_items = std::max(max_wave_items, static_cast<int64_t>(citems.size()) - g->col_w0.back());
     g->col_w0.push_back(static_cast<int64_t>(citems.size()));
   }
   // density/adjoint: (batch, 64-point tile) items per wave, costliest first

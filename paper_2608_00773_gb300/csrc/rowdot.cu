@@ -348,16 +348,14 @@ __global__ void __launch_bounds__(kThreads, 1)
           bulk_copy(smem_u32(sA + kStageA), src, kBlockB, gfull_bar(st));
         }
         const float m = P.qf == 0 ? m0 : P.qf == 1 ? m1 : P.qf == 2 ? m2 : m3;
-        float d0[kSlices], d1[kSlices], d2[kSlices], d3[kSlices];
-        slice6(x[0].x, x[0].y, m, d0);
-        slice6(x[1].x, x[1].y, m, d1);
-        slice6(x[2].x, x[2].y, m, d2);
-        slice6(x[3].x, x[3].y, m, d3);
+        // functions (4q, 4q+1) and (4q+2, 4q+3) as packed pairs
+        float2 d01[kSlices], d23[kSlices];
+        slice6x2(pk2(x[0].x, x[1].x), pk2(x[0].y, x[1].y), m, d01);
+        slice6x2(pk2(x[2].x, x[3].x), pk2(x[2].y, x[3].y), m, d23);
 #pragma unroll
         for (int t = 0; t < kSlices; ++t) {
-          const __nv_bfloat162 lo = __floats2bfloat162_rn(d0[t], d1[t]), hi = __floats2bfloat162_rn(d2[t], d3[t]);
           asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(smem_u32(sA + (1 + t) * kTileBytes + dst_off)),
-                       "r"(*reinterpret_cast<const uint32_t*>(&lo)), "r"(*reinterpret_cast<const uint32_t*>(&hi))
+                       "r"(bf16x2_exact(d01[t])), "r"(bf16x2_exact(d23[t]))
                        : "memory");
         }
         fence_async_smem();
@@ -430,7 +428,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             tc_fence_after();
             const uint32_t a = smem_u32(smem + kSmemStages + st * kStage), bb = a + kStageA;
-            mma_levels(t0, a, bb, ic == 0 ? 0u : 1u);
+            mma_levels(t0, a, bb, ic == 0 ? 0u : 1u, kTile);
             mma_commit(empty_bar(st));
           }
           if (ok) mma_commit(accfull_bar(set));

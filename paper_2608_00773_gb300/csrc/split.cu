@@ -32,13 +32,16 @@
 // consecutive blocks [L0;L1], [L2;L3], [L4;L5].  Six MMAs per K-step cover the
 // twenty-one slice pairs with s + t <= 5 (tc::mma_levels lists them).
 //
-// Outputs per (batch, 64x64 tile): V = (D Phi)^T Phi, W0 = sum_q (D Q)^T Q
-// (three products into one accumulator, sliced against a common exponent per
-// function so that the exact levels keep one unit), and A_yz = (D Y)^T Z,
-// A_zx = (D Z)^T X, A_xy = (D X)^T Y with SO_x = A_yz - A_yz^T etc. applied
-// while scattering; and, as its own launch, the per-column operator of
-// Eq. 19, F = (w Phi)^T Psi with Psi_pj = (v_p + eps_j - V_j) phi_j (output 5,
-// every tile pair, every element into its own block).  One warp-specialised CTA per SM (slicers, one MMA
+// Outputs per (batch, tile pair ti <= tj; tiles of 64 functions, the B tile
+// tj only as wide as its functions rounded up to 16): V = (D Phi)^T Phi,
+// W0 = sum_q (D Q)^T Q (three products into one accumulator, sliced against
+// a common exponent per function so that the exact levels keep one unit),
+// and SO: on a diagonal pair A_yz = (D Y)^T Z, A_zx = (D Z)^T X,
+// A_xy = (D X)^T Y with SO_x = A_yz - A_yz^T etc. applied while scattering,
+// on an off-diagonal pair SO_x = (D Y)^T Z - (D Z)^T Y etc. directly (two
+// K-concatenated products); and, as its own launch, the per-column operator
+// of Eq. 19, F = (w Phi)^T Psi with Psi_pj = (v_p + eps_j - V_j) phi_j
+// (output 5, every tile pair, every element into its own block).  One warp-specialised CTA per SM (slicers, one MMA
 // thread, epilogue warps; 512 TMEM columns) loops over the work items; every
 // mbarrier wait is bounded and sets a status bit instead of hanging.
 #include <cuda.h>
@@ -86,9 +89,10 @@ static_assert(kRawMag + 128 * 4 <= kRawStage, "raw stage overflow");
 static_assert(kSmemTotal <= 232448, "shared memory per CTA");
 
 // ------------------------------------------------------------ kernel
-// The products of one output: n of them, the A-side (D-scaled) and B-side
-// quantities of product pr in bits 2pr..2pr+1 of qa and qb (0 Phi, 1 X, 2 Y,
-// 3 Z).
+// The products of one item, K-concatenated into one accumulator: n of them,
+// the A-side (D-scaled) and B-side quantities of product pr in bits
+// 2pr..2pr+1 of qa and qb (0 Phi, 1 X, 2 Y, 3 Z); a two-product item
+// subtracts its second product (its D is negated).
 struct Products {
   int n;
   unsigned qa, qb;
@@ -96,27 +100,43 @@ struct Products {
   __device__ __forceinline__ int b(int pr) const { return static_cast<int>((qb >> (2 * pr)) & 3u); }
 };
 
-__device__ __forceinline__ Products products_of(int o) {
+// Items cover the tile pairs ti <= tj of a batch.  SO_k is the antisymmetric
+// part of A_k (A_yz = (D Y)^T Z, A_zx = (D Z)^T X, A_xy = (D X)^T Y): on a
+// diagonal tile pair the item computes A_k and the epilogue takes
+// A_k(i, j) - A_k(j, i); on an off-diagonal pair (ti < tj) it computes
+// SO_k itself, e.g. SO_x(ti, tj) = (D Y_ti)^T Z_tj - (D Z_ti)^T Y_tj, since
+// A_yz(j, i) = (D Z_i)^T Y_j: every item then keeps its full 64-function
+// tile on the M side and the narrower tile tj on the N side.
+__device__ __forceinline__ Products products_of(int o, bool offdiag) {
   switch (o) {
-    case 0: return {1, 0u, 0u};                // V
-    case 1: return {3, 0x39u, 0x39u};          // W0: (X, X), (Y, Y), (Z, Z)
-    case 2: return {1, 2u, 3u};                // A_yz -> SO_x
-    case 3: return {1, 3u, 1u};                // A_zx -> SO_y
-    case 4: return {1, 1u, 2u};                // A_xy -> SO_z
-    default: return {1, 0u, 1u};               // per-column operator: (w Phi)^T Psi
+    case 0: return {1, 0u, 0u};                                 // V
+    case 1: return {3, 0x39u, 0x39u};                           // W0: (X, X), (Y, Y), (Z, Z)
+    case 2: return offdiag ? Products{2, 0xEu, 0xBu} : Products{1, 2u, 3u};  // SO_x: (Y, Z) - (Z, Y)
+    case 3: return offdiag ? Products{2, 0x7u, 0xDu} : Products{1, 3u, 1u};  // SO_y: (Z, X) - (X, Z)
+    case 4: return offdiag ? Products{2, 0x9u, 0x6u} : Products{1, 1u, 2u};  // SO_z: (X, Y) - (Y, X)
+    default: return {1, 0u, 1u};                                // per-column operator: (w Phi)^T Psi
   }
 }
 
+__device__ __forceinline__ Products item_products(const int4& item) {
+  return products_of(item.y, item.y >= 2 && item.y <= 4 && item.z != item.w);
+}
+
+// B-tile width of an item: the functions of tile tj rounded up to 16 (the
+// MMA's N granularity)
+__device__ __forceinline__ int item_nb(int nb, int tj) { return (min(kTile, nb - tj * kTile) + 15) & ~15; }
+
 // Rounding constants of one item's rows: 0..63 the A side (column exponents
-// of the D-scaled quantity), 64..127 the B side.  W0 slices its three
-// gradient products against one exponent per function (the maximum over x,
-// y, z), so that its K-concatenated products share units.
+// of the D-scaled quantity), 64..127 the B side.  An item with several
+// K-concatenated products (W0, off-diagonal SO) slices them against one
+// exponent per function (the maximum over its products), so that they share
+// units.
 __global__ void k_item_prep(DevGrid G, const int4* __restrict__ items, const int* __restrict__ colexp,
                             float* __restrict__ mag) {
   const int n = blockIdx.x;
   const int4 item = items[n];
   const int64_t b = item.x;
-  const int o = item.y, t = threadIdx.x, side = t >> 6, r = t & 63;
+  const int t = threadIdx.x, side = t >> 6, r = t & 63;
   const int64_t fn0 = G.bat_fn_ptr[b];
   const int nb = static_cast<int>(G.bat_fn_ptr[b + 1] - fn0);
   const int* cexp = colexp + 8 * fn0;
@@ -124,12 +144,8 @@ __global__ void k_item_prep(DevGrid G, const int4* __restrict__ items, const int
   int e = -30000;
   if (f < nb) {
     const int base = side ? 4 : 0;
-    if (o == 1) {
-      e = max(cexp[(base + 1) * nb + f], max(cexp[(base + 2) * nb + f], cexp[(base + 3) * nb + f]));
-    } else {
-      const Products P = products_of(o);
-      e = cexp[(base + (side ? P.b(0) : P.a(0))) * nb + f];
-    }
+    const Products P = item_products(item);
+    for (int pr = 0; pr < P.n; ++pr) e = max(e, cexp[(base + (side ? P.b(pr) : P.a(pr))) * nb + f]);
   }
   mag[static_cast<int64_t>(n) * 128 + t] = magic0(e);
 }
@@ -140,14 +156,11 @@ __device__ __forceinline__ void sts64(unsigned char* p, uint32_t a, uint32_t b) 
   asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(smem_u32(p)), "r"(a), "r"(b) : "memory");
 }
 
-__device__ __forceinline__ uint32_t bf2(float lo, float hi) {
-  const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
-  return *reinterpret_cast<const uint32_t*>(&v);
-}
 
-// One work item = (batch, output, 64x64 tile).  Its K dimension is a stream
-// of steps of 16 points; W0 streams its three gradient products one after
-// the other (a K-concatenation into one accumulator, common exponents).
+// One work item = (batch, output, tile pair).  Its K dimension is a stream
+// of steps of 16 points; W0 and the off-diagonal SO items interleave their
+// products step by step (a K-concatenation into one accumulator, common
+// exponents; the subtracted SO product slices -D).
 //
 // Warp roles (one CTA per SM, items strided over the CTAs):
 //   warp 17     (one thread) loads step g's raw operands into raw stage
@@ -156,15 +169,16 @@ __device__ __forceinline__ uint32_t bf2(float lo, float hi) {
 //               and n_b), the step's 16 D values and, on an item's first
 //               step, the item's rounding constants; one mbarrier (raw_full)
 //               counts the bytes;
-//   warps 0-7   thread (row r, points 4q..4q+3) reads its raw values, frees
-//               the raw stage, forms the D-scaled A values in double-float,
-//               slices both sides into six BF16 digits and stores them (8
-//               bytes per slice and side) into operand stage g mod 4 once the
-//               MMAs that last read it have completed (empty[stage], a
-//               tcgen05.commit), then arrives on full[stage];
+//   warps 0-7   thread (row r, points 4q..4q+3) reads its raw values, forms
+//               the D-scaled A values in double-float, slices both sides
+//               (the B side only on the item's B rows) into six BF16 digits
+//               and stores them (8 bytes per slice and side) into operand
+//               stage g mod 4 once the MMAs that last read it have completed
+//               (empty[stage], a tcgen05.commit), arrives on full[stage] and
+//               frees the raw stage;
 //   warp 16     (one thread) waits full[stage], issues the six MMAs into the
 //               item's accumulator set (items alternate between two sets of
-//               192 TMEM columns), commits empty[stage], and after an item's
+//               up to 192 TMEM columns), commits empty[stage], and after an item's
 //               last step commits accfull[set];
 //   warps 8-15  wait accfull[set], read the six levels, combine and scatter
 //               (two groups of four warps take alternate 16-column chunks;
@@ -248,9 +262,13 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int n = blockIdx.x; n < n_items; n += gridDim.x) {
       const int n_steps = n_steps_next;
       if (n + static_cast<int>(gridDim.x) < n_items) n_steps_next = steps[n + gridDim.x];
+      const int4 item = items[n];
+      const int nbB = item_nb(static_cast<int>(G.bat_fn_ptr[item.x + 1] - G.bat_fn_ptr[item.x]), item.w);
+      const int n_prod = item_products(item).n;
+      const bool b_row = r < nbB;  // this warp's rows of the B tile exist (nbB is a multiple of 16)
       float mA = 0.f, mB = 0.f;
       bool ok = true;
-      for (int s = 0; s < n_steps; ++s, ++g) {
+      for (int s = 0, pr = 0; s < n_steps; ++s, ++g, pr = (pr + 1 == n_prod) ? 0 : pr + 1) {
         const int rs = g % kRaw, st = g % kStages;
         if (!mbar_wait_abort(rawfull_bar(rs), (g / kRaw) & 1, s_abort, status, G.wait_ns)) {
           ok = false;
@@ -262,37 +280,43 @@ __global__ void __launch_bounds__(kThreads, 1)
           mB = reinterpret_cast<const float*>(raw + kRawMag)[64 + r];
         }
         const float4 a01 = lds128(raw + rc0), a23 = lds128(raw + rc1);
-        const float4 b01 = lds128(raw + kRawTile + rc0), b23 = lds128(raw + kRawTile + rc1);
-        const float4 d01 = lds128(raw + kRawD + q * 32), d23 = lds128(raw + kRawD + q * 32 + 16);
+        float4 b01 = make_float4(0.f, 0.f, 0.f, 0.f), b23 = b01;
+        if (b_row) {
+          b01 = lds128(raw + kRawTile + rc0);
+          b23 = lds128(raw + kRawTile + rc1);
+        }
+        float4 d01 = lds128(raw + kRawD + q * 32), d23 = lds128(raw + kRawD + q * 32 + 16);
+        if (pr == 1 && n_prod == 2) {  // the subtracted product of an off-diagonal SO item: -D (exact)
+          d01 = make_float4(-d01.x, -d01.y, -d01.z, -d01.w);
+          d23 = make_float4(-d23.x, -d23.y, -d23.z, -d23.w);
+        }
         if (!mbar_wait_abort(empty_bar(st), ((g / kStages) & 1) ^ 1, s_abort, status, G.wait_ns)) {
           ok = false;
           break;
         }
         unsigned char* sA = smem + kSmemStages + st * kStage;
         unsigned char* sB = sA + kStageA;
+        // points (4q, 4q+1) and (4q+2, 4q+3) as packed pairs
         {  // A side: D-scaled values in double-float
-          const df x0 = df_mul(df{a01.x, a01.y}, df{d01.x, d01.y});
-          const df x1 = df_mul(df{a01.z, a01.w}, df{d01.z, d01.w});
-          const df x2 = df_mul(df{a23.x, a23.y}, df{d23.x, d23.y});
-          const df x3 = df_mul(df{a23.z, a23.w}, df{d23.z, d23.w});
-          float e0[kSlices], e1[kSlices], e2[kSlices], e3[kSlices];
-          slice6(x0.hi, x0.lo, mA, e0);
-          slice6(x1.hi, x1.lo, mA, e1);
-          slice6(x2.hi, x2.lo, mA, e2);
-          slice6(x3.hi, x3.lo, mA, e3);
+          float2 xh01, xl01, xh23, xl23;
+          df_mul2(pk2(a01.x, a01.z), pk2(a01.y, a01.w), pk2(d01.x, d01.z), pk2(d01.y, d01.w),
+                  pk2(-d01.x, -d01.z), xh01, xl01);
+          df_mul2(pk2(a23.x, a23.z), pk2(a23.y, a23.w), pk2(d23.x, d23.z), pk2(d23.y, d23.w),
+                  pk2(-d23.x, -d23.z), xh23, xl23);
+          float2 e01[kSlices], e23[kSlices];
+          slice6x2(xh01, xl01, mA, e01);
+          slice6x2(xh23, xl23, mA, e23);
 #pragma unroll
           for (int t = 0; t < kSlices; ++t)  // A: [Z, A0..A5]
-            sts64(sA + (1 + t) * kTileBytes + dst_off, bf2(e0[t], e1[t]), bf2(e2[t], e3[t]));
+            sts64(sA + (1 + t) * kTileBytes + dst_off, bf16x2_exact(e01[t]), bf16x2_exact(e23[t]));
         }
-        {  // B side
-          float e0[kSlices], e1[kSlices], e2[kSlices], e3[kSlices];
-          slice6(b01.x, b01.y, mB, e0);
-          slice6(b01.z, b01.w, mB, e1);
-          slice6(b23.x, b23.y, mB, e2);
-          slice6(b23.z, b23.w, mB, e3);
+        if (b_row) {  // B side: tiles of nbB rows
+          float2 e01[kSlices], e23[kSlices];
+          slice6x2(pk2(b01.x, b01.z), pk2(b01.y, b01.w), mB, e01);
+          slice6x2(pk2(b23.x, b23.z), pk2(b23.y, b23.w), mB, e23);
 #pragma unroll
           for (int t = 0; t < kSlices; ++t)  // B: [B0, B2, B4, B1, B3, B5]
-            sts64(sB + b_tile(t) * kTileBytes + dst_off, bf2(e0[t], e1[t]), bf2(e2[t], e3[t]));
+            sts64(sB + b_tile(t) * nbB * kRowBytes + dst_off, bf16x2_exact(e01[t]), bf16x2_exact(e23[t]));
         }
         fence_async_smem();
         mbar_arrive(full_bar(st));
@@ -312,7 +336,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int n = blockIdx.x; n < n_items; n += gridDim.x) {
         const int4 item = items[n];
         const int n_steps = steps[n];
-        const Products P = products_of(item.y);
+        const Products P = item_products(item);
         const CUtensorMap* map = maps + item.x;
         const float2* drow = dpad + static_cast<int64_t>(item.x) * kDPitch;
         const int i0 = item.z * kTile, j0 = item.w * kTile;
@@ -323,7 +347,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             ok = false;
             break;
           }
-          const int c = P.n == 1 ? s : s / 3, pr = s - c * P.n;
+          const int c = P.n == 1 ? s : s / P.n, pr = s - c * P.n;
           const uint32_t dst = smem_u32(smem + kSmemRaw + rs * kRawStage);
           const uint32_t fb = rawfull_bar(rs);
           arrive_expect_tx(fb, 2 * kRawTile + kKc * 8 + (s == 0 ? 128 * 4 : 0));
@@ -345,6 +369,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       int g = 0, k = 0;
       for (int n = blockIdx.x; n < n_items; n += gridDim.x, ++k) {
         const int n_steps = steps[n];
+        const int4 item = items[n];
+        const int nbB = item_nb(static_cast<int>(G.bat_fn_ptr[item.x + 1] - G.bat_fn_ptr[item.x]), item.w);
         const int set = k & 1;
         if (!mbar_wait_abort(accempty_bar(set), ((k >> 1) & 1) ^ 1, s_abort, status, G.wait_ns, 64)) break;
         tc_fence_after();
@@ -358,7 +384,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           tc_fence_after();
           const uint32_t a = smem_u32(smem + kSmemStages + st * kStage), bb = a + kStageA;
-          mma_levels(t0, a, bb, s == 0 ? 0u : 1u);
+          mma_levels(t0, a, bb, s == 0 ? 0u : 1u, nbB);
           mma_commit(empty_bar(st));
         }
         if (!ok) break;
@@ -385,14 +411,14 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int64_t b = item.x;
       const int o = item.y, i0 = item.z * kTile, j0 = item.w * kTile;
       const int nb = static_cast<int>(G.bat_fn_ptr[b + 1] - G.bat_fn_ptr[b]);
-      const int N = (min(kTile, nb - j0) + 15) & ~15;
+      const int N = item_nb(nb, item.w);  // accumulator blocks are N columns wide
       const int* idx = G.bat_idx + G.bat_idx_ptr[b];
       double* out = (o == 0 || o == 5) ? V : o == 1 ? W0 : o == 2 ? SOx : o == 3 ? SOy : SOz;
       for (int c0 = eg * 16; c0 < N; c0 += 32) {
 #pragma unroll
         for (int blk = 0; blk < 3; ++blk) {
           float vv[16];
-          tmem_ld16(tmem + lane_base + set * kSetCols + blk * kTile + c0, vv);
+          tmem_ld16(tmem + lane_base + set * kSetCols + blk * N + c0, vv);
 #pragma unroll
           for (int i = 0; i < 16; ++i) stg[(blk * 128 + et) * kEpiPitch + i] = vv[i];
         }
@@ -423,6 +449,8 @@ __global__ void __launch_bounds__(kThreads, 1)
           } else if (o <= 1) {
             if (i > j) continue;
           } else {
+            // SO: a diagonal tile pair holds A_k, so A_k(i, j) - A_k(j, i) goes
+            // to (i, j), i < j; an off-diagonal one holds SO_k itself (i < j)
             if (i == j) continue;
             if (i > j) { ri = j; rj = i; sgn = -1.0; }
           }

@@ -63,23 +63,27 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
 //   [A1;A2] x [B1,B3]     -> blocks 1-2   (4 pairs)
 //   [A4;A5] x B0          -> block 2      (2 pairs)
 //   [A3;A4] x B1          -> block 2      (2 pairs)
-constexpr int kLevelTile = 2048;     // bytes per operand tile
+constexpr int kLevelTile = 2048;     // bytes per 64-row operand tile
 constexpr uint32_t kLevelSBO = 256;  // bytes between 8-row groups
+constexpr int kRowBytes = 32;        // one row of 16 K values (BF16)
 
 // tile position of B slice t in the stage
 __host__ __device__ constexpr int b_tile(int t) { return (t & 1) ? 3 + (t >> 1) : (t >> 1); }
 
-// a, b: shared addresses of tile Z of A and of the first B tile; acc = 0 starts
-// the accumulators (the first MMA covers all three blocks)
-__device__ __forceinline__ void mma_levels(uint32_t tmem, uint32_t a, uint32_t b, uint32_t acc) {
+// a, b: shared addresses of tile Z of A (64-row tiles) and of the first B
+// tile; the six B tiles hold nb rows each (nb a multiple of 16, <= 64;
+// tile pos at b + pos * nb * 32), so the three accumulator blocks are nb
+// columns wide ([L0;L1] at tmem, [L2;L3] at tmem + nb, [L4;L5] at tmem +
+// 2 nb); acc = 0 starts the accumulators (the first MMA covers all three)
+__device__ __forceinline__ void mma_levels(uint32_t tmem, uint32_t a, uint32_t b, uint32_t acc, int nb) {
   auto A = [&](int q) { return make_desc(a + q * kLevelTile, kLevelSBO); };
-  auto Bt = [&](int pos) { return make_desc(b + pos * kLevelTile, kLevelSBO); };
-  mma_bf16(tmem, A(1), Bt(0), make_idesc(128, 192), acc);
-  mma_bf16(tmem, A(0), Bt(3), make_idesc(128, 192), 1u);
-  mma_bf16(tmem + 64, A(3), Bt(0), make_idesc(128, 128), 1u);
-  mma_bf16(tmem + 64, A(2), Bt(3), make_idesc(128, 128), 1u);
-  mma_bf16(tmem + 128, A(5), Bt(0), make_idesc(128, 64), 1u);
-  mma_bf16(tmem + 128, A(4), Bt(3), make_idesc(128, 64), 1u);
+  auto Bt = [&](int pos) { return make_desc(b + pos * nb * kRowBytes, kLevelSBO); };
+  mma_bf16(tmem, A(1), Bt(0), make_idesc(128, 3 * nb), acc);
+  mma_bf16(tmem, A(0), Bt(3), make_idesc(128, 3 * nb), 1u);
+  mma_bf16(tmem + nb, A(3), Bt(0), make_idesc(128, 2 * nb), 1u);
+  mma_bf16(tmem + nb, A(2), Bt(3), make_idesc(128, 2 * nb), 1u);
+  mma_bf16(tmem + 2 * nb, A(5), Bt(0), make_idesc(128, nb), 1u);
+  mma_bf16(tmem + 2 * nb, A(4), Bt(3), make_idesc(128, nb), 1u);
 }
 
 __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
@@ -261,6 +265,57 @@ __device__ __forceinline__ void slice6(float h, float l, float m0, float d[kSlic
     const float t = __fsub_rn(__fadd_rn(x, m), m);
     d[s] = t;
     x = __fsub_rn(x, t);
+    m = __fmul_rn(m, 0x1p-8f);
+  }
+}
+
+// ------------------------------------------------------------ pairs
+// Two FP32 values operated on by the packed float2 instructions of sm_100
+// and later (CUDA's __fadd2_rn, __fmul2_rn, __ffma2_rn): each half is
+// rounded on its own exactly as the scalar instruction would, and one
+// instruction does the work of two (the slicers are bound by instruction
+// issue, not by FP32 lanes).  a - b is fma(b, -1, a), one rounding of the
+// exact difference, as the scalar subtraction.
+__device__ __forceinline__ float2 pk2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }  // a b + c
+
+// BF16 pair (low half = .x) of two FP32 values that are exact in BF16 (their
+// low 16 bits are zero): the upper halves, by byte permute
+__device__ __forceinline__ uint32_t bf16x2_exact(float2 v) {
+  uint32_t r;
+  asm("prmt.b32 %0, %1, %2, 0x7632;" : "=r"(r) : "r"(__float_as_uint(v.x)), "r"(__float_as_uint(v.y)));
+  return r;
+}
+
+// double-float products of two pairs (x = xh + xl, y = yh + yl per half),
+// the same operations as df_mul: p = xh yh, e = fma(xh, yh, -p) (with
+// -p = xh (-yh) rounded, nyh = -yh), e = fma(xh, yl, e), e = fma(xl, yh, e),
+// then the fast two-sum of p and e
+__device__ __forceinline__ void df_mul2(float2 xh, float2 xl, float2 yh, float2 yl, float2 nyh, float2& rh,
+                                        float2& rl) {
+  const float2 p = mul2(xh, yh);
+  float2 e = fma2(xh, yh, mul2(xh, nyh));
+  e = fma2(xh, yl, e);
+  e = fma2(xl, yh, e);
+  rh = add2(p, e);
+  rl = sub2(e, sub2(rh, p));
+}
+
+// slice6 on a pair of values (h + l per half) against the same rounding
+// constant m0 for both: d[s] holds digit s of both halves, weighted
+__device__ __forceinline__ void slice6x2(float2 h, float2 l, float m0, float2 d[kSlices]) {
+  float2 x = h;
+  float m = m0;
+#pragma unroll
+  for (int s = 0; s < kSlices; ++s) {
+    if (s == 3) x = add2(x, l);
+    const float2 mm = pk2(m, m);
+    const float2 t = sub2(add2(x, mm), mm);
+    d[s] = t;
+    if (s + 1 < kSlices) x = sub2(x, t);
     m = __fmul_rn(m, 0x1p-8f);
   }
 }
