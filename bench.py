@@ -303,6 +303,8 @@ def main():
     ap.add_argument("--cpu-stride-all", type=int, default=2, help="all-core sample of the cpu baseline")
     ap.add_argument("--ref-stride", type=int, default=7)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--separate", action="store_true",
+                    help="time the three separate calls instead of the one-pass q4c_scf_pass")
     ap.add_argument("--print-source-hash", action="store_true",
                     help="print the sha256 of each profiled kernel's sources and exit")
     args = ap.parse_args()
@@ -360,10 +362,20 @@ def main():
             phase_prec[name] = "fp64"
     torch.cuda.synchronize()
 
-    def step(_prec=None):
+    def separate_step():
         q.q4c_integrate(tables, grid, v, phase_prec["integrate"], out=mats, stream=stream)
         q.q4c_density(tables, grid, P, phase_prec["density"], out=n_out, stream=stream)
         q.q4c_integrate_backward(tables, grid, G, phase_prec["backward"], out=g_out, stream=stream)
+
+    # one pass per step (q4c_scf_pass: one basis evaluation per wave for the
+    # three parts) where all phases run in one precision
+    fused = len(set(phase_prec.values())) == 1 and not args.separate
+
+    def step(_prec=None):
+        if not fused:
+            return separate_step()
+        q.q4c_scf_pass(tables, grid, v, [P, None, None, None, None], G, phase_prec["integrate"], H_out=mats,
+                       n_out=n_out, dLdv_out=g_out, stream=stream)
 
     prec = args.prec
     for _ in range(args.warmup):
@@ -461,6 +473,17 @@ def main():
 
     # ---- the integration alone (q4c_integrate, device time, L2 flushed)
     extra = {}
+    if fused:  # the same step as three separate calls, for comparison
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(5)]
+        for a_, b_ in evs:
+            flush.zero_()
+            a_.record(stream)
+            separate_step()
+            b_.record(stream)
+        torch.cuda.synchronize()
+        grid.status()
+        extra["separate_calls"] = {"ms_per_step": max_over_ranks(statistics.mean(a_.elapsed_time(b_) for a_, b_ in evs),
+                                                                 world), "steps": len(evs)}
     evi = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     for a_, b_ in evi:
         flush.zero_()
@@ -556,7 +579,8 @@ def main():
         "config": {"workload": wl.name, "atoms": wl.n_atoms, "n_basis": int(info.n_basis),
                    "points": int(info.n_points), "batches": int(info.n_batches), "max_nb": int(info.max_nb),
                    "precision": prec, "phase_precision": phase_prec,
-                   "step": "q4c_integrate + q4c_density + q4c_integrate_backward",
+                   "step": ("q4c_scf_pass (integration + density + adjoint, one basis evaluation per wave)"
+                            if fused else "q4c_integrate + q4c_density + q4c_integrate_backward"),
                    "l2": "512 MB buffer written between timed steps", "replicas": world},
         "flops_per_step": fl,
         "phase_ms": {k: v_[0] / args.steps for k, v_ in kern.items()},

@@ -380,6 +380,27 @@ Q4C_API q4c_status q4c_integrate_backward(const q4c_tables* tables, const q4c_gr
                                   const q4c_matrices* G, q4c_precision prec, double* dLdv_dev,
                                   q4c_stream stream);
 
+/* One pass per SCF step over the grid (the gradient-density row of the
+ * method's density update batched with the integration; Eqs. 4, 21, 29-30,
+ * 39-40): per wave of batches the basis (Phi and its gradient, Eq. 12 with
+ * Appendix B) is evaluated once and feeds, from the same tiles, each part
+ * whose arguments are given:
+ *   H != NULL:  the integration of v_dev into H (exactly as q4c_integrate:
+ *               V, W0, SOx, SOy, SOz [nnz] overwritten, spinor_SS if set);
+ *   P != NULL:  the density n_dev[n_points] = sum_M sum_ij P^M_ij f^M_ij(p)
+ *               (q4c_density_full; with only P->V it is q4c_density, Eq. 39);
+ *   G != NULL:  the adjoint dLdv_dev[n_points] of q4c_integrate_backward.
+ * All arrays are device arrays on the grid's pattern or points (batch order),
+ * caller-owned; NULL slots inside P or G count as zero.  Each result equals
+ * that of its separate call up to the order of the FP64 additions; the saving
+ * is the basis evaluation and offset tables the separate calls would repeat.
+ * Q4C_EINVAL for a missing array (H without v or an output, P without n_dev,
+ * G without dLdv_dev), Q4C_EUNSUPPORTED where the split path's batch limits
+ * are exceeded (as for the separate calls). */
+Q4C_API q4c_status q4c_scf_pass(const q4c_tables* tables, const q4c_grid* grid, const double* v_dev,
+                                const q4c_matrices* H, const q4c_matrices* P, double* n_dev,
+                                const q4c_matrices* G, double* dLdv_dev, q4c_precision prec, q4c_stream stream);
+
 /* q4c_integrate with prec = Q4C_FP64 for callers that cannot allocate device
  * memory when they integrate (an application whose own pool owns the device
  * memory, or a loop that must not pay for cudaMalloc/cudaFree, which can

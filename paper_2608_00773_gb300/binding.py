@@ -27,7 +27,7 @@ EXPORTS = ["nao_tabulate", "nao_tabulate_knots", "q4c_tables_destroy", "q4c_tabl
            "q4c_grid_get_info", "q4c_grid_export", "q4c_grid_export_shifts", "q4c_grid_kpattern", "q4c_kfold", "q4c_grid_points", "q4c_integrate", "q4c_density", "q4c_density_full",
            "q4c_spinor_basis", "q4c_spinor_transform", "q4c_spinor_density_matrices", "q4c_grid_batch_spinors",
            "q4c_tables_set_columns", "q4c_integrate_columns", "q4c_tables_set_kappa", "q4c_spinor_nnz",
-           "q4c_integrate_backward", "q4c_integrate_noalloc", "q4c_basis_eval", "q4c_grid_status", "q4c_set_wait_limit_ns", "q4c_profile", "q4c_profile_read",
+           "q4c_integrate_backward", "q4c_scf_pass", "q4c_integrate_noalloc", "q4c_basis_eval", "q4c_grid_status", "q4c_set_wait_limit_ns", "q4c_profile", "q4c_profile_read",
            "q4c_last_error"]
 
 
@@ -102,6 +102,8 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     L.q4c_spinor_transform.argtypes = [vp, vp, C.POINTER(Matrices), vp, vp, vp]
     L.q4c_spinor_density_matrices.argtypes = [vp, vp, vp, C.POINTER(Matrices), vp]
     L.q4c_grid_batch_spinors.argtypes = [vp, i64, vp, vp, vp]
+    L.q4c_scf_pass.argtypes = [vp, vp, vp, C.POINTER(Matrices), C.POINTER(Matrices), vp, C.POINTER(Matrices), vp,
+                               C.c_int, vp]
     L.q4c_integrate_noalloc.argtypes = [vp, vp, vp, C.POINTER(Matrices), vp]
     L.q4c_basis_eval.argtypes = [vp, vp, i64, vp, vp, vp, vp]
     L.q4c_grid_status.argtypes = [vp, vp]
@@ -398,6 +400,34 @@ def q4c_integrate_backward(tables: Tables, grid: Grid, G: Sequence, prec="fp64",
     m = Matrices(*[_ptr(g) for g in G], 0)
     _check(load().q4c_integrate_backward(tables.h, grid.h, C.byref(m), _prec(prec), _ptr(out), _stream(stream)))
     return out
+
+
+def q4c_scf_pass(tables: Tables, grid: Grid, v=None, P: Optional[Sequence] = None, G: Optional[Sequence] = None,
+                 prec="fp64", H_out=None, n_out=None, dLdv_out=None, spinor: bool = False, stream=None):
+    """One pass over the grid with one basis evaluation per wave: H from v (if
+    v is given), the density of P = [PV, PW0, PSOx, PSOy, PSOz] (if given) and
+    dL/dv of G (if given).  Returns (H list or None, n or None, dLdv or None)."""
+    import torch
+    ref = next((x for x in ([v] + list(P or []) + list(G or [])) if x is not None), None)
+    dev = ref.device if ref is not None else torch.device("cuda", torch.cuda.current_device())
+    H = None
+    if v is not None:
+        H = H_out if H_out is not None else [torch.empty(grid.nnz, dtype=torch.float64, device=dev) for _ in range(5)]
+        if H_out is None:
+            H.append(torch.empty(8 * grid.nnz, dtype=torch.float64, device=dev) if spinor else None)
+    n = None
+    if P is not None:
+        n = n_out if n_out is not None else torch.empty(grid.n_points, dtype=torch.float64, device=dev)
+    g = None
+    if G is not None:
+        g = dLdv_out if dLdv_out is not None else torch.empty(grid.n_points, dtype=torch.float64, device=dev)
+    mH = Matrices(*[_ptr(x) for x in H[:5]], _ptr(H[5]) if len(H) > 5 else 0) if H is not None else None
+    mP = Matrices(*[_ptr(x) for x in P], 0) if P is not None else None
+    mG = Matrices(*[_ptr(x) for x in G], 0) if G is not None else None
+    _check(load().q4c_scf_pass(tables.h, grid.h, _ptr(v), C.byref(mH) if mH else None,
+                               C.byref(mP) if mP else None, _ptr(n), C.byref(mG) if mG else None, _ptr(g),
+                               _prec(prec), _stream(stream)))
+    return H, n, g
 
 
 def q4c_basis_eval(tables: Tables, grid: Grid, xyz, stream=None):

@@ -112,3 +112,20 @@ extern "C" q4c_status q4c_integrate_columns(const q4c_tables* t, const q4c_grid*
     return Q4C_ENOMEM;
   }
 }
+
+extern "C" q4c_status q4c_scf_pass(const q4c_tables* t, const q4c_grid* g, const double* v, const q4c_matrices* H,
+                                   const q4c_matrices* P, double* n, const q4c_matrices* G, double* dLdv,
+                                   q4c_precision prec, q4c_stream stream) {
+  if (q4c_status st = check_pair(t, g, "q4c_scf_pass")) return st;
+  Q4C_CHECK_ARG(prec == Q4C_FP64 || prec == Q4C_SPLIT, "q4c_scf_pass: unknown precision");
+  Q4C_CHECK_ARG(!H || (v && H->V && H->W0 && H->SOx && H->SOy && H->SOz),
+                "q4c_scf_pass: H needs v and all five output arrays");
+  Q4C_CHECK_ARG(!P || n, "q4c_scf_pass: P given without a density array");
+  Q4C_CHECK_ARG(!G || dLdv, "q4c_scf_pass: G given without a gradient array");
+  try {
+    return scf_pass(t, g, v, H, P, n, G, dLdv, prec == Q4C_SPLIT, reinterpret_cast<cudaStream_t>(stream));
+  } catch (const std::exception& e) {
+    set_error(std::string("q4c_scf_pass: ") + e.what());
+    return Q4C_ENOMEM;
+  }
+}

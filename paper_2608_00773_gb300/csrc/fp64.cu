@@ -259,25 +259,29 @@ q4c_status mirror_and_spinor(const q4c_grid* g, const q4c_matrices* out, cudaStr
   return Q4C_OK;
 }
 
+// the products of one wave (its basis tiles in place)
+q4c_status products_fp64_wave(const q4c_grid* g, int wv, const double* v, const q4c_matrices* out,
+                              cudaStream_t s) {
+  const int64_t t0 = g->wave_t0[wv], t1 = g->wave_t0[wv + 1];
+  if (t1 <= t0) return Q4C_OK;
+  KernelScope ks("products_fp64", s);
+  k_products_fp64<<<static_cast<unsigned>(t1 - t0), 256, 0, s>>>(g->tables->view(), g->view(), g->d_tiles, t0,
+                                                                   g->d_scr_off, 0, g->d_scratch, v, out->V,
+                                                                   out->W0, out->SOx, out->SOy, out->SOz);
+  Q4C_CUDA(cudaGetLastError());
+  return Q4C_OK;
+}
+
 q4c_status integrate_fp64(const q4c_tables* t, const q4c_grid* g, const double* v, const q4c_matrices* out,
                           cudaStream_t s) {
   double* outs[5] = {out->V, out->W0, out->SOx, out->SOy, out->SOz};
   for (double* o : outs) Q4C_CUDA(cudaMemsetAsync(o, 0, sizeof(double) * g->nnz, s));
-  const DevBasis B = t->view();
-  const DevGrid G = g->view();
   for (size_t wv = 0; wv + 1 < g->wave_b0.size(); ++wv) {
     const int64_t b0 = g->wave_b0[wv], b1 = g->wave_b0[wv + 1];
     if (b1 > b0) {
       if (q4c_status st = launch_basis_tiles(t, g, b0, b1, nullptr, nullptr, s)) return st;
     }
-    const int64_t t0 = g->wave_t0[wv], t1 = g->wave_t0[wv + 1];
-    if (t1 > t0) {
-      KernelScope ks("products_fp64", s);
-      k_products_fp64<<<static_cast<unsigned>(t1 - t0), 256, 0, s>>>(B, G, g->d_tiles, t0, g->d_scr_off, 0,
-                                                                       g->d_scratch, v, out->V, out->W0, out->SOx,
-                                                                       out->SOy, out->SOz);
-      Q4C_CUDA(cudaGetLastError());
-    }
+    if (q4c_status st = products_fp64_wave(g, static_cast<int>(wv), v, out, s)) return st;
   }
   return mirror_and_spinor(g, out, s);
 }
@@ -472,19 +476,26 @@ __global__ void k_density_fp64(DevBasis B, DevGrid G, int64_t b0, const int64_t*
   }
 }
 
-q4c_status density_fp64(const q4c_tables* t, const q4c_grid* g, const double* P, double* n, cudaStream_t s) {
-  const DevBasis B = t->view();
-  const DevGrid G = g->view();
+// the density of one wave (its basis tiles in place)
+q4c_status density_fp64_wave(const q4c_grid* g, int wv, const double* P, double* n, cudaStream_t s) {
+  const int64_t b0 = g->wave_b0[wv], b1 = g->wave_b0[wv + 1];
+  if (b1 <= b0) return Q4C_OK;
   const size_t smem = sizeof(double) * kRows * std::max(g->max_nb, 1);
   Q4C_CUDA(cudaFuncSetAttribute(k_density_fp64, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 static_cast<int>(smem)));
+  KernelScope ks("density_fp64", s);
+  k_density_fp64<<<static_cast<unsigned>(b1 - b0), 128, smem, s>>>(g->tables->view(), g->view(), b0, g->d_scr_off,
+                                                                   g->d_scratch, P, n);
+  Q4C_CUDA(cudaGetLastError());
+  return Q4C_OK;
+}
+
+q4c_status density_fp64(const q4c_tables* t, const q4c_grid* g, const double* P, double* n, cudaStream_t s) {
   for (size_t wv = 0; wv + 1 < g->wave_b0.size(); ++wv) {
     const int64_t b0 = g->wave_b0[wv], b1 = g->wave_b0[wv + 1];
     if (b1 <= b0) continue;
     if (q4c_status st = launch_basis_tiles(t, g, b0, b1, nullptr, nullptr, s)) return st;
-    KernelScope ks("density_fp64", s);
-    k_density_fp64<<<static_cast<unsigned>(b1 - b0), 128, smem, s>>>(B, G, b0, g->d_scr_off, g->d_scratch, P, n);
-    Q4C_CUDA(cudaGetLastError());
+    if (q4c_status st = density_fp64_wave(g, static_cast<int>(wv), P, n, s)) return st;
   }
   return Q4C_OK;
 }
@@ -555,22 +566,31 @@ __global__ void k_backward_fp64(DevBasis B, DevGrid G, int64_t b0, const int64_t
   }
 }
 
-q4c_status backward_fp64(const q4c_tables* t, const q4c_grid* g, const q4c_matrices* Gm, double* dLdv,
-                         cudaStream_t s, bool weighted) {
-  const DevBasis B = t->view();
-  const DevGrid G = g->view();
+// the adjoint (weighted) or gradient density (unweighted) of one wave (its
+// basis tiles in place)
+q4c_status backward_fp64_wave(const q4c_grid* g, int wv, const q4c_matrices* Gm, double* dLdv, bool weighted,
+                              cudaStream_t s) {
+  const int64_t b0 = g->wave_b0[wv], b1 = g->wave_b0[wv + 1];
+  if (b1 <= b0) return Q4C_OK;
   const size_t smem = sizeof(double) * 5 * kRowsB * std::max(g->max_nb, 1);
   Q4C_CUDA(cudaFuncSetAttribute(k_backward_fp64, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 static_cast<int>(smem)));
+  KernelScope ks("backward_fp64", s);
+  k_backward_fp64<<<static_cast<unsigned>(b1 - b0), 128, smem, s>>>(g->tables->view(), g->view(), b0,
+                                                                    g->d_scr_off, g->d_scratch, Gm->V, Gm->W0,
+                                                                    Gm->SOx, Gm->SOy, Gm->SOz, dLdv,
+                                                                    weighted ? 1 : 0);
+  Q4C_CUDA(cudaGetLastError());
+  return Q4C_OK;
+}
+
+q4c_status backward_fp64(const q4c_tables* t, const q4c_grid* g, const q4c_matrices* Gm, double* dLdv,
+                         cudaStream_t s, bool weighted) {
   for (size_t wv = 0; wv + 1 < g->wave_b0.size(); ++wv) {
     const int64_t b0 = g->wave_b0[wv], b1 = g->wave_b0[wv + 1];
     if (b1 <= b0) continue;
     if (q4c_status st = launch_basis_tiles(t, g, b0, b1, nullptr, nullptr, s)) return st;
-    KernelScope ks("backward_fp64", s);
-    k_backward_fp64<<<static_cast<unsigned>(b1 - b0), 128, smem, s>>>(B, G, b0, g->d_scr_off, g->d_scratch, Gm->V,
-                                                                      Gm->W0, Gm->SOx, Gm->SOy, Gm->SOz, dLdv,
-                                                                      weighted ? 1 : 0);
-    Q4C_CUDA(cudaGetLastError());
+    if (q4c_status st = backward_fp64_wave(g, static_cast<int>(wv), Gm, dLdv, weighted, s)) return st;
   }
   return Q4C_OK;
 }

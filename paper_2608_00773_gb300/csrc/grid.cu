@@ -909,7 +909,7 @@ extern "C" q4c_status grid_partition(const q4c_grid_desc* d, const q4c_tables* t
     if (e == cudaSuccess) e = cudaMalloc(&g->d_colexp, sizeof(int) * 8 * std::max<int64_t>(g->h_bat_fn_ptr[nB], 1));
     if (e == cudaSuccess) e = cudaMalloc(&g->d_rowexp, sizeof(int) * 4 * nP);
     if (e == cudaSuccess) e = cudaMalloc(&g->d_gsl, static_cast<size_t>(std::max<int64_t>(g->gsl_bytes, 16)));
-    if (e == cudaSuccess) e = cudaMalloc(&g->d_gdf, sizeof(float2) * 5 * std::max<int64_t>(g->nnz, 1));
+    if (e == cudaSuccess) e = cudaMalloc(&g->d_gdf, sizeof(float2) * 10 * std::max<int64_t>(g->nnz, 1));
     if (e == cudaSuccess) e = cudaMalloc(&g->d_bat_idx, sizeof(int) * g->idx_entries);
     if (e == cudaSuccess) e = cudaMalloc(&g->d_split_mag, sizeof(float) * 128 * max_wave_items);
     if (e == cudaSuccess) e = cudaMalloc(&g->d_dpad, sizeof(float2) * kDPitch * std::max<int64_t>(nB, 1));

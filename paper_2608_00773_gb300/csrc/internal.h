@@ -210,7 +210,7 @@ struct q4c_grid {
   int64_t* d_bat_idx_ptr = nullptr;
   int* d_bat_idx = nullptr;                // per batch n_b x n_b value offsets (-1 outside)
   unsigned* d_status = nullptr;            // bit 0: a bounded wait expired
-  float2* d_gdf = nullptr;                 // [5][nnz] FP32-pair copies of the density/adjoint matrices
+  float2* d_gdf = nullptr;                 // [10][nnz] FP32-pair copies of the density (0-4) and adjoint (5-9) matrices
   int64_t split_ws_bytes = 0;
   void* d_split_ws = nullptr;
   q4c::DevGrid view() const;
@@ -250,6 +250,22 @@ q4c_status integrate_split(const q4c_tables* t, const q4c_grid* g, const double*
                            cudaStream_t s);
 q4c_status integrate_columns_split(const q4c_tables* t, const q4c_grid* g, const double* v, double* F,
                                    cudaStream_t s);
+// per-wave pieces of the split path, for the fused pass (fused.cu)
+q4c_status products_wave(const q4c_grid* g, int wv, const q4c_matrices* out, cudaStream_t s);
+q4c_status rowdot_prepare(const q4c_grid* g, const double* const mats[5], int slot0, const float2* mdf[5],
+                          unsigned* present, cudaStream_t s);
+q4c_status rowdot_wave(const q4c_grid* g, int wv, int mode, const float2* const mdf[5], unsigned present,
+                       bool weighted, double* out, cudaStream_t s);
+// per-wave pieces of the FP64 path
+q4c_status products_fp64_wave(const q4c_grid* g, int wv, const double* v, const q4c_matrices* out,
+                              cudaStream_t s);
+q4c_status density_fp64_wave(const q4c_grid* g, int wv, const double* P, double* n, cudaStream_t s);
+q4c_status backward_fp64_wave(const q4c_grid* g, int wv, const q4c_matrices* G, double* dLdv, bool weighted,
+                              cudaStream_t s);
+// the fused pass (fused.cu)
+q4c_status scf_pass(const q4c_tables* t, const q4c_grid* g, const double* v, const q4c_matrices* H,
+                    const q4c_matrices* P, double* n, const q4c_matrices* Gm, double* dLdv, bool split,
+                    cudaStream_t s);
 // grid.cu
 q4c_status becke_weights(const double* d_raw_xyz, const double* d_base_w, int64_t n_raw, int pts_per_atom,
                          const double* d_atom_xyz, const double* d_inv_rab, int n_atoms, double r_c, double r_nb,

@@ -535,6 +535,62 @@ __global__ void __launch_bounds__(kThreads, 1)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
 }
 
+// FP32-pair copies of the present matrices into slots [slot0, slot0 + 5) of
+// the grid's buffer; returns the mask of present matrices
+q4c_status prepare(const q4c_grid* g, const double* const mats[5], int slot0, const float2* mdf[5],
+                   unsigned* present, cudaStream_t s) {
+  int dev = 0, n_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+  *present = 0;
+  KernelScope ks("split_gslice", s);
+  for (int m = 0; m < 5; ++m) {
+    mdf[m] = nullptr;
+    if (!mats[m] || g->nnz == 0) continue;
+    float2* dst = g->d_gdf + (slot0 + m) * g->nnz;
+    const unsigned blocks = static_cast<unsigned>(std::min<int64_t>((g->nnz + 255) / 256, 8 * n_sm));
+    k_to_df<<<blocks, 256, 0, s>>>(mats[m], g->nnz, dst);
+    mdf[m] = dst;
+    *present |= 1u << m;
+  }
+  Q4C_CUDA(cudaGetLastError());
+  return Q4C_OK;
+}
+
+// one wave [b0, b1) of the density (MODE 0) or adjoint (MODE 1): G' digit
+// blocks and the row-dot kernel; the wave's offset tables and basis tiles
+// (with per-point exponents) must already be in place
+template <int MODE>
+q4c_status wave(const q4c_grid* g, int wv, const float2* const mdf[5], unsigned present, bool weighted,
+                double* out, cudaStream_t s) {
+  const int64_t b0 = g->wave_b0[wv], b1 = g->wave_b0[wv + 1];
+  if (b1 <= b0) return Q4C_OK;
+  int dev = 0, n_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+  Q4C_CUDA(cudaFuncSetAttribute(k_split_rowdot<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemTotal));
+  {
+    KernelScope ks("split_gslice", s);
+    k_gslice<<<dim3(static_cast<unsigned>(b1 - b0), MODE == 0 ? 1 : 5), 256, 0, s>>>(
+        g->view(), b0, MODE == 0 ? 5 : 2, mdf[0], mdf[1], mdf[2], mdf[3], mdf[4], g->d_gsl_off,
+        reinterpret_cast<uint32_t*>(g->d_gsl));
+  }
+  Q4C_CUDA(cudaGetLastError());
+  const int64_t i0 = g->rd_w0[wv], i1 = g->rd_w0[wv + 1];
+  const int n_items = static_cast<int>(i1 - i0);
+  if (n_items == 0) return Q4C_OK;
+  const int grid = std::min(n_items, n_sm);
+  {
+    KernelScope ks(MODE == 0 ? "split_density" : "split_backward", s);
+    k_split_rowdot<MODE><<<grid, kThreads, kSmemTotal, s>>>(
+        g->view(), g->d_rd_items + i0, n_items, reinterpret_cast<const CUtensorMap*>(g->d_tmaps) + g->n_batches,
+        g->d_scr_off, g->d_scratch, g->d_rowexp, g->d_gsl_off, reinterpret_cast<const unsigned char*>(g->d_gsl),
+        present, weighted ? 1 : 0, out, g->d_status);
+  }
+  Q4C_CUDA(cudaGetLastError());
+  return Q4C_OK;
+}
+
 template <int MODE>
 q4c_status run(const q4c_tables* t, const q4c_grid* g, const double* const mats[5], double* out, cudaStream_t s,
                bool weighted) {
@@ -542,57 +598,32 @@ q4c_status run(const q4c_tables* t, const q4c_grid* g, const double* const mats[
     set_error("the split density/adjoint need at most 512 active functions per batch");
     return Q4C_EUNSUPPORTED;
   }
-  const int n_waves = static_cast<int>(g->wave_b0.size()) - 1;
-  Q4C_CUDA(cudaFuncSetAttribute(k_split_rowdot<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemTotal));
-  int dev = 0, n_sm = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
-  const char* name = MODE == 0 ? "split_density" : "split_backward";
-  // FP32-pair copies of the matrices
-  const float2* mdf[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  const float2* mdf[5];
   unsigned present = 0;
-  {
-    KernelScope ks("split_gslice", s);
-    for (int m = 0; m < 5; ++m) {
-      if (!mats[m] || g->nnz == 0) continue;
-      float2* dst = g->d_gdf + m * g->nnz;
-      const unsigned blocks = static_cast<unsigned>(std::min<int64_t>((g->nnz + 255) / 256, 8 * n_sm));
-      k_to_df<<<blocks, 256, 0, s>>>(mats[m], g->nnz, dst);
-      mdf[m] = dst;
-      present |= 1u << m;
-    }
-  }
-  Q4C_CUDA(cudaGetLastError());
+  if (q4c_status st = prepare(g, mats, 0, mdf, &present, s)) return st;
+  const int n_waves = static_cast<int>(g->wave_b0.size()) - 1;
   for (int wv = 0; wv < n_waves; ++wv) {
     const int64_t b0 = g->wave_b0[wv], b1 = g->wave_b0[wv + 1];
     if (b1 <= b0) continue;
     if (q4c_status st = launch_fill_idx(t, g, b0, b1, s)) return st;
-    {
-      KernelScope ks("split_gslice", s);
-      k_gslice<<<dim3(static_cast<unsigned>(b1 - b0), MODE == 0 ? 1 : 5), 256, 0, s>>>(
-          g->view(), b0, MODE == 0 ? 5 : 2, mdf[0], mdf[1], mdf[2], mdf[3], mdf[4], g->d_gsl_off,
-          reinterpret_cast<uint32_t*>(g->d_gsl));
-    }
-    Q4C_CUDA(cudaGetLastError());
     if (q4c_status st = launch_basis_df(t, g, b0, b1, nullptr, nullptr, g->d_rowexp, MODE == 0 ? 1 : 4, s)) return st;
-    const int64_t i0 = g->rd_w0[wv], i1 = g->rd_w0[wv + 1];
-    const int n_items = static_cast<int>(i1 - i0);
-    if (n_items == 0) continue;
-    const int grid = std::min(n_items, n_sm);
-    {
-      KernelScope ks(name, s);
-      k_split_rowdot<MODE><<<grid, kThreads, kSmemTotal, s>>>(
-          g->view(), g->d_rd_items + i0, n_items, reinterpret_cast<const CUtensorMap*>(g->d_tmaps) + g->n_batches,
-          g->d_scr_off, g->d_scratch, g->d_rowexp,
-          g->d_gsl_off, reinterpret_cast<const unsigned char*>(g->d_gsl), present, weighted ? 1 : 0, out,
-          g->d_status);
-    }
-    Q4C_CUDA(cudaGetLastError());
+    if (q4c_status st = wave<MODE>(g, wv, mdf, present, weighted, out, s)) return st;
   }
   return Q4C_OK;
 }
 
 }  // namespace rowdot
+
+q4c_status rowdot_prepare(const q4c_grid* g, const double* const mats[5], int slot0, const float2* mdf[5],
+                          unsigned* present, cudaStream_t s) {
+  return rowdot::prepare(g, mats, slot0, mdf, present, s);
+}
+
+q4c_status rowdot_wave(const q4c_grid* g, int wv, int mode, const float2* const mdf[5], unsigned present,
+                       bool weighted, double* out, cudaStream_t s) {
+  return mode == 0 ? rowdot::wave<0>(g, wv, mdf, present, weighted, out, s)
+                   : rowdot::wave<1>(g, wv, mdf, present, weighted, out, s);
+}
 
 q4c_status density_split(const q4c_tables* t, const q4c_grid* g, const double* P, double* n, cudaStream_t s) {
   const double* mats[5] = {P, nullptr, nullptr, nullptr, nullptr};

@@ -471,6 +471,35 @@ __global__ void __launch_bounds__(kThreads, 1)
 
 }  // namespace split
 
+// the products of one wave [b0, b1): rounding constants and the products
+// kernel over the wave's items; the wave's offset tables, basis tiles,
+// column exponents and D row must already be in place
+q4c_status products_wave(const q4c_grid* g, int wv, const q4c_matrices* out, cudaStream_t s) {
+  const int64_t i0 = g->split_w0[wv], i1 = g->split_w0[wv + 1];
+  const int n_items = static_cast<int>(i1 - i0);
+  if (n_items == 0) return Q4C_OK;
+  Q4C_CUDA(cudaFuncSetAttribute(split::k_split_products, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                split::kSmemTotal));
+  int dev = 0, n_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+  {
+    KernelScope ks("split_prep", s);
+    split::k_item_prep<<<n_items, 128, 0, s>>>(g->view(), g->d_split_items + i0, g->d_colexp, g->d_split_mag);
+  }
+  Q4C_CUDA(cudaGetLastError());
+  const int grid = std::min(n_items, n_sm);
+  {
+    KernelScope ks("split_products", s);
+    split::k_split_products<<<grid, split::kThreads, split::kSmemTotal, s>>>(
+        g->view(), g->d_split_items + i0, g->d_split_steps + i0, n_items,
+        reinterpret_cast<const CUtensorMap*>(g->d_tmaps), g->d_dpad, g->d_split_mag, out->V, out->W0, out->SOx,
+        out->SOy, out->SOz, g->d_status);
+  }
+  Q4C_CUDA(cudaGetLastError());
+  return Q4C_OK;
+}
+
 q4c_status integrate_split(const q4c_tables* t, const q4c_grid* g, const double* v, const q4c_matrices* out,
                            cudaStream_t s) {
   if (g->max_np > 341) {  // exactness bound of the level sums (and the D buffer)
@@ -480,33 +509,12 @@ q4c_status integrate_split(const q4c_tables* t, const q4c_grid* g, const double*
   double* outs[5] = {out->V, out->W0, out->SOx, out->SOy, out->SOz};
   for (double* o : outs) Q4C_CUDA(cudaMemsetAsync(o, 0, sizeof(double) * g->nnz, s));
   const int n_waves = static_cast<int>(g->wave_b0.size()) - 1;
-  Q4C_CUDA(cudaFuncSetAttribute(split::k_split_products, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                split::kSmemTotal));
-  int dev = 0, n_sm = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
   for (int wv = 0; wv < n_waves; ++wv) {
     const int64_t b0 = g->wave_b0[wv], b1 = g->wave_b0[wv + 1];
     if (b1 <= b0) continue;
     if (q4c_status st = launch_fill_idx(t, g, b0, b1, s)) return st;
     if (q4c_status st = launch_basis_df(t, g, b0, b1, v, g->d_colexp, nullptr, 4, s, g->d_dpad)) return st;
-    const int64_t i0 = g->split_w0[wv], i1 = g->split_w0[wv + 1];
-    const int n_items = static_cast<int>(i1 - i0);
-    if (n_items == 0) continue;
-    {
-      KernelScope ks("split_prep", s);
-      split::k_item_prep<<<n_items, 128, 0, s>>>(g->view(), g->d_split_items + i0, g->d_colexp, g->d_split_mag);
-    }
-    Q4C_CUDA(cudaGetLastError());
-    const int grid = std::min(n_items, n_sm);
-    {
-      KernelScope ks("split_products", s);
-      split::k_split_products<<<grid, split::kThreads, split::kSmemTotal, s>>>(
-          g->view(), g->d_split_items + i0, g->d_split_steps + i0, n_items,
-          reinterpret_cast<const CUtensorMap*>(g->d_tmaps), g->d_dpad, g->d_split_mag, out->V, out->W0, out->SOx,
-          out->SOy, out->SOz, g->d_status);
-    }
-    Q4C_CUDA(cudaGetLastError());
+    if (q4c_status st = products_wave(g, wv, out, s)) return st;
   }
   return mirror_and_spinor(g, out, s);
 }
