@@ -303,6 +303,7 @@ def main():
     ap.add_argument("--cpu-stride-all", type=int, default=2, help="all-core sample of the cpu baseline")
     ap.add_argument("--ref-stride", type=int, default=7)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="keep the default tile shapes (skip q4c_autotune)")
     ap.add_argument("--separate", action="store_true",
                     help="time the three separate calls instead of the one-pass q4c_scf_pass")
     ap.add_argument("--print-source-hash", action="store_true",
@@ -347,6 +348,9 @@ def main():
     fl = step_flops(info)
     F_step = sum(fl.values())
     stream = torch.cuda.current_stream()
+
+    # tile shapes of the split path, per batch-size bucket, by the library's tuner (setup, untimed)
+    tiling = q.q4c_autotune(tables, grid, v) if args.prec == "split" and not args.no_tune else q.q4c_grid_tiling(grid)
 
     # precision per phase: the requested one where the library provides it
     phase_prec = {}
@@ -583,6 +587,8 @@ def main():
                             if fused else "q4c_integrate + q4c_density + q4c_integrate_backward"),
                    "l2": "512 MB buffer written between timed steps", "replicas": world},
         "flops_per_step": fl,
+        "tiling": [{"nb_max": t["nb_max"] if t["nb_max"] < (1 << 29) else None, "k_steps_per_stage": t["k_steps"],
+                    "batches": t["batches"], "tuner_ms": [t["ms_one"], t["ms_two"]]} for t in tiling],
         "phase_ms": {k: v_[0] / args.steps for k, v_ in kern.items()},
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": launches_total,
         **extra,

@@ -401,6 +401,33 @@ Q4C_API q4c_status q4c_scf_pass(const q4c_tables* tables, const q4c_grid* grid, 
                                 const q4c_matrices* H, const q4c_matrices* P, double* n_dev,
                                 const q4c_matrices* G, double* dLdv_dev, q4c_precision prec, q4c_stream stream);
 
+/* Tile shapes of the split path's batch products, chosen per batch-size
+ * bucket (the active functions n_b of a batch: <= 32, <= 64, <= 128, more;
+ * Q4C_TILE_BUCKETS buckets).  A shape is the number of 16-point K-steps one
+ * pipeline stage of the tensor-core kernel carries: 1 (four stages in
+ * flight) or 2 (two stages of twice the points, half the handshakes per
+ * point); the 64-function tiles and their N width (the functions of the B
+ * tile rounded up to 16) follow from the batch.  A new grid uses 1 for every
+ * bucket.  Not in the paper: a library control of the kernels.
+ *
+ * q4c_autotune times both shapes on the grid's first wave of batches with
+ * potential v_dev (each bucket's products launched once untimed and three
+ * times between CUDA events on `stream`, into scratch outputs it allocates
+ * and frees), keeps the faster one per bucket in the grid, and synchronises
+ * the stream.  The choice applies to every later split-path integration
+ * (q4c_integrate, q4c_integrate_columns, q4c_scf_pass) on the grid; results
+ * do not depend on it beyond the order of FP64 additions.
+ * q4c_grid_tiling reports a bucket: its largest n_b, the shape in use, the
+ * grid's batches in it, and the tuner's mean time per launch for one and two
+ * K-steps (-1 if not timed); NULL outputs are skipped.
+ * q4c_grid_set_tiling sets a bucket's shape by hand (1 or 2).  Q4C_EINVAL
+ * for a bucket outside 0..Q4C_TILE_BUCKETS-1 or another shape. */
+#define Q4C_TILE_BUCKETS 4
+Q4C_API q4c_status q4c_autotune(const q4c_tables* tables, q4c_grid* grid, const double* v_dev, q4c_stream stream);
+Q4C_API q4c_status q4c_grid_tiling(const q4c_grid* grid, int32_t bucket, int32_t* nb_max, int32_t* k_steps,
+                                   int64_t* batches, double* ms_one, double* ms_two);
+Q4C_API q4c_status q4c_grid_set_tiling(q4c_grid* grid, int32_t bucket, int32_t k_steps);
+
 /* q4c_integrate with prec = Q4C_FP64 for callers that cannot allocate device
  * memory when they integrate (an application whose own pool owns the device
  * memory, or a loop that must not pay for cudaMalloc/cudaFree, which can

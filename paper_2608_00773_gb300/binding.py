@@ -27,7 +27,7 @@ EXPORTS = ["nao_tabulate", "nao_tabulate_knots", "q4c_tables_destroy", "q4c_tabl
            "q4c_grid_get_info", "q4c_grid_export", "q4c_grid_export_shifts", "q4c_grid_kpattern", "q4c_kfold", "q4c_grid_points", "q4c_integrate", "q4c_density", "q4c_density_full",
            "q4c_spinor_basis", "q4c_spinor_transform", "q4c_spinor_density_matrices", "q4c_grid_batch_spinors",
            "q4c_tables_set_columns", "q4c_integrate_columns", "q4c_tables_set_kappa", "q4c_spinor_nnz",
-           "q4c_integrate_backward", "q4c_scf_pass", "q4c_integrate_noalloc", "q4c_basis_eval", "q4c_grid_status", "q4c_set_wait_limit_ns", "q4c_profile", "q4c_profile_read",
+           "q4c_integrate_backward", "q4c_scf_pass", "q4c_autotune", "q4c_grid_tiling", "q4c_grid_set_tiling", "q4c_integrate_noalloc", "q4c_basis_eval", "q4c_grid_status", "q4c_set_wait_limit_ns", "q4c_profile", "q4c_profile_read",
            "q4c_last_error"]
 
 
@@ -105,6 +105,9 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     L.q4c_scf_pass.argtypes = [vp, vp, vp, C.POINTER(Matrices), C.POINTER(Matrices), vp, C.POINTER(Matrices), vp,
                                C.c_int, vp]
     L.q4c_integrate_noalloc.argtypes = [vp, vp, vp, C.POINTER(Matrices), vp]
+    L.q4c_autotune.argtypes = [vp, vp, vp, vp]
+    L.q4c_grid_tiling.argtypes = [vp, i32, vp, vp, vp, vp, vp]
+    L.q4c_grid_set_tiling.argtypes = [vp, i32, i32]
     L.q4c_basis_eval.argtypes = [vp, vp, i64, vp, vp, vp, vp]
     L.q4c_grid_status.argtypes = [vp, vp]
     L.q4c_set_wait_limit_ns.argtypes = [C.c_uint64]
@@ -428,6 +431,30 @@ def q4c_scf_pass(tables: Tables, grid: Grid, v=None, P: Optional[Sequence] = Non
                                C.byref(mP) if mP else None, _ptr(n), C.byref(mG) if mG else None, _ptr(g),
                                _prec(prec), _stream(stream)))
     return H, n, g
+
+
+TILE_BUCKETS = 4
+
+
+def q4c_grid_tiling(grid: Grid):
+    """Per batch-size bucket: dict(nb_max, k_steps, batches, ms_one, ms_two)."""
+    out = []
+    for k in range(TILE_BUCKETS):
+        nb, ks, nbt = C.c_int32(), C.c_int32(), C.c_int64()
+        m1, m2 = C.c_double(), C.c_double()
+        _check(load().q4c_grid_tiling(grid.h, k, C.byref(nb), C.byref(ks), C.byref(nbt), C.byref(m1), C.byref(m2)))
+        out.append(dict(nb_max=nb.value, k_steps=ks.value, batches=nbt.value, ms_one=m1.value, ms_two=m2.value))
+    return out
+
+
+def q4c_autotune(tables: Tables, grid: Grid, v, stream=None):
+    """Choose the split path's stage shape per batch-size bucket by timing both; returns q4c_grid_tiling."""
+    _check(load().q4c_autotune(tables.h, grid.h, _ptr(v), _stream(stream)))
+    return q4c_grid_tiling(grid)
+
+
+def q4c_grid_set_tiling(grid: Grid, bucket: int, k_steps: int):
+    _check(load().q4c_grid_set_tiling(grid.h, int(bucket), int(k_steps)))
 
 
 def q4c_basis_eval(tables: Tables, grid: Grid, xyz, stream=None):

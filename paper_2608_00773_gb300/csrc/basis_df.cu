@@ -275,8 +275,8 @@ __global__ void __launch_bounds__(256, 4) k_basis_df(DevBasis B, DevGrid G, DfTa
         const float h = static_cast<float>(Dp);
         dpad[b * kDPitch + p] = make_float2(h, static_cast<float>(Dp - static_cast<double>(h)));
       }
-    } else if (dpad && a == 0 && p < ((np + 15) & ~15)) {
-      dpad[b * kDPitch + p] = make_float2(0.f, 0.f);  // the K-step of 16 points reads zeros past n_p
+    } else if (dpad && a == 0 && p < ((np + 31) & ~31)) {
+      dpad[b * kDPitch + p] = make_float2(0.f, 0.f);  // stages of 16 or 32 points read zeros past n_p
     }
     const df vdf = (NQ == 2 && live) ? split_d(v[p0 + p]) : df{0.f, 0.f};
     int lmax = 0;

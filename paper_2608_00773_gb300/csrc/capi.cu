@@ -129,3 +129,39 @@ extern "C" q4c_status q4c_scf_pass(const q4c_tables* t, const q4c_grid* g, const
     return Q4C_ENOMEM;
   }
 }
+
+extern "C" q4c_status q4c_autotune(const q4c_tables* t, q4c_grid* g, const double* v, q4c_stream stream) {
+  if (q4c_status st = check_pair(t, g, "q4c_autotune")) return st;
+  Q4C_CHECK_ARG(v, "q4c_autotune: NULL potential");
+  try {
+    return autotune_split(t, g, v, reinterpret_cast<cudaStream_t>(stream));
+  } catch (const std::exception& e) {
+    set_error(std::string("q4c_autotune: ") + e.what());
+    return Q4C_ENOMEM;
+  }
+}
+
+extern "C" q4c_status q4c_grid_tiling(const q4c_grid* g, int32_t bucket, int32_t* nb_max, int32_t* k_steps,
+                                      int64_t* batches, double* ms_one, double* ms_two) {
+  Q4C_CHECK_ARG(g, "q4c_grid_tiling: NULL grid");
+  Q4C_CHECK_ARG(bucket >= 0 && bucket < kTileBuckets, "q4c_grid_tiling: bucket out of range");
+  if (nb_max) *nb_max = kBucketNb[bucket];
+  if (k_steps) *k_steps = g->split_ks[bucket];
+  if (batches) {
+    int64_t n = 0;
+    for (int64_t b = 0; b < g->n_batches; ++b)
+      if (tile_bucket(g->h_bat_fn_ptr[b + 1] - g->h_bat_fn_ptr[b]) == bucket) ++n;
+    *batches = n;
+  }
+  if (ms_one) *ms_one = g->tune_ms[bucket][0];
+  if (ms_two) *ms_two = g->tune_ms[bucket][1];
+  return Q4C_OK;
+}
+
+extern "C" q4c_status q4c_grid_set_tiling(q4c_grid* g, int32_t bucket, int32_t k_steps) {
+  Q4C_CHECK_ARG(g, "q4c_grid_set_tiling: NULL grid");
+  Q4C_CHECK_ARG(bucket >= 0 && bucket < kTileBuckets, "q4c_grid_set_tiling: bucket out of range");
+  Q4C_CHECK_ARG(k_steps == 1 || k_steps == 2, "q4c_grid_set_tiling: k_steps must be 1 or 2");
+  g->split_ks[bucket] = k_steps;
+  return Q4C_OK;
+}

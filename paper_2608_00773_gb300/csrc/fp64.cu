@@ -400,28 +400,13 @@ q4c_status integrate_columns_fp64(const q4c_tables* t, const q4c_grid* g, const 
   const DevGrid G = g->view();
   for (size_t wv = 0; wv + 1 < g->wave_b0.size(); ++wv) {
     const int64_t b0 = g->wave_b0[wv], b1 = g->wave_b0[wv + 1];
-    if (b1 <= b0) continue;
-    std::vector<int4> tiles;  // every tile pair (ti, tj) of the wave's batches
-    for (int64_t b = b0; b < b1; ++b) {
-      const int nt = static_cast<int>((g->h_bat_fn_ptr[b + 1] - g->h_bat_fn_ptr[b] + kT - 1) / kT);
-      for (int i = 0; i < nt; ++i)
-        for (int j = 0; j < nt; ++j) tiles.push_back(make_int4(static_cast<int>(b), i, j, 0));
-    }
-    if (tiles.empty()) continue;
+    const int64_t t0 = g->colt_w0[wv], t1 = g->colt_w0[wv + 1];  // every tile pair of the wave's batches
+    if (b1 <= b0 || t1 <= t0) continue;
     if (q4c_status st = launch_basis_tiles(t, g, b0, b1, nullptr, nullptr, s)) return st;
-    int4* d_tiles = nullptr;
-    Q4C_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&d_tiles), sizeof(int4) * tiles.size(), s));
-    Q4C_CUDA(cudaMemcpyAsync(d_tiles, tiles.data(), sizeof(int4) * tiles.size(), cudaMemcpyHostToDevice, s));
-    {
-      KernelScope ks("columns_fp64", s);
-      k_columns_fp64<<<static_cast<unsigned>(tiles.size()), 256, 0, s>>>(B, G, d_tiles, g->d_scr_off, g->d_scratch,
-                                                                          v, t->d_col_eps, t->d_col_coef, F);
-    }
-    const cudaError_t e = cudaGetLastError();
-    // the host list must outlive the asynchronous copy
-    Q4C_CUDA(cudaStreamSynchronize(s));
-    Q4C_CUDA(cudaFreeAsync(d_tiles, s));
-    Q4C_CUDA(e);
+    KernelScope ks("columns_fp64", s);
+    k_columns_fp64<<<static_cast<unsigned>(t1 - t0), 256, 0, s>>>(B, G, g->d_col_tiles + t0, g->d_scr_off,
+                                                                    g->d_scratch, v, t->d_col_eps, t->d_col_coef, F);
+    Q4C_CUDA(cudaGetLastError());
   }
   return Q4C_OK;
 }

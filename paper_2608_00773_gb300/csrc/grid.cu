@@ -758,6 +758,17 @@ extern "C" q4c_status grid_partition(const q4c_grid_desc* d, const q4c_tables* t
   g->wave_b0.push_back(nB);
   g->wave_t0.push_back(static_cast<int64_t>(tiles.size()));
   g->scratch_doubles = std::max<int64_t>(peak, 1);
+  // per-column operator on the FP64 path (not symmetric): every tile pair
+  std::vector<int4> col_tiles;
+  g->colt_w0.push_back(0);
+  for (size_t wv = 0; wv + 1 < g->wave_b0.size(); ++wv) {
+    for (int64_t b = g->wave_b0[wv]; b < g->wave_b0[wv + 1]; ++b) {
+      const int nt = static_cast<int>((g->h_bat_fn_ptr[b + 1] - g->h_bat_fn_ptr[b] + 31) / 32);
+      for (int i = 0; i < nt; ++i)
+        for (int j = 0; j < nt; ++j) col_tiles.push_back(make_int4(static_cast<int>(b), i, j, 0));
+    }
+    g->colt_w0.push_back(static_cast<int64_t>(col_tiles.size()));
+  }
 
   // per-batch dense tables of pattern offsets, idx[i * n_b + j] = value
   // offset of element (i, j) (local functions) or -1 outside the pattern;
@@ -777,53 +788,67 @@ extern "C" q4c_status grid_partition(const q4c_grid_desc* d, const q4c_tables* t
 
   // ---- split path: (batch, output, ti, tj) items per wave, tiles of 64
   // functions, tile pairs ti <= tj only (SO: the antisymmetric part of A_k on
-  // diagonal pairs, two K-concatenated products on off-diagonal ones).
-  // Batches with the most work first; the items of one batch stay adjacent
-  // (W0, three products, leading) so that concurrent CTAs share its tiles in L2.
+  // diagonal pairs, two K-concatenated products on off-diagonal ones).  The
+  // batches of a wave are grouped by batch-size bucket (each bucket is one
+  // launch with its own stage shape), the costliest first within a bucket;
+  // the items of one batch stay adjacent (W0, three products, leading) so
+  // that concurrent CTAs share its tiles in L2.
   std::vector<int4> sitems;
-  std::vector<int> ssteps;
   int64_t max_wave_items = 1;
   g->split_w0.push_back(0);
   for (size_t wv = 0; wv + 1 < g->wave_b0.size(); ++wv) {
-    std::vector<std::pair<double, int64_t>> bl;
+    struct Key {
+      int bucket;
+      double cost;
+      int64_t b;
+    };
+    std::vector<Key> bl;
     for (int64_t b = g->wave_b0[wv]; b < g->wave_b0[wv + 1]; ++b) {
       const double np = static_cast<double>(bptr[b + 1] - bptr[b]);
-      const double nb = static_cast<double>(g->h_bat_fn_ptr[b + 1] - g->h_bat_fn_ptr[b]);
-      bl.push_back({np * nb * nb, b});
+      const int64_t nbi = g->h_bat_fn_ptr[b + 1] - g->h_bat_fn_ptr[b];
+      const double nb = static_cast<double>(nbi);
+      bl.push_back({tile_bucket(nbi), np * nb * nb, b});
     }
-    std::stable_sort(bl.begin(), bl.end(), [](const auto& a, const auto& b) { return a.first > b.first; });
-    for (const auto& x : bl) {
-      const int64_t b = x.second;
+    std::stable_sort(bl.begin(), bl.end(), [](const Key& x, const Key& y) {
+      return x.bucket != y.bucket ? x.bucket < y.bucket : x.cost > y.cost;
+    });
+    std::vector<int64_t> bw(kTileBuckets + 1, -1);
+    for (const Key& x : bl) {
+      for (int k = 0; k <= x.bucket; ++k)
+        if (bw[k] < 0) bw[k] = static_cast<int64_t>(sitems.size());
+      const int64_t b = x.b;
       const int nb = static_cast<int>(g->h_bat_fn_ptr[b + 1] - g->h_bat_fn_ptr[b]);
       const int nt = (nb + 63) / 64;
       for (int o : {1, 0, 2, 3, 4})
         for (int i = 0; i < nt; ++i)
-          for (int j = i; j < nt; ++j) {
-            sitems.push_back(make_int4(static_cast<int>(b), o, i, j));
-            const int n_prod = o == 1 ? 3 : (o >= 2 && i != j) ? 2 : 1;
-            ssteps.push_back(static_cast<int>((bptr[b + 1] - bptr[b] + 15) / 16) * n_prod);
-          }
+          for (int j = i; j < nt; ++j) sitems.push_back(make_int4(static_cast<int>(b), o, i, j));
     }
+    for (int k = 0; k <= kTileBuckets; ++k)
+      if (bw[k] < 0) bw[k] = static_cast<int64_t>(sitems.size());
+    g->split_bw0.insert(g->split_bw0.end(), bw.begin(), bw.end());
     max_wave_items = std::max(max_wave_items, static_cast<int64_t>(sitems.size()) - g->split_w0.back());
     g->split_w0.push_back(static_cast<int64_t>(sitems.size()));
   }
   // per-column operator (output 5): one product on every tile pair (it is
-  // not symmetric), in the same batch order
+  // not symmetric), in the same batch order and buckets
   std::vector<int4> citems;
-  std::vector<int> csteps;
   g->col_w0.push_back(0);
   for (size_t wv = 0; wv + 1 < g->wave_b0.size(); ++wv) {
+    std::vector<int64_t> bw(kTileBuckets + 1, -1);
     for (int64_t n = g->split_w0[wv]; n < g->split_w0[wv + 1]; ++n) {
       const int4 it = sitems[n];
-      if (it.y != 0 || it.z != 0 || it.w != 0) continue;  // once per batch (its first V item)
+      if (it.y != 1 || it.z != 0 || it.w != 0) continue;  // once per batch (its first item)
       const int64_t b = it.x;
-      const int nt = static_cast<int>((g->h_bat_fn_ptr[b + 1] - g->h_bat_fn_ptr[b] + 63) / 64);
+      const int64_t nbi = g->h_bat_fn_ptr[b + 1] - g->h_bat_fn_ptr[b];
+      for (int k = 0; k <= tile_bucket(nbi); ++k)
+        if (bw[k] < 0) bw[k] = static_cast<int64_t>(citems.size());
+      const int nt = static_cast<int>((nbi + 63) / 64);
       for (int i = 0; i < nt; ++i)
-        for (int j = 0; j < nt; ++j) {
-          citems.push_back(make_int4(static_cast<int>(b), 5, i, j));
-          csteps.push_back(static_cast<int>((bptr[b + 1] - bptr[b] + 15) / 16));
-        }
+        for (int j = 0; j < nt; ++j) citems.push_back(make_int4(static_cast<int>(b), 5, i, j));
     }
+    for (int k = 0; k <= kTileBuckets; ++k)
+      if (bw[k] < 0) bw[k] = static_cast<int64_t>(citems.size());
+    g->col_bw0.insert(g->col_bw0.end(), bw.begin(), bw.end());
     max_wave_items = std::max(max_wave_items, static_cast<int64_t>(citems.size()) - g->col_w0.back());
     g->col_w0.push_back(static_cast<int64_t>(citems.size()));
   }
@@ -893,9 +918,8 @@ extern "C" q4c_status grid_partition(const q4c_grid_desc* d, const q4c_tables* t
       (st = up(&g->d_blk_col, g->h_blk_col)) || (st = up(&g->d_blk_T, blk_T)) || (st = up(&g->d_blk_role, blk_role)) ||
       (st = up(&g->d_blk_shift, g->h_blk_shift)) || (st = up(&g->d_kblk_q0, g->h_kblk_q0)) ||
       (st = up(&g->d_kblk_q1, g->h_kblk_q1)) || (st = up(&g->d_kblk_off, g->h_kblk_off)) ||
-      (st = up(&g->d_scr_off, g->h_scr_off)) || (st = up(&g->d_tiles, tiles)) || (st = up(&g->d_sched, sched)) ||
-      (st = up(&g->d_split_items, sitems)) || (st = up(&g->d_split_steps, ssteps)) ||
-      (st = up(&g->d_col_items, citems)) || (st = up(&g->d_col_steps, csteps)) ||
+      (st = up(&g->d_scr_off, g->h_scr_off)) || (st = up(&g->d_tiles, tiles)) || (st = up(&g->d_col_tiles, col_tiles)) || (st = up(&g->d_sched, sched)) ||
+      (st = up(&g->d_split_items, sitems)) || (st = up(&g->d_col_items, citems)) ||
       (st = up(&g->d_rd_items, rditems)) ||
       (st = up(&g->d_bat_idx_ptr, idx_ptr)) ||
       (st = up(&g->d_gsl_off, gsl_off))) {
@@ -937,8 +961,8 @@ extern "C" void q4c_grid_destroy(q4c_grid* g) {
   void* ptrs[] = {g->d_xyz, g->d_x, g->d_y, g->d_z, g->d_w, g->d_atom_xyz, g->d_atom_sp, g->d_atom_fn0,
                   g->d_pt_ptr, g->d_bat_atom_ptr, g->d_bat_atoms, g->d_bat_atom_fn0, g->d_bat_fn_ptr,
                   g->d_fn_info, g->d_bat_pair_ptr, g->d_pair_off, g->d_blk_off, g->d_blk_row, g->d_blk_col,
-                  g->d_blk_T, g->d_scr_off, g->d_tiles, g->d_scratch, g->d_sched, g->d_counter, g->d_split_ws,
-                  g->d_split_items, g->d_split_steps, g->d_col_items, g->d_col_steps, g->d_split_mag, g->d_dpad, g->d_tmaps, g->d_colexp, g->d_status, g->d_rd_items, g->d_rowexp, g->d_gsl, g->d_gsl_off,
+                  g->d_blk_T, g->d_scr_off, g->d_tiles, g->d_col_tiles, g->d_scratch, g->d_sched, g->d_counter, g->d_split_ws,
+                  g->d_split_items, g->d_col_items, g->d_split_mag, g->d_dpad, g->d_tmaps, g->d_colexp, g->d_status, g->d_rd_items, g->d_rowexp, g->d_gsl, g->d_gsl_off,
                   g->d_bat_idx_ptr, g->d_bat_idx, g->d_pts_df, g->d_atoms_df, g->d_gdf,
                   g->d_c_xyz, g->d_c_sp, g->d_blk_role, g->d_blk_shift, g->d_kblk_q0, g->d_kblk_q1,
                   g->d_kblk_off};

@@ -14,7 +14,16 @@ namespace q4c {
 
 constexpr int kMaxL = 4;
 constexpr int kMaxBatch = 1024;
-constexpr int kDPitch = 352;  // points per batch row of the D = w v table (>= 16 * ceil(341 / 16))
+constexpr int kDPitch = 352;  // points per batch row of the D = w v table (>= 32 * ceil(341 / 32))
+// batch-size buckets of the split path's tile-shape choice: n_b <= 32, 64,
+// 128 and above
+constexpr int kTileBuckets = 4;
+constexpr int kBucketNb[kTileBuckets] = {32, 64, 128, 1 << 30};
+inline int tile_bucket(int64_t nb) {
+  int k = 0;
+  while (k + 1 < kTileBuckets && nb > kBucketNb[k]) ++k;
+  return k;
+}
 
 // ---------------------------------------------------------------- errors
 void set_error(const std::string& msg);
@@ -183,6 +192,8 @@ struct q4c_grid {
   int64_t* d_scr_off = nullptr;
   std::vector<int64_t> wave_t0;            // [n_waves+1] ranges into the tile list
   int4* d_tiles = nullptr;                 // (batch, ti, tj, 0), ti <= tj, 32x32 tiles
+  std::vector<int64_t> colt_w0;            // [n_waves+1] ranges into d_col_tiles
+  int4* d_col_tiles = nullptr;             // per-column operator, FP64 path: every 32x32 tile pair (batch, ti, tj, 0)
   double* d_scratch = nullptr;
   int64_t scratch_doubles = 0;
   // split path: work items (batch, output, ti, tj) per wave, sorted by cost,
@@ -190,11 +201,14 @@ struct q4c_grid {
   int* d_sched = nullptr;
   int* d_counter = nullptr;                // [n_waves]
   std::vector<int64_t> split_w0;           // [n_waves+1] ranges into d_split_items
+  // [n_waves][kTileBuckets+1] item ranges of each batch-size bucket (the
+  // items of a wave are grouped by bucket), and the same for d_col_items
+  std::vector<int64_t> split_bw0, col_bw0;
+  int split_ks[4] = {1, 1, 1, 1};          // K-steps of 16 points per pipeline stage, per bucket (tuner)
+  double tune_ms[4][2] = {{-1, -1}, {-1, -1}, {-1, -1}, {-1, -1}};  // tuner timings per bucket and shape
   int4* d_split_items = nullptr;
-  int* d_split_steps = nullptr;            // K-steps of 16 points per item (3x for W0)
   std::vector<int64_t> col_w0;             // [n_waves+1] ranges into d_col_items
   int4* d_col_items = nullptr;             // per-column operator: (batch, 5, ti, tj), every tile pair
-  int* d_col_steps = nullptr;
   float* d_split_mag = nullptr;            // [items of the largest wave][128] rounding constants
   void* d_tmaps = nullptr;                 // [2][n_batches] 3-D TMA maps (points, functions, quantity) of the
                                            // tiles: boxes 16 x 64 (products), 64 x 16 (density, adjoint)
@@ -262,6 +276,8 @@ q4c_status products_fp64_wave(const q4c_grid* g, int wv, const double* v, const 
 q4c_status density_fp64_wave(const q4c_grid* g, int wv, const double* P, double* n, cudaStream_t s);
 q4c_status backward_fp64_wave(const q4c_grid* g, int wv, const q4c_matrices* G, double* dLdv, bool weighted,
                               cudaStream_t s);
+// split.cu: the tile-shape tuner (stores its choice in the grid)
+q4c_status autotune_split(const q4c_tables* t, q4c_grid* g, const double* v, cudaStream_t s);
 // the fused pass (fused.cu)
 q4c_status scf_pass(const q4c_tables* t, const q4c_grid* g, const double* v, const q4c_matrices* H,
                     const q4c_matrices* P, double* n, const q4c_matrices* Gm, double* dLdv, bool split,

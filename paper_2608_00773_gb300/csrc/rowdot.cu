@@ -104,10 +104,15 @@ __device__ __forceinline__ int fexp(float x) {  // |x| < 2^fexp(x) for x != 0
   return static_cast<int>((__float_as_uint(x) >> 23) & 0xFF) - 126;
 }
 
+// width of j-tile jt: its functions rounded up to 16 (the MMA's N
+// granularity); its G' digit tiles hold that many rows
+__device__ __forceinline__ int jt_width(int nb, int jt) { return (min(kTile, nb - jt * kTile) + 15) & ~15; }
+
 // Pre-pass: one CTA per (batch, matrix).  Column exponents e_j (|G'_ij| <=
 // 2^e_j over i), then the six digits of every G'_ij written as the B operand
-// tiles of the main kernel: block (jt, ic) = six 2 KB tiles of 64 rows (j) x
-// 16 K (i) in the no-swizzle K-major layout; padding rows and columns are 0.
+// tiles of the main kernel: block (jt, ic) (a 12 KB slot) = six tiles of
+// jt_width rows (j) x 16 K (i), 32 bytes a row, in the no-swizzle K-major
+// layout, back to back; padding rows and columns are 0.
 __global__ void __launch_bounds__(256) k_gslice(DevGrid G, int64_t b0, int anti_from, const float2* M0,
                                                 const float2* M1, const float2* M2, const float2* M3,
                                                 const float2* M4, const int64_t* __restrict__ gsl_off,
@@ -145,10 +150,12 @@ __global__ void __launch_bounds__(256) k_gslice(DevGrid G, int64_t b0, int anti_
   }
   __syncthreads();
   // pass 2: the six digits of every element, in the B-operand tile layout
-  const int words = n_jt * n_ic * (kTileBytes / 4);  // word positions (one per element pair)
+  for (int jt = 0; jt < n_jt; ++jt) {
+  const int tw = jt_width(nb, jt) * 8;  // words of one tile (one per element pair)
+  const int words = n_ic * tw;
   for (int w = threadIdx.x; w < words; w += blockDim.x) {
-    const int blk = w / (kTileBytes / 4), pos = w - blk * (kTileBytes / 4);
-    const int jt = blk / n_ic, ic = blk - jt * n_ic;
+    const int ic = w / tw, pos = w - ic * tw;
+    const int blk = jt * n_ic + ic;
     // pos -> byte offset rg*SBO + kq*LBO + r8*16 + kp*4
     const int rg = pos >> 6, kq = (pos >> 5) & 1, r8 = (pos >> 2) & 7, kp = pos & 3;
     const int j = jt * kTile + rg * 8 + r8, i = ic * kKc + kq * 8 + kp * 2;
@@ -168,8 +175,9 @@ __global__ void __launch_bounds__(256) k_gslice(DevGrid G, int64_t b0, int anti_
 #pragma unroll
     for (int s = 0; s < kSlices; ++s) {
       const __nv_bfloat162 h2 = __floats2bfloat162_rn(d0[s], d1[s]);
-      o[b_tile(s) * (kTileBytes / 4)] = *reinterpret_cast<const uint32_t*>(&h2);  // [B0, B2, B4, B1, B3, B5]
+      o[b_tile(s) * tw] = *reinterpret_cast<const uint32_t*>(&h2);  // [B0, B2, B4, B1, B3, B5]
     }
+  }
   }
 }
 
@@ -344,8 +352,9 @@ __global__ void __launch_bounds__(kThreads, 1)
           const unsigned char* src =
               gblk + (static_cast<int64_t>(P.gm) * I.n_jt * I.n_ic + static_cast<int64_t>(it.jt) * I.n_ic + it.ic) *
                          kBlockB;
-          arrive_expect_tx(gfull_bar(st), kBlockB);
-          bulk_copy(smem_u32(sA + kStageA), src, kBlockB, gfull_bar(st));
+          const uint32_t bytes = kSlices * jt_width(I.nb, it.jt) * kRowBytes;  // the j-tile's six digit tiles
+          arrive_expect_tx(gfull_bar(st), bytes);
+          bulk_copy(smem_u32(sA + kStageA), src, bytes, gfull_bar(st));
         }
         const float m = P.qf == 0 ? m0 : P.qf == 1 ? m1 : P.qf == 2 ? m2 : m3;
         // functions (4q, 4q+1) and (4q+2, 4q+3) as packed pairs
@@ -419,6 +428,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           tc_fence_after();
           const uint32_t t0 = tmem + set * kSetCols;
+          const int nbj = jt_width(I.nb, grp / n_prod);  // groups run (j-tile, product) in order
           for (int ic = 0; ic < I.n_ic; ++ic, ++g) {
             const int st = g % kStages;
             if (!mbar_wait_abort(full_bar(st), (g / kStages) & 1, s_abort, status, G.wait_ns, 32) ||
@@ -428,7 +438,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             tc_fence_after();
             const uint32_t a = smem_u32(smem + kSmemStages + st * kStage), bb = a + kStageA;
-            mma_levels(t0, a, bb, ic == 0 ? 0u : 1u, kTile);
+            mma_levels(t0, a, bb, ic == 0 ? 0u : 1u, nbj);
             mma_commit(empty_bar(st));
           }
           if (ok) mma_commit(accfull_bar(set));
@@ -462,7 +472,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int set = k & 1;
         const int j0 = jt * kTile;
         const Product P = prod_at(kk);
-        const int N = (min(kTile, I.nb - j0) + 15) & ~15;
+        const int N = jt_width(I.nb, jt);  // accumulator blocks are N columns wide
         const float2* Rrow = base + P.qr * I.plane + p;
         // R of this thread's point, 8 columns per chunk; the first chunk's
         // values load while the MMAs finish, later ones one chunk ahead
@@ -492,7 +502,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           if (c0 + 16 < N) load_R(c0 + 16, Rn);
           float v0[8], v1[8], v2[8];
           const uint32_t ta = tmem + lane_base + set * kSetCols + c0;
-          tmem_ld8x3(ta, ta + kTile, ta + 2 * kTile, v0, v1, v2);
+          tmem_ld8x3(ta, ta + N, ta + 2 * N, v0, v1, v2);
 #pragma unroll
           for (int i = 0; i < 8; ++i) {
             const df u = two_sum(v0[i], v1[i]);

@@ -65,28 +65,41 @@ constexpr int kProdWarp = 17;                // warp 17 issues the TMA loads of 
 constexpr int kThreads = 18 * 32;
 constexpr int kEpiPitch = 17;                // floats per staged TMEM lane (16 columns + pad)
 constexpr int kEpiStage = 3 * 128 * kEpiPitch * 4;  // one group's staging, 26 KB
-constexpr int kStageA = (kSlices + 1) * kTileBytes;  // [Z, A0..A5]
-constexpr int kStageB = kSlices * kTileBytes;        // [B0..B5]
-constexpr int kStage = kStageA + kStageB;            // 26 KB
-constexpr int kStages = 4;                           // ring depth of sliced operands
-// raw ring: per K-step the A and B boxes (64 functions x 16 points of (hi, lo),
-// 128-byte rows, swizzled), the step's D values and, on an item's first step,
-// the item's 128 rounding constants
-constexpr int kRaw = 4;
-constexpr int kRawTile = kTile * kKc * 8;            // 8 KB
-constexpr int kRawD = 2 * kRawTile;                  // offset of D (16 x 8 B)
-constexpr int kRawMag = kRawD + kKc * 8;             // offset of the rounding constants (128 x 4 B)
-constexpr int kRawStage = 17 * 1024;                 // 1024-aligned stages (swizzle atoms)
-constexpr int kSmemRaw = 0;
-constexpr int kSmemStages = kSmemRaw + kRaw * kRawStage;
-constexpr int kSmemEpi = kSmemStages + kStages * kStage;  // epilogue staging, 2 x 26 KB
-constexpr int kSmemBar = kSmemEpi + 2 * kEpiStage;
-constexpr int kNumBars = 2 * kStages + 5 + 2 * kRaw;  // full, empty, accfull[2], accempty[2], drain, raw full/empty
-constexpr int kSmemTotal = kSmemBar + kNumBars * 8 + 16;
-constexpr uint32_t kTmemCols = 512;  // two accumulator sets of three 64-column blocks
+constexpr int kStageA = (kSlices + 1) * kTileBytes;  // [Z, A0..A5] of one K-step
+constexpr int kStageB = kSlices * kTileBytes;        // [B0..B5] of one K-step
+constexpr int kHalf = kStageA + kStageB;             // one K-step's operands, 26 KB
+constexpr int kRawTile = kTile * kKc * 8;            // one 64 x 16 box of (hi, lo), 8 KB
+constexpr uint32_t kTmemCols = 512;  // two accumulator sets of three blocks of up to 64 columns
 constexpr uint32_t kSetCols = 256;
-static_assert(kRawMag + 128 * 4 <= kRawStage, "raw stage overflow");
-static_assert(kSmemTotal <= 232448, "shared memory per CTA");
+
+// Shared-memory layout of the kernel with KS K-steps of 16 points per
+// pipeline stage (the stage shape the tuner chooses per batch-size bucket):
+// KS = 1 keeps four operand and four raw stages, KS = 2 two of each (twice
+// the points per handshake, the same points in flight).
+//   raw stage:     per K-step h the A and B boxes (64 functions x 16 points
+//                  of (hi, lo), 128-byte rows, swizzled) at h * 16 KB, the
+//                  stage's D values (KS x 16 x 8 B) and, on an item's first
+//                  stage, the item's 128 rounding constants;
+//   operand stage: per K-step h the six A digit tiles after a zero tile and
+//                  the six B digit tiles, at h * 26 KB.
+template <int KS>
+struct Layout {
+  static constexpr int kStages = KS == 1 ? 4 : 2;  // ring depth of sliced operands
+  static constexpr int kRaw = KS == 1 ? 4 : 2;     // ring depth of raw boxes
+  static constexpr int kStage = KS * kHalf;
+  static constexpr int kRawD = KS * 2 * kRawTile;              // offset of D
+  static constexpr int kRawMag = kRawD + KS * kKc * 8;         // offset of the rounding constants
+  static constexpr int kRawStage = ((kRawMag + 128 * 4 + 1023) / 1024) * 1024;  // 1024-aligned (swizzle atoms)
+  static constexpr int kSmemRaw = 0;
+  static constexpr int kSmemStages = kSmemRaw + kRaw * kRawStage;
+  static constexpr int kSmemEpi = kSmemStages + kStages * kStage;  // epilogue staging, 2 x 26 KB
+  static constexpr int kSmemBar = kSmemEpi + 2 * kEpiStage;
+  // full, empty, accfull[2], accempty[2], drain, raw full/empty
+  static constexpr int kNumBars = 2 * kStages + 5 + 2 * kRaw;
+  static constexpr int kSmemTotal = kSmemBar + kNumBars * 8 + 16;
+  static_assert(kSmemTotal <= 232448, "shared memory per CTA");
+};
+static_assert(Layout<1>::kRawStage == 17 * 1024 && Layout<1>::kStage == 26624, "the one-step layout");
 
 // ------------------------------------------------------------ kernel
 // The products of one item, K-concatenated into one accumulator: n of them,
@@ -188,11 +201,22 @@ __device__ __forceinline__ void sts64(unsigned char* p, uint32_t a, uint32_t b) 
 // Every wait is bounded; a role that times out sets the status bit and an
 // abort flag that ends the other roles' waits, and the MMA thread drains its
 // outstanding MMAs (bounded) before tensor memory is freed.
+template <int KS>
 __global__ void __launch_bounds__(kThreads, 1)
-    k_split_products(DevGrid G, const int4* __restrict__ items, const int* __restrict__ steps, int n_items,
+    k_split_products(DevGrid G, const int4* __restrict__ items, int n_items,
                      const CUtensorMap* __restrict__ maps, const float2* __restrict__ dpad,
                      const float* __restrict__ mag, double* V, double* W0, double* SOx, double* SOy, double* SOz,
                      unsigned* status) {
+  using L = Layout<KS>;
+  constexpr int kStages = L::kStages, kRaw = L::kRaw, kStage = L::kStage, kRawStage = L::kRawStage;
+  constexpr int kRawD = L::kRawD, kRawMag = L::kRawMag, kSmemRaw = L::kSmemRaw, kSmemStages = L::kSmemStages;
+  constexpr int kSmemEpi = L::kSmemEpi, kSmemBar = L::kSmemBar, kNumBars = L::kNumBars;
+  // stages of KS x 16 points per item: the batch's points, times the products
+  // the item K-concatenates
+  auto item_stages = [&](const int4& it) {
+    const int np = static_cast<int>(G.pt_ptr[it.x + 1] - G.pt_ptr[it.x]);
+    return (np + KS * kKc - 1) / (KS * kKc) * item_products(it).n;
+  };
   extern __shared__ __align__(1024) unsigned char smem[];
   float* stage = reinterpret_cast<float*>(smem + kSmemEpi);
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kSmemBar);
@@ -213,10 +237,10 @@ __global__ void __launch_bounds__(kThreads, 1)
   auto rawfull_bar = [&](int rs) { return bar0 + 8u * (2 * kStages + 5 + rs); };
   auto rawempty_bar = [&](int rs) { return bar0 + 8u * (2 * kStages + 5 + kRaw + rs); };
 
-  // zero tile Z at the head of each stage (never overwritten)
-  for (int i = tid; i < kStages * kTileBytes / 16; i += kThreads) {
-    const int st = i / (kTileBytes / 16), off = i - st * (kTileBytes / 16);
-    reinterpret_cast<uint4*>(smem + kSmemStages + st * kStage)[off] = make_uint4(0, 0, 0, 0);
+  // zero tile Z at the head of each K-step's A tiles (never overwritten)
+  for (int i = tid; i < kStages * KS * kTileBytes / 16; i += kThreads) {
+    const int sh = i / (kTileBytes / 16), off = i - sh * (kTileBytes / 16);
+    reinterpret_cast<uint4*>(smem + kSmemStages + sh * kHalf)[off] = make_uint4(0, 0, 0, 0);
   }
   fence_async_smem();  // the zero tiles are read by the tensor cores (async proxy)
   if (tid == 0) {
@@ -257,12 +281,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     // the 8-byte slot of (r, 4q) in a K-major core-matrix operand tile
     const int rc0 = r * 128 + (((2 * q) ^ (r & 7)) << 4), rc1 = r * 128 + (((2 * q + 1) ^ (r & 7)) << 4);
     const int dst_off = (r >> 3) * kSBO + (q >> 1) * kLBO + (r & 7) * 16 + (q & 1) * 8;
-    int g = 0;  // steps sliced by this CTA
-    int n_steps_next = blockIdx.x < n_items ? steps[blockIdx.x] : 0;
+    int g = 0;  // stages sliced by this CTA
     for (int n = blockIdx.x; n < n_items; n += gridDim.x) {
-      const int n_steps = n_steps_next;
-      if (n + static_cast<int>(gridDim.x) < n_items) n_steps_next = steps[n + gridDim.x];
       const int4 item = items[n];
+      const int n_steps = item_stages(item);
       const int nbB = item_nb(static_cast<int>(G.bat_fn_ptr[item.x + 1] - G.bat_fn_ptr[item.x]), item.w);
       const int n_prod = item_products(item).n;
       const bool b_row = r < nbB;  // this warp's rows of the B tile exist (nbB is a multiple of 16)
@@ -279,44 +301,54 @@ __global__ void __launch_bounds__(kThreads, 1)
           mA = reinterpret_cast<const float*>(raw + kRawMag)[r];
           mB = reinterpret_cast<const float*>(raw + kRawMag)[64 + r];
         }
-        const float4 a01 = lds128(raw + rc0), a23 = lds128(raw + rc1);
-        float4 b01 = make_float4(0.f, 0.f, 0.f, 0.f), b23 = b01;
-        if (b_row) {
-          b01 = lds128(raw + kRawTile + rc0);
-          b23 = lds128(raw + kRawTile + rc1);
-        }
-        float4 d01 = lds128(raw + kRawD + q * 32), d23 = lds128(raw + kRawD + q * 32 + 16);
-        if (pr == 1 && n_prod == 2) {  // the subtracted product of an off-diagonal SO item: -D (exact)
-          d01 = make_float4(-d01.x, -d01.y, -d01.z, -d01.w);
-          d23 = make_float4(-d23.x, -d23.y, -d23.z, -d23.w);
+        float4 a01[KS], a23[KS], b01[KS], b23[KS], d01[KS], d23[KS];
+#pragma unroll
+        for (int h = 0; h < KS; ++h) {
+          const unsigned char* box = raw + h * 2 * kRawTile;
+          a01[h] = lds128(box + rc0);
+          a23[h] = lds128(box + rc1);
+          b01[h] = b23[h] = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (b_row) {
+            b01[h] = lds128(box + kRawTile + rc0);
+            b23[h] = lds128(box + kRawTile + rc1);
+          }
+          d01[h] = lds128(raw + kRawD + h * kKc * 8 + q * 32);
+          d23[h] = lds128(raw + kRawD + h * kKc * 8 + q * 32 + 16);
+          if (pr == 1 && n_prod == 2) {  // the subtracted product of an off-diagonal SO item: -D (exact)
+            d01[h] = make_float4(-d01[h].x, -d01[h].y, -d01[h].z, -d01[h].w);
+            d23[h] = make_float4(-d23[h].x, -d23[h].y, -d23[h].z, -d23[h].w);
+          }
         }
         if (!mbar_wait_abort(empty_bar(st), ((g / kStages) & 1) ^ 1, s_abort, status, G.wait_ns)) {
           ok = false;
           break;
         }
-        unsigned char* sA = smem + kSmemStages + st * kStage;
-        unsigned char* sB = sA + kStageA;
-        // points (4q, 4q+1) and (4q+2, 4q+3) as packed pairs
-        {  // A side: D-scaled values in double-float
-          float2 xh01, xl01, xh23, xl23;
-          df_mul2(pk2(a01.x, a01.z), pk2(a01.y, a01.w), pk2(d01.x, d01.z), pk2(d01.y, d01.w),
-                  pk2(-d01.x, -d01.z), xh01, xl01);
-          df_mul2(pk2(a23.x, a23.z), pk2(a23.y, a23.w), pk2(d23.x, d23.z), pk2(d23.y, d23.w),
-                  pk2(-d23.x, -d23.z), xh23, xl23);
-          float2 e01[kSlices], e23[kSlices];
-          slice6x2(xh01, xl01, mA, e01);
-          slice6x2(xh23, xl23, mA, e23);
 #pragma unroll
-          for (int t = 0; t < kSlices; ++t)  // A: [Z, A0..A5]
-            sts64(sA + (1 + t) * kTileBytes + dst_off, bf16x2_exact(e01[t]), bf16x2_exact(e23[t]));
-        }
-        if (b_row) {  // B side: tiles of nbB rows
-          float2 e01[kSlices], e23[kSlices];
-          slice6x2(pk2(b01.x, b01.z), pk2(b01.y, b01.w), mB, e01);
-          slice6x2(pk2(b23.x, b23.z), pk2(b23.y, b23.w), mB, e23);
+        for (int h = 0; h < KS; ++h) {
+          unsigned char* sA = smem + kSmemStages + st * kStage + h * kHalf;
+          unsigned char* sB = sA + kStageA;
+          // points (4q, 4q+1) and (4q+2, 4q+3) of K-step h as packed pairs
+          {  // A side: D-scaled values in double-float
+            float2 xh01, xl01, xh23, xl23;
+            df_mul2(pk2(a01[h].x, a01[h].z), pk2(a01[h].y, a01[h].w), pk2(d01[h].x, d01[h].z),
+                    pk2(d01[h].y, d01[h].w), pk2(-d01[h].x, -d01[h].z), xh01, xl01);
+            df_mul2(pk2(a23[h].x, a23[h].z), pk2(a23[h].y, a23[h].w), pk2(d23[h].x, d23[h].z),
+                    pk2(d23[h].y, d23[h].w), pk2(-d23[h].x, -d23[h].z), xh23, xl23);
+            float2 e01[kSlices], e23[kSlices];
+            slice6x2(xh01, xl01, mA, e01);
+            slice6x2(xh23, xl23, mA, e23);
 #pragma unroll
-          for (int t = 0; t < kSlices; ++t)  // B: [B0, B2, B4, B1, B3, B5]
-            sts64(sB + b_tile(t) * nbB * kRowBytes + dst_off, bf16x2_exact(e01[t]), bf16x2_exact(e23[t]));
+            for (int t = 0; t < kSlices; ++t)  // A: [Z, A0..A5]
+              sts64(sA + (1 + t) * kTileBytes + dst_off, bf16x2_exact(e01[t]), bf16x2_exact(e23[t]));
+          }
+          if (b_row) {  // B side: tiles of nbB rows
+            float2 e01[kSlices], e23[kSlices];
+            slice6x2(pk2(b01[h].x, b01[h].z), pk2(b01[h].y, b01[h].w), mB, e01);
+            slice6x2(pk2(b23[h].x, b23[h].z), pk2(b23[h].y, b23[h].w), mB, e23);
+#pragma unroll
+            for (int t = 0; t < kSlices; ++t)  // B: [B0, B2, B4, B1, B3, B5]
+              sts64(sB + b_tile(t) * nbB * kRowBytes + dst_off, bf16x2_exact(e01[t]), bf16x2_exact(e23[t]));
+          }
         }
         fence_async_smem();
         mbar_arrive(full_bar(st));
@@ -335,7 +367,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       int g = 0;
       for (int n = blockIdx.x; n < n_items; n += gridDim.x) {
         const int4 item = items[n];
-        const int n_steps = steps[n];
+        const int n_steps = item_stages(item);
         const Products P = item_products(item);
         const CUtensorMap* map = maps + item.x;
         const float2* drow = dpad + static_cast<int64_t>(item.x) * kDPitch;
@@ -347,13 +379,17 @@ __global__ void __launch_bounds__(kThreads, 1)
             ok = false;
             break;
           }
-          const int c = P.n == 1 ? s : s / P.n, pr = s - c * P.n;
+          const int c = P.n == 1 ? s : s / P.n, pr = s - c * P.n;  // c: this stage's chunk of KS x 16 points
           const uint32_t dst = smem_u32(smem + kSmemRaw + rs * kRawStage);
           const uint32_t fb = rawfull_bar(rs);
-          arrive_expect_tx(fb, 2 * kRawTile + kKc * 8 + (s == 0 ? 128 * 4 : 0));
-          tma_load_3d(dst, map, c * kKc, i0, P.a(pr), fb);
-          tma_load_3d(dst + kRawTile, map, c * kKc, j0, P.b(pr), fb);
-          bulk_copy(dst + kRawD, drow + c * kKc, kKc * 8, fb);
+          arrive_expect_tx(fb, KS * (2 * kRawTile + kKc * 8) + (s == 0 ? 128 * 4 : 0));
+#pragma unroll
+          for (int h = 0; h < KS; ++h) {
+            const int x = (c * KS + h) * kKc;  // first point of K-step h (16-byte aligned coordinate)
+            tma_load_3d(dst + h * 2 * kRawTile, map, x, i0, P.a(pr), fb);
+            tma_load_3d(dst + h * 2 * kRawTile + kRawTile, map, x, j0, P.b(pr), fb);
+          }
+          bulk_copy(dst + kRawD, drow + c * KS * kKc, KS * kKc * 8, fb);
           if (s == 0) bulk_copy(dst + kRawMag, mag + static_cast<int64_t>(n) * 128, 128 * 4, fb);
         }
         if (!ok) break;
@@ -368,8 +404,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (lane == 0) {
       int g = 0, k = 0;
       for (int n = blockIdx.x; n < n_items; n += gridDim.x, ++k) {
-        const int n_steps = steps[n];
         const int4 item = items[n];
+        const int n_steps = item_stages(item);
         const int nbB = item_nb(static_cast<int>(G.bat_fn_ptr[item.x + 1] - G.bat_fn_ptr[item.x]), item.w);
         const int set = k & 1;
         if (!mbar_wait_abort(accempty_bar(set), ((k >> 1) & 1) ^ 1, s_abort, status, G.wait_ns, 64)) break;
@@ -383,8 +419,11 @@ __global__ void __launch_bounds__(kThreads, 1)
             break;
           }
           tc_fence_after();
-          const uint32_t a = smem_u32(smem + kSmemStages + st * kStage), bb = a + kStageA;
-          mma_levels(t0, a, bb, s == 0 ? 0u : 1u, nbB);
+#pragma unroll
+          for (int h = 0; h < KS; ++h) {
+            const uint32_t a = smem_u32(smem + kSmemStages + st * kStage + h * kHalf), bb = a + kStageA;
+            mma_levels(t0, a, bb, (s == 0 && h == 0) ? 0u : 1u, nbB);
+          }
           mma_commit(empty_bar(st));
         }
         if (!ok) break;
@@ -471,33 +510,69 @@ __global__ void __launch_bounds__(kThreads, 1)
 
 }  // namespace split
 
-// the products of one wave [b0, b1): rounding constants and the products
-// kernel over the wave's items; the wave's offset tables, basis tiles,
-// column exponents and D row must already be in place
-q4c_status products_wave(const q4c_grid* g, int wv, const q4c_matrices* out, cudaStream_t s) {
-  const int64_t i0 = g->split_w0[wv], i1 = g->split_w0[wv + 1];
-  const int n_items = static_cast<int>(i1 - i0);
-  if (n_items == 0) return Q4C_OK;
-  Q4C_CUDA(cudaFuncSetAttribute(split::k_split_products, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                split::kSmemTotal));
+namespace {
+
+// one launch of the products kernel with KS K-steps per stage over items
+// [i0, i0 + n): a persistent grid of at most one CTA per SM
+template <int KS>
+q4c_status launch_products(const q4c_grid* g, const int4* items, int n, const float* mag, double* V, double* W0,
+                           double* SOx, double* SOy, double* SOz, const char* name, cudaStream_t s) {
+  using L = split::Layout<KS>;
+  Q4C_CUDA(cudaFuncSetAttribute(split::k_split_products<KS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                L::kSmemTotal));
   int dev = 0, n_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
-  {
-    KernelScope ks("split_prep", s);
-    split::k_item_prep<<<n_items, 128, 0, s>>>(g->view(), g->d_split_items + i0, g->d_colexp, g->d_split_mag);
-  }
-  Q4C_CUDA(cudaGetLastError());
-  const int grid = std::min(n_items, n_sm);
-  {
-    KernelScope ks("split_products", s);
-    split::k_split_products<<<grid, split::kThreads, split::kSmemTotal, s>>>(
-        g->view(), g->d_split_items + i0, g->d_split_steps + i0, n_items,
-        reinterpret_cast<const CUtensorMap*>(g->d_tmaps), g->d_dpad, g->d_split_mag, out->V, out->W0, out->SOx,
-        out->SOy, out->SOz, g->d_status);
-  }
+  KernelScope ks(name, s);
+  split::k_split_products<KS><<<std::min(n, n_sm), split::kThreads, L::kSmemTotal, s>>>(
+      g->view(), items, n, reinterpret_cast<const CUtensorMap*>(g->d_tmaps), g->d_dpad, mag, V, W0, SOx, SOy, SOz,
+      g->d_status);
   Q4C_CUDA(cudaGetLastError());
   return Q4C_OK;
+}
+
+// items[0, n) with their rounding constants mag[128 n]
+q4c_status launch_products_ks(int ks, const q4c_grid* g, const int4* items, int n, const float* mag, double* V,
+                              double* W0, double* SOx, double* SOy, double* SOz, const char* name, cudaStream_t s) {
+  if (n <= 0) return Q4C_OK;
+  return ks == 2 ? launch_products<2>(g, items, n, mag, V, W0, SOx, SOy, SOz, name, s)
+                 : launch_products<1>(g, items, n, mag, V, W0, SOx, SOy, SOz, name, s);
+}
+
+// items of one wave: rounding constants of all of them, then one launch per
+// batch-size bucket with the stage shape chosen for that bucket
+q4c_status products_items(const q4c_grid* g, const int4* d_items, const std::vector<int64_t>& bucket_w0, int wv,
+                          double* V, double* W0, double* SOx, double* SOy, double* SOz, const char* name,
+                          cudaStream_t s) {
+  const int64_t* r = bucket_w0.data() + static_cast<size_t>(wv) * (kTileBuckets + 1);
+  const int64_t i0 = r[0], i1 = r[kTileBuckets];
+  if (i1 <= i0) return Q4C_OK;
+  {
+    KernelScope ks("split_prep", s);
+    split::k_item_prep<<<static_cast<unsigned>(i1 - i0), 128, 0, s>>>(g->view(), d_items + i0, g->d_colexp,
+                                                                       g->d_split_mag);
+  }
+  Q4C_CUDA(cudaGetLastError());
+  // the rounding constants of item n sit at mag[(n - i0) * 128]; each bucket
+  // launch gets its own item list and the constants of its first item
+  for (int k = 0; k < kTileBuckets; ++k) {
+    const int64_t b0 = r[k], b1 = r[k + 1];
+    if (b1 <= b0) continue;
+    if (q4c_status st = launch_products_ks(g->split_ks[k], g, d_items + b0, static_cast<int>(b1 - b0),
+                                           g->d_split_mag + (b0 - i0) * 128, V, W0, SOx, SOy, SOz, name, s))
+      return st;
+  }
+  return Q4C_OK;
+}
+
+}  // namespace
+
+// the products of one wave: rounding constants and the products kernels
+// over the wave's items; the wave's offset tables, basis tiles, column
+// exponents and D row must already be in place
+q4c_status products_wave(const q4c_grid* g, int wv, const q4c_matrices* out, cudaStream_t s) {
+  return products_items(g, g->d_split_items, g->split_bw0, wv, out->V, out->W0, out->SOx, out->SOy, out->SOz,
+                        "split_products", s);
 }
 
 q4c_status integrate_split(const q4c_tables* t, const q4c_grid* g, const double* v, const q4c_matrices* out,
@@ -531,35 +606,77 @@ q4c_status integrate_columns_split(const q4c_tables* t, const q4c_grid* g, const
   }
   Q4C_CUDA(cudaMemsetAsync(F, 0, sizeof(double) * g->nnz, s));
   const int n_waves = static_cast<int>(g->wave_b0.size()) - 1;
-  Q4C_CUDA(cudaFuncSetAttribute(split::k_split_products, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                split::kSmemTotal));
-  int dev = 0, n_sm = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
   for (int wv = 0; wv < n_waves; ++wv) {
     const int64_t b0 = g->wave_b0[wv], b1 = g->wave_b0[wv + 1];
     if (b1 <= b0) continue;
     if (q4c_status st = launch_fill_idx(t, g, b0, b1, s)) return st;
     if (q4c_status st = launch_basis_df(t, g, b0, b1, v, g->d_colexp, nullptr, 2, s, g->d_dpad)) return st;
-    const int64_t i0 = g->col_w0[wv], i1 = g->col_w0[wv + 1];
-    const int n_items = static_cast<int>(i1 - i0);
-    if (n_items == 0) continue;
-    {
-      KernelScope ks("split_prep", s);
-      split::k_item_prep<<<n_items, 128, 0, s>>>(g->view(), g->d_col_items + i0, g->d_colexp, g->d_split_mag);
-    }
-    Q4C_CUDA(cudaGetLastError());
-    const int grid = std::min(n_items, n_sm);
-    {
-      KernelScope ks("split_columns", s);
-      split::k_split_products<<<grid, split::kThreads, split::kSmemTotal, s>>>(
-          g->view(), g->d_col_items + i0, g->d_col_steps + i0, n_items,
-          reinterpret_cast<const CUtensorMap*>(g->d_tmaps), g->d_dpad, g->d_split_mag, F, nullptr, nullptr,
-          nullptr, nullptr, g->d_status);
-    }
-    Q4C_CUDA(cudaGetLastError());
+    if (q4c_status st = products_items(g, g->d_col_items, g->col_bw0, wv, F, nullptr, nullptr, nullptr, nullptr,
+                                       "split_columns", s))
+      return st;
   }
   return Q4C_OK;
+}
+
+// Tile-shape tuner: on the first wave, with the wave's tables, tiles and
+// rounding constants in place, each batch-size bucket's items run with one
+// and with two K-steps per stage (one untimed launch, then three timed by
+// CUDA events on the stream) into scratch outputs; the faster shape is kept
+// for the bucket.
+q4c_status autotune_split(const q4c_tables* t, q4c_grid* g, const double* v, cudaStream_t s) {
+  if (g->max_np > 341 || g->wave_b0.size() < 2) return Q4C_OK;
+  for (int k = 0; k < kTileBuckets; ++k) g->tune_ms[k][0] = g->tune_ms[k][1] = -1.0;
+  const int64_t b0 = g->wave_b0[0], b1 = g->wave_b0[1];
+  if (b1 <= b0) return Q4C_OK;
+  if (q4c_status st = launch_fill_idx(t, g, b0, b1, s)) return st;
+  if (q4c_status st = launch_basis_df(t, g, b0, b1, v, g->d_colexp, nullptr, 4, s, g->d_dpad)) return st;
+  const int64_t* r = g->split_bw0.data();
+  const int64_t i0 = r[0], i1 = r[kTileBuckets];
+  if (i1 <= i0) return Q4C_OK;
+  split::k_item_prep<<<static_cast<unsigned>(i1 - i0), 128, 0, s>>>(g->view(), g->d_split_items + i0, g->d_colexp,
+                                                                     g->d_split_mag);
+  Q4C_CUDA(cudaGetLastError());
+  double* scratch = nullptr;
+  Q4C_CUDA(cudaMalloc(&scratch, sizeof(double) * 5 * std::max<int64_t>(g->nnz, 1)));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  q4c_status status = Q4C_OK;
+  auto fail = [&](q4c_status st) { status = st; };
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    set_error("q4c_autotune: cudaEventCreate failed");
+    status = Q4C_ECUDA;
+  }
+  double* o[5];
+  for (int m = 0; m < 5; ++m) o[m] = scratch + m * std::max<int64_t>(g->nnz, 1);
+  for (int k = 0; k < kTileBuckets && status == Q4C_OK; ++k) {
+    const int64_t c0 = r[k], c1 = r[k + 1];
+    if (c1 <= c0) continue;
+    const float* mag = g->d_split_mag + (c0 - i0) * 128;
+    for (int ks = 1; ks <= 2 && status == Q4C_OK; ++ks) {
+      float ms = 0.f;
+      if (q4c_status st = launch_products_ks(ks, g, g->d_split_items + c0, static_cast<int>(c1 - c0), mag, o[0],
+                                             o[1], o[2], o[3], o[4], "split_tune", s)) {
+        fail(st);
+        break;
+      }
+      cudaEventRecord(e0, s);
+      for (int rep = 0; rep < 3 && status == Q4C_OK; ++rep)
+        if (q4c_status st = launch_products_ks(ks, g, g->d_split_items + c0, static_cast<int>(c1 - c0), mag, o[0],
+                                               o[1], o[2], o[3], o[4], "split_tune", s))
+          fail(st);
+      cudaEventRecord(e1, s);
+      if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+        set_error("q4c_autotune: timing failed");
+        fail(Q4C_ECUDA);
+        break;
+      }
+      g->tune_ms[k][ks - 1] = ms / 3.0;
+    }
+    if (status == Q4C_OK) g->split_ks[k] = g->tune_ms[k][1] >= 0.0 && g->tune_ms[k][1] < g->tune_ms[k][0] ? 2 : 1;
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(scratch);
+  return status;
 }
 
 }  // namespace q4c
