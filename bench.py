@@ -587,8 +587,9 @@ def main():
                             if fused else "q4c_integrate + q4c_density + q4c_integrate_backward"),
                    "l2": "512 MB buffer written between timed steps", "replicas": world},
         "flops_per_step": fl,
-        "tiling": [{"nb_max": t["nb_max"] if t["nb_max"] < (1 << 29) else None, "k_steps_per_stage": t["k_steps"],
-                    "batches": t["batches"], "tuner_ms": [t["ms_one"], t["ms_two"]]} for t in tiling],
+        "tiling": [{"kernel": "products" if k < len(tiling) - 1 else "density/adjoint",
+                    "nb_max": t["nb_max"] if t["nb_max"] < (1 << 29) else None, "k_steps_per_stage": t["k_steps"],
+                    "batches": t["batches"], "tuner_ms": [t["ms_one"], t["ms_two"]]} for k, t in enumerate(tiling)],
         "phase_ms": {k: v_[0] / args.steps for k, v_ in kern.items()},
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": launches_total,
         **extra,

@@ -417,11 +417,15 @@ Q4C_API q4c_status q4c_scf_pass(const q4c_tables* tables, const q4c_grid* grid, 
  * the stream.  The choice applies to every later split-path integration
  * (q4c_integrate, q4c_integrate_columns, q4c_scf_pass) on the grid; results
  * do not depend on it beyond the order of FP64 additions.
- * q4c_grid_tiling reports a bucket: its largest n_b, the shape in use, the
- * grid's batches in it, and the tuner's mean time per launch for one and two
- * K-steps (-1 if not timed); NULL outputs are skipped.
+ * The density/adjoint kernel (row-dot products over 16-function K-steps)
+ * has one such shape per grid, tuned on the same wave with its adjoint; it is
+ * addressed as bucket Q4C_TILE_BUCKETS below.
+ * q4c_grid_tiling reports a bucket: its largest n_b (512 for the row-dot
+ * kernel), the shape in use, the grid's batches in it (all for the row-dot
+ * kernel), and the tuner's mean time per launch for one and two K-steps
+ * (-1 if not timed); NULL outputs are skipped.
  * q4c_grid_set_tiling sets a bucket's shape by hand (1 or 2).  Q4C_EINVAL
- * for a bucket outside 0..Q4C_TILE_BUCKETS-1 or another shape. */
+ * for a bucket outside 0..Q4C_TILE_BUCKETS or another shape. */
 #define Q4C_TILE_BUCKETS 4
 Q4C_API q4c_status q4c_autotune(const q4c_tables* tables, q4c_grid* grid, const double* v_dev, q4c_stream stream);
 Q4C_API q4c_status q4c_grid_tiling(const q4c_grid* grid, int32_t bucket, int32_t* nb_max, int32_t* k_steps,

@@ -437,9 +437,10 @@ TILE_BUCKETS = 4
 
 
 def q4c_grid_tiling(grid: Grid):
-    """Per batch-size bucket: dict(nb_max, k_steps, batches, ms_one, ms_two)."""
+    """Per batch-size bucket of the products kernel, then the density/adjoint
+    kernel (last entry): dict(nb_max, k_steps, batches, ms_one, ms_two)."""
     out = []
-    for k in range(TILE_BUCKETS):
+    for k in range(TILE_BUCKETS + 1):
         nb, ks, nbt = C.c_int32(), C.c_int32(), C.c_int64()
         m1, m2 = C.c_double(), C.c_double()
         _check(load().q4c_grid_tiling(grid.h, k, C.byref(nb), C.byref(ks), C.byref(nbt), C.byref(m1), C.byref(m2)))

@@ -144,7 +144,15 @@ extern "C" q4c_status q4c_autotune(const q4c_tables* t, q4c_grid* g, const doubl
 extern "C" q4c_status q4c_grid_tiling(const q4c_grid* g, int32_t bucket, int32_t* nb_max, int32_t* k_steps,
                                       int64_t* batches, double* ms_one, double* ms_two) {
   Q4C_CHECK_ARG(g, "q4c_grid_tiling: NULL grid");
-  Q4C_CHECK_ARG(bucket >= 0 && bucket < kTileBuckets, "q4c_grid_tiling: bucket out of range");
+  Q4C_CHECK_ARG(bucket >= 0 && bucket <= kTileBuckets, "q4c_grid_tiling: bucket out of range");
+  if (bucket == kTileBuckets) {  // the density/adjoint kernel (one shape per grid)
+    if (nb_max) *nb_max = 512;
+    if (k_steps) *k_steps = g->rd_ks;
+    if (batches) *batches = g->n_batches;
+    if (ms_one) *ms_one = g->rd_tune_ms[0];
+    if (ms_two) *ms_two = g->rd_tune_ms[1];
+    return Q4C_OK;
+  }
   if (nb_max) *nb_max = kBucketNb[bucket];
   if (k_steps) *k_steps = g->split_ks[bucket];
   if (batches) {
@@ -160,8 +168,11 @@ extern "C" q4c_status q4c_grid_tiling(const q4c_grid* g, int32_t bucket, int32_t
 
 extern "C" q4c_status q4c_grid_set_tiling(q4c_grid* g, int32_t bucket, int32_t k_steps) {
   Q4C_CHECK_ARG(g, "q4c_grid_set_tiling: NULL grid");
-  Q4C_CHECK_ARG(bucket >= 0 && bucket < kTileBuckets, "q4c_grid_set_tiling: bucket out of range");
+  Q4C_CHECK_ARG(bucket >= 0 && bucket <= kTileBuckets, "q4c_grid_set_tiling: bucket out of range");
   Q4C_CHECK_ARG(k_steps == 1 || k_steps == 2, "q4c_grid_set_tiling: k_steps must be 1 or 2");
-  g->split_ks[bucket] = k_steps;
+  if (bucket == kTileBuckets)
+    g->rd_ks = k_steps;
+  else
+    g->split_ks[bucket] = k_steps;
   return Q4C_OK;
 }

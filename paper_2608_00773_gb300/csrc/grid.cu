@@ -934,6 +934,8 @@ extern "C" q4c_status grid_partition(const q4c_grid_desc* d, const q4c_tables* t
     if (e == cudaSuccess) e = cudaMalloc(&g->d_rowexp, sizeof(int) * 4 * nP);
     if (e == cudaSuccess) e = cudaMalloc(&g->d_gsl, static_cast<size_t>(std::max<int64_t>(g->gsl_bytes, 16)));
     if (e == cudaSuccess) e = cudaMalloc(&g->d_gdf, sizeof(float2) * 10 * std::max<int64_t>(g->nnz, 1));
+    if (e == cudaSuccess) e = cudaMalloc(&g->d_gzero, 12288);
+    if (e == cudaSuccess) e = cudaMemset(g->d_gzero, 0, 12288);
     if (e == cudaSuccess) e = cudaMalloc(&g->d_bat_idx, sizeof(int) * g->idx_entries);
     if (e == cudaSuccess) e = cudaMalloc(&g->d_split_mag, sizeof(float) * 128 * max_wave_items);
     if (e == cudaSuccess) e = cudaMalloc(&g->d_dpad, sizeof(float2) * kDPitch * std::max<int64_t>(nB, 1));
@@ -963,7 +965,7 @@ extern "C" void q4c_grid_destroy(q4c_grid* g) {
                   g->d_fn_info, g->d_bat_pair_ptr, g->d_pair_off, g->d_blk_off, g->d_blk_row, g->d_blk_col,
                   g->d_blk_T, g->d_scr_off, g->d_tiles, g->d_col_tiles, g->d_scratch, g->d_sched, g->d_counter, g->d_split_ws,
                   g->d_split_items, g->d_col_items, g->d_split_mag, g->d_dpad, g->d_tmaps, g->d_colexp, g->d_status, g->d_rd_items, g->d_rowexp, g->d_gsl, g->d_gsl_off,
-                  g->d_bat_idx_ptr, g->d_bat_idx, g->d_pts_df, g->d_atoms_df, g->d_gdf,
+                  g->d_bat_idx_ptr, g->d_bat_idx, g->d_pts_df, g->d_atoms_df, g->d_gdf, g->d_gzero,
                   g->d_c_xyz, g->d_c_sp, g->d_blk_role, g->d_blk_shift, g->d_kblk_q0, g->d_kblk_q1,
                   g->d_kblk_off};
   for (void* p : ptrs) cudaFree(p);

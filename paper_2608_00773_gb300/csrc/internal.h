@@ -206,6 +206,8 @@ struct q4c_grid {
   std::vector<int64_t> split_bw0, col_bw0;
   int split_ks[4] = {1, 1, 1, 1};          // K-steps of 16 points per pipeline stage, per bucket (tuner)
   double tune_ms[4][2] = {{-1, -1}, {-1, -1}, {-1, -1}, {-1, -1}};  // tuner timings per bucket and shape
+  int rd_ks = 1;                           // K-steps per stage of the density/adjoint kernel (tuner)
+  double rd_tune_ms[2] = {-1, -1};         // tuner timings of the adjoint with one and two K-steps
   int4* d_split_items = nullptr;
   std::vector<int64_t> col_w0;             // [n_waves+1] ranges into d_col_items
   int4* d_col_items = nullptr;             // per-column operator: (batch, 5, ti, tj), every tile pair
@@ -218,6 +220,7 @@ struct q4c_grid {
   int2* d_rd_items = nullptr;              // (batch, 64-point tile) for density/adjoint
   int* d_rowexp = nullptr;                 // [n_points][4] per-point exponents
   unsigned char* d_gsl = nullptr;          // G' digit blocks of one wave (density/adjoint)
+  unsigned char* d_gzero = nullptr;        // one zero G' digit block (12 KB)
   int64_t* d_gsl_off = nullptr;            // [n_batches] byte offsets into d_gsl (per wave)
   int64_t gsl_bytes = 0;
   int64_t idx_entries = 0;                 // size of the per-wave dense offset tables
@@ -276,8 +279,9 @@ q4c_status products_fp64_wave(const q4c_grid* g, int wv, const double* v, const 
 q4c_status density_fp64_wave(const q4c_grid* g, int wv, const double* P, double* n, cudaStream_t s);
 q4c_status backward_fp64_wave(const q4c_grid* g, int wv, const q4c_matrices* G, double* dLdv, bool weighted,
                               cudaStream_t s);
-// split.cu: the tile-shape tuner (stores its choice in the grid)
+// split.cu: the tile-shape tuner (stores its choice in the grid); rowdot.cu: its row-dot part
 q4c_status autotune_split(const q4c_tables* t, q4c_grid* g, const double* v, cudaStream_t s);
+q4c_status autotune_rowdot(q4c_grid* g, double* out, cudaStream_t s);
 // the fused pass (fused.cu)
 q4c_status scf_pass(const q4c_tables* t, const q4c_grid* g, const double* v, const q4c_matrices* H,
                     const q4c_matrices* P, double* n, const q4c_matrices* Gm, double* dLdv, bool split,

@@ -39,22 +39,35 @@ constexpr int kEpiThreads = 256;
 constexpr int kMmaWarp = 16;  // warp 16 owns tensor memory and issues the MMAs
 constexpr int kProdWarp = 17;  // warp 17 issues the TMA loads of F
 constexpr int kThreads = 18 * 32;
-constexpr int kStageA = (kSlices + 1) * kTileBytes;  // [Z, A0..A5]
-constexpr int kStage = kStageA + kBlockB;            // 26 KB
-constexpr int kStages = 4;
-// raw ring: per K-step the box of F (16 functions x 64 points of (hi, lo),
-// 512-byte rows) and, on an item's first step, the points' exponents
-constexpr int kRaw = 4;
-constexpr int kRawTile = kKc * kTile * 8;  // 8 KB
-constexpr int kRawExp = kRawTile;          // [64][4] per-point exponents
-constexpr int kRawStage = 9 * 1024;
-constexpr int kSmemRaw = 0;
-constexpr int kSmemStages = kSmemRaw + kRaw * kRawStage;
-constexpr int kSmemY = kSmemStages + kStages * kStage;  // [4][64] double partials per point
-constexpr int kSmemBar = kSmemY + 4 * kTile * 8;
-// full, empty, accfull[2], accempty[2], drain, raw full/empty, G' copy full
-constexpr int kNumBars = 3 * kStages + 5 + 2 * kRaw;
-constexpr int kSmemTotal = kSmemBar + kNumBars * 8 + 16;
+constexpr int kStageA = (kSlices + 1) * kTileBytes;  // [Z, A0..A5] of one K-step
+constexpr int kHalf = kStageA + kBlockB;             // one K-step's operands, 26 KB
+constexpr int kRawTile = kKc * kTile * 8;            // one box of F (16 functions x 64 points), 8 KB
+
+// Shared-memory layout with KS K-steps of 16 functions per pipeline stage
+// (the stage shape the tuner chooses): KS = 1 keeps four operand and four
+// raw stages, KS = 2 three of each.
+//   raw stage:     per K-step h the box of F (16 functions x 64 points of
+//                  (hi, lo), 512-byte rows) at h * 8 KB and, on an item's
+//                  first stage, the points' exponents;
+//   operand stage: per K-step h the six F digit tiles after a zero tile and
+//                  the j-tile's six G' digit tiles, at h * 26 KB.
+template <int KS>
+struct Layout {
+  static constexpr int kStages = KS == 1 ? 4 : 3;
+  static constexpr int kRaw = KS == 1 ? 4 : 3;
+  static constexpr int kStage = KS * kHalf;
+  static constexpr int kRawExp = KS * kRawTile;  // [64][4] per-point exponents
+  static constexpr int kRawStage = kRawExp + 1024;
+  static constexpr int kSmemRaw = 0;
+  static constexpr int kSmemStages = kSmemRaw + kRaw * kRawStage;
+  static constexpr int kSmemY = kSmemStages + kStages * kStage;  // [4][64] double partials per point
+  static constexpr int kSmemBar = kSmemY + 4 * kTile * 8;
+  // full, empty, accfull[2], accempty[2], drain, raw full/empty, G' copy full
+  static constexpr int kNumBars = 3 * kStages + 5 + 2 * kRaw;
+  static constexpr int kSmemTotal = kSmemBar + kNumBars * 8 + 16;
+  static_assert(kSmemTotal <= 232448, "shared memory per CTA");
+};
+static_assert(Layout<1>::kRawStage == 9 * 1024 && Layout<1>::kStage == 26624, "the one-step layout");
 constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kSetCols = 256;
 constexpr int kMaxNb = 512;
@@ -182,7 +195,8 @@ __global__ void __launch_bounds__(256) k_gslice(DevGrid G, int64_t b0, int anti_
 }
 
 // the work of one item (batch, 64-point tile): groups (j-tile, product) in
-// order, each a K-loop of n_ic steps over the functions i
+// order, each a K-loop over the functions i in chunks of 16 (n_ic chunks,
+// KS chunks per pipeline stage)
 struct ItemInfo {
   int64_t b, bp0;
   int pt, np, ldp, nb, n_jt, n_ic;
@@ -203,8 +217,8 @@ __device__ __forceinline__ ItemInfo item_info(const DevGrid& G, int2 it) {
   return I;
 }
 
-// position in an item's step sequence (j-tile, product, i-chunk), advanced
-// without divisions
+// position in an item's stage sequence (j-tile, product, stage of the
+// K-loop), advanced without divisions
 struct StepIter {
   int ic = 0, kk = 0, jt = 0;
   __device__ __forceinline__ void next(int n_ic, int n_prod) {
@@ -239,13 +253,17 @@ struct StepIter {
 //               over the item's groups and write each point's result at the
 //               end of the item.
 // Every wait is bounded; a timeout sets the status bit and an abort flag.
-template <int MODE>  // 0: density, 1: adjoint
+template <int MODE, int KS>  // MODE 0: density, 1: adjoint; KS: K-steps per stage
 __global__ void __launch_bounds__(kThreads, 1)
     k_split_rowdot(DevGrid G, const int2* __restrict__ items, int n_items, const CUtensorMap* __restrict__ maps,
                    const int64_t* __restrict__ scr_off, const double* __restrict__ scratch,
                    const int* __restrict__ rowexp, const int64_t* __restrict__ gsl_off,
-                   const unsigned char* __restrict__ gsl, unsigned present, int weighted,
-                   double* __restrict__ out, unsigned* status) {
+                   const unsigned char* __restrict__ gsl, const unsigned char* __restrict__ gzero,
+                   unsigned present, int weighted, double* __restrict__ out, unsigned* status) {
+  using L = Layout<KS>;
+  constexpr int kStages = L::kStages, kRaw = L::kRaw, kStage = L::kStage, kRawStage = L::kRawStage;
+  constexpr int kRawExp = L::kRawExp, kSmemRaw = L::kSmemRaw, kSmemStages = L::kSmemStages;
+  constexpr int kSmemY = L::kSmemY, kSmemBar = L::kSmemBar, kNumBars = L::kNumBars;
   extern __shared__ __align__(1024) unsigned char smem[];
   double* sY = reinterpret_cast<double*>(smem + kSmemY);    // [part][point]
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kSmemBar);
@@ -273,9 +291,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (present & (1u << product_of(k).gm)) plist |= static_cast<unsigned>(k) << (3 * n_prod++);
   auto prod_at = [&](int kk) { return product_of(static_cast<int>((plist >> (3 * kk)) & 7u)); };
 
-  for (int i = tid; i < kStages * kTileBytes / 16; i += kThreads) {  // tile Z of every stage
-    const int st = i / (kTileBytes / 16), off = i - st * (kTileBytes / 16);
-    reinterpret_cast<uint4*>(smem + kSmemStages + st * kStage)[off] = make_uint4(0, 0, 0, 0);
+  for (int i = tid; i < kStages * KS * kTileBytes / 16; i += kThreads) {  // tile Z of every K-step
+    const int sh = i / (kTileBytes / 16), off = i - sh * (kTileBytes / 16);
+    reinterpret_cast<uint4*>(smem + kSmemStages + sh * kHalf)[off] = make_uint4(0, 0, 0, 0);
   }
   fence_async_smem();  // the zero tiles are read by the tensor cores (async proxy)
   if (tid == 0) {
@@ -322,7 +340,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       const ItemInfo I = item_info(G, items[n]);
       const bool live = I.pt * kTile + p < I.np;
       const unsigned char* gblk = gsl + gsl_off[I.b];
-      const int n_steps = I.n_jt * n_prod * I.n_ic;
+      const int n_st = (I.n_ic + KS - 1) / KS;  // stages per group
+      const int n_steps = I.n_jt * n_prod * n_st;
       float m0 = 0.f, m1 = 0.f, m2 = 0.f, m3 = 0.f;  // rounding constants of the point's four quantities
       StepIter it;
       for (int s = 0; s < n_steps; ++s, ++g) {
@@ -339,33 +358,48 @@ __global__ void __launch_bounds__(kThreads, 1)
           m2 = magic0(e.z);
           m3 = magic0(e.w);
         }
-        float2 x[4];
+        float2 x[KS][4];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) x[k] = *reinterpret_cast<const float2*>(raw + (4 * q + k) * (kTile * 8) + p * 8);
+        for (int h = 0; h < KS; ++h)
+#pragma unroll
+          for (int k = 0; k < 4; ++k)
+            x[h][k] = *reinterpret_cast<const float2*>(raw + h * kRawTile + (4 * q + k) * (kTile * 8) + p * 8);
         if (!mbar_wait_abort(empty_bar(st), ((g / kStages) & 1) ^ 1, s_abort, status, G.wait_ns)) {
           ok = false;
           break;
         }
         const Product P = prod_at(it.kk);
         unsigned char* sA = smem + kSmemStages + st * kStage;
-        if (tid == 0) {  // this step's G' digits: one 12 KB block
-          const unsigned char* src =
-              gblk + (static_cast<int64_t>(P.gm) * I.n_jt * I.n_ic + static_cast<int64_t>(it.jt) * I.n_ic + it.ic) *
-                         kBlockB;
+        if (tid == 0) {  // this stage's G' digits: one block (up to 12 KB) per K-step
           const uint32_t bytes = kSlices * jt_width(I.nb, it.jt) * kRowBytes;  // the j-tile's six digit tiles
-          arrive_expect_tx(gfull_bar(st), bytes);
-          bulk_copy(smem_u32(sA + kStageA), src, bytes, gfull_bar(st));
+          arrive_expect_tx(gfull_bar(st), KS * bytes);
+#pragma unroll
+          for (int h = 0; h < KS; ++h) {
+            // a K-step past the last chunk of functions (odd chunk counts,
+            // KS = 2) multiplies zeros: its F box is zero-filled and its G'
+            // block is the zero block
+            const int ic = it.ic * KS + h;
+            const unsigned char* src =
+                ic < I.n_ic ? gblk + (static_cast<int64_t>(P.gm) * I.n_jt * I.n_ic +
+                                      static_cast<int64_t>(it.jt) * I.n_ic + ic) * kBlockB
+                            : gzero;
+            bulk_copy(smem_u32(sA + h * kHalf + kStageA), src, bytes, gfull_bar(st));
+          }
         }
         const float m = P.qf == 0 ? m0 : P.qf == 1 ? m1 : P.qf == 2 ? m2 : m3;
-        // functions (4q, 4q+1) and (4q+2, 4q+3) as packed pairs
-        float2 d01[kSlices], d23[kSlices];
-        slice6x2(pk2(x[0].x, x[1].x), pk2(x[0].y, x[1].y), m, d01);
-        slice6x2(pk2(x[2].x, x[3].x), pk2(x[2].y, x[3].y), m, d23);
 #pragma unroll
-        for (int t = 0; t < kSlices; ++t) {
-          asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(smem_u32(sA + (1 + t) * kTileBytes + dst_off)),
-                       "r"(bf16x2_exact(d01[t])), "r"(bf16x2_exact(d23[t]))
-                       : "memory");
+        for (int h = 0; h < KS; ++h) {
+          // functions (4q, 4q+1) and (4q+2, 4q+3) of K-step h as packed pairs
+          float2 d01[kSlices], d23[kSlices];
+          slice6x2(pk2(x[h][0].x, x[h][1].x), pk2(x[h][0].y, x[h][1].y), m, d01);
+          slice6x2(pk2(x[h][2].x, x[h][3].x), pk2(x[h][2].y, x[h][3].y), m, d23);
+#pragma unroll
+          for (int t = 0; t < kSlices; ++t) {
+            asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(
+                             smem_u32(sA + h * kHalf + (1 + t) * kTileBytes + dst_off)),
+                         "r"(bf16x2_exact(d01[t])), "r"(bf16x2_exact(d23[t]))
+                         : "memory");
+          }
         }
         fence_async_smem();
         mbar_arrive(full_bar(st));
@@ -375,7 +409,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         // TMA box overwrite values that were still on their way).
         __syncwarp();
         if (lane == 0) mbar_arrive(rawempty_bar(rs));
-        it.next(I.n_ic, n_prod);
+        it.next(n_st, n_prod);
       }
       // agree on stopping (a wait that gave up in one warp ends every role)
       if (bar_red_or(1, kSlicers, !ok || *s_abort)) break;
@@ -394,7 +428,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         const ItemInfo I = item_info(G, items[n]);
         const CUtensorMap* map = maps + I.b;
         const int r0 = I.pt * kTile, rows = min(kTile, I.np - r0);
-        const int n_steps = I.n_jt * n_prod * I.n_ic;
+        const int n_st = (I.n_ic + KS - 1) / KS;
+        const int n_steps = I.n_jt * n_prod * n_st;
         StepIter it;
         for (int s = 0; s < n_steps; ++s, ++g) {
           const int rs = g % kRaw;
@@ -403,10 +438,12 @@ __global__ void __launch_bounds__(kThreads, 1)
             break;
           }
           const uint32_t dst = smem_u32(smem + kSmemRaw + rs * kRawStage), fb = rawfull_bar(rs);
-          arrive_expect_tx(fb, kRawTile + (s == 0 ? rows * 16 : 0));
-          tma_load_3d(dst, map, r0, it.ic * kKc, prod_at(it.kk).qf, fb);
+          arrive_expect_tx(fb, KS * kRawTile + (s == 0 ? rows * 16 : 0));
+#pragma unroll
+          for (int h = 0; h < KS; ++h)  // boxes past the last function read zeros
+            tma_load_3d(dst + h * kRawTile, map, r0, (it.ic * KS + h) * kKc, prod_at(it.kk).qf, fb);
           if (s == 0) bulk_copy(dst + kRawExp, rowexp + 4 * (I.bp0 + r0), rows * 16, fb);
-          it.next(I.n_ic, n_prod);
+          it.next(n_st, n_prod);
         }
       }
       // no copy outlives the CTA: the last kRaw issued steps have landed
@@ -429,7 +466,8 @@ __global__ void __launch_bounds__(kThreads, 1)
           tc_fence_after();
           const uint32_t t0 = tmem + set * kSetCols;
           const int nbj = jt_width(I.nb, grp / n_prod);  // groups run (j-tile, product) in order
-          for (int ic = 0; ic < I.n_ic; ++ic, ++g) {
+          const int n_st = (I.n_ic + KS - 1) / KS;
+          for (int c = 0; c < n_st; ++c, ++g) {
             const int st = g % kStages;
             if (!mbar_wait_abort(full_bar(st), (g / kStages) & 1, s_abort, status, G.wait_ns, 32) ||
                 !mbar_wait_abort(gfull_bar(st), (g / kStages) & 1, s_abort, status, G.wait_ns, 32)) {
@@ -437,8 +475,11 @@ __global__ void __launch_bounds__(kThreads, 1)
               break;
             }
             tc_fence_after();
-            const uint32_t a = smem_u32(smem + kSmemStages + st * kStage), bb = a + kStageA;
-            mma_levels(t0, a, bb, ic == 0 ? 0u : 1u, nbj);
+#pragma unroll
+            for (int h = 0; h < KS; ++h) {
+              const uint32_t a = smem_u32(smem + kSmemStages + st * kStage + h * kHalf), bb = a + kStageA;
+              mma_levels(t0, a, bb, (c == 0 && h == 0) ? 0u : 1u, nbj);
+            }
             mma_commit(empty_bar(st));
           }
           if (ok) mma_commit(accfull_bar(set));
@@ -568,37 +609,57 @@ q4c_status prepare(const q4c_grid* g, const double* const mats[5], int slot0, co
 }
 
 // one wave [b0, b1) of the density (MODE 0) or adjoint (MODE 1): G' digit
-// blocks and the row-dot kernel; the wave's offset tables and basis tiles
-// (with per-point exponents) must already be in place
+// blocks and the row-dot kernel with KS K-steps per stage; the wave's offset
+// tables and basis tiles (with per-point exponents) must already be in place
 template <int MODE>
-q4c_status wave(const q4c_grid* g, int wv, const float2* const mdf[5], unsigned present, bool weighted,
-                double* out, cudaStream_t s) {
+q4c_status gslice_wave(const q4c_grid* g, int wv, const float2* const mdf[5], cudaStream_t s) {
   const int64_t b0 = g->wave_b0[wv], b1 = g->wave_b0[wv + 1];
   if (b1 <= b0) return Q4C_OK;
+  KernelScope ks("split_gslice", s);
+  k_gslice<<<dim3(static_cast<unsigned>(b1 - b0), MODE == 0 ? 1 : 5), 256, 0, s>>>(
+      g->view(), b0, MODE == 0 ? 5 : 2, mdf[0], mdf[1], mdf[2], mdf[3], mdf[4], g->d_gsl_off,
+      reinterpret_cast<uint32_t*>(g->d_gsl));
+  Q4C_CUDA(cudaGetLastError());
+  return Q4C_OK;
+}
+
+// the row-dot kernel of one wave (its G' blocks in place)
+template <int MODE, int KS>
+q4c_status rowdot_kernel(const q4c_grid* g, int wv, unsigned present, bool weighted, double* out, cudaStream_t s,
+                         const char* name) {
   int dev = 0, n_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
-  Q4C_CUDA(cudaFuncSetAttribute(k_split_rowdot<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemTotal));
-  {
-    KernelScope ks("split_gslice", s);
-    k_gslice<<<dim3(static_cast<unsigned>(b1 - b0), MODE == 0 ? 1 : 5), 256, 0, s>>>(
-        g->view(), b0, MODE == 0 ? 5 : 2, mdf[0], mdf[1], mdf[2], mdf[3], mdf[4], g->d_gsl_off,
-        reinterpret_cast<uint32_t*>(g->d_gsl));
-  }
-  Q4C_CUDA(cudaGetLastError());
+  Q4C_CUDA(cudaFuncSetAttribute(k_split_rowdot<MODE, KS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                Layout<KS>::kSmemTotal));
   const int64_t i0 = g->rd_w0[wv], i1 = g->rd_w0[wv + 1];
   const int n_items = static_cast<int>(i1 - i0);
   if (n_items == 0) return Q4C_OK;
   const int grid = std::min(n_items, n_sm);
   {
-    KernelScope ks(MODE == 0 ? "split_density" : "split_backward", s);
-    k_split_rowdot<MODE><<<grid, kThreads, kSmemTotal, s>>>(
+    KernelScope ks(name, s);
+    k_split_rowdot<MODE, KS><<<grid, kThreads, Layout<KS>::kSmemTotal, s>>>(
         g->view(), g->d_rd_items + i0, n_items, reinterpret_cast<const CUtensorMap*>(g->d_tmaps) + g->n_batches,
         g->d_scr_off, g->d_scratch, g->d_rowexp, g->d_gsl_off, reinterpret_cast<const unsigned char*>(g->d_gsl),
-        present, weighted ? 1 : 0, out, g->d_status);
+        g->d_gzero, present, weighted ? 1 : 0, out, g->d_status);
   }
   Q4C_CUDA(cudaGetLastError());
   return Q4C_OK;
+}
+
+template <int MODE>
+q4c_status kernel_ks(const q4c_grid* g, int wv, unsigned present, bool weighted, double* out, cudaStream_t s, int ks,
+                     const char* name) {
+  if (ks == 2) return rowdot_kernel<MODE, 2>(g, wv, present, weighted, out, s, name);
+  return rowdot_kernel<MODE, 1>(g, wv, present, weighted, out, s, name);
+}
+
+template <int MODE>
+q4c_status wave(const q4c_grid* g, int wv, const float2* const mdf[5], unsigned present, bool weighted,
+                double* out, cudaStream_t s) {
+  if (g->wave_b0[wv + 1] <= g->wave_b0[wv]) return Q4C_OK;
+  if (q4c_status st = gslice_wave<MODE>(g, wv, mdf, s)) return st;
+  return kernel_ks<MODE>(g, wv, present, weighted, out, s, g->rd_ks, MODE == 0 ? "split_density" : "split_backward");
 }
 
 template <int MODE>
@@ -633,6 +694,53 @@ q4c_status rowdot_wave(const q4c_grid* g, int wv, int mode, const float2* const 
                        bool weighted, double* out, cudaStream_t s) {
   return mode == 0 ? rowdot::wave<0>(g, wv, mdf, present, weighted, out, s)
                    : rowdot::wave<1>(g, wv, mdf, present, weighted, out, s);
+}
+
+// the tuner's part for the row-dot kernel: the adjoint kernel of wave 0 with
+// both stage shapes (G' from zero matrices, sliced once: the kernel's work
+// does not depend on the values), one untimed launch each, then three rounds
+// alternating the shapes, each launch between CUDA events; the faster shape
+// is kept for the grid.  The wave's offset tables and basis tiles with
+// per-point exponents must be in place.
+q4c_status autotune_rowdot(q4c_grid* g, double* out, cudaStream_t s) {
+  g->rd_tune_ms[0] = g->rd_tune_ms[1] = -1.0;
+  if (g->wave_b0.size() < 2 || g->max_nb > rowdot::kMaxNb || g->nnz == 0) return Q4C_OK;
+  if (g->wave_b0[1] <= g->wave_b0[0]) return Q4C_OK;
+  const float2* mdf[5];
+  for (int m = 0; m < 5; ++m) mdf[m] = g->d_gdf + (5 + m) * g->nnz;
+  Q4C_CUDA(cudaMemsetAsync(g->d_gdf + 5 * g->nnz, 0, sizeof(float2) * 5 * g->nnz, s));
+  if (q4c_status st = rowdot::gslice_wave<1>(g, 0, mdf, s)) return st;
+  cudaEvent_t ev[2][3][2] = {};
+  q4c_status status = Q4C_OK;
+  for (int k = 0; k < 2; ++k)
+    for (int r = 0; r < 3; ++r)
+      for (int e = 0; e < 2; ++e)
+        if (cudaEventCreate(&ev[k][r][e]) != cudaSuccess) status = Q4C_ECUDA;
+  for (int ks = 1; ks <= 2 && status == Q4C_OK; ++ks)
+    status = rowdot::kernel_ks<1>(g, 0, 31u, true, out, s, ks, "split_tune");
+  for (int r = 0; r < 3 && status == Q4C_OK; ++r)
+    for (int ks = 1; ks <= 2 && status == Q4C_OK; ++ks) {
+      cudaEventRecord(ev[ks - 1][r][0], s);
+      status = rowdot::kernel_ks<1>(g, 0, 31u, true, out, s, ks, "split_tune");
+      cudaEventRecord(ev[ks - 1][r][1], s);
+    }
+  if (status == Q4C_OK && cudaStreamSynchronize(s) != cudaSuccess) status = Q4C_ECUDA;
+  for (int k = 0; k < 2 && status == Q4C_OK; ++k) {
+    double sum = 0.0;
+    for (int r = 0; r < 3; ++r) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, ev[k][r][0], ev[k][r][1]) != cudaSuccess) status = Q4C_ECUDA;
+      sum += ms;
+    }
+    g->rd_tune_ms[k] = sum / 3.0;
+  }
+  if (status == Q4C_OK) g->rd_ks = g->rd_tune_ms[1] < g->rd_tune_ms[0] ? 2 : 1;
+  else set_error("q4c_autotune: timing of the density/adjoint kernel failed");
+  for (int k = 0; k < 2; ++k)
+    for (int r = 0; r < 3; ++r)
+      for (int e = 0; e < 2; ++e)
+        if (ev[k][r][e]) cudaEventDestroy(ev[k][r][e]);
+  return status;
 }
 
 q4c_status density_split(const q4c_tables* t, const q4c_grid* g, const double* P, double* n, cudaStream_t s) {

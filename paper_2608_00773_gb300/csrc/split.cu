@@ -622,14 +622,23 @@ q4c_status integrate_columns_split(const q4c_tables* t, const q4c_grid* g, const
 // rounding constants in place, each batch-size bucket's items run with one
 // and with two K-steps per stage (one untimed launch, then three timed by
 // CUDA events on the stream) into scratch outputs; the faster shape is kept
-// for the bucket.
+// for the bucket.  The density/adjoint kernel's shape is chosen the same way
+// (one per grid) on the same tiles.
 q4c_status autotune_split(const q4c_tables* t, q4c_grid* g, const double* v, cudaStream_t s) {
   if (g->max_np > 341 || g->wave_b0.size() < 2) return Q4C_OK;
   for (int k = 0; k < kTileBuckets; ++k) g->tune_ms[k][0] = g->tune_ms[k][1] = -1.0;
   const int64_t b0 = g->wave_b0[0], b1 = g->wave_b0[1];
   if (b1 <= b0) return Q4C_OK;
   if (q4c_status st = launch_fill_idx(t, g, b0, b1, s)) return st;
-  if (q4c_status st = launch_basis_df(t, g, b0, b1, v, g->d_colexp, nullptr, 4, s, g->d_dpad)) return st;
+  if (q4c_status st = launch_basis_df(t, g, b0, b1, v, g->d_colexp, g->d_rowexp, 4, s, g->d_dpad)) return st;
+  {  // the density/adjoint kernel's shape (one per grid), on the same tiles
+    double* out = nullptr;
+    Q4C_CUDA(cudaMalloc(&out, sizeof(double) * std::max<int64_t>(g->n_pts, 1)));
+    const q4c_status st = autotune_rowdot(g, out, s);
+    cudaStreamSynchronize(s);
+    cudaFree(out);
+    if (st) return st;
+  }
   const int64_t* r = g->split_bw0.data();
   const int64_t i0 = r[0], i1 = r[kTileBuckets];
   if (i1 <= i0) return Q4C_OK;

@@ -24,7 +24,7 @@ def cases():
 
 
 def _set_all(grid, ks):
-    for k in range(q.binding.TILE_BUCKETS):
+    for k in range(q.binding.TILE_BUCKETS + 1):  # the products buckets and the density/adjoint kernel
         q.q4c_grid_set_tiling(grid, k, ks)
 
 
@@ -32,12 +32,20 @@ def _set_all(grid, ks):
 def test_every_shape_matches_oracle_and_each_other(name, cases):
     lib, orc = cases[name]
     outs = {}
+    li, oi = point_map(lib.ex["point_id"], orc.ids)
+    n_ref = orc.ob.density(orc.xyz, orc.random(61, "P"), orc.pat)
+    g_ref = orc.ob.adjoint(orc.xyz, orc.w, orc.G(62), orc.pat)
     for ks in (1, 2):
         _set_all(lib.grid, ks)
         outs[ks] = lib.integrate("split", spinor=True)
+        n = q.q4c_density(lib.tables, lib.grid, lib.random(61, "P"), "split").cpu().numpy()
+        g = q.q4c_integrate_backward(lib.tables, lib.grid, lib.G(62), "split").cpu().numpy()
         lib.grid.status()
         for m, r in zip(outs[ks][:5], orc.mats):
             assert rel_fro(m, r) <= 1e-9
+        assert rel_fro(n[li], n_ref[oi]) <= 1e-9
+        assert rel_fro(g[li], g_ref[oi]) <= 1e-9
+        outs[ks] = outs[ks] + [n, g]
     _set_all(lib.grid, 1)
     for a, b in zip(outs[1], outs[2]):
         assert rel_fro(b, a) <= 1e-13
@@ -69,7 +77,7 @@ def test_shapes_in_the_column_operator_and_the_one_pass_call(cases):
 
 def test_set_tiling_rejects_bad_arguments(cases):
     lib, _ = cases["water"]
-    for bucket, ks in ((-1, 1), (4, 1), (0, 3), (0, 0)):
+    for bucket, ks in ((-1, 1), (5, 1), (0, 3), (4, 0)):
         with pytest.raises(q.Q4CError) as e:
             q.q4c_grid_set_tiling(lib.grid, bucket, ks)
         assert e.value.status == 1
@@ -88,10 +96,10 @@ def test_autotune_times_every_used_bucket_and_keeps_the_faster():
     torch.cuda.synchronize()
     lib.grid.status()
     used = [t for t in tiling if t["batches"] > 0]
-    assert len(used) >= 3
+    assert len(used) >= 4 and tiling[-1]["batches"] == lib.grid.info.n_batches  # the last: density/adjoint
     for t in used:
         assert t["ms_one"] > 0 and t["ms_two"] > 0
         assert t["k_steps"] == (2 if t["ms_two"] < t["ms_one"] else 1)
-    assert sum(t["batches"] for t in tiling) == lib.grid.info.n_batches
+    assert sum(t["batches"] for t in tiling[:-1]) == lib.grid.info.n_batches
     for a, b in zip(after[:5], before[:5]):
         assert float(torch.linalg.norm(a - b) / torch.linalg.norm(b)) <= 1e-13
