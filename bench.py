@@ -196,6 +196,47 @@ def host_cores() -> int:
         return os.cpu_count() or 1
 
 
+def oracle_molecules_sample(wl, stride: int, threads: int = 1):
+    """Batched molecules are independent: one oracle step for every stride-th
+    molecule, each on its own grid, pattern and v, the molecules dealt to
+    `threads` concurrent parts; returns (wall seconds, fraction of the
+    workload's algorithmic FLOPs those molecules carry)."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    import oracle as O
+    from workloads import ADJOINT_KINDS, fill_pattern, potential
+    mols = list(range(0, wl.n_molecules, stride))
+    jobs = []
+    for m in mols:
+        wm = wl.molecule(m)
+        xyz, w, ids = O.grid(wm)
+        ob = O.OracleBasis(wm)
+        pat = ob.pattern()
+        P = fill_pattern(pat.blk_ptr, pat.blk_col, pat.blk_off, wm.nf_of_atom, 11, "P")
+        G = [fill_pattern(pat.blk_ptr, pat.blk_col, pat.blk_off, wm.nf_of_atom, 12, k, a) for k, a in ADJOINT_KINDS]
+        jobs.append((ob, pat, xyz, w, potential(xyz, wm), P, G))
+
+    def one(job):
+        ob, pat, xyz, w, v, P, G = job
+        ob.matrix_blocks(xyz, w, v, pat)
+        ob.density(xyz, P, pat)
+        ob.adjoint(xyz, w, G, pat)
+
+    t0 = time.perf_counter()
+    if threads == 1:
+        for j in jobs:
+            one(j)
+    else:
+        with ThreadPoolExecutor(max_workers=threads) as ex:
+            list(ex.map(one, jobs))
+    t = time.perf_counter() - t0
+    # the sampled molecules' share of the work: their atoms' functions squared, weighted by atoms
+    nf = wl.nf_of_atom.astype(np.float64)
+    cost = np.array([float(nf[wl.mol_atom_ptr[m]:wl.mol_atom_ptr[m + 1]].sum()) ** 2 *
+                     (wl.mol_atom_ptr[m + 1] - wl.mol_atom_ptr[m]) for m in range(wl.n_molecules)])
+    return t, float(cost[mols].sum() / cost.sum())
+
+
 def oracle_step_sample(wl, stride: int, threads: int = 1):
     """One oracle step (matrices, density, adjoint) on the raw grid points with
     id % stride == 0, the points dealt round-robin to `threads` parts that run
@@ -206,6 +247,8 @@ def oracle_step_sample(wl, stride: int, threads: int = 1):
 
     import oracle as O
     from workloads import ADJOINT_KINDS, fill_pattern, potential
+    if getattr(wl, "mol_atom_ptr", None) is not None:
+        return oracle_molecules_sample(wl, stride, threads)
     xyz, w, ids = O.grid(wl, stride=stride)
     ob = O.OracleBasis(wl)
     pat = ob.pattern()
@@ -240,23 +283,31 @@ def run_reference(args, wl):
     rank, world, _ = dist_init()
     if rank != 0:
         return
-    flops = workload_flops(wl)
     cores = host_cores()
-    times = []
+    batched = getattr(wl, "mol_atom_ptr", None) is not None
+    if batched:  # independent molecules: the FLOPs of the sampled molecules, each on its own grid
+        flops = sum(workload_flops(wl.molecule(m)) for m in range(0, wl.n_molecules, args.ref_stride))
+    else:
+        flops = workload_flops(wl)
+    times, fracs = [], []
     for _ in range(args.warmup):
         oracle_step_sample(wl, args.ref_stride, cores)
     for _ in range(args.steps):
         t, frac = oracle_step_sample(wl, args.ref_stride, cores)
-        times.append(t / frac)
-    t_step = statistics.mean(times)
-    val = flops / t_step / 1e12
+        times.append(t)
+        fracs.append(frac)
+    t_sample = statistics.mean(times)
+    t_step = t_sample / fracs[0]
+    val = (flops / t_sample if batched else flops / t_step) / 1e12
+    sample = (f"every {args.ref_stride}-th molecule on its own grid" if batched else
+              f"raw grid ids divisible by {args.ref_stride}")
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "TFLOP/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": wl.name, "note": f"oracle (plain FP64 C, {cores} host threads) on a uniform "
-                       f"1/{args.ref_stride} sample of the raw grid, time scaled to the full workload"},
+                       f"sample ({sample}), time scaled to the full workload"},
             "cpu_baseline": {"value": val, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
-                             "sample": f"raw grid ids divisible by {args.ref_stride}, split over {cores} threads"},
+                             "sample": f"{sample}, split over {cores} threads"},
             "e2e": {"value": val, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
@@ -298,7 +349,9 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=3,
                     help="FP64-path steps timed after the split run for the speedup (0: skip)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="cluster64", choices=["cluster64", "water"])
+    ap.add_argument("--workload", default="cluster64", choices=["cluster64", "water", "molecules", "cluster512"],
+                    help="cluster64: the 64-atom cluster (default); molecules: 2,000 independent molecules "
+                         "in one grid; cluster512: the 512-atom cluster of the adjoint configuration")
     ap.add_argument("--cpu-stride", type=int, default=16, help="one-core sample of the cpu baseline")
     ap.add_argument("--cpu-stride-all", type=int, default=2, help="all-core sample of the cpu baseline")
     ap.add_argument("--ref-stride", type=int, default=7)
@@ -314,9 +367,22 @@ def main():
             print(f"source_sha256[{name}]: {kernel_source_hash(name)}")
         return
 
-    from workloads import cluster64, water
-    wl = cluster64() if args.workload == "cluster64" else water()
+    from workloads import cluster512, cluster64, molecule_batch, water
+    wl = {"cluster64": cluster64, "water": water, "molecules": molecule_batch, "cluster512": cluster512}[args.workload]()
+    # sample strides that keep the oracle's share of a run to seconds
+    if args.workload in ("molecules", "cluster512"):
+        default_strides = {"molecules": (200, 20), "cluster512": (4000, 400)}[args.workload]
+        if args.cpu_stride == 16:
+            args.cpu_stride = default_strides[0]
+        if args.cpu_stride_all == 2:
+            args.cpu_stride_all = default_strides[1]
     if args.impl == "reference":
+        if args.workload == "cluster512":
+            print(json.dumps({"impl": "reference", "unavailable": "the oracle's FLOP count of the 512-atom cluster "
+                              "needs its full grid (about 8 min of host time), beyond this arm's few-minute bound"}))
+            return
+        if args.workload == "molecules" and args.ref_stride == 7:
+            args.ref_stride = 100
         return run_reference(args, wl)
 
     import torch
@@ -333,7 +399,12 @@ def main():
     ex = grid.export()
     info = grid.info
     pat = (ex["blk_ptr"], ex["blk_col"], ex["blk_off"])
-    v_h = potential(ex["xyz"], wl)
+    if getattr(wl, "mol_atom_ptr", None) is not None:  # each point's potential from its own molecule
+        from workloads import molecule_potential
+        ppa = wl.n_rad * wl.n_theta * wl.n_phi
+        v_h = molecule_potential(ex["xyz"], ex["point_id"] // ppa, wl, device=dev)
+    else:
+        v_h = potential(ex["xyz"], wl, device=dev if grid.n_points > 4_000_000 else None)
     P_h = fill_pattern(*pat, wl.nf_of_atom, 11, "P")
     G_h = [fill_pattern(*pat, wl.nf_of_atom, 12, k, a) for k, a in ADJOINT_KINDS]
     v = torch.tensor(v_h, device=dev)
@@ -505,6 +576,8 @@ def main():
         "tensor_frac_note": f"x {S_PAIRS} slice pairs / {peak_src} bf16 burst, whole call incl. basis and scatter"}
 
     # ---- FP64 comparison path and split error (reported beside the value)
+    if args.workload in ("molecules", "cluster512") and args.fp64_steps == 3:
+        args.fp64_steps = 1  # the FP64 path takes tens of seconds per step there
     if prec == "split" and args.fp64_steps > 0:
         ref = [torch.empty_like(m) for m in mats[:5]]
         q.q4c_integrate(tables, grid, v, "fp64", out=ref + [None], stream=stream)
@@ -512,6 +585,20 @@ def main():
         torch.cuda.synchronize()
         extra["split_rel_err_vs_fp64"] = {n: float(torch.linalg.norm(a - b) / torch.linalg.norm(b))
                                           for n, a, b in zip(["V", "W0", "SOx", "SOy", "SOz"], mats[:5], ref)}
+        if getattr(wl, "mol_atom_ptr", None) is not None:
+            # every molecule on its own: the largest relative error over the molecules, per matrix
+            offs = ex["blk_off"][ex["blk_ptr"][wl.mol_atom_ptr]]
+            worst = {}
+            for nme, a, b in zip(["V", "W0", "SOx", "SOy", "SOz"], mats[:5], ref):
+                d = (a - b).double() ** 2
+                r = b.double() ** 2
+                cd = torch.cat([torch.zeros(1, dtype=torch.float64, device=dev), torch.cumsum(d, 0)])
+                cr = torch.cat([torch.zeros(1, dtype=torch.float64, device=dev), torch.cumsum(r, 0)])
+                o = torch.tensor(offs, device=dev)
+                num, den = cd[o[1:]] - cd[o[:-1]], cr[o[1:]] - cr[o[:-1]]
+                worst[nme] = float(torch.sqrt(num / torch.clamp(den, min=1e-300)).max())
+            extra["split_rel_err_vs_fp64_worst_molecule"] = worst
+            extra["molecules"] = int(wl.n_molecules)
         # the same step on the FP64 path (device time, L2 flushed), for the split/FP64 speedup
         fp64_phase = {"integrate": "fp64", "density": "fp64", "backward": "fp64"}
 

@@ -116,8 +116,8 @@ template <typename Out>
 __device__ __forceinline__ void atom_functions(const DevBasis& B, int species, double dx, double dy, double dz,
                                                Out&& out) {
   const int r0 = __ldg(B.sp_rad0 + species), nr = __ldg(B.sp_nrad + species);
-  const double r2 = dx * dx + dy * dy + dz * dz;
-  if (!(r2 < B.r_c2)) {
+  const double r = centre_distance(dx, dy, dz);
+  if (!(r < B.r_c)) {
     int k = 0;
     for (int q = 0; q < nr; ++q) {
       const int l = __ldg(B.rad_l + r0 + q);
@@ -129,7 +129,6 @@ __device__ __forceinline__ void atom_functions(const DevBasis& B, int species, d
   for (int q = 0; q < nr; ++q) lmax = max(lmax, __ldg(B.rad_l + r0 + q));
   double S[(kMaxL + 1) * (kMaxL + 1)], dS[3 * (kMaxL + 1) * (kMaxL + 1)];
   solid_harmonics(dx, dy, dz, lmax, S, dS);
-  const double r = sqrt(r2);
   const double inv_r = r > 0.0 ? 1.0 / r : 0.0;
   const double ux = dx * inv_r, uy = dy * inv_r, uz = dz * inv_r;
   int k = 0;

@@ -266,7 +266,16 @@ __global__ void __launch_bounds__(256, 4) k_basis_df(DevBasis B, DevGrid G, DfTa
     const df dy = df_sub(T.pts[3 * (p0 + pp) + 1], T.atoms[3 * A + 1]);
     const df dz = df_sub(T.pts[3 * (p0 + pp) + 2], T.atoms[3 * A + 2]);
     const df r2 = df_add(df_add(df_mul(dx, dx), df_mul(dy, dy)), df_mul(dz, dz));
-    const bool in = live && r2.hi < T.rc2;
+    // inside the cutoff sphere, below the first knot: in FP32 away from the
+    // two spheres; within FP32 rounding of either (where the gradient jumps),
+    // from the FP64 coordinates as the FP64 path decides
+    bool in = live && r2.hi < T.rc2, below = r2.hi < T.rmin2;
+    if (live && (fabsf(r2.hi - T.rc2) <= T.rc2 * 0x1p-18f || fabsf(r2.hi - T.rmin2) <= T.rmin2 * 0x1p-18f)) {
+      const double r64 = centre_distance(G.x[p0 + p] - G.c_xyz[3 * A], G.y[p0 + p] - G.c_xyz[3 * A + 1],
+                                         G.z[p0 + p] - G.c_xyz[3 * A + 2]);
+      in = r64 < B.r_c;
+      below = r64 < B.r_min;
+    }
     int eD = -30000;
     if (colexp && live) {
       const double Dp = NQ == 2 ? G.w[p0 + p] : G.w[p0 + p] * v[p0 + p];
@@ -291,7 +300,6 @@ __global__ void __launch_bounds__(256, 4) k_basis_df(DevBasis B, DevGrid G, DfTa
     const df ir = pos ? df_div(df{1.f, 0.f}, r) : df{0.f, 0.f};
     const df ux = df_mul(dx, ir), uy = df_mul(dy, ir), uz = df_mul(dz, ir);
     // log-grid interval and local coordinate s (shared by the atom's radials)
-    const bool below = r.hi < T.rmin;
     int k = 0;
     df s = {0.f, 0.f};
     if (in && !below) {

@@ -361,7 +361,7 @@ __global__ void __launch_bounds__(256) k_columns_fp64(DevBasis B, DevGrid G, con
       if (p < np && fj < nb && s_rad[f] >= 0) {
         const int64_t gp = p0 + p;
         const double dx = G.x[gp] - s_c[0][f], dy = G.y[gp] - s_c[1][f], dz = G.z[gp] - s_c[2][f];
-        const double Vr = column_potential(B, vcoef, s_rad[f], sqrt(dx * dx + dy * dy + dz * dz));
+        const double Vr = column_potential(B, vcoef, s_rad[f], centre_distance(dx, dy, dz));
         th = base[static_cast<int64_t>(fj) * ldp + p] * G.w[gp] * (v[gp] + s_eps[f] - Vr);
       }
       sb[kk][f] = th;

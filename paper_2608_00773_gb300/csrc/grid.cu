@@ -97,7 +97,7 @@ __global__ void k_becke(const double* __restrict__ raw, const double* __restrict
   bool near = false;
   for (int B = range.x; B < range.y; ++B) {
     const double dx = px - atom_xyz[3 * B], dy = py - atom_xyz[3 * B + 1], dz = pz - atom_xyz[3 * B + 2];
-    const double d = sqrt(dx * dx + dy * dy + dz * dz);
+    const double d = centre_distance(dx, dy, dz);
     if (d < r_c) near = true;
     if (d < r_nb) {
       if (nn == kMaxNeighbours) {
@@ -586,7 +586,7 @@ extern "C" q4c_status grid_partition(const q4c_grid_desc* d, const q4c_tables* t
       for (int64_t i = p0; i < p1; ++i) {
         const double dx = g->h_xyz[3 * i] - cx[3 * A], dy = g->h_xyz[3 * i + 1] - cx[3 * A + 1],
                      dz = g->h_xyz[3 * i + 2] - cx[3 * A + 2];
-        if (std::sqrt(dx * dx + dy * dy + dz * dz) < r_c) {
+        if (centre_distance(dx, dy, dz) < r_c) {
           act[b].push_back(A);
           break;
         }

@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -23,6 +24,23 @@ inline int tile_bucket(int64_t nb) {
   int k = 0;
   while (k + 1 < kTileBuckets && nb > kBucketNb[k]) ++k;
   return k;
+}
+
+// Distance of a point from a centre as every decision on it is taken (is the
+// point inside the cutoff sphere r < r_c, is it below the first knot r <
+// r_min): the squares summed as (dx dx + dy dy) + dz dz, each operation
+// rounded on its own (no fused multiply-add), then a correctly rounded square
+// root.  The radial functions' gradients jump at r_c and at r_min, so a point
+// within rounding of either sphere must land on the same side in every path
+// and in a plain FP64 evaluation of the same formula.
+__host__ __device__ inline double centre_distance(double dx, double dy, double dz) {
+#ifdef __CUDA_ARCH__
+  return sqrt(__dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz)));
+#else
+  volatile double xx = dx * dx, yy = dy * dy, zz = dz * dz;  // stored: no contraction into an FMA
+  volatile double s = xx + yy;
+  return std::sqrt(s + zz);
+#endif
 }
 
 // ---------------------------------------------------------------- errors
@@ -64,7 +82,7 @@ struct DevBasis {
   const int* sp_rad0;    // [n_species] first radial of each species
   const int* sp_nrad;    // [n_species]
   const int* sp_nfn;     // [n_species]
-  double r_c, r_c2, r_min, inv_rmin, inv_h;
+  double r_c, r_min, inv_rmin, inv_h;
   int n_log;
 };
 
@@ -76,7 +94,7 @@ struct DfTables {
   const df* pts;          // [n_points][3] kept points (batch order)
   const df* atoms;        // [n_centres][3] centre positions (atoms and periodic images)
   df inv_h_df;
-  float inv_h, inv_rmin, rmin, rc2;
+  float inv_h, inv_rmin, rmin2, rc2;  // FP32 copies: 1/h, 1/r_min, r_min^2, r_c^2
 };
 
 // Grid, batches and pattern as seen by kernels.

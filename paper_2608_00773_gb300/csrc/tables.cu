@@ -61,7 +61,6 @@ DevBasis q4c_tables::view() const {
   b.sp_nrad = d_sp_nrad;
   b.sp_nfn = d_sp_nfn;
   b.r_c = r_c;
-  b.r_c2 = r_c * r_c;
   b.r_min = r_min;
   b.inv_rmin = 1.0 / r_min;
   b.inv_h = 1.0 / h;
@@ -78,7 +77,7 @@ DfTables q4c_tables::df_view() const {
   d.inv_h_df = df{static_cast<float>(ih), static_cast<float>(ih - static_cast<float>(ih))};
   d.inv_h = static_cast<float>(ih);
   d.inv_rmin = static_cast<float>(1.0 / r_min);
-  d.rmin = static_cast<float>(r_min);
+  d.rmin2 = static_cast<float>(r_min * r_min);
   d.rc2 = static_cast<float>(r_c * r_c);
   return d;
 }

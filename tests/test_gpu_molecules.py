@@ -83,18 +83,32 @@ def test_each_molecule_matches_its_own_oracle(prec, small):
 
 def test_two_thousand_molecules_sampled():
     """The batched-molecule configuration at full size (2,000 molecules of
-    3-40 atoms, 40 x 200 points per atom, one grid, one split call); five
-    small molecules are checked against the oracle, each on its own."""
+    3-40 atoms, 40 x 200 points per atom, one grid, one split call): every
+    molecule's blocks against the FP64 path (the largest relative error over
+    the molecules, per matrix), and 20 molecules spread over the sizes, the
+    three largest among them, each against its own oracle."""
     import time
+    from concurrent.futures import ThreadPoolExecutor
     t0 = time.time()
     wl = molecule_batch()
     tables, grid, ex, v = _lib(wl)
     t1 = time.time()
-    outs = [o.cpu().numpy() for o in q.q4c_integrate(tables, grid, v, "split")[:5]]
+    split = [o.cpu().numpy() for o in q.q4c_integrate(tables, grid, v, "split")[:5]]
+    fp64 = [o.cpu().numpy() for o in q.q4c_integrate(tables, grid, v, "fp64")[:5]]
     grid.status()
-    print(f"setup + v {t1 - t0:.1f} s, integrate {time.time() - t1:.1f} s, points {grid.n_points}, "
+    print(f"setup + v {t1 - t0:.1f} s, integrate (both paths) {time.time() - t1:.1f} s, points {grid.n_points}, "
           f"batches {grid.info.n_batches}, basis {grid.info.n_basis}")
+    worst = {}
+    for n, a, b in zip(NAMES, split, fp64):
+        worst[n] = max(rel_fro(a[o0:o1], b[o0:o1])
+                       for o0, o1 in ((_mol_slice(ex, wl, m)[4], _mol_slice(ex, wl, m)[5])
+                                      for m in range(wl.n_molecules)))
+    print("worst molecule, split vs FP64:", worst)
+    assert max(worst.values()) <= 1e-12
     sizes = np.diff(wl.mol_atom_ptr)
-    mols = [int(m) for m in np.where(sizes <= 5)[0][:5]]
-    assert len(mols) == 5
-    _check_molecules(wl, ex, outs, mols, TOL["split"])
+    order = np.argsort(sizes, kind="stable")
+    pick = list(order[np.linspace(0, len(order) - 4, 17).astype(int)]) + list(order[-3:])
+    mols = sorted(set(int(m) for m in pick))
+    assert len(mols) >= 20 and sizes[mols].max() == sizes.max() and sizes[mols].min() == sizes.min()
+    with ThreadPoolExecutor(max_workers=8) as pool:  # the oracle's C calls release the GIL
+        list(pool.map(lambda m: _check_molecules(wl, ex, split, [m], TOL["split"]), mols))
