@@ -245,7 +245,11 @@ Q4C_API q4c_status q4c_integrate(const q4c_tables* tables, const q4c_grid* grid,
 
 /* Density (Eqs. 39-40): n_p = sum_ij P_ij phi_i(p) phi_j(p), P_dev device
  * [nnz] on the block pattern (any P; only its symmetric part contributes),
- * n_dev device [n_points] in batch order, overwritten. */
+ * n_dev device [n_points] in batch order, overwritten.  Q4C_SPLIT takes
+ * batches of up to 4096 active functions (above 512 the sum over i runs in
+ * exact segments of 512 combined in FP64), Q4C_FP64 up to 7264;
+ * Q4C_EUNSUPPORTED beyond.  The split limit holds for q4c_density_full and
+ * q4c_integrate_backward too; their FP64 path takes up to 5811. */
 Q4C_API q4c_status q4c_density(const q4c_tables* tables, const q4c_grid* grid, const double* P_dev,
                        q4c_precision prec, double* n_dev, q4c_stream stream);
 
@@ -420,7 +424,7 @@ Q4C_API q4c_status q4c_scf_pass(const q4c_tables* tables, const q4c_grid* grid, 
  * The density/adjoint kernel (row-dot products over 16-function K-steps)
  * has one such shape per grid, tuned on the same wave with its adjoint; it is
  * addressed as bucket Q4C_TILE_BUCKETS below.
- * q4c_grid_tiling reports a bucket: its largest n_b (512 for the row-dot
+ * q4c_grid_tiling reports a bucket: its largest n_b (4096 for the row-dot
  * kernel), the shape in use, the grid's batches in it (all for the row-dot
  * kernel), and the tuner's mean time per launch for one and two K-steps
  * (-1 if not timed); NULL outputs are skipped.

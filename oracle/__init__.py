@@ -7,5 +7,6 @@ takes its inputs from workloads/.
 """
 from .oracle import (  # noqa: F401
     build, lib, OracleBasis, gauss_legendre, radial_shells, cutoff, tabulate, spline_eval,
-    ylm_spherical, solid_harmonic, K_lm, becke_weight, partition_weight, PARTITIONS, grid, Pattern,
+    ylm_spherical, solid_harmonic, K_lm, becke_weight, partition_weight, PARTITIONS, grid, grid_near, centres,
+    Pattern,
 )

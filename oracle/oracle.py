@@ -78,10 +78,16 @@ def lib() -> C.CDLL:
             L.orc_grid_cell.argtypes = [C.c_int, _dp, C.c_void_p, C.c_int, C.c_int, C.c_double, C.c_int,
                                         C.c_int, C.c_double, C.c_double, C.c_int, C.c_longlong, _dp, _dp, _lp]
             L.orc_grid_cell.restype = C.c_long
+            L.orc_grid_near.argtypes = [C.c_int, _dp, C.c_void_p, C.c_int, C.c_int, C.c_double, C.c_int,
+                                        C.c_int, C.c_double, C.c_double, C.c_int, C.c_int, _dp, C.c_long,
+                                        _dp, _dp, _lp]
+            L.orc_grid_near.restype = C.c_long
             L.orc_pattern.argtypes = [bp, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
             L.orc_pattern.restype = C.c_long
             L.orc_matrix_pairs.argtypes = [bp, C.c_long, _dp, _dp, _dp, C.c_long, _ip, _ip,
                                            _dp, _dp, _dp, _dp, _dp]
+            L.orc_matrix_entries.argtypes = [bp, C.c_long, _dp, _dp, _dp, C.c_long, _ip, _ip, _ip, _ip, _ip,
+                                             _dp, _dp, _dp, _dp, _dp]
             L.orc_matrix_blocks.argtypes = [bp, C.c_long, _dp, _dp, _dp, _lp, _ip, _ip, _lp,
                                             _dp, _dp, _dp, _dp, _dp]
             L.orc_matrix_blocks.restype = C.c_int
@@ -181,6 +187,36 @@ def grid(wl, stride: int = 1):
     return xyz[:3 * n].reshape(n, 3).copy(), w[:n].copy(), ids[:n].copy()
 
 
+def centres(wl) -> np.ndarray:
+    """Positions of the atoms and, in a periodic cell, their images in the
+    oracle's centre order (cell-major, T lexicographic in [-n_shell, n_shell]^3)."""
+    if wl.lattice is None:
+        return _f64(wl.xyz).reshape(-1, 3).copy()
+    s = wl.n_shell
+    L = _f64(wl.lattice).reshape(3, 3)
+    T = np.array([(a, b, c) for a in range(-s, s + 1) for b in range(-s, s + 1) for c in range(-s, s + 1)],
+                 dtype=np.float64)
+    return ((T @ L)[:, None, :] + _f64(wl.xyz).reshape(1, -1, 3)).reshape(-1, 3)
+
+
+def grid_near(wl, targets):
+    """The kept grid points (stride 1) within r_c of at least one target
+    position: (xyz, w, raw id), the same points and weights as grid(wl)
+    restricted to them, in raw id order."""
+    targets = _f64(targets).reshape(-1, 3)
+    # buffer bound: the raw points of atoms within r_c + r_nb of a target
+    d = np.linalg.norm(_f64(wl.xyz).reshape(-1, 1, 3) - targets[None], axis=2)
+    cap = max(1, int((d < wl.r_c + wl.r_nb).any(axis=1).sum()) * wl.n_rad * wl.n_theta * wl.n_phi)
+    xyz = np.zeros(3 * cap); w = np.zeros(cap); ids = np.zeros(cap, dtype=np.int64)
+    lat = None if wl.lattice is None else _f64(wl.lattice).reshape(-1)
+    n = lib().orc_grid_near(wl.n_atoms, _f64(wl.xyz).reshape(-1), None if lat is None else lat.ctypes.data,
+                            wl.n_shell, wl.n_rad, wl.R, wl.n_theta, wl.n_phi, wl.r_c, wl.r_nb,
+                            PARTITIONS[wl.partition], len(targets), targets.reshape(-1), cap, xyz, w, ids)
+    if n > cap:
+        raise RuntimeError("grid_near: buffer bound exceeded")
+    return xyz[:3 * n].reshape(n, 3).copy(), w[:n].copy(), ids[:n].copy()
+
+
 # --------------------------------------------------------------------------
 # basis, pattern, matrices
 # --------------------------------------------------------------------------
@@ -258,6 +294,18 @@ class OracleBasis:
         pi = np.ascontiguousarray(pi, np.int32); pj = np.ascontiguousarray(pj, np.int32)
         outs = [np.zeros(len(pi)) for _ in range(5)]
         lib().orc_matrix_pairs(C.byref(self.s), len(w), xyz, w, v, len(pi), pi, pj, *outs)
+        return outs
+
+    def matrix_entries(self, xyz, w, v, A, B, T, i, j):
+        """V, W0, SOx, SOy, SOz at listed elements (i, j) (local function
+        indices) of blocks (A, B, T), periodic images included (Eqs. 24-25,
+        29-30 and the SS reading)."""
+        xyz = _f64(xyz).reshape(-1); w = _f64(w); v = _f64(v)
+        ia = lambda x: np.ascontiguousarray(x, np.int32).reshape(-1)
+        A, B, i, j = ia(A), ia(B), ia(i), ia(j)
+        T = np.ascontiguousarray(T, np.int32).reshape(-1, 3)
+        outs = [np.zeros(len(A)) for _ in range(5)]
+        lib().orc_matrix_entries(C.byref(self.s), len(w), xyz, w, v, len(A), A, B, T.reshape(-1), i, j, *outs)
         return outs
 
     def matrix_blocks(self, xyz, w, v, pat: Pattern):

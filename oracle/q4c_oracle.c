@@ -512,6 +512,7 @@ long orc_grid_cell(int n_atoms, const double* xyz, const double* lattice, int n_
   int side = orc_cell_side(lattice, n_shell);
   int nc = orc_centres(n_atoms, xyz, lattice, n_shell, &cen);
   int cell0 = (side * side * side - 1) / 2; /* T = (0, 0, 0) */
+  double* nbr = (double*)malloc(sizeof(double) * 3 * (size_t)nc);
   long kept = 0;
   for (int A = 0; A < n_atoms; ++A) {
     for (int i = 0; i < n_rad; ++i) {
@@ -529,8 +530,19 @@ long orc_grid_cell(int n_atoms, const double* xyz, const double* lattice, int n_
             if (sqrt(dx * dx + dy * dy + dz * dz) < r_c) near = 1;
           }
           if (!near) continue;
-          double w = wr[i] * wt[a] * (2.0 * M_PI / n_phi) *
-                     orc_partition_weight(nc, cen, cell0 * n_atoms + A, p, r_nb, scheme);
+          /* the weight depends only on the centres within r_nb of p, in
+           * ascending order: it is taken over exactly that list */
+          int nn = 0, own_n = -1;
+          for (int B = 0; B < nc; ++B) {
+            double dx = p[0] - cen[3 * B], dy = p[1] - cen[3 * B + 1], dz = p[2] - cen[3 * B + 2];
+            if (sqrt(dx * dx + dy * dy + dz * dz) < r_nb) {
+              if (B == cell0 * n_atoms + A) own_n = nn;
+              for (int d = 0; d < 3; ++d) nbr[3 * nn + d] = cen[3 * B + d];
+              ++nn;
+            }
+          }
+          if (own_n < 0) continue; /* the owner is not a neighbour: weight 0 */
+          double w = wr[i] * wt[a] * (2.0 * M_PI / n_phi) * orc_partition_weight(nn, nbr, own_n, p, r_nb, scheme);
           if (w == 0.0) continue;
           out_xyz[3 * kept] = p[0]; out_xyz[3 * kept + 1] = p[1]; out_xyz[3 * kept + 2] = p[2];
           out_w[kept] = w;
@@ -540,7 +552,100 @@ long orc_grid_cell(int n_atoms, const double* xyz, const double* lattice, int n_
       }
     }
   }
-  free(rr); free(wr); free(ct); free(wt); free(cen);
+  free(rr); free(wr); free(ct); free(wt); free(cen); free(nbr);
+  return kept;
+}
+
+/* The kept points of orc_grid_cell (stride 1) that lie within r_c of at
+ * least one of n_t target positions, with the same weights and raw ids, in
+ * raw id order.  They are found on two restricted sets, both exact: a kept
+ * point lies within r_nb of its generating atom (the partition weight is 0
+ * otherwise), so only atoms within r_c + r_nb of a target generate one; and
+ * every centre within r_nb of such a point lies within r_c + r_nb of that
+ * target.  The partition weight depends only on the centres within r_nb of
+ * the point, in ascending order, so it is taken over exactly that list
+ * (the same neighbour set in the same order as over the full list).
+ * Returns the number of points (at most max_out are written), or -1 if a
+ * target is farther than r_c from every centre (it would keep nothing). */
+long orc_grid_near(int n_atoms, const double* xyz, const double* lattice, int n_shell, int n_rad, double R,
+                   int n_theta, int n_phi, double r_c, double r_nb, int scheme, int n_t, const double* targets,
+                   long max_out, double* out_xyz, double* out_w, long long* out_id) {
+  double* rr = (double*)malloc(sizeof(double) * n_rad);
+  double* wr = (double*)malloc(sizeof(double) * n_rad);
+  double* ct = (double*)malloc(sizeof(double) * n_theta);
+  double* wt = (double*)malloc(sizeof(double) * n_theta);
+  orc_radial_shells(n_rad, R, rr, wr);
+  orc_gauss_legendre(n_theta, ct, wt);
+  double* cen = NULL;
+  int side = orc_cell_side(lattice, n_shell);
+  int nc = orc_centres(n_atoms, xyz, lattice, n_shell, &cen);
+  int cell0 = (side * side * side - 1) / 2;
+  /* centres within r_c + r_nb of some target, ascending */
+  double* sub = (double*)malloc(sizeof(double) * 3 * (size_t)nc);
+  int* sub_id = (int*)malloc(sizeof(int) * nc);
+  int ns = 0;
+  for (int c = 0; c < nc; ++c) {
+    for (int t = 0; t < n_t; ++t) {
+      double dx = cen[3 * c] - targets[3 * t], dy = cen[3 * c + 1] - targets[3 * t + 1],
+             dz = cen[3 * c + 2] - targets[3 * t + 2];
+      if (sqrt(dx * dx + dy * dy + dz * dz) < r_c + r_nb) {
+        for (int d = 0; d < 3; ++d) sub[3 * ns + d] = cen[3 * c + d];
+        sub_id[ns++] = c;
+        break;
+      }
+    }
+  }
+  double* nbr = (double*)malloc(sizeof(double) * 3 * (size_t)(ns > 0 ? ns : 1));
+  long kept = 0;
+  for (int A = 0; A < n_atoms; ++A) {
+    int own = -1; /* the generating atom (cell 0) in the restricted list */
+    for (int k = 0; k < ns; ++k)
+      if (sub_id[k] == cell0 * n_atoms + A) own = k;
+    if (own < 0) continue; /* farther than r_c + r_nb from every target */
+    for (int i = 0; i < n_rad; ++i) {
+      for (int a = 0; a < n_theta; ++a) {
+        double st = sqrt(1.0 - ct[a] * ct[a]);
+        for (int bb = 0; bb < n_phi; ++bb) {
+          long long id = (((long long)A * n_rad + i) * n_theta + a) * n_phi + bb;
+          double ph = (bb + 0.5) * 2.0 * M_PI / n_phi;
+          double p[3] = {xyz[3 * A] + rr[i] * st * cos(ph), xyz[3 * A + 1] + rr[i] * st * sin(ph),
+                         xyz[3 * A + 2] + rr[i] * ct[a]};
+          int close = 0;
+          for (int t = 0; t < n_t && !close; ++t) {
+            double dx = p[0] - targets[3 * t], dy = p[1] - targets[3 * t + 1], dz = p[2] - targets[3 * t + 2];
+            if (sqrt(dx * dx + dy * dy + dz * dz) < r_c) close = 1;
+          }
+          if (!close) continue;
+          int near = 0;
+          for (int B = 0; B < ns && !near; ++B) {
+            double dx = p[0] - sub[3 * B], dy = p[1] - sub[3 * B + 1], dz = p[2] - sub[3 * B + 2];
+            if (sqrt(dx * dx + dy * dy + dz * dz) < r_c) near = 1;
+          }
+          if (!near) continue;
+          /* the centres within r_nb of p, ascending, and the owner among them */
+          int nn = 0, own_n = -1;
+          for (int B = 0; B < ns; ++B) {
+            double dx = p[0] - sub[3 * B], dy = p[1] - sub[3 * B + 1], dz = p[2] - sub[3 * B + 2];
+            if (sqrt(dx * dx + dy * dy + dz * dz) < r_nb) {
+              if (B == own) own_n = nn;
+              for (int d = 0; d < 3; ++d) nbr[3 * nn + d] = sub[3 * B + d];
+              ++nn;
+            }
+          }
+          if (own_n < 0) continue; /* the owner is not a neighbour: weight 0 */
+          double w = wr[i] * wt[a] * (2.0 * M_PI / n_phi) * orc_partition_weight(nn, nbr, own_n, p, r_nb, scheme);
+          if (w == 0.0) continue;
+          if (kept < max_out) {
+            out_xyz[3 * kept] = p[0]; out_xyz[3 * kept + 1] = p[1]; out_xyz[3 * kept + 2] = p[2];
+            out_w[kept] = w;
+            out_id[kept] = id;
+          }
+          ++kept;
+        }
+      }
+    }
+  }
+  free(rr); free(wr); free(ct); free(wt); free(cen); free(sub); free(sub_id); free(nbr);
   return kept;
 }
 
@@ -668,6 +773,84 @@ void orc_matrix_pairs(const orc_basis* b, long n_pts, const double* xyz, const d
     SOz[q] = acc_get(&acc[5 * q + 4]);
   }
   free(used); free(list); free(phi); free(grad); free(acc);
+  ftab_free(&t);
+}
+
+/* Listed elements of the block matrices, periodic images included: element
+ * q is (i, j) of block (A, B, T) (i, j local function indices of atoms A
+ * and B, T = ET[3q..3q+2]), the sum over the points and over the cells T_a
+ * of the centre set with T_a + T in it of w v times the integrand of
+ * phi_i centred at R_A + T_a L and phi_j at R_B + (T_a + T) L (the restricted
+ * real-space sum of Eqs. 24-25 with Eqs. 29-30 and the SS reading: what
+ * orc_matrix_blocks accumulates into that element). */
+void orc_matrix_entries(const orc_basis* b, long n_pts, const double* xyz, const double* w, const double* v,
+                        long n_e, const int* EA, const int* EB, const int* ET, const int* Ei, const int* Ej,
+                        double* V, double* W0, double* SOx, double* SOy, double* SOz) {
+  ftab t;
+  ftab_init(b, &t);
+  int side = orc_cell_side(b->lattice, b->n_shell), s = side / 2, ncell = side * side * side;
+  orc_acc* acc = (orc_acc*)calloc(5 * (size_t)n_e, sizeof(orc_acc));
+  /* per point, the cells T_a with R_A + T_a L within r_c of it, for each
+   * atom A that heads an element (phi_i vanishes at the other cells) */
+  int* close = (int*)malloc(sizeof(int) * (size_t)b->n_atoms * ncell);
+  int* nclose = (int*)calloc(b->n_atoms, sizeof(int));
+  int* is_row = (int*)calloc(b->n_atoms, sizeof(int));
+  for (long q = 0; q < n_e; ++q) is_row[EA[q]] = 1;
+  for (long p = 0; p < n_pts; ++p) {
+    const double* P = xyz + 3 * p;
+    double wv = w[p] * v[p];
+    for (int A = 0; A < b->n_atoms; ++A) {
+      if (!is_row[A]) continue;
+      nclose[A] = 0;
+      for (int cell = 0; cell < ncell; ++cell) {
+        int Ta[3];
+        double sa[3];
+        orc_cell_T(side, cell, Ta);
+        orc_shift(b->lattice, Ta, sa);
+        double dx = P[0] - (b->xyz[3 * A] + sa[0]), dy = P[1] - (b->xyz[3 * A + 1] + sa[1]),
+               dz = P[2] - (b->xyz[3 * A + 2] + sa[2]);
+        if (sqrt(dx * dx + dy * dy + dz * dz) < b->r_c) close[(size_t)A * ncell + nclose[A]++] = cell;
+      }
+    }
+    for (long q = 0; q < n_e; ++q) {
+      int A = EA[q], B = EB[q];
+      int i = t.afirst[A] + Ei[q], j = t.afirst[B] + Ej[q];
+      for (int k = 0; k < nclose[A]; ++k) {
+        const int cell = close[(size_t)A * ncell + k];
+        int Ta[3], Tb[3];
+        orc_cell_T(side, cell, Ta);
+        int inside = 1;
+        for (int k = 0; k < 3; ++k) {
+          Tb[k] = Ta[k] + ET[3 * q + k];
+          if (Tb[k] < -s || Tb[k] > s) inside = 0;
+        }
+        if (!inside) continue;
+        double sa[3], sb[3], ca[3], cb[3];
+        orc_shift(b->lattice, Ta, sa);
+        orc_shift(b->lattice, Tb, sb);
+        for (int d = 0; d < 3; ++d) {
+          ca[d] = b->xyz[3 * A + d] + sa[d];
+          cb[d] = b->xyz[3 * B + d] + sb[d];
+        }
+        double pi, pj, gi[3], gj[3];
+        phi_at(b, t.fr[i], t.fl[i], t.fm[i], ca, P, &pi, gi);
+        phi_at(b, t.fr[j], t.fl[j], t.fm[j], cb, P, &pj, gj);
+        acc_add(&acc[5 * q + 0], wv * (pi * pj));
+        acc_add(&acc[5 * q + 1], wv * (gi[0] * gj[0] + gi[1] * gj[1] + gi[2] * gj[2]));
+        acc_add(&acc[5 * q + 2], wv * (gi[1] * gj[2] - gi[2] * gj[1]));
+        acc_add(&acc[5 * q + 3], wv * (gi[2] * gj[0] - gi[0] * gj[2]));
+        acc_add(&acc[5 * q + 4], wv * (gi[0] * gj[1] - gi[1] * gj[0]));
+      }
+    }
+  }
+  for (long q = 0; q < n_e; ++q) {
+    V[q] = acc_get(&acc[5 * q + 0]);
+    W0[q] = acc_get(&acc[5 * q + 1]);
+    SOx[q] = acc_get(&acc[5 * q + 2]);
+    SOy[q] = acc_get(&acc[5 * q + 3]);
+    SOz[q] = acc_get(&acc[5 * q + 4]);
+  }
+  free(acc); free(close); free(nclose); free(is_row);
   ftab_free(&t);
 }
 

@@ -146,7 +146,7 @@ extern "C" q4c_status q4c_grid_tiling(const q4c_grid* g, int32_t bucket, int32_t
   Q4C_CHECK_ARG(g, "q4c_grid_tiling: NULL grid");
   Q4C_CHECK_ARG(bucket >= 0 && bucket <= kTileBuckets, "q4c_grid_tiling: bucket out of range");
   if (bucket == kTileBuckets) {  // the density/adjoint kernel (one shape per grid)
-    if (nb_max) *nb_max = 512;
+    if (nb_max) *nb_max = 4096;
     if (k_steps) *k_steps = g->rd_ks;
     if (batches) *batches = g->n_batches;
     if (ms_one) *ms_one = g->rd_tune_ms[0];

@@ -413,8 +413,9 @@ q4c_status integrate_columns_fp64(const q4c_tables* t, const q4c_grid* g, const 
 
 // ------------------------------------------------------------- density
 // One CTA per batch, one thread per point; P rows gathered into shared
-// memory kRows at a time: n_p = sum_i Phi_pi sum_j P_ij Phi_pj.
-constexpr int kRows = 16;
+// memory kRows at a time: n_p = sum_i Phi_pi sum_j P_ij Phi_pj.  kRows is 16,
+// or fewer where 16 rows of a large batch would not fit in shared memory.
+template <int kRows>
 __global__ void k_density_fp64(DevBasis B, DevGrid G, int64_t b0, const int64_t* __restrict__ scr_off,
                                const double* __restrict__ scratch, const double* __restrict__ P,
                                double* __restrict__ n_out) {
@@ -465,11 +466,18 @@ __global__ void k_density_fp64(DevBasis B, DevGrid G, int64_t b0, const int64_t*
 q4c_status density_fp64_wave(const q4c_grid* g, int wv, const double* P, double* n, cudaStream_t s) {
   const int64_t b0 = g->wave_b0[wv], b1 = g->wave_b0[wv + 1];
   if (b1 <= b0) return Q4C_OK;
-  const size_t smem = sizeof(double) * kRows * std::max(g->max_nb, 1);
-  Q4C_CUDA(cudaFuncSetAttribute(k_density_fp64, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                static_cast<int>(smem)));
+  constexpr size_t kSmemMax = 232448;
+  const size_t row = sizeof(double) * std::max(g->max_nb, 1);  // one P row of a batch
+  const int rows = 16 * row <= kSmemMax ? 16 : 8 * row <= kSmemMax ? 8 : 4;
+  if (rows * row > kSmemMax) {
+    set_error("the FP64 density needs at most 7264 active functions per batch");
+    return Q4C_EUNSUPPORTED;
+  }
+  const size_t smem = rows * row;
+  auto k_density = rows == 16 ? k_density_fp64<16> : rows == 8 ? k_density_fp64<8> : k_density_fp64<4>;
+  Q4C_CUDA(cudaFuncSetAttribute(k_density, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
   KernelScope ks("density_fp64", s);
-  k_density_fp64<<<static_cast<unsigned>(b1 - b0), 128, smem, s>>>(g->tables->view(), g->view(), b0, g->d_scr_off,
+  k_density<<<static_cast<unsigned>(b1 - b0), 128, smem, s>>>(g->tables->view(), g->view(), b0, g->d_scr_off,
                                                                    g->d_scratch, P, n);
   Q4C_CUDA(cudaGetLastError());
   return Q4C_OK;
@@ -489,7 +497,9 @@ q4c_status density_fp64(const q4c_tables* t, const q4c_grid* g, const double* P,
 // dL/dv_p = w_p sum_ij [G^V phi_i phi_j + G^W grad_i.grad_j
 //                        + G^x (Y_i Z_j - Z_i Y_j) + G^y (Z_i X_j - X_i Z_j)
 //                        + G^z (X_i Y_j - Y_i X_j)]
-constexpr int kRowsB = 8;
+// kRowsB rows of G per pass: 8, or 4, 2 or 1 where five 8-row blocks of a
+// large batch would not fit in shared memory
+template <int kRowsB>
 __global__ void k_backward_fp64(DevBasis B, DevGrid G, int64_t b0, const int64_t* __restrict__ scr_off,
                                 const double* __restrict__ scratch, const double* GV, const double* GW,
                                 const double* Gx, const double* Gy, const double* Gz, double* __restrict__ dLdv,
@@ -557,14 +567,21 @@ q4c_status backward_fp64_wave(const q4c_grid* g, int wv, const q4c_matrices* Gm,
                               cudaStream_t s) {
   const int64_t b0 = g->wave_b0[wv], b1 = g->wave_b0[wv + 1];
   if (b1 <= b0) return Q4C_OK;
-  const size_t smem = sizeof(double) * 5 * kRowsB * std::max(g->max_nb, 1);
-  Q4C_CUDA(cudaFuncSetAttribute(k_backward_fp64, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                static_cast<int>(smem)));
+  constexpr size_t kSmemMax = 232448;
+  const size_t row = sizeof(double) * 5 * std::max(g->max_nb, 1);  // five G rows of a batch
+  if (row > kSmemMax) {
+    set_error("the FP64 adjoint needs at most 5811 active functions per batch");
+    return Q4C_EUNSUPPORTED;
+  }
+  const int rows = 8 * row <= kSmemMax ? 8 : 4 * row <= kSmemMax ? 4 : 2 * row <= kSmemMax ? 2 : 1;
+  const size_t smem = rows * row;
+  auto kern = rows == 8 ? k_backward_fp64<8> : rows == 4 ? k_backward_fp64<4> : rows == 2 ? k_backward_fp64<2>
+                                                                                        : k_backward_fp64<1>;
+  Q4C_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
   KernelScope ks("backward_fp64", s);
-  k_backward_fp64<<<static_cast<unsigned>(b1 - b0), 128, smem, s>>>(g->tables->view(), g->view(), b0,
-                                                                    g->d_scr_off, g->d_scratch, Gm->V, Gm->W0,
-                                                                    Gm->SOx, Gm->SOy, Gm->SOz, dLdv,
-                                                                    weighted ? 1 : 0);
+  kern<<<static_cast<unsigned>(b1 - b0), 128, smem, s>>>(g->tables->view(), g->view(), b0, g->d_scr_off,
+                                                         g->d_scratch, Gm->V, Gm->W0, Gm->SOx, Gm->SOy, Gm->SOz,
+                                                         dLdv, weighted ? 1 : 0);
   Q4C_CUDA(cudaGetLastError());
   return Q4C_OK;
 }

@@ -30,8 +30,8 @@ q4c_status scf_pass(const q4c_tables* t, const q4c_grid* g, const double* v, con
       set_error("q4c_scf_pass: the split path needs batches of at most 341 points");
       return Q4C_EUNSUPPORTED;
     }
-    if ((do_n || do_g) && g->max_nb > 512) {
-      set_error("q4c_scf_pass: the split density/adjoint need at most 512 active functions per batch");
+    if ((do_n || do_g) && g->max_nb > 4096) {
+      set_error("q4c_scf_pass: the split density/adjoint need at most 4096 active functions per batch");
       return Q4C_EUNSUPPORTED;
     }
   }

@@ -10,6 +10,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <memory>
 #include <numeric>
 #include <thread>
 
@@ -21,6 +22,65 @@
 namespace q4c {
 
 constexpr int kMaxNeighbours = 512;
+
+// Centres binned into cubes of side `size` from the corner `lo` (n[3] bins a
+// side), CSR over bins in (z, y, x) order, centres ascending within a bin:
+// every centre within `size` of a point lies in the 27 bins around the
+// point's bin.  ptr == NULL: no bins (each point scans its candidate range).
+struct CellList {
+  const int* ptr;
+  const int* idx;
+  double lo[3];
+  double size;
+  int n[3];
+};
+
+struct HostCellList {
+  std::vector<int> ptr, idx;
+  double lo[3] = {0, 0, 0};
+  double size = 1;
+  int n[3] = {1, 1, 1};
+  HostCellList(const double* xyz, int count, double side) : size(side) {
+    double hi[3] = {-1e300, -1e300, -1e300};
+    for (int d = 0; d < 3; ++d) lo[d] = 1e300;
+    for (int c = 0; c < count; ++c)
+      for (int d = 0; d < 3; ++d) {
+        lo[d] = std::min(lo[d], xyz[3 * c + d]);
+        hi[d] = std::max(hi[d], xyz[3 * c + d]);
+      }
+    for (int d = 0; d < 3; ++d) n[d] = std::max(1, static_cast<int>(std::floor((hi[d] - lo[d]) / size)) + 1);
+    std::vector<int> bin(count);
+    ptr.assign(static_cast<size_t>(n[0]) * n[1] * n[2] + 1, 0);
+    for (int c = 0; c < count; ++c) {
+      int k[3];
+      for (int d = 0; d < 3; ++d) k[d] = std::min(n[d] - 1, static_cast<int>(std::floor((xyz[3 * c + d] - lo[d]) / size)));
+      bin[c] = (k[2] * n[1] + k[1]) * n[0] + k[0];
+      ++ptr[bin[c] + 1];
+    }
+    for (size_t b = 0; b + 1 < ptr.size(); ++b) ptr[b + 1] += ptr[b];
+    idx.resize(count);
+    std::vector<int> fill(ptr.begin(), ptr.end() - 1);
+    for (int c = 0; c < count; ++c) idx[fill[bin[c]]++] = c;  // ascending within a bin
+  }
+  // centres within distance `reach` of the box [a, b] (a superset: whole bins), ascending
+  void near_box(const double a[3], const double b[3], double reach, std::vector<int>& out) const {
+    out.clear();
+    int k0[3], k1[3];
+    for (int d = 0; d < 3; ++d) {
+      k0[d] = static_cast<int>(std::max(-1.0, std::floor((a[d] - reach - lo[d]) / size)));
+      k1[d] = static_cast<int>(std::min(static_cast<double>(n[d]), std::floor((b[d] + reach - lo[d]) / size)));
+      k0[d] = std::max(k0[d], 0);
+      k1[d] = std::min(k1[d], n[d] - 1);
+    }
+    for (int z = k0[2]; z <= k1[2]; ++z)
+      for (int y = k0[1]; y <= k1[1]; ++y)
+        for (int x = k0[0]; x <= k1[0]; ++x) {
+          const int bb = (z * n[1] + y) * n[0] + x;
+          out.insert(out.end(), idx.begin() + ptr[bb], idx.begin() + ptr[bb + 1]);
+        }
+    std::sort(out.begin(), out.end());
+  }
+};
 
 // Gauss-Legendre nodes (ascending) and weights by Newton's method on P_n,
 // with P_n' from (1 - x^2) P_n' = n (P_{n-1} - x P_n).
@@ -81,7 +141,7 @@ __device__ __forceinline__ double stratmann_s(double mu) {
 // mu_AB = (|r - R_A| - |r - R_B|)/|R_A - R_B|.  near = some atom within r_c.
 __global__ void k_becke(const double* __restrict__ raw, const double* __restrict__ base_w, int64_t n_raw,
                         int pts_per_atom, int owner_base, const double* __restrict__ atom_xyz,
-                        const int2* __restrict__ cand, double r_c, double r_nb, int scheme,
+                        const int2* __restrict__ cand, CellList bins, double r_c, double r_nb, int scheme,
                         double* __restrict__ w_out, unsigned char* __restrict__ near_out,
                         int* __restrict__ overflow) {
   const int64_t p = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
@@ -95,15 +155,14 @@ __global__ void k_becke(const double* __restrict__ raw, const double* __restrict
   double nb_d[kMaxNeighbours];
   int nn = 0, own_slot = -1;
   bool near = false;
-  for (int B = range.x; B < range.y; ++B) {
+  bool full = false;  // more than kMaxNeighbours centres within r_nb
+  auto consider = [&](int B) {
     const double dx = px - atom_xyz[3 * B], dy = py - atom_xyz[3 * B + 1], dz = pz - atom_xyz[3 * B + 2];
     const double d = centre_distance(dx, dy, dz);
     if (d < r_c) near = true;
     if (d < r_nb) {
       if (nn == kMaxNeighbours) {
-        atomicExch(overflow, 1);
-        w_out[p] = 0.0;
-        near_out[p] = 0;
+        full = true;
         return;
       }
       if (B == owner) own_slot = nn;
@@ -111,6 +170,29 @@ __global__ void k_becke(const double* __restrict__ raw, const double* __restrict
       nb_d[nn] = d;
       ++nn;
     }
+  };
+  if (bins.ptr) {  // the 27 bins around the point (bins are at least max(r_c, r_nb) wide)
+    const double pc[3] = {px, py, pz};
+    int k0[3], k1[3];
+    for (int d = 0; d < 3; ++d) {
+      const double k = fmin(fmax(floor((pc[d] - bins.lo[d]) / bins.size), -2.0), bins.n[d] + 1.0);
+      k0[d] = max(static_cast<int>(k) - 1, 0);
+      k1[d] = min(static_cast<int>(k) + 1, bins.n[d] - 1);
+    }
+    for (int z = k0[2]; z <= k1[2] && !full; ++z)
+      for (int y = k0[1]; y <= k1[1] && !full; ++y)
+        for (int x = k0[0]; x <= k1[0] && !full; ++x) {
+          const int bb = (z * bins.n[1] + y) * bins.n[0] + x;
+          for (int q = bins.ptr[bb]; q < bins.ptr[bb + 1] && !full; ++q) consider(bins.idx[q]);
+        }
+  } else {
+    for (int B = range.x; B < range.y && !full; ++B) consider(B);
+  }
+  if (full) {
+    atomicExch(overflow, 1);
+    w_out[p] = 0.0;
+    near_out[p] = 0;
+    return;
   }
   near_out[p] = near ? 1 : 0;
   if (!near || own_slot < 0) {
@@ -180,7 +262,7 @@ static q4c_status up(T** dst, const std::vector<T>& src) {
 template <typename F>
 static void parallel_for(int64_t n, F&& f) {
   unsigned nt = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
-  if (n < 4096) nt = 1;
+  if (n < 64) nt = 1;
   std::vector<std::thread> th;
   for (unsigned t = 0; t < nt; ++t)
     th.emplace_back([&, t] {
@@ -402,6 +484,12 @@ extern "C" q4c_status grid_partition(const q4c_grid_desc* d, const q4c_tables* t
       }
   });
 
+  // ---- centre bins of a single system (one molecule or a periodic cell):
+  // cubes at least max(r_c, r_nb) wide, so that a point finds its neighbours
+  // in the 27 bins around it; batched molecules scan their own atoms instead
+  std::unique_ptr<HostCellList> bins;
+  if (n_mol == 1) bins.reset(new HostCellList(g->h_c_xyz.data(), nC, std::max(r_c, d->r_nb)));
+
   // ---- Becke weights on the device
   std::vector<double> wfull(n_raw);
   std::vector<unsigned char> nearv(n_raw);
@@ -410,10 +498,12 @@ extern "C" q4c_status grid_partition(const q4c_grid_desc* d, const q4c_tables* t
     unsigned char* d_near = nullptr;
     int* d_ovf = nullptr;
     int2* d_cand = nullptr;
+    int *d_bptr = nullptr, *d_bidx = nullptr;
     auto cleanup = [&] {
       cudaFree(d_raw); cudaFree(d_base); cudaFree(d_w); cudaFree(d_axyz); cudaFree(d_near); cudaFree(d_ovf);
-      cudaFree(d_cand);
+      cudaFree(d_cand); cudaFree(d_bptr); cudaFree(d_bidx);
     };
+    CellList cl{};
     cudaError_t e = cudaSuccess;
     int ovf = 0;
     do {
@@ -429,9 +519,22 @@ extern "C" q4c_status grid_partition(const q4c_grid_desc* d, const q4c_tables* t
       if ((e = cudaMemcpy(d_raw, raw.data(), sizeof(double) * 3 * n_raw, cudaMemcpyHostToDevice))) break;
       if ((e = cudaMemcpy(d_base, base.data(), sizeof(double) * n_raw, cudaMemcpyHostToDevice))) break;
       if ((e = cudaMemcpy(d_axyz, g->h_c_xyz.data(), sizeof(double) * 3 * nC, cudaMemcpyHostToDevice))) break;
+      if (bins) {
+        if ((e = cudaMalloc(&d_bptr, sizeof(int) * bins->ptr.size()))) break;
+        if ((e = cudaMalloc(&d_bidx, sizeof(int) * bins->idx.size()))) break;
+        if ((e = cudaMemcpy(d_bptr, bins->ptr.data(), sizeof(int) * bins->ptr.size(), cudaMemcpyHostToDevice))) break;
+        if ((e = cudaMemcpy(d_bidx, bins->idx.data(), sizeof(int) * bins->idx.size(), cudaMemcpyHostToDevice))) break;
+        cl.ptr = d_bptr;
+        cl.idx = d_bidx;
+        cl.size = bins->size;
+        for (int k = 0; k < 3; ++k) {
+          cl.lo[k] = bins->lo[k];
+          cl.n[k] = bins->n[k];
+        }
+      }
       const int threads = 128;
       const int64_t blocks = (n_raw + threads - 1) / threads;
-      k_becke<<<static_cast<unsigned>(blocks), threads>>>(d_raw, d_base, n_raw, ppa, cell0 * nA, d_axyz, d_cand,
+      k_becke<<<static_cast<unsigned>(blocks), threads>>>(d_raw, d_base, n_raw, ppa, cell0 * nA, d_axyz, d_cand, cl,
                                                           r_c, d->r_nb, d->partition, d_w, d_near, d_ovf);
       if ((e = cudaGetLastError())) break;
       if ((e = cudaMemcpy(wfull.data(), d_w, sizeof(double) * n_raw, cudaMemcpyDeviceToHost))) break;
@@ -578,8 +681,21 @@ extern "C" q4c_status grid_partition(const q4c_grid_desc* d, const q4c_tables* t
       rad = std::max(rad, std::sqrt(s));
     }
     const double* cx = g->h_c_xyz.data();
-    const int2 range = cand[g->h_pid[p0] / ppa];  // the batch's molecule
-    for (int A = range.x; A < range.y; ++A) {
+    // candidates: the batch's molecule, or the binned centres near the batch's box
+    std::vector<int> near;
+    if (bins) {
+      double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+      for (int64_t i = p0; i < p1; ++i)
+        for (int k = 0; k < 3; ++k) {
+          lo[k] = std::min(lo[k], g->h_xyz[3 * i + k]);
+          hi[k] = std::max(hi[k], g->h_xyz[3 * i + k]);
+        }
+      bins->near_box(lo, hi, r_c, near);
+    } else {
+      const int2 range = cand[g->h_pid[p0] / ppa];  // the batch's molecule
+      for (int A = range.x; A < range.y; ++A) near.push_back(A);
+    }
+    for (int A : near) {
       double s = 0;
       for (int k = 0; k < 3; ++k) s += (cx[3 * A + k] - c[k]) * (cx[3 * A + k] - c[k]);
       if (std::sqrt(s) >= rad + r_c + 1e-9) continue;
@@ -600,26 +716,39 @@ extern "C" q4c_status grid_partition(const q4c_grid_desc* d, const q4c_tables* t
   std::vector<int> blk_row;
   int64_t off = 0;
   const int s2 = 2 * g->n_shell, side2 = 2 * s2 + 1;
-  for (int A = 0; A < nA; ++A) {
-    for (int B = mol_ptr[atom_mol[A]]; B < mol_ptr[atom_mol[A] + 1]; ++B) {
-      for (int cell = 0; cell < side2 * side2 * side2; ++cell) {
-        const int T[3] = {cell / (side2 * side2) - s2, (cell / side2) % side2 - s2, cell % side2 - s2};
-        double sh[3] = {0, 0, 0};
-        if (periodic)
-          for (int k = 0; k < 3; ++k)
-            for (int dd = 0; dd < 3; ++dd) sh[dd] += T[k] * d->lattice[3 * k + dd];
-        const double dx = d->xyz[3 * A] - d->xyz[3 * B] - sh[0], dy = d->xyz[3 * A + 1] - d->xyz[3 * B + 1] - sh[1],
-                     dz = d->xyz[3 * A + 2] - d->xyz[3 * B + 2] - sh[2];
-        if (std::sqrt(dx * dx + dy * dy + dz * dz) < 2.0 * r_c) {
-          g->h_blk_col.push_back(B);
-          g->h_blk_shift.insert(g->h_blk_shift.end(), {T[0], T[1], T[2]});
-          blk_row.push_back(A);
-          g->h_blk_off.push_back(off);
-          off += static_cast<int64_t>(g->h_nf_atom[A]) * g->h_nf_atom[B];
+  {
+    // each row on its own (rows in parallel), then concatenated in row order
+    std::vector<std::vector<int>> rowB(nA), rowT(nA);
+    parallel_for(nA, [&](int64_t A) {
+      for (int B = mol_ptr[atom_mol[A]]; B < mol_ptr[atom_mol[A] + 1]; ++B) {
+        for (int cell = 0; cell < side2 * side2 * side2; ++cell) {
+          const int T[3] = {cell / (side2 * side2) - s2, (cell / side2) % side2 - s2, cell % side2 - s2};
+          double sh[3] = {0, 0, 0};
+          if (periodic)
+            for (int k = 0; k < 3; ++k)
+              for (int dd = 0; dd < 3; ++dd) sh[dd] += T[k] * d->lattice[3 * k + dd];
+          const double dx = d->xyz[3 * A] - d->xyz[3 * B] - sh[0], dy = d->xyz[3 * A + 1] - d->xyz[3 * B + 1] - sh[1],
+                       dz = d->xyz[3 * A + 2] - d->xyz[3 * B + 2] - sh[2];
+          if (std::sqrt(dx * dx + dy * dy + dz * dz) < 2.0 * r_c) {
+            rowB[A].push_back(B);
+            rowT[A].insert(rowT[A].end(), {T[0], T[1], T[2]});
+          }
         }
       }
+    });
+    for (int A = 0; A < nA; ++A) {
+      for (size_t k = 0; k < rowB[A].size(); ++k) {
+        const int B = rowB[A][k];
+        g->h_blk_col.push_back(B);
+        g->h_blk_shift.insert(g->h_blk_shift.end(), rowT[A].begin() + 3 * k, rowT[A].begin() + 3 * k + 3);
+        blk_row.push_back(A);
+        g->h_blk_off.push_back(off);
+        off += static_cast<int64_t>(g->h_nf_atom[A]) * g->h_nf_atom[B];
+      }
+      g->h_blk_ptr[A + 1] = static_cast<int64_t>(g->h_blk_col.size());
+      std::vector<int>().swap(rowB[A]);
+      std::vector<int>().swap(rowT[A]);
     }
-    g->h_blk_ptr[A + 1] = static_cast<int64_t>(g->h_blk_col.size());
   }
   g->h_blk_off.push_back(off);
   g->n_blocks = static_cast<int64_t>(g->h_blk_col.size());

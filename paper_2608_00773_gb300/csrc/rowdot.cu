@@ -13,7 +13,11 @@
 // Each U is computed from six BF16 slices of F (per-point exponents) and of
 // G' (per-column exponents) with the same tile sequence and exact-level
 // accumulation as the integration (see split.cu): levels 0-2 are exact
-// integer sums (K = n_b <= 512), levels 3-5 are rounded 2^-24 below.
+// integer sums for K <= 512 terms, levels 3-5 are rounded 2^-24 below.  A
+// batch of more than 512 functions splits K into segments of at most 512
+// (32 chunks of 16), each a group of its own: its level sums are exact, and
+// the epilogue adds its row-dot into the point's running sum like any other
+// group's (the dot with R is linear in U).
 //
 // G' does not depend on the points, so a pre-pass slices every batch's G'
 // once into BF16 digit tiles laid out exactly as the MMA reads them (per
@@ -70,7 +74,8 @@ struct Layout {
 static_assert(Layout<1>::kRawStage == 9 * 1024 && Layout<1>::kStage == 26624, "the one-step layout");
 constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kSetCols = 256;
-constexpr int kMaxNb = 512;
+constexpr int kMaxNb = 4096;
+constexpr int kSegIc = 32;  // chunks of 16 functions per exact K segment (K <= 512)
 
 struct Product {
   int qf, gm, qr;
@@ -194,14 +199,19 @@ __global__ void __launch_bounds__(256) k_gslice(DevGrid G, int64_t b0, int anti_
   }
 }
 
-// the work of one item (batch, 64-point tile): groups (j-tile, product) in
-// order, each a K-loop over the functions i in chunks of 16 (n_ic chunks,
-// KS chunks per pipeline stage)
+// the work of one item (batch, 64-point tile): groups (j-tile, product, K
+// segment) in order, each a K-loop over the segment's functions i in chunks
+// of 16 (n_ic chunks in all, KS chunks per pipeline stage)
 struct ItemInfo {
   int64_t b, bp0;
-  int pt, np, ldp, nb, n_jt, n_ic;
+  int pt, np, ldp, nb, n_jt, n_ic, n_seg, n_stot;
   int64_t plane;
 };
+
+// pipeline stages of K segment seg
+__device__ __forceinline__ int seg_stages(int n_ic, int seg, int ks) {
+  return (min(kSegIc, n_ic - seg * kSegIc) + ks - 1) / ks;
+}
 
 __device__ __forceinline__ ItemInfo item_info(const DevGrid& G, int2 it) {
   ItemInfo I;
@@ -213,23 +223,35 @@ __device__ __forceinline__ ItemInfo item_info(const DevGrid& G, int2 it) {
   I.nb = static_cast<int>(G.bat_fn_ptr[I.b + 1] - G.bat_fn_ptr[I.b]);
   I.n_jt = (I.nb + kTile - 1) / kTile;
   I.n_ic = (I.nb + kKc - 1) / kKc;
+  I.n_seg = (I.n_ic + kSegIc - 1) / kSegIc;
   I.plane = static_cast<int64_t>(I.nb) * I.ldp;
   return I;
 }
 
-// position in an item's stage sequence (j-tile, product, stage of the
-// K-loop), advanced without divisions
+template <int KS>
+__device__ __forceinline__ int stages_per_product(const ItemInfo& I) {  // all segments of one (j-tile, product)
+  return (I.n_seg - 1) * (kSegIc / KS) + seg_stages(I.n_ic, I.n_seg - 1, KS);
+}
+
+// position in an item's stage sequence (j-tile, product, K segment, stage
+// within the segment), advanced without divisions
+template <int KS>
 struct StepIter {
-  int ic = 0, kk = 0, jt = 0;
-  __device__ __forceinline__ void next(int n_ic, int n_prod) {
-    if (++ic == n_ic) {
-      ic = 0;
-      if (++kk == n_prod) {
-        kk = 0;
-        ++jt;
+  int st = 0, seg = 0, kk = 0, jt = 0;
+  __device__ __forceinline__ void next(const ItemInfo& I, int n_prod) {
+    if (++st == seg_stages(I.n_ic, seg, KS)) {
+      st = 0;
+      if (++seg == I.n_seg) {
+        seg = 0;
+        if (++kk == n_prod) {
+          kk = 0;
+          ++jt;
+        }
       }
     }
   }
+  // chunk of 16 functions read by K-step h of this stage
+  __device__ __forceinline__ int chunk(int h) const { return seg * kSegIc + st * KS + h; }
 };
 
 // One work item = (batch, 64-point tile); its groups (j-tile, product) run
@@ -340,10 +362,9 @@ __global__ void __launch_bounds__(kThreads, 1)
       const ItemInfo I = item_info(G, items[n]);
       const bool live = I.pt * kTile + p < I.np;
       const unsigned char* gblk = gsl + gsl_off[I.b];
-      const int n_st = (I.n_ic + KS - 1) / KS;  // stages per group
-      const int n_steps = I.n_jt * n_prod * n_st;
+      const int n_steps = I.n_jt * n_prod * stages_per_product<KS>(I);
       float m0 = 0.f, m1 = 0.f, m2 = 0.f, m3 = 0.f;  // rounding constants of the point's four quantities
-      StepIter it;
+      StepIter<KS> it;
       for (int s = 0; s < n_steps; ++s, ++g) {
         const int rs = g % kRaw, st = g % kStages;
         if (!mbar_wait_abort(rawfull_bar(rs), (g / kRaw) & 1, s_abort, status, G.wait_ns)) {
@@ -378,7 +399,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             // a K-step past the last chunk of functions (odd chunk counts,
             // KS = 2) multiplies zeros: its F box is zero-filled and its G'
             // block is the zero block
-            const int ic = it.ic * KS + h;
+            const int ic = it.chunk(h);
             const unsigned char* src =
                 ic < I.n_ic ? gblk + (static_cast<int64_t>(P.gm) * I.n_jt * I.n_ic +
                                       static_cast<int64_t>(it.jt) * I.n_ic + ic) * kBlockB
@@ -409,7 +430,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         // TMA box overwrite values that were still on their way).
         __syncwarp();
         if (lane == 0) mbar_arrive(rawempty_bar(rs));
-        it.next(n_st, n_prod);
+        it.next(I, n_prod);
       }
       // agree on stopping (a wait that gave up in one warp ends every role)
       if (bar_red_or(1, kSlicers, !ok || *s_abort)) break;
@@ -428,9 +449,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         const ItemInfo I = item_info(G, items[n]);
         const CUtensorMap* map = maps + I.b;
         const int r0 = I.pt * kTile, rows = min(kTile, I.np - r0);
-        const int n_st = (I.n_ic + KS - 1) / KS;
-        const int n_steps = I.n_jt * n_prod * n_st;
-        StepIter it;
+        const int n_steps = I.n_jt * n_prod * stages_per_product<KS>(I);
+        StepIter<KS> it;
         for (int s = 0; s < n_steps; ++s, ++g) {
           const int rs = g % kRaw;
           if (!mbar_wait_abort(rawempty_bar(rs), ((g / kRaw) & 1) ^ 1, s_abort, status, G.wait_ns, 32)) {
@@ -441,9 +461,9 @@ __global__ void __launch_bounds__(kThreads, 1)
           arrive_expect_tx(fb, KS * kRawTile + (s == 0 ? rows * 16 : 0));
 #pragma unroll
           for (int h = 0; h < KS; ++h)  // boxes past the last function read zeros
-            tma_load_3d(dst + h * kRawTile, map, r0, (it.ic * KS + h) * kKc, prod_at(it.kk).qf, fb);
+            tma_load_3d(dst + h * kRawTile, map, r0, it.chunk(h) * kKc, prod_at(it.kk).qf, fb);
           if (s == 0) bulk_copy(dst + kRawExp, rowexp + 4 * (I.bp0 + r0), rows * 16, fb);
-          it.next(n_st, n_prod);
+          it.next(I, n_prod);
         }
       }
       // no copy outlives the CTA: the last kRaw issued steps have landed
@@ -457,7 +477,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       bool ok = true;
       for (int n = blockIdx.x; n < n_items && ok; n += gridDim.x) {
         const ItemInfo I = item_info(G, items[n]);
-        for (int grp = 0; grp < I.n_jt * n_prod && ok; ++grp, ++k) {
+        int seg = 0, kk = 0, jt = 0;  // groups run (j-tile, product, segment) in order
+        for (int grp = 0; grp < I.n_jt * n_prod * I.n_seg && ok; ++grp, ++k) {
           const int set = k & 1;
           if (!mbar_wait_abort(accempty_bar(set), ((k >> 1) & 1) ^ 1, s_abort, status, G.wait_ns, 64)) {
             ok = false;
@@ -465,8 +486,15 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           tc_fence_after();
           const uint32_t t0 = tmem + set * kSetCols;
-          const int nbj = jt_width(I.nb, grp / n_prod);  // groups run (j-tile, product) in order
-          const int n_st = (I.n_ic + KS - 1) / KS;
+          const int nbj = jt_width(I.nb, jt);
+          const int n_st = seg_stages(I.n_ic, seg, KS);
+          if (++seg == I.n_seg) {
+            seg = 0;
+            if (++kk == n_prod) {
+              kk = 0;
+              ++jt;
+            }
+          }
           for (int c = 0; c < n_st; ++c, ++g) {
             const int st = g % kStages;
             if (!mbar_wait_abort(full_bar(st), (g / kStages) & 1, s_abort, status, G.wait_ns, 32) ||
@@ -508,8 +536,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int p = I.pt * kTile + r;
       const bool live = p < I.np;
       df y = {0.f, 0.f};  // running sum over the item's groups
-      int kk = 0, jt = 0;
-      for (int grp = 0; grp < I.n_jt * n_prod; ++grp, ++k) {
+      int seg = 0, kk = 0, jt = 0;
+      for (int grp = 0; grp < I.n_jt * n_prod * I.n_seg; ++grp, ++k) {
         const int set = k & 1;
         const int j0 = jt * kTile;
         const Product P = prod_at(kk);
@@ -563,9 +591,12 @@ __global__ void __launch_bounds__(kThreads, 1)
         tc_fence_before();
         mbar_arrive(accempty_bar(set));
         y = df_add(y, df{P.factor * yh, P.factor * yl});  // factor 1 or 2: exact
-        if (++kk == n_prod) {
-          kk = 0;
-          ++jt;
+        if (++seg == I.n_seg) {
+          seg = 0;
+          if (++kk == n_prod) {
+            kk = 0;
+            ++jt;
+          }
         }
       }
       if (!ok) break;
@@ -666,7 +697,7 @@ template <int MODE>
 q4c_status run(const q4c_tables* t, const q4c_grid* g, const double* const mats[5], double* out, cudaStream_t s,
                bool weighted) {
   if (g->max_nb > kMaxNb) {
-    set_error("the split density/adjoint need at most 512 active functions per batch");
+    set_error("the split density/adjoint need at most 4096 active functions per batch");
     return Q4C_EUNSUPPORTED;
   }
   const float2* mdf[5];

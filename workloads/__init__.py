@@ -340,6 +340,93 @@ def periodic_cell(seed: int = 1005, cell=(9.0, 10.0, 11.0), n_atoms: int = 3, n_
                     n_phi=n_phi, r_nb=r_nb, batch_max=batch_max, lattice=L, n_shell=n_shell)
 
 
+HEAVY64_L = [0] * 4 + [1] * 4 + [2] * 4 + [3] * 4                # 4 radials per l, l = 0..3: 64
+
+
+def _place_periodic(rng, L, count, z_range, sep, placed, placed_sep):
+    """`count` positions uniform in x, y over the orthorhombic cell L and in
+    z over z_range (taken modulo the cell), rejected when closer than `sep` to
+    a position placed by this call or `placed_sep[k]` to placed[k] (minimum
+    image in all three directions); a hash of 4 Bohr cells finds the
+    neighbours."""
+    cell = 4.0
+    nc = np.maximum((L // cell).astype(int), 1)
+    size = L / nc
+    buckets = {}
+
+    def key(c):
+        return tuple((np.floor(c / size).astype(int)) % nc)
+
+    for q, sq in zip(placed, placed_sep):
+        buckets.setdefault(key(q), []).append((q, sq))
+    reach = int(math.ceil(max([sep] + list(placed_sep)) / size.min()))
+    offs = [np.array(o) - reach for o in np.ndindex(2 * reach + 1, 2 * reach + 1, 2 * reach + 1)]
+    out, tries = [], 0
+    while len(out) < count:
+        tries += 1
+        if tries > 200 * count + 100000:
+            raise RuntimeError("could not place atoms with the requested separation")
+        c = np.array([rng.uniform(0.0, L[0]), rng.uniform(0.0, L[1]), rng.uniform(*z_range) % L[2]])
+        k = np.array(key(c))
+        ok = True
+        for o in offs:
+            for q, sq in buckets.get(tuple((k + o) % nc), ()):
+                dv = c - q
+                dv -= L * np.round(dv / L)
+                if dv @ dv < sq * sq:
+                    ok = False
+                    break
+            if not ok:
+                break
+        if ok:
+            out.append(c)
+            buckets.setdefault(tuple(k), []).append((c, sep))
+    return np.array(out).reshape(-1, 3)
+
+
+def slab(seed: int = 2005, n_atoms: int = 3383, cell=(100.0, 100.0, 25.0), heavy_frac: float = 0.3,
+         heavy_half: float = 8.0, n_rad: int = 40, n_theta: int = 12, n_phi: int = 25, batch_max: int = 300,
+         name: Optional[str] = None) -> Workload:
+    """The periodic-slab configuration (the shape of the paper's largest
+    layered perovskite cell): an orthorhombic cell of n_atoms, a fraction
+    heavy_frac heavy (one third Pb Z=82, two thirds I Z=53, four radial
+    functions per l = 0..3: 64 functions) in the layer |z - c/2| < heavy_half
+    at least 4 Bohr apart, the rest light (H 2s1p = 5 functions, C and N
+    3s2p1d = 14, drawn in the proportions 1728 : 1152 : 144) in the rest of
+    the cell at least 1.8 Bohr from any atom (minimum image); exponents
+    log-uniform in [0.1, 10] per species; 40 x (12 x 25) points per atom,
+    batches <= 300, r_nb = 12 and the image shell T in {-1, 0, 1}^3 (every
+    cell edge is at least 2 r_nb)."""
+    rng = np.random.default_rng(seed)
+    L = np.asarray(cell, dtype=np.float64)
+    sp = [Species("Pb", 82.0, HEAVY64_L, _draw_alphas(rng, len(HEAVY64_L))),
+          Species("I", 53.0, HEAVY64_L, _draw_alphas(rng, len(HEAVY64_L))),
+          Species("H", 1.0, LIGHT_MIX_L["H"], _draw_alphas(rng, 3)),
+          Species("C", 6.0, LIGHT_MIX_L["O"], _draw_alphas(rng, 6)),
+          Species("N", 7.0, LIGHT_MIX_L["O"], _draw_alphas(rng, 6))]
+    n_heavy = int(round(heavy_frac * n_atoms))
+    n_light = n_atoms - n_heavy
+    zc = 0.5 * L[2]
+    heavy = _place_periodic(rng, L, n_heavy, (zc - heavy_half, zc + heavy_half), 4.0, [], [])
+    light = _place_periodic(rng, L, n_light, (zc + heavy_half, zc - heavy_half + L[2]), 1.8,
+                            list(heavy), [1.8] * n_heavy)
+    hk = (rng.uniform(size=n_heavy) >= 1.0 / 3.0).astype(np.int32)           # 0 Pb, 1 I
+    u = rng.uniform(size=n_light) * (1728 + 1152 + 144)
+    lk = np.where(u < 1728, 2, np.where(u < 1728 + 1152, 3, 4)).astype(np.int32)
+    return Workload(name or f"slab-{n_atoms}atom", np.vstack([heavy, light]), np.concatenate([hk, lk]), sp,
+                    n_rad=n_rad, n_theta=n_theta, n_phi=n_phi, r_nb=12.0, batch_max=batch_max,
+                    lattice=np.diag(L), n_shell=1)
+
+
+def small_slab(n_atoms: int = 304, seed: int = 2006, n_rad: int = 20, n_theta: int = 8, n_phi: int = 16,
+               batch_max: int = 300) -> Workload:
+    """The slab's density and layering in a 30 x 30 x 25 Bohr cell (304
+    atoms for the same atoms per volume): batches of up to about 800
+    functions on a grid the oracle samples in seconds."""
+    return slab(seed=seed, n_atoms=n_atoms, cell=(30.0, 30.0, 25.0), n_rad=n_rad, n_theta=n_theta, n_phi=n_phi,
+                batch_max=batch_max, name=f"small-slab-{n_atoms}atom")
+
+
 def _erf(x: np.ndarray) -> np.ndarray:
     try:
         from scipy.special import erf
@@ -359,6 +446,14 @@ def _images(wl: Workload, reach: float) -> np.ndarray:
     return T @ L
 
 
+def _near_box(P, centres, reach):
+    """Indices of the centres within `reach` of the bounding box of points P
+    (a periodic term vanishes exactly beyond 2 r_c, so the others add zeros)."""
+    lo, hi = P.min(0), P.max(0)
+    gap = np.maximum(0.0, np.maximum(lo[None, :] - centres, centres - hi[None, :]))
+    return np.nonzero((gap * gap).sum(-1) < reach * reach)[0]
+
+
 def _smoothstep_cut(d: np.ndarray, r_on: float, r_off: float) -> np.ndarray:
     s = np.clip((d - r_on) / (r_off - r_on), 0.0, 1.0)
     return 1.0 - s * s * s * (10.0 - 15.0 * s + 6.0 * s * s)
@@ -369,8 +464,10 @@ def potential(points: np.ndarray, wl: Workload, chunk: int = 65536, device=None)
     erf(d)/d -> 2/sqrt(pi) (1 - d^2/3 + d^4/10) for d < 1e-4.
     Periodic workloads sum over the images within 2 r_c, each term times a
     quintic smoothstep that goes from 1 at 2 r_c - 1 to 0 at 2 r_c (the bare
-    lattice sum of -Z/r diverges).  device (a torch device) evaluates the same
-    expression in FP64 with torch there, for inputs of many million points."""
+    lattice sum of -Z/r diverges); each chunk of points sums over the images
+    within 2 r_c of its bounding box only.  device (a torch device) evaluates
+    the same expression in FP64 with torch there, for inputs of many million
+    points."""
     points = np.ascontiguousarray(points, dtype=np.float64).reshape(-1, 3)
     Z = wl.Z_of_atom
     centres, Zc = wl.xyz, Z
@@ -383,26 +480,39 @@ def potential(points: np.ndarray, wl: Workload, chunk: int = 65536, device=None)
         return _potential_torch(points, centres, Zc, wl, periodic, device)
     out = np.empty(points.shape[0], dtype=np.float64)
     c = 2.0 / math.sqrt(math.pi)
+    if periodic:
+        chunk = min(chunk, 4096)  # consecutive points: tight boxes, few images each
     for s in range(0, points.shape[0], chunk):
         P = points[s:s + chunk]
-        d = np.sqrt(((P[:, None, :] - centres[None, :, :]) ** 2).sum(-1))
+        cs, zs = centres, Zc
+        if periodic:
+            near = _near_box(P, centres, 2.0 * wl.r_c)
+            cs, zs = centres[near], Zc[near]
+        d = np.sqrt(((P[:, None, :] - cs[None, :, :]) ** 2).sum(-1))
         small = d < 1e-4
         ds = np.where(small, 1.0, d)
         f = np.where(small, c * (1.0 - d * d / 3.0 + d ** 4 / 10.0), _erf(ds) / ds)
         if periodic:
             f = f * _smoothstep_cut(d, 2.0 * wl.r_c - 1.0, 2.0 * wl.r_c)
-        out[s:s + chunk] = -(f * Zc[None, :]).sum(-1)
+        out[s:s + chunk] = -(f * zs[None, :]).sum(-1)
     return out
 
 
 def _potential_torch(points, centres, Zc, wl, periodic, device) -> np.ndarray:
     import torch
-    C = torch.tensor(centres, dtype=torch.float64, device=device)
-    Zt = torch.tensor(Zc, dtype=torch.float64, device=device)
     out = np.empty(points.shape[0], dtype=np.float64)
     c = 2.0 / math.sqrt(math.pi)
-    step = max(1, (1 << 26) // max(len(Zc), 1))
+    if periodic:  # chunks of consecutive points, each with the images near its bounding box
+        step = 16384
+    else:
+        C = torch.tensor(centres, dtype=torch.float64, device=device)
+        Zt = torch.tensor(Zc, dtype=torch.float64, device=device)
+        step = max(1, (1 << 26) // max(len(Zc), 1))
     for s in range(0, points.shape[0], step):
+        if periodic:
+            near = _near_box(points[s:s + step], centres, 2.0 * wl.r_c)
+            C = torch.tensor(centres[near], dtype=torch.float64, device=device)
+            Zt = torch.tensor(Zc[near], dtype=torch.float64, device=device)
         P = torch.tensor(points[s:s + step], dtype=torch.float64, device=device)
         d = torch.sqrt(((P[:, None, :] - C[None, :, :]) ** 2).sum(-1))
         small = d < 1e-4
