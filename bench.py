@@ -253,8 +253,9 @@ def oracle_step_sample(wl, stride: int, threads: int = 1):
     ob = O.OracleBasis(wl)
     pat = ob.pattern()
     v = potential(xyz, wl)
-    P = fill_pattern(pat.blk_ptr, pat.blk_col, pat.blk_off, wl.nf_of_atom, 11, "P")
-    G = [fill_pattern(pat.blk_ptr, pat.blk_col, pat.blk_off, wl.nf_of_atom, 12, k, a) for k, a in ADJOINT_KINDS]
+    P = fill_pattern(pat.blk_ptr, pat.blk_col, pat.blk_off, wl.nf_of_atom, 11, "P", blk_T=pat.blk_T)
+    G = [fill_pattern(pat.blk_ptr, pat.blk_col, pat.blk_off, wl.nf_of_atom, 12, k, a, blk_T=pat.blk_T)
+         for k, a in ADJOINT_KINDS]
     parts = [np.arange(k, len(w), threads) for k in range(threads)]  # interleaved: even cost per thread
 
     def chunk(k):
@@ -349,9 +350,11 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=3,
                     help="FP64-path steps timed after the split run for the speedup (0: skip)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="cluster64", choices=["cluster64", "water", "molecules", "cluster512"],
+    ap.add_argument("--workload", default="cluster64",
+                    choices=["cluster64", "water", "molecules", "cluster512", "slab"],
                     help="cluster64: the 64-atom cluster (default); molecules: 2,000 independent molecules "
-                         "in one grid; cluster512: the 512-atom cluster of the adjoint configuration")
+                         "in one grid; cluster512: the 512-atom cluster of the adjoint configuration; slab: "
+                         "the 3,383-atom periodic slab")
     ap.add_argument("--cpu-stride", type=int, default=16, help="one-core sample of the cpu baseline")
     ap.add_argument("--cpu-stride-all", type=int, default=2, help="all-core sample of the cpu baseline")
     ap.add_argument("--ref-stride", type=int, default=7)
@@ -367,19 +370,24 @@ def main():
             print(f"source_sha256[{name}]: {kernel_source_hash(name)}")
         return
 
-    from workloads import cluster512, cluster64, molecule_batch, water
-    wl = {"cluster64": cluster64, "water": water, "molecules": molecule_batch, "cluster512": cluster512}[args.workload]()
+    from workloads import cluster512, cluster64, molecule_batch, slab, water
+    wl = {"cluster64": cluster64, "water": water, "molecules": molecule_batch, "cluster512": cluster512,
+          "slab": slab}[args.workload]()
+    big = args.workload in ("molecules", "cluster512", "slab")
+    if args.workload == "slab" and args.steps == 60:
+        args.steps = 3  # a step of the slab takes seconds
     # sample strides that keep the oracle's share of a run to seconds
-    if args.workload in ("molecules", "cluster512"):
-        default_strides = {"molecules": (200, 20), "cluster512": (4000, 400)}[args.workload]
+    if big:
+        default_strides = {"molecules": (200, 20), "cluster512": (4000, 400), "slab": (40000, 0)}[args.workload]
         if args.cpu_stride == 16:
             args.cpu_stride = default_strides[0]
         if args.cpu_stride_all == 2:
             args.cpu_stride_all = default_strides[1]
     if args.impl == "reference":
-        if args.workload == "cluster512":
-            print(json.dumps({"impl": "reference", "unavailable": "the oracle's FLOP count of the 512-atom cluster "
-                              "needs its full grid (about 8 min of host time), beyond this arm's few-minute bound"}))
+        if args.workload in ("cluster512", "slab"):
+            print(json.dumps({"impl": "reference", "unavailable": f"the oracle's FLOP count of the {wl.name} workload "
+                              "needs its full grid (8 min of host time for the 512-atom cluster, hours for the "
+                              "slab), beyond this arm's few-minute bound"}))
             return
         if args.workload == "molecules" and args.ref_stride == 7:
             args.ref_stride = 100
@@ -405,8 +413,8 @@ def main():
         v_h = molecule_potential(ex["xyz"], ex["point_id"] // ppa, wl, device=dev)
     else:
         v_h = potential(ex["xyz"], wl, device=dev if grid.n_points > 4_000_000 else None)
-    P_h = fill_pattern(*pat, wl.nf_of_atom, 11, "P")
-    G_h = [fill_pattern(*pat, wl.nf_of_atom, 12, k, a) for k, a in ADJOINT_KINDS]
+    P_h = fill_pattern(*pat, wl.nf_of_atom, 11, "P", blk_T=ex["blk_T"])
+    G_h = [fill_pattern(*pat, wl.nf_of_atom, 12, k, a, blk_T=ex["blk_T"]) for k, a in ADJOINT_KINDS]
     v = torch.tensor(v_h, device=dev)
     P = torch.tensor(P_h, device=dev)
     G = [torch.tensor(g, device=dev) for g in G_h]
@@ -549,7 +557,8 @@ def main():
     # ---- the integration alone (q4c_integrate, device time, L2 flushed)
     extra = {}
     if fused:  # the same step as three separate calls, for comparison
-        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(5)]
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(min(5, args.steps))]
         for a_, b_ in evs:
             flush.zero_()
             a_.record(stream)
@@ -576,9 +585,10 @@ def main():
         "tensor_frac_note": f"x {S_PAIRS} slice pairs / {peak_src} bf16 burst, whole call incl. basis and scatter"}
 
     # ---- FP64 comparison path and split error (reported beside the value)
-    if args.workload in ("molecules", "cluster512") and args.fp64_steps == 3:
-        args.fp64_steps = 1  # the FP64 path takes tens of seconds per step there
-    if prec == "split" and args.fp64_steps > 0:
+    if big and args.fp64_steps == 3:
+        # the FP64 path takes tens of seconds per step there (minutes on the slab)
+        args.fp64_steps = 0 if args.workload == "slab" else 1
+    if prec == "split" and (args.fp64_steps > 0 or args.workload == "slab"):
         ref = [torch.empty_like(m) for m in mats[:5]]
         q.q4c_integrate(tables, grid, v, "fp64", out=ref + [None], stream=stream)
         q.q4c_integrate(tables, grid, v, "split", out=mats, stream=stream)
@@ -599,6 +609,8 @@ def main():
                 worst[nme] = float(torch.sqrt(num / torch.clamp(den, min=1e-300)).max())
             extra["split_rel_err_vs_fp64_worst_molecule"] = worst
             extra["molecules"] = int(wl.n_molecules)
+        del ref
+    if prec == "split" and args.fp64_steps > 0:
         # the same step on the FP64 path (device time, L2 flushed), for the split/FP64 speedup
         fp64_phase = {"integrate": "fp64", "density": "fp64", "backward": "fp64"}
 
@@ -655,13 +667,18 @@ def main():
     if not args.no_cpu_baseline and world == 1:
         cores = host_cores()
         t1, f1 = oracle_step_sample(wl, args.cpu_stride, 1)
-        tn, fn_ = oracle_step_sample(wl, args.cpu_stride_all, cores)
-        cpu = {"value": F_step * fn_ / tn / 1e12, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
-               "sample": f"raw grid ids divisible by {args.cpu_stride_all} ({fn_:.4f} of the workload) split over "
-                         f"{cores} threads, {tn:.1f} s wall",
-               "single_core": {"value": F_step * f1 / t1 / 1e12, "cores": 1,
-                               "sample": f"raw grid ids divisible by {args.cpu_stride} ({f1:.4f} of the workload), "
-                                         f"{t1:.1f} s of one core"}}
+        single = {"value": F_step * f1 / t1 / 1e12, "cores": 1,
+                  "sample": f"raw grid ids divisible by {args.cpu_stride} ({f1:.6f} of the workload), "
+                            f"{t1:.1f} s of one core"}
+        if args.cpu_stride_all > 0:
+            tn, fn_ = oracle_step_sample(wl, args.cpu_stride_all, cores)
+            cpu = {"value": F_step * fn_ / tn / 1e12, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
+                   "sample": f"raw grid ids divisible by {args.cpu_stride_all} ({fn_:.4f} of the workload) split "
+                             f"over {cores} threads, {tn:.1f} s wall", "single_core": single}
+        else:  # one part only: each concurrent part would hold its own full-pattern accumulators
+            cpu = {"value": single["value"], "unit": "TFLOP/s", "cores": 1, "kind": "oracle",
+                   "sample": single["sample"] + "; one thread only (the oracle's matrices hold 5 x nnz compensated "
+                                                "accumulators per concurrent part, 17 GB here)"}
     line = {
         "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_ms, "higher_is_better": True, "scaling": "weak",
