@@ -833,6 +833,7 @@ extern "C" q4c_status grid_partition(const q4c_grid_desc* d, const q4c_tables* t
   g->h_bat_atoms.resize(g->h_bat_atom_ptr[nB]);
   std::vector<int> fn_info(g->h_bat_fn_ptr[nB]);
   std::vector<int64_t> pair_off(pair_ptr[nB]);
+  std::vector<int> pair_blk(pair_ptr[nB]);
   parallel_for(nB, [&](int64_t b) {
     const int na = static_cast<int>(act[b].size());
     int f = 0;
@@ -852,6 +853,7 @@ extern "C" q4c_status grid_partition(const q4c_grid_desc* d, const q4c_tables* t
         // the batch (active at opposite ends of it), so the pair adds nothing
         const int64_t q = find_block(c_atom(A), c_atom(Cc), T);
         pair_off[pair_ptr[b] + static_cast<int64_t>(a) * na + c] = q < 0 ? -1 : g->h_blk_off[q];
+        pair_blk[pair_ptr[b] + static_cast<int64_t>(a) * na + c] = static_cast<int>(q);
       }
     }
   });
@@ -1023,6 +1025,12 @@ extern "C" q4c_status grid_partition(const q4c_grid_desc* d, const q4c_tables* t
     return cost(a) > cost(b);
   });
 
+  // ---- per-block column and row maxima segments: [nf_B columns][nf_A rows]
+  std::vector<int64_t> cm_off(g->n_blocks + 1, 0);
+  for (int64_t q = 0; q < g->n_blocks; ++q)
+    cm_off[q + 1] = cm_off[q] + g->h_nf_atom[blk_row[q]] + g->h_nf_atom[g->h_blk_col[q]];
+  g->cm_total = std::max<int64_t>(cm_off[g->n_blocks], 1);
+
   // ---- upload
   std::vector<double> sx(nP), sy(nP), sz(nP);
   for (int64_t i = 0; i < nP; ++i) {
@@ -1043,6 +1051,7 @@ extern "C" q4c_status grid_partition(const q4c_grid_desc* d, const q4c_tables* t
       (st = up(&g->d_bat_atoms, g->h_bat_atoms)) || (st = up(&g->d_bat_atom_fn0, bat_atom_fn0)) ||
       (st = up(&g->d_bat_fn_ptr, g->h_bat_fn_ptr)) || (st = up(&g->d_fn_info, fn_info)) ||
       (st = up(&g->d_bat_pair_ptr, pair_ptr)) || (st = up(&g->d_pair_off, pair_off)) ||
+      (st = up(&g->d_pair_blk, pair_blk)) || (st = up(&g->d_cm_off, cm_off)) ||
       (st = up(&g->d_blk_off, g->h_blk_off)) || (st = up(&g->d_blk_row, blk_row)) ||
       (st = up(&g->d_blk_col, g->h_blk_col)) || (st = up(&g->d_blk_T, blk_T)) || (st = up(&g->d_blk_role, blk_role)) ||
       (st = up(&g->d_blk_shift, g->h_blk_shift)) || (st = up(&g->d_kblk_q0, g->h_kblk_q0)) ||
@@ -1063,6 +1072,7 @@ extern "C" q4c_status grid_partition(const q4c_grid_desc* d, const q4c_tables* t
     if (e == cudaSuccess) e = cudaMalloc(&g->d_rowexp, sizeof(int) * 4 * nP);
     if (e == cudaSuccess) e = cudaMalloc(&g->d_gsl, static_cast<size_t>(std::max<int64_t>(g->gsl_bytes, 16)));
     if (e == cudaSuccess) e = cudaMalloc(&g->d_gdf, sizeof(float2) * 10 * std::max<int64_t>(g->nnz, 1));
+    if (e == cudaSuccess) e = cudaMalloc(&g->d_cm, sizeof(float) * 10 * g->cm_total);
     if (e == cudaSuccess) e = cudaMalloc(&g->d_gzero, 12288);
     if (e == cudaSuccess) e = cudaMemset(g->d_gzero, 0, 12288);
     if (e == cudaSuccess) e = cudaMalloc(&g->d_bat_idx, sizeof(int) * g->idx_entries);
@@ -1072,7 +1082,8 @@ extern "C" q4c_status grid_partition(const q4c_grid_desc* d, const q4c_tables* t
     if (e == cudaSuccess) e = cudaMalloc(&g->d_status, sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMemset(g->d_status, 0, sizeof(unsigned));
     g->split_ws_bytes = static_cast<int64_t>(sizeof(int)) * (8 * g->h_bat_fn_ptr[nB] + 4 * nP) +
-                        static_cast<int64_t>(sizeof(float2)) * 5 * g->nnz + g->gsl_bytes;
+                        static_cast<int64_t>(sizeof(float2)) * 5 * g->nnz + g->gsl_bytes +
+                        static_cast<int64_t>(sizeof(float)) * 10 * g->cm_total;
     if (e != cudaSuccess) {
       set_error(std::string("grid_partition: workspace: ") + cudaGetErrorString(e));
       q4c_grid_destroy(g);
@@ -1096,7 +1107,7 @@ extern "C" void q4c_grid_destroy(q4c_grid* g) {
                   g->d_split_items, g->d_col_items, g->d_split_mag, g->d_dpad, g->d_tmaps, g->d_colexp, g->d_status, g->d_rd_items, g->d_rowexp, g->d_gsl, g->d_gsl_off,
                   g->d_bat_idx_ptr, g->d_bat_idx, g->d_pts_df, g->d_atoms_df, g->d_gdf, g->d_gzero,
                   g->d_c_xyz, g->d_c_sp, g->d_blk_role, g->d_blk_shift, g->d_kblk_q0, g->d_kblk_q1,
-                  g->d_kblk_off};
+                  g->d_kblk_off, g->d_cm_off, g->d_cm, g->d_pair_blk};
   for (void* p : ptrs) cudaFree(p);
   delete g;
 }

@@ -246,6 +246,14 @@ struct q4c_grid {
   int* d_bat_idx = nullptr;                // per batch n_b x n_b value offsets (-1 outside)
   unsigned* d_status = nullptr;            // bit 0: a bounded wait expired
   float2* d_gdf = nullptr;                 // [10][nnz] FP32-pair copies of the density (0-4) and adjoint (5-9) matrices
+  // per pattern block q, at cm_off[q]: the largest |value| of each of its
+  // nf_B columns, then of each of its nf_A rows (FP32, rounded up), for each
+  // of the ten matrices of d_gdf ([10][cm_total]); the G' pre-pass bounds a
+  // batch column's largest element from them
+  int64_t* d_cm_off = nullptr;             // [n_blocks + 1]
+  int64_t cm_total = 0;
+  float* d_cm = nullptr;
+  int* d_pair_blk = nullptr;               // per batch, n_a^2: pattern block of centre pair (a, b) or -1
   int64_t split_ws_bytes = 0;
   void* d_split_ws = nullptr;
   q4c::DevGrid view() const;

@@ -85,7 +85,7 @@ struct Product {
 // (F quantity, G matrix, R quantity, factor) of adjoint product k, packed one
 // byte per product (qf | gm << 2 | qr << 5 | (factor == 2) << 7) so that the
 // lookup stays in registers; matrices 2-4 enter through their antisymmetric
-// parts, which the pre-pass slices.  The density is product 0.
+// parts, which the preparation forms once per call.  The density is product 0.
 constexpr uint64_t kProducts = 0x00ull | (0x25ull << 8) | (0x46ull << 16) | (0x67ull << 24) | (0xEAull << 32) |
                                (0xAFull << 40) | (0xD1ull << 48);
 
@@ -95,27 +95,70 @@ __device__ __forceinline__ Product product_of(int k) {
           (c >> 7) ? 2.0f : 1.0f};
 }
 
-// FP32-pair copy of an FP64 matrix: x = hi + lo within 2^-48 relative
-__global__ void k_to_df(const double* __restrict__ M, int64_t n, float2* __restrict__ out) {
-  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
-       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    const double x = M[i];
-    const float h = __double2float_rn(x);
-    out[i] = make_float2(h, __double2float_rn(x - static_cast<double>(h)));
+// One CTA per pattern block q (A, B, T) (grid-stride): the FP32-pair copy
+// of the block's values x (x = hi + lo within 2^-48 relative), and at
+// cm_off[q] the largest |x| of each of its nf_B columns, then of each of its
+// nf_A rows, rounded up to FP32.  With anti, x is the antisymmetric part
+// (G - G^T)/2 in FP64, G^T read from the partner block (B, A, -T) through
+// shared memory where both sides have at most 64 functions, else straight
+// from memory (only that part enters the adjoint's cross-product terms).
+__global__ void __launch_bounds__(128) k_prepare_blocks(DevBasis B, DevGrid G, const double* __restrict__ M,
+                                                       int anti, int64_t n_blocks, const int* __restrict__ blk_row,
+                                                       const int* __restrict__ blk_col,
+                                                       const int64_t* __restrict__ blk_off,
+                                                       const int* __restrict__ blk_T,
+                                                       const int64_t* __restrict__ cm_off, float2* __restrict__ out,
+                                                       float* __restrict__ cm) {
+  __shared__ double sT[64 * 65];  // G^T of the block: sT[i * 65 + j] = partner (j, i)
+  for (int64_t q = blockIdx.x; q < n_blocks; q += gridDim.x) {
+    const int nfA = __ldg(B.sp_nfn + G.atom_sp[blk_row[q]]), nfB = __ldg(B.sp_nfn + G.atom_sp[blk_col[q]]);
+    const double* X = M + blk_off[q];
+    const int ne = nfA * nfB;
+    const int qt = anti ? blk_T[q] : -1;
+    const double* XT = qt >= 0 ? M + blk_off[qt] : nullptr;  // nfB rows x nfA columns
+    const bool tile = XT && nfA <= 64 && nfB <= 64;
+    if (tile) {
+      __syncthreads();
+      for (int e = threadIdx.x; e < ne; e += blockDim.x) {
+        const int r = e / nfA, c = e - r * nfA;
+        sT[c * 65 + r] = XT[e];
+      }
+      __syncthreads();
+    }
+    auto val = [&](int i, int j) {
+      const double x = X[static_cast<int64_t>(i) * nfB + j];
+      if (!anti) return x;
+      const double xt = tile ? sT[i * 65 + j] : XT ? XT[static_cast<int64_t>(j) * nfA + i] : 0.0;
+      return 0.5 * (x - xt);
+    };
+    float2* o = out + blk_off[q];
+    for (int e = threadIdx.x; e < ne; e += blockDim.x) {
+      const int i = e / nfB, j = e - i * nfB;
+      const double x = val(i, j);
+      const float h = __double2float_rn(x);
+      o[e] = make_float2(h, __double2float_rn(x - static_cast<double>(h)));
+    }
+    float* mx = cm + cm_off[q];
+    for (int j = threadIdx.x; j < nfB; j += blockDim.x) {
+      double m = 0.0;
+      for (int i = 0; i < nfA; ++i) m = fmax(m, fabs(val(i, j)));
+      mx[j] = __double2float_ru(m);
+    }
+    for (int i = threadIdx.x; i < nfA; i += blockDim.x) {
+      double m = 0.0;
+      for (int j = 0; j < nfB; ++j) m = fmax(m, fabs(val(i, j)));
+      mx[nfB + i] = __double2float_ru(m);
+    }
   }
 }
 
-// G'_ij of the batch (i, j local) from the FP32-pair matrix through the
-// batch's dense offset table (the antisymmetric part in double-float)
-__device__ __forceinline__ df gprime_df(const float2* M, const int* __restrict__ idx, int nb, int anti, int i,
-                                        int j) {
+// G'_ij of the batch (i, j local) from the prepared FP32-pair matrix (the
+// antisymmetric part where that is what enters) through the batch's dense
+// offset table
+__device__ __forceinline__ df gprime_df(const float2* M, const int* __restrict__ idx, int nb, int i, int j) {
   const int o = __ldg(idx + i * nb + j);
   const float2 g = o < 0 ? make_float2(0.f, 0.f) : __ldg(M + o);
-  if (!anti) return df{g.x, g.y};
-  const int oT = __ldg(idx + j * nb + i);
-  const float2 gT = oT < 0 ? make_float2(0.f, 0.f) : __ldg(M + oT);
-  const df d = df_sub(df{g.x, g.y}, df{gT.x, gT.y});
-  return df{0.5f * d.hi, 0.5f * d.lo};  // exact
+  return df{g.x, g.y};
 }
 
 __device__ __forceinline__ int fexp(float x) {  // |x| < 2^fexp(x) for x != 0
@@ -126,44 +169,45 @@ __device__ __forceinline__ int fexp(float x) {  // |x| < 2^fexp(x) for x != 0
 // granularity); its G' digit tiles hold that many rows
 __device__ __forceinline__ int jt_width(int nb, int jt) { return (min(kTile, nb - jt * kTile) + 15) & ~15; }
 
-// Pre-pass: one CTA per (batch, matrix).  Column exponents e_j (|G'_ij| <=
-// 2^e_j over i), then the six digits of every G'_ij written as the B operand
-// tiles of the main kernel: block (jt, ic) (a 12 KB slot) = six tiles of
-// jt_width rows (j) x 16 K (i), 32 bytes a row, in the no-swizzle K-major
-// layout, back to back; padding rows and columns are 0.
-__global__ void __launch_bounds__(256) k_gslice(DevGrid G, int64_t b0, int anti_from, const float2* M0,
+// Pre-pass: one CTA per (batch, matrix).  Column exponents e_j (|G'_ij| <
+// 2^e_j over the batch's i), then the six digits of every G'_ij written as
+// the B operand tiles of the main kernel: block (jt, ic) (a 12 KB slot) =
+// six tiles of jt_width rows (j) x 16 K (i), 32 bytes a row, in the
+// no-swizzle K-major layout, back to back; padding rows and columns are 0.
+// The column bound is the largest column maximum (k_prepare_blocks) of the
+// blocks (a, c) of column j's centre c over the batch's active centres a,
+// whose functions are exactly the batch's i.
+__global__ void __launch_bounds__(256) k_gslice(DevGrid G, int64_t b0, const float2* M0,
                                                 const float2* M1, const float2* M2, const float2* M3,
-                                                const float2* M4, const int64_t* __restrict__ gsl_off,
-                                                uint32_t* __restrict__ gsl) {
-  __shared__ unsigned sMax[kMaxNb];  // bits of max_i |hi(G'_ij)| (non-negative floats order as integers)
+                                                const float2* M4, const float* C0, const float* C1,
+                                                const float* C2, const float* C3, const float* C4,
+                                                const int* __restrict__ pair_blk, const int64_t* __restrict__ cm_off,
+                                                const int64_t* __restrict__ gsl_off, uint32_t* __restrict__ gsl) {
+  __shared__ unsigned sMax[kMaxNb];  // bits of the bound of max_i |G'_ij| (non-negative floats order as integers)
   const int64_t b = b0 + blockIdx.x;
   const int m = blockIdx.y;
   const float2* mats[5] = {M0, M1, M2, M3, M4};
+  const float* maxs[5] = {C0, C1, C2, C3, C4};
   const float2* M = mats[m];
   if (M == nullptr) return;
-  const int anti = m >= anti_from;
+  const float* CM = maxs[m];
   const int nb = static_cast<int>(G.bat_fn_ptr[b + 1] - G.bat_fn_ptr[b]);
   const int* idx = G.bat_idx + G.bat_idx_ptr[b];
   const int n_jt = (nb + kTile - 1) / kTile, n_ic = (nb + kKc - 1) / kKc;
   uint32_t* out = gsl + (gsl_off[b] + static_cast<int64_t>(m) * n_jt * n_ic * kBlockB) / 4;
-  for (int j = threadIdx.x; j < nb; j += blockDim.x) sMax[j] = 0u;
-  __syncthreads();
-  // pass 1: column maxima, element-parallel, four gathers in flight per thread
-  constexpr int kU = 4;
-  const int nn = nb * nb;
-  for (int e0 = threadIdx.x; e0 < nn; e0 += kU * blockDim.x) {
-    df x[kU];
-#pragma unroll
-    for (int u = 0; u < kU; ++u) {
-      const int e = e0 + u * blockDim.x;
-      x[u] = e < nn ? gprime_df(M, idx, nb, anti, e / nb, e - (e / nb) * nb) : df{0.f, 0.f};
-    }
-#pragma unroll
-    for (int u = 0; u < kU; ++u) {
-      const int e = e0 + u * blockDim.x;
-      if (e >= nn) break;
-      const float a = fabsf(x[u].hi);
-      if (a > 0.f) atomicMax(&sMax[e - (e / nb) * nb], __float_as_uint(a));
+  // pass 1: column bounds, a thread per column over the batch's centres
+  {
+    const int a0 = G.bat_atom_ptr[b], na = G.bat_atom_ptr[b + 1] - a0;
+    const int* pb = pair_blk + G.bat_pair_ptr[b];
+    const int* info = G.fn_info + G.bat_fn_ptr[b];
+    for (int j = threadIdx.x; j < nb; j += blockDim.x) {
+      const int c = info[j] >> 16, jj = info[j] & 0xffff;
+      float mx = 0.f;
+      for (int a = 0; a < na; ++a) {
+        const int q = pb[a * na + c];  // block (a, c): its column jj
+        if (q >= 0) mx = fmaxf(mx, __ldg(CM + cm_off[q] + jj));
+      }
+      sMax[j] = __float_as_uint(mx);
     }
   }
   __syncthreads();
@@ -181,8 +225,8 @@ __global__ void __launch_bounds__(256) k_gslice(DevGrid G, int64_t b0, int anti_
     if (j < nb) {
       const unsigned mb = sMax[j];
       const float m0 = magic0(mb ? fexp(__uint_as_float(mb)) : -30000);
-      const df x0 = i < nb ? gprime_df(M, idx, nb, anti, i, j) : df{0.f, 0.f};
-      const df x1 = i + 1 < nb ? gprime_df(M, idx, nb, anti, i + 1, j) : df{0.f, 0.f};
+      const df x0 = i < nb ? gprime_df(M, idx, nb, i, j) : df{0.f, 0.f};
+      const df x1 = i + 1 < nb ? gprime_df(M, idx, nb, i + 1, j) : df{0.f, 0.f};
       slice6(x0.hi, x0.lo, m0, d0);
       slice6(x1.hi, x1.lo, m0, d1);
     } else {
@@ -618,7 +662,9 @@ __global__ void __launch_bounds__(kThreads, 1)
 }
 
 // FP32-pair copies of the present matrices into slots [slot0, slot0 + 5) of
-// the grid's buffer; returns the mask of present matrices
+// the grid's buffer (of the antisymmetric parts of matrices 2-4, the SO
+// slots), with their per-block column and row maxima; returns the mask of
+// present matrices
 q4c_status prepare(const q4c_grid* g, const double* const mats[5], int slot0, const float2* mdf[5],
                    unsigned* present, cudaStream_t s) {
   int dev = 0, n_sm = 0;
@@ -630,8 +676,10 @@ q4c_status prepare(const q4c_grid* g, const double* const mats[5], int slot0, co
     mdf[m] = nullptr;
     if (!mats[m] || g->nnz == 0) continue;
     float2* dst = g->d_gdf + (slot0 + m) * g->nnz;
-    const unsigned blocks = static_cast<unsigned>(std::min<int64_t>((g->nnz + 255) / 256, 8 * n_sm));
-    k_to_df<<<blocks, 256, 0, s>>>(mats[m], g->nnz, dst);
+    const unsigned nblk = static_cast<unsigned>(std::min<int64_t>(g->n_blocks, 64 * n_sm));
+    k_prepare_blocks<<<nblk, 128, 0, s>>>(g->tables->view(), g->view(), mats[m], m >= 2 ? 1 : 0, g->n_blocks,
+                                          g->d_blk_row, g->d_blk_col, g->d_blk_off, g->d_blk_T, g->d_cm_off, dst,
+                                          g->d_cm + (slot0 + m) * g->cm_total);
     mdf[m] = dst;
     *present |= 1u << m;
   }
@@ -646,10 +694,14 @@ template <int MODE>
 q4c_status gslice_wave(const q4c_grid* g, int wv, const float2* const mdf[5], cudaStream_t s) {
   const int64_t b0 = g->wave_b0[wv], b1 = g->wave_b0[wv + 1];
   if (b1 <= b0) return Q4C_OK;
+  // each matrix's block maxima sit in the slot of its FP32-pair copy
+  const float* cmp[5];
+  for (int m = 0; m < 5; ++m)
+    cmp[m] = mdf[m] ? g->d_cm + ((mdf[m] - g->d_gdf) / std::max<int64_t>(g->nnz, 1)) * g->cm_total : nullptr;
   KernelScope ks("split_gslice", s);
   k_gslice<<<dim3(static_cast<unsigned>(b1 - b0), MODE == 0 ? 1 : 5), 256, 0, s>>>(
-      g->view(), b0, MODE == 0 ? 5 : 2, mdf[0], mdf[1], mdf[2], mdf[3], mdf[4], g->d_gsl_off,
-      reinterpret_cast<uint32_t*>(g->d_gsl));
+      g->view(), b0, mdf[0], mdf[1], mdf[2], mdf[3], mdf[4], cmp[0], cmp[1], cmp[2], cmp[3],
+      cmp[4], g->d_pair_blk, g->d_cm_off, g->d_gsl_off, reinterpret_cast<uint32_t*>(g->d_gsl));
   Q4C_CUDA(cudaGetLastError());
   return Q4C_OK;
 }
@@ -740,6 +792,7 @@ q4c_status autotune_rowdot(q4c_grid* g, double* out, cudaStream_t s) {
   const float2* mdf[5];
   for (int m = 0; m < 5; ++m) mdf[m] = g->d_gdf + (5 + m) * g->nnz;
   Q4C_CUDA(cudaMemsetAsync(g->d_gdf + 5 * g->nnz, 0, sizeof(float2) * 5 * g->nnz, s));
+  Q4C_CUDA(cudaMemsetAsync(g->d_cm + 5 * g->cm_total, 0, sizeof(float) * 5 * g->cm_total, s));
   if (q4c_status st = rowdot::gslice_wave<1>(g, 0, mdf, s)) return st;
   cudaEvent_t ev[2][3][2] = {};
   q4c_status status = Q4C_OK;
