@@ -152,15 +152,6 @@ __global__ void __launch_bounds__(128) k_prepare_blocks(DevBasis B, DevGrid G, c
   }
 }
 
-// G'_ij of the batch (i, j local) from the prepared FP32-pair matrix (the
-// antisymmetric part where that is what enters) through the batch's dense
-// offset table
-__device__ __forceinline__ df gprime_df(const float2* M, const int* __restrict__ idx, int nb, int i, int j) {
-  const int o = __ldg(idx + i * nb + j);
-  const float2 g = o < 0 ? make_float2(0.f, 0.f) : __ldg(M + o);
-  return df{g.x, g.y};
-}
-
 __device__ __forceinline__ int fexp(float x) {  // |x| < 2^fexp(x) for x != 0
   return static_cast<int>((__float_as_uint(x) >> 23) & 0xFF) - 126;
 }
@@ -186,11 +177,9 @@ __global__ void __launch_bounds__(256) k_gslice(DevGrid G, int64_t b0, const flo
   __shared__ unsigned sMax[kMaxNb];  // bits of the bound of max_i |G'_ij| (non-negative floats order as integers)
   const int64_t b = b0 + blockIdx.x;
   const int m = blockIdx.y;
-  const float2* mats[5] = {M0, M1, M2, M3, M4};
-  const float* maxs[5] = {C0, C1, C2, C3, C4};
-  const float2* M = mats[m];
+  const float2* M = m == 0 ? M0 : m == 1 ? M1 : m == 2 ? M2 : m == 3 ? M3 : M4;  // (no local array)
   if (M == nullptr) return;
-  const float* CM = maxs[m];
+  const float* CM = m == 0 ? C0 : m == 1 ? C1 : m == 2 ? C2 : m == 3 ? C3 : C4;
   const int nb = static_cast<int>(G.bat_fn_ptr[b + 1] - G.bat_fn_ptr[b]);
   const int* idx = G.bat_idx + G.bat_idx_ptr[b];
   const int n_jt = (nb + kTile - 1) / kTile, n_ic = (nb + kKc - 1) / kKc;
@@ -211,35 +200,56 @@ __global__ void __launch_bounds__(256) k_gslice(DevGrid G, int64_t b0, const flo
     }
   }
   __syncthreads();
-  // pass 2: the six digits of every element, in the B-operand tile layout
+  // pass 2: the six digits of every element, in the B-operand tile layout;
+  // a thread takes kU words (element pairs) at a time and issues all their
+  // offset loads, then all their value loads, before slicing any
+  constexpr int kU = 4;
   for (int jt = 0; jt < n_jt; ++jt) {
-  const int tw = jt_width(nb, jt) * 8;  // words of one tile (one per element pair)
-  const int words = n_ic * tw;
-  for (int w = threadIdx.x; w < words; w += blockDim.x) {
-    const int ic = w / tw, pos = w - ic * tw;
-    const int blk = jt * n_ic + ic;
-    // pos -> byte offset rg*SBO + kq*LBO + r8*16 + kp*4
-    const int rg = pos >> 6, kq = (pos >> 5) & 1, r8 = (pos >> 2) & 7, kp = pos & 3;
-    const int j = jt * kTile + rg * 8 + r8, i = ic * kKc + kq * 8 + kp * 2;
-    float d0[kSlices], d1[kSlices];
-    if (j < nb) {
-      const unsigned mb = sMax[j];
-      const float m0 = magic0(mb ? fexp(__uint_as_float(mb)) : -30000);
-      const df x0 = i < nb ? gprime_df(M, idx, nb, i, j) : df{0.f, 0.f};
-      const df x1 = i + 1 < nb ? gprime_df(M, idx, nb, i + 1, j) : df{0.f, 0.f};
-      slice6(x0.hi, x0.lo, m0, d0);
-      slice6(x1.hi, x1.lo, m0, d1);
-    } else {
+    const int tw = jt_width(nb, jt) * 8;  // words of one tile (one per element pair)
+    const int words = n_ic * tw;
+    for (int w0 = threadIdx.x; w0 < words; w0 += kU * blockDim.x) {
+      int i_[kU], j_[kU], o0[kU], o1[kU];
 #pragma unroll
-      for (int s = 0; s < kSlices; ++s) d0[s] = d1[s] = 0.f;
-    }
-    uint32_t* o = out + static_cast<int64_t>(blk) * (kBlockB / 4) + pos;
+      for (int u = 0; u < kU; ++u) {
+        const int w = w0 + u * blockDim.x;
+        const int ic = w / tw, pos = w - ic * tw;
+        // pos -> byte offset rg*SBO + kq*LBO + r8*16 + kp*4
+        const int rg = pos >> 6, kq = (pos >> 5) & 1, r8 = (pos >> 2) & 7, kp = pos & 3;
+        j_[u] = jt * kTile + rg * 8 + r8;
+        i_[u] = ic * kKc + kq * 8 + kp * 2;
+        const bool ok = w < words && j_[u] < nb;
+        o0[u] = ok && i_[u] < nb ? __ldg(idx + i_[u] * nb + j_[u]) : -1;
+        o1[u] = ok && i_[u] + 1 < nb ? __ldg(idx + (i_[u] + 1) * nb + j_[u]) : -1;
+      }
+      float2 x0[kU], x1[kU];
 #pragma unroll
-    for (int s = 0; s < kSlices; ++s) {
-      const __nv_bfloat162 h2 = __floats2bfloat162_rn(d0[s], d1[s]);
-      o[b_tile(s) * tw] = *reinterpret_cast<const uint32_t*>(&h2);  // [B0, B2, B4, B1, B3, B5]
+      for (int u = 0; u < kU; ++u) {
+        x0[u] = o0[u] < 0 ? make_float2(0.f, 0.f) : __ldg(M + o0[u]);
+        x1[u] = o1[u] < 0 ? make_float2(0.f, 0.f) : __ldg(M + o1[u]);
+      }
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const int w = w0 + u * blockDim.x;
+        if (w >= words) break;
+        const int ic = w / tw, pos = w - ic * tw;
+        float d0[kSlices], d1[kSlices];
+        if (j_[u] < nb) {
+          const unsigned mb = sMax[j_[u]];
+          const float m0 = magic0(mb ? fexp(__uint_as_float(mb)) : -30000);
+          slice6(x0[u].x, x0[u].y, m0, d0);
+          slice6(x1[u].x, x1[u].y, m0, d1);
+        } else {
+#pragma unroll
+          for (int s = 0; s < kSlices; ++s) d0[s] = d1[s] = 0.f;
+        }
+        uint32_t* o = out + static_cast<int64_t>(jt * n_ic + ic) * (kBlockB / 4) + pos;
+#pragma unroll
+        for (int s = 0; s < kSlices; ++s) {
+          const __nv_bfloat162 h2 = __floats2bfloat162_rn(d0[s], d1[s]);
+          o[b_tile(s) * tw] = *reinterpret_cast<const uint32_t*>(&h2);  // [B0, B2, B4, B1, B3, B5]
+        }
+      }
     }
-  }
   }
 }
 
