@@ -51,6 +51,8 @@ TRAFFIC_PROFILES = {
     "split_products": ("k_split_products_cluster64.md", ["split.cu", "tc.cuh", "df.cuh", "internal.h"]),
     "split_backward": ("k_split_rowdot_cluster64.md", ["rowdot.cu", "tc.cuh", "df.cuh", "internal.h"]),
     "split_density": ("k_split_rowdot_cluster64.md", ["rowdot.cu", "tc.cuh", "df.cuh", "internal.h"]),
+    "split_gslice": ("k_gslice_cluster64.md", ["rowdot.cu", "tc.cuh", "df.cuh", "internal.h"]),
+    "basis_df": ("k_basis_df_cluster64.md", ["basis_df.cu", "df.cuh", "internal.h"]),
 }
 
 
