@@ -353,10 +353,11 @@ def main():
                     help="FP64-path steps timed after the split run for the speedup (0: skip)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="cluster64",
-                    choices=["cluster64", "water", "molecules", "cluster512", "slab"],
+                    choices=["cluster64", "water", "molecules", "cluster512", "slab", "small_slab"],
                     help="cluster64: the 64-atom cluster (default); molecules: 2,000 independent molecules "
                          "in one grid; cluster512: the 512-atom cluster of the adjoint configuration; slab: "
-                         "the 3,383-atom periodic slab")
+                         "the 3,383-atom periodic slab; small_slab: its density and batch sizes in a 304-atom "
+                         "cell (a profiling case of a few GB)")
     ap.add_argument("--cpu-stride", type=int, default=16, help="one-core sample of the cpu baseline")
     ap.add_argument("--cpu-stride-all", type=int, default=2, help="all-core sample of the cpu baseline")
     ap.add_argument("--ref-stride", type=int, default=7)
@@ -372,21 +373,22 @@ def main():
             print(f"source_sha256[{name}]: {kernel_source_hash(name)}")
         return
 
-    from workloads import cluster512, cluster64, molecule_batch, slab, water
+    from workloads import cluster512, cluster64, molecule_batch, slab, small_slab, water
     wl = {"cluster64": cluster64, "water": water, "molecules": molecule_batch, "cluster512": cluster512,
-          "slab": slab}[args.workload]()
-    big = args.workload in ("molecules", "cluster512", "slab")
+          "slab": slab, "small_slab": small_slab}[args.workload]()
+    big = args.workload in ("molecules", "cluster512", "slab", "small_slab")
     if args.workload == "slab" and args.steps == 60:
         args.steps = 3  # a step of the slab takes seconds
     # sample strides that keep the oracle's share of a run to seconds
     if big:
-        default_strides = {"molecules": (200, 20), "cluster512": (4000, 400), "slab": (40000, 0)}[args.workload]
+        default_strides = {"molecules": (200, 20), "cluster512": (4000, 400), "slab": (40000, 0),
+                           "small_slab": (4000, 0)}[args.workload]
         if args.cpu_stride == 16:
             args.cpu_stride = default_strides[0]
         if args.cpu_stride_all == 2:
             args.cpu_stride_all = default_strides[1]
     if args.impl == "reference":
-        if args.workload in ("cluster512", "slab"):
+        if args.workload in ("cluster512", "slab", "small_slab"):
             print(json.dumps({"impl": "reference", "unavailable": f"the oracle's FLOP count of the {wl.name} workload "
                               "needs its full grid (8 min of host time for the 512-atom cluster, hours for the "
                               "slab), beyond this arm's few-minute bound"}))
